@@ -1,0 +1,25 @@
+"""GB300-native exact modular matrix products for CKKS linear algebra.
+
+Python binding of the C-ABI library ``libmodpp.so`` (declared in
+``include/modpp.h``).  Every step of the hot path runs in the library's CUDA
+kernels; this package only marshals arguments (device pointers, sizes, the
+current CUDA stream) and allocates the caller-side workspace through PyTorch.
+
+The binding is loaded on first use of an API name, so ``synth`` (the seeded
+input generators) can be imported on machines without the compiled library.
+If the library is missing, every API call raises: there is no fallback.
+"""
+from __future__ import annotations
+
+_API_NAMES = (
+    "modpp_mm", "modpp_mm_grouped", "pc_mm", "pc_mv", "cc_mm", "plan_info",
+    "workspace_bytes", "last_status", "Path", "ModppError", "lib", "library_path",
+    "tile_config", "GroupedPlan",
+)
+
+
+def __getattr__(name):
+    if name in _API_NAMES:
+        from . import api
+        return getattr(api, name)
+    raise AttributeError(name)
