@@ -1,0 +1,186 @@
+/*
+ * modpp.h -- C ABI of the GB300 (sm_103a) Mod-PP-MM library.
+ *
+ * The library computes the exact modular matrix products to which
+ * "Fast Homomorphic Linear Algebra with BLAS" (Bae, Cheon, Hanrot, Park,
+ * Stehle; arXiv 2503.16080) reduces encrypted linear algebra:
+ *
+ *   Mod-PP-MM   C_j = U * A_j  mod q_j   for every RNS prime q_j
+ *
+ * (Sec. 5, notation ModPPMM_{q; d1, d2, d3}).  PC-MM and PC-Mv are two such
+ * products, one on the a-part and one on the b-part of the ciphertext matrix
+ * (Alg. 6 / Thm th:pcmm, written for the row format of Eq. mat_row_format).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - Matrices are row-major; leading dimensions are in elements.
+ * - Residue matrices are uint64 and canonical: every entry of A_j lies in
+ *   [0, q_j).  Outputs are canonical in [0, q_j).
+ * - U holds small signed integers in [-128, 127] (the integer-quantised
+ *   plaintext matrix), stored as int8 or as int32 (see modpp_u_kind).
+ * - Primes: odd, 3 <= q_j < 2^62.  They need not be distinct.
+ * - Every data pointer (U, A, B, C, outputs, workspace) is a DEVICE pointer
+ *   owned by the caller.  `primes_host` is a host array.  `stream` is a
+ *   cudaStream_t (NULL = legacy default stream).
+ * - The library never allocates device memory on the call path: scratch
+ *   space is the caller's workspace, sized by the matching *_workspace
+ *   query.  The workspace must be 256-byte aligned and must not be used by
+ *   two calls that may run concurrently.
+ * - Calls are asynchronous: they validate arguments on the host, enqueue
+ *   kernels on `stream` and return.  An argument error returns a negative
+ *   modpp_status before anything is enqueued.  A failure detected on the
+ *   device (a bounded wait that timed out) is recorded in the workspace's
+ *   status word and read back with modpp_status_read().
+ * - Output buffers must not overlap inputs.
+ */
+#ifndef MODPP_H
+#define MODPP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    MODPP_OK = 0,
+    MODPP_ERR_ARG = -1,         /* bad size, null pointer or leading dimension */
+    MODPP_ERR_PRIME = -2,       /* a prime is even, < 3 or >= 2^62 */
+    MODPP_ERR_WORKSPACE = -3,   /* workspace null, misaligned or too small */
+    MODPP_ERR_UNSUPPORTED = -4, /* valid request this build does not serve */
+    MODPP_ERR_CUDA = -5,        /* a CUDA runtime, driver or cuBLAS call failed */
+    MODPP_ERR_RANGE = -6,       /* reserved: input values outside their documented range */
+    MODPP_ERR_TIMEOUT = -7      /* a bounded device-side wait gave up (status word) */
+} modpp_status;
+
+/* Which arithmetic carries the products. */
+typedef enum {
+    /* Default. Exact small-integer digits on the sm_103a tensor cores
+     * (tcgen05.mma kind::f16, FP32 accumulation in TMEM, K split so every
+     * partial sum stays within the 2^24 exact-integer range of FP32), with
+     * a fused modular epilogue. */
+    MODPP_PATH_F16 = 0,
+    /* Strategy 1 of Sec. 6.1 (Lemma le:strategy1), as the paper ran it:
+     * base K = floor(sqrt(2^53/k)) signed digits, one binary64 GEMM (cuBLAS
+     * DGEMM) per digit pair, exact integer recombination mod q_j. */
+    MODPP_PATH_FP64 = 1,
+    /* Strategy 1 with the asymmetric base K_A = floor(2^53 / (k * 128))
+     * for the residue operand (U needs one digit because |U| <= 128). */
+    MODPP_PATH_FP64_TIGHT = 2
+} modpp_path;
+
+typedef enum {
+    MODPP_U_I8 = 0,  /* int8_t entries */
+    MODPP_U_I32 = 1  /* int32_t entries, values in [-128, 127] */
+} modpp_u_kind;
+
+/* Human-readable name of a modpp_status value (static string). */
+const char *modpp_status_string(int status);
+
+/* Version of this ABI: (major << 16) | minor. */
+int modpp_abi_version(void);
+
+/*
+ * Planning query (host only, no GPU needed).  For a product with inner
+ * dimension k modulo q on `path`, reports how the operands are split:
+ *   digits      number of residue digits (F16: ceil(bits(q)/10) balanced
+ *               10-bit digits; FP64: the Strategy 1 digit count k1)
+ *   digit_bits  F16: 10; FP64: floor(log2(base))
+ *   k_chunk     F16: inner-dimension chunk whose FP32 partial sums stay
+ *               exact (256); FP64: k (one DGEMM covers the whole k)
+ * Returns MODPP_OK or an error for invalid k or q.
+ */
+int modpp_plan_info(int64_t k, uint64_t q, int path, int *digits, int *digit_bits,
+                    int64_t *k_chunk);
+
+/*
+ * Workspace bytes for modpp_mm with these sizes (0 for invalid arguments).
+ */
+size_t modpp_mm_workspace(int64_t d, int64_t k, int64_t n, const uint64_t *primes_host, int P,
+                          int path);
+
+/*
+ * Mod-PP-MM over P primes (Sec. 5, ModPPMM; Thm th:pcmm):
+ *   C_j[r][c] = ( sum_t U[r][t] * A_j[t][c] ) mod q_j,   0 <= j < P.
+ *
+ *   U       d x k, kind `ukind`, leading dimension ldu >= k.
+ *   A       P matrices k x n; A_j starts at A + j*strideA, leading dim lda >= n.
+ *   C       P matrices d x n; C_j starts at C + j*strideC, leading dim ldc >= n.
+ *   primes_host  P primes (host memory).
+ *   P       1 <= P <= 32.
+ *   path    a modpp_path value.
+ *   ws, ws_bytes  workspace of at least modpp_mm_workspace(...) bytes.
+ * Sizes: 0 <= d, n < 2^31; 0 <= k <= 2^20.  k = 0 writes zeros.
+ * Returns MODPP_OK once the work is enqueued, or a negative modpp_status.
+ */
+int modpp_mm(int64_t d, int64_t k, int64_t n, const void *U, int ukind, int64_t ldu,
+             const uint64_t *A, int64_t lda, int64_t strideA, uint64_t *C, int64_t ldc,
+             int64_t strideC, const uint64_t *primes_host, int P, int path, void *ws,
+             size_t ws_bytes, void *stream);
+
+/*
+ * Workspace bytes for pc_mm / pc_mv with these sizes (0 for invalid arguments).
+ */
+size_t pc_mm_workspace(int64_t d, int64_t kct, int64_t N, const uint64_t *primes_host, int P,
+                       int path);
+
+/*
+ * PC-MM in the row format (Alg. 6 and Thm th:pcmm, transposed to the row
+ * identity A * Toep(s)^t + B = Delta*M of Eq. mat_row_format): row t of
+ * (A_j, B_j) is the RNS residue j of a ciphertext whose plaintext is row t
+ * of the kct x N message matrix.  Computes the two Mod-PP-MMs
+ *   Aout_j = U * A_j mod q_j,   Bout_j = U * B_j mod q_j,
+ * so that Aout * Toep(s)^t + Bout = U * (Delta*M + E): row r of the output
+ * encrypts row r of U*M under the same secret.  No rescale is applied.
+ *
+ *   U            d x kct int8, contiguous (ldu = kct).
+ *   A, B         [P][kct][N] contiguous residues.
+ *   Aout, Bout   [P][d][N] contiguous.
+ *   1 <= P <= 16.
+ */
+int pc_mm(int64_t d, int64_t kct, int64_t N, const int8_t *U, const uint64_t *A,
+          const uint64_t *B, uint64_t *Aout, uint64_t *Bout, const uint64_t *primes_host, int P,
+          int path, void *ws, size_t ws_bytes, void *stream);
+
+/*
+ * PC-Mv: the same pair of Mod-PP-MMs on a thin batch of `nvec` columns
+ * (Thm th:pcmm with a small d3; the CP-Mv remark of Sec. 5.1).  Arguments
+ * as pc_mm with N replaced by nvec.  The kernel streams U once per
+ * (prime, part) plane, which is the memory-bound regime.
+ */
+int pc_mv(int64_t d, int64_t kct, int64_t nvec, const int8_t *U, const uint64_t *A,
+          const uint64_t *B, uint64_t *Aout, uint64_t *Bout, const uint64_t *primes_host, int P,
+          int path, void *ws, size_t ws_bytes, void *stream);
+
+/*
+ * Kernel timing for measurement (no counterpart in the paper: instrumentation).
+ * While enabled, every launch of the kernels named by modpp_kernel_id is
+ * bracketed by a pair of CUDA events recorded on the launch's stream.
+ * modpp_profile_read() waits for the recorded events of one kernel, returns
+ * the sum of their elapsed times in milliseconds and the number of launches,
+ * and forgets them.  Enabling or disabling also forgets all records.
+ * Events are host-side driver objects; no device memory is allocated.
+ */
+typedef enum {
+    MODPP_KERNEL_GEMM = 0,   /* tensor-core digit GEMM + modular epilogue */
+    MODPP_KERNEL_SPLIT = 1,  /* residue -> f16 digit planes */
+    MODPP_KERNEL_U16 = 2     /* U -> f16 */
+} modpp_kernel_id;
+
+int modpp_profile_enable(int on);
+int modpp_profile_read(int kernel, double *total_ms, int64_t *launches);
+
+/*
+ * Waits for `stream`, reads and clears the device status word kept in the
+ * workspace `ws`.  Returns MODPP_OK, MODPP_ERR_TIMEOUT (a bounded device wait
+ * gave up; the kernel returned early and its outputs are unspecified) or
+ * MODPP_ERR_CUDA.
+ */
+int modpp_status_read(void *ws, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MODPP_H */

@@ -12,9 +12,9 @@ If the library is missing, every API call raises: there is no fallback.
 from __future__ import annotations
 
 _API_NAMES = (
-    "modpp_mm", "modpp_mm_grouped", "pc_mm", "pc_mv", "cc_mm", "plan_info",
-    "workspace_bytes", "last_status", "Path", "ModppError", "lib", "library_path",
-    "tile_config", "GroupedPlan",
+    "modpp_mm", "pc_mm", "pc_mv", "plan_info", "workspace_bytes", "last_status", "Path",
+    "ModppError", "lib", "library_path", "profile_enable", "profile_read", "KERNEL_GEMM",
+    "KERNEL_SPLIT", "KERNEL_U16",
 )
 
 

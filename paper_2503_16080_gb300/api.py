@@ -1,0 +1,260 @@
+"""ctypes binding of ``libmodpp.so`` (C ABI in ``include/modpp.h``).
+
+Argument marshalling only: tensors are passed as device pointers with their
+sizes and strides, the stream is PyTorch's current CUDA stream, and the
+caller-side workspace is a PyTorch allocation.  All arithmetic runs in the
+library's CUDA kernels.  If the library was not built, every call raises
+``ModppError``; there is no other implementation to fall back to.
+"""
+from __future__ import annotations
+
+import ctypes
+import enum
+import os
+import threading
+from typing import Sequence
+
+import numpy as np
+import torch
+
+from .build import LIB_PATH
+
+__all__ = ["ModppError", "Path", "lib", "library_path", "modpp_mm", "pc_mm", "pc_mv",
+           "plan_info", "workspace_bytes", "last_status"]
+
+
+class ModppError(RuntimeError):
+    """A library call returned a negative modpp_status."""
+
+    def __init__(self, code: int, what: str):
+        self.code = code
+        super().__init__(f"{what}: {_status_string(code)} ({code})")
+
+
+class Path(enum.IntEnum):
+    F16 = 0          # exact f16 digits on tcgen05 (default)
+    FP64 = 1         # Strategy 1, base floor(sqrt(2^53/k)), cuBLAS DGEMM
+    FP64_TIGHT = 2   # Strategy 1 with the asymmetric base floor(2^53/(128k))
+
+
+_PATH_NAMES = {"f16": Path.F16, "fp64": Path.FP64, "fp64_tight": Path.FP64_TIGHT}
+
+_lib = None
+_lib_lock = threading.Lock()
+
+
+def library_path() -> str:
+    return LIB_PATH
+
+
+def lib() -> ctypes.CDLL:
+    """Load the compiled library (raises ModppError if it is missing)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    with _lib_lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(LIB_PATH):
+            raise ModppError(-5, f"libmodpp.so not built at {LIB_PATH} "
+                                 "(run __graft_entry__.build())")
+        L = ctypes.CDLL(LIB_PATH)
+        P, I64, I, U64, SZ = (ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_uint64,
+                              ctypes.c_size_t)
+        L.modpp_status_string.argtypes = [I]
+        L.modpp_status_string.restype = ctypes.c_char_p
+        L.modpp_abi_version.restype = I
+        L.modpp_plan_info.argtypes = [I64, U64, I, P, P, P]
+        L.modpp_mm_workspace.argtypes = [I64, I64, I64, P, I, I]
+        L.modpp_mm_workspace.restype = SZ
+        L.modpp_mm.argtypes = [I64, I64, I64, P, I, I64, P, I64, I64, P, I64, I64, P, I, I, P, SZ, P]
+        L.pc_mm_workspace.argtypes = [I64, I64, I64, P, I, I]
+        L.pc_mm_workspace.restype = SZ
+        L.pc_mm.argtypes = [I64, I64, I64, P, P, P, P, P, P, I, I, P, SZ, P]
+        L.pc_mv.argtypes = [I64, I64, I64, P, P, P, P, P, P, I, I, P, SZ, P]
+        L.modpp_status_read.argtypes = [P, P]
+        L.modpp_profile_enable.argtypes = [I]
+        L.modpp_profile_read.argtypes = [I, P, P]
+        _lib = L
+        return L
+
+
+def _status_string(code: int) -> str:
+    try:
+        return lib().modpp_status_string(int(code)).decode()
+    except ModppError:
+        return "library not loaded"
+
+
+def _path(path) -> int:
+    if isinstance(path, str):
+        return int(_PATH_NAMES[path.lower()])
+    return int(Path(path))
+
+
+def _primes_arr(primes: Sequence[int]) -> np.ndarray:
+    arr = np.ascontiguousarray([int(q) for q in primes], dtype=np.uint64)
+    return arr
+
+
+def _stream_handle(stream) -> int:
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return int(s.cuda_stream)
+
+
+# Grow-only workspace cache, one per device.  Calls that share a device and
+# run on different streams must pass their own workspace.
+_ws_cache: dict[int, torch.Tensor] = {}
+
+
+def _workspace(nbytes: int, device: torch.device, workspace: torch.Tensor | None) -> tuple[int, int]:
+    if workspace is not None:
+        ptr = workspace.data_ptr()
+        if workspace.device != device or ptr % 256 or workspace.numel() * workspace.element_size() < nbytes:
+            raise ValueError("workspace: wrong device, misaligned or too small")
+        return ptr, workspace.numel() * workspace.element_size()
+    idx = device.index if device.index is not None else torch.cuda.current_device()
+    buf = _ws_cache.get(idx)
+    if buf is None or buf.numel() < nbytes:
+        _ws_cache.pop(idx, None)
+        buf = torch.empty(max(nbytes, 1 << 20), dtype=torch.uint8, device=device)
+        _ws_cache[idx] = buf
+    assert buf.data_ptr() % 256 == 0
+    return buf.data_ptr(), buf.numel()
+
+
+def _check(rc: int, what: str) -> None:
+    if rc != 0:
+        raise ModppError(rc, what)
+
+
+def plan_info(k: int, q: int, path="f16") -> dict:
+    """Digit split chosen for inner dimension k and prime q (host only)."""
+    dg, bits, chunk = ctypes.c_int(), ctypes.c_int(), ctypes.c_int64()
+    _check(lib().modpp_plan_info(int(k), int(q), _path(path), ctypes.byref(dg), ctypes.byref(bits),
+                                 ctypes.byref(chunk)), "modpp_plan_info")
+    return {"digits": dg.value, "digit_bits": bits.value, "k_chunk": chunk.value}
+
+
+def workspace_bytes(d: int, k: int, n: int, primes: Sequence[int], path="f16",
+                    kind: str = "modpp_mm") -> int:
+    pr = _primes_arr(primes)
+    fn = lib().modpp_mm_workspace if kind == "modpp_mm" else lib().pc_mm_workspace
+    return int(fn(int(d), int(k), int(n), pr.ctypes.data, len(pr), _path(path)))
+
+
+def last_status(device: torch.device | int | None = None, stream=None,
+                workspace: torch.Tensor | None = None) -> int:
+    """Device status word of the last call that used this workspace (syncs the stream)."""
+    if workspace is None:
+        dev = torch.device("cuda", device if isinstance(device, int) else
+                           (device.index if device is not None and device.index is not None
+                            else torch.cuda.current_device()))
+        workspace = _ws_cache.get(dev.index)
+        if workspace is None:
+            return 0
+    return int(lib().modpp_status_read(ctypes.c_void_p(workspace.data_ptr()),
+                                       ctypes.c_void_p(_stream_handle(stream))))
+
+
+KERNEL_GEMM, KERNEL_SPLIT, KERNEL_U16 = 0, 1, 2
+
+
+def profile_enable(on: bool) -> None:
+    """Bracket every launch of the library's kernels with CUDA events (measurement)."""
+    _check(lib().modpp_profile_enable(1 if on else 0), "modpp_profile_enable")
+
+
+def profile_read(kernel: int) -> tuple[float, int]:
+    """(total milliseconds, launches) recorded for `kernel` since the last read."""
+    ms, n = ctypes.c_double(), ctypes.c_int64()
+    _check(lib().modpp_profile_read(int(kernel), ctypes.byref(ms), ctypes.byref(n)),
+           "modpp_profile_read")
+    return ms.value, n.value
+
+
+def _check_residues(A: torch.Tensor, name: str) -> None:
+    if not A.is_cuda or A.dtype != torch.uint64:
+        raise TypeError(f"{name} must be a CUDA uint64 tensor")
+
+
+def modpp_mm(U: torch.Tensor, A: torch.Tensor, primes: Sequence[int], *, path="f16",
+             out: torch.Tensor | None = None, stream=None,
+             workspace: torch.Tensor | None = None) -> torch.Tensor:
+    """C[j] = U @ A[j] mod primes[j] (exact), on the GPU.
+
+    U: (d, k) int8 or int32 CUDA tensor with values in [-128, 127], unit stride along k.
+    A: (P, k, n) (or (k, n)) uint64 CUDA tensor of canonical residues, unit stride along n.
+    Returns (P, d, n) (or (d, n)) uint64.
+    """
+    squeeze = A.dim() == 2
+    A3 = A.unsqueeze(0) if squeeze else A
+    _check_residues(A3, "A")
+    if not U.is_cuda or U.dtype not in (torch.int8, torch.int32) or U.dim() != 2:
+        raise TypeError("U must be a 2-D CUDA int8 or int32 tensor")
+    if U.stride(1) != 1 or A3.stride(2) != 1:
+        raise ValueError("U and A need unit stride along their last dimension")
+    P, k, n = A3.shape
+    d = U.shape[0]
+    if U.shape[1] != k or len(primes) != P:
+        raise ValueError("shape mismatch between U, A and primes")
+    if out is None:
+        out = torch.empty((P, d, n), dtype=torch.uint64, device=A3.device)
+    out3 = out.unsqueeze(0) if out.dim() == 2 else out
+    if out3.shape != (P, d, n) or out3.stride(2) != 1:
+        raise ValueError("out must be (P, d, n) with unit stride along n")
+    pr = _primes_arr(primes)
+    p = _path(path)
+    need = int(lib().modpp_mm_workspace(d, k, n, pr.ctypes.data, P, p))
+    if need == 0:
+        raise ModppError(-1, "modpp_mm_workspace")
+    ws_ptr, ws_len = _workspace(need, A3.device, workspace)
+    ukind = 0 if U.dtype == torch.int8 else 1
+    rc = lib().modpp_mm(d, k, n, U.data_ptr(), ukind, U.stride(0), A3.data_ptr(), A3.stride(1),
+                        A3.stride(0), out3.data_ptr(), out3.stride(1), out3.stride(0),
+                        pr.ctypes.data, P, p, ws_ptr, ws_len, _stream_handle(stream))
+    _check(rc, "modpp_mm")
+    return out3[0] if squeeze else out3
+
+
+def _pc(fn_name: str, U, A, B, primes, path, out, stream, workspace):
+    _check_residues(A, "A")
+    _check_residues(B, "B")
+    if not U.is_cuda or U.dtype != torch.int8 or U.dim() != 2 or not U.is_contiguous():
+        raise TypeError("U must be a contiguous 2-D CUDA int8 tensor")
+    if not (A.is_contiguous() and B.is_contiguous()) or A.shape != B.shape or A.dim() != 3:
+        raise ValueError("A and B must be contiguous (P, kct, N) tensors of equal shape")
+    P, kct, N = A.shape
+    d = U.shape[0]
+    if U.shape[1] != kct or len(primes) != P:
+        raise ValueError("shape mismatch between U, A/B and primes")
+    if out is None:
+        out = (torch.empty((P, d, N), dtype=torch.uint64, device=A.device),
+               torch.empty((P, d, N), dtype=torch.uint64, device=A.device))
+    Aout, Bout = out
+    if not (Aout.is_contiguous() and Bout.is_contiguous()) or Aout.shape != (P, d, N) \
+            or Bout.shape != (P, d, N):
+        raise ValueError("outputs must be contiguous (P, d, N) tensors")
+    pr = _primes_arr(primes)
+    p = _path(path)
+    need = int(lib().pc_mm_workspace(d, kct, N, pr.ctypes.data, P, p))
+    if need == 0:
+        raise ModppError(-1, "pc_mm_workspace")
+    ws_ptr, ws_len = _workspace(need, A.device, workspace)
+    rc = getattr(lib(), fn_name)(d, kct, N, U.data_ptr(), A.data_ptr(), B.data_ptr(),
+                                 Aout.data_ptr(), Bout.data_ptr(), pr.ctypes.data, P, p, ws_ptr,
+                                 ws_len, _stream_handle(stream))
+    _check(rc, fn_name)
+    return Aout, Bout
+
+
+def pc_mm(U: torch.Tensor, A: torch.Tensor, B: torch.Tensor, primes: Sequence[int], *,
+          path="f16", out=None, stream=None, workspace=None):
+    """Row-format PC-MM: (U @ A[j] mod q_j, U @ B[j] mod q_j) for every prime."""
+    return _pc("pc_mm", U, A, B, primes, path, out, stream, workspace)
+
+
+def pc_mv(U: torch.Tensor, A: torch.Tensor, B: torch.Tensor, primes: Sequence[int], *,
+          path="f16", out=None, stream=None, workspace=None):
+    """PC-Mv on a thin batch: same products as pc_mm with a small column count."""
+    return _pc("pc_mv", U, A, B, primes, path, out, stream, workspace)

@@ -1,0 +1,40 @@
+// Device-side modular arithmetic on 64-bit residues.
+//   Barrett reduction (P. Barrett, CRYPTO 1986) with mu = floor(2^64/q);
+//   Shoup's precomputed-quotient multiplication (V. Shoup, NTL) for a fixed
+//   multiplier w with w' = floor(w * 2^64 / q).
+// Moduli satisfy 2 < q < 2^62, so 3q fits in 64 bits.
+#pragma once
+#include <cstdint>
+
+namespace modpp {
+
+// t mod q for any 64-bit t.  floor(t*mu/2^64) underestimates floor(t/q) by
+// at most 2, so at most two corrections follow.
+__device__ __forceinline__ uint64_t barrett_u64(uint64_t t, uint64_t q, uint64_t mu) {
+    uint64_t r = t - __umul64hi(t, mu) * q;
+    if (r >= q) r -= q;
+    if (r >= q) r -= q;
+    return r;
+}
+
+// Canonical residue of a signed 64-bit value.
+__device__ __forceinline__ uint64_t smod_i64(int64_t x, uint64_t q, uint64_t mu) {
+    const uint64_t mag = x < 0 ? static_cast<uint64_t>(-(x + 1)) + 1u : static_cast<uint64_t>(x);
+    const uint64_t r = barrett_u64(mag, q, mu);
+    return (x < 0 && r != 0) ? q - r : r;
+}
+
+// a * w mod q for a < 2^64 and w < q, given ws = floor(w * 2^64 / q).
+__device__ __forceinline__ uint64_t shoup_mulmod(uint64_t a, uint64_t w, uint64_t ws, uint64_t q) {
+    const uint64_t qh = __umul64hi(a, ws);
+    uint64_t r = a * w - qh * q;
+    if (r >= q) r -= q;
+    return r;
+}
+
+__device__ __forceinline__ uint64_t add_mod(uint64_t a, uint64_t b, uint64_t q) {
+    const uint64_t s = a + b;
+    return s >= q ? s - q : s;
+}
+
+}  // namespace modpp

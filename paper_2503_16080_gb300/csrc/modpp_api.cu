@@ -1,0 +1,532 @@
+// Host side of the C ABI declared in include/modpp.h: argument checks,
+// workspace layout, TMA descriptors, and the kernel / cuBLAS sequence of each
+// path.  Nothing here allocates device memory except the cuBLAS handle that
+// the FP64 path creates once per device on first use.
+#include <cublas_v2.h>
+#include <cuda.h>
+#include <cuda_runtime.h>
+
+#include <cstdlib>
+#include <cstring>
+#include <mutex>
+#include <vector>
+
+#include "modpp.h"
+#include "modpp_internal.h"
+
+using namespace modpp;
+
+namespace {
+
+constexpr size_t kAlign = 256;
+constexpr size_t kHeaderBytes = 256;        // status word + reserve
+constexpr size_t kCublasWsBytes = 32u << 20;  // cuBLAS scratch inside the workspace
+constexpr int64_t kMaxK = int64_t(1) << 20;
+constexpr int kMaxDevices = 64;
+
+size_t align_up(size_t x) { return (x + kAlign - 1) & ~(kAlign - 1); }
+
+bool prime_ok(uint64_t q) { return q >= 3 && (q & 1u) && q < (uint64_t(1) << 62); }
+
+int check_primes(const uint64_t *primes, int P, int max_planes) {
+    if (P < 1 || P > max_planes || primes == nullptr) return MODPP_ERR_ARG;
+    for (int j = 0; j < P; ++j)
+        if (!prime_ok(primes[j])) return MODPP_ERR_PRIME;
+    return MODPP_OK;
+}
+
+int check_sizes(int64_t d, int64_t k, int64_t n) {
+    if (d < 0 || k < 0 || n < 0) return MODPP_ERR_ARG;
+    if (d >= (int64_t(1) << 31) || n >= (int64_t(1) << 31) || k > kMaxK) return MODPP_ERR_ARG;
+    return MODPP_OK;
+}
+
+bool path_ok(int path) {
+    return path == MODPP_PATH_F16 || path == MODPP_PATH_FP64 || path == MODPP_PATH_FP64_TIGHT;
+}
+
+struct PlaneIn {
+    const uint64_t *A;
+    int64_t lda;
+    uint64_t q;
+    uint64_t *C;
+    int64_t ldc;
+};
+
+// ------------------------------------------------------------ f16 layout
+struct F16Layout {
+    int L = 0;
+    int64_t kp = 0, n_blocks = 0, rows = 0;
+    size_t off_u16 = 0, off_d = 0, total = 0;
+};
+
+F16Layout f16_layout(int64_t d, int64_t k, int64_t n, const uint64_t *qs, int planes) {
+    F16Layout lay;
+    for (int i = 0; i < planes; ++i) {
+        const int l = f16_digit_count(qs[i]);
+        if (l > lay.L) lay.L = l;
+    }
+    lay.kp = (k + 7) / 8 * 8;
+    lay.n_blocks = (n + kNC - 1) / kNC;
+    lay.rows = static_cast<int64_t>(planes) * lay.n_blocks * lay.L * kNC;
+    lay.off_u16 = kHeaderBytes;
+    lay.off_d = lay.off_u16 + align_up(static_cast<size_t>(d) * lay.kp * 2);
+    lay.total = lay.off_d + align_up(static_cast<size_t>(lay.rows) * lay.kp * 2);
+    return lay;
+}
+
+// ------------------------------------------------------------ fp64 layout
+struct Fp64Layout {
+    uint64_t base = 0;
+    int k1max = 0;
+    size_t off_u = 0, off_a = 0, off_p = 0, off_cublas = 0, total = 0;
+};
+
+uint64_t isqrt_u64(uint64_t x) {
+    uint64_t r = 0;
+    for (int b = 31; b >= 0; --b) {
+        const uint64_t c = r | (uint64_t(1) << b);
+        if (static_cast<unsigned __int128>(c) * c <= x) r = c;
+    }
+    return r;
+}
+
+// Lemma le:strategy1: K = floor(sqrt(2^53 / d2)).  The tight variant takes
+// the largest base with d2 * 128 * (K - 1) < 2^53 for the residue operand,
+// since |U| <= 128 needs a single digit.
+uint64_t fp64_base(int64_t k, bool tight) {
+    const uint64_t two53 = uint64_t(1) << 53;
+    if (tight) return two53 / (static_cast<uint64_t>(k) * 128u);
+    return isqrt_u64(two53 / static_cast<uint64_t>(k));
+}
+
+// Smallest count c with K^c > theta (the decomposition needs |r| < K^c).
+int fp64_digit_count(uint64_t theta, uint64_t K) {
+    int c = 1;
+    unsigned __int128 p = K;
+    while (p <= theta) {
+        p *= K;
+        ++c;
+    }
+    return c;
+}
+
+Fp64Layout fp64_layout(int64_t d, int64_t k, int64_t n, const uint64_t *qs, int planes,
+                       bool tight) {
+    Fp64Layout lay;
+    lay.base = fp64_base(k > 0 ? k : 1, tight);
+    for (int i = 0; i < planes; ++i) {
+        const int c = fp64_digit_count((qs[i] - 1) / 2, lay.base);
+        if (c > lay.k1max) lay.k1max = c;
+    }
+    lay.off_u = kHeaderBytes;
+    lay.off_a = lay.off_u + align_up(static_cast<size_t>(d) * k * 8);
+    lay.off_p = lay.off_a + align_up(static_cast<size_t>(k) * lay.k1max * n * 8);
+    lay.off_cublas = lay.off_p + align_up(static_cast<size_t>(d) * lay.k1max * n * 8);
+    lay.total = lay.off_cublas + kCublasWsBytes;
+    return lay;
+}
+
+// ------------------------------------------------------------ device state
+int device_sms() {
+    static int cache[kMaxDevices] = {0};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return 0;
+    if (cache[dev] == 0) {
+        int v = 0;
+        if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
+        cache[dev] = v;
+    }
+    return cache[dev];
+}
+
+uint64_t wait_limit_ns() {
+    static uint64_t v = [] {
+        const char *e = std::getenv("MODPP_WAIT_LIMIT_MS");
+        long ms = e ? std::atol(e) : 2000;
+        if (ms <= 0) ms = 2000;
+        return static_cast<uint64_t>(ms) * 1000000ull;
+    }();
+    return v;
+}
+
+using EncodeTiledFn = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *,
+                                   const cuuint64_t *, const cuuint64_t *, const cuuint32_t *,
+                                   const cuuint32_t *, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                   CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_fn() {
+    static EncodeTiledFn fn = [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult r{};
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                             &r) != cudaSuccess ||
+            r != cudaDriverEntryPointSuccess)
+            return static_cast<EncodeTiledFn>(nullptr);
+        return reinterpret_cast<EncodeTiledFn>(p);
+    }();
+    return fn;
+}
+
+// 2-D f16 tensor [outer][inner] with 128-byte swizzled boxes of
+// box_inner x box_outer (box_inner * 2 = 128 bytes).  Elements outside the
+// tensor read as zero.
+bool make_map_f16(CUtensorMap *m, const void *base, uint64_t inner, uint64_t outer,
+                  uint32_t box_inner, uint32_t box_outer) {
+    EncodeTiledFn fn = encode_fn();
+    if (!fn) return false;
+    cuuint64_t dims[2] = {inner, outer};
+    cuuint64_t strides[1] = {inner * 2};
+    cuuint32_t box[2] = {box_inner, box_outer};
+    cuuint32_t estr[2] = {1, 1};
+    return fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2, const_cast<void *>(base), dims, strides, box,
+              estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+              CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) ==
+           CUDA_SUCCESS;
+}
+
+int cuda_status(cudaError_t e) { return e == cudaSuccess ? MODPP_OK : MODPP_ERR_CUDA; }
+
+// ------------------------------------------------------------ kernel timing
+struct EventPair {
+    cudaEvent_t start = nullptr, stop = nullptr;
+};
+struct KernelTimer {
+    std::vector<EventPair> pool;
+    size_t used = 0;
+};
+constexpr int kTimedKernels = 3;
+std::mutex g_prof_mu;
+bool g_prof_on = false;
+KernelTimer g_timers[kTimedKernels];
+
+// Records the start event of a timed launch; returns the pair to close, or null.
+EventPair *timer_begin(int kernel, cudaStream_t st) {
+    if (!g_prof_on) return nullptr;
+    std::lock_guard<std::mutex> lock(g_prof_mu);
+    KernelTimer &t = g_timers[kernel];
+    if (t.used == t.pool.size()) {
+        EventPair e;
+        if (cudaEventCreate(&e.start) != cudaSuccess || cudaEventCreate(&e.stop) != cudaSuccess)
+            return nullptr;
+        t.pool.push_back(e);
+    }
+    EventPair *e = &t.pool[t.used++];
+    if (cudaEventRecord(e->start, st) != cudaSuccess) return nullptr;
+    return e;
+}
+void timer_end(EventPair *e, cudaStream_t st) {
+    if (e) cudaEventRecord(e->stop, st);
+}
+
+int zero_outputs(int64_t d, int64_t n, const PlaneIn *pl, int planes, cudaStream_t st) {
+    for (int i = 0; i < planes; ++i) {
+        if (d == 0 || n == 0) continue;
+        cudaError_t e = cudaMemset2DAsync(pl[i].C, static_cast<size_t>(pl[i].ldc) * 8, 0,
+                                          static_cast<size_t>(n) * 8, static_cast<size_t>(d), st);
+        if (e != cudaSuccess) return MODPP_ERR_CUDA;
+    }
+    return MODPP_OK;
+}
+
+// ------------------------------------------------------------ f16 path
+int run_f16(int64_t d, int64_t k, int64_t n, const void *U, int ukind, int64_t ldu,
+            const PlaneIn *pl, int planes, void *ws, size_t ws_bytes, cudaStream_t st) {
+    uint64_t qs[kMaxPlanes];
+    for (int i = 0; i < planes; ++i) qs[i] = pl[i].q;
+    const F16Layout lay = f16_layout(d, k, n, qs, planes);
+    if (ws_bytes < lay.total) return MODPP_ERR_WORKSPACE;
+    if (lay.rows >= (int64_t(1) << 31)) return MODPP_ERR_UNSUPPORTED;
+    uint8_t *w = static_cast<uint8_t *>(ws);
+    int *status = reinterpret_cast<int *>(w);
+    if (cudaMemsetAsync(status, 0, sizeof(int), st) != cudaSuccess) return MODPP_ERR_CUDA;
+    if (d == 0 || n == 0) return MODPP_OK;
+    if (k == 0) return zero_outputs(d, n, pl, planes, st);
+
+    __half *U16 = reinterpret_cast<__half *>(w + lay.off_u16);
+    __half *D = reinterpret_cast<__half *>(w + lay.off_d);
+    EventPair *ev = timer_begin(MODPP_KERNEL_U16, st);
+    int rc = cuda_status(launch_u_to_f16(U, ukind, ldu, static_cast<int>(d), static_cast<int>(k),
+                                         static_cast<int>(lay.kp), U16, st));
+    timer_end(ev, st);
+    if (rc) return rc;
+
+    SplitParams sp{};
+    sp.k = static_cast<int>(k);
+    sp.n = static_cast<int>(n);
+    sp.kp = static_cast<int>(lay.kp);
+    sp.n_blocks = static_cast<int>(lay.n_blocks);
+    sp.planes = planes;
+    sp.digits = lay.L;
+    sp.D = D;
+    const uint64_t thresh = f16_lift_threshold(lay.L);
+    for (int i = 0; i < planes; ++i) sp.sp[i] = SplitPlane{pl[i].A, pl[i].lda, pl[i].q, thresh};
+    ev = timer_begin(MODPP_KERNEL_SPLIT, st);
+    rc = cuda_status(launch_split_digits(sp, st));
+    timer_end(ev, st);
+    if (rc) return rc;
+
+    CUtensorMap tmU, tmD;
+    if (!make_map_f16(&tmU, U16, static_cast<uint64_t>(lay.kp), static_cast<uint64_t>(d), kBK, kBM))
+        return MODPP_ERR_CUDA;
+    if (!make_map_f16(&tmD, D, static_cast<uint64_t>(lay.kp), static_cast<uint64_t>(lay.rows), kBK,
+                      static_cast<uint32_t>(lay.L * kNC)))
+        return MODPP_ERR_CUDA;
+
+    GemmParams gp{};
+    gp.d = static_cast<int>(d);
+    gp.n = static_cast<int>(n);
+    gp.k = static_cast<int>(k);
+    gp.m_blocks = static_cast<int>((d + kBM - 1) / kBM);
+    gp.n_blocks = static_cast<int>(lay.n_blocks);
+    gp.planes = planes;
+    gp.kb_total = static_cast<int>((k + kBK - 1) / kBK);
+    const int64_t tiles = static_cast<int64_t>(gp.m_blocks) * gp.n_blocks * planes;
+    if (tiles >= (int64_t(1) << 31)) return MODPP_ERR_UNSUPPORTED;
+    gp.num_tiles = static_cast<int>(tiles);
+    gp.status = status;
+    gp.timeout_ns = wait_limit_ns();
+    for (int i = 0; i < planes; ++i) gp.pc[i] = make_plane_const(pl[i].q, pl[i].C, pl[i].ldc);
+    const int sms = device_sms();
+    if (sms <= 0) return MODPP_ERR_CUDA;
+    ev = timer_begin(MODPP_KERNEL_GEMM, st);
+    rc = cuda_status(launch_gemm_f16(tmU, tmD, gp, lay.L, sms, st));
+    timer_end(ev, st);
+    return rc;
+}
+
+// ------------------------------------------------------------ fp64 path
+std::mutex g_cublas_mu;
+cublasHandle_t g_cublas[kMaxDevices] = {nullptr};
+
+int run_fp64(int64_t d, int64_t k, int64_t n, const void *U, int ukind, int64_t ldu,
+             const PlaneIn *pl, int planes, void *ws, size_t ws_bytes, cudaStream_t st,
+             bool tight) {
+    uint64_t qs[kMaxPlanes];
+    for (int i = 0; i < planes; ++i) qs[i] = pl[i].q;
+    const Fp64Layout lay = fp64_layout(d, k, n, qs, planes, tight);
+    if (ws_bytes < lay.total) return MODPP_ERR_WORKSPACE;
+    if (lay.k1max > 8) return MODPP_ERR_UNSUPPORTED;
+    uint8_t *w = static_cast<uint8_t *>(ws);
+    int *status = reinterpret_cast<int *>(w);
+    if (cudaMemsetAsync(status, 0, sizeof(int), st) != cudaSuccess) return MODPP_ERR_CUDA;
+    if (d == 0 || n == 0) return MODPP_OK;
+    if (k == 0) return zero_outputs(d, n, pl, planes, st);
+
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev >= kMaxDevices) return MODPP_ERR_CUDA;
+    std::lock_guard<std::mutex> lock(g_cublas_mu);
+    if (!g_cublas[dev] && cublasCreate(&g_cublas[dev]) != CUBLAS_STATUS_SUCCESS)
+        return MODPP_ERR_CUDA;
+    cublasHandle_t h = g_cublas[dev];
+    if (cublasSetStream(h, st) != CUBLAS_STATUS_SUCCESS ||
+        cublasSetWorkspace(h, w + lay.off_cublas, kCublasWsBytes) != CUBLAS_STATUS_SUCCESS ||
+        cublasSetMathMode(h, CUBLAS_DEFAULT_MATH) != CUBLAS_STATUS_SUCCESS)
+        return MODPP_ERR_CUDA;
+
+    double *Ud = reinterpret_cast<double *>(w + lay.off_u);
+    double *Ad = reinterpret_cast<double *>(w + lay.off_a);
+    double *Pd = reinterpret_cast<double *>(w + lay.off_p);
+    int rc = cuda_status(
+        launch_u_to_f64(U, ukind, ldu, static_cast<int>(d), static_cast<int>(k), Ud, st));
+    if (rc) return rc;
+    for (int i = 0; i < planes; ++i) {
+        const uint64_t q = pl[i].q;
+        const int digits = fp64_digit_count((q - 1) / 2, lay.base);
+        Fp64SplitParams sp{pl[i].A, pl[i].lda, static_cast<int>(k), static_cast<int>(n), digits, q,
+                           lay.base, Ad};
+        rc = cuda_status(launch_fp64_split(sp, st));
+        if (rc) return rc;
+        // Row-major P (d x digits*n) = U (d x k) * Adig (k x digits*n), issued
+        // column-major as P^T = Adig^T * U^T.
+        const double one = 1.0, zero = 0.0;
+        const int m = digits * static_cast<int>(n);
+        if (cublasDgemm(h, CUBLAS_OP_N, CUBLAS_OP_N, m, static_cast<int>(d), static_cast<int>(k),
+                        &one, Ad, m, Ud, static_cast<int>(k), &zero, Pd, m) != CUBLAS_STATUS_SUCCESS)
+            return MODPP_ERR_CUDA;
+        Fp64RecombineParams rp{};
+        rp.P = Pd;
+        rp.d = static_cast<int>(d);
+        rp.n = static_cast<int>(n);
+        rp.digits = digits;
+        rp.q = q;
+        rp.mu = host_barrett_mu(q);
+        uint64_t pk = 1 % q;
+        const uint64_t Kq = lay.base % q;
+        for (int t = 0; t < digits; ++t) {
+            rp.powK[t] = pk;
+            rp.powKs[t] = host_shoup(pk, q);
+            pk = host_mulmod(pk, Kq, q);
+        }
+        rp.C = pl[i].C;
+        rp.ldc = pl[i].ldc;
+        rc = cuda_status(launch_fp64_recombine(rp, st));
+        if (rc) return rc;
+    }
+    return MODPP_OK;
+}
+
+size_t layout_bytes(int64_t d, int64_t k, int64_t n, const uint64_t *qs, int planes, int path) {
+    if (path == MODPP_PATH_F16) return f16_layout(d, k, n, qs, planes).total;
+    return fp64_layout(d, k, n, qs, planes, path == MODPP_PATH_FP64_TIGHT).total;
+}
+
+int dispatch(int64_t d, int64_t k, int64_t n, const void *U, int ukind, int64_t ldu,
+             const PlaneIn *pl, int planes, int path, void *ws, size_t ws_bytes, void *stream) {
+    if (ws == nullptr || (reinterpret_cast<uintptr_t>(ws) & (kAlign - 1)) != 0)
+        return MODPP_ERR_WORKSPACE;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (path == MODPP_PATH_F16) return run_f16(d, k, n, U, ukind, ldu, pl, planes, ws, ws_bytes, st);
+    return run_fp64(d, k, n, U, ukind, ldu, pl, planes, ws, ws_bytes, st,
+                    path == MODPP_PATH_FP64_TIGHT);
+}
+
+int pc_common(int64_t d, int64_t kct, int64_t N, const int8_t *U, const uint64_t *A,
+              const uint64_t *B, uint64_t *Aout, uint64_t *Bout, const uint64_t *primes, int P,
+              int path, void *ws, size_t ws_bytes, void *stream) {
+    int rc = check_sizes(d, kct, N);
+    if (rc) return rc;
+    rc = check_primes(primes, P, kMaxPlanes / 2);
+    if (rc) return rc;
+    if (!path_ok(path)) return MODPP_ERR_ARG;
+    const bool work = d > 0 && N > 0;
+    if (work && (Aout == nullptr || Bout == nullptr)) return MODPP_ERR_ARG;
+    if (work && kct > 0 && (U == nullptr || A == nullptr || B == nullptr)) return MODPP_ERR_ARG;
+    PlaneIn pl[kMaxPlanes];
+    for (int j = 0; j < P; ++j) {
+        pl[j] = PlaneIn{A + static_cast<int64_t>(j) * kct * N, N, primes[j],
+                        Aout + static_cast<int64_t>(j) * d * N, N};
+        pl[P + j] = PlaneIn{B + static_cast<int64_t>(j) * kct * N, N, primes[j],
+                            Bout + static_cast<int64_t>(j) * d * N, N};
+    }
+    return dispatch(d, kct, N, U, MODPP_U_I8, kct, pl, 2 * P, path, ws, ws_bytes, stream);
+}
+
+}  // namespace
+
+// ====================================================================== ABI
+extern "C" {
+
+const char *modpp_status_string(int status) {
+    switch (status) {
+        case MODPP_OK: return "MODPP_OK";
+        case MODPP_ERR_ARG: return "MODPP_ERR_ARG: invalid size, pointer or leading dimension";
+        case MODPP_ERR_PRIME: return "MODPP_ERR_PRIME: prime must be odd, >= 3 and < 2^62";
+        case MODPP_ERR_WORKSPACE: return "MODPP_ERR_WORKSPACE: workspace null, misaligned or too small";
+        case MODPP_ERR_UNSUPPORTED: return "MODPP_ERR_UNSUPPORTED: request outside this build's limits";
+        case MODPP_ERR_CUDA: return "MODPP_ERR_CUDA: a CUDA, driver or cuBLAS call failed";
+        case MODPP_ERR_RANGE: return "MODPP_ERR_RANGE: input value outside its documented range";
+        case MODPP_ERR_TIMEOUT: return "MODPP_ERR_TIMEOUT: a bounded device wait gave up";
+        default: return "unknown modpp status";
+    }
+}
+
+int modpp_abi_version(void) { return (1 << 16) | 0; }
+
+int modpp_plan_info(int64_t k, uint64_t q, int path, int *digits, int *digit_bits,
+                    int64_t *k_chunk) {
+    if (k < 1 || k > kMaxK || !prime_ok(q) || !path_ok(path)) return MODPP_ERR_ARG;
+    int dg, bits;
+    int64_t chunk;
+    if (path == MODPP_PATH_F16) {
+        dg = f16_digit_count(q);
+        bits = kDigitBits;
+        chunk = kChunkK;
+    } else {
+        const uint64_t K = fp64_base(k, path == MODPP_PATH_FP64_TIGHT);
+        dg = fp64_digit_count((q - 1) / 2, K);
+        bits = bit_length(K) - 1;
+        chunk = k;
+    }
+    if (digits) *digits = dg;
+    if (digit_bits) *digit_bits = bits;
+    if (k_chunk) *k_chunk = chunk;
+    return MODPP_OK;
+}
+
+size_t modpp_mm_workspace(int64_t d, int64_t k, int64_t n, const uint64_t *primes_host, int P,
+                          int path) {
+    if (check_sizes(d, k, n) || check_primes(primes_host, P, kMaxPlanes) || !path_ok(path))
+        return 0;
+    return layout_bytes(d, k, n, primes_host, P, path);
+}
+
+int modpp_mm(int64_t d, int64_t k, int64_t n, const void *U, int ukind, int64_t ldu,
+             const uint64_t *A, int64_t lda, int64_t strideA, uint64_t *C, int64_t ldc,
+             int64_t strideC, const uint64_t *primes_host, int P, int path, void *ws,
+             size_t ws_bytes, void *stream) {
+    int rc = check_sizes(d, k, n);
+    if (rc) return rc;
+    rc = check_primes(primes_host, P, kMaxPlanes);
+    if (rc) return rc;
+    if (!path_ok(path) || (ukind != MODPP_U_I8 && ukind != MODPP_U_I32)) return MODPP_ERR_ARG;
+    const bool work = d > 0 && n > 0;
+    if (work && C == nullptr) return MODPP_ERR_ARG;
+    if (work && k > 0 && (U == nullptr || A == nullptr)) return MODPP_ERR_ARG;
+    if (ldu < k || lda < n || ldc < n) return MODPP_ERR_ARG;
+    if (P > 1 && (strideA < k * lda || strideC < d * ldc)) return MODPP_ERR_ARG;
+    PlaneIn pl[kMaxPlanes];
+    for (int j = 0; j < P; ++j)
+        pl[j] = PlaneIn{A + static_cast<int64_t>(j) * strideA, lda, primes_host[j],
+                        C + static_cast<int64_t>(j) * strideC, ldc};
+    return dispatch(d, k, n, U, ukind, ldu, pl, P, path, ws, ws_bytes, stream);
+}
+
+size_t pc_mm_workspace(int64_t d, int64_t kct, int64_t N, const uint64_t *primes_host, int P,
+                       int path) {
+    if (check_sizes(d, kct, N) || check_primes(primes_host, P, kMaxPlanes / 2) || !path_ok(path))
+        return 0;
+    uint64_t qs[kMaxPlanes];
+    for (int j = 0; j < P; ++j) qs[j] = qs[P + j] = primes_host[j];
+    return layout_bytes(d, kct, N, qs, 2 * P, path);
+}
+
+int pc_mm(int64_t d, int64_t kct, int64_t N, const int8_t *U, const uint64_t *A,
+          const uint64_t *B, uint64_t *Aout, uint64_t *Bout, const uint64_t *primes_host, int P,
+          int path, void *ws, size_t ws_bytes, void *stream) {
+    return pc_common(d, kct, N, U, A, B, Aout, Bout, primes_host, P, path, ws, ws_bytes, stream);
+}
+
+int pc_mv(int64_t d, int64_t kct, int64_t nvec, const int8_t *U, const uint64_t *A,
+          const uint64_t *B, uint64_t *Aout, uint64_t *Bout, const uint64_t *primes_host, int P,
+          int path, void *ws, size_t ws_bytes, void *stream) {
+    return pc_common(d, kct, nvec, U, A, B, Aout, Bout, primes_host, P, path, ws, ws_bytes,
+                     stream);
+}
+
+int modpp_profile_enable(int on) {
+    std::lock_guard<std::mutex> lock(g_prof_mu);
+    g_prof_on = on != 0;
+    for (auto &t : g_timers) t.used = 0;
+    return MODPP_OK;
+}
+
+int modpp_profile_read(int kernel, double *total_ms, int64_t *launches) {
+    if (kernel < 0 || kernel >= kTimedKernels) return MODPP_ERR_ARG;
+    std::lock_guard<std::mutex> lock(g_prof_mu);
+    KernelTimer &t = g_timers[kernel];
+    double sum = 0.0;
+    for (size_t i = 0; i < t.used; ++i) {
+        float ms = 0.f;
+        if (cudaEventSynchronize(t.pool[i].stop) != cudaSuccess ||
+            cudaEventElapsedTime(&ms, t.pool[i].start, t.pool[i].stop) != cudaSuccess)
+            return MODPP_ERR_CUDA;
+        sum += ms;
+    }
+    if (total_ms) *total_ms = sum;
+    if (launches) *launches = static_cast<int64_t>(t.used);
+    t.used = 0;
+    return MODPP_OK;
+}
+
+int modpp_status_read(void *ws, void *stream) {
+    if (ws == nullptr) return MODPP_ERR_WORKSPACE;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (cudaStreamSynchronize(st) != cudaSuccess) return MODPP_ERR_CUDA;
+    int v = 0;
+    if (cudaMemcpy(&v, ws, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return MODPP_ERR_CUDA;
+    if (v != 0 && cudaMemset(ws, 0, sizeof(int)) != cudaSuccess) return MODPP_ERR_CUDA;
+    return v;
+}
+
+}  // extern "C"

@@ -1,0 +1,196 @@
+// Operand preparation kernels (memory-bound passes around the GEMMs).
+//
+// f16 path (default):
+//   u_to_f16        U (int8/int32, d x k) -> U16 (f16, d x kp, zero padded), K-major.
+//   split_digits    A_j (u64 residues, k x n) -> balanced 10-bit digits:
+//                   a = sum_l 2^(10 l) * D_l with D_l in [-512, 511], written as f16
+//                   (exact) and transposed to K-major rows (plane, n_block, l, col).
+//                   This is the limb split of the residue operand; the digit
+//                   identity is Eq. decomp of Sec. 6.1 with base 2^10.
+// FP64 path (Strategy 1, Lemma le:strategy1):
+//   u_to_f64, fp64_split (signed base-K digits of the centred residue),
+//   fp64_recombine (sum_i K^i * P_i mod q from the exact binary64 products).
+#include <cuda_fp16.h>
+
+#include "modarith.cuh"
+#include "modpp_internal.h"
+
+namespace modpp {
+
+// ---------------------------------------------------------------- U -> f16
+__global__ void u_to_f16_kernel(const void *__restrict__ U, int ukind, int64_t ldu, int d, int k,
+                                int kp, __half *__restrict__ U16) {
+    const int64_t total = static_cast<int64_t>(d) * kp;
+    for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < total;
+         i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        const int64_t r = i / kp;
+        const int t = static_cast<int>(i - r * kp);
+        int v = 0;
+        if (t < k) {
+            v = ukind == 0 ? static_cast<int>(static_cast<const int8_t *>(U)[r * ldu + t])
+                           : static_cast<const int32_t *>(U)[r * ldu + t];
+        }
+        U16[i] = __int2half_rn(v);
+    }
+}
+
+cudaError_t launch_u_to_f16(const void *U, int ukind, int64_t ldu, int d, int k, int kp,
+                            __half *U16, cudaStream_t s) {
+    const int64_t total = static_cast<int64_t>(d) * kp;
+    if (total == 0) return cudaSuccess;
+    int blocks = static_cast<int>((total + 255) / 256);
+    if (blocks > 152 * 32) blocks = 152 * 32;
+    u_to_f16_kernel<<<blocks, 256, 0, s>>>(U, ukind, ldu, d, k, kp, U16);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- digits
+// Block tile: 64 inner indices t x 32 columns c of one plane.
+// Phase 1 reads A coalesced along c, computes the L digits of each residue
+// and stores them in shared memory as [l][c][t].  Phase 2 writes each
+// (l, c) row of 64 digits (128 bytes) contiguously along t.
+constexpr int kSplitT = 64;
+constexpr int kSplitRow = kSplitT + 4;  // padded row (halves): 136-byte rows
+
+template <int L>
+__global__ void __launch_bounds__(256) split_digits_kernel(const __grid_constant__ SplitParams p) {
+    __shared__ __align__(16) __half tile[L * kNC * kSplitRow];
+    const int plane = blockIdx.z;
+    const int t0 = blockIdx.x * kSplitT;
+    const int nb = blockIdx.y;
+    const int c0 = nb * kNC;
+    const SplitPlane sp = p.sp[plane];
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+
+#pragma unroll
+    for (int i = 0; i < kSplitT / 8; ++i) {
+        const int tl = ty + 8 * i;
+        const int t = t0 + tl, c = c0 + tx;
+        uint64_t a = 0;
+        if (t < p.k && c < p.n) a = sp.A[static_cast<int64_t>(t) * sp.lda + c];
+        // Lift into the balanced window, then peel digits from the bottom:
+        // d = ((x + 512) mod 1024) - 512, x <- (x - d) / 1024 (exact).
+        int64_t x = a > sp.thresh ? static_cast<int64_t>(a - sp.q) : static_cast<int64_t>(a);
+#pragma unroll
+        for (int l = 0; l < L; ++l) {
+            const int dgt = static_cast<int>((x + 512) & 1023) - 512;
+            x = (x - dgt) >> kDigitBits;
+            tile[(l * kNC + tx) * kSplitRow + tl] = __int2half_rn(dgt);
+        }
+    }
+    __syncthreads();
+
+    // 16 threads per 128-byte row, 4 halves (8 bytes) each.
+    const int sub = threadIdx.x & 15;
+    const int t = t0 + 4 * sub;
+    for (int row = threadIdx.x >> 4; row < L * kNC; row += 16) {
+        if (t < p.kp) {
+            const int l = row / kNC, c = row - l * kNC;
+            const int64_t grow = ((static_cast<int64_t>(plane) * p.n_blocks + nb) * L + l) * kNC + c;
+            const uint2 v = *reinterpret_cast<const uint2 *>(&tile[row * kSplitRow + 4 * sub]);
+            *reinterpret_cast<uint2 *>(p.D + grow * p.kp + t) = v;
+        }
+    }
+}
+
+cudaError_t launch_split_digits(const SplitParams &p, cudaStream_t s) {
+    if (p.kp == 0 || p.n_blocks == 0 || p.planes == 0) return cudaSuccess;
+    dim3 grid((p.kp + kSplitT - 1) / kSplitT, p.n_blocks, p.planes);
+    switch (p.digits) {
+        case 1: split_digits_kernel<1><<<grid, 256, 0, s>>>(p); break;
+        case 2: split_digits_kernel<2><<<grid, 256, 0, s>>>(p); break;
+        case 3: split_digits_kernel<3><<<grid, 256, 0, s>>>(p); break;
+        case 4: split_digits_kernel<4><<<grid, 256, 0, s>>>(p); break;
+        case 5: split_digits_kernel<5><<<grid, 256, 0, s>>>(p); break;
+        case 6: split_digits_kernel<6><<<grid, 256, 0, s>>>(p); break;
+        case 7: split_digits_kernel<7><<<grid, 256, 0, s>>>(p); break;
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- FP64 path
+__global__ void u_to_f64_kernel(const void *__restrict__ U, int ukind, int64_t ldu, int d, int k,
+                                double *__restrict__ Ud) {
+    const int64_t total = static_cast<int64_t>(d) * k;
+    for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < total;
+         i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        const int64_t r = i / k;
+        const int64_t t = i - r * k;
+        const int v = ukind == 0 ? static_cast<int>(static_cast<const int8_t *>(U)[r * ldu + t])
+                                 : static_cast<const int32_t *>(U)[r * ldu + t];
+        Ud[i] = static_cast<double>(v);
+    }
+}
+
+cudaError_t launch_u_to_f64(const void *U, int ukind, int64_t ldu, int d, int k, double *Ud,
+                            cudaStream_t s) {
+    const int64_t total = static_cast<int64_t>(d) * k;
+    if (total == 0) return cudaSuccess;
+    int blocks = static_cast<int>((total + 255) / 256);
+    if (blocks > 152 * 32) blocks = 152 * 32;
+    u_to_f64_kernel<<<blocks, 256, 0, s>>>(U, ukind, ldu, d, k, Ud);
+    return cudaGetLastError();
+}
+
+// Signed base-K digits (Eq. decomp): the centred residue r = sum_i r_i K^i
+// with every r_i of the sign of r and |r_i| < K.
+__global__ void fp64_split_kernel(const Fp64SplitParams p) {
+    const int64_t total = static_cast<int64_t>(p.k) * p.n;
+    const int64_t ldo = static_cast<int64_t>(p.digits) * p.n;
+    for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < total;
+         i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        const int64_t t = i / p.n;
+        const int64_t c = i - t * p.n;
+        const uint64_t a = p.A[t * p.lda + c];
+        const bool neg = a > p.q / 2;  // centred representative in (-q/2, q/2]
+        uint64_t mag = neg ? p.q - a : a;
+        double *o = p.out + t * ldo + c;
+        for (int dgt = 0; dgt < p.digits; ++dgt) {
+            const uint64_t qd = mag / p.base;
+            const uint64_t r = mag - qd * p.base;
+            mag = qd;
+            o[static_cast<int64_t>(dgt) * p.n] = neg ? -static_cast<double>(r) : static_cast<double>(r);
+        }
+    }
+}
+
+cudaError_t launch_fp64_split(const Fp64SplitParams &p, cudaStream_t s) {
+    const int64_t total = static_cast<int64_t>(p.k) * p.n;
+    if (total == 0) return cudaSuccess;
+    int blocks = static_cast<int>((total + 255) / 256);
+    if (blocks > 152 * 32) blocks = 152 * 32;
+    fp64_split_kernel<<<blocks, 256, 0, s>>>(p);
+    return cudaGetLastError();
+}
+
+// C = sum_i K^i * P_i mod q.  Each P_i entry is an exact integer below 2^53
+// in magnitude, so the conversion to int64 is exact.
+__global__ void fp64_recombine_kernel(const __grid_constant__ Fp64RecombineParams p) {
+    const int64_t total = static_cast<int64_t>(p.d) * p.n;
+    const int64_t ldp = static_cast<int64_t>(p.digits) * p.n;
+    for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < total;
+         i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        const int64_t r = i / p.n;
+        const int64_t c = i - r * p.n;
+        const double *row = p.P + r * ldp + c;
+        uint64_t acc = 0;
+        for (int dgt = 0; dgt < p.digits; ++dgt) {
+            const int64_t v = __double2ll_rn(row[static_cast<int64_t>(dgt) * p.n]);
+            const uint64_t red = smod_i64(v, p.q, p.mu);
+            acc = add_mod(acc, shoup_mulmod(red, p.powK[dgt], p.powKs[dgt], p.q), p.q);
+        }
+        p.C[r * p.ldc + c] = acc;
+    }
+}
+
+cudaError_t launch_fp64_recombine(const Fp64RecombineParams &p, cudaStream_t s) {
+    const int64_t total = static_cast<int64_t>(p.d) * p.n;
+    if (total == 0) return cudaSuccess;
+    int blocks = static_cast<int>((total + 255) / 256);
+    if (blocks > 152 * 32) blocks = 152 * 32;
+    fp64_recombine_kernel<<<blocks, 256, 0, s>>>(p);
+    return cudaGetLastError();
+}
+
+}  // namespace modpp

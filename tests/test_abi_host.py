@@ -1,0 +1,120 @@
+"""CPU-side checks of the C ABI: the library loads, exports every function that
+include/modpp.h declares, and its host logic (planning, workspace sizes,
+argument validation) behaves as documented.  No call here reaches the GPU."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_2503_16080_gb300 import build, synth
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "modpp.h")
+
+
+@pytest.fixture(scope="module")
+def api():
+    build.build()
+    from paper_2503_16080_gb300 import api as a
+    return a
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    names = re.findall(r"^[A-Za-z_][\w \*]*?\b(\w+)\s*\(", text, flags=re.M)
+    return sorted(set(n for n in names if n not in ("defined",)))
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for required in ("modpp_mm", "modpp_mm_workspace", "pc_mm", "pc_mv", "pc_mm_workspace",
+                     "modpp_plan_info", "modpp_status_read", "modpp_status_string"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(api):
+    L = ctypes.CDLL(api.library_path())
+    missing = [n for n in declared_functions() if not hasattr(L, n)]
+    assert not missing, missing
+
+
+def test_status_strings(api):
+    L = api.lib()
+    assert L.modpp_status_string(0) == b"MODPP_OK"
+    for code in range(-1, -8, -1):
+        assert L.modpp_status_string(code).startswith(b"MODPP_ERR")
+    assert L.modpp_abi_version() >> 16 == 1
+
+
+@pytest.mark.parametrize("bits,digits", [(10, 1), (11, 2), (40, 4), (41, 5), (50, 5), (51, 6),
+                                         (60, 6), (61, 7), (62, 7)])
+def test_f16_digit_counts(api, bits, digits):
+    q = synth.ntt_primes(bits, 1, two_adicity=1 if bits <= 11 else 17)[0]
+    info = api.plan_info(4096, q, "f16")
+    assert info == {"digits": digits, "digit_bits": 10, "k_chunk": 256}
+    # The chunk bound: 256 * 128 * 512 = 2^24, the exact-integer range of binary32.
+    assert info["k_chunk"] * 128 * 2 ** (info["digit_bits"] - 1) == 2 ** 24
+
+
+def test_fp64_plan_matches_lemma(api):
+    # Lemma le:strategy1 at d2 = 2^12: K = 1482910 (2^20.5), three digits for 50..62-bit q.
+    for bits in (50, 54, 62):
+        q = synth.ntt_primes(bits, 1)[0]
+        info = api.plan_info(4096, q, "fp64")
+        assert info["digits"] == 3 and info["digit_bits"] == 20 and info["k_chunk"] == 4096
+    q = synth.ntt_primes(50, 1)[0]
+    tight = api.plan_info(4096, q, "fp64_tight")  # base floor(2^53 / 2^19) = 2^34
+    assert tight["digits"] == 2 and tight["digit_bits"] == 34
+
+
+def test_workspace_sizes(api):
+    q = synth.ntt_primes(50, 3)
+    # f16: 256 B header + U16 (d x kp halves) + digits (planes x n_blocks x 5 x 32 x kp halves)
+    ws = api.workspace_bytes(4096, 4096, 4096, q[:1])
+    assert ws == 256 + 4096 * 4096 * 2 + 128 * 5 * 32 * 4096 * 2
+    pc = api.workspace_bytes(4096, 4096, 4096, q, kind="pc_mm")
+    assert pc == 256 + 4096 * 4096 * 2 + 6 * 128 * 5 * 32 * 4096 * 2
+    assert api.workspace_bytes(-1, 4, 4, q[:1]) == 0
+    assert api.workspace_bytes(4, 4, 4, [4]) == 0
+
+
+def _call(api, d=4, k=4, n=4, U=1, A=1, C=1, primes=(97,), path=0, ws=256, ws_bytes=1 << 20,
+          ldu=None, lda=None, ldc=None, ukind=0):
+    pr = np.ascontiguousarray(primes, dtype=np.uint64)
+    return api.lib().modpp_mm(d, k, n, U, ukind, k if ldu is None else ldu, A,
+                              n if lda is None else lda, k * n, C, n if ldc is None else ldc,
+                              d * n, pr.ctypes.data if len(pr) else None, len(pr), path, ws,
+                              ws_bytes, None)
+
+
+def test_argument_errors_before_any_launch(api):
+    ARG, PRIME, WS = -1, -2, -3
+    assert _call(api, d=-1) == ARG
+    assert _call(api, k=(1 << 20) + 1) == ARG
+    assert _call(api, U=None) == ARG
+    assert _call(api, A=None) == ARG
+    assert _call(api, C=None) == ARG
+    assert _call(api, ldu=3) == ARG
+    assert _call(api, lda=3) == ARG
+    assert _call(api, ldc=2) == ARG
+    assert _call(api, ukind=7) == ARG
+    assert _call(api, path=9) == ARG
+    assert _call(api, primes=()) == ARG
+    assert _call(api, primes=(98,)) == PRIME
+    assert _call(api, primes=(1,)) == PRIME
+    assert _call(api, primes=((1 << 62) + 1,)) == PRIME
+    assert _call(api, primes=tuple([97] * 33)) == ARG
+    assert _call(api, ws=None) == WS
+    assert _call(api, ws=128) == WS          # not 256-byte aligned
+    assert _call(api, ws_bytes=16) == WS     # too small
+
+
+def test_pc_argument_errors(api):
+    L = api.lib()
+    pr = np.ascontiguousarray([97] * 17, dtype=np.uint64)
+    assert L.pc_mm(4, 4, 4, 1, 1, 1, 1, 1, pr.ctypes.data, 17, 0, 256, 1 << 20, None) == -1
+    assert L.pc_mv(4, 4, 4, 1, None, 1, 1, 1, pr.ctypes.data, 1, 0, 256, 1 << 20, None) == -1
+    assert L.modpp_status_read(None, None) == -3

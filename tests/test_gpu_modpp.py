@@ -1,0 +1,125 @@
+"""GPU parity of the Mod-PP-MM path against the CPU oracle (bit-exact).
+
+Every case draws seeded inputs from ``synth``, runs the CUDA library through
+the C ABI (Python binding) and compares all outputs, or sampled rows at full
+size, with ``oracle.mod_pp_mm`` element by element."""
+import numpy as np
+import pytest
+import torch
+
+from paper_2503_16080_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+P50 = synth.ntt_primes(50, 4)
+P40 = synth.ntt_primes(40, 2)
+P60 = synth.ntt_primes(60, 2)
+P62 = synth.ntt_primes(62, 1)
+
+
+@pytest.fixture(scope="module")
+def mp(cuda_ok):
+    import paper_2503_16080_gb300 as m
+    m.lib()
+    return m
+
+
+def to_gpu(x):
+    return torch.from_numpy(np.ascontiguousarray(x)).cuda()
+
+
+def run_and_compare(mp, oracle_mod, U, A, primes, path="f16", rows=None):
+    C = mp.modpp_mm(to_gpu(U), to_gpu(A), primes, path=path)
+    torch.cuda.synchronize()
+    assert mp.last_status() == 0
+    got = C.cpu().numpy()
+    if rows is None:
+        want = oracle_mod.mod_pp_mm(U.astype(np.int32), A, primes)
+        assert np.array_equal(got, want)
+    else:
+        want = oracle_mod.mod_pp_mm_rows(U.astype(np.int32), A, primes, rows)
+        assert np.array_equal(got[:, rows], want)
+    return got
+
+
+@pytest.mark.parametrize("shape", [(1, 1, 1), (256, 256, 256), (130, 300, 70), (257, 513, 33),
+                                   (128, 64, 32), (5, 1000, 200), (384, 1024, 96), (129, 8, 31)])
+def test_f16_exact_shapes(mp, oracle_mod, shape):
+    d, k, n = shape
+    U = synth.uniform_int8(sum(shape), 1, (d, k))
+    A = synth.uniform_mod(sum(shape), 2, (2, k, n), P50[0])
+    A[1] = synth.uniform_mod(sum(shape), 3, (k, n), P50[1])
+    run_and_compare(mp, oracle_mod, U, A, P50[:2])
+
+
+@pytest.mark.parametrize("primes", [P40, P60, P62, [97, 65537], [P50[0], P60[0], P40[0]]])
+def test_f16_prime_widths(mp, oracle_mod, primes):
+    d, k, n = 200, 700, 90
+    U = synth.uniform_int8(11, 1, (d, k))
+    A = np.stack([synth.uniform_mod(11, 2 + j, (k, n), q) for j, q in enumerate(primes)])
+    run_and_compare(mp, oracle_mod, U, A, primes)
+
+
+@pytest.mark.parametrize("k", [255, 256, 257, 1024, 4096])
+def test_f16_extreme_accumulation(mp, oracle_mod, k):
+    # U = -128 and residue q - 512 (lowest digit -512, others 0): every chunk
+    # sum of digit 0 reaches +2^24, the edge of binary32's exact integers.
+    q = P50[0]
+    d, n = 128, 64
+    U = np.full((d, k), -128, dtype=np.int8)
+    A = np.full((1, k, n), q - 512, dtype=np.uint64)
+    got = run_and_compare(mp, oracle_mod, U, A, [q])
+    assert np.all(got == (65536 * k) % q)
+    # Mixed extremes: +127/-128 rows against digit patterns +-511/-512 in every position.
+    S = sum(1 << (10 * i) for i in range(5))
+    vals = np.array([(511 * S) % q, (q - 512 * S) % q if 512 * S < q else 1, q - 1, 0, 511, q - 512],
+                    dtype=np.uint64)
+    A2 = vals[synth.u64(k, 5, k * n) % np.uint64(len(vals))].reshape(1, k, n)
+    U2 = np.where(synth.u64(k, 6, d * k).reshape(d, k) & np.uint64(1), 127, -128).astype(np.int8)
+    run_and_compare(mp, oracle_mod, U2, A2, [q])
+
+
+def test_int32_u_kind(mp, oracle_mod):
+    U = synth.uniform_int8(3, 1, (70, 333)).astype(np.int32)
+    A = synth.uniform_mod(3, 2, (1, 333, 45), P50[2])
+    run_and_compare(mp, oracle_mod, U, A, [P50[2]])
+
+
+def test_zero_k_and_empty(mp):
+    U = torch.zeros((7, 0), dtype=torch.int8, device="cuda")
+    A = torch.zeros((1, 0, 5), dtype=torch.uint64, device="cuda")
+    C = mp.modpp_mm(U, A, [P50[0]])
+    assert C.shape == (1, 7, 5) and int(C.cpu().numpy().max()) == 0
+    U = torch.zeros((0, 4), dtype=torch.int8, device="cuda")
+    A = torch.zeros((1, 4, 5), dtype=torch.uint64, device="cuda")
+    assert mp.modpp_mm(U, A, [P50[0]]).shape == (1, 0, 5)
+
+
+@pytest.mark.parametrize("path", ["fp64", "fp64_tight"])
+def test_fp64_path_exact(mp, oracle_mod, path):
+    U = synth.uniform_int8(21, 1, (96, 520))
+    A = np.stack([synth.uniform_mod(21, 2 + j, (520, 40), q) for j, q in enumerate(P50[:2])])
+    run_and_compare(mp, oracle_mod, U, A, P50[:2], path=path)
+
+
+def test_strided_planes_and_leading_dims(mp, oracle_mod):
+    q = P50[0]
+    U_full = synth.uniform_int8(31, 1, (64, 300))
+    A_full = synth.uniform_mod(31, 2, (2, 260, 100), q)
+    U = to_gpu(U_full)[:, :250]
+    A = to_gpu(A_full)[:, :250, :80]
+    out = torch.zeros((2, 64, 96), dtype=torch.uint64, device="cuda")
+    mp.modpp_mm(U, A, [q, q], out=out[:, :, :80])
+    got = out.cpu().numpy()
+    want = oracle_mod.mod_pp_mm(U_full[:, :250].astype(np.int32),
+                                np.ascontiguousarray(A_full[:, :250, :80]), [q, q])
+    assert np.array_equal(got[:, :, :80], want)
+    assert np.all(got[:, :, 80:] == 0)
+
+
+def test_repeat_calls_are_identical(mp):
+    U = to_gpu(synth.uniform_int8(41, 1, (256, 512)))
+    A = to_gpu(synth.uniform_mod(41, 2, (3, 512, 128), P50[0]))
+    a = mp.modpp_mm(U, A, [P50[0]] * 3).clone()
+    b = mp.modpp_mm(U, A, [P50[0]] * 3)
+    assert torch.equal(a, b)
