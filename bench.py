@@ -36,7 +36,7 @@ if ROOT not in sys.path:
 METRIC = ("PC-MM/CC-MM time and slowdown vs FP64 matmul, same n, 1 GB300; "
           "exact Mod-PP-MM TOPS")
 UNIT = "TOPS"
-D = K = N = 4096
+D = K = N = 4096  # overridden by --n (profiling of smaller cases only)
 NPRIMES = 3
 PRIME_BITS = 50
 SEED = 2024
@@ -246,7 +246,12 @@ def run_ours(args):
     value = mod_ops_per_step() * args.steps * ws / (max_ms * 1e-3) / 1e12
 
     line = None
-    if rank == 0:
+    if rank == 0 and args.quick:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms_per_step, "quick": True,
+                "gemm_avg_ms": gemm_ms / max(gemm_n, 1), "split_avg_ms": split_ms / max(split_n, 1),
+                "u16_avg_ms": u16_ms / max(u16_n, 1), "n": N}
+    elif rank == 0:
         peaks, peak_src = load_peaks()
         digits = pkg.plan_info(K, primes[0])["digits"]
         planes = 2 * NPRIMES
@@ -368,7 +373,15 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64-limb comparison")
+    ap.add_argument("--quick", action="store_true",
+                    help="timed loop only (no FP64, e2e or CPU legs): for profiler runs")
+    ap.add_argument("--n", type=int, default=4096,
+                    help="square size d = k = N (default 4096, the benchmark workload)")
     args = ap.parse_args()
+    global D, K, N, WORKLOAD
+    if args.n != 4096:
+        D = K = N = args.n
+        WORKLOAD = WORKLOAD.replace("n=4096", f"n={args.n}").replace("4096", str(args.n))
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
