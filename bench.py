@@ -44,8 +44,8 @@ WORKLOAD = ("PC-MM n=4096: U 4096x4096 int8 (N(0,1)*2^5) x row-RLWE ciphertext m
             "4096 cts of degree 4096, L=3 primes of 50 bits, a- and b-part (6 Mod-PP-MM planes)")
 
 
-def mod_ops_per_step(d=D, k=K, n=N, planes=2 * NPRIMES) -> float:
-    return 2.0 * d * k * n * planes
+def mod_ops_per_step() -> float:
+    return 2.0 * D * K * N * 2 * NPRIMES
 
 
 # ----------------------------------------------------------------- helpers
