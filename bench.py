@@ -196,6 +196,8 @@ def run_ours(args):
     __graft_entry__.build()
     import paper_2503_16080_gb300 as pkg
 
+    if args.digit_bits:
+        pkg.set_digit_bits(args.digit_bits)
     primes, U_np, A_np, B_np = make_inputs()
     U = torch.from_numpy(U_np).to(dev)
     A = torch.from_numpy(A_np).to(dev)
@@ -250,7 +252,7 @@ def run_ours(args):
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms_per_step, "quick": True,
                 "gemm_avg_ms": gemm_ms / max(gemm_n, 1), "split_avg_ms": split_ms / max(split_n, 1),
-                "u16_avg_ms": u16_ms / max(u16_n, 1), "n": N}
+                "u16_avg_ms": u16_ms / max(u16_n, 1), "n": N, "digit_bits": pkg.get_digit_bits()}
     elif rank == 0:
         peaks, peak_src = load_peaks()
         digits = pkg.plan_info(K, primes[0])["digits"]
@@ -375,6 +377,8 @@ def main():
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64-limb comparison")
     ap.add_argument("--quick", action="store_true",
                     help="timed loop only (no FP64, e2e or CPU legs): for profiler runs")
+    ap.add_argument("--digit-bits", type=int, default=0,
+                    help="digit width of the f16 path (8, 9, 10; 0 = library default)")
     ap.add_argument("--n", type=int, default=4096,
                     help="square size d = k = N (default 4096, the benchmark workload)")
     args = ap.parse_args()

@@ -59,7 +59,8 @@ typedef enum {
     /* Default. Exact small-integer digits on the sm_103a tensor cores
      * (tcgen05.mma kind::f16, FP32 accumulation in TMEM, K split so every
      * partial sum stays within the 2^24 exact-integer range of FP32), with
-     * a fused modular epilogue. */
+     * a fused modular epilogue.  Residues are split into balanced b-bit
+     * digits (modpp_set_digit_bits). */
     MODPP_PATH_F16 = 0,
     /* Strategy 1 of Sec. 6.1 (Lemma le:strategy1), as the paper ran it:
      * base K = floor(sqrt(2^53/k)) signed digits, one binary64 GEMM (cuBLAS
@@ -82,13 +83,24 @@ const char *modpp_status_string(int status);
 int modpp_abi_version(void);
 
 /*
+ * Digit width b of the F16 path (process-wide tuning setting, host only).
+ * Residues are split into balanced b-bit digits, b in {8, 9, 10}; the inner
+ * dimension is accumulated in exact FP32 chunks of 2^(18-b).  Narrower
+ * digits mean more digit products but fewer drains of the accumulators.
+ * 0 restores the default.  Returns MODPP_OK or MODPP_ERR_ARG.  Changing it
+ * while calls are in flight on other threads is not supported.
+ */
+int modpp_set_digit_bits(int bits);
+int modpp_get_digit_bits(void);
+
+/*
  * Planning query (host only, no GPU needed).  For a product with inner
  * dimension k modulo q on `path`, reports how the operands are split:
- *   digits      number of residue digits (F16: ceil(bits(q)/10) balanced
- *               10-bit digits; FP64: the Strategy 1 digit count k1)
- *   digit_bits  F16: 10; FP64: floor(log2(base))
+ *   digits      number of residue digits (F16: ceil(bits(q)/b) balanced
+ *               b-bit digits; FP64: the Strategy 1 digit count k1)
+ *   digit_bits  F16: b (see modpp_set_digit_bits); FP64: floor(log2(base))
  *   k_chunk     F16: inner-dimension chunk whose FP32 partial sums stay
- *               exact (256); FP64: k (one DGEMM covers the whole k)
+ *               exact, 2^(18-b); FP64: k (one DGEMM covers the whole k)
  * Returns MODPP_OK or an error for invalid k or q.
  */
 int modpp_plan_info(int64_t k, uint64_t q, int path, int *digits, int *digit_bits,

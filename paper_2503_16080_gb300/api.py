@@ -73,6 +73,8 @@ def lib() -> ctypes.CDLL:
         L.pc_mm.argtypes = [I64, I64, I64, P, P, P, P, P, P, I, I, P, SZ, P]
         L.pc_mv.argtypes = [I64, I64, I64, P, P, P, P, P, P, I, I, P, SZ, P]
         L.modpp_status_read.argtypes = [P, P]
+        L.modpp_set_digit_bits.argtypes = [I]
+        L.modpp_get_digit_bits.restype = I
         L.modpp_profile_enable.argtypes = [I]
         L.modpp_profile_read.argtypes = [I, P, P]
         _lib = L
@@ -158,6 +160,15 @@ def last_status(device: torch.device | int | None = None, stream=None,
 
 
 KERNEL_GEMM, KERNEL_SPLIT, KERNEL_U16 = 0, 1, 2
+
+
+def set_digit_bits(bits: int) -> None:
+    """Digit width b in {8, 9, 10} of the f16 path (0 = default); process-wide."""
+    _check(lib().modpp_set_digit_bits(int(bits)), "modpp_set_digit_bits")
+
+
+def get_digit_bits() -> int:
+    return int(lib().modpp_get_digit_bits())
 
 
 def profile_enable(on: bool) -> None:

@@ -2,13 +2,13 @@
 //
 // For one output plane (prime q, part A or B) the kernel computes
 //   C[r][c] = sum_t U[r][t] * A[t][c]  mod q
-// from the balanced 10-bit digits A = sum_l 2^(10 l) D_l (D_l in [-512, 511]):
-//   C = sum_l 2^(10 l) * (U * D_l)  mod q.
+// from balanced b-bit digits A = sum_l 2^(b l) D_l (|D_l| <= 2^(b-1), b = 8..10):
+//   C = sum_l 2^(b l) * (U * D_l)  mod q.
 // Every U * D_l runs on tcgen05.mma kind::f16 (f16 operands, FP32 accumulate
 // in TMEM).  f16 holds U in [-128, 127] and D_l exactly, and the products
 // are exact; the FP32 sums stay exact because the inner dimension is cut into
-// chunks of 256: |sum| <= 256 * 128 * 512 = 2^24, the largest range in which
-// FP32 represents every integer.  After each chunk the epilogue warps move the
+// chunks of 2^(18-b): |sum| <= 2^(18-b) * 128 * 2^(b-1) = 2^24, the largest
+// range in which FP32 represents every integer.  After each chunk the epilogue warps move the
 // chunk's sums out of TMEM into 64-bit integer registers; after the last
 // chunk of a tile they recombine the digits modulo q (Barrett + Shoup) and
 // store canonical residues.  This is the limb-splitting reduction of Sec. 6.1
@@ -62,7 +62,7 @@ __device__ __forceinline__ void decode_tile(int tile, int m_blocks, int n_blocks
     plane = rest / n_blocks;
 }
 
-template <int L>
+template <int L, int DB>
 __global__ void __launch_bounds__(kThreads, 1)
     gemm_f16_kernel(const __grid_constant__ CUtensorMap tmU, const __grid_constant__ CUtensorMap tmD,
                     const __grid_constant__ GemmParams p) {
@@ -107,6 +107,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem_base = *tmem_slot;
+    constexpr int kChunkKB = chunk_k(DB) / kBK;
     const int n_chunks = (p.kb_total + kChunkKB - 1) / kChunkKB;
 
     if (warp == 0) {
@@ -211,11 +212,11 @@ __global__ void __launch_bounds__(kThreads, 1)
                     for (int c = 0; c < 16; ++c) {
                         const int64_t v = __float2int_rn(__uint_as_float(r[c]));
                         if (l < 3)
-                            acc_lo[c] += v << (kDigitBits * l);
+                            acc_lo[c] += v << (DB * l);
                         else if (l < 6)
-                            acc_hi[c] += v << (kDigitBits * (l - 3));
+                            acc_hi[c] += v << (DB * (l - 3));
                         else
-                            acc_top[c] += v;
+                            acc_top[c] += v << (DB * (l - 6));
                     }
                 }
                 tc_fence_before();
@@ -223,7 +224,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                 if (lane == 0) mbar_arrive(&tempty[buf]);
             }
             if (!ok) break;
-            // value = lo + 2^30 hi + 2^60 top  (mod q)
+            // value = lo + 2^(3b) hi + 2^(6b) top  (mod q)
             const int row = mb * kBM + quarter * 32 + lane;
             const int col0 = nb * kNC + half * 16;
             if (row < p.d) {
@@ -233,12 +234,12 @@ __global__ void __launch_bounds__(kThreads, 1)
                 for (int c = 0; c < 16; ++c) {
                     uint64_t v = smod_i64(acc_lo[c], pc.q, pc.mu);
                     if (L > 3)
-                        v = add_mod(v, shoup_mulmod(smod_i64(acc_hi[c], pc.q, pc.mu), pc.w30,
-                                                    pc.w30s, pc.q),
+                        v = add_mod(v, shoup_mulmod(smod_i64(acc_hi[c], pc.q, pc.mu), pc.wg1,
+                                                    pc.wg1s, pc.q),
                                     pc.q);
                     if (L > 6)
-                        v = add_mod(v, shoup_mulmod(smod_i64(acc_top[c], pc.q, pc.mu), pc.w60,
-                                                    pc.w60s, pc.q),
+                        v = add_mod(v, shoup_mulmod(smod_i64(acc_top[c], pc.q, pc.mu), pc.wg2,
+                                                    pc.wg2s, pc.q),
                                     pc.q);
                     if (col0 + c < p.n) out[c] = v;
                 }
@@ -255,30 +256,42 @@ __global__ void __launch_bounds__(kThreads, 1)
     if (threadIdx.x == 0 && (*abort_flag || *drain_abort)) atomicExch(p.status, -7);
 }
 
-template <int L>
+template <int L, int DB>
 static cudaError_t launch_gemm_l(const CUtensorMap &tmU, const CUtensorMap &tmD,
                                  const GemmParams &p, int num_sms, cudaStream_t s) {
     using Cfg = GemmCfg<L>;
-    cudaError_t e = cudaFuncSetAttribute(gemm_f16_kernel<L>,
+    cudaError_t e = cudaFuncSetAttribute(gemm_f16_kernel<L, DB>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          Cfg::SMEM_BYTES);
     if (e != cudaSuccess) return e;
     const int grid = p.num_tiles < num_sms ? p.num_tiles : num_sms;
-    gemm_f16_kernel<L><<<grid, kThreads, Cfg::SMEM_BYTES, s>>>(tmU, tmD, p);
+    gemm_f16_kernel<L, DB><<<grid, kThreads, Cfg::SMEM_BYTES, s>>>(tmU, tmD, p);
     return cudaGetLastError();
 }
 
-cudaError_t launch_gemm_f16(const CUtensorMap &tmU, const CUtensorMap &tmD, const GemmParams &p,
-                            int digits, int num_sms, cudaStream_t s) {
-    if (p.num_tiles == 0) return cudaSuccess;
+template <int DB>
+static cudaError_t launch_gemm_db(const CUtensorMap &tmU, const CUtensorMap &tmD,
+                                  const GemmParams &p, int digits, int num_sms, cudaStream_t s) {
     switch (digits) {
-        case 1: return launch_gemm_l<1>(tmU, tmD, p, num_sms, s);
-        case 2: return launch_gemm_l<2>(tmU, tmD, p, num_sms, s);
-        case 3: return launch_gemm_l<3>(tmU, tmD, p, num_sms, s);
-        case 4: return launch_gemm_l<4>(tmU, tmD, p, num_sms, s);
-        case 5: return launch_gemm_l<5>(tmU, tmD, p, num_sms, s);
-        case 6: return launch_gemm_l<6>(tmU, tmD, p, num_sms, s);
-        case 7: return launch_gemm_l<7>(tmU, tmD, p, num_sms, s);
+        case 1: return launch_gemm_l<1, DB>(tmU, tmD, p, num_sms, s);
+        case 2: return launch_gemm_l<2, DB>(tmU, tmD, p, num_sms, s);
+        case 3: return launch_gemm_l<3, DB>(tmU, tmD, p, num_sms, s);
+        case 4: return launch_gemm_l<4, DB>(tmU, tmD, p, num_sms, s);
+        case 5: return launch_gemm_l<5, DB>(tmU, tmD, p, num_sms, s);
+        case 6: return launch_gemm_l<6, DB>(tmU, tmD, p, num_sms, s);
+        case 7: return launch_gemm_l<7, DB>(tmU, tmD, p, num_sms, s);
+        case 8: return launch_gemm_l<8, DB>(tmU, tmD, p, num_sms, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_gemm_f16(const CUtensorMap &tmU, const CUtensorMap &tmD, const GemmParams &p,
+                            int digits, int digit_bits, int num_sms, cudaStream_t s) {
+    if (p.num_tiles == 0) return cudaSuccess;
+    switch (digit_bits) {
+        case 8: return launch_gemm_db<8>(tmU, tmD, p, digits, num_sms, s);
+        case 9: return launch_gemm_db<9>(tmU, tmD, p, digits, num_sms, s);
+        case 10: return launch_gemm_db<10>(tmU, tmD, p, digits, num_sms, s);
         default: return cudaErrorInvalidValue;
     }
 }

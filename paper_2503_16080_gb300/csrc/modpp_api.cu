@@ -6,6 +6,7 @@
 #include <cuda.h>
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <cstdlib>
 #include <cstring>
 #include <mutex>
@@ -41,6 +42,15 @@ int check_sizes(int64_t d, int64_t k, int64_t n) {
     return MODPP_OK;
 }
 
+// Digit width of the f16 path: 0 selects the default.  Narrower digits allow
+// deeper exact FP32 chunks (fewer TMEM drains) at the cost of more digits.
+constexpr int kDefaultDigitBits = 9;
+std::atomic<int> g_digit_bits{0};
+int current_digit_bits() {
+    const int b = g_digit_bits.load();
+    return b == 0 ? kDefaultDigitBits : b;
+}
+
 bool path_ok(int path) {
     return path == MODPP_PATH_F16 || path == MODPP_PATH_FP64 || path == MODPP_PATH_FP64_TIGHT;
 }
@@ -55,6 +65,7 @@ struct PlaneIn {
 
 // ------------------------------------------------------------ f16 layout
 struct F16Layout {
+    int b = 0;
     int L = 0;
     int64_t kp = 0, n_blocks = 0, rows = 0;
     size_t off_u16 = 0, off_d = 0, total = 0;
@@ -62,8 +73,9 @@ struct F16Layout {
 
 F16Layout f16_layout(int64_t d, int64_t k, int64_t n, const uint64_t *qs, int planes) {
     F16Layout lay;
+    lay.b = current_digit_bits();
     for (int i = 0; i < planes; ++i) {
-        const int l = f16_digit_count(qs[i]);
+        const int l = f16_digit_count(qs[i], lay.b);
         if (l > lay.L) lay.L = l;
     }
     lay.kp = (k + 7) / 8 * 8;
@@ -258,8 +270,9 @@ int run_f16(int64_t d, int64_t k, int64_t n, const void *U, int ukind, int64_t l
     sp.n_blocks = static_cast<int>(lay.n_blocks);
     sp.planes = planes;
     sp.digits = lay.L;
+    sp.digit_bits = lay.b;
     sp.D = D;
-    const uint64_t thresh = f16_lift_threshold(lay.L);
+    const uint64_t thresh = f16_lift_threshold(lay.L, lay.b);
     for (int i = 0; i < planes; ++i) sp.sp[i] = SplitPlane{pl[i].A, pl[i].lda, pl[i].q, thresh};
     ev = timer_begin(MODPP_KERNEL_SPLIT, st);
     rc = cuda_status(launch_split_digits(sp, st));
@@ -286,11 +299,12 @@ int run_f16(int64_t d, int64_t k, int64_t n, const void *U, int ukind, int64_t l
     gp.num_tiles = static_cast<int>(tiles);
     gp.status = status;
     gp.timeout_ns = wait_limit_ns();
-    for (int i = 0; i < planes; ++i) gp.pc[i] = make_plane_const(pl[i].q, pl[i].C, pl[i].ldc);
+    for (int i = 0; i < planes; ++i)
+        gp.pc[i] = make_plane_const(pl[i].q, lay.b, pl[i].C, pl[i].ldc);
     const int sms = device_sms();
     if (sms <= 0) return MODPP_ERR_CUDA;
     ev = timer_begin(MODPP_KERNEL_GEMM, st);
-    rc = cuda_status(launch_gemm_f16(tmU, tmD, gp, lay.L, sms, st));
+    rc = cuda_status(launch_gemm_f16(tmU, tmD, gp, lay.L, lay.b, sms, st));
     timer_end(ev, st);
     return rc;
 }
@@ -421,7 +435,15 @@ const char *modpp_status_string(int status) {
     }
 }
 
-int modpp_abi_version(void) { return (1 << 16) | 0; }
+int modpp_abi_version(void) { return (1 << 16) | 1; }
+
+int modpp_set_digit_bits(int bits) {
+    if (bits != 0 && (bits < kMinDigitBits || bits > kMaxDigitBits)) return MODPP_ERR_ARG;
+    g_digit_bits.store(bits);
+    return MODPP_OK;
+}
+
+int modpp_get_digit_bits(void) { return current_digit_bits(); }
 
 int modpp_plan_info(int64_t k, uint64_t q, int path, int *digits, int *digit_bits,
                     int64_t *k_chunk) {
@@ -429,9 +451,9 @@ int modpp_plan_info(int64_t k, uint64_t q, int path, int *digits, int *digit_bit
     int dg, bits;
     int64_t chunk;
     if (path == MODPP_PATH_F16) {
-        dg = f16_digit_count(q);
-        bits = kDigitBits;
-        chunk = kChunkK;
+        bits = current_digit_bits();
+        dg = f16_digit_count(q, bits);
+        chunk = chunk_k(bits);
     } else {
         const uint64_t K = fp64_base(k, path == MODPP_PATH_FP64_TIGHT);
         dg = fp64_digit_count((q - 1) / 2, K);

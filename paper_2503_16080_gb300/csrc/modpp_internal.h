@@ -14,19 +14,22 @@ constexpr int kMaxPlanes = 32;       // (prime, part) output planes per launch
 constexpr int kBM = 128;             // output rows per tile (UMMA M)
 constexpr int kNC = 32;              // output columns per tile
 constexpr int kBK = 64;              // f16 elements per K block (one 128-byte row)
-constexpr int kDigitBits = 10;       // balanced digits in [-512, 511]
-constexpr int kChunkK = 256;         // FP32-exact inner chunk: 256 * 128 * 512 = 2^24
-constexpr int kChunkKB = kChunkK / kBK;
-constexpr int kMaxDigits = 7;        // q < 2^62 needs at most 7 ten-bit digits
+constexpr int kMinDigitBits = 8;     // balanced b-bit digits in [-2^(b-1), 2^(b-1) - 1]
+constexpr int kMaxDigitBits = 10;
+constexpr int kMaxDigits = 8;        // q < 2^62 needs at most 8 eight-bit digits
+
+// Inner-dimension chunk whose FP32 partial sums stay exact for b-bit digits:
+// chunk * 128 * 2^(b-1) = 2^24 (|U| <= 128), i.e. chunk = 2^(18 - b).
+__host__ __device__ constexpr int chunk_k(int digit_bits) { return 1 << (18 - digit_bits); }
 
 // Constants of one output plane (one prime, one part).
 struct PlaneConst {
     uint64_t q;
     uint64_t mu;    // floor(2^64 / q), Barrett
-    uint64_t w30;   // 2^30 mod q
-    uint64_t w30s;  // floor(w30 * 2^64 / q), Shoup
-    uint64_t w60;   // 2^60 mod q
-    uint64_t w60s;
+    uint64_t wg1;   // 2^(3b) mod q: weight of digit group 1 (digits 3..5)
+    uint64_t wg1s;  // floor(wg1 * 2^64 / q), Shoup
+    uint64_t wg2;   // 2^(6b) mod q: weight of digit group 2 (digits 6..8)
+    uint64_t wg2s;
     uint64_t *C;    // output plane, d x n, leading dimension ldc
     int64_t ldc;
 };
@@ -52,7 +55,7 @@ struct SplitPlane {
 };
 
 struct SplitParams {
-    int k, n, kp, n_blocks, planes, digits;
+    int k, n, kp, n_blocks, planes, digits, digit_bits;
     __half *D;          // digit matrix: rows (plane, n_block, digit, col), kp columns
     SplitPlane sp[kMaxPlanes];
 };
@@ -84,28 +87,29 @@ inline int bit_length(uint64_t q) {
     }
     return b;
 }
-// Number of balanced 10-bit digits covering residues mod q: the window of L
-// such digits holds 2^(10L) consecutive integers, so q <= 2^(10L).
-inline int f16_digit_count(uint64_t q) { return (bit_length(q - 1) + kDigitBits - 1) / kDigitBits; }
+// Number of balanced b-bit digits covering residues mod q: the window of L
+// such digits holds 2^(bL) consecutive integers, so q <= 2^(bL).
+inline int f16_digit_count(uint64_t q, int b) { return (bit_length(q - 1) + b - 1) / b; }
 
 // Largest value kept positive when lifting a residue into the balanced
-// window [-512*S, 511*S], S = sum_{i<L} 2^(10 i); saturated to 2^63 - 1.
-inline uint64_t f16_lift_threshold(int L) {
+// window [-2^(b-1) S, (2^(b-1) - 1) S], S = sum_{i<L} 2^(b i); saturated to
+// 2^63 - 1 (then no residue needs lifting).
+inline uint64_t f16_lift_threshold(int L, int b) {
     unsigned __int128 S = 0;
-    for (int i = 0; i < L; ++i) S += static_cast<unsigned __int128>(1) << (kDigitBits * i);
-    unsigned __int128 T = S * 511u;
+    for (int i = 0; i < L; ++i) S += static_cast<unsigned __int128>(1) << (b * i);
+    unsigned __int128 T = S * ((1u << (b - 1)) - 1u);
     const unsigned __int128 cap = (static_cast<unsigned __int128>(1) << 63) - 1;
     return static_cast<uint64_t>(T > cap ? cap : T);
 }
 
-inline PlaneConst make_plane_const(uint64_t q, uint64_t *C, int64_t ldc) {
+inline PlaneConst make_plane_const(uint64_t q, int b, uint64_t *C, int64_t ldc) {
     PlaneConst p{};
     p.q = q;
     p.mu = host_barrett_mu(q);
-    p.w30 = host_pow2_mod(30, q);
-    p.w30s = host_shoup(p.w30, q);
-    p.w60 = host_pow2_mod(60, q);
-    p.w60s = host_shoup(p.w60, q);
+    p.wg1 = host_pow2_mod(3 * b, q);
+    p.wg1s = host_shoup(p.wg1, q);
+    p.wg2 = host_pow2_mod(6 * b, q);
+    p.wg2s = host_shoup(p.wg2, q);
     p.C = C;
     p.ldc = ldc;
     return p;
@@ -117,7 +121,7 @@ cudaError_t launch_u_to_f16(const void *U, int ukind, int64_t ldu, int d, int k,
                             __half *U16, cudaStream_t s);
 cudaError_t launch_split_digits(const SplitParams &p, cudaStream_t s);
 cudaError_t launch_gemm_f16(const CUtensorMap &tmU, const CUtensorMap &tmD, const GemmParams &p,
-                            int digits, int num_sms, cudaStream_t s);
+                            int digits, int digit_bits, int num_sms, cudaStream_t s);
 
 // FP64-limb (Strategy 1) helpers.
 struct Fp64SplitParams {

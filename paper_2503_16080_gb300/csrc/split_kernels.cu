@@ -2,11 +2,11 @@
 //
 // f16 path (default):
 //   u_to_f16        U (int8/int32, d x k) -> U16 (f16, d x kp, zero padded), K-major.
-//   split_digits    A_j (u64 residues, k x n) -> balanced 10-bit digits:
-//                   a = sum_l 2^(10 l) * D_l with D_l in [-512, 511], written as f16
-//                   (exact) and transposed to K-major rows (plane, n_block, l, col).
+//   split_digits    A_j (u64 residues, k x n) -> balanced b-bit digits (b = 8..10):
+//                   a = sum_l 2^(b l) * D_l with D_l in [-2^(b-1), 2^(b-1) - 1], written
+//                   as f16 (exact) and transposed to K-major rows (plane, n_block, l, col).
 //                   This is the limb split of the residue operand; the digit
-//                   identity is Eq. decomp of Sec. 6.1 with base 2^10.
+//                   identity is Eq. decomp of Sec. 6.1 with base 2^b.
 // FP64 path (Strategy 1, Lemma le:strategy1):
 //   u_to_f64, fp64_split (signed base-K digits of the centred residue),
 //   fp64_recombine (sum_i K^i * P_i mod q from the exact binary64 products).
@@ -52,8 +52,10 @@ cudaError_t launch_u_to_f16(const void *U, int ukind, int64_t ldu, int d, int k,
 constexpr int kSplitT = 64;
 constexpr int kSplitRow = kSplitT + 4;  // padded row (halves): 136-byte rows
 
-template <int L>
+template <int L, int DB>
 __global__ void __launch_bounds__(256) split_digits_kernel(const __grid_constant__ SplitParams p) {
+    constexpr int64_t kHalf = int64_t(1) << (DB - 1);
+    constexpr int64_t kMask = (int64_t(1) << DB) - 1;
     __shared__ __align__(16) __half tile[L * kNC * kSplitRow];
     const int plane = blockIdx.z;
     const int t0 = blockIdx.x * kSplitT;
@@ -69,12 +71,12 @@ __global__ void __launch_bounds__(256) split_digits_kernel(const __grid_constant
         uint64_t a = 0;
         if (t < p.k && c < p.n) a = sp.A[static_cast<int64_t>(t) * sp.lda + c];
         // Lift into the balanced window, then peel digits from the bottom:
-        // d = ((x + 512) mod 1024) - 512, x <- (x - d) / 1024 (exact).
+        // d = ((x + 2^(b-1)) mod 2^b) - 2^(b-1), x <- (x - d) / 2^b (exact).
         int64_t x = a > sp.thresh ? static_cast<int64_t>(a - sp.q) : static_cast<int64_t>(a);
 #pragma unroll
         for (int l = 0; l < L; ++l) {
-            const int dgt = static_cast<int>((x + 512) & 1023) - 512;
-            x = (x - dgt) >> kDigitBits;
+            const int dgt = static_cast<int>(((x + kHalf) & kMask) - kHalf);
+            x = (x - dgt) >> DB;
             tile[(l * kNC + tx) * kSplitRow + tl] = __int2half_rn(dgt);
         }
     }
@@ -93,19 +95,32 @@ __global__ void __launch_bounds__(256) split_digits_kernel(const __grid_constant
     }
 }
 
+template <int DB>
+static bool launch_split_db(const SplitParams &p, dim3 grid, cudaStream_t s) {
+    switch (p.digits) {
+        case 1: split_digits_kernel<1, DB><<<grid, 256, 0, s>>>(p); return true;
+        case 2: split_digits_kernel<2, DB><<<grid, 256, 0, s>>>(p); return true;
+        case 3: split_digits_kernel<3, DB><<<grid, 256, 0, s>>>(p); return true;
+        case 4: split_digits_kernel<4, DB><<<grid, 256, 0, s>>>(p); return true;
+        case 5: split_digits_kernel<5, DB><<<grid, 256, 0, s>>>(p); return true;
+        case 6: split_digits_kernel<6, DB><<<grid, 256, 0, s>>>(p); return true;
+        case 7: split_digits_kernel<7, DB><<<grid, 256, 0, s>>>(p); return true;
+        case 8: split_digits_kernel<8, DB><<<grid, 256, 0, s>>>(p); return true;
+        default: return false;
+    }
+}
+
 cudaError_t launch_split_digits(const SplitParams &p, cudaStream_t s) {
     if (p.kp == 0 || p.n_blocks == 0 || p.planes == 0) return cudaSuccess;
     dim3 grid((p.kp + kSplitT - 1) / kSplitT, p.n_blocks, p.planes);
-    switch (p.digits) {
-        case 1: split_digits_kernel<1><<<grid, 256, 0, s>>>(p); break;
-        case 2: split_digits_kernel<2><<<grid, 256, 0, s>>>(p); break;
-        case 3: split_digits_kernel<3><<<grid, 256, 0, s>>>(p); break;
-        case 4: split_digits_kernel<4><<<grid, 256, 0, s>>>(p); break;
-        case 5: split_digits_kernel<5><<<grid, 256, 0, s>>>(p); break;
-        case 6: split_digits_kernel<6><<<grid, 256, 0, s>>>(p); break;
-        case 7: split_digits_kernel<7><<<grid, 256, 0, s>>>(p); break;
-        default: return cudaErrorInvalidValue;
+    bool ok = false;
+    switch (p.digit_bits) {
+        case 8: ok = launch_split_db<8>(p, grid, s); break;
+        case 9: ok = launch_split_db<9>(p, grid, s); break;
+        case 10: ok = launch_split_db<10>(p, grid, s); break;
+        default: break;
     }
+    if (!ok) return cudaErrorInvalidValue;
     return cudaGetLastError();
 }
 

@@ -49,14 +49,32 @@ def test_status_strings(api):
     assert L.modpp_abi_version() >> 16 == 1
 
 
-@pytest.mark.parametrize("bits,digits", [(10, 1), (11, 2), (40, 4), (41, 5), (50, 5), (51, 6),
-                                         (60, 6), (61, 7), (62, 7)])
-def test_f16_digit_counts(api, bits, digits):
+@pytest.mark.parametrize("b", [8, 9, 10])
+@pytest.mark.parametrize("bits", [8, 9, 10, 11, 40, 41, 50, 51, 60, 61, 62])
+def test_f16_digit_counts(api, b, bits):
     q = synth.ntt_primes(bits, 1, two_adicity=1 if bits <= 11 else 17)[0]
-    info = api.plan_info(4096, q, "f16")
-    assert info == {"digits": digits, "digit_bits": 10, "k_chunk": 256}
-    # The chunk bound: 256 * 128 * 512 = 2^24, the exact-integer range of binary32.
-    assert info["k_chunk"] * 128 * 2 ** (info["digit_bits"] - 1) == 2 ** 24
+    api.set_digit_bits(b)
+    try:
+        info = api.plan_info(4096, q, "f16")
+    finally:
+        api.set_digit_bits(0)
+    # L balanced b-bit digits cover 2^(bL) consecutive integers: need q <= 2^(bL).
+    L = -(-(q - 1).bit_length() // b)
+    assert info == {"digits": L, "digit_bits": b, "k_chunk": 2 ** (18 - b)}
+    assert q <= 2 ** (b * L) and q > 2 ** (b * (L - 1))
+    # The chunk bound: chunk * 128 * 2^(b-1) = 2^24, the exact-integer range of binary32.
+    assert info["k_chunk"] * 128 * 2 ** (b - 1) == 2 ** 24
+
+
+def test_digit_bits_setting(api):
+    assert api.get_digit_bits() in (8, 9, 10)
+    with pytest.raises(api.ModppError):
+        api.set_digit_bits(7)
+    with pytest.raises(api.ModppError):
+        api.set_digit_bits(11)
+    api.set_digit_bits(10)
+    assert api.get_digit_bits() == 10
+    api.set_digit_bits(0)
 
 
 def test_fp64_plan_matches_lemma(api):
@@ -72,11 +90,12 @@ def test_fp64_plan_matches_lemma(api):
 
 def test_workspace_sizes(api):
     q = synth.ntt_primes(50, 3)
-    # f16: 256 B header + U16 (d x kp halves) + digits (planes x n_blocks x 5 x 32 x kp halves)
+    L = api.plan_info(4096, q[0])["digits"]
+    # f16: 256 B header + U16 (d x kp halves) + digits (planes x n_blocks x L x 32 x kp halves)
     ws = api.workspace_bytes(4096, 4096, 4096, q[:1])
-    assert ws == 256 + 4096 * 4096 * 2 + 128 * 5 * 32 * 4096 * 2
+    assert ws == 256 + 4096 * 4096 * 2 + 128 * L * 32 * 4096 * 2
     pc = api.workspace_bytes(4096, 4096, 4096, q, kind="pc_mm")
-    assert pc == 256 + 4096 * 4096 * 2 + 6 * 128 * 5 * 32 * 4096 * 2
+    assert pc == 256 + 4096 * 4096 * 2 + 6 * 128 * L * 32 * 4096 * 2
     assert api.workspace_bytes(-1, 4, 4, q[:1]) == 0
     assert api.workspace_bytes(4, 4, 4, [4]) == 0
 

@@ -24,6 +24,13 @@ def mp(cuda_ok):
     return m
 
 
+@pytest.fixture(params=[8, 9, 10])
+def digit_bits(request, mp):
+    mp.set_digit_bits(request.param)
+    yield request.param
+    mp.set_digit_bits(0)
+
+
 def to_gpu(x):
     return torch.from_numpy(np.ascontiguousarray(x)).cuda()
 
@@ -44,7 +51,7 @@ def run_and_compare(mp, oracle_mod, U, A, primes, path="f16", rows=None):
 
 @pytest.mark.parametrize("shape", [(1, 1, 1), (256, 256, 256), (130, 300, 70), (257, 513, 33),
                                    (128, 64, 32), (5, 1000, 200), (384, 1024, 96), (129, 8, 31)])
-def test_f16_exact_shapes(mp, oracle_mod, shape):
+def test_f16_exact_shapes(mp, oracle_mod, shape, digit_bits):
     d, k, n = shape
     U = synth.uniform_int8(sum(shape), 1, (d, k))
     A = synth.uniform_mod(sum(shape), 2, (2, k, n), P50[0])
@@ -53,7 +60,7 @@ def test_f16_exact_shapes(mp, oracle_mod, shape):
 
 
 @pytest.mark.parametrize("primes", [P40, P60, P62, [97, 65537], [P50[0], P60[0], P40[0]]])
-def test_f16_prime_widths(mp, oracle_mod, primes):
+def test_f16_prime_widths(mp, oracle_mod, primes, digit_bits):
     d, k, n = 200, 700, 90
     U = synth.uniform_int8(11, 1, (d, k))
     A = np.stack([synth.uniform_mod(11, 2 + j, (k, n), q) for j, q in enumerate(primes)])
@@ -61,18 +68,21 @@ def test_f16_prime_widths(mp, oracle_mod, primes):
 
 
 @pytest.mark.parametrize("k", [255, 256, 257, 1024, 4096])
-def test_f16_extreme_accumulation(mp, oracle_mod, k):
-    # U = -128 and residue q - 512 (lowest digit -512, others 0): every chunk
-    # sum of digit 0 reaches +2^24, the edge of binary32's exact integers.
+def test_f16_extreme_accumulation(mp, oracle_mod, k, digit_bits):
+    # U = -128 and residue q - 2^(b-1) (lowest digit -2^(b-1), others 0): every
+    # chunk sum of digit 0 reaches +2^24, the edge of binary32's exact integers.
     q = P50[0]
+    b = digit_bits
+    h = 1 << (b - 1)
     d, n = 128, 64
     U = np.full((d, k), -128, dtype=np.int8)
-    A = np.full((1, k, n), q - 512, dtype=np.uint64)
+    A = np.full((1, k, n), q - h, dtype=np.uint64)
     got = run_and_compare(mp, oracle_mod, U, A, [q])
-    assert np.all(got == (65536 * k) % q)
-    # Mixed extremes: +127/-128 rows against digit patterns +-511/-512 in every position.
-    S = sum(1 << (10 * i) for i in range(5))
-    vals = np.array([(511 * S) % q, (q - 512 * S) % q if 512 * S < q else 1, q - 1, 0, 511, q - 512],
+    assert np.all(got == (128 * h * k) % q)
+    # Mixed extremes: +127/-128 rows against digit patterns +-(2^(b-1)) in every position.
+    L = -(-(q - 1).bit_length() // b)
+    S = sum(1 << (b * i) for i in range(L))
+    vals = np.array([((h - 1) * S) % q, (q - h * S) % q if h * S < q else 1, q - 1, 0, h - 1, q - h],
                     dtype=np.uint64)
     A2 = vals[synth.u64(k, 5, k * n) % np.uint64(len(vals))].reshape(1, k, n)
     U2 = np.where(synth.u64(k, 6, d * k).reshape(d, k) & np.uint64(1), 127, -128).astype(np.int8)
