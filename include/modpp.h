@@ -184,6 +184,42 @@ int modpp_profile_enable(int on);
 int modpp_profile_read(int kernel, double *total_ms, int64_t *launches);
 
 /*
+ * Mod-PP-MM without any device allocation by the caller or the library.
+ * (No counterpart in the paper: this is an interface for callers that cannot
+ * allocate device memory, for example applications whose memory manager owns
+ * the whole GPU, plugin hosts that forbid device allocation on the call path,
+ * or code that cannot accept an allocation's synchronisation and latency.)
+ *
+ * Same computation, arguments and layouts as modpp_mm on MODPP_PATH_F16, but
+ * the scratch space is a fixed array of MODPP_STATIC_SCRATCH_BYTES (64 MiB)
+ * compiled into the library.  Every GPU that loads the library holds that
+ * array until the process exits.  The caller still passes the inputs and the
+ * outputs (device pointers).
+ *
+ * - The first call on each device looks up the array's device address
+ *   (cudaGetSymbolAddress) with that device current, and caches it.  Make
+ *   that first call before any stream capture on the device.
+ * - A request whose scratch need, modpp_mm_workspace(d, k, n, primes, P,
+ *   MODPP_PATH_F16), exceeds MODPP_STATIC_SCRATCH_BYTES is rejected with
+ *   MODPP_ERR_WORKSPACE before anything is enqueued.  Invalid sizes or primes
+ *   return MODPP_ERR_ARG / MODPP_ERR_PRIME as in modpp_mm.
+ * - It calls no cudaMalloc, cudaFree or other allocating routine.
+ * - All calls on a device share the one array, which keeps the last call's
+ *   contents.  Each call clears what must start at zero (the status word)
+ *   and overwrites the rest before reading it.  Calls whose execution can
+ *   overlap on the GPU (different streams without ordering, or several host
+ *   threads) race on the array and give unspecified results: serialise them.
+ * - Device-side status: modpp_status_read() is not available for this entry
+ *   point (the status word lives in the static array).
+ */
+#define MODPP_STATIC_SCRATCH_BYTES ((size_t)64 << 20)
+
+size_t modpp_mm_static_capacity(void);
+int modpp_mm_static(int64_t d, int64_t k, int64_t n, const void *U, int ukind, int64_t ldu,
+                    const uint64_t *A, int64_t lda, int64_t strideA, uint64_t *C, int64_t ldc,
+                    int64_t strideC, const uint64_t *primes_host, int P, void *stream);
+
+/*
  * Waits for `stream`, reads and clears the device status word kept in the
  * workspace `ws`.  Returns MODPP_OK, MODPP_ERR_TIMEOUT (a bounded device wait
  * gave up; the kernel returned early and its outputs are unspecified) or
