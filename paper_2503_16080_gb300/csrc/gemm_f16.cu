@@ -15,15 +15,17 @@
 // (Lemma le:strategy1, exact chopping) with the digit base and chunk sized for
 // FP32 tensor-core accumulation instead of binary64 BLAS.
 //
-// Tile: 128 output rows x 32 output columns x L digits.  The L digit rows of
-// the 32 columns are adjacent in the digit matrix, so one UMMA of N = 32 L
+// Tile: 128 output rows x NC output columns x L digits, NC = tile_cols(L)
+// (64, 48, 40 or 32, so that N = NC * L is 224..256).  The L digit rows of the
+// NC columns are adjacent in the digit matrix, so one UMMA of N = NC * L
 // computes all digits of the tile and reuses the U tile L times.
 //
 // Warp roles (320 threads, one CTA per SM, persistent over tiles):
 //   warp 0      TMA producer: U and digit tiles -> shared-memory ring
 //   warp 1      TMEM owner and single-thread MMA issuer
-//   warps 2-9   epilogue: TMEM -> registers, integer accumulation, modular
-//               recombination, global stores
+//   warps 2-9   epilogue: TMEM -> registers, int64 accumulation of each
+//               group of three digits (one IMAD.WIDE per value), modular
+//               recombination at the end of the tile, global stores
 // Two TMEM accumulators (columns 0.. and 256..) alternate between chunks, so
 // the epilogue drains one while the tensor cores fill the other.
 #include <cuda_fp16.h>
@@ -36,7 +38,8 @@ namespace modpp {
 
 template <int L>
 struct GemmCfg {
-    static constexpr int BN = L * kNC;
+    static constexpr int NC = tile_cols(L);
+    static constexpr int BN = L * NC;
     static constexpr int A_BYTES = kBM * kBK * 2;
     static constexpr int B_BYTES = BN * kBK * 2;
     static constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
@@ -119,7 +122,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                 int mb, nb, plane;
                 decode_tile(tile, p.m_blocks, p.n_blocks, mb, nb, plane);
                 const int ay = mb * kBM;
-                const int by = (plane * p.n_blocks + nb) * L * kNC;
+                const int by = (plane * p.n_blocks + nb) * L * Cfg::NC;
                 for (int kb = 0; kb < p.kb_total; ++kb, ++it) {
                     const int s = static_cast<int>(it % STAGES);
                     const uint32_t ph = (it / STAGES) & 1u;
@@ -182,18 +185,26 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
     } else {
         // ------------------------------------------------ epilogue warps
+        constexpr int NC = Cfg::NC;
+        constexpr int NCH = NC / 2;          // columns per epilogue warp
+        constexpr int G = (L + 2) / 3;       // digit groups: digits 3g, 3g+1, 3g+2
         const int ew = warp - 2;
         const int quarter = warp & 3;  // TMEM lane quarter this warp may access
-        const int half = ew >> 2;      // which 16 of the tile's 32 columns
+        const int half = ew >> 2;      // which half of the tile's columns
         const uint32_t lane_off = static_cast<uint32_t>(quarter * 32) << 16;
-        int64_t acc_lo[16], acc_hi[16], acc_top[16];
+        // grp[g][c] = sum over chunks of sum_{j<3} 2^(b j) * C_{3g+j}.  A chunk
+        // adds at most 2^24 (1 + 2^b + 2^(2b)) < 2^(25+2b); with at most
+        // 2^(2+b) chunks (k <= 2^20) the total stays below 2^(27+3b) <= 2^57.
+        int64_t grp[G][NCH];
         uint32_t g = 0;
         bool ok = true;
         for (int tile = blockIdx.x; ok && tile < p.num_tiles; tile += gridDim.x) {
             int mb, nb, plane;
             decode_tile(tile, p.m_blocks, p.n_blocks, mb, nb, plane);
 #pragma unroll
-            for (int c = 0; c < 16; ++c) acc_lo[c] = acc_hi[c] = acc_top[c] = 0;
+            for (int gi = 0; gi < G; ++gi)
+#pragma unroll
+                for (int c = 0; c < NCH; ++c) grp[gi][c] = 0;
             for (int ch = 0; ch < n_chunks; ++ch, ++g) {
                 const uint32_t buf = g & 1u, use = g >> 1;
                 const bool got = mbar_wait_bounded(&tfull[buf], use & 1u, abort_flag, p.timeout_ns);
@@ -202,43 +213,38 @@ __global__ void __launch_bounds__(kThreads, 1)
                     break;
                 }
                 tc_fence_after();
-                const uint32_t base = tmem_base + lane_off + buf * Cfg::ACC_STRIDE + half * 16;
+                const uint32_t base = tmem_base + lane_off + buf * Cfg::ACC_STRIDE + half * NCH;
 #pragma unroll
                 for (int l = 0; l < L; ++l) {
-                    uint32_t r[16];
-                    tmem_ld_32x32b_x16(base + l * kNC, r);
+                    uint32_t r[NCH];
+                    tmem_ld_cols<NCH>(base + l * NC, r);
                     tmem_wait_ld();
+                    constexpr int kW[3] = {1, 1 << DB, 1 << (2 * DB)};
 #pragma unroll
-                    for (int c = 0; c < 16; ++c) {
-                        const int64_t v = __float2int_rn(__uint_as_float(r[c]));
-                        if (l < 3)
-                            acc_lo[c] += v << (DB * l);
-                        else if (l < 6)
-                            acc_hi[c] += v << (DB * (l - 3));
-                        else
-                            acc_top[c] += v << (DB * (l - 6));
-                    }
+                    for (int c = 0; c < NCH; ++c)
+                        grp[l / 3][c] = mad_wide_s32(__float2int_rn(__uint_as_float(r[c])),
+                                                     kW[l % 3], grp[l / 3][c]);
                 }
                 tc_fence_before();
                 __syncwarp();
                 if (lane == 0) mbar_arrive(&tempty[buf]);
             }
             if (!ok) break;
-            // value = lo + 2^(3b) hi + 2^(6b) top  (mod q)
+            // value = grp0 + 2^(3b) grp1 + 2^(6b) grp2  (mod q)
             const int row = mb * kBM + quarter * 32 + lane;
-            const int col0 = nb * kNC + half * 16;
+            const int col0 = nb * NC + half * NCH;
             if (row < p.d) {
                 const PlaneConst &pc = p.pc[plane];
                 uint64_t *out = pc.C + static_cast<int64_t>(row) * pc.ldc + col0;
 #pragma unroll
-                for (int c = 0; c < 16; ++c) {
-                    uint64_t v = smod_i64(acc_lo[c], pc.q, pc.mu);
-                    if (L > 3)
-                        v = add_mod(v, shoup_mulmod(smod_i64(acc_hi[c], pc.q, pc.mu), pc.wg1,
+                for (int c = 0; c < NCH; ++c) {
+                    uint64_t v = smod_i64(grp[0][c], pc.q, pc.mu);
+                    if constexpr (G > 1)
+                        v = add_mod(v, shoup_mulmod(smod_i64(grp[1][c], pc.q, pc.mu), pc.wg1,
                                                     pc.wg1s, pc.q),
                                     pc.q);
-                    if (L > 6)
-                        v = add_mod(v, shoup_mulmod(smod_i64(acc_top[c], pc.q, pc.mu), pc.wg2,
+                    if constexpr (G > 2)
+                        v = add_mod(v, shoup_mulmod(smod_i64(grp[2][c], pc.q, pc.mu), pc.wg2,
                                                     pc.wg2s, pc.q),
                                     pc.q);
                     if (col0 + c < p.n) out[c] = v;

@@ -78,9 +78,10 @@ F16Layout f16_layout(int64_t d, int64_t k, int64_t n, const uint64_t *qs, int pl
         const int l = f16_digit_count(qs[i], lay.b);
         if (l > lay.L) lay.L = l;
     }
+    const int nc = tile_cols(lay.L);
     lay.kp = (k + 7) / 8 * 8;
-    lay.n_blocks = (n + kNC - 1) / kNC;
-    lay.rows = static_cast<int64_t>(planes) * lay.n_blocks * lay.L * kNC;
+    lay.n_blocks = (n + nc - 1) / nc;
+    lay.rows = static_cast<int64_t>(planes) * lay.n_blocks * lay.L * nc;
     lay.off_u16 = kHeaderBytes;
     lay.off_d = lay.off_u16 + align_up(static_cast<size_t>(d) * lay.kp * 2);
     lay.total = lay.off_d + align_up(static_cast<size_t>(lay.rows) * lay.kp * 2);
@@ -283,7 +284,7 @@ int run_f16(int64_t d, int64_t k, int64_t n, const void *U, int ukind, int64_t l
     if (!make_map_f16(&tmU, U16, static_cast<uint64_t>(lay.kp), static_cast<uint64_t>(d), kBK, kBM))
         return MODPP_ERR_CUDA;
     if (!make_map_f16(&tmD, D, static_cast<uint64_t>(lay.kp), static_cast<uint64_t>(lay.rows), kBK,
-                      static_cast<uint32_t>(lay.L * kNC)))
+                      static_cast<uint32_t>(lay.L * tile_cols(lay.L))))
         return MODPP_ERR_CUDA;
 
     GemmParams gp{};

@@ -12,7 +12,14 @@ namespace modpp {
 
 constexpr int kMaxPlanes = 32;       // (prime, part) output planes per launch
 constexpr int kBM = 128;             // output rows per tile (UMMA M)
-constexpr int kNC = 32;              // output columns per tile
+// Output columns per tile for L digits: the UMMA N = L * cols is a multiple
+// of 16 up to 256 (192..256 for L >= 3), each of the two epilogue column halves
+// is a whole number of 4-column TMEM loads, and the epilogue's int64 group
+// accumulators (one per 3 digits and column) fit the register budget.
+__host__ __device__ constexpr int tile_cols(int L) {
+    return L <= 3 ? 64 : (L <= 5 ? 48 : (L == 6 ? 40 : 32));
+}
+constexpr int kMaxTileCols = 64;
 constexpr int kBK = 64;              // f16 elements per K block (one 128-byte row)
 constexpr int kMinDigitBits = 8;     // balanced b-bit digits in [-2^(b-1), 2^(b-1) - 1]
 constexpr int kMaxDigitBits = 10;
@@ -37,7 +44,7 @@ struct PlaneConst {
 struct GemmParams {
     int d, n, k;      // output rows, output columns, inner dimension
     int m_blocks;     // ceil(d / kBM)
-    int n_blocks;     // ceil(n / kNC)
+    int n_blocks;     // ceil(n / tile_cols(L))
     int planes;
     int kb_total;     // ceil(k / kBK)
     int num_tiles;    // planes * n_blocks * m_blocks

@@ -45,7 +45,7 @@ cudaError_t launch_u_to_f16(const void *U, int ukind, int64_t ldu, int d, int k,
 }
 
 // ---------------------------------------------------------------- digits
-// Block tile: 64 inner indices t x 32 columns c of one plane.
+// Block tile: 64 inner indices t x NC columns c (one column block) of one plane.
 // Phase 1 reads A coalesced along c, computes the L digits of each residue
 // and stores them in shared memory as [l][c][t].  Phase 2 writes each
 // (l, c) row of 64 digits (128 bytes) contiguously along t.
@@ -54,20 +54,20 @@ constexpr int kSplitRow = kSplitT + 4;  // padded row (halves): 136-byte rows
 
 template <int L, int DB>
 __global__ void __launch_bounds__(256) split_digits_kernel(const __grid_constant__ SplitParams p) {
+    constexpr int NC = tile_cols(L);
     constexpr int64_t kHalf = int64_t(1) << (DB - 1);
     constexpr int64_t kMask = (int64_t(1) << DB) - 1;
-    __shared__ __align__(16) __half tile[L * kNC * kSplitRow];
+    __shared__ __align__(16) __half tile[L * NC * kSplitRow];
     const int plane = blockIdx.z;
     const int t0 = blockIdx.x * kSplitT;
     const int nb = blockIdx.y;
-    const int c0 = nb * kNC;
+    const int c0 = nb * NC;
     const SplitPlane sp = p.sp[plane];
-    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
 
-#pragma unroll
-    for (int i = 0; i < kSplitT / 8; ++i) {
-        const int tl = ty + 8 * i;
-        const int t = t0 + tl, c = c0 + tx;
+#pragma unroll 4
+    for (int e = threadIdx.x; e < kSplitT * NC; e += 256) {
+        const int tl = e / NC, cl = e - (e / NC) * NC;
+        const int t = t0 + tl, c = c0 + cl;
         uint64_t a = 0;
         if (t < p.k && c < p.n) a = sp.A[static_cast<int64_t>(t) * sp.lda + c];
         // Lift into the balanced window, then peel digits from the bottom:
@@ -77,7 +77,7 @@ __global__ void __launch_bounds__(256) split_digits_kernel(const __grid_constant
         for (int l = 0; l < L; ++l) {
             const int dgt = static_cast<int>(((x + kHalf) & kMask) - kHalf);
             x = (x - dgt) >> DB;
-            tile[(l * kNC + tx) * kSplitRow + tl] = __int2half_rn(dgt);
+            tile[(l * NC + cl) * kSplitRow + tl] = __int2half_rn(dgt);
         }
     }
     __syncthreads();
@@ -85,10 +85,9 @@ __global__ void __launch_bounds__(256) split_digits_kernel(const __grid_constant
     // 16 threads per 128-byte row, 4 halves (8 bytes) each.
     const int sub = threadIdx.x & 15;
     const int t = t0 + 4 * sub;
-    for (int row = threadIdx.x >> 4; row < L * kNC; row += 16) {
+    for (int row = threadIdx.x >> 4; row < L * NC; row += 16) {
         if (t < p.kp) {
-            const int l = row / kNC, c = row - l * kNC;
-            const int64_t grow = ((static_cast<int64_t>(plane) * p.n_blocks + nb) * L + l) * kNC + c;
+            const int64_t grow = (static_cast<int64_t>(plane) * p.n_blocks + nb) * L * NC + row;
             const uint2 v = *reinterpret_cast<const uint2 *>(&tile[row * kSplitRow + 4 * sub]);
             *reinterpret_cast<uint2 *>(p.D + grow * p.kp + t) = v;
         }
