@@ -188,6 +188,8 @@ __global__ void __launch_bounds__(kThreads, 1)
         constexpr int NC = Cfg::NC;
         constexpr int NCH = NC / 2;          // columns per epilogue warp
         constexpr int G = (L + 2) / 3;       // digit groups: digits 3g, 3g+1, 3g+2
+        constexpr int CW = (L >= 7 || NCH % 8 != 0) ? 4 : 8;  // columns per TMEM load group
+        constexpr int kDigitWeight[3] = {1, 1 << DB, 1 << (2 * DB)};
         const int ew = warp - 2;
         const int quarter = warp & 3;  // TMEM lane quarter this warp may access
         const int half = ew >> 2;      // which half of the tile's columns
@@ -214,16 +216,21 @@ __global__ void __launch_bounds__(kThreads, 1)
                 }
                 tc_fence_after();
                 const uint32_t base = tmem_base + lane_off + buf * Cfg::ACC_STRIDE + half * NCH;
+                // All L digits of a group of CW columns are loaded before one
+                // wait, so a chunk costs NCH / CW TMEM round trips, not L.
 #pragma unroll
-                for (int l = 0; l < L; ++l) {
-                    uint32_t r[NCH];
-                    tmem_ld_cols<NCH>(base + l * NC, r);
+                for (int c0 = 0; c0 < NCH; c0 += CW) {
+                    uint32_t r[L][CW];
+#pragma unroll
+                    for (int l = 0; l < L; ++l) tmem_ld_group<CW>(base + l * NC + c0, r[l]);
                     tmem_wait_ld();
-                    constexpr int kW[3] = {1, 1 << DB, 1 << (2 * DB)};
 #pragma unroll
-                    for (int c = 0; c < NCH; ++c)
-                        grp[l / 3][c] = mad_wide_s32(__float2int_rn(__uint_as_float(r[c])),
-                                                     kW[l % 3], grp[l / 3][c]);
+                    for (int l = 0; l < L; ++l)
+#pragma unroll
+                        for (int c = 0; c < CW; ++c)
+                            grp[l / 3][c0 + c] = mad_wide_s32(
+                                __float2int_rn(__uint_as_float(r[l][c])), kDigitWeight[l % 3],
+                                grp[l / 3][c0 + c]);
                 }
                 tc_fence_before();
                 __syncwarp();

@@ -172,6 +172,16 @@ __device__ __forceinline__ int64_t mad_wide_s32(int32_t a, int32_t b, int64_t ac
     return d;
 }
 
+// CW (4 or 8) consecutive 32-bit columns for the warp's 32 lanes.
+template <int CW>
+__device__ __forceinline__ void tmem_ld_group(uint32_t taddr, uint32_t *r) {
+    static_assert(CW == 4 || CW == 8, "group width");
+    if constexpr (CW == 8)
+        tmem_ld_32x32b_x8(taddr, r);
+    else
+        tmem_ld_32x32b_x4(taddr, r);
+}
+
 __device__ __forceinline__ void tmem_wait_ld() {
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }

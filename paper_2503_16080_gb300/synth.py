@@ -44,6 +44,15 @@ def u64(seed: int, stream: int, count: int, start: int = 0) -> np.ndarray:
         return _mix(base + idx * _GAMMA)
 
 
+def u64_at(seed: int, stream: int, index: np.ndarray) -> np.ndarray:
+    """The draws of the stream at the given flat indices (same bits as u64)."""
+    with np.errstate(over="ignore"):
+        base = (np.uint64(seed & 0xFFFFFFFFFFFFFFFF) * _G1
+                + np.uint64(stream & 0xFFFFFFFFFFFFFFFF) * _G2)
+        idx = np.asarray(index, dtype=np.uint64) + np.uint64(1)
+        return _mix(base + idx * _GAMMA)
+
+
 def _mulhi(x: np.ndarray, q: int) -> np.ndarray:
     """floor(x * q / 2^64) for uint64 x and q < 2^64, exactly, in uint64 pieces."""
     qh, ql = np.uint64(q >> 32), np.uint64(q & 0xFFFFFFFF)
@@ -62,10 +71,20 @@ def uniform_mod(seed: int, stream: int, shape, q: int) -> np.ndarray:
     return _mulhi(u64(seed, stream, n), int(q)).reshape(shape)
 
 
+def uniform_mod_at(seed: int, stream: int, index: np.ndarray, q: int) -> np.ndarray:
+    """Entries of uniform_mod(seed, stream, shape, q) at the given flat indices."""
+    return _mulhi(u64_at(seed, stream, index), int(q))
+
+
 def uniform_int8(seed: int, stream: int, shape) -> np.ndarray:
     """Uniform integers in [-128, 127] (int8 range)."""
     n = int(np.prod(shape))
     return (u64(seed, stream, n) >> np.uint64(56)).astype(np.uint8).view(np.int8).reshape(shape)
+
+
+def uniform_int8_at(seed: int, stream: int, index: np.ndarray) -> np.ndarray:
+    """Entries of uniform_int8(seed, stream, shape) at the given flat indices."""
+    return (u64_at(seed, stream, index) >> np.uint64(56)).astype(np.uint8).view(np.int8)
 
 
 def uniform_unit(seed: int, stream: int, shape) -> np.ndarray:
@@ -168,3 +187,62 @@ def random_primes(seed: int, stream: int, count: int, lo_bits: int, hi_bits: int
         if c not in out:
             out.append(c)
     return out
+
+
+# --------------------------------------------------------------------------
+# The same streams drawn on a torch device (bit-identical to the numpy ones).
+# Large residue matrices are generated where they are used; the CPU can
+# regenerate any sampled entry through the *_at functions above.
+# --------------------------------------------------------------------------
+
+def _to_i64(v: int) -> int:
+    v &= 0xFFFFFFFFFFFFFFFF
+    return v - (1 << 64) if v >= (1 << 63) else v
+
+
+def _shr(x, k: int):
+    """Logical right shift of an int64 tensor holding uint64 bits."""
+    import torch
+    return torch.bitwise_and(torch.bitwise_right_shift(x, k), _to_i64((1 << (64 - k)) - 1))
+
+
+def u64_torch(seed: int, stream: int, count: int, device, start: int = 0):
+    """Same bits as u64(seed, stream, count, start), as an int64 tensor on `device`."""
+    import torch
+    base = _to_i64((seed & 0xFFFFFFFFFFFFFFFF) * 0xD1B54A32D192ED03
+                   + (stream & 0xFFFFFFFFFFFFFFFF) * 0xABC98388FB8FAC03)
+    z = torch.arange(start + 1, start + 1 + count, dtype=torch.int64, device=device)
+    z = z * _to_i64(0x9E3779B97F4A7C15) + base
+    z = torch.bitwise_xor(z, _shr(z, 30)) * _to_i64(0xBF58476D1CE4E5B9)
+    z = torch.bitwise_xor(z, _shr(z, 27)) * _to_i64(0x94D049BB133111EB)
+    return torch.bitwise_xor(z, _shr(z, 31))
+
+
+def uniform_mod_torch(seed: int, stream: int, shape, q: int, device, chunk: int = 1 << 26):
+    """uniform_mod(seed, stream, shape, q) generated on `device` (torch.uint64)."""
+    import torch
+    n = int(np.prod(shape))
+    out = torch.empty(n, dtype=torch.int64, device=device)
+    qh, ql = int(q) >> 32, int(q) & 0xFFFFFFFF
+    m32 = 0xFFFFFFFF
+    for s0 in range(0, n, chunk):
+        cnt = min(chunk, n - s0)
+        x = u64_torch(seed, stream, cnt, device, start=s0)
+        xh, xl = _shr(x, 32), torch.bitwise_and(x, m32)
+        ll, hl, lh = xl * ql, xh * ql, xl * qh
+        mid = _shr(ll, 32) + torch.bitwise_and(hl, m32) + torch.bitwise_and(lh, m32)
+        out[s0:s0 + cnt] = xh * qh + _shr(hl, 32) + _shr(lh, 32) + _shr(mid, 32)
+    return out.view(torch.uint64).reshape(shape)
+
+
+def uniform_int8_torch(seed: int, stream: int, shape, device, chunk: int = 1 << 26):
+    """uniform_int8(seed, stream, shape) generated on `device` (torch.int8)."""
+    import torch
+    n = int(np.prod(shape))
+    out = torch.empty(n, dtype=torch.int8, device=device)
+    for s0 in range(0, n, chunk):
+        cnt = min(chunk, n - s0)
+        x = u64_torch(seed, stream, cnt, device, start=s0)
+        # top byte as a signed int8: arithmetic shift keeps the sign bit
+        out[s0:s0 + cnt] = torch.bitwise_right_shift(x, 56).to(torch.int8)
+    return out.reshape(shape)
