@@ -46,7 +46,7 @@ struct GemmCfg {
     static constexpr int SMEM_LIMIT = 232448;  // opt-in dynamic shared memory per CTA
     static constexpr int RESERVED = 1024 + 256;
     static constexpr int FIT = (SMEM_LIMIT - RESERVED) / STAGE_BYTES;
-    static constexpr int STAGES = FIT > 6 ? 6 : FIT;
+    static constexpr int STAGES = FIT > 8 ? 8 : FIT;
     static constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + RESERVED;
     static constexpr uint32_t TMEM_COLS = 512;
     static constexpr uint32_t ACC_STRIDE = 256;
@@ -170,8 +170,8 @@ __global__ void __launch_bounds__(kThreads, 1)
                         const uint32_t b_addr = a_addr + Cfg::A_BYTES;
 #pragma unroll
                         for (int ks = 0; ks < kBK / 16; ++ks) {
-                            umma_f16_ss(dtm, sdesc_kmajor_sw128(a_addr + ks * 32),
-                                        sdesc_kmajor_sw128(b_addr + ks * 32), idesc,
+                            umma_f16_ss(dtm, sdesc_kmajor<kRowBytes>(a_addr + ks * 32),
+                                        sdesc_kmajor<kRowBytes>(b_addr + ks * 32), idesc,
                                         (kb > kb0 || ks > 0) ? 1u : 0u);
                         }
                         umma_commit(&empty[s]);

@@ -181,9 +181,9 @@ EncodeTiledFn encode_fn() {
     return fn;
 }
 
-// 2-D f16 tensor [outer][inner] with 128-byte swizzled boxes of
-// box_inner x box_outer (box_inner * 2 = 128 bytes).  Elements outside the
-// tensor read as zero.
+// 2-D f16 tensor [outer][inner] with swizzled boxes of box_inner x box_outer
+// (box_inner * 2 = kRowBytes, the swizzle span).  Elements outside the tensor
+// read as zero.
 bool make_map_f16(CUtensorMap *m, const void *base, uint64_t inner, uint64_t outer,
                   uint32_t box_inner, uint32_t box_outer) {
     EncodeTiledFn fn = encode_fn();
@@ -193,7 +193,8 @@ bool make_map_f16(CUtensorMap *m, const void *base, uint64_t inner, uint64_t out
     cuuint32_t box[2] = {box_inner, box_outer};
     cuuint32_t estr[2] = {1, 1};
     return fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2, const_cast<void *>(base), dims, strides, box,
-              estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+              estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+              kRowBytes == 128 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B,
               CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) ==
            CUDA_SUCCESS;
 }

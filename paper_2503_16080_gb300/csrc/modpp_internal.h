@@ -20,7 +20,9 @@ __host__ __device__ constexpr int tile_cols(int L) {
     return L <= 3 ? 64 : (L <= 5 ? 48 : (L == 6 ? 40 : 32));
 }
 constexpr int kMaxTileCols = 64;
-constexpr int kBK = 64;              // f16 elements per K block (one 128-byte row)
+constexpr int kBK = 64;              // f16 elements per K block: one 128-byte row
+constexpr int kRowBytes = kBK * 2;   // swizzle span of the operand tiles (64 or 128)
+static_assert(kRowBytes == 64 || kRowBytes == 128, "K block must be a 64- or 128-byte row");
 constexpr int kMinDigitBits = 8;     // balanced b-bit digits in [-2^(b-1), 2^(b-1) - 1]
 constexpr int kMaxDigitBits = 10;
 constexpr int kMaxDigits = 8;        // q < 2^62 needs at most 8 eight-bit digits

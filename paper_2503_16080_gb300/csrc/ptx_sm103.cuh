@@ -187,22 +187,25 @@ __device__ __forceinline__ void tmem_wait_ld() {
 }
 
 // Shared-memory matrix descriptor for a K-major operand tile stored in the
-// 128-byte swizzled canonical layout that a TMA load with
-// CU_TENSOR_MAP_SWIZZLE_128B produces: rows of 128 bytes, 8-row (1024-byte)
-// swizzle atoms stacked along M/N.
+// swizzled canonical layout that a TMA load with the matching swizzle mode
+// produces: rows of ROW_BYTES (64 or 128) bytes, 8-row swizzle atoms of
+// 8 * ROW_BYTES bytes stacked along M/N.
 //   bits  0-13  start address >> 4
-//   bits 16-29  leading-dimension byte offset >> 4 (unused for this layout)
-//   bits 32-45  stride-dimension byte offset >> 4 (1024 B between atoms)
+//   bits 16-29  leading-dimension byte offset >> 4 (unused for these layouts)
+//   bits 32-45  stride-dimension byte offset >> 4 (8 * ROW_BYTES between atoms)
 //   bits 46-47  descriptor version (1 for tcgen05)
-//   bits 49-51  base offset (0: atoms are 1024-byte aligned)
-//   bits 61-63  layout type (2 = SWIZZLE_128B)
-__device__ __forceinline__ uint64_t sdesc_kmajor_sw128(uint32_t smem_addr) {
+//   bits 49-51  base offset (0: atoms are aligned to their size)
+//   bits 61-63  layout type (2 = SWIZZLE_128B, 4 = SWIZZLE_64B)
+template <int ROW_BYTES>
+__device__ __forceinline__ uint64_t sdesc_kmajor(uint32_t smem_addr) {
+    static_assert(ROW_BYTES == 64 || ROW_BYTES == 128, "swizzle span");
+    constexpr uint64_t kLayout = ROW_BYTES == 128 ? 2 : 4;
     uint64_t d = 0;
     d |= static_cast<uint64_t>((smem_addr & 0x3FFFFu) >> 4);
     d |= static_cast<uint64_t>(1) << 16;
-    d |= static_cast<uint64_t>(1024 >> 4) << 32;
+    d |= static_cast<uint64_t>((8 * ROW_BYTES) >> 4) << 32;
     d |= static_cast<uint64_t>(1) << 46;
-    d |= static_cast<uint64_t>(2) << 61;
+    d |= kLayout << 61;
     return d;
 }
 
