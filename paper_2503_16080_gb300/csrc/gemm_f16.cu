@@ -243,18 +243,33 @@ __global__ void __launch_bounds__(kThreads, 1)
             if (row < p.d) {
                 const PlaneConst &pc = p.pc[plane];
                 uint64_t *out = pc.C + static_cast<int64_t>(row) * pc.ldc + col0;
+                // Whole 32-byte sectors per lane when the row segment is aligned
+                // and inside the matrix; element stores otherwise.
+                const bool vec = (reinterpret_cast<uintptr_t>(out) & 31u) == 0 && col0 + NCH <= p.n;
 #pragma unroll
-                for (int c = 0; c < NCH; ++c) {
-                    uint64_t v = smod_i64(grp[0][c], pc.q, pc.mu);
-                    if constexpr (G > 1)
-                        v = add_mod(v, shoup_mulmod(smod_i64(grp[1][c], pc.q, pc.mu), pc.wg1,
-                                                    pc.wg1s, pc.q),
-                                    pc.q);
-                    if constexpr (G > 2)
-                        v = add_mod(v, shoup_mulmod(smod_i64(grp[2][c], pc.q, pc.mu), pc.wg2,
-                                                    pc.wg2s, pc.q),
-                                    pc.q);
-                    if (col0 + c < p.n) out[c] = v;
+                for (int c0 = 0; c0 < NCH; c0 += 4) {
+                    uint64_t v[4];
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                        const int c = c0 + j;
+                        uint64_t x = smod_i64(grp[0][c], pc.q, pc.mu);
+                        if constexpr (G > 1)
+                            x = add_mod(x, shoup_mulmod(smod_i64(grp[1][c], pc.q, pc.mu), pc.wg1,
+                                                        pc.wg1s, pc.q),
+                                        pc.q);
+                        if constexpr (G > 2)
+                            x = add_mod(x, shoup_mulmod(smod_i64(grp[2][c], pc.q, pc.mu), pc.wg2,
+                                                        pc.wg2s, pc.q),
+                                        pc.q);
+                        v[j] = x;
+                    }
+                    if (vec) {
+                        st_global_v4_u64(out + c0, v[0], v[1], v[2], v[3]);
+                    } else {
+#pragma unroll
+                        for (int j = 0; j < 4; ++j)
+                            if (col0 + c0 + j < p.n) out[c0 + j] = v[j];
+                    }
                 }
             }
         }

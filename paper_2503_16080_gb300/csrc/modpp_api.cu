@@ -44,7 +44,7 @@ int check_sizes(int64_t d, int64_t k, int64_t n) {
 
 // Digit width of the f16 path: 0 selects the default.  Narrower digits allow
 // deeper exact FP32 chunks (fewer TMEM drains) at the cost of more digits.
-constexpr int kDefaultDigitBits = 8;
+constexpr int kDefaultDigitBits = 9;
 std::atomic<int> g_digit_bits{0};
 int current_digit_bits() {
     const int b = g_digit_bits.load();

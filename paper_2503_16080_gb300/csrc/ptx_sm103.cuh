@@ -165,6 +165,14 @@ __device__ __forceinline__ void tmem_ld_cols(uint32_t taddr, uint32_t (&r)[NCH])
     if constexpr (NCH == 32) tmem_ld_32x32b_x16p(taddr + 16, r + 16);
 }
 
+// 32-byte vector store (one full L2 sector per lane); p must be 32-byte aligned.
+__device__ __forceinline__ void st_global_v4_u64(uint64_t *p, uint64_t a, uint64_t b, uint64_t c,
+                                                 uint64_t d) {
+    asm volatile("st.global.v4.u64 [%0], {%1, %2, %3, %4};" ::"l"(p), "l"(a), "l"(b), "l"(c),
+                 "l"(d)
+                 : "memory");
+}
+
 // acc + a * b with a 32x32 -> 64-bit signed product (one IMAD.WIDE).
 __device__ __forceinline__ int64_t mad_wide_s32(int32_t a, int32_t b, int64_t acc) {
     int64_t d;
