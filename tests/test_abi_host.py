@@ -91,11 +91,14 @@ def test_fp64_plan_matches_lemma(api):
 def test_workspace_sizes(api):
     q = synth.ntt_primes(50, 3)
     L = api.plan_info(4096, q[0])["digits"]
-    # f16: 256 B header + U16 (d x kp halves) + digits (planes x n_blocks x L x 32 x kp halves)
+    # Tile columns per digit count (UMMA N = L * nc between 192 and 256).
+    nc = 64 if L <= 3 else 48 if L <= 5 else 40 if L == 6 else 32
+    nb = -(-4096 // nc)
+    # f16: 256 B header + U16 (d x kp halves) + digits (planes x n_blocks x L x nc x kp halves)
     ws = api.workspace_bytes(4096, 4096, 4096, q[:1])
-    assert ws == 256 + 4096 * 4096 * 2 + 128 * L * 32 * 4096 * 2
+    assert ws == 256 + 4096 * 4096 * 2 + nb * L * nc * 4096 * 2
     pc = api.workspace_bytes(4096, 4096, 4096, q, kind="pc_mm")
-    assert pc == 256 + 4096 * 4096 * 2 + 6 * 128 * L * 32 * 4096 * 2
+    assert pc == 256 + 4096 * 4096 * 2 + 6 * nb * L * nc * 4096 * 2
     assert api.workspace_bytes(-1, 4, 4, q[:1]) == 0
     assert api.workspace_bytes(4, 4, 4, [4]) == 0
 
