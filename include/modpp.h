@@ -166,6 +166,64 @@ int pc_mv(int64_t d, int64_t kct, int64_t nvec, const int8_t *U, const uint64_t 
           int path, void *ws, size_t ws_bytes, void *stream);
 
 /*
+ * Grouped Mod-PP-MM: many independent products of uneven sizes, each with its
+ * own prime list, computed by three launches for the whole group.
+ *
+ *   C_i,j = U_i * A_i,j  mod q_i,j     for every problem i and prime j.
+ *
+ * One modpp_problem describes problem i with the layout of modpp_mm:
+ *   U      d x k int8 (values in [-128, 127]), leading dimension ldu >= k;
+ *   A      P planes k x n, plane j at A + j*strideA, leading dimension lda >= n;
+ *   C      P planes d x n, plane j at C + j*strideC, leading dimension ldc >= n;
+ *   primes host array of P primes (odd, 3 <= q < 2^62); 1 <= P <= 32.
+ * Sizes as modpp_mm (0 <= d, n < 2^31; 0 <= k <= 2^20; k = 0 gives zeros).
+ *
+ * A plan binds the problems (device pointers) and the caller's workspace.
+ * - modpp_group_workspace(): bytes the plan needs (0 on invalid problems).
+ * - modpp_group_plan_create(): validates, lays out the workspace, writes the
+ *   device tables (synchronises `stream` once), and, if `tune` is non-zero,
+ *   chooses the digit width (8, 9 or 10 bits) by timing each candidate on the
+ *   problems themselves.  Tuning runs the products, so the outputs are
+ *   written.  The choice is cached per process, keyed by the sizes, prime
+ *   widths and GPU name, and appended to the file named by the environment
+ *   variable MODPP_TUNE_CACHE when it is set.  Without tuning the process-wide
+ *   width (modpp_set_digit_bits) is used.
+ * - modpp_group_run(): enqueues the three launches on `stream`.
+ * - modpp_group_run_graph(): the first call runs the group once and captures
+ *   the launches in a CUDA graph; every call launches that graph on `stream`.
+ * - modpp_group_plan_info(): chosen digit width, number of GEMM tiles, tuning
+ *   source (0 none, 1 timed, 2 cached) and the timed milliseconds of widths
+ *   8, 9, 10 (tuned_ms[3]; 0 where not timed).
+ * - modpp_group_plan_destroy(): frees the plan's host state and graph.
+ * The workspace's status word (modpp_status_read) reports device timeouts of
+ * the last run.  A plan must not be run concurrently with itself.
+ * (Grouped launch over a device problem table: this build's own scheduling
+ * layer; the products are Mod-PP-MMs as defined in Sec. 5.)
+ */
+typedef struct {
+    int64_t d, k, n;
+    const int8_t *U;
+    int64_t ldu;
+    const uint64_t *A;
+    int64_t lda, strideA;
+    uint64_t *C;
+    int64_t ldc, strideC;
+    const uint64_t *primes;
+    int P;
+} modpp_problem;
+
+typedef struct modpp_group_plan modpp_group_plan;
+
+size_t modpp_group_workspace(const modpp_problem *probs, int count);
+int modpp_group_plan_create(const modpp_problem *probs, int count, void *ws, size_t ws_bytes,
+                            int tune, void *stream, modpp_group_plan **plan);
+int modpp_group_run(modpp_group_plan *plan, void *stream);
+int modpp_group_run_graph(modpp_group_plan *plan, void *stream);
+int modpp_group_plan_info(const modpp_group_plan *plan, int *digit_bits, int *tiles, int *tuned,
+                          double *tuned_ms);
+void modpp_group_plan_destroy(modpp_group_plan *plan);
+
+/*
  * Kernel timing for measurement (no counterpart in the paper: instrumentation).
  * While enabled, every launch of the kernels named by modpp_kernel_id is
  * bracketed by a pair of CUDA events recorded on the launch's stream.

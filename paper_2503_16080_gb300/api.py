@@ -73,6 +73,14 @@ def lib() -> ctypes.CDLL:
         L.pc_mm.argtypes = [I64, I64, I64, P, P, P, P, P, P, I, I, P, SZ, P]
         L.pc_mv.argtypes = [I64, I64, I64, P, P, P, P, P, P, I, I, P, SZ, P]
         L.modpp_status_read.argtypes = [P, P]
+        L.modpp_group_workspace.argtypes = [P, I]
+        L.modpp_group_workspace.restype = SZ
+        L.modpp_group_plan_create.argtypes = [P, I, P, SZ, I, P, P]
+        L.modpp_group_run.argtypes = [P, P]
+        L.modpp_group_run_graph.argtypes = [P, P]
+        L.modpp_group_plan_info.argtypes = [P, P, P, P, P]
+        L.modpp_group_plan_destroy.argtypes = [P]
+        L.modpp_group_plan_destroy.restype = None
         L.modpp_set_digit_bits.argtypes = [I]
         L.modpp_get_digit_bits.restype = I
         L.modpp_profile_enable.argtypes = [I]
@@ -203,7 +211,7 @@ def modpp_mm(U: torch.Tensor, A: torch.Tensor, primes: Sequence[int], *, path="f
     _check_residues(A3, "A")
     if not U.is_cuda or U.dtype not in (torch.int8, torch.int32) or U.dim() != 2:
         raise TypeError("U must be a 2-D CUDA int8 or int32 tensor")
-    if U.stride(1) != 1 or A3.stride(2) != 1:
+    if (U.numel() and U.stride(1) != 1) or (A3.numel() and A3.stride(2) != 1):
         raise ValueError("U and A need unit stride along their last dimension")
     P, k, n = A3.shape
     d = U.shape[0]
@@ -221,9 +229,12 @@ def modpp_mm(U: torch.Tensor, A: torch.Tensor, primes: Sequence[int], *, path="f
         raise ModppError(-1, "modpp_mm_workspace")
     ws_ptr, ws_len = _workspace(need, A3.device, workspace)
     ukind = 0 if U.dtype == torch.int8 else 1
-    rc = lib().modpp_mm(d, k, n, U.data_ptr(), ukind, U.stride(0), A3.data_ptr(), A3.stride(1),
-                        A3.stride(0), out3.data_ptr(), out3.stride(1), out3.stride(0),
-                        pr.ctypes.data, P, p, ws_ptr, ws_len, _stream_handle(stream))
+    ldu = U.stride(0) if U.numel() else k
+    lda, sa = (A3.stride(1), A3.stride(0)) if A3.numel() else (n, k * n)
+    ldc, sc = (out3.stride(1), out3.stride(0)) if out3.numel() else (n, d * n)
+    rc = lib().modpp_mm(d, k, n, U.data_ptr(), ukind, ldu, A3.data_ptr(), lda, sa,
+                        out3.data_ptr(), ldc, sc, pr.ctypes.data, P, p, ws_ptr, ws_len,
+                        _stream_handle(stream))
     _check(rc, "modpp_mm")
     return out3[0] if squeeze else out3
 
@@ -269,3 +280,111 @@ def pc_mv(U: torch.Tensor, A: torch.Tensor, B: torch.Tensor, primes: Sequence[in
           path="f16", out=None, stream=None, workspace=None):
     """PC-Mv on a thin batch: same products as pc_mm with a small column count."""
     return _pc("pc_mv", U, A, B, primes, path, out, stream, workspace)
+
+
+# --------------------------------------------------------------------------
+# Grouped Mod-PP-MM
+# --------------------------------------------------------------------------
+
+class _Problem(ctypes.Structure):
+    _fields_ = [("d", ctypes.c_int64), ("k", ctypes.c_int64), ("n", ctypes.c_int64),
+                ("U", ctypes.c_void_p), ("ldu", ctypes.c_int64),
+                ("A", ctypes.c_void_p), ("lda", ctypes.c_int64), ("strideA", ctypes.c_int64),
+                ("C", ctypes.c_void_p), ("ldc", ctypes.c_int64), ("strideC", ctypes.c_int64),
+                ("primes", ctypes.c_void_p), ("P", ctypes.c_int)]
+
+
+class GroupedPlan:
+    """A grouped Mod-PP-MM over problems (U_i, A_i, primes_i).
+
+    U_i: (d, k) contiguous int8 CUDA tensor; A_i: (P, k, n) contiguous uint64 CUDA
+    tensor; primes_i: P primes.  Outputs are allocated (``self.outputs[i]`` is
+    (P, d, n) uint64) unless given.  ``tune`` lets the library time the digit
+    widths on these problems and keep the fastest.
+    """
+
+    def __init__(self, problems, outputs=None, tune: bool = True, stream=None,
+                 workspace: torch.Tensor | None = None):
+        self._plan = ctypes.c_void_p()
+        self._keep = []
+        self.outputs = []
+        arr = (_Problem * len(problems))()
+        dev = None
+        for i, (U, A, primes) in enumerate(problems):
+            A3 = A.unsqueeze(0) if A.dim() == 2 else A
+            _check_residues(A3, "A")
+            if not U.is_cuda or U.dtype != torch.int8 or U.dim() != 2:
+                raise TypeError("U must be a 2-D CUDA int8 tensor")
+            if U.numel() and U.stride(1) != 1:
+                raise ValueError("U needs unit stride along k")
+            if A3.numel() and A3.stride(2) != 1:
+                raise ValueError("A needs unit stride along n")
+            P, k, n = A3.shape
+            d = U.shape[0]
+            if U.shape[1] != k or len(primes) != P:
+                raise ValueError(f"problem {i}: shape mismatch")
+            C = outputs[i] if outputs is not None else torch.empty(
+                (P, d, n), dtype=torch.uint64, device=A3.device)
+            if C.shape != (P, d, n) or C.stride(2) != 1:
+                raise ValueError(f"problem {i}: output must be (P, d, n) with unit stride along n")
+            pr = _primes_arr(primes)
+            self._keep += [U, A3, C, pr]
+            self.outputs.append(C)
+            # Leading dimensions of empty operands are not meaningful: use the
+            # dense ones so the library's checks hold.
+            ldu = U.stride(0) if U.numel() else k
+            lda, sa = (A3.stride(1), A3.stride(0)) if A3.numel() else (n, k * n)
+            arr[i] = _Problem(d, k, n, U.data_ptr(), ldu, A3.data_ptr(), lda, sa,
+                              C.data_ptr(), C.stride(1), C.stride(0), pr.ctypes.data, P)
+            dev = A3.device
+        self._arr = arr
+        need = int(lib().modpp_group_workspace(ctypes.byref(arr), len(problems)))
+        if need == 0:
+            raise ModppError(-1, "modpp_group_workspace")
+        if workspace is None:
+            workspace = torch.empty(need, dtype=torch.uint8, device=dev)
+        if workspace.data_ptr() % 256 or workspace.numel() * workspace.element_size() < need:
+            raise ValueError("workspace misaligned or too small")
+        self.workspace = workspace
+        _check(lib().modpp_group_plan_create(ctypes.byref(arr), len(problems),
+                                             workspace.data_ptr(), need, 1 if tune else 0,
+                                             _stream_handle(stream), ctypes.byref(self._plan)),
+               "modpp_group_plan_create")
+
+    def run(self, stream=None, graph: bool = False) -> list:
+        fn = lib().modpp_group_run_graph if graph else lib().modpp_group_run
+        _check(fn(self._plan, _stream_handle(stream)), "modpp_group_run")
+        return self.outputs
+
+    def info(self) -> dict:
+        b, tiles, tuned = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        ms = (ctypes.c_double * 3)()
+        _check(lib().modpp_group_plan_info(self._plan, ctypes.byref(b), ctypes.byref(tiles),
+                                           ctypes.byref(tuned), ms), "modpp_group_plan_info")
+        return {"digit_bits": b.value, "tiles": tiles.value,
+                "tuned": {0: "no", 1: "timed", 2: "cached"}[tuned.value],
+                "tuned_ms": {8 + i: ms[i] for i in range(3)}}
+
+    def status(self, stream=None) -> int:
+        return int(lib().modpp_status_read(ctypes.c_void_p(self.workspace.data_ptr()),
+                                           ctypes.c_void_p(_stream_handle(stream))))
+
+    def close(self) -> None:
+        if self._plan:
+            lib().modpp_group_plan_destroy(self._plan)
+            self._plan = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def modpp_mm_grouped(problems, *, tune: bool = True, graph: bool = False, stream=None):
+    """One-shot grouped Mod-PP-MM; returns the list of (P, d, n) outputs."""
+    plan = GroupedPlan(problems, tune=tune, stream=stream)
+    out = plan.run(stream=stream, graph=graph)
+    torch.cuda.current_stream().synchronize()
+    plan.close()
+    return out

@@ -1,314 +1,25 @@
-// Exact Mod-PP-MM on the sm_103a tensor cores.
-//
-// For one output plane (prime q, part A or B) the kernel computes
-//   C[r][c] = sum_t U[r][t] * A[t][c]  mod q
-// from balanced b-bit digits A = sum_l 2^(b l) D_l (|D_l| <= 2^(b-1), b = 8..10):
-//   C = sum_l 2^(b l) * (U * D_l)  mod q.
-// Every U * D_l runs on tcgen05.mma kind::f16 (f16 operands, FP32 accumulate
-// in TMEM).  f16 holds U in [-128, 127] and D_l exactly, and the products
-// are exact; the FP32 sums stay exact because the inner dimension is cut into
-// chunks of 2^(18-b): |sum| <= 2^(18-b) * 128 * 2^(b-1) = 2^24, the largest
-// range in which FP32 represents every integer.  After each chunk the epilogue warps move the
-// chunk's sums out of TMEM into 64-bit integer registers; after the last
-// chunk of a tile they recombine the digits modulo q (Barrett + Shoup) and
-// store canonical residues.  This is the limb-splitting reduction of Sec. 6.1
-// (Lemma le:strategy1, exact chopping) with the digit base and chunk sized for
-// FP32 tensor-core accumulation instead of binary64 BLAS.
-//
-// Tile: 128 output rows x NC output columns x L digits, NC = tile_cols(L)
-// (64, 48, 40 or 32, so that N = NC * L is 224..256).  The L digit rows of the
-// NC columns are adjacent in the digit matrix, so one UMMA of N = NC * L
-// computes all digits of the tile and reuses the U tile L times.
-//
-// Warp roles (320 threads, one CTA per SM, persistent over tiles):
-//   warp 0      TMA producer: U and digit tiles -> shared-memory ring
-//   warp 1      TMEM owner and single-thread MMA issuer
-//   warps 2-9   epilogue: TMEM -> registers, int64 accumulation of each
-//               group of three digits (one IMAD.WIDE per value), modular
-//               recombination at the end of the tile, global stores
-// Two TMEM accumulators (columns 0.. and 256..) alternate between chunks, so
-// the epilogue drains one while the tensor cores fill the other.
-#include <cuda_fp16.h>
-
-#include "modarith.cuh"
-#include "modpp_internal.h"
-#include "ptx_sm103.cuh"
+// Single-problem launch of the tensor-core Mod-PP-MM kernel
+// (gemm_f16_kernel.cuh): every plane of one modpp_mm / pc_mm call shares U,
+// the sizes and the digit count.
+#include "gemm_f16_kernel.cuh"
 
 namespace modpp {
-
-template <int L>
-struct GemmCfg {
-    static constexpr int NC = tile_cols(L);
-    static constexpr int BN = L * NC;
-    static constexpr int A_BYTES = kBM * kBK * 2;
-    static constexpr int B_BYTES = BN * kBK * 2;
-    static constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
-    static constexpr int SMEM_LIMIT = 232448;  // opt-in dynamic shared memory per CTA
-    static constexpr int RESERVED = 1024 + 256;
-    static constexpr int FIT = (SMEM_LIMIT - RESERVED) / STAGE_BYTES;
-    static constexpr int STAGES = FIT > 8 ? 8 : FIT;
-    static constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + RESERVED;
-    static constexpr uint32_t TMEM_COLS = 512;
-    static constexpr uint32_t ACC_STRIDE = 256;
-    static_assert(BN % 16 == 0 && BN <= 256, "UMMA N for M = 128");
-    static_assert(STAGES >= 2, "pipeline depth");
-};
-
-constexpr int kThreads = 320;
-constexpr int kEpiWarps = 8;
-
-__device__ __forceinline__ void decode_tile(int tile, int m_blocks, int n_blocks, int &mb, int &nb,
-                                            int &plane) {
-    mb = tile % m_blocks;
-    const int rest = tile / m_blocks;
-    nb = rest % n_blocks;
-    plane = rest / n_blocks;
-}
-
-template <int L, int DB>
-__global__ void __launch_bounds__(kThreads, 1)
-    gemm_f16_kernel(const __grid_constant__ CUtensorMap tmU, const __grid_constant__ CUtensorMap tmD,
-                    const __grid_constant__ GemmParams p) {
-    using Cfg = GemmCfg<L>;
-    constexpr int STAGES = Cfg::STAGES;
-    extern __shared__ uint8_t smem_raw[];
-    const uint32_t raw = smem_u32(smem_raw);
-    uint8_t *smem = smem_raw + (((raw + 1023u) & ~1023u) - raw);
-    uint64_t *full = reinterpret_cast<uint64_t *>(smem + STAGES * Cfg::STAGE_BYTES);
-    uint64_t *empty = full + STAGES;
-    uint64_t *tfull = empty + STAGES;
-    uint64_t *tempty = tfull + 2;
-    uint64_t *drain = tempty + 2;
-    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(drain + 1);
-    volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
-    volatile int *drain_abort = abort_flag + 1;
-
-    const int warp = threadIdx.x >> 5;
-    const int lane = threadIdx.x & 31;
-
-    if (threadIdx.x == 0) {
-        for (int s = 0; s < STAGES; ++s) {
-            mbar_init(&full[s], 1);
-            mbar_init(&empty[s], 1);
-        }
-        for (int b = 0; b < 2; ++b) {
-            mbar_init(&tfull[b], 1);
-            mbar_init(&tempty[b], kEpiWarps);
-        }
-        mbar_init(drain, 1);
-        *abort_flag = 0;
-        *drain_abort = 0;
-        fence_mbar_init();
-        tma_prefetch_desc(&tmU);
-        tma_prefetch_desc(&tmD);
-    }
-    if (warp == 1) {
-        tmem_alloc(tmem_slot, Cfg::TMEM_COLS);
-        tmem_relinquish();
-    }
-    tc_fence_before();
-    __syncthreads();
-    tc_fence_after();
-    const uint32_t tmem_base = *tmem_slot;
-    constexpr int kChunkKB = chunk_k(DB) / kBK;
-    const int n_chunks = (p.kb_total + kChunkKB - 1) / kChunkKB;
-
-    if (warp == 0) {
-        // ------------------------------------------------ TMA producer
-        if (lane == 0) {
-            uint32_t it = 0;
-            bool ok = true;
-            for (int tile = blockIdx.x; ok && tile < p.num_tiles; tile += gridDim.x) {
-                int mb, nb, plane;
-                decode_tile(tile, p.m_blocks, p.n_blocks, mb, nb, plane);
-                const int ay = mb * kBM;
-                const int by = (plane * p.n_blocks + nb) * L * Cfg::NC;
-                for (int kb = 0; kb < p.kb_total; ++kb, ++it) {
-                    const int s = static_cast<int>(it % STAGES);
-                    const uint32_t ph = (it / STAGES) & 1u;
-                    if (!mbar_wait_bounded(&empty[s], ph ^ 1u, abort_flag, p.timeout_ns)) {
-                        ok = false;
-                        break;
-                    }
-                    uint8_t *sa = smem + s * Cfg::STAGE_BYTES;
-                    mbar_arrive_expect_tx(&full[s], Cfg::STAGE_BYTES);
-                    tma_load_2d(sa, &tmU, &full[s], kb * kBK, ay);
-                    tma_load_2d(sa + Cfg::A_BYTES, &tmD, &full[s], kb * kBK, by);
-                }
-            }
-            // Every issued load must land before the CTA may exit.
-            for (uint32_t j = it > static_cast<uint32_t>(STAGES) ? it - STAGES : 0u; j < it; ++j)
-                mbar_wait_bounded(&full[j % STAGES], (j / STAGES) & 1u, drain_abort, p.timeout_ns);
-        }
-    } else if (warp == 1) {
-        // ------------------------------------------------ MMA issuer
-        if (lane == 0) {
-            constexpr uint32_t idesc = idesc_f16_f32(kBM, Cfg::BN);
-            uint32_t it = 0, g = 0;
-            bool ok = true;
-            for (int tile = blockIdx.x; ok && tile < p.num_tiles; tile += gridDim.x) {
-                for (int ch = 0; ok && ch < n_chunks; ++ch, ++g) {
-                    const uint32_t buf = g & 1u, use = g >> 1;
-                    if (!mbar_wait_bounded(&tempty[buf], (use & 1u) ^ 1u, abort_flag,
-                                           p.timeout_ns)) {
-                        ok = false;
-                        break;
-                    }
-                    tc_fence_after();
-                    const uint32_t dtm = tmem_base + buf * Cfg::ACC_STRIDE;
-                    const int kb0 = ch * kChunkKB;
-                    const int kb1 = min(kb0 + kChunkKB, p.kb_total);
-                    for (int kb = kb0; kb < kb1; ++kb, ++it) {
-                        const int s = static_cast<int>(it % STAGES);
-                        const uint32_t ph = (it / STAGES) & 1u;
-                        if (!mbar_wait_bounded(&full[s], ph, abort_flag, p.timeout_ns)) {
-                            ok = false;
-                            break;
-                        }
-                        tc_fence_after();
-                        const uint32_t a_addr = smem_u32(smem + s * Cfg::STAGE_BYTES);
-                        const uint32_t b_addr = a_addr + Cfg::A_BYTES;
-#pragma unroll
-                        for (int ks = 0; ks < kBK / 16; ++ks) {
-                            umma_f16_ss(dtm, sdesc_kmajor<kRowBytes>(a_addr + ks * 32),
-                                        sdesc_kmajor<kRowBytes>(b_addr + ks * 32), idesc,
-                                        (kb > kb0 || ks > 0) ? 1u : 0u);
-                        }
-                        umma_commit(&empty[s]);
-                    }
-                    if (!ok) break;
-                    umma_commit(&tfull[buf]);
-                }
-            }
-            umma_commit(drain);
-            mbar_wait_bounded(drain, 0, drain_abort, p.timeout_ns);
-        }
-    } else {
-        // ------------------------------------------------ epilogue warps
-        constexpr int NC = Cfg::NC;
-        constexpr int NCH = NC / 2;          // columns per epilogue warp
-        constexpr int G = (L + 2) / 3;       // digit groups: digits 3g, 3g+1, 3g+2
-        constexpr int CW = (L >= 7 || NCH % 8 != 0) ? 4 : 8;  // columns per TMEM load group
-        constexpr int kDigitWeight[3] = {1, 1 << DB, 1 << (2 * DB)};
-        const int ew = warp - 2;
-        const int quarter = warp & 3;  // TMEM lane quarter this warp may access
-        const int half = ew >> 2;      // which half of the tile's columns
-        const uint32_t lane_off = static_cast<uint32_t>(quarter * 32) << 16;
-        // grp[g][c] = sum over chunks of sum_{j<3} 2^(b j) * C_{3g+j}.  A chunk
-        // adds at most 2^24 (1 + 2^b + 2^(2b)) < 2^(25+2b); with at most
-        // 2^(2+b) chunks (k <= 2^20) the total stays below 2^(27+3b) <= 2^57.
-        int64_t grp[G][NCH];
-        uint32_t g = 0;
-        bool ok = true;
-        for (int tile = blockIdx.x; ok && tile < p.num_tiles; tile += gridDim.x) {
-            int mb, nb, plane;
-            decode_tile(tile, p.m_blocks, p.n_blocks, mb, nb, plane);
-#pragma unroll
-            for (int gi = 0; gi < G; ++gi)
-#pragma unroll
-                for (int c = 0; c < NCH; ++c) grp[gi][c] = 0;
-            for (int ch = 0; ch < n_chunks; ++ch, ++g) {
-                const uint32_t buf = g & 1u, use = g >> 1;
-                const bool got = mbar_wait_bounded(&tfull[buf], use & 1u, abort_flag, p.timeout_ns);
-                if (!__all_sync(0xffffffffu, got)) {
-                    ok = false;
-                    break;
-                }
-                tc_fence_after();
-                const uint32_t base = tmem_base + lane_off + buf * Cfg::ACC_STRIDE + half * NCH;
-                // All L digits of a group of CW columns are loaded before one
-                // wait, so a chunk costs NCH / CW TMEM round trips, not L.
-#pragma unroll
-                for (int c0 = 0; c0 < NCH; c0 += CW) {
-                    uint32_t r[L][CW];
-#pragma unroll
-                    for (int l = 0; l < L; ++l) tmem_ld_group<CW>(base + l * NC + c0, r[l]);
-                    tmem_wait_ld();
-#pragma unroll
-                    for (int l = 0; l < L; ++l)
-#pragma unroll
-                        for (int c = 0; c < CW; ++c)
-                            grp[l / 3][c0 + c] = mad_wide_s32(
-                                __float2int_rn(__uint_as_float(r[l][c])), kDigitWeight[l % 3],
-                                grp[l / 3][c0 + c]);
-                }
-                tc_fence_before();
-                __syncwarp();
-                if (lane == 0) mbar_arrive(&tempty[buf]);
-            }
-            if (!ok) break;
-            // value = grp0 + 2^(3b) grp1 + 2^(6b) grp2  (mod q)
-            const int row = mb * kBM + quarter * 32 + lane;
-            const int col0 = nb * NC + half * NCH;
-            if (row < p.d) {
-                const PlaneConst &pc = p.pc[plane];
-                uint64_t *out = pc.C + static_cast<int64_t>(row) * pc.ldc + col0;
-                // Whole 32-byte sectors per lane when the row segment is aligned
-                // and inside the matrix; element stores otherwise.
-                const bool vec = (reinterpret_cast<uintptr_t>(out) & 31u) == 0 && col0 + NCH <= p.n;
-#pragma unroll
-                for (int c0 = 0; c0 < NCH; c0 += 4) {
-                    uint64_t v[4];
-#pragma unroll
-                    for (int j = 0; j < 4; ++j) {
-                        const int c = c0 + j;
-                        uint64_t x = smod_i64(grp[0][c], pc.q, pc.mu);
-                        if constexpr (G > 1)
-                            x = add_mod(x, shoup_mulmod(smod_i64(grp[1][c], pc.q, pc.mu), pc.wg1,
-                                                        pc.wg1s, pc.q),
-                                        pc.q);
-                        if constexpr (G > 2)
-                            x = add_mod(x, shoup_mulmod(smod_i64(grp[2][c], pc.q, pc.mu), pc.wg2,
-                                                        pc.wg2s, pc.q),
-                                        pc.q);
-                        v[j] = x;
-                    }
-                    if (vec) {
-                        st_global_v4_u64(out + c0, v[0], v[1], v[2], v[3]);
-                    } else {
-#pragma unroll
-                        for (int j = 0; j < 4; ++j)
-                            if (col0 + c0 + j < p.n) out[c0 + j] = v[j];
-                    }
-                }
-            }
-        }
-    }
-
-    tc_fence_before();
-    __syncthreads();
-    if (warp == 1) {
-        tc_fence_after();
-        tmem_dealloc(tmem_base, Cfg::TMEM_COLS);
-    }
-    if (threadIdx.x == 0 && (*abort_flag || *drain_abort)) atomicExch(p.status, -7);
-}
-
-template <int L, int DB>
-static cudaError_t launch_gemm_l(const CUtensorMap &tmU, const CUtensorMap &tmD,
-                                 const GemmParams &p, int num_sms, cudaStream_t s) {
-    using Cfg = GemmCfg<L>;
-    cudaError_t e = cudaFuncSetAttribute(gemm_f16_kernel<L, DB>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         Cfg::SMEM_BYTES);
-    if (e != cudaSuccess) return e;
-    const int grid = p.num_tiles < num_sms ? p.num_tiles : num_sms;
-    gemm_f16_kernel<L, DB><<<grid, kThreads, Cfg::SMEM_BYTES, s>>>(tmU, tmD, p);
-    return cudaGetLastError();
-}
 
 template <int DB>
 static cudaError_t launch_gemm_db(const CUtensorMap &tmU, const CUtensorMap &tmD,
                                   const GemmParams &p, int digits, int num_sms, cudaStream_t s) {
     switch (digits) {
-        case 1: return launch_gemm_l<1, DB>(tmU, tmD, p, num_sms, s);
-        case 2: return launch_gemm_l<2, DB>(tmU, tmD, p, num_sms, s);
-        case 3: return launch_gemm_l<3, DB>(tmU, tmD, p, num_sms, s);
-        case 4: return launch_gemm_l<4, DB>(tmU, tmD, p, num_sms, s);
-        case 5: return launch_gemm_l<5, DB>(tmU, tmD, p, num_sms, s);
-        case 6: return launch_gemm_l<6, DB>(tmU, tmD, p, num_sms, s);
-        case 7: return launch_gemm_l<7, DB>(tmU, tmD, p, num_sms, s);
-        case 8: return launch_gemm_l<8, DB>(tmU, tmD, p, num_sms, s);
+#define MODPP_CASE(LL) \
+    case LL: return launch_gemm_kernel<LL, DB, tile_cols(LL), false>(tmU, tmD, p, num_sms, s);
+        MODPP_CASE(1)
+        MODPP_CASE(2)
+        MODPP_CASE(3)
+        MODPP_CASE(4)
+        MODPP_CASE(5)
+        MODPP_CASE(6)
+        MODPP_CASE(7)
+        MODPP_CASE(8)
+#undef MODPP_CASE
         default: return cudaErrorInvalidValue;
     }
 }

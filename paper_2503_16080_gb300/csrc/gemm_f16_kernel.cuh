@@ -1,0 +1,368 @@
+// Exact Mod-PP-MM on the sm_103a tensor cores: the kernel template shared by
+// the single-problem launch (gemm_f16.cu) and the grouped launch (grouped.cu).
+//
+// For one output plane (prime q, part A or B) the kernel computes
+//   C[r][c] = sum_t U[r][t] * A[t][c]  mod q
+// from balanced b-bit digits A = sum_l 2^(b l) D_l (|D_l| <= 2^(b-1), b = 8..10):
+//   C = sum_l 2^(b l) * (U * D_l)  mod q.
+// Every U * D_l runs on tcgen05.mma kind::f16 (f16 operands, FP32 accumulate
+// in TMEM).  f16 holds U in [-128, 127] and D_l exactly, and the products
+// are exact; the FP32 sums stay exact because the inner dimension is cut into
+// chunks of 2^(18-b): |sum| <= 2^(18-b) * 128 * 2^(b-1) = 2^24, the largest
+// range in which FP32 represents every integer.  After each chunk the
+// epilogue warps move the chunk's sums out of TMEM into 64-bit integer
+// registers; after the last chunk of a tile they recombine the digits modulo
+// q (Barrett + Shoup) and store canonical residues.  This is the
+// limb-splitting reduction of Sec. 6.1 (Lemma le:strategy1, exact chopping)
+// with the digit base and chunk sized for FP32 tensor-core accumulation
+// instead of binary64 BLAS.
+//
+// Tile: 128 output rows x NC output columns x Lp digits.  The Lp digit rows of
+// the NC columns are adjacent in the digit matrix, so one UMMA of N = NC * Lp
+// computes all digits of the tile and reuses the U tile Lp times.
+//
+// Warp roles (320 threads, one CTA per SM, persistent over tiles):
+//   warp 0      TMA producer: U and digit tiles -> shared-memory ring
+//   warp 1      TMEM owner and single-thread MMA issuer
+//   warps 2-9   epilogue: TMEM -> registers, int64 accumulation of each
+//               group of three digits (one IMAD.WIDE per value), modular
+//               recombination at the end of the tile, global stores
+// Two TMEM accumulators (columns 0.. and 256..) alternate between chunks, so
+// the epilogue drains one while the tensor cores fill the other.
+//
+// GROUPED = false: one problem; all planes share U, the sizes and the digit
+// count L, and the tensor maps are kernel parameters.  GROUPED = true: the
+// tiles of many problems are concatenated; each tile looks up its plane's
+// descriptor (sizes, digit count Lp <= L, tensor maps in global memory).
+#pragma once
+#include <cuda_fp16.h>
+
+#include "modarith.cuh"
+#include "modpp_internal.h"
+#include "ptx_sm103.cuh"
+
+namespace modpp {
+
+template <int L, int NC>
+struct GemmCfg {
+    static constexpr int BN = L * NC;  // largest UMMA N (all L digits)
+    static constexpr int A_BYTES = kBM * kBK * 2;
+    static constexpr int B_BYTES = BN * kBK * 2;
+    static constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
+    static constexpr int SMEM_LIMIT = 232448;  // opt-in dynamic shared memory per CTA
+    static constexpr int RESERVED = 1024 + 256;
+    static constexpr int FIT = (SMEM_LIMIT - RESERVED) / STAGE_BYTES;
+    static constexpr int STAGES = FIT > 8 ? 8 : FIT;
+    static constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + RESERVED;
+    static constexpr uint32_t TMEM_COLS = 512;
+    static constexpr uint32_t ACC_STRIDE = 256;
+    static_assert(BN % 16 == 0 && BN <= 256, "UMMA N for M = 128");
+    static_assert(STAGES >= 2, "pipeline depth");
+};
+
+constexpr int kThreads = 320;
+constexpr int kEpiWarps = 8;
+
+// Everything the three roles need about one tile.
+struct TileJob {
+    const CUtensorMap *tmU;
+    const CUtensorMap *tmD;
+    const PlaneConst *pc;
+    int mb, nb;       // 128-row block, column block
+    int d, n;         // plane sizes (stores are bounded by them)
+    int kb_total;     // inner dimension in 64-element blocks
+    int by;           // first row of the tile's digits in the digit matrix
+    int Lp;           // digits of this plane
+};
+
+template <int L, int NC, bool GROUPED>
+__device__ __forceinline__ TileJob tile_job(int tile, const CUtensorMap *tmU,
+                                            const CUtensorMap *tmD, const GemmParams &p) {
+    TileJob j;
+    if constexpr (!GROUPED) {
+        j.mb = tile % p.m_blocks;
+        const int rest = tile / p.m_blocks;
+        j.nb = rest % p.n_blocks;
+        const int plane = rest / p.n_blocks;
+        j.tmU = tmU;
+        j.tmD = tmD;
+        j.pc = &p.pc[plane];
+        j.d = p.d;
+        j.n = p.n;
+        j.kb_total = p.kb_total;
+        j.by = (plane * p.n_blocks + j.nb) * L * NC;
+        j.Lp = L;
+    } else {
+        // Planes are stored in tile order: find the last plane starting at or
+        // before `tile` (binary search over tile_begin).
+        int lo = 0, hi = p.num_gplanes - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (p.gplanes[mid].tile_begin <= tile) lo = mid;
+            else hi = mid - 1;
+        }
+        const GroupPlane &g = p.gplanes[lo];
+        const int local = tile - g.tile_begin;
+        j.mb = local % g.m_blocks;
+        j.nb = local / g.m_blocks;
+        j.tmU = g.tmU;
+        j.tmD = g.tmD;
+        j.pc = &g.pc;
+        j.d = g.d;
+        j.n = g.n;
+        j.kb_total = g.kb_total;
+        j.by = (g.dplane * g.n_blocks + j.nb) * g.Lp * NC;
+        j.Lp = g.Lp;
+    }
+    return j;
+}
+
+template <int L, int DB, int NC, bool GROUPED>
+__global__ void __launch_bounds__(kThreads, 1)
+    gemm_f16_kernel(const __grid_constant__ CUtensorMap tmU_param,
+                    const __grid_constant__ CUtensorMap tmD_param,
+                    const __grid_constant__ GemmParams p) {
+    using Cfg = GemmCfg<L, NC>;
+    constexpr int STAGES = Cfg::STAGES;
+    extern __shared__ uint8_t smem_raw[];
+    const uint32_t raw = smem_u32(smem_raw);
+    uint8_t *smem = smem_raw + (((raw + 1023u) & ~1023u) - raw);
+    uint64_t *full = reinterpret_cast<uint64_t *>(smem + STAGES * Cfg::STAGE_BYTES);
+    uint64_t *empty = full + STAGES;
+    uint64_t *tfull = empty + STAGES;
+    uint64_t *tempty = tfull + 2;
+    uint64_t *drain = tempty + 2;
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(drain + 1);
+    volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
+    volatile int *drain_abort = abort_flag + 1;
+
+    const int warp = threadIdx.x >> 5;
+    const int lane = threadIdx.x & 31;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < STAGES; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&tfull[b], 1);
+            mbar_init(&tempty[b], kEpiWarps);
+        }
+        mbar_init(drain, 1);
+        *abort_flag = 0;
+        *drain_abort = 0;
+        fence_mbar_init();
+        if constexpr (!GROUPED) {
+            tma_prefetch_desc(&tmU_param);
+            tma_prefetch_desc(&tmD_param);
+        }
+    }
+    if (warp == 1) {
+        tmem_alloc(tmem_slot, Cfg::TMEM_COLS);
+        tmem_relinquish();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem_base = *tmem_slot;
+    constexpr int kChunkKB = chunk_k(DB) / kBK;
+
+    if (warp == 0) {
+        // ------------------------------------------------ TMA producer
+        if (lane == 0) {
+            uint32_t it = 0;
+            bool ok = true;
+            const CUtensorMap *last_map = nullptr;
+            for (int tile = blockIdx.x; ok && tile < p.num_tiles; tile += gridDim.x) {
+                const TileJob j = tile_job<L, NC, GROUPED>(tile, &tmU_param, &tmD_param, p);
+                if constexpr (GROUPED) {
+                    if (j.tmD != last_map) {
+                        // Tensor maps written to global memory before the launch.
+                        tma_fence_acquire_desc(j.tmU);
+                        tma_fence_acquire_desc(j.tmD);
+                        last_map = j.tmD;
+                    }
+                }
+                const int ay = j.mb * kBM;
+                const uint32_t bytes = Cfg::A_BYTES + static_cast<uint32_t>(j.Lp * NC * kBK * 2);
+                for (int kb = 0; kb < j.kb_total; ++kb, ++it) {
+                    const int s = static_cast<int>(it % STAGES);
+                    const uint32_t ph = (it / STAGES) & 1u;
+                    if (!mbar_wait_bounded(&empty[s], ph ^ 1u, abort_flag, p.timeout_ns)) {
+                        ok = false;
+                        break;
+                    }
+                    uint8_t *sa = smem + s * Cfg::STAGE_BYTES;
+                    mbar_arrive_expect_tx(&full[s], bytes);
+                    tma_load_2d(sa, j.tmU, &full[s], kb * kBK, ay);
+                    tma_load_2d(sa + Cfg::A_BYTES, j.tmD, &full[s], kb * kBK, j.by);
+                }
+            }
+            // Every issued load must land before the CTA may exit.
+            for (uint32_t q = it > static_cast<uint32_t>(STAGES) ? it - STAGES : 0u; q < it; ++q)
+                mbar_wait_bounded(&full[q % STAGES], (q / STAGES) & 1u, drain_abort, p.timeout_ns);
+        }
+    } else if (warp == 1) {
+        // ------------------------------------------------ MMA issuer
+        if (lane == 0) {
+            uint32_t it = 0, g = 0;
+            bool ok = true;
+            for (int tile = blockIdx.x; ok && tile < p.num_tiles; tile += gridDim.x) {
+                const TileJob j = tile_job<L, NC, GROUPED>(tile, &tmU_param, &tmD_param, p);
+                const uint32_t idesc = idesc_f16_f32(kBM, j.Lp * NC);
+                const int n_chunks = (j.kb_total + kChunkKB - 1) / kChunkKB;
+                for (int ch = 0; ok && ch < n_chunks; ++ch, ++g) {
+                    const uint32_t buf = g & 1u, use = g >> 1;
+                    if (!mbar_wait_bounded(&tempty[buf], (use & 1u) ^ 1u, abort_flag,
+                                           p.timeout_ns)) {
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint32_t dtm = tmem_base + buf * Cfg::ACC_STRIDE;
+                    const int kb0 = ch * kChunkKB;
+                    const int kb1 = min(kb0 + kChunkKB, j.kb_total);
+                    for (int kb = kb0; kb < kb1; ++kb, ++it) {
+                        const int s = static_cast<int>(it % STAGES);
+                        const uint32_t ph = (it / STAGES) & 1u;
+                        if (!mbar_wait_bounded(&full[s], ph, abort_flag, p.timeout_ns)) {
+                            ok = false;
+                            break;
+                        }
+                        tc_fence_after();
+                        const uint32_t a_addr = smem_u32(smem + s * Cfg::STAGE_BYTES);
+                        const uint32_t b_addr = a_addr + Cfg::A_BYTES;
+#pragma unroll
+                        for (int ks = 0; ks < kBK / 16; ++ks) {
+                            umma_f16_ss(dtm, sdesc_kmajor<kRowBytes>(a_addr + ks * 32),
+                                        sdesc_kmajor<kRowBytes>(b_addr + ks * 32), idesc,
+                                        (kb > kb0 || ks > 0) ? 1u : 0u);
+                        }
+                        umma_commit(&empty[s]);
+                    }
+                    if (!ok) break;
+                    umma_commit(&tfull[buf]);
+                }
+            }
+            umma_commit(drain);
+            mbar_wait_bounded(drain, 0, drain_abort, p.timeout_ns);
+        }
+    } else {
+        // ------------------------------------------------ epilogue warps
+        constexpr int NCH = NC / 2;          // columns per epilogue warp
+        constexpr int G = (L + 2) / 3;       // digit groups: digits 3g, 3g+1, 3g+2
+        constexpr int CW = (L >= 7 || NCH % 8 != 0) ? 4 : 8;  // columns per TMEM load group
+        constexpr int kDigitWeight[3] = {1, 1 << DB, 1 << (2 * DB)};
+        const int ew = warp - 2;
+        const int quarter = warp & 3;  // TMEM lane quarter this warp may access
+        const int half = ew >> 2;      // which half of the tile's columns
+        const uint32_t lane_off = static_cast<uint32_t>(quarter * 32) << 16;
+        // grp[g][c] = sum over chunks of sum_{j<3} 2^(b j) * C_{3g+j}.  A chunk
+        // adds at most 2^24 (1 + 2^b + 2^(2b)) < 2^(25+2b); with at most
+        // 2^(2+b) chunks (k <= 2^20) the total stays below 2^(27+3b) <= 2^57.
+        int64_t grp[G][NCH];
+        uint32_t g = 0;
+        bool ok = true;
+        for (int tile = blockIdx.x; ok && tile < p.num_tiles; tile += gridDim.x) {
+            const TileJob j = tile_job<L, NC, GROUPED>(tile, &tmU_param, &tmD_param, p);
+            const int Lp = GROUPED ? j.Lp : L;
+            const int n_chunks = (j.kb_total + kChunkKB - 1) / kChunkKB;
+#pragma unroll
+            for (int gi = 0; gi < G; ++gi)
+#pragma unroll
+                for (int c = 0; c < NCH; ++c) grp[gi][c] = 0;
+            for (int ch = 0; ch < n_chunks; ++ch, ++g) {
+                const uint32_t buf = g & 1u, use = g >> 1;
+                const bool got = mbar_wait_bounded(&tfull[buf], use & 1u, abort_flag, p.timeout_ns);
+                if (!__all_sync(0xffffffffu, got)) {
+                    ok = false;
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t base = tmem_base + lane_off + buf * Cfg::ACC_STRIDE + half * NCH;
+                // All digits of a group of CW columns are loaded before one
+                // wait, so a chunk costs NCH / CW TMEM round trips, not L.
+#pragma unroll
+                for (int c0 = 0; c0 < NCH; c0 += CW) {
+                    uint32_t r[L][CW];
+#pragma unroll
+                    for (int l = 0; l < L; ++l)
+                        if (l < Lp) tmem_ld_group<CW>(base + l * NC + c0, r[l]);
+                    tmem_wait_ld();
+#pragma unroll
+                    for (int l = 0; l < L; ++l) {
+                        if (l >= Lp) continue;
+#pragma unroll
+                        for (int c = 0; c < CW; ++c)
+                            grp[l / 3][c0 + c] = mad_wide_s32(
+                                __float2int_rn(__uint_as_float(r[l][c])), kDigitWeight[l % 3],
+                                grp[l / 3][c0 + c]);
+                    }
+                }
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&tempty[buf]);
+            }
+            if (!ok) break;
+            // value = grp0 + 2^(3b) grp1 + 2^(6b) grp2  (mod q)
+            const int row = j.mb * kBM + quarter * 32 + lane;
+            const int col0 = j.nb * NC + half * NCH;
+            if (row < j.d) {
+                const PlaneConst &pc = *j.pc;
+                uint64_t *out = pc.C + static_cast<int64_t>(row) * pc.ldc + col0;
+                // Whole 32-byte sectors per lane when the row segment is aligned
+                // and inside the matrix; element stores otherwise.
+                const bool vec =
+                    (reinterpret_cast<uintptr_t>(out) & 31u) == 0 && col0 + NCH <= j.n;
+#pragma unroll
+                for (int c0 = 0; c0 < NCH; c0 += 4) {
+                    uint64_t v[4];
+#pragma unroll
+                    for (int k4 = 0; k4 < 4; ++k4) {
+                        const int c = c0 + k4;
+                        uint64_t x = smod_i64(grp[0][c], pc.q, pc.mu);
+                        if constexpr (G > 1)
+                            x = add_mod(x, shoup_mulmod(smod_i64(grp[1][c], pc.q, pc.mu), pc.wg1,
+                                                        pc.wg1s, pc.q),
+                                        pc.q);
+                        if constexpr (G > 2)
+                            x = add_mod(x, shoup_mulmod(smod_i64(grp[2][c], pc.q, pc.mu), pc.wg2,
+                                                        pc.wg2s, pc.q),
+                                        pc.q);
+                        v[k4] = x;
+                    }
+                    if (vec) {
+                        st_global_v4_u64(out + c0, v[0], v[1], v[2], v[3]);
+                    } else {
+#pragma unroll
+                        for (int k4 = 0; k4 < 4; ++k4)
+                            if (col0 + c0 + k4 < j.n) out[c0 + k4] = v[k4];
+                    }
+                }
+            }
+        }
+    }
+
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        tc_fence_after();
+        tmem_dealloc(tmem_base, Cfg::TMEM_COLS);
+    }
+    if (threadIdx.x == 0 && (*abort_flag || *drain_abort)) atomicExch(p.status, -7);
+}
+
+template <int L, int DB, int NC, bool GROUPED>
+cudaError_t launch_gemm_kernel(const CUtensorMap &tmU, const CUtensorMap &tmD, const GemmParams &p,
+                               int num_sms, cudaStream_t s) {
+    using Cfg = GemmCfg<L, NC>;
+    cudaError_t e = cudaFuncSetAttribute(gemm_f16_kernel<L, DB, NC, GROUPED>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         Cfg::SMEM_BYTES);
+    if (e != cudaSuccess) return e;
+    const int grid = p.num_tiles < num_sms ? p.num_tiles : num_sms;
+    gemm_f16_kernel<L, DB, NC, GROUPED><<<grid, kThreads, Cfg::SMEM_BYTES, s>>>(tmU, tmD, p);
+    return cudaGetLastError();
+}
+
+}  // namespace modpp

@@ -19,6 +19,11 @@ constexpr int kBM = 128;             // output rows per tile (UMMA M)
 __host__ __device__ constexpr int tile_cols(int L) {
     return L <= 3 ? 64 : (L <= 5 ? 48 : (L == 6 ? 40 : 32));
 }
+// Grouped launches share one column width for all problems, whose digit
+// counts Lp <= L vary: every Lp * cols must be a multiple of 16.
+__host__ __device__ constexpr int grouped_tile_cols(int L) {
+    return L <= 3 ? 64 : (L <= 5 ? 48 : 32);
+}
 constexpr int kMaxTileCols = 64;
 constexpr int kBK = 64;              // f16 elements per K block: one 128-byte row
 constexpr int kRowBytes = kBK * 2;   // swizzle span of the operand tiles (64 or 128)
@@ -43,6 +48,19 @@ struct PlaneConst {
     int64_t ldc;
 };
 
+// One (problem, prime) plane of a grouped launch.  Planes are stored in tile
+// order: plane i owns tiles [tile_begin, tile_begin + m_blocks * n_blocks).
+struct GroupPlane {
+    PlaneConst pc;
+    const CUtensorMap *tmU;  // the problem's U16 map (global memory)
+    const CUtensorMap *tmD;  // the problem's digit-matrix map (global memory)
+    int d, n, kb_total;
+    int m_blocks, n_blocks;
+    int Lp;                  // digits of this problem
+    int dplane;              // index of this plane within the problem's digit matrix
+    int tile_begin;
+};
+
 struct GemmParams {
     int d, n, k;      // output rows, output columns, inner dimension
     int m_blocks;     // ceil(d / kBM)
@@ -52,6 +70,8 @@ struct GemmParams {
     int num_tiles;    // planes * n_blocks * m_blocks
     int *status;      // device status word (workspace)
     uint64_t timeout_ns;
+    const GroupPlane *gplanes;  // grouped launches only
+    int num_gplanes;
     PlaneConst pc[kMaxPlanes];
 };
 

@@ -71,6 +71,13 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity
 __device__ __forceinline__ void tma_prefetch_desc(const CUtensorMap *map) {
     asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(map)) : "memory");
 }
+// Makes a tensor map that was written to global memory before the launch
+// visible to the tensor-map proxy used by TMA.
+__device__ __forceinline__ void tma_fence_acquire_desc(const CUtensorMap *map) {
+    asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(
+                     reinterpret_cast<uint64_t>(map))
+                 : "memory");
+}
 // 2-D tiled load of one box into shared memory; completion is signalled on
 // `bar` through its transaction count.  x is the innermost coordinate.
 __device__ __forceinline__ void tma_load_2d(void *smem_dst, const CUtensorMap *map, uint64_t *bar,

@@ -14,6 +14,7 @@
 
 #include "modarith.cuh"
 #include "modpp_internal.h"
+#include "split_tile.cuh"
 
 namespace modpp {
 
@@ -45,53 +46,18 @@ cudaError_t launch_u_to_f16(const void *U, int ukind, int64_t ldu, int d, int k,
 }
 
 // ---------------------------------------------------------------- digits
-// Block tile: 64 inner indices t x NC columns c (one column block) of one plane.
-// Phase 1 reads A coalesced along c, computes the L digits of each residue
-// and stores them in shared memory as [l][c][t].  Phase 2 writes each
-// (l, c) row of 64 digits (128 bytes) contiguously along t.
-constexpr int kSplitT = 64;
-constexpr int kSplitRow = kSplitT + 4;  // padded row (halves): 136-byte rows
-
+// One block per (64 inner indices, one column block, one plane).
 template <int L, int DB>
 __global__ void __launch_bounds__(256) split_digits_kernel(const __grid_constant__ SplitParams p) {
     constexpr int NC = tile_cols(L);
-    constexpr int64_t kHalf = int64_t(1) << (DB - 1);
-    constexpr int64_t kMask = (int64_t(1) << DB) - 1;
     __shared__ __align__(16) __half tile[L * NC * kSplitRow];
     const int plane = blockIdx.z;
-    const int t0 = blockIdx.x * kSplitT;
     const int nb = blockIdx.y;
-    const int c0 = nb * NC;
     const SplitPlane sp = p.sp[plane];
-
-#pragma unroll 4
-    for (int e = threadIdx.x; e < kSplitT * NC; e += 256) {
-        const int tl = e / NC, cl = e - (e / NC) * NC;
-        const int t = t0 + tl, c = c0 + cl;
-        uint64_t a = 0;
-        if (t < p.k && c < p.n) a = sp.A[static_cast<int64_t>(t) * sp.lda + c];
-        // Lift into the balanced window, then peel digits from the bottom:
-        // d = ((x + 2^(b-1)) mod 2^b) - 2^(b-1), x <- (x - d) / 2^b (exact).
-        int64_t x = a > sp.thresh ? static_cast<int64_t>(a - sp.q) : static_cast<int64_t>(a);
-#pragma unroll
-        for (int l = 0; l < L; ++l) {
-            const int dgt = static_cast<int>(((x + kHalf) & kMask) - kHalf);
-            x = (x - dgt) >> DB;
-            tile[(l * NC + cl) * kSplitRow + tl] = __int2half_rn(dgt);
-        }
-    }
-    __syncthreads();
-
-    // 16 threads per 128-byte row, 4 halves (8 bytes) each.
-    const int sub = threadIdx.x & 15;
-    const int t = t0 + 4 * sub;
-    for (int row = threadIdx.x >> 4; row < L * NC; row += 16) {
-        if (t < p.kp) {
-            const int64_t grow = (static_cast<int64_t>(plane) * p.n_blocks + nb) * L * NC + row;
-            const uint2 v = *reinterpret_cast<const uint2 *>(&tile[row * kSplitRow + 4 * sub]);
-            *reinterpret_cast<uint2 *>(p.D + grow * p.kp + t) = v;
-        }
-    }
+    __half *Dblock =
+        p.D + (static_cast<int64_t>(plane) * p.n_blocks + nb) * L * NC * static_cast<int64_t>(p.kp);
+    split_digit_tile<L, DB, NC>(tile, sp.A, sp.lda, sp.q, sp.thresh, p.k, p.n, p.kp, L,
+                                blockIdx.x * kSplitT, nb * NC, Dblock);
 }
 
 template <int DB>
