@@ -368,6 +368,139 @@ def run_ours(args):
     return 0
 
 
+# ----------------------------------------------------------------- secondary workloads
+# Recorded beside the benchmark line (profiles/); the default line
+# is the default PC-MM n=4096 workload above.
+
+def _timed(step, steps, warmup, stream, pkg):
+    import torch
+    for _ in range(warmup):
+        step()
+    torch.cuda.synchronize()
+    pkg.profile_enable(True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    kern = {name: pkg.profile_read(kid) for name, kid in
+            (("gemm", pkg.KERNEL_GEMM), ("split", pkg.KERNEL_SPLIT), ("u16", pkg.KERNEL_U16))}
+    pkg.profile_enable(False)
+    return e0.elapsed_time(e1) / steps, kern
+
+
+def run_secondary(args):
+    import numpy as np
+    import torch
+
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2503_16080_gb300 as pkg
+    from paper_2503_16080_gb300 import synth
+
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream()
+    if args.digit_bits:
+        pkg.set_digit_bits(args.digit_bits)
+    peaks, peak_src = load_peaks()
+    clocks = ClockSampler(0)
+    line = {"metric": METRIC, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f16", "data": "synthetic"}
+    if args.workload in ("pcmm16384", "pcmv"):
+        d = k = 16384
+        n = 16384 if args.workload == "pcmm16384" else 32
+        P = 4
+        primes = synth.ntt_primes(50, P)
+        U = synth.uniform_int8_torch(SEED, 1, (d, k), dev)
+        A = torch.stack([synth.uniform_mod_torch(SEED, 10 + j, (k, n), q, dev)
+                         for j, q in enumerate(primes)])
+        B = torch.stack([synth.uniform_mod_torch(SEED, 20 + j, (k, n), q, dev)
+                         for j, q in enumerate(primes)])
+        Ao = torch.empty((P, d, n), dtype=torch.uint64, device=dev)
+        Bo = torch.empty_like(Ao)
+        fn = pkg.pc_mm if args.workload == "pcmm16384" else pkg.pc_mv
+        clocks.start()
+        ms, kern = _timed(lambda: fn(U, A, B, primes, out=(Ao, Bo)), args.steps, args.warmup,
+                          stream, pkg)
+        clk = clocks.stop()
+        ops = 2.0 * d * k * n * 2 * P
+        L = pkg.plan_info(k, primes[0])["digits"]
+        g_ms = kern["gemm"][0] / max(kern["gemm"][1], 1)
+        gflops = ops * L
+        line.update({
+            "workload": args.workload, "value": ops / (ms * 1e-3) / 1e12, "ms_per_step": ms,
+            "config": {"workload": (f"PC-MM n=16384: U 16384^2 int8 x 16384 row-RLWE cts of degree "
+                                    f"16384, L=4 primes of 50 bits" if n > 32 else
+                                    "PC-Mv: U 16384^2 int8 x batch of 32, L=4 primes of 50 bits"),
+                       "d": d, "k": k, "n": n, "primes": P, "digits": L,
+                       "digit_bits": pkg.get_digit_bits()},
+            "roofline": {"kernel": "gemm_f16_kernel", "bound": "tensor",
+                         "achieved": gflops / (g_ms * 1e-3) / 1e12,
+                         "peak": peaks["bf16_tflops_sustained"], "unit": "TFLOP/s",
+                         "frac": gflops / (g_ms * 1e-3) / 1e12 / peaks["bf16_tflops_sustained"],
+                         "avg_launch_ms": g_ms},
+            "kernels_ms": {kname: v[0] / max(v[1], 1) for kname, v in kern.items()},
+            "hbm_gbs_U_stream": d * k * 2 / (g_ms * 1e-3) / 1e9,
+            "fp64_matmul_ms": None, "clocks": clk})
+        if args.workload == "pcmm16384":
+            Ud = U.to(torch.float64)
+            Md = torch.empty((k, n), dtype=torch.float64, device=dev).uniform_(-1, 1)
+            torch.matmul(Ud[:1024], Md)
+            torch.cuda.synchronize()
+            f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            f0.record(stream)
+            torch.matmul(Ud, Md)
+            f1.record(stream)
+            torch.cuda.synchronize()
+            line["fp64_matmul_ms"] = f0.elapsed_time(f1)
+            line["slowdown_vs_fp64_matmul"] = ms / line["fp64_matmul_ms"]
+    elif args.workload == "grouped":
+        sys.path.insert(0, os.path.join(ROOT, "tests"))
+        seed = 3
+        w = synth.u64(seed, 1, 4 * 64)
+        probs = []
+        ops = 0.0
+        for i in range(64):
+            dd, kk, nn = (256 << int(w[4 * i + j] % np.uint64(6)) for j in range(3))
+            P = 1 + int(w[4 * i + 3] % np.uint64(6))
+            primes = synth.random_primes(seed, 1000 + i, P, 40, 60)
+            U = synth.uniform_int8_torch(seed, 2000 + i, (dd, kk), dev)
+            A = torch.stack([synth.uniform_mod_torch(seed, 10000 + 16 * i + j, (kk, nn), q, dev)
+                             for j, q in enumerate(primes)])
+            probs.append((U, A, primes))
+            ops += 2.0 * dd * kk * nn * P
+        plan = pkg.GroupedPlan(probs, tune=True)
+        clocks.start()
+        ms_graph, kern = _timed(lambda: plan.run(graph=True), args.steps, args.warmup, stream, pkg)
+        clk = clocks.stop()
+        outs = [torch.empty_like(C) for C in plan.outputs]
+
+        def per_problem():
+            for (U, A, primes), C in zip(probs, outs):
+                pkg.modpp_mm(U, A, primes, out=C)
+
+        pkg.set_digit_bits(plan.info()["digit_bits"])
+        ms_loop, kern_loop = _timed(per_problem, args.steps, args.warmup, stream, pkg)
+        same = all(torch.equal(a, b) for a, b in zip(plan.outputs, outs))
+        line.update({
+            "workload": "grouped", "value": ops / (ms_graph * 1e-3) / 1e12, "ms_per_step": ms_graph,
+            "config": {"workload": "64 uneven Mod-PP-MMs: d,k,n in 256*2^{0..5}, 1-6 primes of "
+                                   "40-60 bits, one grouped plan replayed as a CUDA graph",
+                       "problems": 64, "mod_ops": ops, "plan": plan.info()},
+            "per_problem_launches_ms": ms_loop,
+            "grouped_speedup": ms_loop / ms_graph,
+            "grouped_equals_per_problem": same,
+            "launches_grouped": 3, "launches_per_problem": 3 * 64,
+            "kernels_ms_grouped": {kname: v[0] / max(v[1], 1) for kname, v in kern.items()},
+            "clocks": clk})
+        plan.close()
+    print(json.dumps(line))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -379,6 +512,10 @@ def main():
                     help="timed loop only (no FP64, e2e or CPU legs): for profiler runs")
     ap.add_argument("--digit-bits", type=int, default=0,
                     help="digit width of the f16 path (8, 9, 10; 0 = library default)")
+    ap.add_argument("--workload", default="pcmm4096",
+                    choices=["pcmm4096", "pcmm16384", "pcmv", "grouped"],
+                    help="pcmm4096 (default, the benchmark line); the others are recorded "
+                         "beside it")
     ap.add_argument("--n", type=int, default=4096,
                     help="square size d = k = N (default 4096, the benchmark workload)")
     args = ap.parse_args()
@@ -390,6 +527,8 @@ def main():
         args.warmup = 3
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload != "pcmm4096":
+        return run_secondary(args)
     return run_ours(args)
 
 

@@ -80,10 +80,22 @@ __device__ __forceinline__ TileJob tile_job(int tile, const CUtensorMap *tmU,
                                             const CUtensorMap *tmD, const GemmParams &p) {
     TileJob j;
     if constexpr (!GROUPED) {
-        j.mb = tile % p.m_blocks;
-        const int rest = tile / p.m_blocks;
-        j.nb = rest % p.n_blocks;
-        const int plane = rest / p.n_blocks;
+        // Row block fastest: the concurrently running tiles share the digit
+        // tiles of a few column blocks (and U stays in L2).  Plane fastest, for
+        // thin outputs with a large U: the planes of one row block run together
+        // and read that block of U from HBM once.
+        int plane;
+        if (p.plane_fastest) {
+            plane = tile % p.planes;
+            const int rest = tile / p.planes;
+            j.mb = rest % p.m_blocks;
+            j.nb = rest / p.m_blocks;
+        } else {
+            j.mb = tile % p.m_blocks;
+            const int rest = tile / p.m_blocks;
+            j.nb = rest % p.n_blocks;
+            plane = rest / p.n_blocks;
+        }
         j.tmU = tmU;
         j.tmD = tmD;
         j.pc = &p.pc[plane];

@@ -299,6 +299,12 @@ int run_f16(int64_t d, int64_t k, int64_t n, const void *U, int ukind, int64_t l
     const int64_t tiles = static_cast<int64_t>(gp.m_blocks) * gp.n_blocks * planes;
     if (tiles >= (int64_t(1) << 31)) return MODPP_ERR_UNSUPPORTED;
     gp.num_tiles = static_cast<int>(tiles);
+    // U larger than a slice of L2 and few column blocks: run the planes of a
+    // row block together so each U block is read from HBM once.
+    gp.plane_fastest = (static_cast<int64_t>(d) * lay.kp * 2 > (int64_t(48) << 20) &&
+                        lay.n_blocks <= 2 && planes > 1)
+                           ? 1
+                           : 0;
     gp.status = status;
     gp.timeout_ns = wait_limit_ns();
     for (int i = 0; i < planes; ++i)

@@ -68,6 +68,7 @@ struct GemmParams {
     int planes;
     int kb_total;     // ceil(k / kBK)
     int num_tiles;    // planes * n_blocks * m_blocks
+    int plane_fastest;  // tile order: 0 = row block fastest, 1 = plane fastest
     int *status;      // device status word (workspace)
     uint64_t timeout_ns;
     const GroupPlane *gplanes;  // grouped launches only

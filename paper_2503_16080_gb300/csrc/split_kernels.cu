@@ -19,28 +19,48 @@
 namespace modpp {
 
 // ---------------------------------------------------------------- U -> f16
-__global__ void u_to_f16_kernel(const void *__restrict__ U, int ukind, int64_t ldu, int d, int k,
-                                int kp, __half *__restrict__ U16) {
-    const int64_t total = static_cast<int64_t>(d) * kp;
+// One thread converts 8 consecutive entries of a row (one 16-byte store).
+// Rows are processed by blocks of threads along kp; entries at t >= k are 0.
+__global__ void __launch_bounds__(256) u_to_f16_kernel(const void *__restrict__ U, int ukind,
+                                                        int64_t ldu, int d, int k, int kp,
+                                                        __half *__restrict__ U16) {
+    const int groups = kp / 8;  // kp is a multiple of 8
+    const int64_t total = static_cast<int64_t>(d) * groups;
     for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < total;
          i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
-        const int64_t r = i / kp;
-        const int t = static_cast<int>(i - r * kp);
-        int v = 0;
-        if (t < k) {
-            v = ukind == 0 ? static_cast<int>(static_cast<const int8_t *>(U)[r * ldu + t])
-                           : static_cast<const int32_t *>(U)[r * ldu + t];
+        const int64_t r = i / groups;
+        const int t0 = static_cast<int>(i - r * groups) * 8;
+        __align__(16) __half h[8];
+        if (ukind == 0) {
+            const int8_t *src = static_cast<const int8_t *>(U) + r * ldu + t0;
+            const bool vec = t0 + 8 <= k && (reinterpret_cast<uintptr_t>(src) & 7u) == 0;
+            if (vec) {
+                const int2 w = *reinterpret_cast<const int2 *>(src);
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    const int word = j < 4 ? w.x : w.y;
+                    h[j] = __int2half_rn(static_cast<int8_t>((word >> (8 * (j & 3))) & 0xff));
+                }
+            } else {
+#pragma unroll
+                for (int j = 0; j < 8; ++j)
+                    h[j] = __int2half_rn(t0 + j < k ? static_cast<int>(src[j]) : 0);
+            }
+        } else {
+            const int32_t *src = static_cast<const int32_t *>(U) + r * ldu + t0;
+#pragma unroll
+            for (int j = 0; j < 8; ++j) h[j] = __int2half_rn(t0 + j < k ? src[j] : 0);
         }
-        U16[i] = __int2half_rn(v);
+        *reinterpret_cast<uint4 *>(U16 + r * kp + t0) = *reinterpret_cast<const uint4 *>(h);
     }
 }
 
 cudaError_t launch_u_to_f16(const void *U, int ukind, int64_t ldu, int d, int k, int kp,
                             __half *U16, cudaStream_t s) {
-    const int64_t total = static_cast<int64_t>(d) * kp;
+    const int64_t total = static_cast<int64_t>(d) * (kp / 8);
     if (total == 0) return cudaSuccess;
     int blocks = static_cast<int>((total + 255) / 256);
-    if (blocks > 152 * 32) blocks = 152 * 32;
+    if (blocks > 152 * 16) blocks = 152 * 16;
     u_to_f16_kernel<<<blocks, 256, 0, s>>>(U, ukind, ldu, d, k, kp, U16);
     return cudaGetLastError();
 }
