@@ -167,7 +167,9 @@ int pc_mv(int64_t d, int64_t kct, int64_t nvec, const int8_t *U, const uint64_t 
 
 /*
  * Grouped Mod-PP-MM: many independent products of uneven sizes, each with its
- * own prime list, computed by three launches for the whole group.
+ * own prime list, computed by a few launches for the whole group: one U
+ * conversion, then one digit split and one persistent tensor-core GEMM per
+ * class of problems with the same digit count.
  *
  *   C_i,j = U_i * A_i,j  mod q_i,j     for every problem i and prime j.
  *
@@ -188,7 +190,7 @@ int pc_mv(int64_t d, int64_t kct, int64_t nvec, const int8_t *U, const uint64_t 
  *   widths and GPU name, and appended to the file named by the environment
  *   variable MODPP_TUNE_CACHE when it is set.  Without tuning the process-wide
  *   width (modpp_set_digit_bits) is used.
- * - modpp_group_run(): enqueues the three launches on `stream`.
+ * - modpp_group_run(): enqueues the launches on `stream`.
  * - modpp_group_run_graph(): the first call runs the group once and captures
  *   the launches in a CUDA graph; every call launches that graph on `stream`.
  * - modpp_group_plan_info(): chosen digit width, number of GEMM tiles, tuning

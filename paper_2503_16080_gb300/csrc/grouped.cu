@@ -1,18 +1,21 @@
 // Grouped Mod-PP-MM: many products of uneven d x k x n with their own prime
-// lists run in three launches (U -> f16, digit split, persistent tensor-core
-// GEMM) that walk one table of problems.
+// lists run in a few launches (one U -> f16 pass, then a digit split and a
+// persistent tensor-core GEMM per digit-count class) that walk one table of
+// problems.
 //
 // - A plan (modpp_group_plan_create) lays out the caller's workspace, writes
 //   the device tables (one GroupPlane per (problem, prime), the per-problem
-//   TMA tensor maps, the pre-pass job lists) and orders the planes
-//   longest-K first, so the persistent CTAs take the long tiles before the
-//   short ones.
+//   TMA tensor maps, the pre-pass job lists).  Problems are partitioned by
+//   their digit count L (the widest prime decides); each class runs one
+//   split launch and one persistent GEMM launch with the tile width chosen
+//   for that L, and its planes are ordered longest-K first, so the persistent
+//   CTAs take the long tiles before the short ones.
 // - The digit width is chosen per plan by an autotuner: it times every
 //   candidate width on the plan's own problems and keeps the fastest.  The
 //   choice is cached in process, keyed by the problem shapes, prime sizes and
 //   GPU name, and optionally in a text file named by MODPP_TUNE_CACHE.
-// - modpp_group_run_graph captures the three launches in a CUDA graph once
-//   and replays it.
+// - modpp_group_run_graph captures the launches in a CUDA graph once and
+//   replays it.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -88,7 +91,7 @@ __global__ void __launch_bounds__(256) group_split_kernel(const GroupSplitJob *j
 template <int LMAX, int DB>
 static cudaError_t launch_group_kernels(const GroupSplitJob *sjobs, int n_sjobs, int64_t s_blocks,
                                         const GemmParams &gp, int num_sms, cudaStream_t st) {
-    constexpr int NC = grouped_tile_cols(LMAX);
+    constexpr int NC = tile_cols(LMAX);
     if (s_blocks > 0) {
         group_split_kernel<LMAX, DB, NC><<<static_cast<unsigned>(s_blocks), 256, 0, st>>>(sjobs,
                                                                                      n_sjobs);
@@ -135,8 +138,9 @@ struct ProblemCopy {
 };
 
 struct GroupLayout {
-    int b = 0, lmax = 0, nc = 0;
+    int b = 0, lmax = 0;
     std::vector<int> Lp;                 // per problem
+    std::vector<int> nc;                 // per problem: tile_cols(Lp)
     std::vector<int64_t> kp, n_blocks;   // per problem
     std::vector<size_t> off_u16, off_d;  // per problem
     int num_planes = 0;
@@ -153,7 +157,7 @@ GroupLayout group_layout(const std::vector<ProblemCopy> &probs, int b) {
         g.lmax = std::max(g.lmax, L);
         g.num_planes += pc.p.P;
     }
-    g.nc = grouped_tile_cols(g.lmax);
+    for (int L : g.Lp) g.nc.push_back(tile_cols(L));
     size_t off = 256;  // status word
     g.off_planes = off;
     off = galign(off + sizeof(GroupPlane) * g.num_planes);
@@ -166,13 +170,13 @@ GroupLayout group_layout(const std::vector<ProblemCopy> &probs, int b) {
     for (size_t i = 0; i < probs.size(); ++i) {
         const modpp_problem &p = probs[i].p;
         const int64_t kp = (p.k + 7) / 8 * 8;
-        const int64_t nb = (p.n + g.nc - 1) / g.nc;
+        const int64_t nb = (p.n + g.nc[i] - 1) / g.nc[i];
         g.kp.push_back(kp);
         g.n_blocks.push_back(nb);
         g.off_u16.push_back(off);
         off = galign(off + static_cast<size_t>(p.d) * kp * 2);
         g.off_d.push_back(off);
-        off = galign(off + static_cast<size_t>(p.P) * nb * g.Lp[i] * g.nc * kp * 2);
+        off = galign(off + static_cast<size_t>(p.P) * nb * g.Lp[i] * g.nc[i] * kp * 2);
     }
     g.total = off;
     return g;
@@ -289,8 +293,17 @@ void tune_file_append(const std::string &sig, int b) {
 
 }  // namespace
 
+struct GroupClass {
+    int L = 0;
+    int plane_begin = 0, plane_count = 0;
+    int tiles = 0;
+    int sjob_begin = 0, sjob_count = 0;
+    int64_t s_blocks = 0;
+};
+
 struct modpp_group_plan {
     int device = 0;
+    std::vector<GroupClass> classes;
     std::vector<ProblemCopy> probs;
     uint8_t *ws = nullptr;
     size_t ws_bytes = 0;
@@ -298,7 +311,7 @@ struct modpp_group_plan {
     std::vector<uint8_t> staging;  // host image of the device tables (kept for async copies)
     GemmParams gp{};
     int n_ujobs = 0, n_sjobs = 0;
-    int64_t u_blocks = 0, s_blocks = 0;
+    int64_t u_blocks = 0;
     double tuned_ms[kMaxDigitBits + 1] = {0};
     int tuned = 0;  // 1 if the width came from timing, 2 from the cache
     cudaGraph_t graph = nullptr;
@@ -323,28 +336,42 @@ int plan_build(modpp_group_plan *pl, int b, cudaStream_t st) {
     auto *maps = reinterpret_cast<CUtensorMap *>(h + g.off_maps);
     const auto *dmaps = reinterpret_cast<const CUtensorMap *>(w + g.off_maps);
 
-    // Longest inner dimension first (ties: larger output first).
+    // Classes of equal digit count; within a class the longest inner
+    // dimension first (ties: larger output first).
     std::vector<int> order(pl->probs.size());
     for (size_t i = 0; i < order.size(); ++i) order[i] = static_cast<int>(i);
     std::stable_sort(order.begin(), order.end(), [&](int a, int c) {
+        if (g.Lp[a] != g.Lp[c]) return g.Lp[a] > g.Lp[c];
         const modpp_problem &pa = pl->probs[a].p, &pc = pl->probs[c].p;
         if (pa.k != pc.k) return pa.k > pc.k;
         return pa.d * pa.n > pc.d * pc.n;
     });
 
+    pl->classes.clear();
     int np = 0, nu = 0, ns = 0;
     int64_t tiles = 0, ublocks = 0, sblocks = 0;
     for (int i : order) {
         const modpp_problem &p = pl->probs[i].p;
         if (p.d == 0 || p.n == 0 || p.k == 0) continue;  // zero-filled separately
+        const int Lp = g.Lp[i];
+        const int nc = g.nc[i];
+        if (pl->classes.empty() || pl->classes.back().L != Lp) {
+            GroupClass c;
+            c.L = Lp;
+            c.plane_begin = np;
+            c.sjob_begin = ns;
+            pl->classes.push_back(c);
+            tiles = 0;
+            sblocks = 0;
+        }
+        GroupClass &cls = pl->classes.back();
         __half *U16 = reinterpret_cast<__half *>(w + g.off_u16[i]);
         __half *D = reinterpret_cast<__half *>(w + g.off_d[i]);
         const int64_t kp = g.kp[i], nbk = g.n_blocks[i];
-        const int Lp = g.Lp[i];
-        const int64_t rows = static_cast<int64_t>(p.P) * nbk * Lp * g.nc;
+        const int64_t rows = static_cast<int64_t>(p.P) * nbk * Lp * nc;
         if (rows >= (int64_t(1) << 31)) return MODPP_ERR_UNSUPPORTED;
         if (!encode_map(&maps[2 * i], U16, kp, p.d, kBM) ||
-            !encode_map(&maps[2 * i + 1], D, kp, rows, static_cast<uint32_t>(Lp * g.nc)))
+            !encode_map(&maps[2 * i + 1], D, kp, rows, static_cast<uint32_t>(Lp * nc)))
             return MODPP_ERR_CUDA;
         ujobs[nu] = GroupUJob{static_cast<const int8_t *>(p.U), p.ldu, static_cast<int>(p.d),
                               static_cast<int>(p.k), static_cast<int>(kp), U16, ublocks};
@@ -372,14 +399,18 @@ int plan_build(modpp_group_plan *pl, int b, cudaStream_t st) {
             sjobs[ns] = GroupSplitJob{p.A + static_cast<int64_t>(j) * p.strideA, p.lda, q, thresh,
                                       static_cast<int>(p.k), static_cast<int>(p.n),
                                       static_cast<int>(kp), static_cast<int>(nbk), tblocks, Lp,
-                                      D + static_cast<int64_t>(j) * nbk * Lp * g.nc * kp, sblocks};
+                                      D + static_cast<int64_t>(j) * nbk * Lp * nc * kp, sblocks};
             sblocks += static_cast<int64_t>(tblocks) * nbk;
             ++ns;
         }
+        if (tiles >= (int64_t(1) << 31) || sblocks >= (int64_t(1) << 31))
+            return MODPP_ERR_UNSUPPORTED;
+        cls.plane_count = np - cls.plane_begin;
+        cls.sjob_count = ns - cls.sjob_begin;
+        cls.tiles = static_cast<int>(tiles);
+        cls.s_blocks = sblocks;
     }
-    if (tiles >= (int64_t(1) << 31) || ublocks >= (int64_t(1) << 31) ||
-        sblocks >= (int64_t(1) << 31))
-        return MODPP_ERR_UNSUPPORTED;
+    if (ublocks >= (int64_t(1) << 31)) return MODPP_ERR_UNSUPPORTED;
     if (cudaMemcpyAsync(w, h, table_bytes, cudaMemcpyHostToDevice, st) != cudaSuccess)
         return MODPP_ERR_CUDA;
     // The staging buffer must outlive the copy.
@@ -387,7 +418,8 @@ int plan_build(modpp_group_plan *pl, int b, cudaStream_t st) {
 
     GemmParams &gp = pl->gp;
     gp = GemmParams{};
-    gp.num_tiles = static_cast<int>(tiles);
+    gp.num_tiles = 0;
+    for (const auto &c : pl->classes) gp.num_tiles += c.tiles;
     gp.status = reinterpret_cast<int *>(w);
     gp.timeout_ns = group_wait_limit_ns();
     gp.gplanes = reinterpret_cast<const GroupPlane *>(w + g.off_planes);
@@ -395,7 +427,6 @@ int plan_build(modpp_group_plan *pl, int b, cudaStream_t st) {
     pl->n_ujobs = nu;
     pl->n_sjobs = ns;
     pl->u_blocks = ublocks;
-    pl->s_blocks = sblocks;
     if (pl->gexec) {
         cudaGraphExecDestroy(pl->gexec);
         pl->gexec = nullptr;
@@ -428,14 +459,22 @@ int plan_enqueue(modpp_group_plan *pl, cudaStream_t st) {
     const int sms = sms_of_current_device();
     if (sms <= 0) return MODPP_ERR_CUDA;
     const auto *sjobs = reinterpret_cast<const GroupSplitJob *>(w + g.off_sjobs);
-    cudaError_t e;
-    switch (g.b) {
-        case 8: e = launch_group_db<8>(g.lmax, sjobs, pl->n_sjobs, pl->s_blocks, pl->gp, sms, st); break;
-        case 9: e = launch_group_db<9>(g.lmax, sjobs, pl->n_sjobs, pl->s_blocks, pl->gp, sms, st); break;
-        case 10: e = launch_group_db<10>(g.lmax, sjobs, pl->n_sjobs, pl->s_blocks, pl->gp, sms, st); break;
-        default: return MODPP_ERR_ARG;
+    for (const GroupClass &c : pl->classes) {
+        GemmParams gp = pl->gp;
+        gp.gplanes = pl->gp.gplanes + c.plane_begin;
+        gp.num_gplanes = c.plane_count;
+        gp.num_tiles = c.tiles;
+        const GroupSplitJob *cj = sjobs + c.sjob_begin;
+        cudaError_t e;
+        switch (g.b) {
+            case 8: e = launch_group_db<8>(c.L, cj, c.sjob_count, c.s_blocks, gp, sms, st); break;
+            case 9: e = launch_group_db<9>(c.L, cj, c.sjob_count, c.s_blocks, gp, sms, st); break;
+            case 10: e = launch_group_db<10>(c.L, cj, c.sjob_count, c.s_blocks, gp, sms, st); break;
+            default: return MODPP_ERR_ARG;
+        }
+        if (e != cudaSuccess) return MODPP_ERR_CUDA;
     }
-    return e == cudaSuccess ? MODPP_OK : MODPP_ERR_CUDA;
+    return MODPP_OK;
 }
 
 // Times one candidate width on the plan's own problems (median of 3 after a warm-up).
