@@ -132,6 +132,23 @@ int modpp_mm(int64_t d, int64_t k, int64_t n, const void *U, int ukind, int64_t 
              size_t ws_bytes, void *stream);
 
 /*
+ * Mod-PP-MM of two residue matrices (the products of two ciphertext
+ * matrices in Alg. 8, step 2):
+ *   C_j = U_j * A_j mod q_j,   0 <= j < P,
+ * where U_j (d x k, plane j at U + j*strideU, leading dimension ldu) holds
+ * residues in [0, q_j) like A_j.  U_j is split into balanced 8-bit digits, each
+ * digit plane runs the tensor-core product with A_j's digits, and the results
+ * are accumulated with weights 2^(8 i) mod q_j.  Other conventions as modpp_mm
+ * (MODPP_PATH_F16 only); workspace from modpp_mm_wide_workspace.
+ */
+size_t modpp_mm_wide_workspace(int64_t d, int64_t k, int64_t n, const uint64_t *primes_host,
+                               int P);
+int modpp_mm_wide(int64_t d, int64_t k, int64_t n, const uint64_t *U, int64_t ldu, int64_t strideU,
+                  const uint64_t *A, int64_t lda, int64_t strideA, uint64_t *C, int64_t ldc,
+                  int64_t strideC, const uint64_t *primes_host, int P, void *ws, size_t ws_bytes,
+                  void *stream);
+
+/*
  * Workspace bytes for pc_mm / pc_mv with these sizes (0 for invalid arguments).
  */
 size_t pc_mm_workspace(int64_t d, int64_t kct, int64_t N, const uint64_t *primes_host, int P,

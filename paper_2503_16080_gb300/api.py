@@ -73,6 +73,10 @@ def lib() -> ctypes.CDLL:
         L.pc_mm.argtypes = [I64, I64, I64, P, P, P, P, P, P, I, I, P, SZ, P]
         L.pc_mv.argtypes = [I64, I64, I64, P, P, P, P, P, P, I, I, P, SZ, P]
         L.modpp_status_read.argtypes = [P, P]
+        L.modpp_mm_wide_workspace.argtypes = [I64, I64, I64, P, I]
+        L.modpp_mm_wide_workspace.restype = SZ
+        L.modpp_mm_wide.argtypes = [I64, I64, I64, P, I64, I64, P, I64, I64, P, I64, I64, P, I, P,
+                                    SZ, P]
         L.modpp_group_workspace.argtypes = [P, I]
         L.modpp_group_workspace.restype = SZ
         L.modpp_group_plan_create.argtypes = [P, I, P, SZ, I, P, P]
@@ -237,6 +241,35 @@ def modpp_mm(U: torch.Tensor, A: torch.Tensor, primes: Sequence[int], *, path="f
                         _stream_handle(stream))
     _check(rc, "modpp_mm")
     return out3[0] if squeeze else out3
+
+
+def modpp_mm_wide(U: torch.Tensor, A: torch.Tensor, primes: Sequence[int], *,
+                  out: torch.Tensor | None = None, stream=None,
+                  workspace: torch.Tensor | None = None) -> torch.Tensor:
+    """C[j] = U[j] @ A[j] mod primes[j] with both operands residues (uint64, (P, d, k)
+    and (P, k, n), canonical).  Returns (P, d, n) uint64."""
+    _check_residues(U, "U")
+    _check_residues(A, "A")
+    if U.dim() != 3 or A.dim() != 3 or U.shape[0] != A.shape[0] or U.shape[2] != A.shape[1]:
+        raise ValueError("U must be (P, d, k) and A (P, k, n)")
+    P, d, k = U.shape
+    n = A.shape[2]
+    if (U.numel() and U.stride(2) != 1) or (A.numel() and A.stride(2) != 1):
+        raise ValueError("unit stride along the last dimension required")
+    if out is None:
+        out = torch.empty((P, d, n), dtype=torch.uint64, device=A.device)
+    pr = _primes_arr(primes)
+    need = int(lib().modpp_mm_wide_workspace(d, k, n, pr.ctypes.data, P))
+    if need == 0:
+        raise ModppError(-1, "modpp_mm_wide_workspace")
+    ws_ptr, ws_len = _workspace(need, A.device, workspace)
+    lu, su = (U.stride(1), U.stride(0)) if U.numel() else (k, d * k)
+    la, sa = (A.stride(1), A.stride(0)) if A.numel() else (n, k * n)
+    lc, sc = (out.stride(1), out.stride(0)) if out.numel() else (n, d * n)
+    _check(lib().modpp_mm_wide(d, k, n, U.data_ptr(), lu, su, A.data_ptr(), la, sa,
+                               out.data_ptr(), lc, sc, pr.ctypes.data, P, ws_ptr, ws_len,
+                               _stream_handle(stream)), "modpp_mm_wide")
+    return out
 
 
 def _pc(fn_name: str, U, A, B, primes, path, out, stream, workspace):

@@ -341,6 +341,10 @@ __global__ void __launch_bounds__(kThreads, 1)
                             x = add_mod(x, shoup_mulmod(smod_i64(grp[2][c], pc.q, pc.mu), pc.wg2,
                                                         pc.wg2s, pc.q),
                                         pc.q);
+                        if (pc.accumulate) {  // C <- C + wout * x  (wide products)
+                            x = shoup_mulmod(x, pc.wout, pc.wouts, pc.q);
+                            if (col0 + c < j.n) x = add_mod(x, out[c], pc.q);
+                        }
                         v[k4] = x;
                     }
                     if (vec) {

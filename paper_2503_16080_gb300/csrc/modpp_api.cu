@@ -6,6 +6,7 @@
 #include <cuda.h>
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <atomic>
 #include <cstdlib>
 #include <cstring>
@@ -388,6 +389,120 @@ int run_fp64(int64_t d, int64_t k, int64_t n, const void *U, int ukind, int64_t 
     return MODPP_OK;
 }
 
+// ------------------------------------------------------------ wide products
+// C_j = U_j * A_j mod q_j with both operands residues (the products of two
+// ciphertext matrices, Alg. 8 step 2).  U_j is split into balanced 8-bit
+// digits U_j = sum_i 2^(8 i) U_ji (each an int8 matrix the f16 path takes as
+// its plaintext operand); A_j is split once into f16 digits; then, for each
+// i, the tensor-core GEMM adds 2^(8 i) * (U_ji * A_j) into C_j mod q_j.
+struct WideLayout {
+    int LU = 0;                 // 8-bit digits of the left operand
+    F16Layout f16;              // one plane
+    size_t off_udig = 0, off_f16 = 0, total = 0;
+};
+
+WideLayout wide_layout(int64_t d, int64_t k, int64_t n, const uint64_t *qs, int P) {
+    WideLayout w;
+    for (int j = 0; j < P; ++j) w.LU = std::max(w.LU, f16_digit_count(qs[j], 8));
+    // One plane at a time: the largest per-prime layout (tile widths differ
+    // between digit counts, so the largest L need not have the most rows).
+    for (int j = 0; j < P; ++j) {
+        const F16Layout l = f16_layout(d, k, n, &qs[j], 1);
+        if (l.total > w.f16.total) w.f16 = l;
+    }
+    w.off_udig = kHeaderBytes;
+    w.off_f16 = w.off_udig + align_up(static_cast<size_t>(w.LU) * d * k);
+    w.total = w.off_f16 + w.f16.total;
+    return w;
+}
+
+int run_f16_wide(int64_t d, int64_t k, int64_t n, const uint64_t *U, int64_t ldu, int64_t strideU,
+                 const uint64_t *A, int64_t lda, int64_t strideA, uint64_t *C, int64_t ldc,
+                 int64_t strideC, const uint64_t *primes, int P, void *ws, size_t ws_bytes,
+                 cudaStream_t st) {
+    const WideLayout wl = wide_layout(d, k, n, primes, P);
+    if (ws_bytes < wl.total) return MODPP_ERR_WORKSPACE;
+    uint8_t *w = static_cast<uint8_t *>(ws);
+    if (cudaMemsetAsync(w, 0, sizeof(int), st) != cudaSuccess) return MODPP_ERR_CUDA;
+    if (d == 0 || n == 0) return MODPP_OK;
+    int8_t *Udig = reinterpret_cast<int8_t *>(w + wl.off_udig);
+    uint8_t *wf = w + wl.off_f16;  // the f16 path's workspace (one plane)
+    const F16Layout &lay = wl.f16;
+    __half *U16 = reinterpret_cast<__half *>(wf + lay.off_u16);
+    __half *D = reinterpret_cast<__half *>(wf + lay.off_d);
+    const int sms = device_sms();
+    if (sms <= 0) return MODPP_ERR_CUDA;
+    for (int j = 0; j < P; ++j) {
+        const uint64_t q = primes[j];
+        uint64_t *Cj = C + static_cast<int64_t>(j) * strideC;
+        if (k == 0) {
+            PlaneIn pz{nullptr, n, q, Cj, ldc};
+            const int rc = zero_outputs(d, n, &pz, 1, st);
+            if (rc) return rc;
+            continue;
+        }
+        const int LU = f16_digit_count(q, 8);
+        int rc = cuda_status(launch_u64_to_i8_digits(U + static_cast<int64_t>(j) * strideU, ldu,
+                                                     static_cast<int>(d), static_cast<int>(k), q,
+                                                     f16_lift_threshold(LU, 8), LU, Udig, st));
+        if (rc) return rc;
+        // f16 digits of A_j (the plane's own digit count; the layout holds the largest).
+        const int L = f16_digit_count(q, lay.b);
+        const int nc = tile_cols(L);
+        const int64_t nblk = (n + nc - 1) / nc;
+        const int64_t rows = nblk * L * nc;
+        SplitParams sp{};
+        sp.k = static_cast<int>(k);
+        sp.n = static_cast<int>(n);
+        sp.kp = static_cast<int>(lay.kp);
+        sp.n_blocks = static_cast<int>(nblk);
+        sp.planes = 1;
+        sp.digits = L;
+        sp.digit_bits = lay.b;
+        sp.D = D;
+        sp.sp[0] = SplitPlane{A + static_cast<int64_t>(j) * strideA, lda, q,
+                              f16_lift_threshold(L, lay.b)};
+        rc = cuda_status(launch_split_digits(sp, st));
+        if (rc) return rc;
+        CUtensorMap tmU, tmD;
+        if (!make_map_f16(&tmU, U16, static_cast<uint64_t>(lay.kp), static_cast<uint64_t>(d), kBK,
+                          kBM) ||
+            !make_map_f16(&tmD, D, static_cast<uint64_t>(lay.kp), static_cast<uint64_t>(rows), kBK,
+                          static_cast<uint32_t>(L * nc)))
+            return MODPP_ERR_CUDA;
+        GemmParams gp{};
+        gp.d = static_cast<int>(d);
+        gp.n = static_cast<int>(n);
+        gp.k = static_cast<int>(k);
+        gp.m_blocks = static_cast<int>((d + kBM - 1) / kBM);
+        gp.n_blocks = static_cast<int>(nblk);
+        gp.planes = 1;
+        gp.kb_total = static_cast<int>((k + kBK - 1) / kBK);
+        const int64_t tiles = static_cast<int64_t>(gp.m_blocks) * gp.n_blocks;
+        if (tiles >= (int64_t(1) << 31)) return MODPP_ERR_UNSUPPORTED;
+        gp.num_tiles = static_cast<int>(tiles);
+        gp.status = reinterpret_cast<int *>(w);
+        gp.timeout_ns = wait_limit_ns();
+        uint64_t w8 = 1 % q;
+        for (int i = 0; i < LU; ++i) {
+            rc = cuda_status(launch_u_to_f16(Udig + static_cast<int64_t>(i) * d * k, MODPP_U_I8, k,
+                                             static_cast<int>(d), static_cast<int>(k),
+                                             static_cast<int>(lay.kp), U16, st));
+            if (rc) return rc;
+            gp.pc[0] = make_plane_const(q, lay.b, Cj, ldc);
+            gp.pc[0].wout = w8;
+            gp.pc[0].wouts = host_shoup(w8, q);
+            gp.pc[0].accumulate = i > 0 ? 1 : 0;
+            EventPair *ev = timer_begin(MODPP_KERNEL_GEMM, st);
+            rc = cuda_status(launch_gemm_f16(tmU, tmD, gp, L, lay.b, sms, st));
+            timer_end(ev, st);
+            if (rc) return rc;
+            w8 = host_mulmod(w8, 256 % q, q);
+        }
+    }
+    return MODPP_OK;
+}
+
 size_t layout_bytes(int64_t d, int64_t k, int64_t n, const uint64_t *qs, int planes, int path) {
     if (path == MODPP_PATH_F16) return f16_layout(d, k, n, qs, planes).total;
     return fp64_layout(d, k, n, qs, planes, path == MODPP_PATH_FP64_TIGHT).total;
@@ -547,6 +662,31 @@ int modpp_profile_read(int kernel, double *total_ms, int64_t *launches) {
     if (launches) *launches = static_cast<int64_t>(t.used);
     t.used = 0;
     return MODPP_OK;
+}
+
+size_t modpp_mm_wide_workspace(int64_t d, int64_t k, int64_t n, const uint64_t *primes_host,
+                               int P) {
+    if (check_sizes(d, k, n) || check_primes(primes_host, P, kMaxPlanes)) return 0;
+    return wide_layout(d, k, n, primes_host, P).total;
+}
+
+int modpp_mm_wide(int64_t d, int64_t k, int64_t n, const uint64_t *U, int64_t ldu, int64_t strideU,
+                  const uint64_t *A, int64_t lda, int64_t strideA, uint64_t *C, int64_t ldc,
+                  int64_t strideC, const uint64_t *primes_host, int P, void *ws, size_t ws_bytes,
+                  void *stream) {
+    int rc = check_sizes(d, k, n);
+    if (rc) return rc;
+    rc = check_primes(primes_host, P, kMaxPlanes);
+    if (rc) return rc;
+    const bool work = d > 0 && n > 0;
+    if (work && C == nullptr) return MODPP_ERR_ARG;
+    if (work && k > 0 && (U == nullptr || A == nullptr)) return MODPP_ERR_ARG;
+    if (ldu < k || lda < n || ldc < n) return MODPP_ERR_ARG;
+    if (P > 1 && (strideU < d * ldu || strideA < k * lda || strideC < d * ldc)) return MODPP_ERR_ARG;
+    if (ws == nullptr || (reinterpret_cast<uintptr_t>(ws) & (kAlign - 1)) != 0)
+        return MODPP_ERR_WORKSPACE;
+    return run_f16_wide(d, k, n, U, ldu, strideU, A, lda, strideA, C, ldc, strideC, primes_host, P,
+                        ws, ws_bytes, static_cast<cudaStream_t>(stream));
 }
 
 int modpp_status_read(void *ws, void *stream) {

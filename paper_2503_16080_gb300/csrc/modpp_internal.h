@@ -46,6 +46,9 @@ struct PlaneConst {
     uint64_t wg2s;
     uint64_t *C;    // output plane, d x n, leading dimension ldc
     int64_t ldc;
+    uint64_t wout;  // accumulate mode: C <- C + wout * (U*A) mod q
+    uint64_t wouts; // Shoup quotient of wout
+    int accumulate; // 0: C <- U*A mod q
 };
 
 // One (problem, prime) plane of a grouped launch.  Planes are stored in tile
@@ -142,6 +145,9 @@ inline PlaneConst make_plane_const(uint64_t q, int b, uint64_t *C, int64_t ldc) 
     p.wg2s = host_shoup(p.wg2, q);
     p.C = C;
     p.ldc = ldc;
+    p.wout = 1 % q;
+    p.wouts = host_shoup(p.wout, q);
+    p.accumulate = 0;
     return p;
 }
 
@@ -149,6 +155,10 @@ inline PlaneConst make_plane_const(uint64_t q, int b, uint64_t *C, int64_t ldc) 
 // Each returns a cudaError_t from the launch (cudaSuccess when enqueued).
 cudaError_t launch_u_to_f16(const void *U, int ukind, int64_t ldu, int d, int k, int kp,
                             __half *U16, cudaStream_t s);
+// Residues U (d x k, leading dimension ldu, mod q) -> `digits` balanced 8-bit
+// digit planes, int8, plane i at out + i * d * k (leading dimension k).
+cudaError_t launch_u64_to_i8_digits(const uint64_t *U, int64_t ldu, int d, int k, uint64_t q,
+                                    uint64_t thresh, int digits, int8_t *out, cudaStream_t s);
 cudaError_t launch_split_digits(const SplitParams &p, cudaStream_t s);
 cudaError_t launch_gemm_f16(const CUtensorMap &tmU, const CUtensorMap &tmD, const GemmParams &p,
                             int digits, int digit_bits, int num_sms, cudaStream_t s);

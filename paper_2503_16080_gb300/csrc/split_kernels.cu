@@ -65,6 +65,37 @@ cudaError_t launch_u_to_f16(const void *U, int ukind, int64_t ldu, int d, int k,
     return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------- U residues -> int8 digits
+// Balanced 8-bit digits of residues mod q for the left operand of a product
+// of two residue matrices: u = sum_i 2^(8 i) U_i, U_i in [-128, 127].
+__global__ void u64_to_i8_digits_kernel(const uint64_t *__restrict__ U, int64_t ldu, int d, int k,
+                                        uint64_t q, uint64_t thresh, int digits,
+                                        int8_t *__restrict__ out) {
+    const int64_t total = static_cast<int64_t>(d) * k;
+    for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < total;
+         i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        const int64_t r = i / k;
+        const int64_t t = i - r * k;
+        const uint64_t a = U[r * ldu + t];
+        int64_t x = a > thresh ? static_cast<int64_t>(a - q) : static_cast<int64_t>(a);
+        for (int l = 0; l < digits; ++l) {
+            const int dgt = static_cast<int>(((x + 128) & 255) - 128);
+            x = (x - dgt) >> 8;
+            out[static_cast<int64_t>(l) * total + i] = static_cast<int8_t>(dgt);
+        }
+    }
+}
+
+cudaError_t launch_u64_to_i8_digits(const uint64_t *U, int64_t ldu, int d, int k, uint64_t q,
+                                    uint64_t thresh, int digits, int8_t *out, cudaStream_t s) {
+    const int64_t total = static_cast<int64_t>(d) * k;
+    if (total == 0) return cudaSuccess;
+    int blocks = static_cast<int>((total + 255) / 256);
+    if (blocks > 152 * 16) blocks = 152 * 16;
+    u64_to_i8_digits_kernel<<<blocks, 256, 0, s>>>(U, ldu, d, k, q, thresh, digits, out);
+    return cudaGetLastError();
+}
+
 // ---------------------------------------------------------------- digits
 // One block per (64 inner indices, one column block, one plane).
 template <int L, int DB>

@@ -133,3 +133,30 @@ def test_repeat_calls_are_identical(mp):
     a = mp.modpp_mm(U, A, [P50[0]] * 3).clone()
     b = mp.modpp_mm(U, A, [P50[0]] * 3)
     assert torch.equal(a, b)
+
+
+@pytest.mark.parametrize("shape", [(1, 1, 1), (130, 300, 70), (256, 512, 96), (64, 1000, 33)])
+def test_wide_residue_products(mp, oracle_mod, shape, digit_bits):
+    # Both operands residues (Alg. 8 step 2): bit-exact per prime against the oracle.
+    d, k, n = shape
+    primes = [P50[0], P60[0], P40[0], 97]
+    U = np.stack([synth.uniform_mod(sum(shape), 40 + j, (d, k), q) for j, q in enumerate(primes)])
+    A = np.stack([synth.uniform_mod(sum(shape), 50 + j, (k, n), q) for j, q in enumerate(primes)])
+    C = mp.modpp_mm_wide(to_gpu(U), to_gpu(A), primes)
+    torch.cuda.synchronize()
+    got = C.cpu().numpy()
+    for j, q in enumerate(primes):
+        assert np.array_equal(got[j], oracle_mod.mod_pp_mm_residues(U[j], A[j], q)), f"prime {q}"
+
+
+def test_wide_extremes(mp, oracle_mod):
+    q = P62[0]
+    d, k, n = 128, 600, 40
+    U = np.full((1, d, k), q - 1, dtype=np.uint64)
+    A = np.full((1, k, n), q - 1, dtype=np.uint64)
+    got = mp.modpp_mm_wide(to_gpu(U), to_gpu(A), [q]).cpu().numpy()
+    assert np.all(got == k % q)  # (-1)(-1) summed k times
+    U2 = synth.uniform_mod(9, 1, (1, d, k), q)
+    A2 = np.where(synth.u64(9, 2, k * n).reshape(1, k, n) & np.uint64(1), q - 1, (q - 1) // 2)
+    got2 = mp.modpp_mm_wide(to_gpu(U2), to_gpu(A2.astype(np.uint64)), [q]).cpu().numpy()
+    assert np.array_equal(got2[0], oracle_mod.mod_pp_mm_residues(U2[0], A2[0].astype(np.uint64), q))
