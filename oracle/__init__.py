@@ -17,6 +17,10 @@ computes:
 * ``ckks_encode`` / ``rlwe_encrypt_rows`` / ``rlwe_decrypt_rows`` / ``crt2``:
                      textbook coefficient-encoded CKKS (Sec. 2.2).
 * ``toeplitz``       Toep(m) of Sec. 2 (the matrix of u -> u*m).
+* ``tweak_*``, ``automorphism``, ``ks_keygen``, ``keyswitch``, ``rescale``,
+  ``transpose``, ``cc_mm``: the ring operations of the ciphertext-ciphertext
+  product, Alg. 3 (Tweak), Alg. 4 (Transpose) and Alg. 8 (CC-MM), in the
+  paper's order (``ccmm_oracle.c`` plus the compositions below).
 
 Pins against things other than itself live in ``tests/test_oracle_*.py``.
 """
@@ -31,7 +35,7 @@ from typing import Sequence
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-_SRC = os.path.join(_HERE, "modpp_oracle.c")
+_SRCS = [os.path.join(_HERE, "modpp_oracle.c"), os.path.join(_HERE, "ccmm_oracle.c")]
 _OUT_DIR = os.path.join(_HERE, "_build")
 _LIB_PATH = os.path.join(_OUT_DIR, "liboracle_modpp.so")
 
@@ -41,11 +45,11 @@ _lib = None
 def build(force: bool = False) -> str:
     """Compile the C part of the oracle with gcc (OpenMP). Returns the .so path."""
     if (not force and os.path.exists(_LIB_PATH)
-            and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
+            and all(os.path.getmtime(_LIB_PATH) >= os.path.getmtime(f) for f in _SRCS)):
         return _LIB_PATH
     os.makedirs(_OUT_DIR, exist_ok=True)
     tmp = _LIB_PATH + f".tmp{os.getpid()}"
-    cmd = ["gcc", "-O2", "-std=gnu11", "-fPIC", "-shared", "-fopenmp", _SRC, "-o", tmp, "-lm"]
+    cmd = ["gcc", "-O2", "-std=gnu11", "-fPIC", "-shared", "-fopenmp", *_SRCS, "-o", tmp, "-lm"]
     subprocess.run(cmd, check=True)
     os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
@@ -77,6 +81,18 @@ def _load():
     lib.or_rlwe_decrypt_rows.argtypes = [I, I, ctypes.c_int, P, P, P, P, P]
     lib.or_crt2_centered.argtypes = [I, P, P, U64, U64, P, P]
     lib.or_crt2_centered.restype = None
+    lib.or_monomial_mul.argtypes = [I, I, P, P, U64]
+    lib.or_monomial_mul.restype = None
+    lib.or_automorphism.argtypes = [I, I, P, P, U64]
+    lib.or_automorphism.restype = None
+    lib.or_tweak_def.argtypes = [I, I, ctypes.c_int, P, P, P]
+    lib.or_tweak_def.restype = None
+    lib.or_tweak_alg.argtypes = [I, I, ctypes.c_int, P, P, P]
+    lib.or_tweak_alg.restype = None
+    lib.or_ks_keygen.argtypes = [I, ctypes.c_int, P, P, P, P, P, P]
+    lib.or_keyswitch.argtypes = [I, ctypes.c_int, P, P, P, P]
+    lib.or_rescale.argtypes = [I, ctypes.c_int, P, P, P]
+    lib.or_rescale.restype = None
     _lib = lib
     return lib
 
@@ -295,3 +311,208 @@ def crt2(r0: np.ndarray, r1: np.ndarray, q0: int, q1: int) -> np.ndarray:
     if ovf.any():
         raise OverflowError("CRT value outside int64")
     return out
+
+
+# --------------------------------------------------------------------------
+# Ring operations of the ciphertext-ciphertext product (Alg. 3, 4, 8)
+# Ciphertexts: uint64 arrays [..., 2, L, N] (part 0 = a, part 1 = b).
+# Switching keys: [L, 2, L+1, N] modulo the chain plus the special prime P.
+# --------------------------------------------------------------------------
+
+def _u64(x):
+    return np.ascontiguousarray(x, dtype=np.uint64)
+
+
+def monomial_mul(m, t: int, q: int) -> np.ndarray:
+    """X^t * m in Z_q[X]/(X^N+1)."""
+    m64 = _u64(m)
+    out = np.empty_like(m64)
+    _load().or_monomial_mul(m64.size, int(t), _ptr(m64), _ptr(out), int(q))
+    return out
+
+
+def automorphism(m, ell: int, q: int) -> np.ndarray:
+    """m(X) -> m(X^ell) for odd ell (Aut, Sec. 2.2)."""
+    m64 = _u64(m)
+    out = np.empty_like(m64)
+    _load().or_automorphism(m64.size, int(ell), _ptr(m64), _ptr(out), int(q))
+    return out
+
+
+def ct_map(ct, primes, fn) -> np.ndarray:
+    """Apply fn(poly, q) to every part and plane of a ciphertext."""
+    ct = _u64(ct)
+    out = np.empty_like(ct)
+    for part in range(2):
+        for pl, q in enumerate(primes):
+            out[part, pl] = fn(ct[part, pl], q)
+    return out
+
+
+def tweak_def(cts, primes) -> np.ndarray:
+    """ct'_j = sum_{i<n} X^(2ijN/n) ct_i (the definition in Alg. 3)."""
+    cts = _u64(cts)
+    n, _, L, N = cts.shape
+    out = np.empty_like(cts)
+    pr = _u64(primes[:L])
+    _load().or_tweak_def(n, N, L, _ptr(pr), _ptr(cts), _ptr(out))
+    return out
+
+
+def tweak_alg(cts, primes) -> np.ndarray:
+    """Alg. 3 (Tweak), its recursion as stated."""
+    cts = _u64(cts)
+    n, _, L, N = cts.shape
+    out = np.empty_like(cts)
+    pr = _u64(primes[:L])
+    _load().or_tweak_alg(n, N, L, _ptr(pr), _ptr(cts), _ptr(out))
+    return out
+
+
+def ks_keygen(s_old, s_new, primes_with_P, a, e) -> np.ndarray:
+    """Switching key s_old -> s_new modulo P*Q with the RNS gadget (one digit
+    per prime).  a: [L, L+1, N] uniform; e: [L, N] small.  Returns [L, 2, L+1, N]."""
+    L = len(primes_with_P) - 1
+    N = len(s_old)
+    key = np.empty((L, 2, L + 1, N), dtype=np.uint64)
+    pr = _u64(primes_with_P)
+    so = np.ascontiguousarray(s_old, dtype=np.int64)
+    sn = np.ascontiguousarray(s_new, dtype=np.int64)
+    _check(_load().or_ks_keygen(N, L, _ptr(pr), _ptr(so), _ptr(sn), _ptr(_u64(a)),
+                                _ptr(np.ascontiguousarray(e, dtype=np.int64)), _ptr(key)),
+           "ks_keygen")
+    return key
+
+
+def keyswitch(ct, key, primes_with_P) -> np.ndarray:
+    """KeySwitch: digits a mod q_i, sum digit_i * key_i mod PQ, divide by P (rounded)."""
+    ct = _u64(ct)
+    _, L, N = ct.shape
+    out = np.empty_like(ct)
+    _check(_load().or_keyswitch(N, L, _ptr(_u64(primes_with_P)), _ptr(_u64(key)), _ptr(ct),
+                                _ptr(out)), "keyswitch")
+    return out
+
+
+def rescale(ct, primes) -> np.ndarray:
+    """Rescale by the last prime of the chain: round(x / q_{L-1}), L-1 planes."""
+    ct = _u64(ct)
+    _, L, N = ct.shape
+    out = np.empty((2, L - 1, N), dtype=np.uint64)
+    _load().or_rescale(N, L, _ptr(_u64(primes[:L])), _ptr(ct), _ptr(out))
+    return out
+
+
+def negacyclic_int(a, b) -> np.ndarray:
+    """Product in Z[X]/(X^N+1) of two small integer polynomials (exact, int64)."""
+    a = np.asarray(a, dtype=np.int64)
+    b = np.asarray(b, dtype=np.int64)
+    N = len(a)
+    full = np.convolve(a, b)
+    out = full[:N].copy()
+    out[: N - 1] -= full[N:]
+    return out
+
+
+def aut_key_secret(s, ell: int) -> np.ndarray:
+    """s(X^ell) over the integers (the secret an automorphism key switches from)."""
+    N = len(s)
+    out = np.zeros(N, dtype=np.int64)
+    for i, v in enumerate(np.asarray(s, dtype=np.int64)):
+        p = (i * ell) % (2 * N)
+        if p < N:
+            out[p] += v
+        else:
+            out[p - N] -= v
+    return out
+
+
+def aut_ct(ct, ell: int, key, primes_with_P) -> np.ndarray:
+    """Aut (Sec. 2.2): ct(X^ell), then KeySwitch s(X^ell) -> s (none for ell = 1)."""
+    L = ct.shape[1]
+    sig = ct_map(ct, primes_with_P[:L], lambda m, q: automorphism(m, ell, q))
+    if ell == 1:
+        return sig
+    return keyswitch(sig, key, primes_with_P)
+
+
+def transpose(cts, aut_keys, primes_with_P) -> np.ndarray:
+    """Alg. 4 (Transpose) on N ciphertexts [N, 2, L, N].  aut_keys[j] switches
+    s(X^(2j+1)) -> s (aut_keys[0] unused)."""
+    cts = _u64(cts)
+    N, _, L, _ = cts.shape
+    primes = list(primes_with_P[:L])
+    # Step 1: aux = Tweak((X^i ct_i)_i)
+    shifted = np.stack([ct_map(cts[i], primes, lambda m, q, i=i: monomial_mul(m, i, q))
+                        for i in range(N)])
+    aux = tweak_alg(shifted, primes)
+    # Steps 2-5: aux'_j = Aut(N^-1 * aux_{((2j+1)^-1 mod 2N - 1)/2}, 2j+1)
+    auxp = np.empty_like(aux)
+    ninv = [pow(N, -1, q) for q in primes]
+    for j in range(N):
+        ell = 2 * j + 1
+        src = (pow(ell, -1, 2 * N) - 1) // 2
+        scaled = aux[src].copy()
+        for pl, q in enumerate(primes):
+            for part in range(2):
+                scaled[part, pl] = (scaled[part, pl].astype(object) * ninv[pl] % q).astype(np.uint64)
+        auxp[j] = aut_ct(scaled, ell, aut_keys[j], primes_with_P)
+    # Step 6: ct'' = Tweak(aux')
+    ctpp = tweak_alg(auxp, primes)
+    # Steps 7-9: ct'_{j mod N} = -X^(N-j) ct''_{N-j}, j = 1..N  (-X^(N-j) = X^(2N-j)).
+    # Reading of the last iteration (j = N, ct'_0): the proof of the transpose
+    # theorem uses -Tr(X^j m)/N = m_{N-j}, which holds for 1 <= j < N (the
+    # constant term of X^j m is -m_{N-j}); for j = 0 the constant term is +m_0,
+    # so the ensured ct'_0 (column 0) is +ct''_0, without the minus sign.
+    out = np.empty_like(ctpp)
+    for j in range(1, N):
+        out[j] = ct_map(ctpp[N - j], primes, lambda m, q, j=j: monomial_mul(m, 2 * N - j, q))
+    out[0] = ctpp[0]
+    return out
+
+
+def ct_add(x, y, primes) -> np.ndarray:
+    out = np.empty_like(x)
+    for pl, q in enumerate(primes):
+        out[..., pl, :] = ((x[..., pl, :].astype(object) + y[..., pl, :].astype(object)) % q
+                           ).astype(np.uint64)
+    return out
+
+
+def cc_mm(ct1, ct2, aut_keys, relin_key, primes_with_P):
+    """Alg. 8 (CC-MM) on column-wise encryptions [N, 2, L, N] (ciphertext j is
+    column j of the matrix).  Returns the column-wise encryption of M1*M2 after
+    Rescale by q_{L-1}, [N, 2, L-1, N], and the intermediate blocks."""
+    ct1 = _u64(ct1)
+    N, _, L, _ = ct1.shape
+    primes = list(primes_with_P[:L])
+    # Step 1: row-wise encryption of M2.
+    rw = transpose(ct2, aut_keys, primes_with_P)
+    C = np.empty((L, 2 * N, 2 * N), dtype=np.uint64)
+    for pl, q in enumerate(primes):
+        # [A; B]: row r of A holds coefficient r of every column ciphertext.
+        Ub = np.concatenate([ct1[:, 0, pl, :].T, ct1[:, 1, pl, :].T])
+        # [A~' B~']: row t is the row-wise ciphertext t (a-part then b-part).
+        Wb = np.concatenate([rw[:, 0, pl, :], rw[:, 1, pl, :]], axis=1)
+        C[pl] = mod_pp_mm_residues(Ub, Wb, q)                      # Step 2
+    C00, C01 = C[:, :N, :N], C[:, :N, N:]
+    C10, C11 = C[:, N:, :N], C[:, N:, N:]
+
+    def rows_as_cts(Cx):  # row i of Cx is the a-part of ciphertext i, b = 0
+        cts = np.zeros((N, 2, L, N), dtype=np.uint64)
+        cts[:, 0] = np.transpose(Cx, (1, 0, 2))
+        return cts
+
+    D01 = transpose(rows_as_cts(C00), aut_keys, primes_with_P)      # Step 3
+    D23 = transpose(rows_as_cts(C10), aut_keys, primes_with_P)      # Step 4
+    out = np.empty((N, 2, L - 1, N), dtype=np.uint64)
+    for j in range(N):                                               # Step 5
+        r = np.zeros((2, L, N), dtype=np.uint64)
+        r[0] = D01[j, 0]
+        rl = keyswitch(r, relin_key, primes_with_P)                  # Relin(D0, 0)
+        extra = np.zeros((2, L, N), dtype=np.uint64)
+        extra[0] = ct_add(D01[j, 1], D23[j, 0], primes)              # D1 + D2
+        extra[0] = ct_add(extra[0], C01[:, :, j], primes)            # + C01 (column j)
+        extra[1] = ct_add(D23[j, 1], C11[:, :, j], primes)           # D3 + C11
+        out[j] = rescale(ct_add(rl, extra, primes), primes)
+    return out, {"row_wise": rw, "C": C, "D01": D01, "D23": D23}

@@ -1,0 +1,214 @@
+"""Pins for the oracle's ring operations of the ciphertext-ciphertext product:
+Tweak (Alg. 3), Aut, KeySwitch, Rescale, Transpose (Alg. 4), CC-MM (Alg. 8).
+
+Each is checked against something other than itself: the definition of Tweak,
+the coefficient formula of Aut (Sec. 2.2), ring-homomorphism laws, exact
+results on noise-free (trivial) ciphertexts, and decryption identities within
+the error bounds the algebra implies."""
+import numpy as np
+import pytest
+
+from paper_2503_16080_gb300 import synth
+
+PR = synth.ntt_primes(50, 3)
+SP = synth.ntt_primes(60, 1)[0]
+PRP = PR + [SP]
+
+
+def rand_cts(seed, n, N, primes):
+    L = len(primes)
+    cts = np.empty((n, 2, L, N), dtype=np.uint64)
+    for pl, q in enumerate(primes):
+        cts[:, :, pl, :] = synth.uniform_mod(seed, 10 + pl, (n, 2, N), q)
+    return cts
+
+
+@pytest.mark.parametrize("n,N", [(1, 8), (2, 8), (4, 8), (8, 8), (16, 32), (8, 64)])
+def test_tweak_algorithm_equals_definition(oracle_mod, n, N):
+    cts = rand_cts(n + N, n, N, PR[:2])
+    assert np.array_equal(oracle_mod.tweak_alg(cts, PR[:2]), oracle_mod.tweak_def(cts, PR[:2]))
+
+
+def test_tweak_n2_by_hand(oracle_mod):
+    # n = 2: ct'_0 = ct_0 + ct_1 and ct'_1 = ct_0 + X^N ct_1 = ct_0 - ct_1.
+    q = PR[0]
+    cts = rand_cts(5, 2, 8, [q])
+    out = oracle_mod.tweak_alg(cts, [q])
+    a, b = cts[0].astype(object), cts[1].astype(object)
+    assert np.array_equal(out[0], ((a + b) % q).astype(np.uint64))
+    assert np.array_equal(out[1], ((a - b) % q).astype(np.uint64))
+
+
+def test_monomial_rules(oracle_mod):
+    q, N = PR[0], 16
+    m = synth.uniform_mod(1, 1, (N,), q)
+    assert np.array_equal(oracle_mod.monomial_mul(m, 2 * N, q), m)
+    assert np.array_equal(oracle_mod.monomial_mul(m, N, q), np.where(m == 0, 0, np.uint64(q) - m))
+    assert np.array_equal(oracle_mod.monomial_mul(oracle_mod.monomial_mul(m, 3, q), 5, q),
+                          oracle_mod.monomial_mul(m, 8, q))
+
+
+@pytest.mark.parametrize("ell", [1, 3, 5, 31, 33, 63])
+def test_automorphism_coefficient_formula(oracle_mod, ell):
+    # Sec. 2.2 (Aut): the result holds (-1)^floor(l' i / N) x_{l' i mod N}, l' = l^-1 mod 2N.
+    q, N = PR[0], 32
+    x = synth.uniform_mod(ell, 2, (N,), q)
+    out = oracle_mod.automorphism(x, ell, q)
+    li = pow(ell, -1, 2 * N)
+    for i in range(N):
+        src = (li * i) % N
+        sign = -1 if ((li * i) // N) % 2 else 1
+        assert int(out[i]) == (sign * int(x[src])) % q
+
+
+def test_automorphism_is_a_ring_homomorphism(oracle_mod):
+    q, N = PR[1], 64
+    a = synth.uniform_mod(3, 1, (N,), q)
+    b = synth.uniform_mod(3, 2, (N,), q)
+    for ell in (3, 5, 127):
+        lhs = oracle_mod.automorphism(oracle_mod.negacyclic_mul(a, b, q), ell, q)
+        rhs = oracle_mod.negacyclic_mul(oracle_mod.automorphism(a, ell, q),
+                                        oracle_mod.automorphism(b, ell, q), q)
+        assert np.array_equal(lhs, rhs)
+    comp = oracle_mod.automorphism(oracle_mod.automorphism(a, 3, q), 5, q)
+    assert np.array_equal(comp, oracle_mod.automorphism(a, 15, q))
+
+
+def _keys(seed, s_old, s_new, N):
+    L = len(PR)
+    a = np.stack([np.stack([synth.uniform_mod(seed, 100 + 10 * i + k, (N,), q)
+                            for k, q in enumerate(PRP)]) for i in range(L)])
+    e = synth.rounded_gaussian(seed, 200, (L, N))
+    return oracle_mod_ref.ks_keygen(s_old, s_new, PRP, a, e)
+
+
+@pytest.fixture(scope="module")
+def oracle_mod_ref(oracle_mod):
+    return oracle_mod
+
+
+def _decrypt_centered(oracle_mod, ct, s, primes):
+    """a*s + b per plane, then two-prime CRT to a centred integer."""
+    L = ct.shape[1]
+    dec = oracle_mod.rlwe_decrypt_rows(ct[0][:, None, :], ct[1][:, None, :], s, primes[:L])[:, 0]
+    return oracle_mod.crt2(dec[0], dec[1], primes[0], primes[1])
+
+
+def test_keyswitch(oracle_mod):
+    N = 32
+    s_old = synth.ternary(1, 1, N)
+    s_new = synth.ternary(1, 2, N)
+    L = len(PR)
+    a = np.stack([np.stack([synth.uniform_mod(4, 100 + 10 * i + k, (N,), q)
+                            for k, q in enumerate(PRP)]) for i in range(L)])
+    e = synth.rounded_gaussian(4, 200, (L, N))
+    key = oracle_mod.ks_keygen(s_old, s_new, PRP, a, e)
+    # Noise-free trivial ciphertext: (0, b) is unchanged.
+    triv = np.zeros((2, L, N), dtype=np.uint64)
+    triv[1] = rand_cts(2, 1, N, PR)[0, 1]
+    assert np.array_equal(oracle_mod.keyswitch(triv, key, PRP), triv)
+    # An encryption of a small message under s_old decrypts to (almost) the
+    # same message under s_new.
+    m = (synth.uniform_unit(3, 1, (1, N)) * 2.0 ** 40).astype(np.int64)
+    ea = np.stack([synth.uniform_mod(3, 2 + pl, (1, N), q) for pl, q in enumerate(PR)])
+    eb = oracle_mod.rlwe_encrypt_rows(ea, s_old, m, np.zeros_like(m), PR)
+    ct = np.stack([ea[:, 0, :], eb[:, 0, :]])
+    before = _decrypt_centered(oracle_mod, ct, s_old, PR)
+    assert np.array_equal(before, m[0])
+    after = _decrypt_centered(oracle_mod, oracle_mod.keyswitch(ct, key, PRP), s_new, PR)
+    # |error| <= (L * N * max|d_i| * max|e| / P) + 1/2 + N/2 (rounding times s)
+    assert np.max(np.abs(after.astype(object) - before.astype(object))) <= N
+
+
+def test_rescale(oracle_mod):
+    N, L = 16, len(PR)
+    ql = PR[-1]
+    t = synth.uniform_int8(1, 1, (N,)).astype(np.int64) * 1000
+    r = synth.uniform_int8(1, 2, (N,)).astype(np.int64)
+    m = t.astype(object) * ql + r.astype(object)  # |r| < ql/2: round(m / ql) = t exactly
+    ct = np.zeros((2, L, N), dtype=np.uint64)
+    for pl, q in enumerate(PR):
+        ct[1, pl] = (m.astype(object) % q).astype(np.uint64)
+    out = oracle_mod.rescale(ct, PR)
+    assert out.shape == (2, L - 1, N)
+    assert np.all(out[0] == 0)
+    for pl, q in enumerate(PR[:-1]):
+        assert np.array_equal(out[1, pl], (t.astype(object) % q).astype(np.uint64))
+
+
+def _aut_keys(oracle_mod, s, N, seed):
+    L = len(PR)
+    keys = [None]
+    for j in range(1, N):
+        ell = 2 * j + 1
+        a = np.stack([np.stack([synth.uniform_mod(seed + j, 100 + 10 * i + k, (N,), q)
+                                for k, q in enumerate(PRP)]) for i in range(L)])
+        e = synth.rounded_gaussian(seed + j, 200, (L, N))
+        keys.append(oracle_mod.ks_keygen(oracle_mod.aut_key_secret(s, ell), s, PRP, a, e))
+    return keys
+
+
+def _encrypt_columns(oracle_mod, M, s, delta, seed):
+    """Column-wise RLWE: ciphertext j encrypts column j of M."""
+    N = M.shape[0]
+    L = len(PR)
+    m = oracle_mod.ckks_encode(np.ascontiguousarray(M.T), delta)  # row j = column j of M
+    a = np.stack([synth.uniform_mod(seed, 30 + pl, (N, N), q) for pl, q in enumerate(PR)])
+    e = synth.rounded_gaussian(seed, 40, (N, N))
+    b = oracle_mod.rlwe_encrypt_rows(a, s, m, e, PR)
+    cts = np.empty((N, 2, L, N), dtype=np.uint64)
+    cts[:, 0] = np.transpose(a, (1, 0, 2))
+    cts[:, 1] = np.transpose(b, (1, 0, 2))
+    return cts, m, e
+
+
+def test_transpose_trivial_is_exact(oracle_mod):
+    # Noise-free ciphertexts (0, m_i): Alg. 4 returns exactly (0, columns of M).
+    N, L = 16, len(PR)
+    s = synth.ternary(7, 1, N)
+    keys = _aut_keys(oracle_mod, s, N, 1000)
+    M = synth.uniform_mod(7, 2, (N, N), 1 << 20).astype(np.int64) - (1 << 19)
+    cts = np.zeros((N, 2, L, N), dtype=np.uint64)
+    for pl, q in enumerate(PR):
+        cts[:, 1, pl, :] = (M.astype(object) % q).astype(np.uint64)  # ciphertext i holds row i
+    out = oracle_mod.transpose(cts, keys, PRP)
+    assert np.all(out[:, 0] == 0)
+    for pl, q in enumerate(PR):
+        assert np.array_equal(out[:, 1, pl, :], (M.T.astype(object) % q).astype(np.uint64))
+
+
+def test_transpose_encrypted(oracle_mod):
+    N = 16
+    s = synth.ternary(8, 1, N)
+    keys = _aut_keys(oracle_mod, s, N, 2000)
+    M = synth.uniform_unit(8, 2, (N, N))
+    delta = 2.0 ** 40
+    cts, m, e = _encrypt_columns(oracle_mod, M, s, delta, 8)  # ciphertext j = column j
+    out = oracle_mod.transpose(cts, keys, PRP)  # ciphertext i = row i
+    for i in range(N):
+        got = _decrypt_centered(oracle_mod, out[i], s, PR)
+        want = m[:, i] + e[:, i]  # row i of (Delta*M + E): entries (j, i) of the column data
+        assert np.max(np.abs(got.astype(object) - want.astype(object))) <= 64
+
+
+def test_cc_mm_decrypts_to_product(oracle_mod):
+    N = 16
+    s = synth.ternary(9, 1, N)
+    keys = _aut_keys(oracle_mod, s, N, 3000)
+    L = len(PR)
+    a = np.stack([np.stack([synth.uniform_mod(9, 500 + 10 * i + k, (N,), q)
+                            for k, q in enumerate(PRP)]) for i in range(L)])
+    e = synth.rounded_gaussian(9, 600, (L, N))
+    s2 = oracle_mod.negacyclic_int(s, s)
+    relin = oracle_mod.ks_keygen(s2, s, PRP, a, e)
+    delta = 2.0 ** 40
+    M1 = synth.uniform_unit(9, 2, (N, N))
+    M2 = synth.uniform_unit(9, 3, (N, N))
+    c1, _, _ = _encrypt_columns(oracle_mod, M1, s, delta, 11)
+    c2, _, _ = _encrypt_columns(oracle_mod, M2, s, delta, 12)
+    out, _ = oracle_mod.cc_mm(c1, c2, keys, relin, PRP)
+    scale = delta * delta / PR[-1]
+    ref = M1 @ M2
+    for j in range(N):
+        dec = _decrypt_centered(oracle_mod, out[j], s, PR[:-1]).astype(np.float64) / scale
+        assert np.max(np.abs(dec - ref[:, j])) <= 2.0 ** -20
