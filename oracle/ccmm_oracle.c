@@ -87,7 +87,7 @@ void or_tweak_def(int64_t n, int64_t N, int L, const uint64_t *primes, const uin
         uint64_t *o = out + j * W;
         memset(o, 0, sizeof(uint64_t) * (size_t)W);
         for (int64_t i = 0; i < n; ++i) {
-            const int64_t t = 2 * i * j * (N / n);
+            const int64_t t = 2 * i * j * N / n; /* exact for n | 2N */
             for (int part = 0; part < 2; ++part)
                 for (int pl = 0; pl < L; ++pl) {
                     const uint64_t q = primes[pl];

@@ -1,0 +1,75 @@
+"""Seeded CKKS inputs for the ring / CC-MM tests: random ciphertext batches,
+switching keys (generated by the oracle's key generator from seeded secrets,
+masks and errors), and column-wise encryptions of real matrices.
+
+Oracle layout throughout: a ciphertext batch is [n, 2, L, N] (ciphertext,
+part a/b, prime, coefficient); a switching key is [L, 2, L+1, N]."""
+import numpy as np
+
+from paper_2503_16080_gb300 import synth
+
+PR = synth.ntt_primes(50, 3)
+SP = synth.ntt_primes(60, 1)[0]
+PRP = PR + [SP]
+
+
+def rand_cts(seed, n, N, primes):
+    L = len(primes)
+    cts = np.empty((n, 2, L, N), dtype=np.uint64)
+    for pl, q in enumerate(primes):
+        cts[:, :, pl, :] = synth.uniform_mod(seed, 10 + pl, (n, 2, N), q)
+    return cts
+
+
+def switching_key(oracle_mod, s_old, s_new, N, seed, primes_with_P=PRP):
+    L = len(primes_with_P) - 1
+    a = np.stack([np.stack([synth.uniform_mod(seed, 100 + 10 * i + k, (N,), q)
+                            for k, q in enumerate(primes_with_P)]) for i in range(L)])
+    e = synth.rounded_gaussian(seed, 200, (L, N))
+    return oracle_mod.ks_keygen(s_old, s_new, primes_with_P, a, e)
+
+
+def aut_keys(oracle_mod, s, N, seed, primes_with_P=PRP):
+    """Key j switches s(X^(2j+1)) -> s, 1 <= j < N; entry 0 is None."""
+    keys = [None]
+    for j in range(1, N):
+        keys.append(switching_key(oracle_mod, oracle_mod.aut_key_secret(s, 2 * j + 1), s, N,
+                                  seed + j, primes_with_P))
+    return keys
+
+
+def relin_key(oracle_mod, s, N, seed, primes_with_P=PRP):
+    """Switches s^2 -> s."""
+    return switching_key(oracle_mod, oracle_mod.negacyclic_int(s, s), s, N, seed, primes_with_P)
+
+
+def encrypt_columns(oracle_mod, M, s, delta, seed, primes=PR):
+    """Column-wise RLWE: ciphertext j encrypts column j of M."""
+    N = M.shape[0]
+    L = len(primes)
+    m = oracle_mod.ckks_encode(np.ascontiguousarray(M.T), delta)  # row j = column j of M
+    a = np.stack([synth.uniform_mod(seed, 30 + pl, (N, N), q) for pl, q in enumerate(primes)])
+    e = synth.rounded_gaussian(seed, 40, (N, N))
+    b = oracle_mod.rlwe_encrypt_rows(a, s, m, e, primes)
+    cts = np.empty((N, 2, L, N), dtype=np.uint64)
+    cts[:, 0] = np.transpose(a, (1, 0, 2))
+    cts[:, 1] = np.transpose(b, (1, 0, 2))
+    return cts, m, e
+
+
+def to_batch(cts):
+    """[n, 2, L, N] -> the library's part-major batch [2, L, n, N]."""
+    return np.ascontiguousarray(np.transpose(cts, (1, 2, 0, 3)))
+
+
+def from_batch(b):
+    return np.ascontiguousarray(np.transpose(b, (2, 0, 1, 3)))
+
+
+def stack_keys(keys, N, L):
+    """List of keys (None for unused slots) -> [count, L, 2, L+1, N]."""
+    out = np.zeros((len(keys), L, 2, L + 1, N), dtype=np.uint64)
+    for i, k in enumerate(keys):
+        if k is not None:
+            out[i] = k
+    return out

@@ -10,20 +10,11 @@ import pytest
 
 from paper_2503_16080_gb300 import synth
 
-PR = synth.ntt_primes(50, 3)
-SP = synth.ntt_primes(60, 1)[0]
-PRP = PR + [SP]
+import ckks_inputs
+from ckks_inputs import PR, PRP, rand_cts
 
 
-def rand_cts(seed, n, N, primes):
-    L = len(primes)
-    cts = np.empty((n, 2, L, N), dtype=np.uint64)
-    for pl, q in enumerate(primes):
-        cts[:, :, pl, :] = synth.uniform_mod(seed, 10 + pl, (n, 2, N), q)
-    return cts
-
-
-@pytest.mark.parametrize("n,N", [(1, 8), (2, 8), (4, 8), (8, 8), (16, 32), (8, 64)])
+@pytest.mark.parametrize("n,N", [(1, 8), (2, 8), (4, 8), (8, 8), (16, 8), (16, 32), (8, 64)])
 def test_tweak_algorithm_equals_definition(oracle_mod, n, N):
     cts = rand_cts(n + N, n, N, PR[:2])
     assert np.array_equal(oracle_mod.tweak_alg(cts, PR[:2]), oracle_mod.tweak_def(cts, PR[:2]))
@@ -72,19 +63,6 @@ def test_automorphism_is_a_ring_homomorphism(oracle_mod):
         assert np.array_equal(lhs, rhs)
     comp = oracle_mod.automorphism(oracle_mod.automorphism(a, 3, q), 5, q)
     assert np.array_equal(comp, oracle_mod.automorphism(a, 15, q))
-
-
-def _keys(seed, s_old, s_new, N):
-    L = len(PR)
-    a = np.stack([np.stack([synth.uniform_mod(seed, 100 + 10 * i + k, (N,), q)
-                            for k, q in enumerate(PRP)]) for i in range(L)])
-    e = synth.rounded_gaussian(seed, 200, (L, N))
-    return oracle_mod_ref.ks_keygen(s_old, s_new, PRP, a, e)
-
-
-@pytest.fixture(scope="module")
-def oracle_mod_ref(oracle_mod):
-    return oracle_mod
 
 
 def _decrypt_centered(oracle_mod, ct, s, primes):
@@ -137,29 +115,11 @@ def test_rescale(oracle_mod):
 
 
 def _aut_keys(oracle_mod, s, N, seed):
-    L = len(PR)
-    keys = [None]
-    for j in range(1, N):
-        ell = 2 * j + 1
-        a = np.stack([np.stack([synth.uniform_mod(seed + j, 100 + 10 * i + k, (N,), q)
-                                for k, q in enumerate(PRP)]) for i in range(L)])
-        e = synth.rounded_gaussian(seed + j, 200, (L, N))
-        keys.append(oracle_mod.ks_keygen(oracle_mod.aut_key_secret(s, ell), s, PRP, a, e))
-    return keys
+    return ckks_inputs.aut_keys(oracle_mod, s, N, seed)
 
 
 def _encrypt_columns(oracle_mod, M, s, delta, seed):
-    """Column-wise RLWE: ciphertext j encrypts column j of M."""
-    N = M.shape[0]
-    L = len(PR)
-    m = oracle_mod.ckks_encode(np.ascontiguousarray(M.T), delta)  # row j = column j of M
-    a = np.stack([synth.uniform_mod(seed, 30 + pl, (N, N), q) for pl, q in enumerate(PR)])
-    e = synth.rounded_gaussian(seed, 40, (N, N))
-    b = oracle_mod.rlwe_encrypt_rows(a, s, m, e, PR)
-    cts = np.empty((N, 2, L, N), dtype=np.uint64)
-    cts[:, 0] = np.transpose(a, (1, 0, 2))
-    cts[:, 1] = np.transpose(b, (1, 0, 2))
-    return cts, m, e
+    return ckks_inputs.encrypt_columns(oracle_mod, M, s, delta, seed)
 
 
 def test_transpose_trivial_is_exact(oracle_mod):
