@@ -1,0 +1,145 @@
+/*
+ * modpp_ring.h -- C ABI of the ciphertext-ciphertext matrix product (CC-MM,
+ * Alg. 8 of "Fast Homomorphic Linear Algebra with BLAS", arXiv 2503.16080)
+ * and the ring operations it is built from: Tweak (Alg. 3), Transpose
+ * (Alg. 4), KeySwitch with a special prime (Sec. 2.2), and Rescale.
+ *
+ * Ring and ciphertexts
+ * --------------------
+ * R_q = Z_q[X]/(X^N + 1), N a power of two, 2 <= N <= 16384.  The RNS chain
+ * is q_0 .. q_{L-1} (the ciphertext modulus Q is their product) and key
+ * switching uses one special prime P.  Every prime is odd, < 2^62,
+ * congruent to 1 mod 2N (the negacyclic NTT needs a primitive 2N-th root of
+ * unity), and all L+1 primes are distinct.
+ *
+ * A batch of n ciphertexts is stored part-major, [2][L][n][N] uint64:
+ * element ((part * L + j) * n + c) * N + m is coefficient m of part `part`
+ * (0 = a, 1 = b) of ciphertext c, modulo q_j, canonical in [0, q_j).  A
+ * ciphertext (a, b) decrypts to b + a*s (Sec. 2.2).  For a batch of N
+ * ciphertexts the a-part plane j is an N x N matrix whose row c is ciphertext
+ * c: the column-wise and row-wise formats of a ciphertext matrix (Sec. 6) are
+ * the same storage read along the other axis.
+ *
+ * Switching keys: [L][2][L+1][N] uint64 per key (digit i, part, plane over
+ * q_0 .. q_{L-1}, P, coefficient).  Key i encrypts P * g_i * s_old under
+ * s_new modulo P*Q with the RNS gadget g_i = 1 mod q_i, 0 mod q_k (k != i):
+ * key[i][1] = -key[i][0] * s_new + e_i + P * g_i * s_old.  KeySwitch of
+ * (a, b) computes (round(sum_i [a]_{q_i} * key[i][0] / P),
+ * b + round(sum_i [a]_{q_i} * key[i][1] / P)) with the division by P
+ * rounded as x -> (x - [x]_P) / P, [x]_P centred in (-P/2, P/2].
+ * Keys are generated outside the library (the server never sees secrets)
+ * and converted once, in place, by modpp_ring_prepare_keys.
+ *
+ * Conventions are those of modpp.h: device pointers owned by the caller,
+ * asynchronous calls on `stream`, host-side argument checks returning a
+ * negative modpp_status before anything is enqueued, caller workspaces
+ * (256-byte aligned) sized by the *_workspace queries, no device allocation
+ * on the call path, outputs that do not overlap inputs unless stated.
+ */
+#ifndef MODPP_RING_H
+#define MODPP_RING_H
+
+#include "modpp.h"
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct modpp_ring_s *modpp_ring;
+
+/* Device bytes of the ring tables for degree N and L chain primes (0 for
+ * invalid sizes). */
+size_t modpp_ring_bytes(int64_t N, int L);
+
+/*
+ * Writes the NTT tables (powers of a primitive 2N-th root psi of every
+ * prime in bit-reversed order and their Shoup quotients), the RNS constants
+ * (P^-1 mod q_k, q_{L-1}^-1 mod q_k, N^-1 mod q_k) and the index tables of
+ * Alg. 4 into `mem` (device, modpp_ring_bytes(N, L) bytes, owned by the
+ * caller and kept alive until modpp_ring_destroy), and returns a host handle
+ * in *ring.  primes_host: L+1 primes, the chain q_0 .. q_{L-1} then P.
+ * 1 <= L <= 16.  Synchronises `stream` once (the tables are copied from host
+ * memory).  Errors: MODPP_ERR_ARG (sizes, null pointers), MODPP_ERR_PRIME (a
+ * prime that is even, >= 2^62, not 1 mod 2N, or repeated),
+ * MODPP_ERR_WORKSPACE (mem too small or misaligned), MODPP_ERR_CUDA.
+ */
+int modpp_ring_create(int64_t N, int L, const uint64_t *primes_host, void *mem, size_t mem_bytes,
+                      void *stream, modpp_ring *ring);
+int modpp_ring_destroy(modpp_ring ring);
+
+/*
+ * Converts `count` switching keys ([count][L][2][L+1][N], contiguous) in
+ * place from coefficients to the form the key-switching kernels read: the
+ * negacyclic NTT of every polynomial, multiplied by 2^64 mod its prime
+ * (Montgomery form).  Apply once per key; the other calls take prepared keys.
+ */
+int modpp_ring_prepare_keys(modpp_ring ring, uint64_t *keys, int64_t count, void *stream);
+
+/*
+ * KeySwitch (Sec. 2.2) of a batch of n ciphertexts with one prepared key:
+ * out = KeySwitch(ct).  ct and out are [2][L][n][N]; out may equal ct.
+ */
+size_t modpp_keyswitch_workspace(modpp_ring ring, int64_t n);
+int modpp_keyswitch(modpp_ring ring, const uint64_t *ct, uint64_t *out, int64_t n,
+                    const uint64_t *key, void *ws, size_t ws_bytes, void *stream);
+
+/*
+ * Tweak (Alg. 3): out_j = sum_{i<n} X^(2 i j N / n) * ct_i for a batch of n
+ * ciphertexts, n a power of two dividing 2N (an n-point DFT over R_q with
+ * root X^(2N/n)), computed by log2(n) radix-2 stages.  [2][L][n][N]; out must
+ * not overlap ct.
+ */
+size_t modpp_tweak_workspace(modpp_ring ring, int64_t n);
+int modpp_tweak(modpp_ring ring, const uint64_t *ct, uint64_t *out, int64_t n, void *ws,
+                size_t ws_bytes, void *stream);
+
+/*
+ * Transpose (Alg. 4) of `groups` independent ciphertext matrices, each N
+ * ciphertexts (a batch of groups * N ciphertexts, [2][L][groups*N][N]):
+ * turns an encryption of the rows of an N x N matrix into one of its columns
+ * and conversely.  aut_keys: N prepared keys, key j switching
+ * s(X^(2j+1)) -> s (key 0 is never read).  The last step (j = N of the
+ * algorithm, column 0) is taken as ct'_0 = +ct''_0: the trace identity
+ * behind the others, -Tr(X^j m)/N = m_{N-j}, holds for 1 <= j < N only.
+ * out must not overlap ct.
+ */
+size_t modpp_transpose_workspace(modpp_ring ring, int64_t groups);
+int modpp_transpose(modpp_ring ring, const uint64_t *ct, uint64_t *out, int64_t groups,
+                    const uint64_t *aut_keys, void *ws, size_t ws_bytes, void *stream);
+
+/*
+ * Rescale by the last chain prime: x -> round(x / q_{L-1}) on every
+ * coefficient, [2][L][n][N] -> [2][L-1][n][N].  Needs L >= 2.
+ */
+int modpp_rescale(modpp_ring ring, const uint64_t *ct, uint64_t *out, int64_t n, void *stream);
+
+/*
+ * CC-MM (Alg. 8).  ct1, ct2: column-wise encryptions of two N x N matrices
+ * (ciphertext j encrypts column j), [2][L][N][N].  Computes
+ *   1. the row-wise encryption of M2 by Transpose,
+ *   2. C = [A; B] * [A~' B~'] mod q_j for every prime: the four N x N blocks
+ *      C00, C01, C10, C11, as two Mod-PP-MMs of residue matrices
+ *      (modpp_mm_wide),
+ *   3-4. Transpose((C00, 0)) = (D0, D1) and Transpose((C10, 0)) = (D2, D3)
+ *      as one batch of two matrices,
+ *   5. Relin(D0, 0) + (D1 + D2 + C01, D3 + C11) with column j of C01 and C11
+ *      added to ciphertext j, then Rescale by q_{L-1}.
+ * out: [2][L-1][N][N], the column-wise encryption of M1 * M2 at scale
+ * Delta^2 / q_{L-1}.  aut_keys as modpp_transpose; relin_key: one prepared
+ * key switching s^2 -> s.  Needs L >= 2.
+ */
+size_t cc_mm_workspace(modpp_ring ring);
+int cc_mm(modpp_ring ring, const uint64_t *ct1, const uint64_t *ct2, const uint64_t *aut_keys,
+          const uint64_t *relin_key, uint64_t *out, void *ws, size_t ws_bytes, void *stream);
+
+/* Device time (ms) of the stages of the last cc_mm call on this ring, when
+ * timing is switched on with modpp_profile_enable(1); stage 0 = transpose of
+ * ct2, 1 = the two Mod-PP-MMs, 2 = transpose of C00 | C10, 3 = relin and
+ * finish.  Synchronises with the events of the last call. */
+int cc_mm_stage_ms(modpp_ring ring, double ms[4]);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MODPP_RING_H */

@@ -17,10 +17,14 @@ _API_NAMES = (
     "KERNEL_SPLIT", "KERNEL_U16", "set_digit_bits", "get_digit_bits", "GroupedPlan",
     "modpp_mm_grouped", "modpp_mm_wide",
 )
+_RING_NAMES = ("Ring",)
 
 
 def __getattr__(name):
     if name in _API_NAMES:
         from . import api
         return getattr(api, name)
+    if name in _RING_NAMES:
+        from . import ring
+        return getattr(ring, name)
     raise AttributeError(name)

@@ -38,7 +38,8 @@ def _needs_build() -> bool:
         return True
     t = os.path.getmtime(LIB_PATH)
     deps = [os.path.join(SRC_DIR, f) for f in os.listdir(SRC_DIR)]
-    deps.append(os.path.join(ROOT, "include", "modpp.h"))
+    inc = os.path.join(ROOT, "include")
+    deps += [os.path.join(inc, f) for f in os.listdir(inc) if f.endswith(".h")]
     deps.append(os.path.abspath(__file__))
     return any(os.path.getmtime(p) > t for p in deps)
 

@@ -1,0 +1,596 @@
+// Host side of the ring / CC-MM ABI declared in include/modpp_ring.h: ring
+// tables, workspace layouts and the kernel sequence of KeySwitch, Tweak
+// (Alg. 3), Transpose (Alg. 4) and CC-MM (Alg. 8).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <atomic>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "modpp.h"
+#include "modpp_internal.h"
+#include "modpp_ring.h"
+#include "ring_internal.h"
+
+using namespace modpp;
+
+struct modpp_ring_s {
+    int64_t N = 0;
+    int L = 0;
+    int logN = 0;
+    std::vector<uint64_t> primes;  // L + 1: chain, then P
+    char *mem = nullptr;           // caller's device memory holding the tables
+    const NttPlane *tab = nullptr; // [L + 1]
+    const uint64_t *pinv = nullptr, *pinv_s = nullptr;    // P^-1 mod q_k, k < L
+    const uint64_t *qlinv = nullptr, *qlinv_s = nullptr;  // q_{L-1}^-1 mod q_k, k < L-1
+    const uint64_t *ninv = nullptr, *ninv_s = nullptr;    // N^-1 mod q_k, k < L
+    const int *t2_src = nullptr, *t2_ell = nullptr, *t2_kid = nullptr;
+    const int *t3_src = nullptr, *t3_shift = nullptr;
+    const int *kid_zero = nullptr;
+    cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+    bool timed = false;
+};
+
+namespace {
+
+constexpr size_t kAlign = 256;
+constexpr int kMaxChain = 16;
+constexpr int64_t kMaxN = 16384;
+// Bytes of key-switching scratch (digits and products) one chunk may use;
+// MODPP_KS_CHUNK_BYTES overrides it.
+constexpr size_t kKsChunkBytes = size_t(1) << 31;
+size_t ks_chunk_budget() {
+    if (const char *v = std::getenv("MODPP_KS_CHUNK_BYTES")) {
+        const long long x = std::atoll(v);
+        if (x > 0) return static_cast<size_t>(x);
+    }
+    return kKsChunkBytes;
+}
+
+size_t align_up(size_t x) { return (x + kAlign - 1) & ~(kAlign - 1); }
+int cuda_status(cudaError_t e) { return e == cudaSuccess ? MODPP_OK : MODPP_ERR_CUDA; }
+
+using u128 = unsigned __int128;
+uint64_t mulmod(uint64_t a, uint64_t b, uint64_t q) {
+    return static_cast<uint64_t>(static_cast<u128>(a) * b % q);
+}
+uint64_t powmod(uint64_t b, uint64_t e, uint64_t q) {
+    uint64_t r = 1 % q;
+    b %= q;
+    while (e) {
+        if (e & 1) r = mulmod(r, b, q);
+        b = mulmod(b, b, q);
+        e >>= 1;
+    }
+    return r;
+}
+// Inverse modulo a prime by Fermat's little theorem.
+uint64_t invmod(uint64_t a, uint64_t q) { return powmod(a % q, q - 2, q); }
+uint64_t shoup(uint64_t w, uint64_t q) {
+    return static_cast<uint64_t>((static_cast<u128>(w) << 64) / q);
+}
+bool is_prime_u64(uint64_t n) {
+    if (n < 2) return false;
+    for (uint64_t p : {2ull, 3ull, 5ull, 7ull, 11ull, 13ull, 17ull, 19ull, 23ull, 29ull, 31ull, 37ull})
+        if (n % p == 0) return n == p;
+    uint64_t d = n - 1;
+    int s = 0;
+    while ((d & 1) == 0) {
+        d >>= 1;
+        ++s;
+    }
+    // Miller-Rabin with the first 12 prime bases is deterministic below 3.3e24.
+    for (uint64_t a : {2ull, 3ull, 5ull, 7ull, 11ull, 13ull, 17ull, 19ull, 23ull, 29ull, 31ull, 37ull}) {
+        uint64_t x = powmod(a, d, n);
+        if (x == 1 || x == n - 1) continue;
+        bool comp = true;
+        for (int r = 1; r < s; ++r) {
+            x = mulmod(x, x, n);
+            if (x == n - 1) {
+                comp = false;
+                break;
+            }
+        }
+        if (comp) return false;
+    }
+    return true;
+}
+// A primitive 2N-th root of unity mod q (q = 1 mod 2N, N a power of two):
+// x = g^((q-1)/2N) has order dividing 2N, and exactly 2N when x^N = -1.
+uint64_t find_psi(uint64_t q, uint64_t N) {
+    for (uint64_t g = 2; g < q; ++g) {
+        const uint64_t x = powmod(g, (q - 1) / (2 * N), q);
+        if (powmod(x, N, q) == q - 1) return x;
+    }
+    return 0;
+}
+unsigned bitrev(unsigned x, int bits) {
+    unsigned r = 0;
+    for (int i = 0; i < bits; ++i) r |= ((x >> i) & 1u) << (bits - 1 - i);
+    return r;
+}
+int log2_exact(int64_t x) {
+    int l = 0;
+    while ((int64_t(1) << l) < x) ++l;
+    return (int64_t(1) << l) == x ? l : -1;
+}
+
+// Layout of the ring tables inside the caller's memory.
+struct RingLayout {
+    size_t tab, tables, consts, ints, total;
+};
+RingLayout ring_layout(int64_t N, int L) {
+    RingLayout r{};
+    size_t off = 0;
+    r.tab = off;
+    off = align_up(off + sizeof(NttPlane) * (L + 1));
+    r.tables = off;
+    off = align_up(off + sizeof(uint64_t) * 4 * (L + 1) * N);
+    r.consts = off;
+    off = align_up(off + sizeof(uint64_t) * 6 * (L + 1));
+    r.ints = off;
+    off = align_up(off + sizeof(int) * (5 * N + 1));
+    r.total = off;
+    return r;
+}
+
+int64_t batch_words(const modpp_ring_s *r, int64_t n, int L) { return 2 * L * n * r->N; }
+
+// Ciphertexts per key-switching chunk and the chunk's scratch words.
+int64_t ks_chunk(const modpp_ring_s *r, int64_t n) {
+    const int64_t per_ct = static_cast<int64_t>(r->L) * (r->L + 1) * r->N +
+                           2 * static_cast<int64_t>(r->L + 1) * r->N;
+    int64_t nb = static_cast<int64_t>(ks_chunk_budget() / 8) / per_ct;
+    nb = std::max<int64_t>(1, std::min(nb, n));
+    return nb;
+}
+size_t ks_scratch_bytes(const modpp_ring_s *r, int64_t n) {
+    if (n == 0) return 0;
+    const int64_t nb = ks_chunk(r, n);
+    const int64_t Lp = r->L + 1;
+    return align_up(sizeof(uint64_t) * nb * r->L * Lp * r->N) +
+           align_up(sizeof(uint64_t) * nb * 2 * Lp * r->N);
+}
+
+// KeySwitch of ciphertexts [0, count) of a batch with plane stride n, written
+// to a batch with plane stride n_out; key of ciphertext c: keys[kid[c % kper]]
+// (kid < 0: copied unchanged).
+int ks_run(const modpp_ring_s *r, const uint64_t *ct, int64_t n, int64_t count, uint64_t *out,
+           int64_t n_out, const uint64_t *keys, const int *kid, int kper, int b_zero, char *scratch,
+           cudaStream_t st) {
+    if (count == 0) return MODPP_OK;
+    const int L = r->L, Lp = L + 1;
+    const int N = static_cast<int>(r->N);
+    const int64_t nb = ks_chunk(r, count);
+    uint64_t *D = reinterpret_cast<uint64_t *>(scratch);
+    uint64_t *U = reinterpret_cast<uint64_t *>(
+        scratch + align_up(sizeof(uint64_t) * nb * L * Lp * r->N));
+    for (int64_t c0 = 0; c0 < count; c0 += nb) {
+        const int64_t m = std::min(nb, count - c0);
+        cudaError_t e = launch_ks_decompose(ct, n, L, N, c0, m, r->tab, D, st);
+        if (e == cudaSuccess) e = launch_ntt(D, m * L * Lp, N, 1, Lp, r->tab, false, st);
+        if (e == cudaSuccess) e = launch_ks_multacc(D, keys, kid, kper, L, N, c0, m, r->tab, U, st);
+        if (e == cudaSuccess) e = launch_ntt(U, m * 2 * Lp, N, 1, Lp, r->tab, true, st);
+        if (e == cudaSuccess)
+            e = launch_ks_moddown(U, ct, n, L, N, c0, m, kid, kper, b_zero, r->tab, r->pinv,
+                                  r->pinv_s, out, n_out, st);
+        if (e != cudaSuccess) return MODPP_ERR_CUDA;
+    }
+    return MODPP_OK;
+}
+
+// log2(size) radix-2 Tweak stages on a batch of n ciphertexts (n / size
+// independent DFTs of length size), each block of `size` already in
+// bit-reversed order in `a`, ping-ponging with `b`; returns the buffer
+// holding the result.
+uint64_t *tweak_stages(const modpp_ring_s *r, uint64_t *a, uint64_t *b, int64_t n, int64_t size,
+                       int L, cudaStream_t st, int *rc) {
+    *rc = MODPP_OK;
+    for (int64_t half = 1; half < size; half <<= 1) {
+        if (launch_tweak_stage(a, b, n, L, static_cast<int>(r->N), half, r->tab, st) !=
+            cudaSuccess) {
+            *rc = MODPP_ERR_CUDA;
+            return a;
+        }
+        std::swap(a, b);
+    }
+    return a;
+}
+
+size_t transpose_scratch(const modpp_ring_s *r, int64_t groups) {
+    const int64_t n = groups * r->N;
+    return 2 * align_up(sizeof(uint64_t) * batch_words(r, n, r->L)) + ks_scratch_bytes(r, n);
+}
+
+// Alg. 4 on `groups` matrices of N ciphertexts; scratch of transpose_scratch bytes.
+int transpose_run(const modpp_ring_s *r, const uint64_t *ct, uint64_t *out, int64_t groups,
+                  const uint64_t *aut_keys, char *scratch, cudaStream_t st) {
+    const int L = r->L;
+    const int N = static_cast<int>(r->N);
+    const int64_t n = groups * r->N;
+    if (n == 0) return MODPP_OK;
+    const size_t bb = align_up(sizeof(uint64_t) * batch_words(r, n, L));
+    uint64_t *x1 = reinterpret_cast<uint64_t *>(scratch);
+    uint64_t *x2 = reinterpret_cast<uint64_t *>(scratch + bb);
+    char *ks = scratch + 2 * bb;
+    // Step 1: aux = Tweak((X^i ct_i)_i): shift and bit-reverse, then the stages.
+    GatherTables t1{};
+    t1.per = N;
+    t1.brev_bits = r->logN;
+    t1.shift_src = 1;
+    if (launch_ct_gather(ct, x1, n, L, N, t1, r->tab, st) != cudaSuccess) return MODPP_ERR_CUDA;
+    int rc = MODPP_OK;
+    uint64_t *aux = tweak_stages(r, x1, x2, n, r->N, L, st, &rc);
+    if (rc) return rc;
+    uint64_t *other = aux == x1 ? x2 : x1;
+    // Steps 2-5: aux'_j = Aut(N^-1 aux_{((2j+1)^-1 - 1)/2}, 2j+1), written in
+    // bit-reversed order for the second Tweak; then the key switches.
+    GatherTables t2{};
+    t2.per = N;
+    t2.src = r->t2_src;
+    t2.ell = r->t2_ell;
+    t2.scale = r->ninv;
+    t2.scale_s = r->ninv_s;
+    if (launch_ct_gather(aux, other, n, L, N, t2, r->tab, st) != cudaSuccess) return MODPP_ERR_CUDA;
+    rc = ks_run(r, other, n, n, other, n, aut_keys, r->t2_kid, N, 0, ks, st);
+    if (rc) return rc;
+    // Step 6: ct'' = Tweak(aux').
+    uint64_t *ctpp = tweak_stages(r, other, aux, n, r->N, L, st, &rc);
+    if (rc) return rc;
+    // Steps 7-9: ct'_j = X^(2N-j) ct''_{N-j} (1 <= j < N), ct'_0 = ct''_0.
+    GatherTables t3{};
+    t3.per = N;
+    t3.src = r->t3_src;
+    t3.shift = r->t3_shift;
+    if (launch_ct_gather(ctpp, out, n, L, N, t3, r->tab, st) != cudaSuccess) return MODPP_ERR_CUDA;
+    return MODPP_OK;
+}
+
+struct CcLayout {
+    size_t wide, scratch, rw, ut, x, y, z, total;
+};
+CcLayout cc_layout(const modpp_ring_s *r) {
+    CcLayout c{};
+    const int64_t N = r->N;
+    const int L = r->L;
+    const size_t wide = modpp_mm_wide_workspace(2 * N, N, N, r->primes.data(), L);
+    const size_t tr = transpose_scratch(r, 2);
+    size_t off = 0;
+    // The Mod-PP-MM workspace (whose first word is the status word) and the
+    // transpose scratch are used at different times and share one region.
+    c.wide = off;
+    c.scratch = off;
+    off = align_up(off + std::max(wide, tr));
+    c.rw = off;  // row-wise encryption of M2; later the relinearised D0
+    off = align_up(off + sizeof(uint64_t) * batch_words(r, N, L));
+    c.ut = off;  // [L][2N][N]: [A; B] of ct1 per prime
+    off = align_up(off + sizeof(uint64_t) * L * 2 * N * N);
+    c.x = off;   // batch of 2N: a-parts [C00; C10], b-parts 0
+    off = align_up(off + sizeof(uint64_t) * batch_words(r, 2 * N, L));
+    c.y = off;   // [L][2N][N]: [C01; C11]
+    off = align_up(off + sizeof(uint64_t) * L * 2 * N * N);
+    c.z = off;   // Transpose of x
+    off = align_up(off + sizeof(uint64_t) * batch_words(r, 2 * N, L));
+    c.total = off;
+    return c;
+}
+
+bool ws_ok(const void *ws, size_t have, size_t need) {
+    if (need == 0) return true;
+    return ws != nullptr && (reinterpret_cast<uintptr_t>(ws) & (kAlign - 1)) == 0 && have >= need;
+}
+
+
+}  // namespace
+
+extern "C" {
+
+size_t modpp_ring_bytes(int64_t N, int L) {
+    if (N < 2 || N > kMaxN || log2_exact(N) < 0 || L < 1 || L > kMaxChain) return 0;
+    return ring_layout(N, L).total;
+}
+
+int modpp_ring_create(int64_t N, int L, const uint64_t *primes_host, void *mem, size_t mem_bytes,
+                      void *stream, modpp_ring *ring) {
+    if (ring == nullptr || primes_host == nullptr) return MODPP_ERR_ARG;
+    *ring = nullptr;
+    if (N < 2 || N > kMaxN || log2_exact(N) < 0 || L < 1 || L > kMaxChain) return MODPP_ERR_ARG;
+    for (int i = 0; i <= L; ++i) {
+        const uint64_t q = primes_host[i];
+        if (q < 3 || (q & 1) == 0 || q >= (uint64_t(1) << 62) || (q - 1) % (2 * N) != 0 ||
+            !is_prime_u64(q))
+            return MODPP_ERR_PRIME;
+        for (int j = 0; j < i; ++j)
+            if (primes_host[j] == q) return MODPP_ERR_PRIME;
+    }
+    const RingLayout lay = ring_layout(N, L);
+    if (!ws_ok(mem, mem_bytes, lay.total)) return MODPP_ERR_WORKSPACE;
+    auto *r = new (std::nothrow) modpp_ring_s;
+    if (!r) return MODPP_ERR_ARG;
+    r->N = N;
+    r->L = L;
+    r->logN = log2_exact(N);
+    r->primes.assign(primes_host, primes_host + L + 1);
+    r->mem = static_cast<char *>(mem);
+
+    std::vector<char> host(lay.total, 0);
+    const int Lp = L + 1;
+    auto *tabs = reinterpret_cast<uint64_t *>(host.data() + lay.tables);
+    const uint64_t *dtabs = reinterpret_cast<const uint64_t *>(r->mem + lay.tables);
+    auto *tab = reinterpret_cast<NttPlane *>(host.data() + lay.tab);
+    for (int k = 0; k < Lp; ++k) {
+        const uint64_t q = primes_host[k];
+        const uint64_t psi = find_psi(q, N);
+        if (psi == 0) {
+            delete r;
+            return MODPP_ERR_PRIME;
+        }
+        const uint64_t psi_inv = invmod(psi, q);
+        uint64_t *fwd = tabs + (static_cast<int64_t>(4 * k) + 0) * N;
+        uint64_t *fwd_s = tabs + (static_cast<int64_t>(4 * k) + 1) * N;
+        uint64_t *inv = tabs + (static_cast<int64_t>(4 * k) + 2) * N;
+        uint64_t *inv_s = tabs + (static_cast<int64_t>(4 * k) + 3) * N;
+        uint64_t pw = 1, pwi = 1;
+        for (int64_t i = 0; i < N; ++i) {  // psi^i, placed at bitrev(i)
+            const unsigned j = bitrev(static_cast<unsigned>(i), r->logN);
+            fwd[j] = pw;
+            fwd_s[j] = shoup(pw, q);
+            inv[j] = pwi;
+            inv_s[j] = shoup(pwi, q);
+            pw = mulmod(pw, psi, q);
+            pwi = mulmod(pwi, psi_inv, q);
+        }
+        NttPlane &t = tab[k];
+        t.q = q;
+        t.mu = static_cast<uint64_t>((static_cast<u128>(1) << 64) / q);
+        uint64_t y = q;  // -q^-1 mod 2^64 by Newton's iteration
+        for (int it = 0; it < 6; ++it) y *= 2 - q * y;
+        t.qinv_neg = ~y + 1;
+        t.ninv = invmod(static_cast<uint64_t>(N) % q, q);
+        t.ninv_s = shoup(t.ninv, q);
+        t.r64 = static_cast<uint64_t>((static_cast<u128>(1) << 64) % q);
+        t.r64_s = shoup(t.r64, q);
+        t.fwd = dtabs + (static_cast<int64_t>(4 * k) + 0) * N;
+        t.fwd_s = dtabs + (static_cast<int64_t>(4 * k) + 1) * N;
+        t.inv = dtabs + (static_cast<int64_t>(4 * k) + 2) * N;
+        t.inv_s = dtabs + (static_cast<int64_t>(4 * k) + 3) * N;
+    }
+    auto *consts = reinterpret_cast<uint64_t *>(host.data() + lay.consts);
+    const uint64_t P = primes_host[L];
+    const uint64_t ql = primes_host[L - 1];
+    for (int k = 0; k < Lp; ++k) {
+        const uint64_t q = primes_host[k];
+        consts[0 * Lp + k] = invmod(P % q, q);
+        consts[1 * Lp + k] = shoup(consts[0 * Lp + k], q);
+        consts[2 * Lp + k] = k < L - 1 ? invmod(ql % q, q) : 0;
+        consts[3 * Lp + k] = k < L - 1 ? shoup(consts[2 * Lp + k], q) : 0;
+        consts[4 * Lp + k] = tab[k].ninv;
+        consts[5 * Lp + k] = tab[k].ninv_s;
+    }
+    const uint64_t *dconsts = reinterpret_cast<const uint64_t *>(r->mem + lay.consts);
+    r->tab = reinterpret_cast<const NttPlane *>(r->mem + lay.tab);
+    r->pinv = dconsts;
+    r->pinv_s = dconsts + Lp;
+    r->qlinv = dconsts + 2 * Lp;
+    r->qlinv_s = dconsts + 3 * Lp;
+    r->ninv = dconsts + 4 * Lp;
+    r->ninv_s = dconsts + 5 * Lp;
+    // Index tables of Alg. 4 (ints, period N).
+    auto *ints = reinterpret_cast<int *>(host.data() + lay.ints);
+    const int *dints = reinterpret_cast<const int *>(r->mem + lay.ints);
+    int *t2_src = ints, *t2_ell = ints + N, *t2_kid = ints + 2 * N;
+    int *t3_src = ints + 3 * N, *t3_shift = ints + 4 * N;
+    const uint64_t twoN = 2 * static_cast<uint64_t>(N);
+    for (int64_t c = 0; c < N; ++c) {
+        // position c of the bit-reversed second Tweak input holds aux'_j, j = bitrev(c)
+        const int64_t j = bitrev(static_cast<unsigned>(c), r->logN);
+        const uint64_t ell = 2 * static_cast<uint64_t>(j) + 1;
+        uint64_t inv = 1;  // ell^-1 mod 2N by search over odd residues (host, once)
+        for (uint64_t v = 1; v < twoN; v += 2)
+            if ((v * ell) % twoN == 1) {
+                inv = v;
+                break;
+            }
+        t2_src[c] = static_cast<int>((inv - 1) / 2);
+        t2_ell[c] = static_cast<int>(ell);
+        t2_kid[c] = j == 0 ? -1 : static_cast<int>(j);
+        t3_src[c] = c == 0 ? 0 : static_cast<int>(N - c);
+        t3_shift[c] = c == 0 ? 0 : static_cast<int>(2 * N - c);
+    }
+    ints[5 * N] = 0;
+    r->t2_src = dints;
+    r->t2_ell = dints + N;
+    r->t2_kid = dints + 2 * N;
+    r->t3_src = dints + 3 * N;
+    r->t3_shift = dints + 4 * N;
+    r->kid_zero = dints + 5 * N;
+
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    cudaError_t e = cudaMemcpyAsync(mem, host.data(), lay.total, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    for (int i = 0; i < 5 && e == cudaSuccess; ++i) e = cudaEventCreate(&r->ev[i]);
+    if (e != cudaSuccess) {
+        for (auto &ev : r->ev)
+            if (ev) cudaEventDestroy(ev);
+        delete r;
+        return MODPP_ERR_CUDA;
+    }
+    *ring = r;
+    return MODPP_OK;
+}
+
+int modpp_ring_destroy(modpp_ring ring) {
+    if (ring == nullptr) return MODPP_ERR_ARG;
+    for (auto &ev : ring->ev)
+        if (ev) cudaEventDestroy(ev);
+    delete ring;
+    return MODPP_OK;
+}
+
+int modpp_ring_prepare_keys(modpp_ring r, uint64_t *keys, int64_t count, void *stream) {
+    if (r == nullptr || count < 0 || (count > 0 && keys == nullptr)) return MODPP_ERR_ARG;
+    const int Lp = r->L + 1;
+    const int64_t polys = count * r->L * 2 * Lp;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    cudaError_t e = launch_ntt(keys, polys, static_cast<int>(r->N), 1, Lp, r->tab, false, st);
+    if (e == cudaSuccess) e = launch_to_montgomery(keys, polys, static_cast<int>(r->N), 1, Lp, r->tab, st);
+    return cuda_status(e);
+}
+
+size_t modpp_keyswitch_workspace(modpp_ring r, int64_t n) {
+    if (r == nullptr || n < 0) return 0;
+    return std::max<size_t>(kAlign, ks_scratch_bytes(r, n));
+}
+
+int modpp_keyswitch(modpp_ring r, const uint64_t *ct, uint64_t *out, int64_t n, const uint64_t *key,
+                    void *ws, size_t ws_bytes, void *stream) {
+    if (r == nullptr || n < 0) return MODPP_ERR_ARG;
+    if (n > 0 && (ct == nullptr || out == nullptr || key == nullptr)) return MODPP_ERR_ARG;
+    if (!ws_ok(ws, ws_bytes, ks_scratch_bytes(r, n))) return MODPP_ERR_WORKSPACE;
+    return ks_run(r, ct, n, n, out, n, key, r->kid_zero, 1, 0, static_cast<char *>(ws),
+                  static_cast<cudaStream_t>(stream));
+}
+
+size_t modpp_tweak_workspace(modpp_ring r, int64_t n) {
+    if (r == nullptr || n < 0) return 0;
+    return std::max<size_t>(kAlign, align_up(sizeof(uint64_t) * batch_words(r, n, r->L)));
+}
+
+int modpp_tweak(modpp_ring r, const uint64_t *ct, uint64_t *out, int64_t n, void *ws,
+                size_t ws_bytes, void *stream) {
+    if (r == nullptr || n < 0) return MODPP_ERR_ARG;
+    if (n == 0) return MODPP_OK;
+    const int ln = log2_exact(n);
+    if (ln < 0 || n > 2 * r->N || ct == nullptr || out == nullptr) return MODPP_ERR_ARG;
+    if (!ws_ok(ws, ws_bytes, align_up(sizeof(uint64_t) * batch_words(r, n, r->L))))
+        return MODPP_ERR_WORKSPACE;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    uint64_t *w = static_cast<uint64_t *>(ws);
+    // log2(n) stages alternate buffers: start where the last one lands in out.
+    uint64_t *first = (ln % 2 == 1) ? w : out;
+    uint64_t *second = first == w ? out : w;
+    GatherTables t{};
+    t.per = static_cast<int>(n);
+    t.brev_bits = ln;
+    if (n == 1) t.brev_bits = 0;
+    if (launch_ct_gather(ct, first, n, r->L, static_cast<int>(r->N), t, r->tab, st) != cudaSuccess)
+        return MODPP_ERR_CUDA;
+    int rc = MODPP_OK;
+    tweak_stages(r, first, second, n, n, r->L, st, &rc);
+    return rc;
+}
+
+size_t modpp_transpose_workspace(modpp_ring r, int64_t groups) {
+    if (r == nullptr || groups < 0) return 0;
+    return std::max<size_t>(kAlign, transpose_scratch(r, groups));
+}
+
+int modpp_transpose(modpp_ring r, const uint64_t *ct, uint64_t *out, int64_t groups,
+                    const uint64_t *aut_keys, void *ws, size_t ws_bytes, void *stream) {
+    if (r == nullptr || groups < 0) return MODPP_ERR_ARG;
+    if (groups == 0) return MODPP_OK;
+    if (ct == nullptr || out == nullptr || aut_keys == nullptr) return MODPP_ERR_ARG;
+    if (!ws_ok(ws, ws_bytes, transpose_scratch(r, groups))) return MODPP_ERR_WORKSPACE;
+    return transpose_run(r, ct, out, groups, aut_keys, static_cast<char *>(ws),
+                         static_cast<cudaStream_t>(stream));
+}
+
+int modpp_rescale(modpp_ring r, const uint64_t *ct, uint64_t *out, int64_t n, void *stream) {
+    if (r == nullptr || n < 0 || r->L < 2) return MODPP_ERR_ARG;
+    if (n == 0) return MODPP_OK;
+    if (ct == nullptr || out == nullptr) return MODPP_ERR_ARG;
+    return cuda_status(launch_rescale(ct, out, r->L, n * r->N, r->tab, r->qlinv, r->qlinv_s,
+                                      static_cast<cudaStream_t>(stream)));
+}
+
+size_t cc_mm_workspace(modpp_ring r) {
+    if (r == nullptr || r->L < 2) return 0;
+    return cc_layout(r).total;
+}
+
+int cc_mm(modpp_ring r, const uint64_t *ct1, const uint64_t *ct2, const uint64_t *aut_keys,
+          const uint64_t *relin_key, uint64_t *out, void *ws, size_t ws_bytes, void *stream) {
+    if (r == nullptr || r->L < 2) return MODPP_ERR_ARG;
+    if (!ct1 || !ct2 || !aut_keys || !relin_key || !out) return MODPP_ERR_ARG;
+    const CcLayout lay = cc_layout(r);
+    if (!ws_ok(ws, ws_bytes, lay.total)) return MODPP_ERR_WORKSPACE;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    char *base = static_cast<char *>(ws);
+    const int L = r->L;
+    const int64_t N = r->N, NN = N * N;
+    uint64_t *rw = reinterpret_cast<uint64_t *>(base + lay.rw);
+    uint64_t *ut = reinterpret_cast<uint64_t *>(base + lay.ut);
+    uint64_t *x = reinterpret_cast<uint64_t *>(base + lay.x);
+    uint64_t *y = reinterpret_cast<uint64_t *>(base + lay.y);
+    uint64_t *z = reinterpret_cast<uint64_t *>(base + lay.z);
+    char *scratch = base + lay.scratch;
+    const bool timed = profile_active();
+    r->timed = timed;
+    auto mark = [&](int i) {
+        if (timed) cudaEventRecord(r->ev[i], st);
+    };
+    mark(0);
+    // Step 1: row-wise encryption of M2.
+    int rc = transpose_run(r, ct2, rw, 1, aut_keys, scratch, st);
+    if (rc) return rc;
+    mark(1);
+    // Step 2: [A; B] per prime (row r of A: coefficient r of every column
+    // ciphertext), then C[:, :N] = [A; B] * A~' and C[:, N:] = [A; B] * B~'.
+    cudaError_t e = launch_transpose_u64(ct1, ut, static_cast<int>(N), static_cast<int>(N), N, N,
+                                         NN, 2 * NN, L, st);
+    if (e == cudaSuccess)
+        e = launch_transpose_u64(ct1 + L * NN, ut + NN, static_cast<int>(N), static_cast<int>(N), N,
+                                 N, NN, 2 * NN, L, st);
+    if (e == cudaSuccess)
+        e = cudaMemsetAsync(x + static_cast<int64_t>(L) * 2 * NN, 0, sizeof(uint64_t) * L * 2 * NN,
+                            st);
+    if (e != cudaSuccess) return MODPP_ERR_CUDA;
+    const size_t wide_bytes = modpp_mm_wide_workspace(2 * N, N, N, r->primes.data(), L);
+    void *wws = base + lay.wide;
+    rc = modpp_mm_wide(2 * N, N, N, ut, N, 2 * NN, rw, N, NN, x, N, 2 * NN, r->primes.data(), L,
+                       wws, wide_bytes, st);
+    if (rc) return rc;
+    rc = modpp_mm_wide(2 * N, N, N, ut, N, 2 * NN, rw + L * NN, N, NN, y, N, 2 * NN,
+                       r->primes.data(), L, wws, wide_bytes, st);
+    if (rc) return rc;
+    mark(2);
+    // Steps 3-4: Transpose((C00, 0)) and Transpose((C10, 0)) as one batch.
+    rc = transpose_run(r, x, z, 2, aut_keys, scratch, st);
+    if (rc) return rc;
+    mark(3);
+    // Step 5: Relin(D0, 0) into rw (free now), then the sums and Rescale.
+    char *ks = scratch;
+    rc = ks_run(r, z, 2 * N, N, rw, N, relin_key, r->kid_zero, 1, 1, ks, st);
+    if (rc) return rc;
+    CcFinishParams fp{};
+    fp.R = rw;
+    fp.Z = z;
+    fp.Y = y;
+    fp.out = out;
+    fp.L = L;
+    fp.N = static_cast<int>(N);
+    fp.tab = r->tab;
+    fp.qlinv = r->qlinv;
+    fp.qlinv_s = r->qlinv_s;
+    if (launch_cc_finish(fp, st) != cudaSuccess) return MODPP_ERR_CUDA;
+    mark(4);
+    return MODPP_OK;
+}
+
+int cc_mm_stage_ms(modpp_ring r, double ms[4]) {
+    if (r == nullptr || ms == nullptr) return MODPP_ERR_ARG;
+    if (!r->timed) return MODPP_ERR_ARG;
+    for (int i = 0; i < 4; ++i) {
+        float v = 0.f;
+        if (cudaEventSynchronize(r->ev[i + 1]) != cudaSuccess ||
+            cudaEventElapsedTime(&v, r->ev[i], r->ev[i + 1]) != cudaSuccess)
+            return MODPP_ERR_CUDA;
+        ms[i] = v;
+    }
+    return MODPP_OK;
+}
+
+}  // extern "C"

@@ -700,3 +700,10 @@ int modpp_status_read(void *ws, void *stream) {
 }
 
 }  // extern "C"
+
+namespace modpp {
+bool profile_active() {
+    std::lock_guard<std::mutex> lock(g_prof_mu);
+    return g_prof_on;
+}
+}  // namespace modpp

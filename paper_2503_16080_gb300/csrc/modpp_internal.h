@@ -151,6 +151,9 @@ inline PlaneConst make_plane_const(uint64_t q, int b, uint64_t *C, int64_t ldc) 
     return p;
 }
 
+// True while modpp_profile_enable(1) is in effect.
+bool profile_active();
+
 // ------------------------------------------------------------ launchers
 // Each returns a cudaError_t from the launch (cudaSuccess when enqueued).
 cudaError_t launch_u_to_f16(const void *U, int ukind, int64_t ldu, int d, int k, int kp,

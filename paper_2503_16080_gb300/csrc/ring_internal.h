@@ -1,0 +1,77 @@
+// Internal declarations of the ring kernels (NTT, automorphism, key
+// switching, Tweak stages, Rescale) used by the ciphertext-ciphertext product.
+#pragma once
+#include <cuda_runtime.h>
+#include <cstdint>
+
+namespace modpp {
+
+// Per-prime constants and tables of the negacyclic NTT of degree N.
+struct NttPlane {
+    uint64_t q;
+    uint64_t mu;        // floor(2^64 / q), Barrett
+    uint64_t qinv_neg;  // -q^-1 mod 2^64, Montgomery
+    uint64_t ninv, ninv_s;  // N^-1 mod q and its Shoup quotient
+    uint64_t r64, r64_s;    // 2^64 mod q (Montgomery form factor) and its Shoup quotient
+    const uint64_t *fwd;    // psi^bitrev(i), i < N
+    const uint64_t *fwd_s;
+    const uint64_t *inv;    // psi^-bitrev(i)
+    const uint64_t *inv_s;
+};
+
+// Per-ciphertext tables of a gather: every table has period `per` over the
+// batch (ciphertext c reads entry c mod per; source indices are relative to
+// the period block of c).  Null tables mean identity source, shift 0, ell 1.
+// brev_bits > 0 takes the source index as the bit reversal of (c mod per)
+// over brev_bits bits instead of src; shift_src takes the shift equal to the
+// source index (the X^i ct_i of Alg. 4, step 1).
+struct GatherTables {
+    const int *src;
+    const int *shift;
+    const int *ell;
+    const uint64_t *scale;    // per plane, or null
+    const uint64_t *scale_s;
+    int per;
+    int brev_bits;
+    int shift_src;
+};
+
+cudaError_t launch_ntt(uint64_t *polys, int64_t npolys, int N, int64_t inner, int nplanes,
+                       const NttPlane *tab, bool inverse, cudaStream_t s);
+cudaError_t launch_to_montgomery(uint64_t *polys, int64_t npolys, int N, int64_t inner,
+                                 int nplanes, const NttPlane *tab, cudaStream_t s);
+cudaError_t launch_ks_decompose(const uint64_t *ct, int64_t n, int L, int N, int64_t c0,
+                                int64_t nb, const NttPlane *tab, uint64_t *D, cudaStream_t s);
+cudaError_t launch_ks_multacc(const uint64_t *D, const uint64_t *keys, const int *kid, int kper,
+                              int L, int N, int64_t c0, int64_t nb, const NttPlane *tab,
+                              uint64_t *U, cudaStream_t s);
+// Writes ciphertext c0 + c of the chunk to plane stride n_out of `out`.
+cudaError_t launch_ks_moddown(const uint64_t *U, const uint64_t *ct, int64_t n, int L, int N,
+                              int64_t c0, int64_t nb, const int *kid, int kper, int b_zero,
+                              const NttPlane *tab, const uint64_t *pinv, const uint64_t *pinv_s,
+                              uint64_t *out, int64_t n_out, cudaStream_t s);
+cudaError_t launch_ct_gather(const uint64_t *in, uint64_t *out, int64_t n, int L, int N,
+                             const GatherTables &t, const NttPlane *tab, cudaStream_t s);
+cudaError_t launch_tweak_stage(const uint64_t *in, uint64_t *out, int64_t n, int L, int N,
+                               int64_t half, const NttPlane *tab, cudaStream_t s);
+cudaError_t launch_add_planes(const uint64_t *x, const uint64_t *y, uint64_t *out, int parts, int L,
+                              int64_t count, const NttPlane *tab, cudaStream_t s);
+cudaError_t launch_rescale(const uint64_t *in, uint64_t *out, int L, int64_t count,
+                           const NttPlane *tab, const uint64_t *qlinv, const uint64_t *qlinv_s,
+                           cudaStream_t s);
+cudaError_t launch_transpose_u64(const uint64_t *in, uint64_t *out, int rows, int cols,
+                                 int64_t ldi, int64_t ldo, int64_t si, int64_t so, int mats,
+                                 cudaStream_t s);
+// Last step of Alg. 8 fused with Rescale; see ring_kernels.cu.
+struct CcFinishParams {
+    const uint64_t *R;  // relinearised D0: [2][L][N][N]
+    const uint64_t *Z;  // transposed (C00 | C10) batch: [2][L][2N][N]
+    const uint64_t *Y;  // [C01; C11] per prime: [L][2N][N]
+    uint64_t *out;      // [2][L-1][N][N]
+    int L, N;
+    const NttPlane *tab;
+    const uint64_t *qlinv, *qlinv_s;
+};
+cudaError_t launch_cc_finish(const CcFinishParams &p, cudaStream_t s);
+
+}  // namespace modpp

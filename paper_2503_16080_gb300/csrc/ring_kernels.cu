@@ -1,0 +1,496 @@
+// Ring kernels of the ciphertext-ciphertext product (Alg. 8): negacyclic NTT,
+// automorphisms, RNS key switching, Tweak (Alg. 3) stages, the gathers of
+// Transpose (Alg. 4), Rescale, and u64 matrix transposes.
+//
+// Ciphertext batches use the part-major layout [2][planes][n][N]: part 0 is
+// the a-part, part 1 the b-part; polynomial (part, plane, c) holds the N
+// coefficients of ciphertext c modulo prime `plane`.  All residues are
+// canonical in [0, q).
+//
+// NTT: negacyclic transform of Z_q[X]/(X^N+1) by the Cooley-Tukey (forward)
+// and Gentleman-Sande (inverse) butterflies with the powers of a primitive
+// 2N-th root psi in bit-reversed order (Longa and Naehrig, "Speeding up the
+// Number Theoretic Transform for Faster Ideal Lattice-Based Cryptography",
+// CANS 2016).  Products are pointwise in the transformed domain.
+//
+// Key-switching keys are kept in the transformed domain and in Montgomery
+// form (x * 2^64 mod q), so a product with a transformed digit is one
+// Montgomery reduction (P. Montgomery, Math. Comp. 1985).
+#include <cuda_runtime.h>
+
+#include "modarith.cuh"
+#include "ring_internal.h"
+
+namespace modpp {
+
+// ------------------------------------------------------------ arithmetic
+__device__ __forceinline__ uint64_t sub_mod(uint64_t a, uint64_t b, uint64_t q) {
+    return a >= b ? a - b : a + q - b;
+}
+
+// Montgomery product a * b * 2^-64 mod q for a < q, b < q, q odd < 2^62;
+// qinv = -q^-1 mod 2^64.
+__device__ __forceinline__ uint64_t mont_mul(uint64_t a, uint64_t b, uint64_t q, uint64_t qinv) {
+    const uint64_t lo = a * b;
+    const uint64_t hi = __umul64hi(a, b);
+    const uint64_t t = lo * qinv;
+    const uint64_t th = __umul64hi(t, q);
+    // (lo + t*q) is a multiple of 2^64; its carry out of the low word is 1
+    // unless lo == 0.
+    uint64_t r = hi + th + (lo != 0 ? 1u : 0u);
+    if (r >= q) r -= q;
+    return r;
+}
+
+// ------------------------------------------------------------ NTT
+// One CTA transforms one polynomial of N <= 16384 coefficients in shared
+// memory.  Polynomial p uses the tables of plane (p / inner) % nplanes.
+__global__ void __launch_bounds__(512) ntt_kernel(uint64_t *polys, int N, int logN, int64_t inner,
+                                                  int nplanes, const NttPlane *__restrict__ tab,
+                                                  int inverse) {
+    extern __shared__ uint64_t sa[];
+    const int64_t p = blockIdx.x;
+    const int plane = static_cast<int>((p / inner) % nplanes);
+    const NttPlane tp = tab[plane];
+    uint64_t *g = polys + p * N;
+    for (int i = threadIdx.x; i < N; i += blockDim.x) sa[i] = g[i];
+    __syncthreads();
+    const uint64_t q = tp.q;
+    const int half = N >> 1;
+    if (!inverse) {
+        int t = N;
+        for (int m = 1; m < N; m <<= 1) {
+            t >>= 1;
+            for (int b = threadIdx.x; b < half; b += blockDim.x) {
+                const int i = b / t, jj = b - (b / t) * t;
+                const int j = 2 * i * t + jj;
+                const uint64_t S = tp.fwd[m + i], Ss = tp.fwd_s[m + i];
+                const uint64_t U = sa[j];
+                const uint64_t V = shoup_mulmod(sa[j + t], S, Ss, q);
+                sa[j] = add_mod(U, V, q);
+                sa[j + t] = sub_mod(U, V, q);
+            }
+            __syncthreads();
+        }
+        for (int i = threadIdx.x; i < N; i += blockDim.x) g[i] = sa[i];
+    } else {
+        int t = 1;
+        for (int m = N; m > 1; m >>= 1) {
+            const int h = m >> 1;
+            for (int b = threadIdx.x; b < half; b += blockDim.x) {
+                const int i = b / t, jj = b - (b / t) * t;
+                const int j = 2 * i * t + jj;
+                const uint64_t S = tp.inv[h + i], Ss = tp.inv_s[h + i];
+                const uint64_t U = sa[j], V = sa[j + t];
+                sa[j] = add_mod(U, V, q);
+                sa[j + t] = shoup_mulmod(sub_mod(U, V, q), S, Ss, q);
+            }
+            t <<= 1;
+            __syncthreads();
+        }
+        for (int i = threadIdx.x; i < N; i += blockDim.x)
+            g[i] = shoup_mulmod(sa[i], tp.ninv, tp.ninv_s, q);
+    }
+}
+
+cudaError_t launch_ntt(uint64_t *polys, int64_t npolys, int N, int64_t inner, int nplanes,
+                       const NttPlane *tab, bool inverse, cudaStream_t s) {
+    if (npolys == 0) return cudaSuccess;
+    int logN = 0;
+    while ((1 << logN) < N) ++logN;
+    const size_t smem = static_cast<size_t>(N) * 8;
+    cudaError_t e = cudaFuncSetAttribute(ntt_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         static_cast<int>(smem));
+    if (e != cudaSuccess) return e;
+    const int threads = N >= 1024 ? 512 : (N / 2 > 32 ? N / 2 : 32);
+    ntt_kernel<<<static_cast<unsigned>(npolys), threads, smem, s>>>(polys, N, logN, inner, nplanes,
+                                                                   tab, inverse ? 1 : 0);
+    return cudaGetLastError();
+}
+
+// Keys to the evaluation domain in Montgomery form: x -> NTT(x) * 2^64 mod q.
+__global__ void to_montgomery_kernel(uint64_t *polys, int64_t npolys, int N, int64_t inner,
+                                     int nplanes, const NttPlane *__restrict__ tab) {
+    const int64_t total = npolys * N;
+    for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < total;
+         i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        const int64_t p = i / N;
+        const NttPlane &tp = tab[(p / inner) % nplanes];
+        polys[i] = shoup_mulmod(polys[i], tp.r64, tp.r64_s, tp.q);
+    }
+}
+
+cudaError_t launch_to_montgomery(uint64_t *polys, int64_t npolys, int N, int64_t inner,
+                                 int nplanes, const NttPlane *tab, cudaStream_t s) {
+    if (npolys == 0) return cudaSuccess;
+    to_montgomery_kernel<<<152 * 16, 256, 0, s>>>(polys, npolys, N, inner, nplanes, tab);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------ key switching
+// Digits of the a-parts of ciphertexts [c0, c0 + nb) (planes 0..L-1 of a
+// batch [2][L][n][N]): D[c][i][k] = (a_i of ciphertext c) mod q_k, k <= L.
+__global__ void ks_decompose_kernel(const uint64_t *__restrict__ ct, int64_t n, int L, int N,
+                                    int64_t c0, int64_t nb, const NttPlane *__restrict__ tab,
+                                    uint64_t *__restrict__ D) {
+    const int Lp = L + 1;
+    const int64_t total = nb * L * Lp * static_cast<int64_t>(N);
+    for (int64_t x = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; x < total;
+         x += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        const int m = static_cast<int>(x % N);
+        int64_t r = x / N;
+        const int k = static_cast<int>(r % Lp);
+        r /= Lp;
+        const int i = static_cast<int>(r % L);
+        const int64_t c = r / L;
+        const uint64_t v = ct[(static_cast<int64_t>(i) * n + c0 + c) * N + m];  // part 0, plane i
+        D[x] = barrett_u64(v, tab[k].q, tab[k].mu);
+    }
+}
+
+// U[c][part][k] = sum_i D[c][i][k] * key[kid(c)][i][part][k] in the evaluation
+// domain (keys in Montgomery form, digits plain: the product is plain).
+__global__ void ks_multacc_kernel(const uint64_t *__restrict__ D, const uint64_t *__restrict__ keys,
+                                  const int *__restrict__ kid, int kper, int L, int N, int64_t c0,
+                                  int64_t nb,
+                                  const NttPlane *__restrict__ tab, uint64_t *__restrict__ U) {
+    const int Lp = L + 1;
+    const int64_t key_stride = static_cast<int64_t>(L) * 2 * Lp * N;
+    const int64_t total = nb * Lp * static_cast<int64_t>(N);
+    for (int64_t x = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; x < total;
+         x += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        const int m = static_cast<int>(x % N);
+        const int64_t r = x / N;
+        const int k = static_cast<int>(r % Lp);
+        const int64_t c = r / Lp;
+        const uint64_t q = tab[k].q, qinv = tab[k].qinv_neg;
+        const int kc = kid[(c0 + c) % kper];
+        if (kc < 0) continue;
+        const uint64_t *key = keys + static_cast<int64_t>(kc) * key_stride;
+        uint64_t u0 = 0, u1 = 0;
+        for (int i = 0; i < L; ++i) {
+            const uint64_t d = D[((c * L + i) * Lp + k) * N + m];
+            const uint64_t ka = key[((static_cast<int64_t>(i) * 2 + 0) * Lp + k) * N + m];
+            const uint64_t kb = key[((static_cast<int64_t>(i) * 2 + 1) * Lp + k) * N + m];
+            u0 = add_mod(u0, mont_mul(d, ka, q, qinv), q);
+            u1 = add_mod(u1, mont_mul(d, kb, q, qinv), q);
+        }
+        U[((c * 2 + 0) * Lp + k) * N + m] = u0;
+        U[((c * 2 + 1) * Lp + k) * N + m] = u1;
+    }
+}
+
+// ModDown by P and accumulation: out_a = round(U_a / P), out_b = b + round(U_b / P),
+// with round(x / P) = (x_k - r) * P^-1 mod q_k, r = [x]_P centred.
+// Ciphertexts with kid < 0 are copied unchanged.  With b_zero the input
+// b-part is taken as 0 (Relin(D0, 0) in Alg. 8).
+__global__ void ks_moddown_kernel(const uint64_t *__restrict__ U, const uint64_t *__restrict__ ct,
+                                  int64_t n, int L, int N, int64_t c0, int64_t nb,
+                                  const int *__restrict__ kid, int kper, int b_zero,
+                                  const NttPlane *__restrict__ tab,
+                                  const uint64_t *__restrict__ pinv,
+                                  const uint64_t *__restrict__ pinv_s, uint64_t *__restrict__ out,
+                                  int64_t n_out) {
+    const int Lp = L + 1;
+    const uint64_t P = tab[L].q;
+    const int64_t total = nb * 2 * L * static_cast<int64_t>(N);
+    for (int64_t x = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; x < total;
+         x += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        const int m = static_cast<int>(x % N);
+        int64_t r = x / N;
+        const int k = static_cast<int>(r % L);
+        r /= L;
+        const int part = static_cast<int>(r % 2);
+        const int64_t c = r / 2;
+        const int64_t g = ((static_cast<int64_t>(part) * L + k) * n + c0 + c) * N + m;
+        const int64_t go = ((static_cast<int64_t>(part) * L + k) * n_out + c0 + c) * N + m;
+        if (kid[(c0 + c) % kper] < 0) {
+            out[go] = (part == 1 && b_zero) ? 0 : ct[g];
+            continue;
+        }
+        const uint64_t q = tab[k].q;
+        const uint64_t up = U[((c * 2 + part) * Lp + L) * N + m];
+        const uint64_t uk = U[((c * 2 + part) * Lp + k) * N + m];
+        // centred r: up - P if up > P/2; lift r into [0, q)
+        uint64_t rq;
+        if (up > P / 2) {
+            const uint64_t mag = barrett_u64(P - up, q, tab[k].mu);
+            rq = mag == 0 ? 0 : q - mag;
+        } else {
+            rq = barrett_u64(up, q, tab[k].mu);
+        }
+        const uint64_t v = shoup_mulmod(sub_mod(uk, rq, q), pinv[k], pinv_s[k], q);
+        out[go] = (part == 0 || b_zero) ? v : add_mod(ct[g], v, q);
+    }
+}
+
+cudaError_t launch_ks_decompose(const uint64_t *ct, int64_t n, int L, int N, int64_t c0,
+                                int64_t nb, const NttPlane *tab, uint64_t *D, cudaStream_t s) {
+    if (nb == 0) return cudaSuccess;
+    ks_decompose_kernel<<<152 * 16, 256, 0, s>>>(ct, n, L, N, c0, nb, tab, D);
+    return cudaGetLastError();
+}
+cudaError_t launch_ks_multacc(const uint64_t *D, const uint64_t *keys, const int *kid, int kper,
+                              int L, int N, int64_t c0, int64_t nb, const NttPlane *tab,
+                              uint64_t *U, cudaStream_t s) {
+    if (nb == 0) return cudaSuccess;
+    ks_multacc_kernel<<<152 * 16, 256, 0, s>>>(D, keys, kid, kper, L, N, c0, nb, tab, U);
+    return cudaGetLastError();
+}
+cudaError_t launch_ks_moddown(const uint64_t *U, const uint64_t *ct, int64_t n, int L, int N,
+                              int64_t c0, int64_t nb, const int *kid, int kper, int b_zero,
+                              const NttPlane *tab, const uint64_t *pinv, const uint64_t *pinv_s,
+                              uint64_t *out, int64_t n_out, cudaStream_t s) {
+    if (nb == 0) return cudaSuccess;
+    ks_moddown_kernel<<<152 * 16, 256, 0, s>>>(U, ct, n, L, N, c0, nb, kid, kper, b_zero, tab, pinv,
+                                               pinv_s, out, n_out);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------ gathers, Tweak
+// out[c] = scale * X^shift(c) * sigma_ell(c)(in[src(c)]) for every part and
+// plane; the tables repeat with period t.per (ciphertext c reads entry c mod
+// per, and src is relative to the block of `per` ciphertexts holding c).
+// X^t multiplies by a signed rotation (X^N = -1); sigma_ell maps X^i to
+// X^(i*ell mod 2N).  One thread per output coefficient: it reads input
+// coefficient i = (pos - shift) * ell^-1 mod 2N, ell^-1 taken mod 2N.
+__global__ void ct_gather_kernel(const uint64_t *__restrict__ in, uint64_t *__restrict__ out,
+                                 int64_t n, int L, int N, GatherTables t,
+                                 const NttPlane *__restrict__ tab) {
+    const int64_t total = 2 * static_cast<int64_t>(L) * n * N;
+    const int twoN = 2 * N;
+    for (int64_t x = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; x < total;
+         x += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        const int pos = static_cast<int>(x % N);  // output coefficient
+        int64_t r = x / N;
+        const int64_t c = r % n;                  // output ciphertext
+        r /= n;                                   // part * L + plane
+        const int plane = static_cast<int>(r % L);
+        const uint64_t q = tab[plane].q;
+        const int64_t ci = c % t.per;
+        const int64_t si = t.brev_bits > 0
+                               ? static_cast<int64_t>(__brev(static_cast<unsigned>(ci)) >>
+                                                      (32 - t.brev_bits))
+                               : (t.src ? t.src[ci] : ci);
+        const int64_t sc = (c - ci) + si;
+        const int64_t sh = t.shift_src ? si : (t.shift ? t.shift[ci] : 0);
+        // exponent e with X^e = X^pos * X^-shift, then through sigma_ell^-1
+        int64_t e = (pos - sh) % twoN;
+        if (e < 0) e += twoN;
+        if (t.ell) {
+            // inverse of an odd ell modulo 2^64 by Newton's iteration
+            // (each step doubles the number of correct low bits), then mod 2N
+            const uint64_t l = static_cast<uint64_t>(t.ell[ci]);
+            uint64_t y = l;  // correct to 3 bits for odd l
+            for (int k = 0; k < 5; ++k) y *= 2 - l * y;
+            e = static_cast<int64_t>((static_cast<uint64_t>(e) * (y & (twoN - 1))) & (twoN - 1));
+        }
+        bool neg = false;
+        if (e >= N) {
+            e -= N;
+            neg = true;
+        }
+        uint64_t v = in[(r * n + sc) * N + e];
+        if (t.scale) v = shoup_mulmod(v, t.scale[plane], t.scale_s[plane], q);
+        out[(r * n + c) * N + pos] = (neg && v != 0) ? q - v : v;
+    }
+}
+
+cudaError_t launch_ct_gather(const uint64_t *in, uint64_t *out, int64_t n, int L, int N,
+                             const GatherTables &t, const NttPlane *tab, cudaStream_t s) {
+    if (n == 0) return cudaSuccess;
+    ct_gather_kernel<<<152 * 16, 256, 0, s>>>(in, out, n, L, N, t, tab);
+    return cudaGetLastError();
+}
+
+// One radix-2 stage of Tweak (an n-point DFT over R_q with omega = X^(2N/n)):
+// for pairs (lo, hi = lo + half) inside blocks of 2*half,
+//   out_lo = x_lo + X^t x_hi,  out_hi = x_lo - X^t x_hi,  t = (lo mod half) * N / half.
+// Input ciphertexts must be in bit-reversed order before the first stage.
+__global__ void tweak_stage_kernel(const uint64_t *__restrict__ in, uint64_t *__restrict__ out,
+                                   int64_t n, int L, int N, int64_t half,
+                                   const NttPlane *__restrict__ tab) {
+    const int64_t pairs = n / 2;
+    const int64_t total = 2 * static_cast<int64_t>(L) * pairs * N;
+    for (int64_t x = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; x < total;
+         x += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        const int m = static_cast<int>(x % N);
+        int64_t r = x / N;
+        const int64_t pr = r % pairs;
+        r /= pairs;                               // part * L + plane
+        const uint64_t q = tab[r % L].q;
+        const int64_t jj = pr % half;
+        const int64_t lo = (pr / half) * 2 * half + jj;
+        const int64_t hi = lo + half;
+        const int t = static_cast<int>(jj * (N / half));
+        const uint64_t a = in[(r * n + lo) * N + m];
+        int src = m - t;
+        uint64_t y;
+        if (src >= 0) {
+            y = in[(r * n + hi) * N + src];
+        } else {
+            const uint64_t w = in[(r * n + hi) * N + src + N];
+            y = w == 0 ? 0 : q - w;
+        }
+        out[(r * n + lo) * N + m] = add_mod(a, y, q);
+        out[(r * n + hi) * N + m] = sub_mod(a, y, q);
+    }
+}
+
+cudaError_t launch_tweak_stage(const uint64_t *in, uint64_t *out, int64_t n, int L, int N,
+                               int64_t half, const NttPlane *tab, cudaStream_t s) {
+    if (n < 2) return cudaSuccess;
+    tweak_stage_kernel<<<152 * 16, 256, 0, s>>>(in, out, n, L, N, half, tab);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------ elementwise
+// out = x + y (mod q of each plane); arrays [parts][L][count] with planes of
+// `count` words.
+__global__ void add_planes_kernel(const uint64_t *x, const uint64_t *y, uint64_t *out, int parts,
+                                  int L, int64_t count, const NttPlane *__restrict__ tab) {
+    const int64_t total = static_cast<int64_t>(parts) * L * count;
+    for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < total;
+         i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        const int plane = static_cast<int>((i / count) % L);
+        out[i] = add_mod(x[i], y[i], tab[plane].q);
+    }
+}
+
+cudaError_t launch_add_planes(const uint64_t *x, const uint64_t *y, uint64_t *out, int parts, int L,
+                              int64_t count, const NttPlane *tab, cudaStream_t s) {
+    add_planes_kernel<<<152 * 16, 256, 0, s>>>(x, y, out, parts, L, count, tab);
+    return cudaGetLastError();
+}
+
+// Rescale by q_{L-1}: [2][L][count] -> [2][L-1][count],
+// x -> (x_k - r) * q_{L-1}^-1 mod q_k with r = [x]_{q_{L-1}} centred.
+__global__ void rescale_kernel(const uint64_t *__restrict__ in, uint64_t *__restrict__ out, int L,
+                               int64_t count, const NttPlane *__restrict__ tab,
+                               const uint64_t *__restrict__ qlinv,
+                               const uint64_t *__restrict__ qlinv_s) {
+    const uint64_t ql = tab[L - 1].q;
+    const int64_t total = 2 * static_cast<int64_t>(L - 1) * count;
+    for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < total;
+         i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        const int64_t e = i % count;
+        const int64_t r = i / count;
+        const int k = static_cast<int>(r % (L - 1));
+        const int part = static_cast<int>(r / (L - 1));
+        const uint64_t q = tab[k].q;
+        const uint64_t xl = in[(static_cast<int64_t>(part) * L + (L - 1)) * count + e];
+        const uint64_t xk = in[(static_cast<int64_t>(part) * L + k) * count + e];
+        uint64_t rq;
+        if (xl > ql / 2) {
+            const uint64_t mag = barrett_u64(ql - xl, q, tab[k].mu);
+            rq = mag == 0 ? 0 : q - mag;
+        } else {
+            rq = barrett_u64(xl, q, tab[k].mu);
+        }
+        out[i] = shoup_mulmod(sub_mod(xk, rq, q), qlinv[k], qlinv_s[k], q);
+    }
+}
+
+cudaError_t launch_rescale(const uint64_t *in, uint64_t *out, int L, int64_t count,
+                           const NttPlane *tab, const uint64_t *qlinv, const uint64_t *qlinv_s,
+                           cudaStream_t s) {
+    rescale_kernel<<<152 * 16, 256, 0, s>>>(in, out, L, count, tab, qlinv, qlinv_s);
+    return cudaGetLastError();
+}
+
+// out[c][r] = in[r][c] for `mats` matrices of rows x cols (leading dimensions
+// ldi, ldo; matrix strides si, so), through 32 x 32 shared-memory tiles.
+__global__ void transpose_u64_kernel(const uint64_t *__restrict__ in, uint64_t *__restrict__ out,
+                                     int rows, int cols, int64_t ldi, int64_t ldo, int64_t si,
+                                     int64_t so) {
+    __shared__ uint64_t tile[32][33];
+    const int64_t mat = blockIdx.z;
+    const int r0 = blockIdx.y * 32, c0 = blockIdx.x * 32;
+    for (int y = threadIdx.y; y < 32; y += blockDim.y) {
+        const int r = r0 + y, c = c0 + threadIdx.x;
+        if (r < rows && c < cols) tile[y][threadIdx.x] = in[mat * si + r * ldi + c];
+    }
+    __syncthreads();
+    for (int y = threadIdx.y; y < 32; y += blockDim.y) {
+        const int c = c0 + y, r = r0 + threadIdx.x;
+        if (r < rows && c < cols) out[mat * so + c * ldo + r] = tile[threadIdx.x][y];
+    }
+}
+
+cudaError_t launch_transpose_u64(const uint64_t *in, uint64_t *out, int rows, int cols,
+                                 int64_t ldi, int64_t ldo, int64_t si, int64_t so, int mats,
+                                 cudaStream_t s) {
+    if (rows == 0 || cols == 0 || mats == 0) return cudaSuccess;
+    dim3 grid((cols + 31) / 32, (rows + 31) / 32, mats);
+    transpose_u64_kernel<<<grid, dim3(32, 8), 0, s>>>(in, out, rows, cols, ldi, ldo, si, so);
+    return cudaGetLastError();
+}
+
+// Step 5 of Alg. 8 fused with Rescale by q_{L-1}: for ciphertext j and
+// coefficient m,
+//   a = Relin(D0_j, 0)_a + D1_j + D2_j + C01[m][j],
+//   b = Relin(D0_j, 0)_b + D3_j + C11[m][j],
+// then x -> (x_k - r) * q_{L-1}^-1 mod q_k with r = [x]_{q_{L-1}} centred.
+// C01 and C11 are read transposed through a 32 x 32 shared-memory tile.
+__device__ __forceinline__ uint64_t lift_centred(uint64_t x, uint64_t ql, uint64_t q, uint64_t mu) {
+    if (x > ql / 2) {
+        const uint64_t mag = barrett_u64(ql - x, q, mu);
+        return mag == 0 ? 0 : q - mag;
+    }
+    return barrett_u64(x, q, mu);
+}
+
+__global__ void __launch_bounds__(256) cc_finish_kernel(CcFinishParams p) {
+    __shared__ uint64_t tile[32][33];
+    const int N = p.N, L = p.L;
+    const int part = blockIdx.z;
+    const int m0 = blockIdx.x * 32, j0 = blockIdx.y * 32;
+    const int64_t NN = static_cast<int64_t>(N) * N;
+    const int64_t Rpart = static_cast<int64_t>(part) * L * NN;
+    const uint64_t ql = p.tab[L - 1].q;
+    uint64_t rl[4];  // x_{L-1} of this thread's four elements
+    for (int pass = 0; pass < L; ++pass) {
+        const int k = pass == 0 ? L - 1 : pass - 1;
+        const uint64_t q = p.tab[k].q;
+        // transposed tile of C01 (part 0) or C11 (part 1): rows m, columns j
+        const uint64_t *Yk = p.Y + static_cast<int64_t>(k) * 2 * NN + (part ? NN : 0);
+        __syncthreads();
+        for (int y = threadIdx.y; y < 32; y += 8) {
+            const int m = m0 + y, j = j0 + threadIdx.x;
+            if (m < N && j < N) tile[y][threadIdx.x] = Yk[static_cast<int64_t>(m) * N + j];
+        }
+        __syncthreads();
+        for (int e = 0; e < 4; ++e) {
+            const int jl = threadIdx.y + 8 * e;
+            const int j = j0 + jl, m = m0 + threadIdx.x;
+            if (j >= N || m >= N) continue;
+            const int64_t o = static_cast<int64_t>(j) * N + m;
+            const int64_t zk = static_cast<int64_t>(k) * 2 * NN;  // plane k of a 2N batch
+            const int64_t zpart = static_cast<int64_t>(L) * 2 * NN;
+            uint64_t v = p.R[Rpart + k * NN + o];
+            if (part == 0) {
+                v = add_mod(v, p.Z[zpart + zk + o], q);        // D1_j
+                v = add_mod(v, p.Z[zk + NN + o], q);           // D2_j
+            } else {
+                v = add_mod(v, p.Z[zpart + zk + NN + o], q);   // D3_j
+            }
+            v = add_mod(v, tile[threadIdx.x][jl], q);          // C01 / C11, column j
+            if (pass == 0) {
+                rl[e] = v;
+            } else {
+                const uint64_t rq = lift_centred(rl[e], ql, q, p.tab[k].mu);
+                p.out[(static_cast<int64_t>(part) * (L - 1) + k) * NN + o] =
+                    shoup_mulmod(sub_mod(v, rq, q), p.qlinv[k], p.qlinv_s[k], q);
+            }
+        }
+    }
+}
+
+cudaError_t launch_cc_finish(const CcFinishParams &p, cudaStream_t s) {
+    if (p.N == 0) return cudaSuccess;
+    dim3 grid((p.N + 31) / 32, (p.N + 31) / 32, 2);
+    cc_finish_kernel<<<grid, dim3(32, 8), 0, s>>>(p);
+    return cudaGetLastError();
+}
+
+}  // namespace modpp
