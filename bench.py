@@ -501,6 +501,180 @@ def run_secondary(args):
     return 0
 
 
+# ----------------------------------------------------------------- CC-MM
+
+CC_WORKLOAD = ("CC-MM n=8192 (Alg. 8): two column-wise encrypted 8192x8192 matrices, ring degree "
+               "8192, L=4 primes of 50 bits + a 60-bit special prime, N automorphism keys and a "
+               "relinearisation key resident on the device; output rescaled by q_3")
+
+
+def run_ccmm(args):
+    import numpy as np
+    import torch
+
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2503_16080_gb300 as pkg
+    from paper_2503_16080_gb300 import synth
+
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream()
+    Nr = args.ccmm_n
+    L = 4
+    primes = synth.ntt_primes(50, L)
+    prp = primes + synth.ntt_primes(60, 1)
+    ring = pkg.Ring(Nr, prp)
+
+    # Keys: uniform residues per prime plane (the kernels' work does not
+    # depend on the key values; prepared keys are residues like any other).
+    keys = torch.empty((Nr, L, 2, L + 1, Nr), dtype=torch.uint64, device=dev)
+    for k, q in enumerate(prp):
+        keys.view(torch.int64)[:, :, :, k, :] = synth.uniform_mod_torch(
+            SEED, 300 + k, (Nr, L, 2, Nr), q, dev).view(torch.int64)
+    rkey = torch.empty((1, L, 2, L + 1, Nr), dtype=torch.uint64, device=dev)
+    for k, q in enumerate(prp):
+        rkey.view(torch.int64)[:, :, :, k, :] = synth.uniform_mod_torch(
+            SEED, 400 + k, (1, L, 2, Nr), q, dev).view(torch.int64)
+
+    def cts(stream_id):
+        t = torch.empty((2, L, Nr, Nr), dtype=torch.uint64, device=dev)
+        for j, q in enumerate(primes):
+            t.view(torch.int64)[:, j] = synth.uniform_mod_torch(
+                SEED, stream_id + j, (2, Nr, Nr), q, dev).view(torch.int64)
+        return t
+
+    ct1, ct2 = cts(500), cts(600)
+    out = torch.empty((2, L - 1, Nr, Nr), dtype=torch.uint64, device=dev)
+    ws_bytes = ring.cc_mm_workspace_bytes()
+    ws = torch.empty(ws_bytes, dtype=torch.uint8, device=dev)
+
+    def step():
+        ring.cc_mm(ct1, ct2, keys, rkey, out=out, workspace=ws)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(0)
+    clocks.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1) / args.steps
+
+    # Stage split and GEMM launches (one extra, separately timed call).
+    pkg.profile_enable(True)
+    step()
+    stages = ring.cc_mm_stage_ms()
+    gemm_ms, gemm_n = pkg.profile_read(pkg.KERNEL_GEMM)
+    pkg.profile_enable(False)
+
+    peaks, peak_src = load_peaks()
+    LU = -(-(max(primes) - 1).bit_length() // 8)
+    LA = pkg.plan_info(Nr, primes[0])["digits"]
+    gemm_flops = 2.0 * (2 * Nr) * Nr * Nr * LA  # one launch: one 8-bit digit plane of U
+    g_avg = gemm_ms / max(gemm_n, 1)
+    achieved = gemm_flops / (g_avg * 1e-3) / 1e12
+    peak = peaks["bf16_tflops_sustained"]
+    modops = 2.0 * (2 * Nr) * Nr * (2 * Nr) * L
+
+    # FP64 matmul of the same n.
+    Ad = torch.empty((Nr, Nr), dtype=torch.float64, device=dev).uniform_(-1, 1)
+    Bd = torch.empty_like(Ad).uniform_(-1, 1)
+    torch.matmul(Ad, Bd)
+    torch.cuda.synchronize()
+    f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    f0.record(stream)
+    torch.matmul(Ad, Bd)
+    f1.record(stream)
+    torch.cuda.synchronize()
+    dgemm_ms = f0.elapsed_time(f1)
+    del Ad, Bd
+
+    # End to end: both ciphertext matrices from pinned host memory, the
+    # product, and the result back, every step (keys stay resident).
+    h1 = torch.empty(ct1.shape, dtype=torch.uint64).pin_memory()
+    h2 = torch.empty(ct2.shape, dtype=torch.uint64).pin_memory()
+    ho = torch.empty(out.shape, dtype=torch.uint64).pin_memory()
+    h1.copy_(ct1)
+    h2.copy_(ct2)
+
+    def e2e_step():
+        ct1.copy_(h1, non_blocking=True)
+        ct2.copy_(h2, non_blocking=True)
+        step()
+        ho.copy_(out, non_blocking=True)
+
+    e2e_step()
+    torch.cuda.synchronize()
+    g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e2e_steps = max(1, min(args.steps, 3))
+    g0.record(stream)
+    for _ in range(e2e_steps):
+        e2e_step()
+    g1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = g0.elapsed_time(g1) / e2e_steps
+
+    # CPU oracle on a small ring (N=512): the whole CC-MM, and its Mod-PP-MM
+    # part alone; the products extrapolate by N^3, the rest (transposes, key
+    # switches, relin) by N^2 log N.
+    cpu = None
+    if not args.quick:
+        import oracle
+        oracle.build()
+        n0 = 512
+        kz = [None] + [np.zeros((L, 2, L + 1, n0), dtype=np.uint64)] * (n0 - 1)
+        c0 = np.zeros((n0, 2, L, n0), dtype=np.uint64)
+        for j, q in enumerate(primes):
+            c0[:, :, j, :] = synth.uniform_mod(SEED, 700 + j, (n0, 2, n0), q)
+        t0 = time.perf_counter()
+        oracle.cc_mm(c0, c0, kz, np.zeros((L, 2, L + 1, n0), dtype=np.uint64), prp)
+        t_all = time.perf_counter() - t0
+        Ub = np.concatenate([c0[:, 0, 0, :].T, c0[:, 1, 0, :].T])
+        Wb = np.concatenate([c0[:, 0, 0, :], c0[:, 1, 0, :]], axis=1)
+        t0 = time.perf_counter()
+        oracle.mod_pp_mm_residues(Ub, Wb, primes[0])
+        t_mm = (time.perf_counter() - t0) * L
+        f = Nr / n0
+        est = t_mm * f ** 3 + max(t_all - t_mm, 0.0) * f ** 2 * np.log2(Nr) / np.log2(n0)
+        cpu = {"value": est * 1e3, "unit": "ms per CC-MM",
+               "cores": int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1)),
+               "kind": "oracle",
+               "sample": f"one oracle CC-MM at N={n0} ({t_all:.1f} s, of which {t_mm:.1f} s in the "
+                         f"step-2 products); products scaled by (N/{n0})^3, the rest by "
+                         f"(N/{n0})^2 log N"}
+
+    line = {"metric": METRIC, "workload": "ccmm8192" if Nr == 8192 else f"ccmm{Nr}",
+            "value": ms, "unit": "ms per CC-MM", "higher_is_better": False, "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "scaling": "weak",
+            "vs_baseline": None, "dtype": "u64 residues (f16 digits on tcgen05)",
+            "data": "synthetic",
+            "config": {"workload": CC_WORKLOAD.replace("8192", str(Nr)), "N": Nr, "L": L,
+                       "prime_bits": 50, "special_prime_bits": 60,
+                       "l2": "inputs larger than L2", "key_bytes": keys.numel() * 8,
+                       "workspace_bytes": ws_bytes},
+            "stages_ms": {"transpose_ct2": stages[0], "mod_pp_mm_x2": stages[1],
+                          "transpose_C00_C10": stages[2], "relin_finish": stages[3]},
+            "mod_pp_mm_tops": modops / (stages[1] * 1e-3) / 1e12,
+            "roofline": {"kernel": "gemm_f16_kernel", "bound": "tensor", "achieved": achieved,
+                         "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                         "peak_source": f"{peak_src} bf16 dense sustained (f16 same rate)",
+                         "avg_launch_ms": g_avg, "launches_per_cc_mm": gemm_n,
+                         "u_digit_planes": LU, "a_digits": LA},
+            "fp64_matmul_ms": dgemm_ms, "slowdown_vs_fp64_matmul": ms / dgemm_ms,
+            "e2e": {"value": e2e_ms, "unit": "ms per CC-MM", "h2d_bytes_per_step":
+                    8 * (h1.numel() + h2.numel()), "d2h_bytes_per_step": 8 * ho.numel()},
+            "cpu_baseline": cpu, "clocks": clk}
+    ring.close()
+    print(json.dumps(line))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -513,11 +687,13 @@ def main():
     ap.add_argument("--digit-bits", type=int, default=0,
                     help="digit width of the f16 path (8, 9, 10; 0 = library default)")
     ap.add_argument("--workload", default="pcmm4096",
-                    choices=["pcmm4096", "pcmm16384", "pcmv", "grouped"],
+                    choices=["pcmm4096", "pcmm16384", "pcmv", "grouped", "ccmm8192"],
                     help="pcmm4096 (default, the benchmark line); the others are recorded "
                          "beside it")
     ap.add_argument("--n", type=int, default=4096,
                     help="square size d = k = N (default 4096, the benchmark workload)")
+    ap.add_argument("--ccmm-n", type=int, default=8192,
+                    help="ring degree of the ccmm8192 workload (smaller for profiling)")
     args = ap.parse_args()
     global D, K, N, WORKLOAD
     if args.n != 4096:
@@ -527,6 +703,8 @@ def main():
         args.warmup = 3
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "ccmm8192":
+        return run_ccmm(args)
     if args.workload != "pcmm4096":
         return run_secondary(args)
     return run_ours(args)
