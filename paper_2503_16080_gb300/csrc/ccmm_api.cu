@@ -27,7 +27,7 @@ struct modpp_ring_s {
     const uint64_t *pinv = nullptr, *pinv_s = nullptr;    // P^-1 mod q_k, k < L
     const uint64_t *qlinv = nullptr, *qlinv_s = nullptr;  // q_{L-1}^-1 mod q_k, k < L-1
     const uint64_t *ninv = nullptr, *ninv_s = nullptr;    // N^-1 mod q_k, k < L
-    const int *t2_src = nullptr, *t2_ell = nullptr, *t2_kid = nullptr;
+    const int *t2_src = nullptr, *t2_ellinv = nullptr, *t2_kid = nullptr;
     const int *t3_src = nullptr, *t3_shift = nullptr;
     const int *kid_zero = nullptr;
     cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
@@ -170,8 +170,13 @@ int ks_run(const modpp_ring_s *r, const uint64_t *ct, int64_t n, int64_t count, 
         scratch + align_up(sizeof(uint64_t) * nb * L * Lp * r->N));
     for (int64_t c0 = 0; c0 < count; c0 += nb) {
         const int64_t m = std::min(nb, count - c0);
-        cudaError_t e = launch_ks_decompose(ct, n, L, N, c0, m, r->tab, D, st);
-        if (e == cudaSuccess) e = launch_ntt(D, m * L * Lp, N, 1, Lp, r->tab, false, st);
+        cudaError_t e;
+        if (ntt_fast_supported(N)) {
+            e = launch_ks_digits_ntt(ct, n, L, N, c0, m, r->tab, D, st);
+        } else {
+            e = launch_ks_decompose(ct, n, L, N, c0, m, r->tab, D, st);
+            if (e == cudaSuccess) e = launch_ntt(D, m * L * Lp, N, 1, Lp, r->tab, false, st);
+        }
         if (e == cudaSuccess) e = launch_ks_multacc(D, keys, kid, kper, L, N, c0, m, r->tab, U, st);
         if (e == cudaSuccess) e = launch_ntt(U, m * 2 * Lp, N, 1, Lp, r->tab, true, st);
         if (e == cudaSuccess)
@@ -231,7 +236,7 @@ int transpose_run(const modpp_ring_s *r, const uint64_t *ct, uint64_t *out, int6
     GatherTables t2{};
     t2.per = N;
     t2.src = r->t2_src;
-    t2.ell = r->t2_ell;
+    t2.ellinv = r->t2_ellinv;
     t2.scale = r->ninv;
     t2.scale_s = r->ninv_s;
     if (launch_ct_gather(aux, other, n, L, N, t2, r->tab, st) != cudaSuccess) return MODPP_ERR_CUDA;
@@ -381,28 +386,28 @@ int modpp_ring_create(int64_t N, int L, const uint64_t *primes_host, void *mem, 
     // Index tables of Alg. 4 (ints, period N).
     auto *ints = reinterpret_cast<int *>(host.data() + lay.ints);
     const int *dints = reinterpret_cast<const int *>(r->mem + lay.ints);
-    int *t2_src = ints, *t2_ell = ints + N, *t2_kid = ints + 2 * N;
+    int *t2_src = ints, *t2_ellinv = ints + N, *t2_kid = ints + 2 * N;
     int *t3_src = ints + 3 * N, *t3_shift = ints + 4 * N;
     const uint64_t twoN = 2 * static_cast<uint64_t>(N);
     for (int64_t c = 0; c < N; ++c) {
         // position c of the bit-reversed second Tweak input holds aux'_j, j = bitrev(c)
         const int64_t j = bitrev(static_cast<unsigned>(c), r->logN);
         const uint64_t ell = 2 * static_cast<uint64_t>(j) + 1;
-        uint64_t inv = 1;  // ell^-1 mod 2N by search over odd residues (host, once)
-        for (uint64_t v = 1; v < twoN; v += 2)
-            if ((v * ell) % twoN == 1) {
-                inv = v;
-                break;
-            }
+        // ell^-1 modulo 2^64 by Newton's iteration (each step doubles the
+        // correct low bits; ell is odd, so ell is its own inverse mod 8),
+        // then modulo 2N.
+        uint64_t inv = ell;
+        for (int it = 0; it < 5; ++it) inv *= 2 - ell * inv;
+        inv &= twoN - 1;
         t2_src[c] = static_cast<int>((inv - 1) / 2);
-        t2_ell[c] = static_cast<int>(ell);
+        t2_ellinv[c] = static_cast<int>(inv);
         t2_kid[c] = j == 0 ? -1 : static_cast<int>(j);
         t3_src[c] = c == 0 ? 0 : static_cast<int>(N - c);
         t3_shift[c] = c == 0 ? 0 : static_cast<int>(2 * N - c);
     }
     ints[5 * N] = 0;
     r->t2_src = dints;
-    r->t2_ell = dints + N;
+    r->t2_ellinv = dints + N;
     r->t2_kid = dints + 2 * N;
     r->t3_src = dints + 3 * N;
     r->t3_shift = dints + 4 * N;

@@ -75,15 +75,31 @@ struct TileJob {
     int Lp;           // digits of this plane
 };
 
+// Position `local` of a plane's m_blocks x n_blocks tiles in band order:
+// bands of `band` row blocks (the last may be shorter), row block fastest
+// inside a band, then column block.
+__device__ __forceinline__ void band_order(int local, int m_blocks, int n_blocks, int band,
+                                           int &mb, int &nb) {
+    if (band < 1) band = m_blocks;
+    const int per_band = band * n_blocks;
+    const int b = local / per_band;
+    const int first = b * band;
+    const int g = min(band, m_blocks - first);
+    const int r = local - b * per_band;
+    mb = first + r % g;
+    nb = r / g;
+}
+
 template <int L, int NC, bool GROUPED>
 __device__ __forceinline__ TileJob tile_job(int tile, const CUtensorMap *tmU,
                                             const CUtensorMap *tmD, const GemmParams &p) {
     TileJob j;
     if constexpr (!GROUPED) {
-        // Row block fastest: the concurrently running tiles share the digit
-        // tiles of a few column blocks (and U stays in L2).  Plane fastest, for
-        // thin outputs with a large U: the planes of one row block run together
-        // and read that block of U from HBM once.
+        // Row block fastest inside bands of p.band_m row blocks: the
+        // concurrently running tiles share the digit tiles of a few column
+        // blocks and the band's rows of U, which stay in L2.  Plane fastest,
+        // for thin outputs with a large U: the planes of one row block run
+        // together and read that block of U from HBM once.
         int plane;
         if (p.plane_fastest) {
             plane = tile % p.planes;
@@ -91,10 +107,9 @@ __device__ __forceinline__ TileJob tile_job(int tile, const CUtensorMap *tmU,
             j.mb = rest % p.m_blocks;
             j.nb = rest / p.m_blocks;
         } else {
-            j.mb = tile % p.m_blocks;
-            const int rest = tile / p.m_blocks;
-            j.nb = rest % p.n_blocks;
-            plane = rest / p.n_blocks;
+            const int per_plane = p.m_blocks * p.n_blocks;
+            plane = tile / per_plane;
+            band_order(tile - plane * per_plane, p.m_blocks, p.n_blocks, p.band_m, j.mb, j.nb);
         }
         j.tmU = tmU;
         j.tmD = tmD;
@@ -114,9 +129,7 @@ __device__ __forceinline__ TileJob tile_job(int tile, const CUtensorMap *tmU,
             else hi = mid - 1;
         }
         const GroupPlane &g = p.gplanes[lo];
-        const int local = tile - g.tile_begin;
-        j.mb = local % g.m_blocks;
-        j.nb = local / g.m_blocks;
+        band_order(tile - g.tile_begin, g.m_blocks, g.n_blocks, g.band_m, j.mb, j.nb);
         j.tmU = g.tmU;
         j.tmD = g.tmD;
         j.pc = &g.pc;

@@ -391,6 +391,7 @@ int plan_build(modpp_group_plan *pl, int b, cudaStream_t st) {
             gpl.kb_total = static_cast<int>((p.k + kBK - 1) / kBK);
             gpl.m_blocks = m_blocks;
             gpl.n_blocks = static_cast<int>(nbk);
+            gpl.band_m = band_rows(m_blocks, kp);
             gpl.Lp = Lp;
             gpl.dplane = j;
             gpl.tile_begin = static_cast<int>(tiles);

@@ -306,6 +306,7 @@ int run_f16(int64_t d, int64_t k, int64_t n, const void *U, int ukind, int64_t l
                         lay.n_blocks <= 2 && planes > 1)
                            ? 1
                            : 0;
+    gp.band_m = band_rows(gp.m_blocks, lay.kp);
     gp.status = status;
     gp.timeout_ns = wait_limit_ns();
     for (int i = 0; i < planes; ++i)
@@ -481,6 +482,7 @@ int run_f16_wide(int64_t d, int64_t k, int64_t n, const uint64_t *U, int64_t ldu
         const int64_t tiles = static_cast<int64_t>(gp.m_blocks) * gp.n_blocks;
         if (tiles >= (int64_t(1) << 31)) return MODPP_ERR_UNSUPPORTED;
         gp.num_tiles = static_cast<int>(tiles);
+        gp.band_m = band_rows(gp.m_blocks, lay.kp);
         gp.status = reinterpret_cast<int *>(w);
         gp.timeout_ns = wait_limit_ns();
         uint64_t w8 = 1 % q;

@@ -62,6 +62,7 @@ struct GroupPlane {
     int Lp;                  // digits of this problem
     int dplane;              // index of this plane within the problem's digit matrix
     int tile_begin;
+    int band_m;              // row blocks per band of the tile order (see band_rows)
 };
 
 struct GemmParams {
@@ -71,7 +72,8 @@ struct GemmParams {
     int planes;
     int kb_total;     // ceil(k / kBK)
     int num_tiles;    // planes * n_blocks * m_blocks
-    int plane_fastest;  // tile order: 0 = row block fastest, 1 = plane fastest
+    int plane_fastest;  // tile order: 0 = row block fastest (in bands), 1 = plane fastest
+    int band_m;         // row blocks per band of the row-fastest order (see band_rows)
     int *status;      // device status word (workspace)
     uint64_t timeout_ns;
     const GroupPlane *gplanes;  // grouped launches only
@@ -153,6 +155,20 @@ inline PlaneConst make_plane_const(uint64_t q, int b, uint64_t *C, int64_t ldc) 
 
 // True while modpp_profile_enable(1) is in effect.
 bool profile_active();
+
+// Row blocks per band of the tile order.  Tiles run band by band: inside a
+// band the row block varies fastest, then the column block.  The concurrently
+// running tiles then share the band's rows of U and a few column blocks of
+// digits; the band's U rows (kBM * kp f16 each block) stay in L2 while all
+// column blocks pass, so U is read from HBM about once and the digit matrix
+// once per band.  U that fits the budget whole forms a single band.
+constexpr int64_t kBandBytes = int64_t(32) << 20;
+inline int band_rows(int m_blocks, int64_t kp) {
+    const int64_t per_block = static_cast<int64_t>(kBM) * kp * 2;
+    int64_t b = kBandBytes / (per_block > 0 ? per_block : 1);
+    if (b < 1) b = 1;
+    return b >= m_blocks ? m_blocks : static_cast<int>(b);
+}
 
 // ------------------------------------------------------------ launchers
 // Each returns a cudaError_t from the launch (cudaSuccess when enqueued).

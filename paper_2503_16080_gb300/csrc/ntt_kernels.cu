@@ -1,0 +1,291 @@
+// Negacyclic NTT of degree N >= 1024 with 16 coefficients per thread.
+//
+// Same transform as the per-stage kernel in ring_kernels.cu (Cooley-Tukey
+// forward / Gentleman-Sande inverse with bit-reversed powers of psi, Longa and
+// Naehrig, CANS 2016), organised for the GPU: each thread holds 16
+// coefficients in registers and runs up to four butterfly stages on them
+// before the coefficients go back to shared memory, so log2(N) stages take
+// ceil(log2(N) / 4) shared-memory round trips.  The first pass reads global
+// memory and the last writes it.  Butterflies keep values lazily reduced
+// (D. Harvey, "Faster arithmetic for number-theoretic transforms", J. Symb.
+// Comp. 2014): forward values live in [0, 4q), inverse ones in [0, 2q), which
+// needs 4q < 2^64 (q < 2^62).
+//
+// The forward transform can also read its input from the a-part of a
+// ciphertext batch and reduce it modulo the target prime on the fly: the
+// digit decomposition of key switching fused into the transform.
+#include <cuda_runtime.h>
+
+#include <cstdlib>
+
+#include "modarith.cuh"
+#include "ring_internal.h"
+
+namespace modpp {
+namespace {
+
+// Shared-memory index with one padding word per 32: strided groups of
+// threads then fall into different banks.
+__device__ __forceinline__ int pad_idx(int j) { return j + (j >> 5); }
+
+// a * w mod q up to one multiple of q: the result lies in [0, 2q).
+__device__ __forceinline__ uint64_t shoup_lazy(uint64_t a, uint64_t w, uint64_t ws, uint64_t q) {
+    return a * w - __umul64hi(a, ws) * q;
+}
+
+struct NttFastArgs {
+    uint64_t *polys;
+    int N, logN;
+    int64_t inner;
+    int nplanes;
+    const NttPlane *tab;
+    // Key-switching source (forward only): polynomial p = (c * L + i) * (L + 1) + k
+    // reads the a-part plane i of ciphertext c0 + c of a batch with plane
+    // stride n, reduced modulo prime k.  Null: transform polys in place.
+    const uint64_t *ks_ct;
+    int64_t ks_n, ks_c0;
+    int ks_L;
+};
+
+// Constants of the polynomial's prime, held in registers.
+struct PlaneRegs {
+    uint64_t q, q2, mu, ninv, ninv_s;
+    const uint64_t *tw, *tw_s;  // fwd tables (forward) or inv tables (inverse)
+};
+
+// First coefficient of group g in a pass with group stride 2^lu and groups
+// of 2^S: groups are blocks of u * 2^S coefficients split by residue r < u.
+// For u >= 16 consecutive threads take consecutive r (contiguous
+// addresses), otherwise consecutive blocks (distinct padded banks).
+template <int S>
+__device__ __forceinline__ int group_start(int g, int lu, int lnb) {
+    int blk, r;
+    if (lu >= 4) {
+        r = g & ((1 << lu) - 1);
+        blk = g >> lu;
+    } else {
+        blk = g & ((1 << lnb) - 1);
+        r = g >> lnb;
+    }
+    return (blk << (lu + S)) + r;
+}
+
+template <int E, int S, bool FWD>
+__device__ __forceinline__ void ntt_pass(uint64_t *sa, const uint64_t *gin, uint64_t *gout,
+                                         bool reduce_in, int N, int logN, int lu, bool first,
+                                         bool last, const PlaneRegs &pr) {
+    constexpr int G = E >> S;  // groups of 2^S coefficients per thread
+    constexpr int W = 1 << S;
+    const int T = N / E;
+    const int lnb = logN - lu - S;  // log2 of the number of blocks
+    uint64_t v[E];
+#pragma unroll
+    for (int gi = 0; gi < G; ++gi) {
+        const int j0 = group_start<S>(threadIdx.x + T * gi, lu, lnb);
+#pragma unroll
+        for (int k = 0; k < W; ++k) {
+            const int j = j0 + (k << lu);
+            uint64_t x;
+            if (first) {
+                x = gin[j];
+                if (reduce_in) x = barrett_u64(x, pr.q, pr.mu);
+            } else {
+                x = sa[pad_idx(j)];
+            }
+            v[gi * W + k] = x;
+        }
+    }
+#pragma unroll
+    for (int gi = 0; gi < G; ++gi) {
+        const int blk = group_start<S>(threadIdx.x + T * gi, lu, lnb) >> (lu + S);
+#pragma unroll
+        for (int st = 0; st < S; ++st) {
+            // Pairs (k, k + half) of the group, k with bit `half` clear; the
+            // twiddle index depends on k's sub-block only.
+            //   forward: distance d = u * 2^(S-1-st), stage m = N / (2d),
+            //            i = blk * 2^st + (k >> (S - st))
+            //   inverse: distance d = u * 2^st, h = N / (2d),
+            //            i = blk * 2^(S-1-st) + (k >> (st + 1))
+            const int half = FWD ? (W >> (st + 1)) : (1 << st);
+            const int base = FWD ? (N >> (lu + S - st)) + (blk << st)
+                                 : (N >> (lu + st + 1)) + (blk << (S - 1 - st));
+            const int sh = FWD ? (S - st) : (st + 1);
+#pragma unroll
+            for (int k = 0; k < W; ++k) {
+                if (k & half) continue;
+                uint64_t &x = v[gi * W + k];
+                uint64_t &y = v[gi * W + k + half];
+                const int ti = base + (k >> sh);
+                const uint64_t w = pr.tw[ti], ws = pr.tw_s[ti];
+                if (FWD) {
+                    const uint64_t xa = x >= pr.q2 ? x - pr.q2 : x;
+                    const uint64_t t = shoup_lazy(y, w, ws, pr.q);
+                    x = xa + t;
+                    y = xa - t + pr.q2;
+                } else {
+                    uint64_t sm = x + y;
+                    sm = sm >= pr.q2 ? sm - pr.q2 : sm;
+                    const uint64_t d = x - y + pr.q2;
+                    x = sm;
+                    y = shoup_lazy(d, w, ws, pr.q);
+                }
+            }
+        }
+    }
+    // Each thread writes back exactly the positions it read: no barrier
+    // is needed between this pass's reads and writes.
+#pragma unroll
+    for (int gi = 0; gi < G; ++gi) {
+        const int j0 = group_start<S>(threadIdx.x + T * gi, lu, lnb);
+#pragma unroll
+        for (int k = 0; k < W; ++k) {
+            const int j = j0 + (k << lu);
+            uint64_t x = v[gi * W + k];
+            if (last) {
+                if (FWD) {
+                    x = x >= pr.q2 ? x - pr.q2 : x;
+                    x = x >= pr.q ? x - pr.q : x;
+                } else {
+                    x = shoup_mulmod(x, pr.ninv, pr.ninv_s, pr.q);
+                }
+                gout[j] = x;
+            } else {
+                sa[pad_idx(j)] = x;
+            }
+        }
+    }
+    if (!last) __syncthreads();
+}
+
+// E coefficients per thread (N / E threads), passes of up to log2(E) stages.
+template <int E>
+struct NttShape {
+    static constexpr int kLogE = E == 8 ? 3 : (E == 16 ? 4 : 5);
+    static constexpr int kMaxThreads = E == 8 ? 1024 : 512;
+};
+
+template <int E, bool FWD>
+__global__ void __launch_bounds__(NttShape<E>::kMaxThreads, 1) ntt_e_kernel(NttFastArgs a) {
+    constexpr int SM = NttShape<E>::kLogE;
+    extern __shared__ uint64_t sa[];
+    const int64_t p = blockIdx.x;
+    const int N = a.N;
+    int plane;
+    const uint64_t *gin;
+    if (a.ks_ct) {
+        const int Lp = a.ks_L + 1;
+        plane = static_cast<int>(p % Lp);
+        const int64_t r = p / Lp;
+        const int i = static_cast<int>(r % a.ks_L);
+        const int64_t c = r / a.ks_L;
+        gin = a.ks_ct + (static_cast<int64_t>(i) * a.ks_n + a.ks_c0 + c) * N;
+    } else {
+        plane = static_cast<int>((p / a.inner) % a.nplanes);
+        gin = a.polys + p * N;
+    }
+    const NttPlane &tp = a.tab[plane];
+    PlaneRegs pr;
+    pr.q = tp.q;
+    pr.q2 = 2 * tp.q;
+    pr.mu = tp.mu;
+    pr.ninv = tp.ninv;
+    pr.ninv_s = tp.ninv_s;
+    pr.tw = FWD ? tp.fwd : tp.inv;
+    pr.tw_s = FWD ? tp.fwd_s : tp.inv_s;
+    const bool reduce_in = a.ks_ct != nullptr;
+    uint64_t *gout = a.polys + p * N;
+    const int logN = a.logN;
+    int done = 0;
+    bool first = true;
+    while (done < logN) {
+        const int s = logN - done < SM ? logN - done : SM;
+        const bool last = done + s == logN;
+        // forward: distances fall from N/2; inverse: they rise from 1
+        const int lu = FWD ? logN - done - s : done;
+        if (s == SM) {
+            ntt_pass<E, SM, FWD>(sa, gin, gout, reduce_in, N, logN, lu, first, last, pr);
+        } else if (s == 4) {
+            ntt_pass<E, (SM > 4 ? 4 : 1), FWD>(sa, gin, gout, reduce_in, N, logN, lu, first, last, pr);
+        } else if (s == 3) {
+            ntt_pass<E, (SM > 3 ? 3 : 1), FWD>(sa, gin, gout, reduce_in, N, logN, lu, first, last, pr);
+        } else if (s == 2) {
+            ntt_pass<E, 2, FWD>(sa, gin, gout, reduce_in, N, logN, lu, first, last, pr);
+        } else {
+            ntt_pass<E, 1, FWD>(sa, gin, gout, reduce_in, N, logN, lu, first, last, pr);
+        }
+        done += s;
+        first = false;
+    }
+}
+
+// Coefficients per thread for degree N: 16 up to N = 8192, 32 above
+// (MODPP_NTT_E = 8, 16 or 32 overrides where the thread count allows).
+int ntt_e_for(int N) {
+    static const int forced = [] {
+        const char *v = std::getenv("MODPP_NTT_E");
+        return v ? std::atoi(v) : 0;
+    }();
+    int e = (forced == 8 || forced == 16 || forced == 32) ? forced : (N <= 8192 ? 16 : 32);
+    if (e == 8 && N / 8 > NttShape<8>::kMaxThreads) e = 16;
+    if (e == 16 && N / 16 > NttShape<16>::kMaxThreads) e = 32;
+    return e;
+}
+
+template <int E, bool FWD>
+cudaError_t launch_e(const NttFastArgs &a, int64_t npolys, cudaStream_t s) {
+    const int threads = a.N / E;
+    const size_t smem = static_cast<size_t>(a.N + a.N / 32) * sizeof(uint64_t);
+    cudaError_t e = cudaFuncSetAttribute(ntt_e_kernel<E, FWD>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         static_cast<int>(smem));
+    if (e != cudaSuccess) return e;
+    ntt_e_kernel<E, FWD><<<static_cast<unsigned>(npolys), threads, smem, s>>>(a);
+    return cudaGetLastError();
+}
+
+template <bool FWD>
+cudaError_t launch_fast(const NttFastArgs &a, int64_t npolys, cudaStream_t s) {
+    switch (ntt_e_for(a.N)) {
+        case 8: return launch_e<8, FWD>(a, npolys, s);
+        case 16: return launch_e<16, FWD>(a, npolys, s);
+        default: return launch_e<32, FWD>(a, npolys, s);
+    }
+}
+
+}  // namespace
+
+bool ntt_fast_supported(int N) { return N >= 1024 && N <= 16384 && (N & (N - 1)) == 0; }
+
+cudaError_t launch_ntt_fast(uint64_t *polys, int64_t npolys, int N, int64_t inner, int nplanes,
+                            const NttPlane *tab, bool inverse, cudaStream_t s) {
+    if (npolys == 0) return cudaSuccess;
+    NttFastArgs a{};
+    a.polys = polys;
+    a.N = N;
+    a.logN = 0;
+    while ((1 << a.logN) < N) ++a.logN;
+    a.inner = inner;
+    a.nplanes = nplanes;
+    a.tab = tab;
+    return inverse ? launch_fast<false>(a, npolys, s) : launch_fast<true>(a, npolys, s);
+}
+
+cudaError_t launch_ks_digits_ntt(const uint64_t *ct, int64_t n, int L, int N, int64_t c0,
+                                 int64_t nb, const NttPlane *tab, uint64_t *D, cudaStream_t s) {
+    if (nb == 0) return cudaSuccess;
+    NttFastArgs a{};
+    a.polys = D;
+    a.N = N;
+    a.logN = 0;
+    while ((1 << a.logN) < N) ++a.logN;
+    a.inner = 1;
+    a.nplanes = L + 1;
+    a.tab = tab;
+    a.ks_ct = ct;
+    a.ks_n = n;
+    a.ks_c0 = c0;
+    a.ks_L = L;
+    return launch_fast<true>(a, nb * L * (L + 1), s);
+}
+
+}  // namespace modpp

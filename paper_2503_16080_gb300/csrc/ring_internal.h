@@ -21,14 +21,15 @@ struct NttPlane {
 
 // Per-ciphertext tables of a gather: every table has period `per` over the
 // batch (ciphertext c reads entry c mod per; source indices are relative to
-// the period block of c).  Null tables mean identity source, shift 0, ell 1.
+// the period block of c, and per is a power of two).  Null tables mean
+// identity source, shift 0, ell 1.
 // brev_bits > 0 takes the source index as the bit reversal of (c mod per)
 // over brev_bits bits instead of src; shift_src takes the shift equal to the
 // source index (the X^i ct_i of Alg. 4, step 1).
 struct GatherTables {
     const int *src;
     const int *shift;
-    const int *ell;
+    const int *ellinv;        // ell^-1 mod 2N of the automorphism, or null (ell = 1)
     const uint64_t *scale;    // per plane, or null
     const uint64_t *scale_s;
     int per;
@@ -36,8 +37,18 @@ struct GatherTables {
     int shift_src;
 };
 
+// Negacyclic NTT of npolys polynomials in place; polynomial p uses the
+// tables of plane (p / inner) % nplanes.  N >= 1024 runs the 16-per-thread
+// kernel of ntt_kernels.cu, smaller N the per-stage kernel.
 cudaError_t launch_ntt(uint64_t *polys, int64_t npolys, int N, int64_t inner, int nplanes,
                        const NttPlane *tab, bool inverse, cudaStream_t s);
+bool ntt_fast_supported(int N);
+cudaError_t launch_ntt_fast(uint64_t *polys, int64_t npolys, int N, int64_t inner, int nplanes,
+                            const NttPlane *tab, bool inverse, cudaStream_t s);
+// Digits of key switching fused with their forward NTT (N >= 1024):
+// D[c][i][k] = NTT_k(a_i of ciphertext c0 + c mod q_k), c < nb.
+cudaError_t launch_ks_digits_ntt(const uint64_t *ct, int64_t n, int L, int N, int64_t c0,
+                                 int64_t nb, const NttPlane *tab, uint64_t *D, cudaStream_t s);
 cudaError_t launch_to_montgomery(uint64_t *polys, int64_t npolys, int N, int64_t inner,
                                  int nplanes, const NttPlane *tab, cudaStream_t s);
 cudaError_t launch_ks_decompose(const uint64_t *ct, int64_t n, int L, int N, int64_t c0,

@@ -18,6 +18,8 @@
 // Montgomery reduction (P. Montgomery, Math. Comp. 1985).
 #include <cuda_runtime.h>
 
+#include <algorithm>
+
 #include "modarith.cuh"
 #include "ring_internal.h"
 
@@ -43,8 +45,9 @@ __device__ __forceinline__ uint64_t mont_mul(uint64_t a, uint64_t b, uint64_t q,
 }
 
 // ------------------------------------------------------------ NTT
-// One CTA transforms one polynomial of N <= 16384 coefficients in shared
-// memory.  Polynomial p uses the tables of plane (p / inner) % nplanes.
+// One CTA transforms one polynomial in shared memory, one barrier per stage
+// (the transform for N < 1024; larger N use ntt_kernels.cu).  Polynomial p
+// uses the tables of plane (p / inner) % nplanes.
 __global__ void __launch_bounds__(512) ntt_kernel(uint64_t *polys, int N, int logN, int64_t inner,
                                                   int nplanes, const NttPlane *__restrict__ tab,
                                                   int inverse) {
@@ -96,6 +99,7 @@ __global__ void __launch_bounds__(512) ntt_kernel(uint64_t *polys, int N, int lo
 cudaError_t launch_ntt(uint64_t *polys, int64_t npolys, int N, int64_t inner, int nplanes,
                        const NttPlane *tab, bool inverse, cudaStream_t s) {
     if (npolys == 0) return cudaSuccess;
+    if (ntt_fast_supported(N)) return launch_ntt_fast(polys, npolys, N, inner, nplanes, tab, inverse, s);
     int logN = 0;
     while ((1 << logN) < N) ++logN;
     const size_t smem = static_cast<size_t>(N) * 8;
@@ -150,77 +154,82 @@ __global__ void ks_decompose_kernel(const uint64_t *__restrict__ ct, int64_t n, 
 
 // U[c][part][k] = sum_i D[c][i][k] * key[kid(c)][i][part][k] in the evaluation
 // domain (keys in Montgomery form, digits plain: the product is plain).
+// nb * (L+1) < 2^31 and N = 2^logN.
 __global__ void ks_multacc_kernel(const uint64_t *__restrict__ D, const uint64_t *__restrict__ keys,
-                                  const int *__restrict__ kid, int kper, int L, int N, int64_t c0,
-                                  int64_t nb,
-                                  const NttPlane *__restrict__ tab, uint64_t *__restrict__ U) {
+                                  const int *__restrict__ kid, int kper, int L, int logN,
+                                  int64_t c0, int64_t nb, const NttPlane *__restrict__ tab,
+                                  uint64_t *__restrict__ U) {
     const int Lp = L + 1;
-    const int64_t key_stride = static_cast<int64_t>(L) * 2 * Lp * N;
-    const int64_t total = nb * Lp * static_cast<int64_t>(N);
+    const int N = 1 << logN;
+    const int64_t key_stride = static_cast<int64_t>(L) * 2 * Lp << logN;
+    const int64_t total = (nb * Lp) << logN;
     for (int64_t x = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; x < total;
          x += static_cast<int64_t>(gridDim.x) * blockDim.x) {
-        const int m = static_cast<int>(x % N);
-        const int64_t r = x / N;
-        const int k = static_cast<int>(r % Lp);
-        const int64_t c = r / Lp;
-        const uint64_t q = tab[k].q, qinv = tab[k].qinv_neg;
+        const int m = static_cast<int>(x) & (N - 1);
+        const int r = static_cast<int>(x >> logN);
+        const int k = r % Lp;
+        const int c = r / Lp;
         const int kc = kid[(c0 + c) % kper];
         if (kc < 0) continue;
-        const uint64_t *key = keys + static_cast<int64_t>(kc) * key_stride;
+        const uint64_t q = tab[k].q, qinv = tab[k].qinv_neg;
+        const uint64_t *key = keys + kc * key_stride + (static_cast<int64_t>(k) << logN) + m;
+        const uint64_t *d = D + ((static_cast<int64_t>(c) * L * Lp + k) << logN) + m;
+        const int64_t dstep = static_cast<int64_t>(Lp) << logN;     // next digit i
+        const int64_t kstep = static_cast<int64_t>(2 * Lp) << logN; // next key digit i
+        const int64_t kpart = static_cast<int64_t>(Lp) << logN;     // part 1 of a key digit
         uint64_t u0 = 0, u1 = 0;
         for (int i = 0; i < L; ++i) {
-            const uint64_t d = D[((c * L + i) * Lp + k) * N + m];
-            const uint64_t ka = key[((static_cast<int64_t>(i) * 2 + 0) * Lp + k) * N + m];
-            const uint64_t kb = key[((static_cast<int64_t>(i) * 2 + 1) * Lp + k) * N + m];
-            u0 = add_mod(u0, mont_mul(d, ka, q, qinv), q);
-            u1 = add_mod(u1, mont_mul(d, kb, q, qinv), q);
+            const uint64_t di = d[i * dstep];
+            u0 = add_mod(u0, mont_mul(di, key[i * kstep], q, qinv), q);
+            u1 = add_mod(u1, mont_mul(di, key[i * kstep + kpart], q, qinv), q);
         }
-        U[((c * 2 + 0) * Lp + k) * N + m] = u0;
-        U[((c * 2 + 1) * Lp + k) * N + m] = u1;
+        uint64_t *u = U + ((static_cast<int64_t>(c) * 2 * Lp + k) << logN) + m;
+        u[0] = u0;
+        u[kpart] = u1;
     }
 }
 
 // ModDown by P and accumulation: out_a = round(U_a / P), out_b = b + round(U_b / P),
 // with round(x / P) = (x_k - r) * P^-1 mod q_k, r = [x]_P centred.
 // Ciphertexts with kid < 0 are copied unchanged.  With b_zero the input
-// b-part is taken as 0 (Relin(D0, 0) in Alg. 8).
+// b-part is taken as 0 (Relin(D0, 0) in Alg. 8).  blockIdx.y = part * L + k.
 __global__ void ks_moddown_kernel(const uint64_t *__restrict__ U, const uint64_t *__restrict__ ct,
-                                  int64_t n, int L, int N, int64_t c0, int64_t nb,
+                                  int64_t n, int L, int logN, int64_t c0, int64_t nb,
                                   const int *__restrict__ kid, int kper, int b_zero,
                                   const NttPlane *__restrict__ tab,
                                   const uint64_t *__restrict__ pinv,
                                   const uint64_t *__restrict__ pinv_s, uint64_t *__restrict__ out,
                                   int64_t n_out) {
     const int Lp = L + 1;
+    const int N = 1 << logN;
+    const int part = blockIdx.y / L;
+    const int k = blockIdx.y % L;
     const uint64_t P = tab[L].q;
-    const int64_t total = nb * 2 * L * static_cast<int64_t>(N);
+    const uint64_t q = tab[k].q, mu = tab[k].mu, pv = pinv[k], pvs = pinv_s[k];
+    const uint64_t *ctp = ct + ((static_cast<int64_t>(part) * L + k) * n + c0) * N;
+    uint64_t *outp = out + ((static_cast<int64_t>(part) * L + k) * n_out + c0) * N;
+    const int64_t total = nb << logN;
     for (int64_t x = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; x < total;
          x += static_cast<int64_t>(gridDim.x) * blockDim.x) {
-        const int m = static_cast<int>(x % N);
-        int64_t r = x / N;
-        const int k = static_cast<int>(r % L);
-        r /= L;
-        const int part = static_cast<int>(r % 2);
-        const int64_t c = r / 2;
-        const int64_t g = ((static_cast<int64_t>(part) * L + k) * n + c0 + c) * N + m;
-        const int64_t go = ((static_cast<int64_t>(part) * L + k) * n_out + c0 + c) * N + m;
+        const int m = static_cast<int>(x) & (N - 1);
+        const int64_t c = x >> logN;
         if (kid[(c0 + c) % kper] < 0) {
-            out[go] = (part == 1 && b_zero) ? 0 : ct[g];
+            outp[x] = (part == 1 && b_zero) ? 0 : ctp[x];
             continue;
         }
-        const uint64_t q = tab[k].q;
-        const uint64_t up = U[((c * 2 + part) * Lp + L) * N + m];
-        const uint64_t uk = U[((c * 2 + part) * Lp + k) * N + m];
+        const int64_t ub = ((c * 2 + part) * Lp) << logN;
+        const uint64_t up = U[ub + (static_cast<int64_t>(L) << logN) + m];
+        const uint64_t uk = U[ub + (static_cast<int64_t>(k) << logN) + m];
         // centred r: up - P if up > P/2; lift r into [0, q)
         uint64_t rq;
         if (up > P / 2) {
-            const uint64_t mag = barrett_u64(P - up, q, tab[k].mu);
+            const uint64_t mag = barrett_u64(P - up, q, mu);
             rq = mag == 0 ? 0 : q - mag;
         } else {
-            rq = barrett_u64(up, q, tab[k].mu);
+            rq = barrett_u64(up, q, mu);
         }
-        const uint64_t v = shoup_mulmod(sub_mod(uk, rq, q), pinv[k], pinv_s[k], q);
-        out[go] = (part == 0 || b_zero) ? v : add_mod(ct[g], v, q);
+        const uint64_t v = shoup_mulmod(sub_mod(uk, rq, q), pv, pvs, q);
+        outp[x] = (part == 0 || b_zero) ? v : add_mod(ctp[x], v, q);
     }
 }
 
@@ -234,7 +243,11 @@ cudaError_t launch_ks_multacc(const uint64_t *D, const uint64_t *keys, const int
                               int L, int N, int64_t c0, int64_t nb, const NttPlane *tab,
                               uint64_t *U, cudaStream_t s) {
     if (nb == 0) return cudaSuccess;
-    ks_multacc_kernel<<<152 * 16, 256, 0, s>>>(D, keys, kid, kper, L, N, c0, nb, tab, U);
+    const int logN = 31 - __builtin_clz(N);
+    const int64_t total = nb * (L + 1) * N;
+    const int64_t bx = std::min<int64_t>((total + 255) / 256, 152 * 16);
+    ks_multacc_kernel<<<static_cast<unsigned>(bx), 256, 0, s>>>(D, keys, kid, kper, L, logN, c0, nb,
+                                                                tab, U);
     return cudaGetLastError();
 }
 cudaError_t launch_ks_moddown(const uint64_t *U, const uint64_t *ct, int64_t n, int L, int N,
@@ -242,64 +255,68 @@ cudaError_t launch_ks_moddown(const uint64_t *U, const uint64_t *ct, int64_t n, 
                               const NttPlane *tab, const uint64_t *pinv, const uint64_t *pinv_s,
                               uint64_t *out, int64_t n_out, cudaStream_t s) {
     if (nb == 0) return cudaSuccess;
-    ks_moddown_kernel<<<152 * 16, 256, 0, s>>>(U, ct, n, L, N, c0, nb, kid, kper, b_zero, tab, pinv,
-                                               pinv_s, out, n_out);
+    const int logN = 31 - __builtin_clz(N);
+    const int64_t bx = std::min<int64_t>((nb * N + 255) / 256, 152 * 8);
+    ks_moddown_kernel<<<dim3(static_cast<unsigned>(bx), 2 * L), 256, 0, s>>>(
+        U, ct, n, L, logN, c0, nb, kid, kper, b_zero, tab, pinv, pinv_s, out, n_out);
     return cudaGetLastError();
 }
 
 // ------------------------------------------------------------ gathers, Tweak
+// Batches have power-of-two N (and, for Tweak, n and the table period), so
+// every index below is a shift or a mask; blockIdx.y selects the (part,
+// prime) plane, 2L of them.
+__device__ __forceinline__ int ilog2(int x) { return 31 - __clz(x); }
+
 // out[c] = scale * X^shift(c) * sigma_ell(c)(in[src(c)]) for every part and
 // plane; the tables repeat with period t.per (ciphertext c reads entry c mod
 // per, and src is relative to the block of `per` ciphertexts holding c).
 // X^t multiplies by a signed rotation (X^N = -1); sigma_ell maps X^i to
 // X^(i*ell mod 2N).  One thread per output coefficient: it reads input
-// coefficient i = (pos - shift) * ell^-1 mod 2N, ell^-1 taken mod 2N.
+// coefficient i = (pos - shift) * ell^-1 mod 2N.
 __global__ void ct_gather_kernel(const uint64_t *__restrict__ in, uint64_t *__restrict__ out,
-                                 int64_t n, int L, int N, GatherTables t,
+                                 int64_t n, int L, int logN, GatherTables t,
                                  const NttPlane *__restrict__ tab) {
-    const int64_t total = 2 * static_cast<int64_t>(L) * n * N;
-    const int twoN = 2 * N;
+    const int r = blockIdx.y;  // part * L + plane
+    const int plane = r % L;
+    const uint64_t q = tab[plane].q;
+    const int N = 1 << logN;
+    const int twoN_mask = 2 * N - 1;
+    const int per_mask = t.per - 1;
+    uint64_t sc_w = 0, sc_ws = 0;
+    if (t.scale) {
+        sc_w = t.scale[plane];
+        sc_ws = t.scale_s[plane];
+    }
+    const uint64_t *inp = in + static_cast<int64_t>(r) * n * N;
+    uint64_t *outp = out + static_cast<int64_t>(r) * n * N;
+    const int64_t total = n << logN;
     for (int64_t x = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; x < total;
          x += static_cast<int64_t>(gridDim.x) * blockDim.x) {
-        const int pos = static_cast<int>(x % N);  // output coefficient
-        int64_t r = x / N;
-        const int64_t c = r % n;                  // output ciphertext
-        r /= n;                                   // part * L + plane
-        const int plane = static_cast<int>(r % L);
-        const uint64_t q = tab[plane].q;
-        const int64_t ci = c % t.per;
-        const int64_t si = t.brev_bits > 0
-                               ? static_cast<int64_t>(__brev(static_cast<unsigned>(ci)) >>
-                                                      (32 - t.brev_bits))
-                               : (t.src ? t.src[ci] : ci);
-        const int64_t sc = (c - ci) + si;
-        const int64_t sh = t.shift_src ? si : (t.shift ? t.shift[ci] : 0);
-        // exponent e with X^e = X^pos * X^-shift, then through sigma_ell^-1
-        int64_t e = (pos - sh) % twoN;
-        if (e < 0) e += twoN;
-        if (t.ell) {
-            // inverse of an odd ell modulo 2^64 by Newton's iteration
-            // (each step doubles the number of correct low bits), then mod 2N
-            const uint64_t l = static_cast<uint64_t>(t.ell[ci]);
-            uint64_t y = l;  // correct to 3 bits for odd l
-            for (int k = 0; k < 5; ++k) y *= 2 - l * y;
-            e = static_cast<int64_t>((static_cast<uint64_t>(e) * (y & (twoN - 1))) & (twoN - 1));
-        }
-        bool neg = false;
-        if (e >= N) {
-            e -= N;
-            neg = true;
-        }
-        uint64_t v = in[(r * n + sc) * N + e];
-        if (t.scale) v = shoup_mulmod(v, t.scale[plane], t.scale_s[plane], q);
-        out[(r * n + c) * N + pos] = (neg && v != 0) ? q - v : v;
+        const int pos = static_cast<int>(x) & (N - 1);
+        const int64_t c = x >> logN;
+        const int ci = static_cast<int>(c) & per_mask;
+        const int si = t.brev_bits > 0 ? static_cast<int>(__brev(static_cast<unsigned>(ci)) >>
+                                                          (32 - t.brev_bits))
+                                       : (t.src ? t.src[ci] : ci);
+        const int sh = t.shift_src ? si : (t.shift ? t.shift[ci] : 0);
+        int e = (pos - sh) & twoN_mask;
+        if (t.ellinv) e = static_cast<int>((static_cast<int64_t>(e) * t.ellinv[ci]) & twoN_mask);
+        const bool neg = e >= N;
+        e &= N - 1;
+        uint64_t v = inp[((c - ci + si) << logN) + e];
+        if (t.scale) v = shoup_mulmod(v, sc_w, sc_ws, q);
+        outp[x] = (neg && v != 0) ? q - v : v;
     }
 }
 
 cudaError_t launch_ct_gather(const uint64_t *in, uint64_t *out, int64_t n, int L, int N,
                              const GatherTables &t, const NttPlane *tab, cudaStream_t s) {
     if (n == 0) return cudaSuccess;
-    ct_gather_kernel<<<152 * 16, 256, 0, s>>>(in, out, n, L, N, t, tab);
+    const int64_t per_plane = n * N;
+    const int64_t bx = std::min<int64_t>((per_plane + 255) / 256, 152 * 8);
+    ct_gather_kernel<<<dim3(static_cast<unsigned>(bx), 2 * L), 256, 0, s>>>(in, out, n, L,
+                                                                            31 - __builtin_clz(N), t, tab);
     return cudaGetLastError();
 }
 
@@ -307,40 +324,87 @@ cudaError_t launch_ct_gather(const uint64_t *in, uint64_t *out, int64_t n, int L
 // for pairs (lo, hi = lo + half) inside blocks of 2*half,
 //   out_lo = x_lo + X^t x_hi,  out_hi = x_lo - X^t x_hi,  t = (lo mod half) * N / half.
 // Input ciphertexts must be in bit-reversed order before the first stage.
+// Each thread takes two neighbouring coefficients with 16-byte accesses; t is
+// even whenever half < N, so the rotated read stays 16-byte aligned.
 __global__ void tweak_stage_kernel(const uint64_t *__restrict__ in, uint64_t *__restrict__ out,
-                                   int64_t n, int L, int N, int64_t half,
+                                   int64_t n, int L, int logN, int lhalf,
                                    const NttPlane *__restrict__ tab) {
-    const int64_t pairs = n / 2;
-    const int64_t total = 2 * static_cast<int64_t>(L) * pairs * N;
-    for (int64_t x = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; x < total;
-         x += static_cast<int64_t>(gridDim.x) * blockDim.x) {
-        const int m = static_cast<int>(x % N);
-        int64_t r = x / N;
-        const int64_t pr = r % pairs;
-        r /= pairs;                               // part * L + plane
-        const uint64_t q = tab[r % L].q;
-        const int64_t jj = pr % half;
-        const int64_t lo = (pr / half) * 2 * half + jj;
-        const int64_t hi = lo + half;
-        const int t = static_cast<int>(jj * (N / half));
-        const uint64_t a = in[(r * n + lo) * N + m];
-        int src = m - t;
-        uint64_t y;
-        if (src >= 0) {
-            y = in[(r * n + hi) * N + src];
-        } else {
-            const uint64_t w = in[(r * n + hi) * N + src + N];
-            y = w == 0 ? 0 : q - w;
+    const int r = blockIdx.y;  // part * L + plane
+    const uint64_t q = tab[r % L].q;
+    const int N = 1 << logN;
+    const uint64_t *inp = in + static_cast<int64_t>(r) * n * N;
+    uint64_t *outp = out + static_cast<int64_t>(r) * n * N;
+    const int64_t total = (n >> 1) << (logN - 1);  // pairs x coefficient pairs
+    const int64_t half_mask = (int64_t(1) << lhalf) - 1;
+    for (int64_t w = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; w < total;
+         w += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        const int m = (static_cast<int>(w) << 1) & (N - 1);
+        const int64_t pr = w >> (logN - 1);
+        const int64_t jj = pr & half_mask;
+        const int64_t lo = ((pr >> lhalf) << (lhalf + 1)) + jj;
+        const int64_t hi = lo + (int64_t(1) << lhalf);
+        const int tt = static_cast<int>(jj << (logN - lhalf));
+        const ulonglong2 a = *reinterpret_cast<const ulonglong2 *>(inp + (lo << logN) + m);
+        int src = m - tt;
+        ulonglong2 y = *reinterpret_cast<const ulonglong2 *>(inp + (hi << logN) + (src & (N - 1)));
+        if (src < 0) {
+            y.x = y.x == 0 ? 0 : q - y.x;
+            y.y = y.y == 0 ? 0 : q - y.y;
         }
-        out[(r * n + lo) * N + m] = add_mod(a, y, q);
-        out[(r * n + hi) * N + m] = sub_mod(a, y, q);
+        ulonglong2 o0, o1;
+        o0.x = add_mod(a.x, y.x, q);
+        o0.y = add_mod(a.y, y.y, q);
+        o1.x = sub_mod(a.x, y.x, q);
+        o1.y = sub_mod(a.y, y.y, q);
+        *reinterpret_cast<ulonglong2 *>(outp + (lo << logN) + m) = o0;
+        *reinterpret_cast<ulonglong2 *>(outp + (hi << logN) + m) = o1;
+    }
+}
+
+// The same stage for half = N (n = 2N), where t = jj is odd for odd jj: one
+// coefficient per thread.
+__global__ void tweak_stage_scalar_kernel(const uint64_t *__restrict__ in,
+                                          uint64_t *__restrict__ out, int64_t n, int L, int logN,
+                                          int lhalf, const NttPlane *__restrict__ tab) {
+    const int r = blockIdx.y;
+    const uint64_t q = tab[r % L].q;
+    const int N = 1 << logN;
+    const uint64_t *inp = in + static_cast<int64_t>(r) * n * N;
+    uint64_t *outp = out + static_cast<int64_t>(r) * n * N;
+    const int64_t total = (n >> 1) << logN;
+    const int64_t half_mask = (int64_t(1) << lhalf) - 1;
+    for (int64_t w = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; w < total;
+         w += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        const int m = static_cast<int>(w) & (N - 1);
+        const int64_t pr = w >> logN;
+        const int64_t jj = pr & half_mask;
+        const int64_t lo = ((pr >> lhalf) << (lhalf + 1)) + jj;
+        const int64_t hi = lo + (int64_t(1) << lhalf);
+        const int tt = static_cast<int>((jj << logN) >> lhalf);
+        const uint64_t a = inp[(lo << logN) + m];
+        const int src = m - tt;
+        uint64_t y = inp[(hi << logN) + (src & (N - 1))];
+        if (src < 0) y = y == 0 ? 0 : q - y;
+        outp[(lo << logN) + m] = add_mod(a, y, q);
+        outp[(hi << logN) + m] = sub_mod(a, y, q);
     }
 }
 
 cudaError_t launch_tweak_stage(const uint64_t *in, uint64_t *out, int64_t n, int L, int N,
                                int64_t half, const NttPlane *tab, cudaStream_t s) {
     if (n < 2) return cudaSuccess;
-    tweak_stage_kernel<<<152 * 16, 256, 0, s>>>(in, out, n, L, N, half, tab);
+    const int logN = 31 - __builtin_clz(N);
+    const int lhalf = 63 - __builtin_clzll(static_cast<unsigned long long>(half));
+    const int64_t per_plane = (n >> 1) * N;
+    if (lhalf < logN && N >= 2) {
+        const int64_t bx = std::min<int64_t>((per_plane / 2 + 255) / 256, 152 * 8);
+        tweak_stage_kernel<<<dim3(static_cast<unsigned>(bx), 2 * L), 256, 0, s>>>(in, out, n, L,
+                                                                                   logN, lhalf, tab);
+    } else {
+        const int64_t bx = std::min<int64_t>((per_plane + 255) / 256, 152 * 8);
+        tweak_stage_scalar_kernel<<<dim3(static_cast<unsigned>(bx), 2 * L), 256, 0, s>>>(
+            in, out, n, L, logN, lhalf, tab);
+    }
     return cudaGetLastError();
 }
 
