@@ -44,6 +44,12 @@ WORKLOAD = ("PC-MM n=4096: U 4096x4096 int8 (N(0,1)*2^5) x row-RLWE ciphertext m
             "4096 cts of degree 4096, L=3 primes of 50 bits, a- and b-part (6 Mod-PP-MM planes)")
 
 
+# DRAM bytes (read + write) of one gemm_f16_kernel launch of this workload, from
+# one ncu capture of the current kernel (profiles/gemm_f16_pcmm_n4096_traffic.md):
+# 1267857920 read + 792423424 written.
+GEMM_TRAFFIC_N4096 = 1267857920 + 792423424
+
+
 def mod_ops_per_step() -> float:
     return 2.0 * D * K * N * 2 * NPRIMES
 
@@ -262,6 +268,9 @@ def run_ours(args):
         # Algorithmic tensor FLOPs of one GEMM launch: each of the `digits`
         # digit planes of every (prime, part) plane is one d x k x n product.
         gemm_flops = 2.0 * D * K * N * planes * digits
+        # Algorithmic bytes of one launch: the f16 digit matrix and U16 read
+        # once, the u64 outputs written once.
+        gemm_bytes = (planes * K * digits * N * 2 + D * kp * 2 + planes * D * N * 8)
         gemm_avg_s = gemm_ms / max(gemm_n, 1) * 1e-3
         achieved = gemm_flops / gemm_avg_s / 1e12
         peak = peaks["bf16_tflops_sustained"]
@@ -341,7 +350,9 @@ def run_ours(args):
             "roofline": {"kernel": "gemm_f16_kernel", "bound": "tensor", "achieved": achieved,
                          "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                          "peak_source": f"{peak_src} bf16 dense sustained (f16 same rate)",
-                         "traffic": None, "avg_launch_ms": gemm_avg_s * 1e3,
+                         "traffic": GEMM_TRAFFIC_N4096 if (D, K, N) == (4096, 4096, 4096) else None,
+                         "traffic_algorithmic": gemm_bytes,
+                         "avg_launch_ms": gemm_avg_s * 1e3,
                          "flops_per_launch": gemm_flops},
             "split_kernel": {"avg_launch_ms": split_ms / max(split_n, 1),
                              "achieved_gbs": split_gbs, "peak_gbs": peaks["hbm_gbs"],
