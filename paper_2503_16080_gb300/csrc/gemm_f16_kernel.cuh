@@ -120,15 +120,9 @@ __device__ __forceinline__ TileJob tile_job(int tile, const CUtensorMap *tmU,
         j.by = (plane * p.n_blocks + j.nb) * L * NC;
         j.Lp = L;
     } else {
-        // Planes are stored in tile order: find the last plane starting at or
-        // before `tile` (binary search over tile_begin).
-        int lo = 0, hi = p.num_gplanes - 1;
-        while (lo < hi) {
-            const int mid = (lo + hi + 1) >> 1;
-            if (p.gplanes[mid].tile_begin <= tile) lo = mid;
-            else hi = mid - 1;
-        }
-        const GroupPlane &g = p.gplanes[lo];
+        // One table entry per tile names its plane: one dependent load, so
+        // short tiles do not wait on a search through the plane table.
+        const GroupPlane &g = p.gplanes[p.tile_plane[tile]];
         band_order(tile - g.tile_begin, g.m_blocks, g.n_blocks, g.band_m, j.mb, j.nb);
         j.tmU = g.tmU;
         j.tmD = g.tmD;

@@ -52,49 +52,60 @@ struct GroupSplitJob {
     int64_t block_begin;
 };
 
-constexpr int kUElemsPerBlock = 2048;
+// U elements per block of the U -> f16 pass: 8 per thread and step, 4 steps.
+constexpr int kUElemsPerBlock = 8 * 256 * 4;
 
-template <typename Job>
-__device__ __forceinline__ int find_job(const Job *jobs, int njobs, int64_t block) {
-    int lo = 0, hi = njobs - 1;
-    while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (jobs[mid].block_begin <= block) lo = mid;
-        else hi = mid - 1;
+// Each block of the two pre-passes finds its job in a table with one entry
+// per block (written by the plan), not by a search over the job list.
+__global__ void __launch_bounds__(256) group_u_to_f16_kernel(const GroupUJob *jobs,
+                                                             const int *block_job) {
+    const GroupUJob j = jobs[block_job[blockIdx.x]];
+    const int groups = j.kp / 8;  // kp is a multiple of 8
+    const int64_t total = static_cast<int64_t>(j.d) * groups;
+    const int64_t g0 = (blockIdx.x - j.block_begin) * static_cast<int64_t>(kUElemsPerBlock / 8);
+    for (int64_t i = g0 + threadIdx.x; i < g0 + kUElemsPerBlock / 8 && i < total; i += 256) {
+        const int64_t r = i / groups;
+        const int t0 = static_cast<int>(i - r * groups) * 8;
+        const int8_t *src = j.U + r * j.ldu + t0;
+        __align__(16) __half h[8];
+        if (t0 + 8 <= j.k && (reinterpret_cast<uintptr_t>(src) & 7u) == 0) {
+            const int2 w = *reinterpret_cast<const int2 *>(src);
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                const int word = q < 4 ? w.x : w.y;
+                h[q] = __int2half_rn(static_cast<int8_t>((word >> (8 * (q & 3))) & 0xff));
+            }
+        } else {
+#pragma unroll
+            for (int q = 0; q < 8; ++q)
+                h[q] = __int2half_rn(t0 + q < j.k ? static_cast<int>(src[q]) : 0);
+        }
+        *reinterpret_cast<uint4 *>(j.U16 + r * j.kp + t0) = *reinterpret_cast<const uint4 *>(h);
     }
-    return lo;
 }
 
-__global__ void __launch_bounds__(256) group_u_to_f16_kernel(const GroupUJob *jobs, int njobs) {
-    const GroupUJob j = jobs[find_job(jobs, njobs, blockIdx.x)];
-    const int64_t total = static_cast<int64_t>(j.d) * j.kp;
-    const int64_t e0 = (blockIdx.x - j.block_begin) * static_cast<int64_t>(kUElemsPerBlock);
-    for (int64_t e = e0 + threadIdx.x; e < e0 + kUElemsPerBlock && e < total; e += 256) {
-        const int64_t r = e / j.kp;
-        const int t = static_cast<int>(e - r * j.kp);
-        j.U16[e] = __int2half_rn(t < j.k ? static_cast<int>(j.U[r * j.ldu + t]) : 0);
-    }
-}
-
+// Every plane of a class has exactly L = LMAX digits.
 template <int LMAX, int DB, int NC>
-__global__ void __launch_bounds__(256) group_split_kernel(const GroupSplitJob *jobs, int njobs) {
+__global__ void __launch_bounds__(256) group_split_kernel(const GroupSplitJob *jobs,
+                                                          const int *block_job) {
     __shared__ __align__(16) __half tile[LMAX * NC * kSplitRow];
-    const GroupSplitJob j = jobs[find_job(jobs, njobs, blockIdx.x)];
+    const GroupSplitJob j = jobs[block_job[blockIdx.x]];
     const int64_t lb = blockIdx.x - j.block_begin;
     const int tb = static_cast<int>(lb % j.t_blocks);
     const int nb = static_cast<int>(lb / j.t_blocks);
-    __half *Dblock = j.D + static_cast<int64_t>(nb) * j.Lp * NC * static_cast<int64_t>(j.kp);
-    split_digit_tile<LMAX, DB, NC>(tile, j.A, j.lda, j.q, j.thresh, j.k, j.n, j.kp, j.Lp,
+    __half *Dblock = j.D + static_cast<int64_t>(nb) * LMAX * NC * static_cast<int64_t>(j.kp);
+    split_digit_tile<LMAX, DB, NC>(tile, j.A, j.lda, j.q, j.thresh, j.k, j.n, j.kp, LMAX,
                                    tb * kSplitT, nb * NC, Dblock);
 }
 
 template <int LMAX, int DB>
-static cudaError_t launch_group_kernels(const GroupSplitJob *sjobs, int n_sjobs, int64_t s_blocks,
-                                        const GemmParams &gp, int num_sms, cudaStream_t st) {
+static cudaError_t launch_group_kernels(const GroupSplitJob *sjobs, const int *sblock_job,
+                                        int64_t s_blocks, const GemmParams &gp, int num_sms,
+                                        cudaStream_t st) {
     constexpr int NC = tile_cols(LMAX);
     if (s_blocks > 0) {
-        group_split_kernel<LMAX, DB, NC><<<static_cast<unsigned>(s_blocks), 256, 0, st>>>(sjobs,
-                                                                                     n_sjobs);
+        group_split_kernel<LMAX, DB, NC><<<static_cast<unsigned>(s_blocks), 256, 0, st>>>(
+            sjobs, sblock_job);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
@@ -104,12 +115,12 @@ static cudaError_t launch_group_kernels(const GroupSplitJob *sjobs, int n_sjobs,
 }
 
 template <int DB>
-static cudaError_t launch_group_db(int lmax, const GroupSplitJob *sjobs, int n_sjobs,
+static cudaError_t launch_group_db(int lmax, const GroupSplitJob *sjobs, const int *sblock_job,
                                    int64_t s_blocks, const GemmParams &gp, int num_sms,
                                    cudaStream_t st) {
     switch (lmax) {
 #define MODPP_CASE(LL) \
-    case LL: return launch_group_kernels<LL, DB>(sjobs, n_sjobs, s_blocks, gp, num_sms, st);
+    case LL: return launch_group_kernels<LL, DB>(sjobs, sblock_job, s_blocks, gp, num_sms, st);
         MODPP_CASE(1)
         MODPP_CASE(2)
         MODPP_CASE(3)
@@ -144,7 +155,10 @@ struct GroupLayout {
     std::vector<int64_t> kp, n_blocks;   // per problem
     std::vector<size_t> off_u16, off_d;  // per problem
     int num_planes = 0;
-    size_t off_planes = 0, off_ujobs = 0, off_sjobs = 0, off_maps = 0, total = 0;
+    int64_t num_tiles = 0;               // GEMM tiles over all classes
+    int64_t u_blocks = 0, s_blocks = 0;  // pre-pass blocks over all problems / classes
+    size_t off_planes = 0, off_ujobs = 0, off_sjobs = 0, off_tiles = 0, off_ublk = 0, off_sblk = 0,
+           off_maps = 0, total = 0;
 };
 
 GroupLayout group_layout(const std::vector<ProblemCopy> &probs, int b) {
@@ -158,6 +172,15 @@ GroupLayout group_layout(const std::vector<ProblemCopy> &probs, int b) {
         g.num_planes += pc.p.P;
     }
     for (int L : g.Lp) g.nc.push_back(tile_cols(L));
+    for (size_t i = 0; i < probs.size(); ++i) {
+        const modpp_problem &p = probs[i].p;
+        if (p.d == 0 || p.n == 0 || p.k == 0) continue;
+        const int64_t kp = (p.k + 7) / 8 * 8;
+        const int64_t nbk = (p.n + g.nc[i] - 1) / g.nc[i];
+        g.num_tiles += static_cast<int64_t>(p.P) * ((p.d + kBM - 1) / kBM) * nbk;
+        g.u_blocks += (p.d * kp + kUElemsPerBlock - 1) / kUElemsPerBlock;
+        g.s_blocks += static_cast<int64_t>(p.P) * ((kp + kSplitT - 1) / kSplitT) * nbk;
+    }
     size_t off = 256;  // status word
     g.off_planes = off;
     off = galign(off + sizeof(GroupPlane) * g.num_planes);
@@ -165,6 +188,12 @@ GroupLayout group_layout(const std::vector<ProblemCopy> &probs, int b) {
     off = galign(off + sizeof(GroupUJob) * probs.size());
     g.off_sjobs = off;
     off = galign(off + sizeof(GroupSplitJob) * g.num_planes);
+    g.off_tiles = off;  // plane of every tile, class-relative (one int per tile)
+    off = galign(off + sizeof(int) * static_cast<size_t>(g.num_tiles));
+    g.off_ublk = off;   // U job of every U -> f16 block
+    off = galign(off + sizeof(int) * static_cast<size_t>(g.u_blocks));
+    g.off_sblk = off;   // split job of every split block, class-relative
+    off = galign(off + sizeof(int) * static_cast<size_t>(g.s_blocks));
     g.off_maps = off;
     off = galign(off + 2 * sizeof(CUtensorMap) * probs.size());
     for (size_t i = 0; i < probs.size(); ++i) {
@@ -297,6 +326,8 @@ struct GroupClass {
     int L = 0;
     int plane_begin = 0, plane_count = 0;
     int tiles = 0;
+    int64_t tile_base = 0;  // first entry of the class in the tile -> plane table
+    int64_t s_block_base = 0;  // first entry of the class in the split block -> job table
     int sjob_begin = 0, sjob_count = 0;
     int64_t s_blocks = 0;
 };
@@ -334,6 +365,10 @@ int plan_build(modpp_group_plan *pl, int b, cudaStream_t st) {
     auto *ujobs = reinterpret_cast<GroupUJob *>(h + g.off_ujobs);
     auto *sjobs = reinterpret_cast<GroupSplitJob *>(h + g.off_sjobs);
     auto *maps = reinterpret_cast<CUtensorMap *>(h + g.off_maps);
+    auto *tile_plane = reinterpret_cast<int *>(h + g.off_tiles);
+    auto *ublock_job = reinterpret_cast<int *>(h + g.off_ublk);
+    auto *sblock_job = reinterpret_cast<int *>(h + g.off_sblk);
+    int64_t tile_base = 0, s_block_base = 0;
     const auto *dmaps = reinterpret_cast<const CUtensorMap *>(w + g.off_maps);
 
     // Classes of equal digit count; within a class the longest inner
@@ -356,10 +391,16 @@ int plan_build(modpp_group_plan *pl, int b, cudaStream_t st) {
         const int Lp = g.Lp[i];
         const int nc = g.nc[i];
         if (pl->classes.empty() || pl->classes.back().L != Lp) {
+            if (!pl->classes.empty()) {
+                tile_base += pl->classes.back().tiles;
+                s_block_base += pl->classes.back().s_blocks;
+            }
             GroupClass c;
             c.L = Lp;
             c.plane_begin = np;
             c.sjob_begin = ns;
+            c.tile_base = tile_base;
+            c.s_block_base = s_block_base;
             pl->classes.push_back(c);
             tiles = 0;
             sblocks = 0;
@@ -375,7 +416,12 @@ int plan_build(modpp_group_plan *pl, int b, cudaStream_t st) {
             return MODPP_ERR_CUDA;
         ujobs[nu] = GroupUJob{static_cast<const int8_t *>(p.U), p.ldu, static_cast<int>(p.d),
                               static_cast<int>(p.k), static_cast<int>(kp), U16, ublocks};
-        ublocks += (p.d * kp + kUElemsPerBlock - 1) / kUElemsPerBlock;
+        {
+            const int64_t nub = (p.d * kp + kUElemsPerBlock - 1) / kUElemsPerBlock;
+            if (ublocks + nub > g.u_blocks) return MODPP_ERR_UNSUPPORTED;
+            for (int64_t t = 0; t < nub; ++t) ublock_job[ublocks + t] = nu;
+            ublocks += nub;
+        }
         ++nu;
         const int m_blocks = static_cast<int>((p.d + kBM - 1) / kBM);
         const int tblocks = static_cast<int>((kp + kSplitT - 1) / kSplitT);
@@ -395,13 +441,23 @@ int plan_build(modpp_group_plan *pl, int b, cudaStream_t st) {
             gpl.Lp = Lp;
             gpl.dplane = j;
             gpl.tile_begin = static_cast<int>(tiles);
+            if (tile_base + tiles + static_cast<int64_t>(m_blocks) * nbk > g.num_tiles)
+                return MODPP_ERR_UNSUPPORTED;
+            for (int64_t t = 0; t < static_cast<int64_t>(m_blocks) * nbk; ++t)
+                tile_plane[tile_base + tiles + t] = np - cls.plane_begin;
             tiles += static_cast<int64_t>(m_blocks) * nbk;
             ++np;
             sjobs[ns] = GroupSplitJob{p.A + static_cast<int64_t>(j) * p.strideA, p.lda, q, thresh,
                                       static_cast<int>(p.k), static_cast<int>(p.n),
                                       static_cast<int>(kp), static_cast<int>(nbk), tblocks, Lp,
                                       D + static_cast<int64_t>(j) * nbk * Lp * nc * kp, sblocks};
-            sblocks += static_cast<int64_t>(tblocks) * nbk;
+            {
+                const int64_t nsb = static_cast<int64_t>(tblocks) * nbk;
+                if (s_block_base + sblocks + nsb > g.s_blocks) return MODPP_ERR_UNSUPPORTED;
+                for (int64_t t = 0; t < nsb; ++t)
+                    sblock_job[s_block_base + sblocks + t] = ns - cls.sjob_begin;
+                sblocks += nsb;
+            }
             ++ns;
         }
         if (tiles >= (int64_t(1) << 31) || sblocks >= (int64_t(1) << 31))
@@ -454,7 +510,8 @@ int plan_enqueue(modpp_group_plan *pl, cudaStream_t st) {
     }
     if (pl->u_blocks > 0) {
         group_u_to_f16_kernel<<<static_cast<unsigned>(pl->u_blocks), 256, 0, st>>>(
-            reinterpret_cast<const GroupUJob *>(w + g.off_ujobs), pl->n_ujobs);
+            reinterpret_cast<const GroupUJob *>(w + g.off_ujobs),
+            reinterpret_cast<const int *>(w + g.off_ublk));
         if (cudaGetLastError() != cudaSuccess) return MODPP_ERR_CUDA;
     }
     const int sms = sms_of_current_device();
@@ -464,13 +521,15 @@ int plan_enqueue(modpp_group_plan *pl, cudaStream_t st) {
         GemmParams gp = pl->gp;
         gp.gplanes = pl->gp.gplanes + c.plane_begin;
         gp.num_gplanes = c.plane_count;
+        gp.tile_plane = reinterpret_cast<const int *>(w + g.off_tiles) + c.tile_base;
         gp.num_tiles = c.tiles;
         const GroupSplitJob *cj = sjobs + c.sjob_begin;
+        const int *sbj = reinterpret_cast<const int *>(w + g.off_sblk) + c.s_block_base;
         cudaError_t e;
         switch (g.b) {
-            case 8: e = launch_group_db<8>(c.L, cj, c.sjob_count, c.s_blocks, gp, sms, st); break;
-            case 9: e = launch_group_db<9>(c.L, cj, c.sjob_count, c.s_blocks, gp, sms, st); break;
-            case 10: e = launch_group_db<10>(c.L, cj, c.sjob_count, c.s_blocks, gp, sms, st); break;
+            case 8: e = launch_group_db<8>(c.L, cj, sbj, c.s_blocks, gp, sms, st); break;
+            case 9: e = launch_group_db<9>(c.L, cj, sbj, c.s_blocks, gp, sms, st); break;
+            case 10: e = launch_group_db<10>(c.L, cj, sbj, c.s_blocks, gp, sms, st); break;
             default: return MODPP_ERR_ARG;
         }
         if (e != cudaSuccess) return MODPP_ERR_CUDA;

@@ -78,6 +78,7 @@ struct GemmParams {
     uint64_t timeout_ns;
     const GroupPlane *gplanes;  // grouped launches only
     int num_gplanes;
+    const int *tile_plane;      // grouped: plane of every tile (index into gplanes)
     PlaneConst pc[kMaxPlanes];
 };
 
