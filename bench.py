@@ -582,12 +582,23 @@ def run_ccmm(args):
     step()
     stages = ring.cc_mm_stage_ms()
     gemm_ms, gemm_n = pkg.profile_read(pkg.KERNEL_GEMM)
+    pre_ms, pre_n = pkg.profile_read(pkg.KERNEL_SPLIT)
+    post_ms, post_n = pkg.profile_read(pkg.KERNEL_U16)
     pkg.profile_enable(False)
 
     peaks, peak_src = load_peaks()
-    LU = -(-(max(primes) - 1).bit_length() // 8)
-    LA = pkg.plan_info(Nr, primes[0])["digits"]
-    gemm_flops = 2.0 * (2 * Nr) * Nr * Nr * LA  # one launch: one 8-bit digit plane of U
+    crt_primes = pkg.wide_plan_info(Nr, primes)
+    if crt_primes:
+        # CRT form: one launch runs the R small-prime products of one
+        # (chain prime, right operand) pair.
+        products = crt_primes
+        form = {"form": "crt", "small_primes": crt_primes}
+    else:
+        LU = -(-(max(primes) - 1).bit_length() // 8)
+        LA = pkg.plan_info(Nr, primes[0])["digits"]
+        products = LA  # one launch: one 8-bit digit plane of U times LA digits
+        form = {"form": "digits", "u_digit_planes": LU, "a_digits": LA}
+    gemm_flops = 2.0 * (2 * Nr) * Nr * Nr * products
     g_avg = gemm_ms / max(gemm_n, 1)
     achieved = gemm_flops / (g_avg * 1e-3) / 1e12
     peak = peaks["bf16_tflops_sustained"]
@@ -676,7 +687,8 @@ def run_ccmm(args):
                          "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                          "peak_source": f"{peak_src} bf16 dense sustained (f16 same rate)",
                          "avg_launch_ms": g_avg, "launches_per_cc_mm": gemm_n,
-                         "u_digit_planes": LU, "a_digits": LA},
+                         "flops_per_launch": gemm_flops, **form},
+            "wide_passes_ms": {"gemm": gemm_ms, "residue_split": pre_ms, "crt_or_u16": post_ms},
             "fp64_matmul_ms": dgemm_ms, "slowdown_vs_fp64_matmul": ms / dgemm_ms,
             "e2e": {"value": e2e_ms, "unit": "ms per CC-MM", "h2d_bytes_per_step":
                     8 * (h1.numel() + h2.numel()), "d2h_bytes_per_step": 8 * ho.numel()},

@@ -149,6 +149,39 @@ int modpp_mm_wide(int64_t d, int64_t k, int64_t n, const uint64_t *U, int64_t ld
                   void *stream);
 
 /*
+ * Two wide products with the same left operand (the two products of Alg. 8,
+ * step 2): C1_j = U_j * A1_j and C2_j = U_j * A2_j mod q_j, with the layout
+ * conventions of modpp_mm_wide (A1, A2 share lda / strideA; C1, C2 share ldc
+ * / strideC) and its workspace.  In the CRT form U's residue planes are
+ * formed once per prime for both products.
+ */
+int modpp_mm_wide_pair(int64_t d, int64_t k, int64_t n, const uint64_t *U, int64_t ldu,
+                       int64_t strideU, const uint64_t *A1, const uint64_t *A2, int64_t lda,
+                       int64_t strideA, uint64_t *C1, uint64_t *C2, int64_t ldc, int64_t strideC,
+                       const uint64_t *primes_host, int P, void *ws, size_t ws_bytes,
+                       void *stream);
+
+/*
+ * How modpp_mm_wide forms its products.  Digit form: U_j in 8-bit digits
+ * times A_j in b-bit digits, LU x LA tensor-core products per prime.
+ * Multi-modular (CRT) form, the exact lifting variant of Strategy 3 (Sec.
+ * 6.1): both operands lifted to balanced integers and reduced modulo R small
+ * primes p < 256 with k ((p-1)/2)^2 < 2^24 and prod p >= 2.8 k ((q-1)/2)^2,
+ * one tensor-core product per small prime, then the Chinese remainder
+ * theorem modulo q_j.  Both are exact.
+ *   mode 0 (default): the CRT form when it needs at most 10/11 of the digit
+ *                     form's products, else digits;
+ *   mode 1: always digits;  mode 2: the CRT form whenever a prime set exists.
+ * Process-wide; returns MODPP_ERR_ARG for other modes.  Workspace queries
+ * made before a change do not apply after it.
+ */
+int modpp_set_wide_path(int mode);
+int modpp_get_wide_path(void);
+/* Small primes the wide product would use for inner dimension k and these
+ * chain primes (0 = digit form), under the current mode.  Host only. */
+int modpp_wide_plan_info(int64_t k, const uint64_t *primes_host, int P, int *crt_primes);
+
+/*
  * Workspace bytes for pc_mm / pc_mv with these sizes (0 for invalid arguments).
  */
 size_t pc_mm_workspace(int64_t d, int64_t kct, int64_t N, const uint64_t *primes_host, int P,

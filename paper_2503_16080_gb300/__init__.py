@@ -15,7 +15,7 @@ _API_NAMES = (
     "modpp_mm", "pc_mm", "pc_mv", "plan_info", "workspace_bytes", "last_status", "Path",
     "ModppError", "lib", "library_path", "profile_enable", "profile_read", "KERNEL_GEMM",
     "KERNEL_SPLIT", "KERNEL_U16", "set_digit_bits", "get_digit_bits", "GroupedPlan",
-    "modpp_mm_grouped", "modpp_mm_wide",
+    "modpp_mm_grouped", "modpp_mm_wide", "set_wide_path", "get_wide_path", "wide_plan_info",
 )
 _RING_NAMES = ("Ring",)
 

@@ -87,6 +87,9 @@ def lib() -> ctypes.CDLL:
         L.modpp_group_plan_destroy.restype = None
         L.modpp_set_digit_bits.argtypes = [I]
         L.modpp_get_digit_bits.restype = I
+        L.modpp_set_wide_path.argtypes = [I]
+        L.modpp_get_wide_path.restype = I
+        L.modpp_wide_plan_info.argtypes = [I64, P, I, P]
         L.modpp_profile_enable.argtypes = [I]
         L.modpp_profile_read.argtypes = [I, P, P]
         _lib = L
@@ -177,6 +180,25 @@ KERNEL_GEMM, KERNEL_SPLIT, KERNEL_U16 = 0, 1, 2
 def set_digit_bits(bits: int) -> None:
     """Digit width b in {8, 9, 10} of the f16 path (0 = default); process-wide."""
     _check(lib().modpp_set_digit_bits(int(bits)), "modpp_set_digit_bits")
+
+
+def set_wide_path(mode) -> None:
+    """Form of modpp_mm_wide's products: "auto" (0), "digits" (1) or "crt" (2)."""
+    m = {"auto": 0, "digits": 1, "crt": 2}.get(mode, mode)
+    _check(lib().modpp_set_wide_path(int(m)), "modpp_set_wide_path")
+
+
+def get_wide_path() -> int:
+    return int(lib().modpp_get_wide_path())
+
+
+def wide_plan_info(k: int, primes: Sequence[int]) -> int:
+    """Small primes of the CRT form for inner dimension k (0: digit form)."""
+    pr = _primes_arr(primes)
+    out = ctypes.c_int()
+    _check(lib().modpp_wide_plan_info(int(k), pr.ctypes.data, len(pr), ctypes.byref(out)),
+           "modpp_wide_plan_info")
+    return out.value
 
 
 def get_digit_bits() -> int:

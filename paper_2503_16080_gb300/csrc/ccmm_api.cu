@@ -555,11 +555,8 @@ int cc_mm(modpp_ring r, const uint64_t *ct1, const uint64_t *ct2, const uint64_t
     if (e != cudaSuccess) return MODPP_ERR_CUDA;
     const size_t wide_bytes = modpp_mm_wide_workspace(2 * N, N, N, r->primes.data(), L);
     void *wws = base + lay.wide;
-    rc = modpp_mm_wide(2 * N, N, N, ut, N, 2 * NN, rw, N, NN, x, N, 2 * NN, r->primes.data(), L,
-                       wws, wide_bytes, st);
-    if (rc) return rc;
-    rc = modpp_mm_wide(2 * N, N, N, ut, N, 2 * NN, rw + L * NN, N, NN, y, N, 2 * NN,
-                       r->primes.data(), L, wws, wide_bytes, st);
+    rc = modpp_mm_wide_pair(2 * N, N, N, ut, N, 2 * NN, rw, rw + L * NN, N, NN, x, y, N, 2 * NN,
+                            r->primes.data(), L, wws, wide_bytes, st);
     if (rc) return rc;
     mark(2);
     // Steps 3-4: Transpose((C00, 0)) and Transpose((C10, 0)) as one batch.

@@ -72,6 +72,7 @@ struct TileJob {
     int d, n;         // plane sizes (stores are bounded by them)
     int kb_total;     // inner dimension in 64-element blocks
     int by;           // first row of the tile's digits in the digit matrix
+    int uy;           // first row of the plane's U in the U map (per-plane U, mode 1)
     int Lp;           // digits of this plane
 };
 
@@ -118,6 +119,7 @@ __device__ __forceinline__ TileJob tile_job(int tile, const CUtensorMap *tmU,
         j.n = p.n;
         j.kb_total = p.kb_total;
         j.by = (plane * p.n_blocks + j.nb) * L * NC;
+        j.uy = p.u_per_plane ? plane * p.d : 0;
         j.Lp = L;
     } else {
         // One table entry per tile names its plane: one dependent load, so
@@ -131,12 +133,19 @@ __device__ __forceinline__ TileJob tile_job(int tile, const CUtensorMap *tmU,
         j.n = g.n;
         j.kb_total = g.kb_total;
         j.by = (g.dplane * g.n_blocks + j.nb) * g.Lp * NC;
+        j.uy = 0;
         j.Lp = g.Lp;
     }
     return j;
 }
 
-template <int L, int DB, int NC, bool GROUPED>
+// MODE 0: digit products recombined modulo q (above).  MODE 1: one small
+// prime per plane (L = 1): the plane's operands are residues modulo a prime
+// p < 256 in balanced form, the host guarantees |sum| < 2^24 over the whole
+// inner dimension (no chunks), and the epilogue stores the balanced residue
+// of each output modulo p as int8 (the multi-modular products of
+// rns_wide.cu).  Each plane then has its own U rows (p.u_per_plane).
+template <int L, int DB, int NC, bool GROUPED, int MODE = 0>
 __global__ void __launch_bounds__(kThreads, 1)
     gemm_f16_kernel(const __grid_constant__ CUtensorMap tmU_param,
                     const __grid_constant__ CUtensorMap tmD_param,
@@ -184,7 +193,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem_base = *tmem_slot;
-    constexpr int kChunkKB = chunk_k(DB) / kBK;
+    constexpr int kChunkKB = MODE == 1 ? (1 << 20) / kBK : chunk_k(DB) / kBK;
 
     if (warp == 0) {
         // ------------------------------------------------ TMA producer
@@ -202,7 +211,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                         last_map = j.tmD;
                     }
                 }
-                const int ay = j.mb * kBM;
+                const int ay = j.uy + j.mb * kBM;
                 const uint32_t bytes = Cfg::A_BYTES + static_cast<uint32_t>(j.Lp * NC * kBK * 2);
                 for (int kb = 0; kb < j.kb_total; ++kb, ++it) {
                     const int s = static_cast<int>(it % STAGES);
@@ -269,6 +278,59 @@ __global__ void __launch_bounds__(kThreads, 1)
     } else {
         // ------------------------------------------------ epilogue warps
         constexpr int NCH = NC / 2;          // columns per epilogue warp
+        if constexpr (MODE == 1) {
+            const int ew = warp - 2;
+            const int quarter = warp & 3;
+            const int half = ew >> 2;
+            const uint32_t lane_off = static_cast<uint32_t>(quarter * 32) << 16;
+            uint32_t g = 0;
+            for (int tile = blockIdx.x; tile < p.num_tiles; tile += gridDim.x, ++g) {
+                const TileJob j = tile_job<L, NC, GROUPED>(tile, &tmU_param, &tmD_param, p);
+                const uint32_t buf = g & 1u, use = g >> 1;
+                const bool got = mbar_wait_bounded(&tfull[buf], use & 1u, abort_flag, p.timeout_ns);
+                if (!__all_sync(0xffffffffu, got)) break;
+                tc_fence_after();
+                const uint32_t base = tmem_base + lane_off + buf * Cfg::ACC_STRIDE + half * NCH;
+                const PlaneConst &pc = *j.pc;
+                const int pr = static_cast<int>(pc.q);
+                const float pinv = __uint_as_float(static_cast<uint32_t>(pc.mu));
+                const int row = j.mb * kBM + quarter * 32 + lane;
+                const int col0 = j.nb * NC + half * NCH;
+                int8_t *out = reinterpret_cast<int8_t *>(pc.C) + static_cast<int64_t>(row) * pc.ldc +
+                              col0;
+                const bool vec = (reinterpret_cast<uintptr_t>(out) & 15u) == 0;
+#pragma unroll 1
+                for (int c0 = 0; c0 < NCH; c0 += 16) {
+                    uint32_t r[16];
+                    tmem_ld_cols<16>(base + c0, r);
+                    tmem_wait_ld();
+                    // balanced residue of an exact integer |v| < 2^24 modulo p:
+                    // v - p * rint(v / p), corrected by at most one p
+                    uint32_t w[4] = {0, 0, 0, 0};
+#pragma unroll
+                    for (int c = 0; c < 16; ++c) {
+                        const float f = __uint_as_float(r[c]);
+                        int x = __float2int_rn(f) - pr * __float2int_rn(f * pinv);
+                        if (2 * x > pr) x -= pr;
+                        if (2 * x < -pr) x += pr;
+                        w[c >> 2] |= (static_cast<uint32_t>(x) & 0xffu) << (8 * (c & 3));
+                    }
+                    if (row < j.d) {
+                        if (vec && col0 + c0 + 16 <= j.n) {
+                            *reinterpret_cast<uint4 *>(out + c0) = make_uint4(w[0], w[1], w[2], w[3]);
+                        } else {
+#pragma unroll
+                            for (int c = 0; c < 16; ++c)
+                                if (col0 + c0 + c < j.n)
+                                    out[c0 + c] = static_cast<int8_t>((w[c >> 2] >> (8 * (c & 3))) & 0xffu);
+                        }
+                    }
+                }
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&tempty[buf]);
+            }
+        } else {
         constexpr int G = (L + 2) / 3;       // digit groups: digits 3g, 3g+1, 3g+2
         constexpr int CW = (L >= 7 || NCH % 8 != 0) ? 4 : 8;  // columns per TMEM load group
         constexpr int kDigitWeight[3] = {1, 1 << DB, 1 << (2 * DB)};
@@ -364,6 +426,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                 }
             }
         }
+        }  // MODE 0
     }
 
     tc_fence_before();
@@ -375,16 +438,16 @@ __global__ void __launch_bounds__(kThreads, 1)
     if (threadIdx.x == 0 && (*abort_flag || *drain_abort)) atomicExch(p.status, -7);
 }
 
-template <int L, int DB, int NC, bool GROUPED>
+template <int L, int DB, int NC, bool GROUPED, int MODE = 0>
 cudaError_t launch_gemm_kernel(const CUtensorMap &tmU, const CUtensorMap &tmD, const GemmParams &p,
                                int num_sms, cudaStream_t s) {
     using Cfg = GemmCfg<L, NC>;
-    cudaError_t e = cudaFuncSetAttribute(gemm_f16_kernel<L, DB, NC, GROUPED>,
+    cudaError_t e = cudaFuncSetAttribute(gemm_f16_kernel<L, DB, NC, GROUPED, MODE>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          Cfg::SMEM_BYTES);
     if (e != cudaSuccess) return e;
     const int grid = p.num_tiles < num_sms ? p.num_tiles : num_sms;
-    gemm_f16_kernel<L, DB, NC, GROUPED><<<grid, kThreads, Cfg::SMEM_BYTES, s>>>(tmU, tmD, p);
+    gemm_f16_kernel<L, DB, NC, GROUPED, MODE><<<grid, kThreads, Cfg::SMEM_BYTES, s>>>(tmU, tmD, p);
     return cudaGetLastError();
 }
 

@@ -32,6 +32,10 @@ __device__ __forceinline__ uint64_t shoup_mulmod(uint64_t a, uint64_t w, uint64_
     return r;
 }
 
+__device__ __forceinline__ uint64_t sub_mod(uint64_t a, uint64_t b, uint64_t q) {
+    return a >= b ? a - b : a + q - b;
+}
+
 __device__ __forceinline__ uint64_t add_mod(uint64_t a, uint64_t b, uint64_t q) {
     const uint64_t s = a + b;
     return s >= q ? s - q : s;

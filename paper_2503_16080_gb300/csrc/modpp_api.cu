@@ -15,6 +15,7 @@
 
 #include "modpp.h"
 #include "modpp_internal.h"
+#include "rns_wide.h"
 
 using namespace modpp;
 
@@ -396,14 +397,38 @@ int run_fp64(int64_t d, int64_t k, int64_t n, const void *U, int ukind, int64_t 
 // digits U_j = sum_i 2^(8 i) U_ji (each an int8 matrix the f16 path takes as
 // its plaintext operand); A_j is split once into f16 digits; then, for each
 // i, the tensor-core GEMM adds 2^(8 i) * (U_ji * A_j) into C_j mod q_j.
+// Wide products run either as digit products (LU x LA per prime) or in the
+// multi-modular form of rns_wide.cu (R small-prime products per prime),
+// whichever needs fewer tensor-core products (modpp_set_wide_path forces
+// one).
+std::atomic<int> g_wide_path{0};  // 0 automatic, 1 digits, 2 CRT
+
 struct WideLayout {
     int LU = 0;                 // 8-bit digits of the left operand
     F16Layout f16;              // one plane
     size_t off_udig = 0, off_f16 = 0, total = 0;
+    bool rns = false;           // multi-modular form
+    RnsPrimes rp{};
+    RnsLayout rl{};
 };
 
 WideLayout wide_layout(int64_t d, int64_t k, int64_t n, const uint64_t *qs, int P) {
     WideLayout w;
+    const int mode = g_wide_path.load();
+    if (mode != 1 && k > 0 && rns_choose(k, qs, P, &w.rp)) {
+        int digit_products = 0;
+        for (int j = 0; j < P; ++j)
+            digit_products = std::max(digit_products, f16_digit_count(qs[j], 8) *
+                                                          f16_digit_count(qs[j], current_digit_bits()));
+        // The CRT form adds two residue passes and a recombination pass
+        // (memory-bound): take it when it saves more than 10% of the products.
+        if (mode == 2 || w.rp.R * 11 < digit_products * 10) {
+            w.rns = true;
+            w.rl = rns_layout(d, k, n, w.rp.R);
+            w.total = w.rl.total;
+            return w;
+        }
+    }
     for (int j = 0; j < P; ++j) w.LU = std::max(w.LU, f16_digit_count(qs[j], 8));
     // One plane at a time: the largest per-prime layout (tile widths differ
     // between digit counts, so the largest L need not have the most rows).
@@ -417,6 +442,44 @@ WideLayout wide_layout(int64_t d, int64_t k, int64_t n, const uint64_t *qs, int 
     return w;
 }
 
+// CRT form of the wide products for one or two right operands sharing U
+// (A2 / C2 null for one): per chain prime, U's residue planes are formed once.
+int run_rns_wide(int64_t d, int64_t k, int64_t n, const uint64_t *U, int64_t ldu, int64_t strideU,
+                 const uint64_t *A1, const uint64_t *A2, int64_t lda, int64_t strideA,
+                 uint64_t *C1, uint64_t *C2, int64_t ldc, int64_t strideC, const uint64_t *primes,
+                 int P, const WideLayout &wl, uint8_t *w, cudaStream_t st) {
+    const RnsLayout &rl = wl.rl;
+    const int sms = device_sms();
+    if (sms <= 0) return MODPP_ERR_CUDA;
+    CUtensorMap tmU, tmD;
+    if (!make_map_f16(&tmU, w + rl.off_u16, static_cast<uint64_t>(rl.kp),
+                      static_cast<uint64_t>(wl.rp.R) * d, kBK, kBM) ||
+        !make_map_f16(&tmD, w + rl.off_d, static_cast<uint64_t>(rl.kp),
+                      static_cast<uint64_t>(wl.rp.R) * rl.nblk * kRnsTileCols, kBK, kRnsTileCols))
+        return MODPP_ERR_CUDA;
+    for (int j = 0; j < P; ++j) {
+        for (int op = 0; op < (A2 ? 2 : 1); ++op) {
+            const uint64_t *A = (op == 0 ? A1 : A2) + static_cast<int64_t>(j) * strideA;
+            uint64_t *C = (op == 0 ? C1 : C2) + static_cast<int64_t>(j) * strideC;
+            EventPair *ev = timer_begin(MODPP_KERNEL_SPLIT, st);
+            int rc = rns_split(d, k, n, U + static_cast<int64_t>(j) * strideU, ldu, A, lda,
+                               primes[j], wl.rp, rl, w, op == 0, st);
+            timer_end(ev, st);
+            if (rc) return rc;
+            ev = timer_begin(MODPP_KERNEL_GEMM, st);
+            rc = rns_gemm(d, k, n, wl.rp, rl, w, reinterpret_cast<int *>(w), wait_limit_ns(), sms,
+                          tmU, tmD, st);
+            timer_end(ev, st);
+            if (rc) return rc;
+            ev = timer_begin(MODPP_KERNEL_U16, st);
+            rc = rns_crt(d, n, C, ldc, primes[j], wl.rp, rl, w, st);
+            timer_end(ev, st);
+            if (rc) return rc;
+        }
+    }
+    return MODPP_OK;
+}
+
 int run_f16_wide(int64_t d, int64_t k, int64_t n, const uint64_t *U, int64_t ldu, int64_t strideU,
                  const uint64_t *A, int64_t lda, int64_t strideA, uint64_t *C, int64_t ldc,
                  int64_t strideC, const uint64_t *primes, int P, void *ws, size_t ws_bytes,
@@ -426,6 +489,9 @@ int run_f16_wide(int64_t d, int64_t k, int64_t n, const uint64_t *U, int64_t ldu
     uint8_t *w = static_cast<uint8_t *>(ws);
     if (cudaMemsetAsync(w, 0, sizeof(int), st) != cudaSuccess) return MODPP_ERR_CUDA;
     if (d == 0 || n == 0) return MODPP_OK;
+    if (wl.rns)
+        return run_rns_wide(d, k, n, U, ldu, strideU, A, nullptr, lda, strideA, C, nullptr, ldc,
+                            strideC, primes, P, wl, w, st);
     int8_t *Udig = reinterpret_cast<int8_t *>(w + wl.off_udig);
     uint8_t *wf = w + wl.off_f16;  // the f16 path's workspace (one plane)
     const F16Layout &lay = wl.f16;
@@ -570,6 +636,23 @@ int modpp_set_digit_bits(int bits) {
 
 int modpp_get_digit_bits(void) { return current_digit_bits(); }
 
+int modpp_set_wide_path(int mode) {
+    if (mode < 0 || mode > 2) return MODPP_ERR_ARG;
+    g_wide_path.store(mode);
+    return MODPP_OK;
+}
+
+int modpp_get_wide_path(void) { return g_wide_path.load(); }
+
+int modpp_wide_plan_info(int64_t k, const uint64_t *primes_host, int P, int *crt_primes) {
+    if (crt_primes == nullptr || P < 1 || primes_host == nullptr) return MODPP_ERR_ARG;
+    int rc = check_primes(primes_host, P, kMaxPlanes);
+    if (rc) return rc;
+    const WideLayout w = wide_layout(1, k, 1, primes_host, P);
+    *crt_primes = w.rns ? w.rp.R : 0;
+    return MODPP_OK;
+}
+
 int modpp_plan_info(int64_t k, uint64_t q, int path, int *digits, int *digit_bits,
                     int64_t *k_chunk) {
     if (k < 1 || k > kMaxK || !prime_ok(q) || !path_ok(path)) return MODPP_ERR_ARG;
@@ -689,6 +772,36 @@ int modpp_mm_wide(int64_t d, int64_t k, int64_t n, const uint64_t *U, int64_t ld
         return MODPP_ERR_WORKSPACE;
     return run_f16_wide(d, k, n, U, ldu, strideU, A, lda, strideA, C, ldc, strideC, primes_host, P,
                         ws, ws_bytes, static_cast<cudaStream_t>(stream));
+}
+
+int modpp_mm_wide_pair(int64_t d, int64_t k, int64_t n, const uint64_t *U, int64_t ldu,
+                       int64_t strideU, const uint64_t *A1, const uint64_t *A2, int64_t lda,
+                       int64_t strideA, uint64_t *C1, uint64_t *C2, int64_t ldc, int64_t strideC,
+                       const uint64_t *primes_host, int P, void *ws, size_t ws_bytes,
+                       void *stream) {
+    int rc = check_sizes(d, k, n);
+    if (rc) return rc;
+    rc = check_primes(primes_host, P, kMaxPlanes);
+    if (rc) return rc;
+    const WideLayout wl = wide_layout(d, k, n, primes_host, P);
+    if (!wl.rns || d == 0 || n == 0 || k == 0) {
+        rc = modpp_mm_wide(d, k, n, U, ldu, strideU, A1, lda, strideA, C1, ldc, strideC,
+                           primes_host, P, ws, ws_bytes, stream);
+        if (rc) return rc;
+        return modpp_mm_wide(d, k, n, U, ldu, strideU, A2, lda, strideA, C2, ldc, strideC,
+                             primes_host, P, ws, ws_bytes, stream);
+    }
+    if (!U || !A1 || !A2 || !C1 || !C2) return MODPP_ERR_ARG;
+    if (ldu < k || lda < n || ldc < n) return MODPP_ERR_ARG;
+    if (P > 1 && (strideU < d * ldu || strideA < k * lda || strideC < d * ldc)) return MODPP_ERR_ARG;
+    if (ws == nullptr || (reinterpret_cast<uintptr_t>(ws) & (kAlign - 1)) != 0 ||
+        ws_bytes < wl.total)
+        return MODPP_ERR_WORKSPACE;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    uint8_t *w = static_cast<uint8_t *>(ws);
+    if (cudaMemsetAsync(w, 0, sizeof(int), st) != cudaSuccess) return MODPP_ERR_CUDA;
+    return run_rns_wide(d, k, n, U, ldu, strideU, A1, A2, lda, strideA, C1, C2, ldc, strideC,
+                        primes_host, P, wl, w, st);
 }
 
 int modpp_status_read(void *ws, void *stream) {

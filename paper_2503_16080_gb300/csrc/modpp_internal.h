@@ -79,6 +79,7 @@ struct GemmParams {
     const GroupPlane *gplanes;  // grouped launches only
     int num_gplanes;
     const int *tile_plane;      // grouped: plane of every tile (index into gplanes)
+    int u_per_plane;            // 1: plane i reads U rows [i*d, (i+1)*d) of the U map
     PlaneConst pc[kMaxPlanes];
 };
 

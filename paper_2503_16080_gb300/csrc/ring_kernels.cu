@@ -26,9 +26,6 @@
 namespace modpp {
 
 // ------------------------------------------------------------ arithmetic
-__device__ __forceinline__ uint64_t sub_mod(uint64_t a, uint64_t b, uint64_t q) {
-    return a >= b ? a - b : a + q - b;
-}
 
 // Montgomery product a * b * 2^-64 mod q for a < q, b < q, q odd < 2^62;
 // qinv = -q^-1 mod 2^64.

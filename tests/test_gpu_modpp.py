@@ -135,8 +135,16 @@ def test_repeat_calls_are_identical(mp):
     assert torch.equal(a, b)
 
 
-@pytest.mark.parametrize("shape", [(1, 1, 1), (130, 300, 70), (256, 512, 96), (64, 1000, 33)])
-def test_wide_residue_products(mp, oracle_mod, shape, digit_bits):
+@pytest.fixture(params=["digits", "crt"])
+def wide_path(request, mp):
+    mp.set_wide_path(request.param)
+    yield request.param
+    mp.set_wide_path("auto")
+
+
+@pytest.mark.parametrize("shape", [(1, 1, 1), (130, 300, 70), (256, 512, 96), (64, 1000, 33),
+                                   (200, 300, 600)])
+def test_wide_residue_products(mp, oracle_mod, shape, digit_bits, wide_path):
     # Both operands residues (Alg. 8 step 2): bit-exact per prime against the oracle.
     d, k, n = shape
     primes = [P50[0], P60[0], P40[0], 97]
@@ -149,7 +157,7 @@ def test_wide_residue_products(mp, oracle_mod, shape, digit_bits):
         assert np.array_equal(got[j], oracle_mod.mod_pp_mm_residues(U[j], A[j], q)), f"prime {q}"
 
 
-def test_wide_extremes(mp, oracle_mod):
+def test_wide_extremes(mp, oracle_mod, wide_path):
     q = P62[0]
     d, k, n = 128, 600, 40
     U = np.full((1, d, k), q - 1, dtype=np.uint64)
@@ -160,3 +168,28 @@ def test_wide_extremes(mp, oracle_mod):
     A2 = np.where(synth.u64(9, 2, k * n).reshape(1, k, n) & np.uint64(1), q - 1, (q - 1) // 2)
     got2 = mp.modpp_mm_wide(to_gpu(U2), to_gpu(A2.astype(np.uint64)), [q]).cpu().numpy()
     assert np.array_equal(got2[0], oracle_mod.mod_pp_mm_residues(U2[0], A2[0].astype(np.uint64), q))
+
+
+@pytest.mark.parametrize("k", [8192, 4100])
+def test_wide_crt_largest_products(mp, oracle_mod, k):
+    # The CRT form at its bound: |X| = k ((q-1)/2)^2 for 50-bit primes (23 small
+    # primes at k = 8192), both signs, plus random rows; against the oracle.
+    q = P50[0]
+    mp.set_wide_path("crt")
+    try:
+        assert mp.wide_plan_info(k, [q]) > 0
+        d, n = 130, 300
+        hi, lo = (q - 1) // 2, (q + 1) // 2       # balanced lifts +(q-1)/2 and -(q-1)/2
+        U = synth.uniform_mod(k, 1, (1, d, k), q)
+        A = synth.uniform_mod(k, 2, (1, k, n), q)
+        U[0, 0, :] = hi
+        U[0, 1, :] = lo
+        A[0, :, 0] = hi
+        A[0, :, 1] = lo
+        got = mp.modpp_mm_wide(to_gpu(U), to_gpu(A), [q]).cpu().numpy()
+        assert np.array_equal(got[0], oracle_mod.mod_pp_mm_residues(U[0], A[0], q))
+        X = k * ((q - 1) // 2) ** 2
+        assert int(got[0, 0, 0]) == X % q and int(got[0, 1, 1]) == X % q
+        assert int(got[0, 0, 1]) == (-X) % q
+    finally:
+        mp.set_wide_path("auto")
