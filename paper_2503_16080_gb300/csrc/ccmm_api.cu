@@ -192,10 +192,10 @@ int ks_run(const modpp_ring_s *r, const uint64_t *ct, int64_t n, int64_t count, 
 // bit-reversed order in `a`, ping-ponging with `b`; returns the buffer
 // holding the result.
 uint64_t *tweak_stages(const modpp_ring_s *r, uint64_t *a, uint64_t *b, int64_t n, int64_t size,
-                       int L, cudaStream_t st, int *rc) {
+                       int L, cudaStream_t st, int *rc, int parts = 2) {
     *rc = MODPP_OK;
     for (int64_t half = 1; half < size; half <<= 1) {
-        if (launch_tweak_stage(a, b, n, L, static_cast<int>(r->N), half, r->tab, st) !=
+        if (launch_tweak_stage(a, b, n, L, static_cast<int>(r->N), half, r->tab, st, parts) !=
             cudaSuccess) {
             *rc = MODPP_ERR_CUDA;
             return a;
@@ -211,8 +211,13 @@ size_t transpose_scratch(const modpp_ring_s *r, int64_t groups) {
 }
 
 // Alg. 4 on `groups` matrices of N ciphertexts; scratch of transpose_scratch bytes.
+// b_zero: every input b-part is zero (the (C00, 0) and (C10, 0) of Alg. 8):
+// the first Tweak and the gathers before the key switches then run on the
+// a-parts only (a Tweak and Aut of zero are zero), the input's b-parts are
+// never read, and the key switches produce the b-parts.
 int transpose_run(const modpp_ring_s *r, const uint64_t *ct, uint64_t *out, int64_t groups,
-                  const uint64_t *aut_keys, char *scratch, cudaStream_t st) {
+                  const uint64_t *aut_keys, char *scratch, cudaStream_t st, bool b_zero = false) {
+    const int parts1 = b_zero ? 1 : 2;
     const int L = r->L;
     const int N = static_cast<int>(r->N);
     const int64_t n = groups * r->N;
@@ -226,9 +231,10 @@ int transpose_run(const modpp_ring_s *r, const uint64_t *ct, uint64_t *out, int6
     t1.per = N;
     t1.brev_bits = r->logN;
     t1.shift_src = 1;
-    if (launch_ct_gather(ct, x1, n, L, N, t1, r->tab, st) != cudaSuccess) return MODPP_ERR_CUDA;
+    if (launch_ct_gather(ct, x1, n, L, N, t1, r->tab, st, parts1) != cudaSuccess)
+        return MODPP_ERR_CUDA;
     int rc = MODPP_OK;
-    uint64_t *aux = tweak_stages(r, x1, x2, n, r->N, L, st, &rc);
+    uint64_t *aux = tweak_stages(r, x1, x2, n, r->N, L, st, &rc, parts1);
     if (rc) return rc;
     uint64_t *other = aux == x1 ? x2 : x1;
     // Steps 2-5: aux'_j = Aut(N^-1 aux_{((2j+1)^-1 - 1)/2}, 2j+1), written in
@@ -239,8 +245,9 @@ int transpose_run(const modpp_ring_s *r, const uint64_t *ct, uint64_t *out, int6
     t2.ellinv = r->t2_ellinv;
     t2.scale = r->ninv;
     t2.scale_s = r->ninv_s;
-    if (launch_ct_gather(aux, other, n, L, N, t2, r->tab, st) != cudaSuccess) return MODPP_ERR_CUDA;
-    rc = ks_run(r, other, n, n, other, n, aut_keys, r->t2_kid, N, 0, ks, st);
+    if (launch_ct_gather(aux, other, n, L, N, t2, r->tab, st, parts1) != cudaSuccess)
+        return MODPP_ERR_CUDA;
+    rc = ks_run(r, other, n, n, other, n, aut_keys, r->t2_kid, N, b_zero ? 1 : 0, ks, st);
     if (rc) return rc;
     // Step 6: ct'' = Tweak(aux').
     uint64_t *ctpp = tweak_stages(r, other, aux, n, r->N, L, st, &rc);
@@ -273,7 +280,7 @@ CcLayout cc_layout(const modpp_ring_s *r) {
     off = align_up(off + sizeof(uint64_t) * batch_words(r, N, L));
     c.ut = off;  // [L][2N][N]: [A; B] of ct1 per prime
     off = align_up(off + sizeof(uint64_t) * L * 2 * N * N);
-    c.x = off;   // batch of 2N: a-parts [C00; C10], b-parts 0
+    c.x = off;   // batch of 2N: a-parts [C00; C10]; b-parts zero (never written or read)
     off = align_up(off + sizeof(uint64_t) * batch_words(r, 2 * N, L));
     c.y = off;   // [L][2N][N]: [C01; C11]
     off = align_up(off + sizeof(uint64_t) * L * 2 * N * N);
@@ -549,9 +556,6 @@ int cc_mm(modpp_ring r, const uint64_t *ct1, const uint64_t *ct2, const uint64_t
     if (e == cudaSuccess)
         e = launch_transpose_u64(ct1 + L * NN, ut + NN, static_cast<int>(N), static_cast<int>(N), N,
                                  N, NN, 2 * NN, L, st);
-    if (e == cudaSuccess)
-        e = cudaMemsetAsync(x + static_cast<int64_t>(L) * 2 * NN, 0, sizeof(uint64_t) * L * 2 * NN,
-                            st);
     if (e != cudaSuccess) return MODPP_ERR_CUDA;
     const size_t wide_bytes = modpp_mm_wide_workspace(2 * N, N, N, r->primes.data(), L);
     void *wws = base + lay.wide;
@@ -560,7 +564,7 @@ int cc_mm(modpp_ring r, const uint64_t *ct1, const uint64_t *ct2, const uint64_t
     if (rc) return rc;
     mark(2);
     // Steps 3-4: Transpose((C00, 0)) and Transpose((C10, 0)) as one batch.
-    rc = transpose_run(r, x, z, 2, aut_keys, scratch, st);
+    rc = transpose_run(r, x, z, 2, aut_keys, scratch, st, /*b_zero=*/true);
     if (rc) return rc;
     mark(3);
     // Step 5: Relin(D0, 0) into rw (free now), then the sums and Rescale.

@@ -61,10 +61,12 @@ cudaError_t launch_ks_moddown(const uint64_t *U, const uint64_t *ct, int64_t n, 
                               int64_t c0, int64_t nb, const int *kid, int kper, int b_zero,
                               const NttPlane *tab, const uint64_t *pinv, const uint64_t *pinv_s,
                               uint64_t *out, int64_t n_out, cudaStream_t s);
+// parts = 2: both parts of every ciphertext; 1: the a-parts only.
 cudaError_t launch_ct_gather(const uint64_t *in, uint64_t *out, int64_t n, int L, int N,
-                             const GatherTables &t, const NttPlane *tab, cudaStream_t s);
+                             const GatherTables &t, const NttPlane *tab, cudaStream_t s,
+                             int parts = 2);
 cudaError_t launch_tweak_stage(const uint64_t *in, uint64_t *out, int64_t n, int L, int N,
-                               int64_t half, const NttPlane *tab, cudaStream_t s);
+                               int64_t half, const NttPlane *tab, cudaStream_t s, int parts = 2);
 cudaError_t launch_add_planes(const uint64_t *x, const uint64_t *y, uint64_t *out, int parts, int L,
                               int64_t count, const NttPlane *tab, cudaStream_t s);
 cudaError_t launch_rescale(const uint64_t *in, uint64_t *out, int L, int64_t count,

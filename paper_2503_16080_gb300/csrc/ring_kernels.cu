@@ -262,7 +262,7 @@ cudaError_t launch_ks_moddown(const uint64_t *U, const uint64_t *ct, int64_t n, 
 // ------------------------------------------------------------ gathers, Tweak
 // Batches have power-of-two N (and, for Tweak, n and the table period), so
 // every index below is a shift or a mask; blockIdx.y selects the (part,
-// prime) plane, 2L of them.
+// prime) plane: 2L of them, or the L a-part planes only (parts = 1).
 __device__ __forceinline__ int ilog2(int x) { return 31 - __clz(x); }
 
 // out[c] = scale * X^shift(c) * sigma_ell(c)(in[src(c)]) for every part and
@@ -308,11 +308,12 @@ __global__ void ct_gather_kernel(const uint64_t *__restrict__ in, uint64_t *__re
 }
 
 cudaError_t launch_ct_gather(const uint64_t *in, uint64_t *out, int64_t n, int L, int N,
-                             const GatherTables &t, const NttPlane *tab, cudaStream_t s) {
+                             const GatherTables &t, const NttPlane *tab, cudaStream_t s,
+                             int parts) {
     if (n == 0) return cudaSuccess;
     const int64_t per_plane = n * N;
     const int64_t bx = std::min<int64_t>((per_plane + 255) / 256, 152 * 8);
-    ct_gather_kernel<<<dim3(static_cast<unsigned>(bx), 2 * L), 256, 0, s>>>(in, out, n, L,
+    ct_gather_kernel<<<dim3(static_cast<unsigned>(bx), parts * L), 256, 0, s>>>(in, out, n, L,
                                                                             31 - __builtin_clz(N), t, tab);
     return cudaGetLastError();
 }
@@ -388,18 +389,18 @@ __global__ void tweak_stage_scalar_kernel(const uint64_t *__restrict__ in,
 }
 
 cudaError_t launch_tweak_stage(const uint64_t *in, uint64_t *out, int64_t n, int L, int N,
-                               int64_t half, const NttPlane *tab, cudaStream_t s) {
+                               int64_t half, const NttPlane *tab, cudaStream_t s, int parts) {
     if (n < 2) return cudaSuccess;
     const int logN = 31 - __builtin_clz(N);
     const int lhalf = 63 - __builtin_clzll(static_cast<unsigned long long>(half));
     const int64_t per_plane = (n >> 1) * N;
     if (lhalf < logN && N >= 2) {
         const int64_t bx = std::min<int64_t>((per_plane / 2 + 255) / 256, 152 * 8);
-        tweak_stage_kernel<<<dim3(static_cast<unsigned>(bx), 2 * L), 256, 0, s>>>(in, out, n, L,
-                                                                                   logN, lhalf, tab);
+        tweak_stage_kernel<<<dim3(static_cast<unsigned>(bx), parts * L), 256, 0, s>>>(
+            in, out, n, L, logN, lhalf, tab);
     } else {
         const int64_t bx = std::min<int64_t>((per_plane + 255) / 256, 152 * 8);
-        tweak_stage_scalar_kernel<<<dim3(static_cast<unsigned>(bx), 2 * L), 256, 0, s>>>(
+        tweak_stage_scalar_kernel<<<dim3(static_cast<unsigned>(bx), parts * L), 256, 0, s>>>(
             in, out, n, L, logN, lhalf, tab);
     }
     return cudaGetLastError();
