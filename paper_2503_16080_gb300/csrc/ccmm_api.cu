@@ -194,9 +194,17 @@ int ks_run(const modpp_ring_s *r, const uint64_t *ct, int64_t n, int64_t count, 
 uint64_t *tweak_stages(const modpp_ring_s *r, uint64_t *a, uint64_t *b, int64_t n, int64_t size,
                        int L, cudaStream_t st, int *rc, int parts = 2) {
     *rc = MODPP_OK;
-    for (int64_t half = 1; half < size; half <<= 1) {
-        if (launch_tweak_stage(a, b, n, L, static_cast<int>(r->N), half, r->tab, st, parts) !=
-            cudaSuccess) {
+    const int N = static_cast<int>(r->N);
+    for (int64_t half = 1; half < size;) {
+        cudaError_t e;
+        if (4 * half <= size && 4 * half <= N) {  // two stages in one pass
+            e = launch_tweak_radix4(a, b, n, L, N, half, r->tab, st, parts);
+            half <<= 2;
+        } else {
+            e = launch_tweak_stage(a, b, n, L, N, half, r->tab, st, parts);
+            half <<= 1;
+        }
+        if (e != cudaSuccess) {
             *rc = MODPP_ERR_CUDA;
             return a;
         }
@@ -481,8 +489,11 @@ int modpp_tweak(modpp_ring r, const uint64_t *ct, uint64_t *out, int64_t n, void
         return MODPP_ERR_WORKSPACE;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     uint64_t *w = static_cast<uint64_t *>(ws);
-    // log2(n) stages alternate buffers: start where the last one lands in out.
-    uint64_t *first = (ln % 2 == 1) ? w : out;
+    // The passes alternate buffers: start where the last one lands in out.
+    int passes = 0;
+    for (int64_t half = 1; half < n; ++passes)
+        half <<= (4 * half <= n && 4 * half <= r->N) ? 2 : 1;
+    uint64_t *first = (passes % 2 == 1) ? w : out;
     uint64_t *second = first == w ? out : w;
     GatherTables t{};
     t.per = static_cast<int>(n);

@@ -359,6 +359,95 @@ __global__ void tweak_stage_kernel(const uint64_t *__restrict__ in, uint64_t *__
     }
 }
 
+// Two consecutive stages (half = h, then 2h) in one pass, for 4h <= N.  For
+// the four ciphertexts i0 = 4h blk + jj, i1 = i0 + h, i2 = i0 + 2h,
+// i3 = i0 + 3h, with R_t(x) = X^t x, tA = jj N / h and tB = jj N / (2h):
+//   z0 = x0 + R_tA(x1) + R_tB(x2)       + R_{tA+tB}(x3)
+//   z2 = x0 + R_tA(x1) - R_tB(x2)       - R_{tA+tB}(x3)
+//   z1 = x0 - R_tA(x1) + R_{tB+N/2}(x2) - R_{tA+tB+N/2}(x3)
+//   z3 = x0 - R_tA(x1) - R_{tB+N/2}(x2) + R_{tA+tB+N/2}(x3)
+// (the second stage pairs (i1, i3) with twiddle X^(tB + N/2)).  Six rotated
+// reads of contiguous windows give four outputs, instead of eight reads and
+// eight writes for two radix-2 passes.  All rotations are even, so two
+// neighbouring coefficients move together in 16-byte accesses.
+__device__ __forceinline__ ulonglong2 rot_load(const uint64_t *x, int m, int t, int N, uint64_t q) {
+    // coefficient m (and m + 1) of X^t x, 0 <= t < 2N, m and t even
+    int e = (m - t) & (2 * N - 1);
+    const bool neg = e >= N;
+    e &= N - 1;
+    ulonglong2 v = *reinterpret_cast<const ulonglong2 *>(x + e);
+    if (neg) {
+        v.x = v.x == 0 ? 0 : q - v.x;
+        v.y = v.y == 0 ? 0 : q - v.y;
+    }
+    return v;
+}
+
+__global__ void tweak_radix4_kernel(const uint64_t *__restrict__ in, uint64_t *__restrict__ out,
+                                    int64_t n, int L, int logN, int lh,
+                                    const NttPlane *__restrict__ tab) {
+    const int r = blockIdx.y;  // part * L + plane
+    const uint64_t q = tab[r % L].q;
+    const int N = 1 << logN;
+    const uint64_t *inp = in + static_cast<int64_t>(r) * n * N;
+    uint64_t *outp = out + static_cast<int64_t>(r) * n * N;
+    const int64_t total = (n >> 2) << (logN - 1);  // groups of four x coefficient pairs
+    const int64_t h_mask = (int64_t(1) << lh) - 1;
+    for (int64_t w = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; w < total;
+         w += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        const int m = (static_cast<int>(w) << 1) & (N - 1);
+        const int64_t g = w >> (logN - 1);
+        const int64_t jj = g & h_mask;
+        const int64_t i0 = ((g >> lh) << (lh + 2)) + jj;
+        const int64_t h = int64_t(1) << lh;
+        const int tA = static_cast<int>(jj << (logN - lh));
+        const int tB = static_cast<int>(jj << (logN - lh - 1));
+        const int halfN = N >> 1;
+        const uint64_t *x0 = inp + (i0 << logN);
+        const uint64_t *x1 = inp + ((i0 + h) << logN);
+        const uint64_t *x2 = inp + ((i0 + 2 * h) << logN);
+        const uint64_t *x3 = inp + ((i0 + 3 * h) << logN);
+        const ulonglong2 a = *reinterpret_cast<const ulonglong2 *>(x0 + m);
+        const ulonglong2 b = rot_load(x1, m, tA, N, q);
+        const ulonglong2 c0 = rot_load(x2, m, tB, N, q);
+        const ulonglong2 c1 = rot_load(x2, m, tB + halfN, N, q);
+        const ulonglong2 d0 = rot_load(x3, m, tA + tB, N, q);
+        const ulonglong2 d1 = rot_load(x3, m, tA + tB + halfN, N, q);
+        ulonglong2 z0, z1, z2, z3;
+        {
+            const uint64_t p = add_mod(a.x, b.x, q), mm = sub_mod(a.x, b.x, q);
+            const uint64_t s0 = add_mod(c0.x, d0.x, q), s1 = sub_mod(c1.x, d1.x, q);
+            z0.x = add_mod(p, s0, q);
+            z2.x = sub_mod(p, s0, q);
+            z1.x = add_mod(mm, s1, q);
+            z3.x = sub_mod(mm, s1, q);
+        }
+        {
+            const uint64_t p = add_mod(a.y, b.y, q), mm = sub_mod(a.y, b.y, q);
+            const uint64_t s0 = add_mod(c0.y, d0.y, q), s1 = sub_mod(c1.y, d1.y, q);
+            z0.y = add_mod(p, s0, q);
+            z2.y = sub_mod(p, s0, q);
+            z1.y = add_mod(mm, s1, q);
+            z3.y = sub_mod(mm, s1, q);
+        }
+        *reinterpret_cast<ulonglong2 *>(outp + (i0 << logN) + m) = z0;
+        *reinterpret_cast<ulonglong2 *>(outp + ((i0 + h) << logN) + m) = z1;
+        *reinterpret_cast<ulonglong2 *>(outp + ((i0 + 2 * h) << logN) + m) = z2;
+        *reinterpret_cast<ulonglong2 *>(outp + ((i0 + 3 * h) << logN) + m) = z3;
+    }
+}
+
+cudaError_t launch_tweak_radix4(const uint64_t *in, uint64_t *out, int64_t n, int L, int N,
+                                int64_t half, const NttPlane *tab, cudaStream_t s, int parts) {
+    const int logN = 31 - __builtin_clz(N);
+    const int lh = 63 - __builtin_clzll(static_cast<unsigned long long>(half));
+    const int64_t per_plane = (n >> 2) * (N >> 1);
+    const int64_t bx = std::min<int64_t>((per_plane + 255) / 256, 152 * 8);
+    tweak_radix4_kernel<<<dim3(static_cast<unsigned>(bx), parts * L), 256, 0, s>>>(in, out, n, L,
+                                                                                   logN, lh, tab);
+    return cudaGetLastError();
+}
+
 // The same stage for half = N (n = 2N), where t = jj is odd for odd jj: one
 // coefficient per thread.
 __global__ void tweak_stage_scalar_kernel(const uint64_t *__restrict__ in,
