@@ -171,14 +171,23 @@ int ks_run(const modpp_ring_s *r, const uint64_t *ct, int64_t n, int64_t count, 
     for (int64_t c0 = 0; c0 < count; c0 += nb) {
         const int64_t m = std::min(nb, count - c0);
         cudaError_t e;
-        if (ntt_fast_supported(N)) {
-            e = launch_ks_digits_ntt(ct, n, L, N, c0, m, r->tab, D, st);
+        // One key for every ciphertext (relinearisation, modpp_keyswitch):
+        // the fused kernel, whose key reads then hit L2.  One key per
+        // ciphertext (the automorphisms of Alg. 4): the streaming
+        // multiply-accumulate kernel reads the keys at full bandwidth.
+        if (kper == 1 && ks_fused_supported(N)) {
+            e = launch_ks_fused(ct, n, L, N, c0, m, r->tab, keys, kid, kper, U, st);
         } else {
-            e = launch_ks_decompose(ct, n, L, N, c0, m, r->tab, D, st);
-            if (e == cudaSuccess) e = launch_ntt(D, m * L * Lp, N, 1, Lp, r->tab, false, st);
+            if (ntt_fast_supported(N)) {
+                e = launch_ks_digits_ntt(ct, n, L, N, c0, m, r->tab, D, st);
+            } else {
+                e = launch_ks_decompose(ct, n, L, N, c0, m, r->tab, D, st);
+                if (e == cudaSuccess) e = launch_ntt(D, m * L * Lp, N, 1, Lp, r->tab, false, st);
+            }
+            if (e == cudaSuccess)
+                e = launch_ks_multacc(D, keys, kid, kper, L, N, c0, m, r->tab, U, st);
+            if (e == cudaSuccess) e = launch_ntt(U, m * 2 * Lp, N, 1, Lp, r->tab, true, st);
         }
-        if (e == cudaSuccess) e = launch_ks_multacc(D, keys, kid, kper, L, N, c0, m, r->tab, U, st);
-        if (e == cudaSuccess) e = launch_ntt(U, m * 2 * Lp, N, 1, Lp, r->tab, true, st);
         if (e == cudaSuccess)
             e = launch_ks_moddown(U, ct, n, L, N, c0, m, kid, kper, b_zero, r->tab, r->pinv,
                                   r->pinv_s, out, n_out, st);

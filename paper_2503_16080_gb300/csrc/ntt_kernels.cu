@@ -70,10 +70,21 @@ __device__ __forceinline__ int group_start(int g, int lu, int lnb) {
     return (blk << (lu + S)) + r;
 }
 
-template <int E, int S, bool FWD>
+// Sink of a forward transform's last pass in key switching: the transformed
+// digit times the two key polynomials (evaluation domain, Montgomery form),
+// accumulated into two shared-memory accumulators (padded index).
+struct MacSink {
+    uint64_t *acc0, *acc1;
+    const uint64_t *k0, *k1;
+    uint64_t qinv;  // -q^-1 mod 2^64
+    bool assign;    // first digit: the accumulators take the products
+};
+
+template <int E, int S, bool FWD, bool MAC = false>
 __device__ __forceinline__ void ntt_pass(uint64_t *sa, const uint64_t *gin, uint64_t *gout,
                                          bool reduce_in, int N, int logN, int lu, bool first,
-                                         bool last, const PlaneRegs &pr) {
+                                         bool last, const PlaneRegs &pr,
+                                         const MacSink *mk = nullptr) {
     constexpr int G = E >> S;  // groups of 2^S coefficients per thread
     constexpr int W = 1 << S;
     const int T = N / E;
@@ -148,7 +159,15 @@ __device__ __forceinline__ void ntt_pass(uint64_t *sa, const uint64_t *gin, uint
                 } else {
                     x = shoup_mulmod(x, pr.ninv, pr.ninv_s, pr.q);
                 }
-                gout[j] = x;
+                if constexpr (MAC) {
+                    const int idx = pad_idx(j);
+                    const uint64_t p0 = mont_mul(x, mk->k0[j], pr.q, mk->qinv);
+                    const uint64_t p1 = mont_mul(x, mk->k1[j], pr.q, mk->qinv);
+                    mk->acc0[idx] = mk->assign ? p0 : add_mod(mk->acc0[idx], p0, pr.q);
+                    mk->acc1[idx] = mk->assign ? p1 : add_mod(mk->acc1[idx], p1, pr.q);
+                } else {
+                    gout[j] = x;
+                }
             } else {
                 sa[pad_idx(j)] = x;
             }
@@ -218,6 +237,91 @@ __global__ void __launch_bounds__(NttShape<E>::kMaxThreads, 1) ntt_e_kernel(NttF
     }
 }
 
+// All passes of one transform held in `sa`: the first reads gin (or `sa`
+// itself when from_smem), the last writes gout (or the MAC sink).
+template <int E, bool FWD, bool MAC>
+__device__ __forceinline__ void ntt_run(uint64_t *sa, const uint64_t *gin, uint64_t *gout,
+                                        bool reduce_in, int N, int logN, const PlaneRegs &pr,
+                                        bool from_smem, const MacSink *mk) {
+    constexpr int SM = NttShape<E>::kLogE;
+    int done = 0;
+    bool first = !from_smem;
+    while (done < logN) {
+        const int s = logN - done < SM ? logN - done : SM;
+        const bool last = done + s == logN;
+        const int lu = FWD ? logN - done - s : done;
+        if (s == SM) {
+            ntt_pass<E, SM, FWD, MAC>(sa, gin, gout, reduce_in, N, logN, lu, first, last, pr, mk);
+        } else if (s == 4) {
+            ntt_pass<E, (SM > 4 ? 4 : 1), FWD, MAC>(sa, gin, gout, reduce_in, N, logN, lu, first,
+                                                    last, pr, mk);
+        } else if (s == 3) {
+            ntt_pass<E, (SM > 3 ? 3 : 1), FWD, MAC>(sa, gin, gout, reduce_in, N, logN, lu, first,
+                                                    last, pr, mk);
+        } else if (s == 2) {
+            ntt_pass<E, 2, FWD, MAC>(sa, gin, gout, reduce_in, N, logN, lu, first, last, pr, mk);
+        } else {
+            ntt_pass<E, 1, FWD, MAC>(sa, gin, gout, reduce_in, N, logN, lu, first, last, pr, mk);
+        }
+        done += s;
+        first = false;
+    }
+}
+
+struct KsFusedArgs {
+    const uint64_t *ct;  // batch [2][L][n][N]; digits come from the a-parts
+    int64_t n, c0;
+    int L, N, logN;
+    const NttPlane *tab;
+    const uint64_t *keys;  // [count][L][2][L+1][N], prepared
+    const int *kid;
+    int kper;
+    uint64_t *U;  // [nb][2][L+1][N]: sum_i digit_i * key_i[part] mod q_k, coefficients
+};
+
+// Key switching's digits, products and sums for one (ciphertext, target
+// prime k) per CTA, in shared memory: for every digit i the forward
+// transform of (a_i mod q_k), multiplied in its last pass by key i (both
+// parts) and summed into two accumulators; then both inverse transforms,
+// written to U.  Shared memory: three padded polynomials (N <= 8192).
+template <int E>
+__global__ void __launch_bounds__(NttShape<E>::kMaxThreads, 1) ks_fused_kernel(KsFusedArgs a) {
+    extern __shared__ uint64_t smem[];
+    const int N = a.N;
+    const int Wd = N + N / 32;
+    uint64_t *sa = smem, *acc0 = smem + Wd, *acc1 = smem + 2 * Wd;
+    const int Lp = a.L + 1;
+    const int k = static_cast<int>(blockIdx.x % Lp);
+    const int64_t c = blockIdx.x / Lp;
+    const int kc = a.kid[(a.c0 + c) % a.kper];
+    if (kc < 0) return;  // no key switch for this ciphertext (uniform per CTA)
+    const NttPlane &tp = a.tab[k];
+    PlaneRegs fw, iv;
+    fw.q = iv.q = tp.q;
+    fw.q2 = iv.q2 = 2 * tp.q;
+    fw.mu = iv.mu = tp.mu;
+    fw.ninv = iv.ninv = tp.ninv;
+    fw.ninv_s = iv.ninv_s = tp.ninv_s;
+    fw.tw = tp.fwd;
+    fw.tw_s = tp.fwd_s;
+    iv.tw = tp.inv;
+    iv.tw_s = tp.inv_s;
+    const int64_t key_stride = static_cast<int64_t>(a.L) * 2 * Lp * N;
+    const uint64_t *key = a.keys + kc * key_stride;
+    for (int i = 0; i < a.L; ++i) {
+        const uint64_t *gin = a.ct + (static_cast<int64_t>(i) * a.n + a.c0 + c) * N;
+        MacSink mk{acc0, acc1, key + (static_cast<int64_t>(i * 2 + 0) * Lp + k) * N,
+                   key + (static_cast<int64_t>(i * 2 + 1) * Lp + k) * N, tp.qinv_neg, i == 0};
+
+        ntt_run<E, true, true>(sa, gin, nullptr, true, N, a.logN, fw, false, &mk);
+        __syncthreads();  // sa is rewritten by the next digit; acc read by the inverse
+    }
+    uint64_t *u0 = a.U + ((c * 2 + 0) * Lp + k) * N;
+    uint64_t *u1 = a.U + ((c * 2 + 1) * Lp + k) * N;
+    ntt_run<E, false, false>(acc0, nullptr, u0, false, N, a.logN, iv, true, nullptr);
+    ntt_run<E, false, false>(acc1, nullptr, u1, false, N, a.logN, iv, true, nullptr);
+}
+
 // Coefficients per thread for degree N: 16 up to N = 8192, 32 above
 // (MODPP_NTT_E = 8, 16 or 32 overrides where the thread count allows).
 int ntt_e_for(int N) {
@@ -253,6 +357,33 @@ cudaError_t launch_fast(const NttFastArgs &a, int64_t npolys, cudaStream_t s) {
 }
 
 }  // namespace
+
+bool ks_fused_supported(int N) { return N >= 1024 && N <= 8192 && (N & (N - 1)) == 0; }
+
+cudaError_t launch_ks_fused(const uint64_t *ct, int64_t n, int L, int N, int64_t c0, int64_t nb,
+                            const NttPlane *tab, const uint64_t *keys, const int *kid, int kper,
+                            uint64_t *U, cudaStream_t s) {
+    if (nb == 0) return cudaSuccess;
+    KsFusedArgs a{};
+    a.ct = ct;
+    a.n = n;
+    a.c0 = c0;
+    a.L = L;
+    a.N = N;
+    a.logN = 31 - __builtin_clz(N);
+    a.tab = tab;
+    a.keys = keys;
+    a.kid = kid;
+    a.kper = kper;
+    a.U = U;
+    const size_t smem = 3 * static_cast<size_t>(N + N / 32) * sizeof(uint64_t);
+    cudaError_t e = cudaFuncSetAttribute(ks_fused_kernel<16>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         static_cast<int>(smem));
+    if (e != cudaSuccess) return e;
+    ks_fused_kernel<16><<<static_cast<unsigned>(nb * (L + 1)), N / 16, smem, s>>>(a);
+    return cudaGetLastError();
+}
 
 bool ntt_fast_supported(int N) { return N >= 1024 && N <= 16384 && (N & (N - 1)) == 0; }
 

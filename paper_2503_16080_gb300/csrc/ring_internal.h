@@ -45,6 +45,12 @@ cudaError_t launch_ntt(uint64_t *polys, int64_t npolys, int N, int64_t inner, in
 bool ntt_fast_supported(int N);
 cudaError_t launch_ntt_fast(uint64_t *polys, int64_t npolys, int N, int64_t inner, int nplanes,
                             const NttPlane *tab, bool inverse, cudaStream_t s);
+// Key switching's digits, NTTs, key products and inverse NTTs in one kernel
+// (1024 <= N <= 8192): U[c][part][k] = sum_i a_i * key_i[part] mod q_k (coefficients).
+bool ks_fused_supported(int N);
+cudaError_t launch_ks_fused(const uint64_t *ct, int64_t n, int L, int N, int64_t c0, int64_t nb,
+                            const NttPlane *tab, const uint64_t *keys, const int *kid, int kper,
+                            uint64_t *U, cudaStream_t s);
 // Digits of key switching fused with their forward NTT (N >= 1024):
 // D[c][i][k] = NTT_k(a_i of ciphertext c0 + c mod q_k), c < nb.
 cudaError_t launch_ks_digits_ntt(const uint64_t *ct, int64_t n, int L, int N, int64_t c0,

@@ -27,20 +27,6 @@ namespace modpp {
 
 // ------------------------------------------------------------ arithmetic
 
-// Montgomery product a * b * 2^-64 mod q for a < q, b < q, q odd < 2^62;
-// qinv = -q^-1 mod 2^64.
-__device__ __forceinline__ uint64_t mont_mul(uint64_t a, uint64_t b, uint64_t q, uint64_t qinv) {
-    const uint64_t lo = a * b;
-    const uint64_t hi = __umul64hi(a, b);
-    const uint64_t t = lo * qinv;
-    const uint64_t th = __umul64hi(t, q);
-    // (lo + t*q) is a multiple of 2^64; its carry out of the low word is 1
-    // unless lo == 0.
-    uint64_t r = hi + th + (lo != 0 ? 1u : 0u);
-    if (r >= q) r -= q;
-    return r;
-}
-
 // ------------------------------------------------------------ NTT
 // One CTA transforms one polynomial in shared memory, one barrier per stage
 // (the transform for N < 1024; larger N use ntt_kernels.cu).  Polynomial p
