@@ -468,6 +468,29 @@ def run_secondary(args):
             torch.cuda.synchronize()
             line["fp64_matmul_ms"] = f0.elapsed_time(f1)
             line["slowdown_vs_fp64_matmul"] = ms / line["fp64_matmul_ms"]
+    elif args.workload == "umma_sweep":
+        # Tensor throughput of the digit GEMM against UMMA N: one plane of
+        # 8192^3 with primes of 9, 18, 27, 36, 45 and 50 bits gives L = 1..6
+        # digits of 9 bits and tile widths N = L * tile_cols(L).
+        d = k = n = 8192
+        U = synth.uniform_int8_torch(SEED, 1, (d, k), dev)
+        rows = []
+        for bits in (9, 18, 27, 36, 45, 50):
+            q = synth.ntt_primes(bits, 1, two_adicity=1)[0]
+            A = synth.uniform_mod_torch(SEED, 2, (1, k, n), q, dev)
+            C = torch.empty((1, d, n), dtype=torch.uint64, device=dev)
+            ms, kern = _timed(lambda: pkg.modpp_mm(U, A, [q], out=C), args.steps, args.warmup,
+                              stream, pkg)
+            L = pkg.plan_info(k, q)["digits"]
+            g_ms = kern["gemm"][0] / max(kern["gemm"][1], 1)
+            tf = 2.0 * d * k * n * L / (g_ms * 1e-3) / 1e12
+            rows.append({"prime_bits": bits, "digits": L, "umma_n": L * {1: 64, 2: 64, 3: 64,
+                                                                         4: 48, 5: 48, 6: 40}[L],
+                         "gemm_ms": g_ms, "tflops": tf,
+                         "frac": tf / peaks["bf16_tflops_sustained"]})
+        line.update({"workload": "umma_sweep", "unit": "TFLOP/s", "value": rows[-1]["tflops"],
+                     "config": {"workload": "digit GEMM, one plane of 8192^3, L = 1..6 digits"},
+                     "rows": rows})
     elif args.workload == "grouped":
         sys.path.insert(0, os.path.join(ROOT, "tests"))
         seed = 3
@@ -710,7 +733,8 @@ def main():
     ap.add_argument("--digit-bits", type=int, default=0,
                     help="digit width of the f16 path (8, 9, 10; 0 = library default)")
     ap.add_argument("--workload", default="pcmm4096",
-                    choices=["pcmm4096", "pcmm16384", "pcmv", "grouped", "ccmm8192"],
+                    choices=["pcmm4096", "pcmm16384", "pcmv", "grouped", "ccmm8192",
+                             "umma_sweep"],
                     help="pcmm4096 (default, the benchmark line); the others are recorded "
                          "beside it")
     ap.add_argument("--n", type=int, default=4096,
