@@ -128,7 +128,7 @@ RingLayout ring_layout(int64_t N, int L) {
     r.tab = off;
     off = align_up(off + sizeof(NttPlane) * (L + 1));
     r.tables = off;
-    off = align_up(off + sizeof(uint64_t) * 4 * (L + 1) * N);
+    off = align_up(off + sizeof(uint64_t) * 8 * (L + 1) * N);
     r.consts = off;
     off = align_up(off + sizeof(uint64_t) * 6 * (L + 1));
     r.ints = off;
@@ -358,10 +358,12 @@ int modpp_ring_create(int64_t N, int L, const uint64_t *primes_host, void *mem, 
             return MODPP_ERR_PRIME;
         }
         const uint64_t psi_inv = invmod(psi, q);
-        uint64_t *fwd = tabs + (static_cast<int64_t>(4 * k) + 0) * N;
-        uint64_t *fwd_s = tabs + (static_cast<int64_t>(4 * k) + 1) * N;
-        uint64_t *inv = tabs + (static_cast<int64_t>(4 * k) + 2) * N;
-        uint64_t *inv_s = tabs + (static_cast<int64_t>(4 * k) + 3) * N;
+        uint64_t *fwd = tabs + (static_cast<int64_t>(8 * k) + 0) * N;
+        uint64_t *fwd_s = tabs + (static_cast<int64_t>(8 * k) + 1) * N;
+        uint64_t *inv = tabs + (static_cast<int64_t>(8 * k) + 2) * N;
+        uint64_t *inv_s = tabs + (static_cast<int64_t>(8 * k) + 3) * N;
+        uint64_t *fwd2 = tabs + (static_cast<int64_t>(8 * k) + 4) * N;  // 2N words
+        uint64_t *inv2 = tabs + (static_cast<int64_t>(8 * k) + 6) * N;  // 2N words
         uint64_t pw = 1, pwi = 1;
         for (int64_t i = 0; i < N; ++i) {  // psi^i, placed at bitrev(i)
             const unsigned j = bitrev(static_cast<unsigned>(i), r->logN);
@@ -369,6 +371,10 @@ int modpp_ring_create(int64_t N, int L, const uint64_t *primes_host, void *mem, 
             fwd_s[j] = shoup(pw, q);
             inv[j] = pwi;
             inv_s[j] = shoup(pwi, q);
+            fwd2[2 * j] = fwd[j];
+            fwd2[2 * j + 1] = fwd_s[j];
+            inv2[2 * j] = inv[j];
+            inv2[2 * j + 1] = inv_s[j];
             pw = mulmod(pw, psi, q);
             pwi = mulmod(pwi, psi_inv, q);
         }
@@ -382,10 +388,12 @@ int modpp_ring_create(int64_t N, int L, const uint64_t *primes_host, void *mem, 
         t.ninv_s = shoup(t.ninv, q);
         t.r64 = static_cast<uint64_t>((static_cast<u128>(1) << 64) % q);
         t.r64_s = shoup(t.r64, q);
-        t.fwd = dtabs + (static_cast<int64_t>(4 * k) + 0) * N;
-        t.fwd_s = dtabs + (static_cast<int64_t>(4 * k) + 1) * N;
-        t.inv = dtabs + (static_cast<int64_t>(4 * k) + 2) * N;
-        t.inv_s = dtabs + (static_cast<int64_t>(4 * k) + 3) * N;
+        t.fwd = dtabs + (static_cast<int64_t>(8 * k) + 0) * N;
+        t.fwd_s = dtabs + (static_cast<int64_t>(8 * k) + 1) * N;
+        t.inv = dtabs + (static_cast<int64_t>(8 * k) + 2) * N;
+        t.inv_s = dtabs + (static_cast<int64_t>(8 * k) + 3) * N;
+        t.fwd2 = reinterpret_cast<const ulonglong2 *>(dtabs + (static_cast<int64_t>(8 * k) + 4) * N);
+        t.inv2 = reinterpret_cast<const ulonglong2 *>(dtabs + (static_cast<int64_t>(8 * k) + 6) * N);
     }
     auto *consts = reinterpret_cast<uint64_t *>(host.data() + lay.consts);
     const uint64_t P = primes_host[L];

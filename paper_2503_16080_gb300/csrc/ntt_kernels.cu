@@ -50,7 +50,7 @@ struct NttFastArgs {
 // Constants of the polynomial's prime, held in registers.
 struct PlaneRegs {
     uint64_t q, q2, mu, ninv, ninv_s;
-    const uint64_t *tw, *tw_s;  // fwd tables (forward) or inv tables (inverse)
+    const ulonglong2 *tw;  // (twiddle, Shoup quotient) pairs: fwd2 (forward) or inv2 (inverse)
 };
 
 // First coefficient of group g in a pass with group stride 2^lu and groups
@@ -127,15 +127,16 @@ __device__ __forceinline__ void ntt_pass(uint64_t *sa, const uint64_t *gin, uint
                 uint64_t &x = v[gi * W + k];
                 uint64_t &y = v[gi * W + k + half];
                 const int ti = base + (k >> sh);
-                const uint64_t w = pr.tw[ti], ws = pr.tw_s[ti];
+                const ulonglong2 tw = pr.tw[ti];
+                const uint64_t w = tw.x, ws = tw.y;
                 if (FWD) {
-                    const uint64_t xa = x >= pr.q2 ? x - pr.q2 : x;
+                    const uint64_t xa = min(x, x - pr.q2);  // x - 2q when x >= 2q
                     const uint64_t t = shoup_lazy(y, w, ws, pr.q);
                     x = xa + t;
                     y = xa - t + pr.q2;
                 } else {
                     uint64_t sm = x + y;
-                    sm = sm >= pr.q2 ? sm - pr.q2 : sm;
+                    sm = min(sm, sm - pr.q2);
                     const uint64_t d = x - y + pr.q2;
                     x = sm;
                     y = shoup_lazy(d, w, ws, pr.q);
@@ -209,8 +210,7 @@ __global__ void __launch_bounds__(NttShape<E>::kMaxThreads, 1) ntt_e_kernel(NttF
     pr.mu = tp.mu;
     pr.ninv = tp.ninv;
     pr.ninv_s = tp.ninv_s;
-    pr.tw = FWD ? tp.fwd : tp.inv;
-    pr.tw_s = FWD ? tp.fwd_s : tp.inv_s;
+    pr.tw = FWD ? tp.fwd2 : tp.inv2;
     const bool reduce_in = a.ks_ct != nullptr;
     uint64_t *gout = a.polys + p * N;
     const int logN = a.logN;
@@ -302,10 +302,8 @@ __global__ void __launch_bounds__(NttShape<E>::kMaxThreads, 1) ks_fused_kernel(K
     fw.mu = iv.mu = tp.mu;
     fw.ninv = iv.ninv = tp.ninv;
     fw.ninv_s = iv.ninv_s = tp.ninv_s;
-    fw.tw = tp.fwd;
-    fw.tw_s = tp.fwd_s;
-    iv.tw = tp.inv;
-    iv.tw_s = tp.inv_s;
+    fw.tw = tp.fwd2;
+    iv.tw = tp.inv2;
     const int64_t key_stride = static_cast<int64_t>(a.L) * 2 * Lp * N;
     const uint64_t *key = a.keys + kc * key_stride;
     for (int i = 0; i < a.L; ++i) {
@@ -322,14 +320,15 @@ __global__ void __launch_bounds__(NttShape<E>::kMaxThreads, 1) ks_fused_kernel(K
     ntt_run<E, false, false>(acc1, nullptr, u1, false, N, a.logN, iv, true, nullptr);
 }
 
-// Coefficients per thread for degree N: 16 up to N = 8192, 32 above
+// Coefficients per thread for degree N: 8 up to N = 8192 (measured best of
+// 8 / 16 / 32 on the CC-MM n=8192 key switches), 32 above
 // (MODPP_NTT_E = 8, 16 or 32 overrides where the thread count allows).
 int ntt_e_for(int N) {
     static const int forced = [] {
         const char *v = std::getenv("MODPP_NTT_E");
         return v ? std::atoi(v) : 0;
     }();
-    int e = (forced == 8 || forced == 16 || forced == 32) ? forced : (N <= 8192 ? 16 : 32);
+    int e = (forced == 8 || forced == 16 || forced == 32) ? forced : (N <= 8192 ? 8 : 32);
     if (e == 8 && N / 8 > NttShape<8>::kMaxThreads) e = 16;
     if (e == 16 && N / 16 > NttShape<16>::kMaxThreads) e = 32;
     return e;

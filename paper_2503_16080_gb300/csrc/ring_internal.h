@@ -17,6 +17,8 @@ struct NttPlane {
     const uint64_t *fwd_s;
     const uint64_t *inv;    // psi^-bitrev(i)
     const uint64_t *inv_s;
+    const ulonglong2 *fwd2; // (fwd[i], fwd_s[i]) pairs: one 16-byte load per twiddle
+    const ulonglong2 *inv2;
 };
 
 // Per-ciphertext tables of a gather: every table has period `per` over the
