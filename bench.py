@@ -63,6 +63,23 @@ def dist_info():
     return ws, rank, local
 
 
+def max_over_ranks(elapsed_ms: float, device) -> float:
+    """The slowest rank's timed-region length (the job's time); every rank
+    gets it.  One rank: unchanged."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([elapsed_ms], dtype=torch.float64, device=device)
+    if dist.is_available() and dist.is_initialized() and dist.get_world_size() > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_step: float, steps: int, world: int, max_ms: float) -> float:
+    """Units all ranks processed (replicas: each rank runs the whole
+    workload) per second of the slowest rank, in tera-units."""
+    return units_per_step * steps * world / (max_ms * 1e-3) / 1e12
+
+
 def load_peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
@@ -246,12 +263,9 @@ def run_ours(args):
     if pkg.last_status() != 0:
         raise RuntimeError("device status word set during the timed region")
 
-    t = torch.tensor([elapsed_ms], dtype=torch.float64, device=dev)
-    if ws > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    max_ms = float(t.item())
+    max_ms = max_over_ranks(elapsed_ms, dev)
     ms_per_step = max_ms / args.steps
-    value = mod_ops_per_step() * args.steps * ws / (max_ms * 1e-3) / 1e12
+    value = whole_job_rate(mod_ops_per_step(), args.steps, ws, max_ms)
 
     line = None
     if rank == 0 and args.quick:
