@@ -143,3 +143,54 @@ def test_pc_argument_errors(api):
     assert L.pc_mm(4, 4, 4, 1, 1, 1, 1, 1, pr.ctypes.data, 17, 0, 256, 1 << 20, None) == -1
     assert L.pc_mv(4, 4, 4, 1, None, 1, 1, 1, pr.ctypes.data, 1, 0, 256, 1 << 20, None) == -1
     assert L.modpp_status_read(None, None) == -3
+
+
+# ---------------------------------------------------------------- ring / CC-MM ABI (host side)
+
+def _ring_lib(api):
+    from paper_2503_16080_gb300 import ring
+    return ring._register()
+
+
+def test_ring_bytes_sizes(api):
+    L = _ring_lib(api)
+    assert L.modpp_ring_bytes(16, 3) > 0
+    assert L.modpp_ring_bytes(8192, 4) > L.modpp_ring_bytes(4096, 4) > 0
+    for N, Lc in ((12, 3), (1, 3), (32768, 3), (16, 0), (16, 17)):
+        assert L.modpp_ring_bytes(N, Lc) == 0, (N, Lc)
+
+
+def test_ring_create_validates_before_touching_memory(api):
+    import ctypes
+    L = _ring_lib(api)
+    good = synth.ntt_primes(50, 3) + synth.ntt_primes(60, 1)
+    h = ctypes.c_void_p()
+
+    def create(N, primes, mem=None, nbytes=0):
+        arr = np.ascontiguousarray(primes, dtype=np.uint64)
+        return L.modpp_ring_create(N, len(primes) - 1, arr.ctypes.data, mem, nbytes, None,
+                                   ctypes.byref(h))
+    assert create(12, good) == -1                      # N not a power of two
+    assert create(16, good[:3] + [good[0]]) == -2      # repeated prime
+    assert create(16, good[:3] + [good[3] + 2]) == -2  # not prime / not 1 mod 2N
+    assert create(16, good[:3] + [(1 << 62) + 1]) == -2
+    nt = [q for q in synth.ntt_primes(40, 4, two_adicity=1) if (q - 1) % 32 != 0]
+    if nt:
+        assert create(16, good[:3] + nt[:1]) == -2     # prime, but not 1 mod 2N
+    assert create(16, good) == -3                      # valid, but no memory given
+    assert not h.value
+
+
+def test_wide_path_setting_and_plan(api):
+    q = synth.ntt_primes(50, 4)
+    api.set_wide_path("auto")
+    assert api.get_wide_path() == 0
+    assert api.wide_plan_info(8192, q) == 23          # CRT form: 23 primes <= 89
+    assert api.wide_plan_info(16384, q) == 0          # no prime set: digit form
+    api.set_wide_path("digits")
+    try:
+        assert api.wide_plan_info(8192, q) == 0
+    finally:
+        api.set_wide_path("auto")
+    with pytest.raises(api.ModppError):
+        api.set_wide_path(3)

@@ -176,3 +176,33 @@ def test_ring_rejects_bad_arguments(lib_ready):
     with pytest.raises(ValueError):
         R.transpose(dev(np.zeros((2, 3, 8, 16), dtype=np.uint64)),
                     dev(np.zeros((16, 3, 2, 4, 16), dtype=np.uint64)))
+
+
+@pytest.mark.parametrize("N", [2, 4, 8])
+def test_transpose_small_degrees(oracle_mod, lib_ready, N):
+    s = synth.ternary(N, 7, N)
+    keys = C.aut_keys(oracle_mod, s, N, 5000 + N)
+    R = lib_ready.Ring(N, C.PRP)
+    L = len(C.PR)
+    dkeys = R.prepare_keys(dev(C.stack_keys(keys, N, L)))
+    cts = C.rand_cts(9 * N, N, N, C.PR)
+    got = host(R.transpose(dev(C.to_batch(cts)), dkeys))
+    assert np.array_equal(C.from_batch(got), oracle_mod.transpose(cts, keys, C.PRP))
+
+
+def test_cc_mm_two_prime_chain(oracle_mod, lib_ready):
+    # The shortest chain CC-MM accepts: L = 2 (one prime left after Rescale).
+    N = 16
+    prp = C.PR[:2] + [C.SP]
+    s = synth.ternary(21, 1, N)
+    keys = C.aut_keys(oracle_mod, s, N, 21000, prp)
+    rk = C.relin_key(oracle_mod, s, N, 210, prp)
+    R = lib_ready.Ring(N, prp)
+    dkeys = R.prepare_keys(dev(C.stack_keys(keys, N, 2)))
+    drk = R.prepare_keys(dev(rk[None]))
+    c1 = C.rand_cts(31, N, N, C.PR[:2])
+    c2 = C.rand_cts(32, N, N, C.PR[:2])
+    want, _ = oracle_mod.cc_mm(c1, c2, keys, rk, prp)
+    got = C.from_batch(host(R.cc_mm(dev(C.to_batch(c1)), dev(C.to_batch(c2)), dkeys, drk)))
+    assert got.shape == (N, 2, 1, N)
+    assert np.array_equal(got, want)
