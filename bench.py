@@ -568,8 +568,12 @@ def run_secondary(args):
             ops += 2.0 * dd * kk * nn * P
         plan = pkg.GroupedPlan(probs, tune=True)
         clocks.start()
-        ms_graph, kern = _timed(lambda: plan.run(graph=True), args.steps, args.warmup, stream, pkg)
+        ms_graph, _ = _timed(lambda: plan.run(graph=True), args.steps, args.warmup, stream, pkg)
         clk = clocks.stop()
+        # Per-kernel times of the same launches without the graph (events
+        # are not recorded inside a replayed graph).
+        ms_direct, kern = _timed(lambda: plan.run(graph=False), args.steps, args.warmup, stream,
+                                 pkg)
         outs = [torch.empty_like(C) for C in plan.outputs]
 
         def per_problem():
@@ -588,7 +592,10 @@ def run_secondary(args):
             "grouped_speedup": ms_loop / ms_graph,
             "grouped_equals_per_problem": same,
             "launches_grouped": 3, "launches_per_problem": 3 * 64,
-            "kernels_ms_grouped": {kname: v[0] / max(v[1], 1) for kname, v in kern.items()},
+            "plan_direct_ms": ms_direct,
+            "kernels_ms_per_step_grouped": {kname: v[0] / args.steps for kname, v in kern.items()},
+            "kernels_ms_per_step_per_problem": {kname: v[0] / args.steps
+                                                for kname, v in kern_loop.items()},
             "clocks": clk})
         plan.close()
     print(json.dumps(line))

@@ -104,14 +104,19 @@ static cudaError_t launch_group_kernels(const GroupSplitJob *sjobs, const int *s
                                         cudaStream_t st) {
     constexpr int NC = tile_cols(LMAX);
     if (s_blocks > 0) {
+        void *ev = prof_begin(MODPP_KERNEL_SPLIT, st);
         group_split_kernel<LMAX, DB, NC><<<static_cast<unsigned>(s_blocks), 256, 0, st>>>(
             sjobs, sblock_job);
+        prof_end(ev, st);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
     if (gp.num_tiles == 0) return cudaSuccess;
     CUtensorMap dummy{};
-    return launch_gemm_kernel<LMAX, DB, NC, true>(dummy, dummy, gp, num_sms, st);
+    void *ev = prof_begin(MODPP_KERNEL_GEMM, st);
+    const cudaError_t e = launch_gemm_kernel<LMAX, DB, NC, true>(dummy, dummy, gp, num_sms, st);
+    prof_end(ev, st);
+    return e;
 }
 
 template <int DB>
@@ -509,9 +514,11 @@ int plan_enqueue(modpp_group_plan *pl, cudaStream_t st) {
                 return MODPP_ERR_CUDA;
     }
     if (pl->u_blocks > 0) {
+        void *ev = prof_begin(MODPP_KERNEL_U16, st);
         group_u_to_f16_kernel<<<static_cast<unsigned>(pl->u_blocks), 256, 0, st>>>(
             reinterpret_cast<const GroupUJob *>(w + g.off_ujobs),
             reinterpret_cast<const int *>(w + g.off_ublk));
+        prof_end(ev, st);
         if (cudaGetLastError() != cudaSuccess) return MODPP_ERR_CUDA;
     }
     const int sms = sms_of_current_device();

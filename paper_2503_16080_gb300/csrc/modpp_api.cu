@@ -817,6 +817,13 @@ int modpp_status_read(void *ws, void *stream) {
 }  // extern "C"
 
 namespace modpp {
+void *prof_begin(int kernel, cudaStream_t st) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone)
+        return nullptr;
+    return timer_begin(kernel, st);
+}
+void prof_end(void *handle, cudaStream_t st) { timer_end(static_cast<EventPair *>(handle), st); }
 bool profile_active() {
     std::lock_guard<std::mutex> lock(g_prof_mu);
     return g_prof_on;

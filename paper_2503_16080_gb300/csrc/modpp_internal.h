@@ -157,6 +157,11 @@ inline PlaneConst make_plane_const(uint64_t q, int b, uint64_t *C, int64_t ldc) 
 
 // True while modpp_profile_enable(1) is in effect.
 bool profile_active();
+// Kernel timing hooks for other translation units (no-ops when profiling is
+// off or the stream is being captured): prof_begin returns a handle for
+// prof_end, or null.
+void *prof_begin(int kernel, cudaStream_t st);
+void prof_end(void *handle, cudaStream_t st);
 
 // Row blocks per band of the tile order.  Tiles run band by band: inside a
 // band the row block varies fastest, then the column block.  The concurrently
