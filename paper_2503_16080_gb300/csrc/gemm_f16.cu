@@ -7,7 +7,11 @@ namespace modpp {
 
 template <int DB>
 static cudaError_t launch_gemm_db(const CUtensorMap &tmU, const CUtensorMap &tmD,
-                                  const GemmParams &p, int digits, int num_sms, cudaStream_t s) {
+                                  const GemmParams &p, int digits, int num_sms, cudaStream_t s,
+                                  int nc) {
+    if (nc == 32 && digits == 5) return launch_gemm_kernel<5, DB, 32, false>(tmU, tmD, p, num_sms, s);
+    if (nc == 32 && digits == 6) return launch_gemm_kernel<6, DB, 32, false>(tmU, tmD, p, num_sms, s);
+    if (nc != 0 && nc != tile_cols(digits)) return cudaErrorInvalidValue;
     switch (digits) {
 #define MODPP_CASE(LL) \
     case LL: return launch_gemm_kernel<LL, DB, tile_cols(LL), false>(tmU, tmD, p, num_sms, s);
@@ -25,12 +29,12 @@ static cudaError_t launch_gemm_db(const CUtensorMap &tmU, const CUtensorMap &tmD
 }
 
 cudaError_t launch_gemm_f16(const CUtensorMap &tmU, const CUtensorMap &tmD, const GemmParams &p,
-                            int digits, int digit_bits, int num_sms, cudaStream_t s) {
+                            int digits, int digit_bits, int num_sms, cudaStream_t s, int nc) {
     if (p.num_tiles == 0) return cudaSuccess;
     switch (digit_bits) {
-        case 8: return launch_gemm_db<8>(tmU, tmD, p, digits, num_sms, s);
-        case 9: return launch_gemm_db<9>(tmU, tmD, p, digits, num_sms, s);
-        case 10: return launch_gemm_db<10>(tmU, tmD, p, digits, num_sms, s);
+        case 8: return launch_gemm_db<8>(tmU, tmD, p, digits, num_sms, s, nc);
+        case 9: return launch_gemm_db<9>(tmU, tmD, p, digits, num_sms, s, nc);
+        case 10: return launch_gemm_db<10>(tmU, tmD, p, digits, num_sms, s, nc);
         default: return cudaErrorInvalidValue;
     }
 }

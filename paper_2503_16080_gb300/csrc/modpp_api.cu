@@ -69,6 +69,7 @@ struct PlaneIn {
 struct F16Layout {
     int b = 0;
     int L = 0;
+    int nc = 0;  // tile columns
     int64_t kp = 0, n_blocks = 0, rows = 0;
     size_t off_u16 = 0, off_d = 0, total = 0;
 };
@@ -80,7 +81,8 @@ F16Layout f16_layout(int64_t d, int64_t k, int64_t n, const uint64_t *qs, int pl
         const int l = f16_digit_count(qs[i], lay.b);
         if (l > lay.L) lay.L = l;
     }
-    const int nc = tile_cols(lay.L);
+    const int nc = tile_cols_for(lay.L, n);
+    lay.nc = nc;
     lay.kp = (k + 7) / 8 * 8;
     lay.n_blocks = (n + nc - 1) / nc;
     lay.rows = static_cast<int64_t>(planes) * lay.n_blocks * lay.L * nc;
@@ -275,6 +277,7 @@ int run_f16(int64_t d, int64_t k, int64_t n, const void *U, int ukind, int64_t l
     sp.planes = planes;
     sp.digits = lay.L;
     sp.digit_bits = lay.b;
+    sp.nc = lay.nc;
     sp.D = D;
     const uint64_t thresh = f16_lift_threshold(lay.L, lay.b);
     for (int i = 0; i < planes; ++i) sp.sp[i] = SplitPlane{pl[i].A, pl[i].lda, pl[i].q, thresh};
@@ -287,7 +290,7 @@ int run_f16(int64_t d, int64_t k, int64_t n, const void *U, int ukind, int64_t l
     if (!make_map_f16(&tmU, U16, static_cast<uint64_t>(lay.kp), static_cast<uint64_t>(d), kBK, kBM))
         return MODPP_ERR_CUDA;
     if (!make_map_f16(&tmD, D, static_cast<uint64_t>(lay.kp), static_cast<uint64_t>(lay.rows), kBK,
-                      static_cast<uint32_t>(lay.L * tile_cols(lay.L))))
+                      static_cast<uint32_t>(lay.L * lay.nc)))
         return MODPP_ERR_CUDA;
 
     GemmParams gp{};
@@ -315,7 +318,7 @@ int run_f16(int64_t d, int64_t k, int64_t n, const void *U, int ukind, int64_t l
     const int sms = device_sms();
     if (sms <= 0) return MODPP_ERR_CUDA;
     ev = timer_begin(MODPP_KERNEL_GEMM, st);
-    rc = cuda_status(launch_gemm_f16(tmU, tmD, gp, lay.L, lay.b, sms, st));
+    rc = cuda_status(launch_gemm_f16(tmU, tmD, gp, lay.L, lay.b, sms, st, lay.nc));
     timer_end(ev, st);
     return rc;
 }
@@ -515,10 +518,11 @@ int run_f16_wide(int64_t d, int64_t k, int64_t n, const uint64_t *U, int64_t ldu
         if (rc) return rc;
         // f16 digits of A_j (the plane's own digit count; the layout holds the largest).
         const int L = f16_digit_count(q, lay.b);
-        const int nc = tile_cols(L);
+        const int nc = tile_cols_for(L, n);  // as f16_layout for this prime
         const int64_t nblk = (n + nc - 1) / nc;
         const int64_t rows = nblk * L * nc;
         SplitParams sp{};
+        sp.nc = nc;
         sp.k = static_cast<int>(k);
         sp.n = static_cast<int>(n);
         sp.kp = static_cast<int>(lay.kp);
@@ -562,7 +566,7 @@ int run_f16_wide(int64_t d, int64_t k, int64_t n, const uint64_t *U, int64_t ldu
             gp.pc[0].wouts = host_shoup(w8, q);
             gp.pc[0].accumulate = i > 0 ? 1 : 0;
             EventPair *ev = timer_begin(MODPP_KERNEL_GEMM, st);
-            rc = cuda_status(launch_gemm_f16(tmU, tmD, gp, L, lay.b, sms, st));
+            rc = cuda_status(launch_gemm_f16(tmU, tmD, gp, L, lay.b, sms, st, nc));
             timer_end(ev, st);
             if (rc) return rc;
             w8 = host_mulmod(w8, 256 % q, q);

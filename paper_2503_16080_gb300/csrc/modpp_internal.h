@@ -19,6 +19,15 @@ constexpr int kBM = 128;             // output rows per tile (UMMA M)
 __host__ __device__ constexpr int tile_cols(int L) {
     return L <= 3 ? 64 : (L <= 5 ? 48 : (L == 6 ? 40 : 32));
 }
+// Tile columns for L digits and n output columns: thin outputs (n <= 64)
+// with L = 5 or 6 take 32-column tiles when that pads less than the default
+// width (PC-Mv's 32 columns: no padding instead of 8 wasted columns of 40).
+__host__ __device__ constexpr int tile_cols_for(int L, long long n) {
+    return ((L == 5 || L == 6) && n <= 64 &&
+            (n + 31) / 32 * 32 < (n + tile_cols(L) - 1) / tile_cols(L) * tile_cols(L))
+               ? 32
+               : tile_cols(L);
+}
 // Grouped launches share one column width for all problems, whose digit
 // counts Lp <= L vary: every Lp * cols must be a multiple of 16.
 __host__ __device__ constexpr int grouped_tile_cols(int L) {
@@ -93,6 +102,7 @@ struct SplitPlane {
 
 struct SplitParams {
     int k, n, kp, n_blocks, planes, digits, digit_bits;
+    int nc;             // tile columns (tile_cols_for(digits, n))
     __half *D;          // digit matrix: rows (plane, n_block, digit, col), kp columns
     SplitPlane sp[kMaxPlanes];
 };
@@ -187,7 +197,8 @@ cudaError_t launch_u64_to_i8_digits(const uint64_t *U, int64_t ldu, int d, int k
                                     uint64_t thresh, int digits, int8_t *out, cudaStream_t s);
 cudaError_t launch_split_digits(const SplitParams &p, cudaStream_t s);
 cudaError_t launch_gemm_f16(const CUtensorMap &tmU, const CUtensorMap &tmD, const GemmParams &p,
-                            int digits, int digit_bits, int num_sms, cudaStream_t s);
+                            int digits, int digit_bits, int num_sms, cudaStream_t s,
+                            int nc = 0);  // 0: tile_cols(digits)
 
 // FP64-limb (Strategy 1) helpers.
 struct Fp64SplitParams {

@@ -98,9 +98,8 @@ cudaError_t launch_u64_to_i8_digits(const uint64_t *U, int64_t ldu, int d, int k
 
 // ---------------------------------------------------------------- digits
 // One block per (64 inner indices, one column block, one plane).
-template <int L, int DB>
+template <int L, int DB, int NC = tile_cols(L)>
 __global__ void __launch_bounds__(256) split_digits_kernel(const __grid_constant__ SplitParams p) {
-    constexpr int NC = tile_cols(L);
     __shared__ __align__(16) __half tile[L * NC * kSplitRow];
     const int plane = blockIdx.z;
     const int nb = blockIdx.y;
@@ -113,6 +112,15 @@ __global__ void __launch_bounds__(256) split_digits_kernel(const __grid_constant
 
 template <int DB>
 static bool launch_split_db(const SplitParams &p, dim3 grid, cudaStream_t s) {
+    if (p.nc == 32 && p.digits == 5) {
+        split_digits_kernel<5, DB, 32><<<grid, 256, 0, s>>>(p);
+        return true;
+    }
+    if (p.nc == 32 && p.digits == 6) {
+        split_digits_kernel<6, DB, 32><<<grid, 256, 0, s>>>(p);
+        return true;
+    }
+    if (p.nc != 0 && p.nc != tile_cols(p.digits)) return false;
     switch (p.digits) {
         case 1: split_digits_kernel<1, DB><<<grid, 256, 0, s>>>(p); return true;
         case 2: split_digits_kernel<2, DB><<<grid, 256, 0, s>>>(p); return true;
