@@ -144,7 +144,9 @@ __device__ __forceinline__ TileJob tile_job(int tile, const CUtensorMap *tmU,
 // p < 256 in balanced form, the host guarantees |sum| < 2^24 over the whole
 // inner dimension (no chunks), and the epilogue stores the balanced residue
 // of each output modulo p as int8 (the multi-modular products of
-// rns_wide.cu).  Each plane then has its own U rows (p.u_per_plane).
+// rns_wide.cu).  Each plane then has its own U rows (p.u_per_plane).  With
+// the plane's `accumulate` set, the residues already stored are added (the
+// inner dimension in chunks).
 template <int L, int DB, int NC, bool GROUPED, int MODE = 0>
 __global__ void __launch_bounds__(kThreads, 1)
     gemm_f16_kernel(const __grid_constant__ CUtensorMap tmU_param,
@@ -306,6 +308,25 @@ __global__ void __launch_bounds__(kThreads, 1)
                     tmem_wait_ld();
                     // balanced residue of an exact integer |v| < 2^24 modulo p:
                     // v - p * rint(v / p), corrected by at most one p
+                    // accumulate: add the residues already stored (an earlier
+                    // chunk of the inner dimension) and reduce again
+                    uint32_t old[4] = {0, 0, 0, 0};
+                    const bool acc = pc.accumulate && row < j.d;
+                    if (acc) {
+                        if (vec && col0 + c0 + 16 <= j.n) {
+                            const uint4 o = *reinterpret_cast<const uint4 *>(out + c0);
+                            old[0] = o.x;
+                            old[1] = o.y;
+                            old[2] = o.z;
+                            old[3] = o.w;
+                        } else {
+#pragma unroll
+                            for (int c = 0; c < 16; ++c)
+                                if (col0 + c0 + c < j.n)
+                                    old[c >> 2] |= (static_cast<uint32_t>(out[c0 + c]) & 0xffu)
+                                                   << (8 * (c & 3));
+                        }
+                    }
                     uint32_t w[4] = {0, 0, 0, 0};
 #pragma unroll
                     for (int c = 0; c < 16; ++c) {
@@ -313,6 +334,11 @@ __global__ void __launch_bounds__(kThreads, 1)
                         int x = __float2int_rn(f) - pr * __float2int_rn(f * pinv);
                         if (2 * x > pr) x -= pr;
                         if (2 * x < -pr) x += pr;
+                        if (acc) {
+                            x += static_cast<int8_t>((old[c >> 2] >> (8 * (c & 3))) & 0xffu);
+                            if (2 * x > pr) x -= pr;
+                            if (2 * x < -pr) x += pr;
+                        }
                         w[c >> 2] |= (static_cast<uint32_t>(x) & 0xffu) << (8 * (c & 3));
                     }
                     if (row < j.d) {

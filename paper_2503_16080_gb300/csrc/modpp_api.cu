@@ -185,15 +185,15 @@ EncodeTiledFn encode_fn() {
     return fn;
 }
 
-// 2-D f16 tensor [outer][inner] with swizzled boxes of box_inner x box_outer
-// (box_inner * 2 = kRowBytes, the swizzle span).  Elements outside the tensor
-// read as zero.
-bool make_map_f16(CUtensorMap *m, const void *base, uint64_t inner, uint64_t outer,
-                  uint32_t box_inner, uint32_t box_outer) {
+// 2-D f16 tensor [outer][inner] (rows of row_elems elements in memory) with
+// swizzled boxes of box_inner x box_outer (box_inner * 2 = kRowBytes, the
+// swizzle span).  Elements outside the tensor read as zero.
+bool make_map_f16_strided(CUtensorMap *m, const void *base, uint64_t inner, uint64_t outer,
+                          uint64_t row_elems, uint32_t box_inner, uint32_t box_outer) {
     EncodeTiledFn fn = encode_fn();
     if (!fn) return false;
     cuuint64_t dims[2] = {inner, outer};
-    cuuint64_t strides[1] = {inner * 2};
+    cuuint64_t strides[1] = {row_elems * 2};
     cuuint32_t box[2] = {box_inner, box_outer};
     cuuint32_t estr[2] = {1, 1};
     return fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2, const_cast<void *>(base), dims, strides, box,
@@ -201,6 +201,11 @@ bool make_map_f16(CUtensorMap *m, const void *base, uint64_t inner, uint64_t out
               kRowBytes == 128 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B,
               CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) ==
            CUDA_SUCCESS;
+}
+
+bool make_map_f16(CUtensorMap *m, const void *base, uint64_t inner, uint64_t outer,
+                  uint32_t box_inner, uint32_t box_outer) {
+    return make_map_f16_strided(m, base, inner, outer, inner, box_inner, box_outer);
 }
 
 int cuda_status(cudaError_t e) { return e == cudaSuccess ? MODPP_OK : MODPP_ERR_CUDA; }
@@ -427,7 +432,7 @@ WideLayout wide_layout(int64_t d, int64_t k, int64_t n, const uint64_t *qs, int 
         // (memory-bound): take it when it saves more than 10% of the products.
         if (mode == 2 || w.rp.R * 11 < digit_products * 10) {
             w.rns = true;
-            w.rl = rns_layout(d, k, n, w.rp.R);
+            w.rl = rns_layout(d, k, n, w.rp);
             w.total = w.rl.total;
             return w;
         }
@@ -454,12 +459,21 @@ int run_rns_wide(int64_t d, int64_t k, int64_t n, const uint64_t *U, int64_t ldu
     const RnsLayout &rl = wl.rl;
     const int sms = device_sms();
     if (sms <= 0) return MODPP_ERR_CUDA;
-    CUtensorMap tmU, tmD;
-    if (!make_map_f16(&tmU, w + rl.off_u16, static_cast<uint64_t>(rl.kp),
-                      static_cast<uint64_t>(wl.rp.R) * d, kBK, kBM) ||
-        !make_map_f16(&tmD, w + rl.off_d, static_cast<uint64_t>(rl.kp),
-                      static_cast<uint64_t>(wl.rp.R) * rl.nblk * kRnsTileCols, kBK, kRnsTileCols))
-        return MODPP_ERR_CUDA;
+    // One pair of maps per chunk of the inner dimension: base at the chunk's
+    // first index, inner extent the chunk (reads past it are zero), row
+    // stride kp.
+    CUtensorMap tmU[2], tmD[2];
+    for (int ch = 0; ch < wl.rp.chunks; ++ch) {
+        const int64_t k0 = ch * wl.rp.chunk_len;
+        const int64_t len = std::min<int64_t>(wl.rp.chunk_len, rl.kp - k0);
+        if (!make_map_f16_strided(&tmU[ch], w + rl.off_u16 + k0 * 2, static_cast<uint64_t>(len),
+                                  static_cast<uint64_t>(wl.rp.R) * d,
+                                  static_cast<uint64_t>(rl.kp), kBK, kBM) ||
+            !make_map_f16_strided(&tmD[ch], w + rl.off_d + k0 * 2, static_cast<uint64_t>(len),
+                                  static_cast<uint64_t>(wl.rp.R) * rl.nblk * kRnsTileCols,
+                                  static_cast<uint64_t>(rl.kp), kBK, kRnsTileCols))
+            return MODPP_ERR_CUDA;
+    }
     for (int j = 0; j < P; ++j) {
         for (int op = 0; op < (A2 ? 2 : 1); ++op) {
             const uint64_t *A = (op == 0 ? A1 : A2) + static_cast<int64_t>(j) * strideA;

@@ -137,8 +137,9 @@ __global__ void __launch_bounds__(256) rns_split_a_kernel(const uint64_t *__rest
     }
 }
 
-// C[r][c] = X mod q from the R balanced residues res[i][r][c] (int8, plane
-// stride d * n, row stride n).  Per small prime, y = r c_i mod p_i and
+// C[r][c] = X mod q from the R balanced residues res[ch][i][r][c] (int8,
+// plane stride d * n, row stride n; the chunks' residues of one prime add).
+// Per small prime, y = r c_i mod p_i and
 // y / p_i come from shared-memory tables indexed by r; the sum
 // S = sum_i y_i w_i is kept as two 64-bit halves, S = S_hi 2^32 + S_lo with
 // w_i = w_hi 2^32 + w_lo (y_i w_lo < 2^40, y_i w_hi < 2^38: no overflow for
@@ -173,23 +174,31 @@ __global__ void __launch_bounds__(256) rns_crt_kernel(const int8_t *__restrict__
             shi[v] = 0;
             F[v] = 0.f;
         }
-        for (int i = 0; i < cr.R; ++i) {
-            int8_t r[V];
-            if constexpr (V == 4) {
-                const int w = *reinterpret_cast<const int *>(res + i * total + e0);
+        // Residue words in batches of 8 primes: eight loads in flight, then
+        // their sums.
+        for (int i0 = 0; i0 < cr.R; i0 += 8) {
+            uint32_t words[8];
 #pragma unroll
-                for (int v = 0; v < 4; ++v) r[v] = static_cast<int8_t>((w >> (8 * v)) & 0xff);
-            } else {
-                r[0] = res[i * total + e0];
+            for (int u = 0; u < 8; ++u) {
+                const int i = i0 + u;
+                if (i >= cr.R) break;
+                const int8_t *rp = res + static_cast<int64_t>(i) * total + e0;
+                words[u] = V == 4 ? *reinterpret_cast<const uint32_t *>(rp)
+                                  : static_cast<uint32_t>(static_cast<uint8_t>(rp[0]));
             }
-            const uint32_t wl = cr.wlo[i], wh = cr.whi[i];
 #pragma unroll
-            for (int v = 0; v < V; ++v) {
-                const int idx = static_cast<int>(r[v]) + 128;
-                const uint32_t y = ytab[i][idx];
-                slo[v] += static_cast<uint64_t>(y) * wl;
-                shi[v] += static_cast<uint64_t>(y) * wh;
-                F[v] += ftab[i][idx];
+            for (int u = 0; u < 8; ++u) {
+                const int i = i0 + u;
+                if (i >= cr.R) break;
+                const uint32_t wl = cr.wlo[i], wh = cr.whi[i];
+#pragma unroll
+                for (int v = 0; v < V; ++v) {
+                    const int idx = static_cast<int8_t>((words[u] >> (8 * v)) & 0xffu) + 128;
+                    const uint32_t y = ytab[i][idx];
+                    slo[v] += static_cast<uint64_t>(y) * wl;
+                    shi[v] += static_cast<uint64_t>(y) * wh;
+                    F[v] += ftab[i][idx];
+                }
             }
         }
 #pragma unroll
@@ -228,39 +237,67 @@ bool small_prime(int p) {
 
 }  // namespace
 
-bool rns_choose(int64_t k, const uint64_t *qs, int P, RnsPrimes *out) {
-    if (k <= 0 || P < 1) return false;
-    // Largest residue magnitude B with k B^2 < 2^24, capped so residues fit int8.
-    int64_t B = static_cast<int64_t>(std::floor(std::sqrt(static_cast<double>((1 << 24) - 1) /
-                                                          static_cast<double>(k))));
-    while (B > 0 && k * B * B >= (int64_t(1) << 24)) --B;
-    if (B > 125) B = 125;
-    if (B < 1) return false;
-    uint64_t qmax = 0;
-    for (int j = 0; j < P; ++j) qmax = qs[j] > qmax ? qs[j] : qmax;
-    // Need M >= 2.8 k ((qmax - 1) / 2)^2 (then |X| / M < 0.36).
-    const long double need = std::log2(2.8L) + std::log2(static_cast<long double>(k)) +
-                             2.0L * std::log2(static_cast<long double>((qmax - 1) / 2 + 1));
-    RnsPrimes r{};
+namespace {
+// Primes below 2B+1, largest first, until their product reaches 2^need.
+bool pick_primes(int64_t B, long double need, RnsPrimes *r) {
     long double have = 0;
+    r->R = 0;
     for (int p = static_cast<int>(2 * B + 1); p >= 3 && have < need; --p) {
         if (!small_prime(p)) continue;
-        if (r.R == kMaxRnsPrimes) return false;
-        RnsPrime &pp = r.p[r.R++];
+        if (r->R == kMaxRnsPrimes) return false;
+        RnsPrime &pp = r->p[r->R++];
         pp.p = static_cast<uint32_t>(p);
         pp.mag = static_cast<uint32_t>((uint64_t(1) << 32) / static_cast<uint64_t>(p));
         pp.t21 = static_cast<uint32_t>((uint64_t(1) << 21) % static_cast<uint64_t>(p));
         pp.t42 = static_cast<uint32_t>((uint64_t(1) << 42) % static_cast<uint64_t>(p));
         have += std::log2(static_cast<long double>(p));
     }
-    if (have < need) return false;
-    *out = r;
-    return true;
+    return have >= need;
+}
+// Largest B with len B^2 < 2^24, capped.
+int64_t residue_bound(int64_t len, int64_t cap) {
+    int64_t B = static_cast<int64_t>(std::floor(std::sqrt(static_cast<double>((1 << 24) - 1) /
+                                                          static_cast<double>(len))));
+    while (B > 0 && len * B * B >= (int64_t(1) << 24)) --B;
+    return B > cap ? cap : B;
+}
+}  // namespace
+
+bool rns_choose(int64_t k, const uint64_t *qs, int P, RnsPrimes *out) {
+    if (k <= 0 || P < 1) return false;
+    uint64_t qmax = 0;
+    for (int j = 0; j < P; ++j) qmax = qs[j] > qmax ? qs[j] : qmax;
+    // Need M >= 2.8 k ((qmax - 1) / 2)^2 (then |X| / M < 0.36).
+    const long double need = std::log2(2.8L) + std::log2(static_cast<long double>(k)) +
+                             2.0L * std::log2(static_cast<long double>((qmax - 1) / 2 + 1));
+    RnsPrimes one{}, two{};
+    bool ok1 = false, ok2 = false;
+    const int64_t B1 = residue_bound(k, 125);
+    if (B1 >= 1) ok1 = pick_primes(B1, need, &one);
+    one.chunks = 1;
+    one.chunk_len = k;
+    if (k > 64) {
+        const int64_t len = ((k + 1) / 2 + 63) / 64 * 64;
+        const int64_t B2 = residue_bound(len, 63);
+        if (B2 >= 1) ok2 = pick_primes(B2, need, &two);
+        two.chunks = 2;
+        two.chunk_len = len;
+    }
+    if (ok2 && (!ok1 || two.R < one.R)) {
+        *out = two;
+        return true;
+    }
+    if (ok1) {
+        *out = one;
+        return true;
+    }
+    return false;
 }
 
 RnsCrt rns_crt_consts(const RnsPrimes &pr, uint64_t q) {
     RnsCrt c{};
     c.R = pr.R;
+    c.chunks = 1;  // later chunks add into the first chunk's residues in the GEMM epilogue
     c.q = q;
     uint64_t mq = 1 % q;
     for (int i = 0; i < pr.R; ++i) mq = host_mulmod_u(mq, pr.p[i].p, q);
@@ -286,7 +323,8 @@ RnsCrt rns_crt_consts(const RnsPrimes &pr, uint64_t q) {
     return c;
 }
 
-RnsLayout rns_layout(int64_t d, int64_t k, int64_t n, int R) {
+RnsLayout rns_layout(int64_t d, int64_t k, int64_t n, const RnsPrimes &pr) {
+    const int R = pr.R;
     RnsLayout l{};
     l.kp = (k + 7) / 8 * 8;
     l.nblk = (n + kRnsNC - 1) / kRnsNC;
@@ -325,37 +363,44 @@ int rns_split(int64_t d, int64_t k, int64_t n, const uint64_t *U, int64_t ldu, c
 }
 
 int rns_gemm(int64_t d, int64_t k, int64_t n, const RnsPrimes &pr, const RnsLayout &lay,
-             uint8_t *ws, int *status, uint64_t timeout_ns, int num_sms, const CUtensorMap &tmU,
-             const CUtensorMap &tmD, cudaStream_t st) {
+             uint8_t *ws, int *status, uint64_t timeout_ns, int num_sms, const CUtensorMap *tmU,
+             const CUtensorMap *tmD, cudaStream_t st) {
     int8_t *res = reinterpret_cast<int8_t *>(ws + lay.off_res);
-    GemmParams gp{};
-    gp.d = static_cast<int>(d);
-    gp.n = static_cast<int>(n);
-    gp.k = static_cast<int>(k);
-    gp.m_blocks = static_cast<int>((d + kBM - 1) / kBM);
-    gp.n_blocks = static_cast<int>(lay.nblk);
-    gp.planes = pr.R;
-    gp.kb_total = static_cast<int>((k + kBK - 1) / kBK);
-    const int64_t tiles = static_cast<int64_t>(gp.m_blocks) * gp.n_blocks * pr.R;
-    if (tiles >= (int64_t(1) << 31)) return -4;
-    gp.num_tiles = static_cast<int>(tiles);
-    gp.band_m = band_rows(gp.m_blocks, lay.kp);
-    gp.u_per_plane = 1;
-    gp.status = status;
-    gp.timeout_ns = timeout_ns;
-    for (int i = 0; i < pr.R; ++i) {
-        PlaneConst &pc = gp.pc[i];
-        pc.q = pr.p[i].p;
-        const float pinv = 1.0f / static_cast<float>(pr.p[i].p);
-        uint32_t bits;
-        std::memcpy(&bits, &pinv, sizeof(bits));
-        pc.mu = bits;  // mode 1: binary32 bits of 1/p
-        pc.C = reinterpret_cast<uint64_t *>(res + static_cast<int64_t>(i) * d * n);
-        pc.ldc = n;
+    for (int ch = 0; ch < pr.chunks; ++ch) {
+        const int64_t k0 = ch * pr.chunk_len;
+        const int64_t len = std::min(pr.chunk_len, k - k0);
+        GemmParams gp{};
+        gp.d = static_cast<int>(d);
+        gp.n = static_cast<int>(n);
+        gp.k = static_cast<int>(len);
+        gp.m_blocks = static_cast<int>((d + kBM - 1) / kBM);
+        gp.n_blocks = static_cast<int>(lay.nblk);
+        gp.planes = pr.R;
+        gp.kb_total = static_cast<int>((len + kBK - 1) / kBK);
+        const int64_t tiles = static_cast<int64_t>(gp.m_blocks) * gp.n_blocks * pr.R;
+        if (tiles >= (int64_t(1) << 31)) return -4;
+        gp.num_tiles = static_cast<int>(tiles);
+        gp.band_m = band_rows(gp.m_blocks, lay.kp);
+        gp.u_per_plane = 1;
+        gp.status = status;
+        gp.timeout_ns = timeout_ns;
+        for (int i = 0; i < pr.R; ++i) {
+            PlaneConst &pc = gp.pc[i];
+            pc.q = pr.p[i].p;
+            const float pinv = 1.0f / static_cast<float>(pr.p[i].p);
+            uint32_t bits;
+            std::memcpy(&bits, &pinv, sizeof(bits));
+            pc.mu = bits;  // mode 1: binary32 bits of 1/p
+            // every chunk adds into the same residue plane
+            pc.C = reinterpret_cast<uint64_t *>(res + static_cast<int64_t>(i) * d * n);
+            pc.ldc = n;
+            pc.accumulate = ch > 0 ? 1 : 0;
+        }
+        if (launch_gemm_kernel<1, 9, kRnsNC, false, 1>(tmU[ch], tmD[ch], gp, num_sms, st) !=
+            cudaSuccess)
+            return -5;
     }
-    return launch_gemm_kernel<1, 9, kRnsNC, false, 1>(tmU, tmD, gp, num_sms, st) == cudaSuccess
-               ? 0
-               : -5;
+    return 0;
 }
 
 int rns_crt(int64_t d, int64_t n, uint64_t *C, int64_t ldc, uint64_t q, const RnsPrimes &pr,

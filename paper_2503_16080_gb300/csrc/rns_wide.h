@@ -18,11 +18,14 @@ struct RnsPrime {
 };
 struct RnsPrimes {
     int R;
+    int chunks;         // the inner dimension runs as 1 or 2 products (chunks of chunk_len)
+    int64_t chunk_len;  // multiple of 64 when chunks > 1
     RnsPrime p[kMaxRnsPrimes];
 };
 // Constants of the CRT recombination modulo one chain prime q.
 struct RnsCrt {
     int R;
+    int chunks;                   // residue planes per prime, summed before the CRT
     uint64_t q;
     uint64_t mq, mqs;             // M mod q and its Shoup quotient
     int p[kMaxRnsPrimes];
@@ -38,13 +41,16 @@ struct RnsLayout {
     size_t off_u16, off_d, off_res, total;
 };
 
-// Small primes for inner dimension k and the chain primes qs: residues
-// bounded by B with k B^2 < 2^24 (B <= 125), product M >= 2.8 k ((q-1)/2)^2.
-// False when no such set of at most kMaxRnsPrimes primes exists.
+// Small primes for inner dimension k and the chain primes qs, product
+// M >= 2.8 k ((q-1)/2)^2.  The inner dimension runs in one product per prime
+// (residues |r| <= B with k B^2 < 2^24, B <= 125) or in two halves
+// (len B^2 < 2^24 per half, B <= 63 so the two int8 residues add within
+// int8), whichever needs fewer primes.  False when no such set of at most
+// kMaxRnsPrimes primes exists.
 bool rns_choose(int64_t k, const uint64_t *qs, int P, RnsPrimes *out);
 RnsCrt rns_crt_consts(const RnsPrimes &pr, uint64_t q);
 // Workspace of one chain prime's products (reused across chain primes).
-RnsLayout rns_layout(int64_t d, int64_t k, int64_t n, int R);
+RnsLayout rns_layout(int64_t d, int64_t k, int64_t n, const RnsPrimes &pr);
 // Rows of the U map (R * d) and of the residue matrix map (R * nblk * 256).
 constexpr int kRnsTileCols = 256;
 // The three passes of C = U * A mod q for one chain prime (U d x k, A k x n
@@ -55,9 +61,11 @@ constexpr int kRnsTileCols = 256;
 int rns_split(int64_t d, int64_t k, int64_t n, const uint64_t *U, int64_t ldu, const uint64_t *A,
               int64_t lda, uint64_t q, const RnsPrimes &pr, const RnsLayout &lay, uint8_t *ws,
               bool split_u, cudaStream_t st);
+// tmU / tmD: one pair of maps per chunk (base at the chunk's first inner
+// index, inner extent the chunk's length).
 int rns_gemm(int64_t d, int64_t k, int64_t n, const RnsPrimes &pr, const RnsLayout &lay,
-             uint8_t *ws, int *status, uint64_t timeout_ns, int num_sms, const CUtensorMap &tmU,
-             const CUtensorMap &tmD, cudaStream_t st);
+             uint8_t *ws, int *status, uint64_t timeout_ns, int num_sms, const CUtensorMap *tmU,
+             const CUtensorMap *tmD, cudaStream_t st);
 int rns_crt(int64_t d, int64_t n, uint64_t *C, int64_t ldc, uint64_t q, const RnsPrimes &pr,
             const RnsLayout &lay, uint8_t *ws, cudaStream_t st);
 

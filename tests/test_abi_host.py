@@ -185,7 +185,7 @@ def test_wide_path_setting_and_plan(api):
     q = synth.ntt_primes(50, 4)
     api.set_wide_path("auto")
     assert api.get_wide_path() == 0
-    assert api.wide_plan_info(8192, q) == 23          # CRT form: 23 primes <= 89
+    assert api.wide_plan_info(8192, q) == 18          # CRT form: two halves, 18 primes <= 127
     assert api.wide_plan_info(16384, q) == 0          # no prime set: digit form
     api.set_wide_path("digits")
     try:

@@ -170,10 +170,13 @@ def test_wide_extremes(mp, oracle_mod, wide_path):
     assert np.array_equal(got2[0], oracle_mod.mod_pp_mm_residues(U2[0], A2[0].astype(np.uint64), q))
 
 
-@pytest.mark.parametrize("k", [8192, 4100])
+@pytest.mark.parametrize("k", [8192, 6000, 4100])
 def test_wide_crt_largest_products(mp, oracle_mod, k):
-    # The CRT form at its bound: |X| = k ((q-1)/2)^2 for 50-bit primes (23 small
-    # primes at k = 8192), both signs, plus random rows; against the oracle.
+    # k = 8192 and 6000 run the inner dimension in two halves (the second
+    # ragged at 6000), 4100 in one.
+    # The CRT form at its bound: |X| = k ((q-1)/2)^2 for 50-bit primes (18 small
+    # primes over two halves of the inner dimension at k = 8192), both signs,
+    # plus random rows; against the oracle.
     q = P50[0]
     mp.set_wide_path("crt")
     try:
