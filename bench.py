@@ -679,18 +679,21 @@ def run_ccmm(args):
     peaks, peak_src = load_peaks()
     crt_primes = pkg.wide_plan_info(Nr, primes)
     if crt_primes:
-        # CRT form: one launch runs the R small-prime products of one
-        # (chain prime, right operand) pair.
+        # CRT form: R small-prime products of [A;B] (2N x N) times an N x N
+        # operand per (chain prime, right operand), over pieces of k.
         products = crt_primes
         form = {"form": "crt", "small_primes": crt_primes}
     else:
         LU = -(-(max(primes) - 1).bit_length() // 8)
         LA = pkg.plan_info(Nr, primes[0])["digits"]
-        products = LA  # one launch: one 8-bit digit plane of U times LA digits
+        products = LU * LA
         form = {"form": "digits", "u_digit_planes": LU, "a_digits": LA}
-    gemm_flops = 2.0 * (2 * Nr) * Nr * Nr * products
+    # Tensor work of all GEMM launches of one CC-MM: 2 right operands x L
+    # chain primes x `products` products of 2N x N x N.
+    total_flops = 2.0 * (2 * Nr) * Nr * Nr * products * 2 * L
+    gemm_flops = total_flops / max(gemm_n, 1)
     g_avg = gemm_ms / max(gemm_n, 1)
-    achieved = gemm_flops / (g_avg * 1e-3) / 1e12
+    achieved = total_flops / (gemm_ms * 1e-3) / 1e12
     peak = peaks["bf16_tflops_sustained"]
     modops = 2.0 * (2 * Nr) * Nr * (2 * Nr) * L
 

@@ -462,7 +462,7 @@ int run_rns_wide(int64_t d, int64_t k, int64_t n, const uint64_t *U, int64_t ldu
     // One pair of maps per chunk of the inner dimension: base at the chunk's
     // first index, inner extent the chunk (reads past it are zero), row
     // stride kp.
-    CUtensorMap tmU[2], tmD[2];
+    CUtensorMap tmU[kMaxRnsChunks], tmD[kMaxRnsChunks];
     for (int ch = 0; ch < wl.rp.chunks; ++ch) {
         const int64_t k0 = ch * wl.rp.chunk_len;
         const int64_t len = std::min<int64_t>(wl.rp.chunk_len, rl.kp - k0);

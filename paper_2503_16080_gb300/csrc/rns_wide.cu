@@ -270,28 +270,33 @@ bool rns_choose(int64_t k, const uint64_t *qs, int P, RnsPrimes *out) {
     // Need M >= 2.8 k ((qmax - 1) / 2)^2 (then |X| / M < 0.36).
     const long double need = std::log2(2.8L) + std::log2(static_cast<long double>(k)) +
                              2.0L * std::log2(static_cast<long double>((qmax - 1) / 2 + 1));
-    RnsPrimes one{}, two{};
-    bool ok1 = false, ok2 = false;
-    const int64_t B1 = residue_bound(k, 125);
-    if (B1 >= 1) ok1 = pick_primes(B1, need, &one);
-    one.chunks = 1;
-    one.chunk_len = k;
-    if (k > 64) {
-        const int64_t len = ((k + 1) / 2 + 63) / 64 * 64;
-        const int64_t B2 = residue_bound(len, 63);
-        if (B2 >= 1) ok2 = pick_primes(B2, need, &two);
-        two.chunks = 2;
-        two.chunk_len = len;
+    // One to kMaxRnsChunks pieces of the inner dimension (each piece's sums
+    // exact: len B^2 < 2^24; every piece after the first adds into the
+    // stored residues and reduces again, so |r| <= 125 holds for int8).
+    // Cost model: products R, plus 5% per extra piece (the epilogue's
+    // residue read-back and a shorter K loop per tile).
+    bool found = false;
+    double best = 0;
+    for (int c = 1; c <= kMaxRnsChunks; ++c) {
+        int64_t len = k;
+        if (c > 1) {
+            len = ((k + c - 1) / c + 63) / 64 * 64;
+            if ((c - 1) * len >= k) continue;  // fewer real pieces than c
+        }
+        const int64_t B = residue_bound(len, 125);
+        if (B < 1) continue;
+        RnsPrimes r{};
+        if (!pick_primes(B, need, &r)) continue;
+        r.chunks = c;
+        r.chunk_len = len;
+        const double cost = r.R * (1.0 + 0.05 * (c - 1));
+        if (!found || cost < best) {
+            *out = r;
+            best = cost;
+            found = true;
+        }
     }
-    if (ok2 && (!ok1 || two.R < one.R)) {
-        *out = two;
-        return true;
-    }
-    if (ok1) {
-        *out = one;
-        return true;
-    }
-    return false;
+    return found;
 }
 
 RnsCrt rns_crt_consts(const RnsPrimes &pr, uint64_t q) {

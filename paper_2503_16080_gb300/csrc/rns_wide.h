@@ -9,6 +9,7 @@
 namespace modpp {
 
 constexpr int kMaxRnsPrimes = 32;
+constexpr int kMaxRnsChunks = 4;  // pieces of the inner dimension
 
 struct RnsPrime {
     uint32_t p;    // odd prime < 256
@@ -18,7 +19,7 @@ struct RnsPrime {
 };
 struct RnsPrimes {
     int R;
-    int chunks;         // the inner dimension runs as 1 or 2 products (chunks of chunk_len)
+    int chunks;         // the inner dimension runs as 1..kMaxRnsChunks products (chunk_len each)
     int64_t chunk_len;  // multiple of 64 when chunks > 1
     RnsPrime p[kMaxRnsPrimes];
 };
@@ -42,11 +43,10 @@ struct RnsLayout {
 };
 
 // Small primes for inner dimension k and the chain primes qs, product
-// M >= 2.8 k ((q-1)/2)^2.  The inner dimension runs in one product per prime
-// (residues |r| <= B with k B^2 < 2^24, B <= 125) or in two halves
-// (len B^2 < 2^24 per half, B <= 63 so the two int8 residues add within
-// int8), whichever needs fewer primes.  False when no such set of at most
-// kMaxRnsPrimes primes exists.
+// M >= 2.8 k ((q-1)/2)^2.  The inner dimension runs in c = 1..kMaxRnsChunks
+// pieces of length len with len B^2 < 2^24 (residues |r| <= B <= 125),
+// choosing the c with the fewest primes (5% cost per extra piece).  False
+// when no set of at most kMaxRnsPrimes primes exists.
 bool rns_choose(int64_t k, const uint64_t *qs, int P, RnsPrimes *out);
 RnsCrt rns_crt_consts(const RnsPrimes &pr, uint64_t q);
 // Workspace of one chain prime's products (reused across chain primes).

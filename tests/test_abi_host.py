@@ -185,8 +185,9 @@ def test_wide_path_setting_and_plan(api):
     q = synth.ntt_primes(50, 4)
     api.set_wide_path("auto")
     assert api.get_wide_path() == 0
-    assert api.wide_plan_info(8192, q) == 18          # CRT form: two halves, 18 primes <= 127
-    assert api.wide_plan_info(16384, q) == 0          # no prime set: digit form
+    assert api.wide_plan_info(8192, q) == 16          # CRT form: four pieces of k, 16 primes
+    assert api.wide_plan_info(16384, q) == 19         # four pieces of 4096: primes <= 127
+    assert api.wide_plan_info(1 << 20, q) == 0        # no prime set: digit form
     api.set_wide_path("digits")
     try:
         assert api.wide_plan_info(8192, q) == 0

@@ -172,10 +172,10 @@ def test_wide_extremes(mp, oracle_mod, wide_path):
 
 @pytest.mark.parametrize("k", [8192, 6000, 4100])
 def test_wide_crt_largest_products(mp, oracle_mod, k):
-    # k = 8192 and 6000 run the inner dimension in two halves (the second
-    # ragged at 6000), 4100 in one.
-    # The CRT form at its bound: |X| = k ((q-1)/2)^2 for 50-bit primes (18 small
-    # primes over two halves of the inner dimension at k = 8192), both signs,
+    # k = 8192, 6000 and 4100 run the inner dimension in several pieces (the
+    # last one ragged at 6000 and 4100).
+    # The CRT form at its bound: |X| = k ((q-1)/2)^2 for 50-bit primes (16 small
+    # primes over four pieces of the inner dimension at k = 8192), both signs,
     # plus random rows; against the oracle.
     q = P50[0]
     mp.set_wide_path("crt")
