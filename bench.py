@@ -271,7 +271,8 @@ def run_ours(args):
     if rank == 0 and args.quick:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms_per_step, "quick": True,
-                "gemm_avg_ms": gemm_ms / max(gemm_n, 1), "split_avg_ms": split_ms / max(split_n, 1),
+                "gemm_ms_per_step": gemm_ms / args.steps, "split_ms_per_step": split_ms / args.steps,
+                "launches_per_step": (gemm_n + split_n + u16_n) / args.steps,
                 "u16_avg_ms": u16_ms / max(u16_n, 1), "n": N, "digit_bits": pkg.get_digit_bits()}
     elif rank == 0:
         peaks, peak_src = load_peaks()
@@ -279,17 +280,20 @@ def run_ours(args):
         planes = 2 * NPRIMES
         kp = (K + 7) // 8 * 8
         n_pad = (N + 31) // 32 * 32
-        # Algorithmic tensor FLOPs of one GEMM launch: each of the `digits`
-        # digit planes of every (prime, part) plane is one d x k x n product.
+        # Algorithmic tensor FLOPs of one step's GEMM launches: each of the
+        # `digits` digit planes of every (prime, part) plane is one d x k x n
+        # product.  Rates divide each kernel's work per step by its summed
+        # launch time per step.
         gemm_flops = 2.0 * D * K * N * planes * digits
-        # Algorithmic bytes of one launch: the f16 digit matrix and U16 read
-        # once, the u64 outputs written once.
-        gemm_bytes = (planes * K * digits * N * 2 + D * kp * 2 + planes * D * N * 8)
-        gemm_avg_s = gemm_ms / max(gemm_n, 1) * 1e-3
-        achieved = gemm_flops / gemm_avg_s / 1e12
+        # Algorithmic bytes of a step's GEMMs: the f16 digit matrix read once,
+        # U16 once per launch, the u64 outputs written once.
+        gemm_per_step = max(gemm_n, 1) / args.steps
+        gemm_bytes = (planes * K * digits * N * 2 + gemm_per_step * D * kp * 2 + planes * D * N * 8)
+        gemm_step_s = gemm_ms / args.steps * 1e-3
+        achieved = gemm_flops / gemm_step_s / 1e12
         peak = peaks["bf16_tflops_sustained"]
         split_bytes = planes * K * N * 8 + planes * (n_pad // 32) * digits * 32 * kp * 2
-        split_gbs = split_bytes / (split_ms / max(split_n, 1) * 1e-3) / 1e9
+        split_gbs = split_bytes / (split_ms / args.steps * 1e-3) / 1e9
 
         # FP64 comparison: cuBLAS DGEMM of U*M at the same n, and the FP64-limb path.
         Ud = U.to(torch.float64)
@@ -408,10 +412,12 @@ def run_ours(args):
                          "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                          "peak_source": f"{peak_src} bf16 dense sustained (f16 same rate)",
                          "traffic": GEMM_TRAFFIC_N4096 if (D, K, N) == (4096, 4096, 4096) else None,
-                         "traffic_algorithmic": gemm_bytes,
-                         "avg_launch_ms": gemm_avg_s * 1e3,
-                         "flops_per_launch": gemm_flops},
-            "split_kernel": {"avg_launch_ms": split_ms / max(split_n, 1),
+                         "traffic_algorithmic": gemm_bytes / gemm_per_step,
+                         "avg_launch_ms": gemm_step_s * 1e3 / gemm_per_step,
+                         "flops_per_launch": gemm_flops / gemm_per_step,
+                         "launches_per_step": gemm_per_step},
+            "split_kernel": {"ms_per_step": split_ms / args.steps,
+                             "launches_per_step": split_n / args.steps,
                              "achieved_gbs": split_gbs, "peak_gbs": peaks["hbm_gbs"],
                              "frac": split_gbs / peaks["hbm_gbs"]},
             "pc_mm_ms": ms_per_step,
@@ -499,7 +505,8 @@ def run_secondary(args):
         clk = clocks.stop()
         ops = 2.0 * d * k * n * 2 * P
         L = pkg.plan_info(k, primes[0])["digits"]
-        g_ms = kern["gemm"][0] / max(kern["gemm"][1], 1)
+        # GEMM time per step (all launches of a step).
+        g_ms = kern["gemm"][0] / args.steps
         gflops = ops * L
         line.update({
             "workload": args.workload, "value": ops / (ms * 1e-3) / 1e12, "ms_per_step": ms,
@@ -512,8 +519,9 @@ def run_secondary(args):
                          "achieved": gflops / (g_ms * 1e-3) / 1e12,
                          "peak": peaks["bf16_tflops_sustained"], "unit": "TFLOP/s",
                          "frac": gflops / (g_ms * 1e-3) / 1e12 / peaks["bf16_tflops_sustained"],
-                         "avg_launch_ms": g_ms},
-            "kernels_ms": {kname: v[0] / max(v[1], 1) for kname, v in kern.items()},
+                         "gemm_ms_per_step": g_ms,
+                         "launches_per_step": kern["gemm"][1] / args.steps},
+            "kernels_ms_per_step": {kname: v[0] / args.steps for kname, v in kern.items()},
             "hbm_gbs_U_stream": d * k * 2 / (g_ms * 1e-3) / 1e9,
             "fp64_matmul_ms": None, "clocks": clk})
         if args.workload == "pcmm16384":
@@ -542,7 +550,7 @@ def run_secondary(args):
             ms, kern = _timed(lambda: pkg.modpp_mm(U, A, [q], out=C), args.steps, args.warmup,
                               stream, pkg)
             L = pkg.plan_info(k, q)["digits"]
-            g_ms = kern["gemm"][0] / max(kern["gemm"][1], 1)
+            g_ms = kern["gemm"][0] / args.steps
             tf = 2.0 * d * k * n * L / (g_ms * 1e-3) / 1e12
             rows.append({"prime_bits": bits, "digits": L, "umma_n": L * {1: 64, 2: 64, 3: 64,
                                                                          4: 48, 5: 48, 6: 40}[L],
