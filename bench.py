@@ -4,9 +4,10 @@
 Workload (one step): row-format PC-MM with d = kct = N = 4096 and L = 3 RNS
 primes of 50 bits: U (4096 x 4096, N(0,1) quantised to int8 with scale 2^5)
 times the a-part and the b-part of 4096 ciphertexts of ring degree 4096, i.e.
-six exact Mod-PP-MMs C = U * X mod q_j.  The ciphertext coefficients are
-drawn uniform in [0, q_j): RLWE ciphertexts are indistinguishable from uniform,
-and the kernels' work does not depend on the values.
+six exact Mod-PP-MMs C = U * X mod q_j.  The ciphertexts are row-format RLWE
+encryptions of a message matrix M uniform in [-1, 1] at scale 2^40 (ternary
+secret, rounded Gaussian error of width 3.2); the line reports the decrypted
+result's error against the FP64 product U*M.
 
 Metric: exact Mod-PP-MM throughput in TOPS, counting 2*d*k*n multiply-adds
 mod q per (prime, part) plane (so one step is 2 * 4096^3 * 6 = 8.2e11 ops).
@@ -41,7 +42,8 @@ NPRIMES = 3
 PRIME_BITS = 50
 SEED = 2024
 WORKLOAD = ("PC-MM n=4096: U 4096x4096 int8 (N(0,1)*2^5) x row-RLWE ciphertext matrix "
-            "4096 cts of degree 4096, L=3 primes of 50 bits, a- and b-part (6 Mod-PP-MM planes)")
+            "4096 cts of degree 4096 (encryptions of M uniform in [-1,1] at scale 2^40), L=3 primes "
+            "of 50 bits, a- and b-part (6 Mod-PP-MM planes)")
 
 
 # DRAM bytes (read + write) of one gemm_f16_kernel launch of this workload, from
@@ -139,14 +141,90 @@ class ClockSampler:
                 "power_w_max": max(power) if power else None, "reasons": sorted(reasons)}
 
 
-def make_inputs(seed=SEED):
+DELTA = 2.0 ** 40     # CKKS scale of the encrypted message matrix
+DEC_TOL = 2.0 ** -20  # decoded-error tolerance, relative to the scale
+
+
+def _negacyclic_mod(X, s, q: int):
+    """Rows of X (R x N int64 residues mod q, a torch tensor) times the ring
+    element s (length-N int64 tensor, small entries) in Z_q[X]/(X^N + 1).
+
+    Harness arithmetic for encrypting and decrypting the workload (plain
+    PyTorch): the product is X @ S with S the N x N negacyclic matrix of s,
+    computed exactly as five FP64 matrix products of 12-bit limbs of X (each
+    limb product sums below 2^12 * N * max|s| < 2^53) and recombined by Horner
+    steps modulo q in int64."""
+    import torch
+    n = s.shape[0]
+    j = torch.arange(n, device=X.device)
+    diff = j[None, :] - j[:, None]                      # l - j
+    S = s[torch.remainder(diff, n)].to(torch.float64)
+    S = torch.where(diff >= 0, S, -S)
+    r = torch.zeros(X.shape, dtype=torch.int64, device=X.device)
+    for i in (4, 3, 2, 1, 0):
+        limb = ((X >> (12 * i)) & 0xFFF).to(torch.float64)
+        P = torch.matmul(limb, S).to(torch.int64)
+        r = torch.remainder(r * 4096 + P, q)
+    return r
+
+
+def make_inputs(seed=SEED, with_message=False):
+    """U (int8), the a-parts A (uniform mod q_j) and the b-parts
+    B = -A*s + round(Delta*M) + e (mod q_j) of row-format RLWE encryptions of a
+    message matrix M uniform in [-1, 1]: ciphertext t encrypts row t of M
+    under a ternary secret s with rounded-Gaussian error (sigma = 3.2)."""
     import numpy as np
+    import torch
     from paper_2503_16080_gb300 import synth
     primes = synth.ntt_primes(PRIME_BITS, NPRIMES)
     U = synth.quantised_normal_int8(seed, 1, (D, K))
     A = np.stack([synth.uniform_mod(seed, 10 + j, (K, N), q) for j, q in enumerate(primes)])
-    B = np.stack([synth.uniform_mod(seed, 20 + j, (K, N), q) for j, q in enumerate(primes)])
+    M = synth.uniform_unit(seed, 30, (K, N))
+    sec = synth.ternary(seed, 31, N)
+    e = synth.rounded_gaussian(seed, 32, (K, N))
+    dev = torch.device("cuda", torch.cuda.current_device()) if torch.cuda.is_available() \
+        else torch.device("cpu")
+    s_t = torch.from_numpy(sec).to(dev)
+    me = torch.from_numpy(np.floor(M * DELTA + 0.5).astype(np.int64) + e).to(dev)
+    B = np.empty_like(A)
+    for jq, q in enumerate(primes):
+        a_s = _negacyclic_mod(torch.from_numpy(A[jq].view(np.int64)).to(dev), s_t, q)
+        B[jq] = torch.remainder(me - a_s, q).cpu().numpy().view(np.uint64)
+    del me
+    if with_message:
+        return primes, U, A, B, M, sec
     return primes, U, A, B
+
+
+def decrypt_error(U, M, sec, Aout, Bout, primes, rows: int = 64):
+    """Decrypts sampled rows of (U*A, U*B) with the secret, lifts each
+    coefficient by CRT over q_0 q_1 to a centred integer, checks q_2 agrees,
+    decodes by 1/Delta and compares with the FP64 product U*M."""
+    import numpy as np
+    import torch
+    dev = Aout.device
+    idx = np.unique(np.linspace(0, Aout.shape[1] - 1, rows).astype(np.int64))
+    s_t = torch.from_numpy(sec).to(dev)
+    dec = []
+    for jq, q in enumerate(primes):
+        sel = torch.from_numpy(idx).to(dev)
+        xa = Aout[jq].view(torch.int64).index_select(0, sel)
+        xb = Bout[jq].view(torch.int64).index_select(0, sel)
+        dec.append(torch.remainder(_negacyclic_mod(xa, s_t, q) + xb, q).cpu().numpy())
+    q0, q1 = int(primes[0]), int(primes[1])
+    r0 = dec[0].astype(object)
+    r1 = dec[1].astype(object)
+    x = r0 + q0 * (((r1 - r0) * pow(q0, -1, q1)) % q1)
+    half = q0 * q1 // 2
+    x = np.where(x > half, x - q0 * q1, x)
+    agree = all(np.array_equal((x % int(q)).astype(np.uint64), dec[jq].astype(np.uint64))
+                for jq, q in enumerate(primes) if jq >= 2)
+    got = x.astype(np.float64) / DELTA
+    want = U[idx].astype(np.float64) @ M
+    err = float(np.max(np.abs(got - want)))
+    return {"rows_sampled": int(len(idx)), "max_abs_err": err, "tolerance": DEC_TOL,
+            "within_tolerance": err <= DEC_TOL, "other_primes_agree": bool(agree),
+            "reference": "FP64 U*M (numpy) on the same rows"}
 
 
 # ----------------------------------------------------------------- CPU oracle
@@ -221,7 +299,7 @@ def run_ours(args):
 
     if args.digit_bits:
         pkg.set_digit_bits(args.digit_bits)
-    primes, U_np, A_np, B_np = make_inputs()
+    primes, U_np, A_np, B_np, M_np, sec = make_inputs(with_message=True)
     U = torch.from_numpy(U_np).to(dev)
     A = torch.from_numpy(A_np).to(dev)
     B = torch.from_numpy(B_np).to(dev)
@@ -295,10 +373,13 @@ def run_ours(args):
         split_bytes = planes * K * N * 8 + planes * (n_pad // 32) * digits * 32 * kp * 2
         split_gbs = split_bytes / (split_ms / args.steps * 1e-3) / 1e9
 
+        # Decrypted result of the last timed step against the FP64 product U*M.
+        dec = decrypt_error(U_np, M_np, sec, Aout, Bout, primes)
+        ref_out = (Aout.view(torch.int64).clone(), Bout.view(torch.int64).clone())
+
         # FP64 comparison: cuBLAS DGEMM of U*M at the same n, and the FP64-limb path.
         Ud = U.to(torch.float64)
-        Md = torch.from_numpy(np.ascontiguousarray(
-            np.random.default_rng(SEED).uniform(-1, 1, (K, N)))).to(dev)
+        Md = torch.from_numpy(np.ascontiguousarray(M_np)).to(dev)
         for _ in range(2):
             torch.matmul(Ud, Md)
         torch.cuda.synchronize()
@@ -313,6 +394,7 @@ def run_ours(args):
         del Ud, Md
 
         fp64_ms = None
+        fp64_identical = None
         if not args.no_fp64:
             pkg.pc_mm(U, A, B, primes, out=(Aout, Bout), path="fp64")
             torch.cuda.synchronize()
@@ -322,6 +404,9 @@ def run_ours(args):
             g1.record(stream)
             torch.cuda.synchronize()
             fp64_ms = g0.elapsed_time(g1)
+            fp64_identical = bool(torch.equal(Aout.view(torch.int64), ref_out[0]) and
+                                  torch.equal(Bout.view(torch.int64), ref_out[1]))
+        del ref_out
 
         # End to end through the public call with host buffers: every step
         # copies its inputs in from pinned host memory, runs pc_mm and copies
@@ -424,6 +509,8 @@ def run_ours(args):
             "fp64_matmul_ms": dgemm_ms,
             "slowdown_vs_fp64_matmul": ms_per_step / dgemm_ms,
             "fp64_limb_pc_mm_ms": fp64_ms,
+            "fp64_limb_outputs_identical": fp64_identical,
+            "decrypt": dec,
             "int8_limb": "unavailable: tcgen05.mma kind::i8 is not supported on sm_103a (ptxas)",
             "cpu_baseline": {"value": cpu_tops, "unit": UNIT, "cores": cpu_threads,
                              "kind": "oracle",
