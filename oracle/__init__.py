@@ -378,8 +378,10 @@ def ks_keygen(s_old, s_new, primes_with_P, a, e) -> np.ndarray:
     pr = _u64(primes_with_P)
     so = np.ascontiguousarray(s_old, dtype=np.int64)
     sn = np.ascontiguousarray(s_new, dtype=np.int64)
-    _check(_load().or_ks_keygen(N, L, _ptr(pr), _ptr(so), _ptr(sn), _ptr(_u64(a)),
-                                _ptr(np.ascontiguousarray(e, dtype=np.int64)), _ptr(key)),
+    a64 = _u64(a)
+    e64 = np.ascontiguousarray(e, dtype=np.int64)
+    _check(_load().or_ks_keygen(N, L, _ptr(pr), _ptr(so), _ptr(sn), _ptr(a64), _ptr(e64),
+                                _ptr(key)),
            "ks_keygen")
     return key
 
@@ -389,7 +391,9 @@ def keyswitch(ct, key, primes_with_P) -> np.ndarray:
     ct = _u64(ct)
     _, L, N = ct.shape
     out = np.empty_like(ct)
-    _check(_load().or_keyswitch(N, L, _ptr(_u64(primes_with_P)), _ptr(_u64(key)), _ptr(ct),
+    pr = _u64(primes_with_P)
+    key64 = _u64(key)
+    _check(_load().or_keyswitch(N, L, _ptr(pr), _ptr(key64), _ptr(ct),
                                 _ptr(out)), "keyswitch")
     return out
 
@@ -399,7 +403,8 @@ def rescale(ct, primes) -> np.ndarray:
     ct = _u64(ct)
     _, L, N = ct.shape
     out = np.empty((2, L - 1, N), dtype=np.uint64)
-    _load().or_rescale(N, L, _ptr(_u64(primes[:L])), _ptr(ct), _ptr(out))
+    pr = _u64(primes[:L])
+    _load().or_rescale(N, L, _ptr(pr), _ptr(ct), _ptr(out))
     return out
 
 
