@@ -145,26 +145,53 @@ DELTA = 2.0 ** 40     # CKKS scale of the encrypted message matrix
 DEC_TOL = 2.0 ** -20  # decoded-error tolerance, relative to the scale
 
 
-def _negacyclic_mod(X, s, q: int):
-    """Rows of X (R x N int64 residues mod q, a torch tensor) times the ring
-    element s (length-N int64 tensor, small entries) in Z_q[X]/(X^N + 1).
+def _mul_pow2_mod(r, bits: int, q: int):
+    """(r * 2^bits) mod q for int64 residues 0 <= r < q < 2^60, in steps of at
+    most 3 bits so every intermediate product stays below 2^63."""
+    import torch
+    while bits > 0:
+        k = min(3, bits)
+        r = torch.remainder(r * (1 << k), q)
+        bits -= k
+    return r
 
-    Harness arithmetic for encrypting and decrypting the workload (plain
-    PyTorch): the product is X @ S with S the N x N negacyclic matrix of s,
-    computed exactly as five FP64 matrix products of 12-bit limbs of X (each
-    limb product sums below 2^12 * N * max|s| < 2^53) and recombined by Horner
-    steps modulo q in int64."""
+
+def negacyclic_matrix(s, dtype):
+    """The N x N matrix S of a ring element s of Z[X]/(X^N + 1): the row vector
+    of x's coefficients times S is the coefficient vector of x*s."""
     import torch
     n = s.shape[0]
-    j = torch.arange(n, device=X.device)
+    j = torch.arange(n, device=s.device)
     diff = j[None, :] - j[:, None]                      # l - j
-    S = s[torch.remainder(diff, n)].to(torch.float64)
-    S = torch.where(diff >= 0, S, -S)
-    r = torch.zeros(X.shape, dtype=torch.int64, device=X.device)
-    for i in (4, 3, 2, 1, 0):
-        limb = ((X >> (12 * i)) & 0xFFF).to(torch.float64)
-        P = torch.matmul(limb, S).to(torch.int64)
-        r = torch.remainder(r * 4096 + P, q)
+    S = s[torch.remainder(diff, n)].to(dtype)
+    return torch.where(diff >= 0, S, -S)
+
+
+def negacyclic_rows_mod(X, S, q: int, limb_bits: int = 12):
+    """Rows of X (R x N int64 residues mod q < 2^60) times the small ring
+    element whose negacyclic matrix is S, modulo q.
+
+    Harness arithmetic for encrypting, key generation and decryption (plain
+    PyTorch): X is cut into limb_bits-bit limbs, each limb times S is one
+    floating-point matrix product whose sums are integers of magnitude below
+    2^limb_bits * N * max|s| (exact: below 2^53 for FP64 S, below 2^24 for
+    FP32 S, whose products run as TF32 with limbs of at most 10 bits), and the
+    limb products are recombined by Horner steps modulo q in int64."""
+    import torch
+    nl = -(-int(q).bit_length() // limb_bits)
+    mask = (1 << limb_bits) - 1
+    tf32 = S.dtype == torch.float32
+    old = torch.backends.cuda.matmul.allow_tf32
+    torch.backends.cuda.matmul.allow_tf32 = tf32
+    try:
+        r = torch.zeros(X.shape, dtype=torch.int64, device=X.device)
+        for i in reversed(range(nl)):
+            limb = ((X >> (limb_bits * i)) & mask).to(S.dtype)
+            P = torch.matmul(limb, S).to(torch.int64)
+            del limb
+            r = torch.remainder(_mul_pow2_mod(r, limb_bits, q) + P, q)
+    finally:
+        torch.backends.cuda.matmul.allow_tf32 = old
     return r
 
 
@@ -184,16 +211,25 @@ def make_inputs(seed=SEED, with_message=False):
     e = synth.rounded_gaussian(seed, 32, (K, N))
     dev = torch.device("cuda", torch.cuda.current_device()) if torch.cuda.is_available() \
         else torch.device("cpu")
-    s_t = torch.from_numpy(sec).to(dev)
+    S = negacyclic_matrix(torch.from_numpy(sec).to(dev), torch.float64)
     me = torch.from_numpy(np.floor(M * DELTA + 0.5).astype(np.int64) + e).to(dev)
     B = np.empty_like(A)
     for jq, q in enumerate(primes):
-        a_s = _negacyclic_mod(torch.from_numpy(A[jq].view(np.int64)).to(dev), s_t, q)
+        a_s = negacyclic_rows_mod(torch.from_numpy(A[jq].view(np.int64)).to(dev), S, q)
         B[jq] = torch.remainder(me - a_s, q).cpu().numpy().view(np.uint64)
-    del me
+    del me, S
     if with_message:
         return primes, U, A, B, M, sec
     return primes, U, A, B
+
+
+def _precision_bits(want, err: float) -> float:
+    """Relative precision in bits, log2 max|M| - log2 max|M - M~| (the paper's
+    measure, Sec. 6), over the sampled entries."""
+    import math
+    import numpy as np
+    top = float(np.max(np.abs(want)))
+    return math.log2(top) - math.log2(err) if err > 0 and top > 0 else float("inf")
 
 
 def decrypt_error(U, M, sec, Aout, Bout, primes, rows: int = 64):
@@ -204,13 +240,13 @@ def decrypt_error(U, M, sec, Aout, Bout, primes, rows: int = 64):
     import torch
     dev = Aout.device
     idx = np.unique(np.linspace(0, Aout.shape[1] - 1, rows).astype(np.int64))
-    s_t = torch.from_numpy(sec).to(dev)
+    S = negacyclic_matrix(torch.from_numpy(sec).to(dev), torch.float64)
     dec = []
     for jq, q in enumerate(primes):
         sel = torch.from_numpy(idx).to(dev)
         xa = Aout[jq].view(torch.int64).index_select(0, sel)
         xb = Bout[jq].view(torch.int64).index_select(0, sel)
-        dec.append(torch.remainder(_negacyclic_mod(xa, s_t, q) + xb, q).cpu().numpy())
+        dec.append(torch.remainder(negacyclic_rows_mod(xa, S, q) + xb, q).cpu().numpy())
     q0, q1 = int(primes[0]), int(primes[1])
     r0 = dec[0].astype(object)
     r1 = dec[1].astype(object)
@@ -223,8 +259,117 @@ def decrypt_error(U, M, sec, Aout, Bout, primes, rows: int = 64):
     want = U[idx].astype(np.float64) @ M
     err = float(np.max(np.abs(got - want)))
     return {"rows_sampled": int(len(idx)), "max_abs_err": err, "tolerance": DEC_TOL,
+            "precision_bits": _precision_bits(want, err),
             "within_tolerance": err <= DEC_TOL, "other_primes_agree": bool(agree),
             "reference": "FP64 U*M (numpy) on the same rows"}
+
+
+def _switching_keys(s_old, S32, prp, seed: int, stream: int):
+    """Switching keys s_old[r] -> s for every row r of s_old (K x N small int64),
+    in the library's key layout [K, L, 2, L+1, N] (digit, part a/b, prime):
+    a uniform, b = e - a*s + [prime == digit] P s_old mod each prime, with the
+    RNS gadget of one digit per chain prime and P the special prime (last)."""
+    import torch
+    from paper_2503_16080_gb300 import synth
+    K, n = s_old.shape
+    L = len(prp) - 1
+    P = int(prp[-1])
+    dev = s_old.device
+    keys = torch.empty((K, L, 2, L + 1, n), dtype=torch.uint64, device=dev)
+    kv = keys.view(torch.int64)
+    e = synth.rounded_gaussian_torch(seed, stream + 90, (K * L, n), dev)
+    for k, q in enumerate(prp):
+        a = synth.uniform_mod_torch(seed, stream + k, (K * L, n), q, dev).view(torch.int64)
+        kv[:, :, 0, k, :] = a.view(K, L, n)
+        b = torch.remainder(e.to(torch.int64) - negacyclic_rows_mod(a, S32, q, 10), q)
+        del a
+        b = b.view(K, L, n)
+        if k < L:  # |P mod q| < 2^50 and |s_old| <= N <= 2^13: the product fits int64
+            b[:, k, :] = torch.remainder(b[:, k, :] + (P % q) * s_old, q)
+        kv[:, :, 1, k, :] = b
+        del b
+    return keys
+
+
+def ccmm_inputs(n: int, primes, prp, dev, seed: int = SEED):
+    """Real CKKS inputs for CC-MM at ring degree n (plain PyTorch harness):
+    a ternary secret s; column-wise encryptions of M1 and M2 (uniform in
+    [-1, 1], scale 2^40; ciphertext j encrypts column j); the automorphism
+    keys (slot j switches s(X^(2j+1)) -> s) and the relinearisation key
+    (s^2 -> s).  The negacyclic products by s run as TF32 matrix products of
+    10-bit limbs (exact: every sum is an integer below 2^24), checked on two
+    rows against the FP64 form."""
+    import numpy as np
+    import torch
+    from paper_2503_16080_gb300 import synth
+    L = len(primes)
+    s = torch.from_numpy(synth.ternary(seed, 800, n)).to(dev)
+    S32 = negacyclic_matrix(s, torch.float32)
+    probe = synth.uniform_mod_torch(seed, 801, (2, n), prp[-1], dev).view(torch.int64)
+    if not torch.equal(negacyclic_rows_mod(probe, S32, prp[-1], 10),
+                       negacyclic_rows_mod(probe, negacyclic_matrix(s, torch.float64), prp[-1])):
+        raise RuntimeError("TF32 limb products are not exact on this device")
+
+    def encrypt_columns(M, stream):
+        ct = torch.empty((2, L, n, n), dtype=torch.uint64, device=dev)
+        cv = ct.view(torch.int64)
+        me = torch.floor(M.t() * DELTA + 0.5).to(torch.int64)
+        me += synth.rounded_gaussian_torch(seed, stream + 50, (n, n), dev).to(torch.int64)
+        for j, q in enumerate(primes):
+            a = synth.uniform_mod_torch(seed, stream + j, (n, n), q, dev).view(torch.int64)
+            cv[0, j] = a
+            cv[1, j] = torch.remainder(me - negacyclic_rows_mod(a, S32, q, 10), q)
+        return ct
+
+    M1 = synth.uniform_unit_torch(seed, 810, (n, n), dev)
+    M2 = synth.uniform_unit_torch(seed, 811, (n, n), dev)
+    ct1, ct2 = encrypt_columns(M1, 500), encrypt_columns(M2, 600)
+    c = torch.arange(n, device=dev)
+    pos = torch.remainder(c[None, :] * (2 * c[:, None] + 1), 2 * n)
+    sign = torch.where(pos < n, 1, -1).to(torch.int64)
+    s_aut = torch.zeros((n, n), dtype=torch.int64, device=dev)
+    s_aut.scatter_(1, torch.remainder(pos, n), sign * s[None, :])
+    del pos, sign
+    keys = _switching_keys(s_aut, S32, prp, seed, 300)
+    del s_aut
+    s2 = torch.matmul(s.to(torch.float64)[None, :], negacyclic_matrix(s, torch.float64))
+    rkey = _switching_keys(s2.to(torch.int64), S32, prp, seed, 400)
+    return {"s": s, "S32": S32, "M1": M1, "M2": M2, "ct1": ct1, "ct2": ct2, "keys": keys,
+            "rkey": rkey}
+
+
+def ccmm_decrypt_error(inp, out, primes, cols: int = 64):
+    """Decrypts sampled ciphertexts (columns) of the CC-MM output, lifts by CRT
+    over q_0 q_1 (q_2 checked), decodes at scale Delta^2 / q_{L-1} and compares
+    with the FP64 product M1 * M2 on the same columns."""
+    import numpy as np
+    import torch
+    n = out.shape[2]
+    Lo = out.shape[1]
+    idx = np.unique(np.linspace(0, n - 1, cols).astype(np.int64))
+    sel = torch.from_numpy(idx).to(out.device)
+    ov = out.view(torch.int64)
+    dec = []
+    for k in range(Lo):
+        q = int(primes[k])
+        xa = ov[0, k].index_select(0, sel)
+        xb = ov[1, k].index_select(0, sel)
+        dec.append(torch.remainder(negacyclic_rows_mod(xa, inp["S32"], q, 10) + xb, q)
+                   .cpu().numpy())
+    q0, q1 = int(primes[0]), int(primes[1])
+    r0, r1 = dec[0].astype(object), dec[1].astype(object)
+    x = r0 + q0 * (((r1 - r0) * pow(q0, -1, q1)) % q1)
+    x = np.where(x > q0 * q1 // 2, x - q0 * q1, x)
+    agree = all(np.array_equal((x % int(primes[k])).astype(np.uint64), dec[k].astype(np.uint64))
+                for k in range(2, Lo))
+    scale = DELTA * DELTA / float(primes[len(primes) - 1])
+    got = x.astype(np.float64) / scale
+    want = torch.matmul(inp["M1"], inp["M2"].index_select(1, sel)).t().cpu().numpy()
+    err = float(np.max(np.abs(got - want)))
+    return {"cols_sampled": int(len(idx)), "max_abs_err": err, "tolerance": DEC_TOL,
+            "precision_bits": _precision_bits(want, err),
+            "within_tolerance": err <= DEC_TOL, "other_primes_agree": bool(agree),
+            "scale": "Delta^2 / q_3", "reference": "FP64 M1*M2 (cuBLAS) on the same columns"}
 
 
 # ----------------------------------------------------------------- CPU oracle
@@ -701,7 +846,8 @@ def run_secondary(args):
 
 CC_WORKLOAD = ("CC-MM n=8192 (Alg. 8): two column-wise encrypted 8192x8192 matrices, ring degree "
                "8192, L=4 primes of 50 bits + a 60-bit special prime, N automorphism keys and a "
-               "relinearisation key resident on the device; output rescaled by q_3")
+               "relinearisation key resident on the device; output rescaled by q_3; real "
+               "encryptions of M1, M2 uniform in [-1,1] at scale 2^40 under a ternary secret")
 
 
 def run_ccmm(args):
@@ -722,25 +868,14 @@ def run_ccmm(args):
     prp = primes + synth.ntt_primes(60, 1)
     ring = pkg.Ring(Nr, prp)
 
-    # Keys: uniform residues per prime plane (the kernels' work does not
-    # depend on the key values; prepared keys are residues like any other).
-    keys = torch.empty((Nr, L, 2, L + 1, Nr), dtype=torch.uint64, device=dev)
-    for k, q in enumerate(prp):
-        keys.view(torch.int64)[:, :, :, k, :] = synth.uniform_mod_torch(
-            SEED, 300 + k, (Nr, L, 2, Nr), q, dev).view(torch.int64)
-    rkey = torch.empty((1, L, 2, L + 1, Nr), dtype=torch.uint64, device=dev)
-    for k, q in enumerate(prp):
-        rkey.view(torch.int64)[:, :, :, k, :] = synth.uniform_mod_torch(
-            SEED, 400 + k, (1, L, 2, Nr), q, dev).view(torch.int64)
-
-    def cts(stream_id):
-        t = torch.empty((2, L, Nr, Nr), dtype=torch.uint64, device=dev)
-        for j, q in enumerate(primes):
-            t.view(torch.int64)[:, j] = synth.uniform_mod_torch(
-                SEED, stream_id + j, (2, Nr, Nr), q, dev).view(torch.int64)
-        return t
-
-    ct1, ct2 = cts(500), cts(600)
+    # Real inputs: column-wise encryptions of M1 and M2 under a ternary secret,
+    # valid automorphism and relinearisation keys (the kernels' work does not
+    # depend on the values; the decrypted product is checked after timing).
+    inp = ccmm_inputs(Nr, primes, prp, dev)
+    ct1, ct2 = inp["ct1"], inp["ct2"]
+    keys = ring.prepare_keys(inp["keys"])   # in place: evaluation-domain Montgomery form
+    rkey = ring.prepare_keys(inp["rkey"])
+    torch.cuda.synchronize()
     out = torch.empty((2, L - 1, Nr, Nr), dtype=torch.uint64, device=dev)
     ws_bytes = ring.cc_mm_workspace_bytes()
     ws = torch.empty(ws_bytes, dtype=torch.uint8, device=dev)
@@ -761,6 +896,7 @@ def run_ccmm(args):
     torch.cuda.synchronize()
     clk = clocks.stop()
     ms = e0.elapsed_time(e1) / args.steps
+    dec = ccmm_decrypt_error(inp, out, primes)
 
     # Stage split and GEMM launches (one extra, separately timed call).
     pkg.profile_enable(True)
@@ -878,6 +1014,7 @@ def run_ccmm(args):
                          "flops_per_launch": gemm_flops, **form},
             "wide_passes_ms": {"gemm": gemm_ms, "residue_split": pre_ms, "crt_or_u16": post_ms},
             "fp64_matmul_ms": dgemm_ms, "slowdown_vs_fp64_matmul": ms / dgemm_ms,
+            "decrypt": dec,
             "e2e": {"value": e2e_ms, "unit": "ms per CC-MM", "h2d_bytes_per_step":
                     8 * (h1.numel() + h2.numel()), "d2h_bytes_per_step": 8 * ho.numel()},
             "cpu_baseline": cpu, "clocks": clk}

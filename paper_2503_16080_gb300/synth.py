@@ -246,3 +246,36 @@ def uniform_int8_torch(seed: int, stream: int, shape, device, chunk: int = 1 << 
         # top byte as a signed int8: arithmetic shift keeps the sign bit
         out[s0:s0 + cnt] = torch.bitwise_right_shift(x, 56).to(torch.int8)
     return out.reshape(shape)
+
+
+def uniform_unit_torch(seed: int, stream: int, shape, device, chunk: int = 1 << 26):
+    """uniform_unit(seed, stream, shape) generated on `device` (float64, same values)."""
+    import torch
+    n = int(np.prod(shape))
+    out = torch.empty(n, dtype=torch.float64, device=device)
+    for s0 in range(0, n, chunk):
+        cnt = min(chunk, n - s0)
+        x = u64_torch(seed, stream, cnt, device, start=s0)
+        out[s0:s0 + cnt] = _shr(x, 11).to(torch.float64) * (2.0 ** -52) - 1.0
+    return out.reshape(shape)
+
+
+def rounded_gaussian_torch(seed: int, stream: int, shape, device, sigma: float = 3.2,
+                           tail: float = 6.0, chunk: int = 1 << 25):
+    """The rounded_gaussian draw generated on `device` (int8; |e| <= tail * sigma < 128).
+    Same Box-Muller formula on the same uniform bits; the device's log and cos
+    may differ from the host's in the last bit, so a value can differ where
+    the scaled draw sits on a rounding boundary."""
+    import torch
+    n = int(np.prod(shape))
+    out = torch.empty(n, dtype=torch.int8, device=device)
+    for s0 in range(0, n, chunk):
+        cnt = min(chunk, n - s0)
+        u1 = (_shr(u64_torch(seed, stream, cnt, device, start=s0), 11).to(torch.float64) + 0.5) \
+            * 2.0 ** -53
+        u2 = (_shr(u64_torch(seed, stream, cnt, device, start=n + s0), 11).to(torch.float64)
+              + 0.5) * 2.0 ** -53
+        x = torch.sqrt(-2.0 * torch.log(u1)) * torch.cos(2.0 * math.pi * u2) * sigma
+        x = torch.clamp(x, -tail * sigma, tail * sigma)
+        out[s0:s0 + cnt] = torch.floor(x + 0.5).to(torch.int8)
+    return out.reshape(shape)

@@ -1,7 +1,9 @@
 """CC-MM (Alg. 8) at the benchmark's size, N = 8192 with L = 4 primes of 50
 bits and a 60-bit special prime, in the launch configuration the benchmark
-times, checked on sampled outputs the oracle computes one by one; and a
-decryption check with real keys at N = 1024.
+times, checked on sampled outputs the oracle computes one by one; a
+decryption check with real keys at N = 8192 (keys and encryptions from the
+benchmark's plain-PyTorch harness, itself pinned to the oracle's key
+generator on the CPU); and one at N = 1024 with the oracle's own keys.
 
 Full size uses noise-free ciphertexts (a = 0, b = an arbitrary residue
 matrix).  For them every KeySwitch sees a zero a-part and returns its input,
@@ -112,4 +114,23 @@ def test_cc_mm_n1024_decrypts(oracle_mod, pkg):
         val = oracle_mod.crt2(dec[0], dec[1], C.PR[0], C.PR[1]).astype(np.float64) / scale
         ref = M1 @ M2[:, j]
         assert np.max(np.abs(val - ref)) <= 2.0 ** -20, j
+    ring.close()
+
+
+def test_cc_mm_n8192_real_keys_decrypts(pkg):
+    import bench
+    N, L = 8192, 4
+    primes = synth.ntt_primes(50, L)
+    prp = primes + synth.ntt_primes(60, 1)
+    dev = torch.device("cuda")
+    ring = pkg.Ring(N, prp)
+    inp = bench.ccmm_inputs(N, primes, prp, dev, seed=77)
+    keys = ring.prepare_keys(inp.pop("keys"))
+    rkey = ring.prepare_keys(inp.pop("rkey"))
+    out = ring.cc_mm(inp["ct1"], inp["ct2"], keys, rkey)
+    torch.cuda.synchronize()
+    del keys, rkey
+    r = bench.ccmm_decrypt_error(inp, out, primes, cols=48)
+    assert r["other_primes_agree"], r
+    assert r["within_tolerance"], r
     ring.close()
