@@ -200,19 +200,29 @@ int ks_run(const modpp_ring_s *r, const uint64_t *ct, int64_t n, int64_t count, 
 // independent DFTs of length size), each block of `size` already in
 // bit-reversed order in `a`, ping-ponging with `b`; returns the buffer
 // holding the result.
+// Stages the next Tweak pass takes at stage half `half`: three (radix 8) or
+// two (radix 4) while the group of 8h or 4h ciphertexts fits both the Tweak's
+// size and the ring degree (even rotations), else one.
+int tweak_pass_stages(int64_t half, int64_t size, int64_t N) {
+    if (8 * half <= size && 8 * half <= N) return 3;
+    if (4 * half <= size && 4 * half <= N) return 2;
+    return 1;
+}
+
 uint64_t *tweak_stages(const modpp_ring_s *r, uint64_t *a, uint64_t *b, int64_t n, int64_t size,
                        int L, cudaStream_t st, int *rc, int parts = 2) {
     *rc = MODPP_OK;
     const int N = static_cast<int>(r->N);
     for (int64_t half = 1; half < size;) {
         cudaError_t e;
-        if (4 * half <= size && 4 * half <= N) {  // two stages in one pass
+        const int k = tweak_pass_stages(half, size, N);
+        if (k == 3)
+            e = launch_tweak_radix8(a, b, n, L, N, half, r->tab, st, parts);
+        else if (k == 2)
             e = launch_tweak_radix4(a, b, n, L, N, half, r->tab, st, parts);
-            half <<= 2;
-        } else {
+        else
             e = launch_tweak_stage(a, b, n, L, N, half, r->tab, st, parts);
-            half <<= 1;
-        }
+        half <<= k;
         if (e != cudaSuccess) {
             *rc = MODPP_ERR_CUDA;
             return a;
@@ -509,7 +519,7 @@ int modpp_tweak(modpp_ring r, const uint64_t *ct, uint64_t *out, int64_t n, void
     // The passes alternate buffers: start where the last one lands in out.
     int passes = 0;
     for (int64_t half = 1; half < n; ++passes)
-        half <<= (4 * half <= n && 4 * half <= r->N) ? 2 : 1;
+        half <<= tweak_pass_stages(half, n, r->N);
     uint64_t *first = (passes % 2 == 1) ? w : out;
     uint64_t *second = first == w ? out : w;
     GatherTables t{};

@@ -78,6 +78,8 @@ cudaError_t launch_tweak_stage(const uint64_t *in, uint64_t *out, int64_t n, int
 // Stages half and 2 half in one pass (4 half <= N, n a multiple of 4 half).
 cudaError_t launch_tweak_radix4(const uint64_t *in, uint64_t *out, int64_t n, int L, int N,
                                 int64_t half, const NttPlane *tab, cudaStream_t s, int parts = 2);
+cudaError_t launch_tweak_radix8(const uint64_t *in, uint64_t *out, int64_t n, int L, int N,
+                                int64_t half, const NttPlane *tab, cudaStream_t s, int parts = 2);
 cudaError_t launch_add_planes(const uint64_t *x, const uint64_t *y, uint64_t *out, int parts, int L,
                               int64_t count, const NttPlane *tab, cudaStream_t s);
 cudaError_t launch_rescale(const uint64_t *in, uint64_t *out, int L, int64_t count,

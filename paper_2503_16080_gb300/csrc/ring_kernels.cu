@@ -434,6 +434,113 @@ cudaError_t launch_tweak_radix4(const uint64_t *in, uint64_t *out, int64_t n, in
     return cudaGetLastError();
 }
 
+// Three consecutive stages (half = h, 2h, 4h) in one pass, for 8h <= N.  For
+// the eight ciphertexts x_k = i0 + k h (k < 8), i0 = 8h blk + jj, with
+// tA = jj N / h, tB = jj N / (2h), tC = jj N / (4h):
+//   the first two stages are the radix-4 pass on x0..x3 (giving z0..z3) and
+//   on x4..x7 (giving z4..z7); the third pairs (z_k, z_{k+4}) with twiddle
+//   X^(c_k), c_k = tC + k N / 4 (element i0 + k h sits at index jj + k h of
+//   its block of 8h).  R_{c_k}(z_{k+4}) is read directly as rotated windows
+//   of x4..x7, with the signs and the N/2 shifts of z_{k+4}'s radix-4 row:
+//     k = 0:  R_c x4 + R_{c+tA} x5 + R_{c+tB} x6       + R_{c+tA+tB} x7
+//     k = 1:  R_c x4 - R_{c+tA} x5 + R_{c+tB+N/2} x6 - R_{c+tA+tB+N/2} x7
+//     k = 2:  R_c x4 + R_{c+tA} x5 - R_{c+tB} x6       - R_{c+tA+tB} x7
+//     k = 3:  R_c x4 - R_{c+tA} x5 - R_{c+tB+N/2} x6 + R_{c+tA+tB+N/2} x7
+//   and the outputs are z_k + R_{c_k}(z_{k+4}) at i0 + k h and the difference
+//   at i0 + (k + 4) h.
+// 22 rotated 16-byte reads (the re-reads of a window hit in L2) and eight
+// writes per thread replace three radix-2 passes' reads and writes of the
+// batch.  All rotations stay even (8h <= N), so coefficient pairs move together.
+__global__ void tweak_radix8_kernel(const uint64_t *__restrict__ in, uint64_t *__restrict__ out,
+                                    int64_t n, int L, int logN, int lh,
+                                    const NttPlane *__restrict__ tab) {
+    const int r = blockIdx.y;  // part * L + plane
+    const uint64_t q = tab[r % L].q;
+    const int N = 1 << logN;
+    const uint64_t *inp = in + static_cast<int64_t>(r) * n * N;
+    uint64_t *outp = out + static_cast<int64_t>(r) * n * N;
+    const int64_t total = (n >> 3) << (logN - 1);  // groups of eight x coefficient pairs
+    const int64_t h_mask = (int64_t(1) << lh) - 1;
+    const int halfN = N >> 1, quarterN = N >> 2;
+    for (int64_t w = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; w < total;
+         w += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        const int m = (static_cast<int>(w) << 1) & (N - 1);
+        const int64_t g = w >> (logN - 1);
+        const int64_t jj = g & h_mask;
+        const int64_t i0 = ((g >> lh) << (lh + 3)) + jj;
+        const int64_t h = int64_t(1) << lh;
+        const int tA = static_cast<int>(jj << (logN - lh));
+        const int tB = static_cast<int>(jj << (logN - lh - 1));
+        const int tC = static_cast<int>(jj << (logN - lh - 2));
+        const uint64_t *x[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) x[k] = inp + ((i0 + k * h) << logN);
+        // z0..z3: the first two stages on x0..x3
+        const ulonglong2 a = *reinterpret_cast<const ulonglong2 *>(x[0] + m);
+        const ulonglong2 b = rot_load(x[1], m, tA, N, q);
+        const ulonglong2 c0 = rot_load(x[2], m, tB, N, q);
+        const ulonglong2 c1 = rot_load(x[2], m, tB + halfN, N, q);
+        const ulonglong2 d0 = rot_load(x[3], m, tA + tB, N, q);
+        const ulonglong2 d1 = rot_load(x[3], m, tA + tB + halfN, N, q);
+        ulonglong2 z[4];
+        {
+            const uint64_t p = add_mod(a.x, b.x, q), mm = sub_mod(a.x, b.x, q);
+            const uint64_t s0 = add_mod(c0.x, d0.x, q), s1 = sub_mod(c1.x, d1.x, q);
+            z[0].x = add_mod(p, s0, q);
+            z[2].x = sub_mod(p, s0, q);
+            z[1].x = add_mod(mm, s1, q);
+            z[3].x = sub_mod(mm, s1, q);
+        }
+        {
+            const uint64_t p = add_mod(a.y, b.y, q), mm = sub_mod(a.y, b.y, q);
+            const uint64_t s0 = add_mod(c0.y, d0.y, q), s1 = sub_mod(c1.y, d1.y, q);
+            z[0].y = add_mod(p, s0, q);
+            z[2].y = sub_mod(p, s0, q);
+            z[1].y = add_mod(mm, s1, q);
+            z[3].y = sub_mod(mm, s1, q);
+        }
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const int c = tC + k * quarterN;
+            const int tb = (k & 1) ? tB + halfN : tB;
+            const ulonglong2 e4 = rot_load(x[4], m, c, N, q);
+            const ulonglong2 e5 = rot_load(x[5], m, c + tA, N, q);
+            const ulonglong2 e6 = rot_load(x[6], m, c + tb, N, q);
+            const ulonglong2 e7 = rot_load(x[7], m, c + tA + tb, N, q);
+            // u = e4 +- e5 +- e6 +- e7 with the signs of row k
+            ulonglong2 u;
+            {
+                const uint64_t p = (k & 1) ? sub_mod(e4.x, e5.x, q) : add_mod(e4.x, e5.x, q);
+                const uint64_t s = (k & 1) ? sub_mod(e6.x, e7.x, q) : add_mod(e6.x, e7.x, q);
+                u.x = (k & 2) ? sub_mod(p, s, q) : add_mod(p, s, q);
+            }
+            {
+                const uint64_t p = (k & 1) ? sub_mod(e4.y, e5.y, q) : add_mod(e4.y, e5.y, q);
+                const uint64_t s = (k & 1) ? sub_mod(e6.y, e7.y, q) : add_mod(e6.y, e7.y, q);
+                u.y = (k & 2) ? sub_mod(p, s, q) : add_mod(p, s, q);
+            }
+            ulonglong2 o0, o1;
+            o0.x = add_mod(z[k].x, u.x, q);
+            o0.y = add_mod(z[k].y, u.y, q);
+            o1.x = sub_mod(z[k].x, u.x, q);
+            o1.y = sub_mod(z[k].y, u.y, q);
+            *reinterpret_cast<ulonglong2 *>(outp + ((i0 + k * h) << logN) + m) = o0;
+            *reinterpret_cast<ulonglong2 *>(outp + ((i0 + (k + 4) * h) << logN) + m) = o1;
+        }
+    }
+}
+
+cudaError_t launch_tweak_radix8(const uint64_t *in, uint64_t *out, int64_t n, int L, int N,
+                                int64_t half, const NttPlane *tab, cudaStream_t s, int parts) {
+    const int logN = 31 - __builtin_clz(N);
+    const int lh = 63 - __builtin_clzll(static_cast<unsigned long long>(half));
+    const int64_t per_plane = (n >> 3) * (N >> 1);
+    const int64_t bx = std::min<int64_t>((per_plane + 255) / 256, 152 * 8);
+    tweak_radix8_kernel<<<dim3(static_cast<unsigned>(bx), parts * L), 256, 0, s>>>(in, out, n, L,
+                                                                                   logN, lh, tab);
+    return cudaGetLastError();
+}
+
 // The same stage for half = N (n = 2N), where t = jj is odd for odd jj: one
 // coefficient per thread.
 __global__ void tweak_stage_scalar_kernel(const uint64_t *__restrict__ in,
