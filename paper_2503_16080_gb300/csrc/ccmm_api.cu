@@ -28,7 +28,6 @@ struct modpp_ring_s {
     const uint64_t *qlinv = nullptr, *qlinv_s = nullptr;  // q_{L-1}^-1 mod q_k, k < L-1
     const uint64_t *ninv = nullptr, *ninv_s = nullptr;    // N^-1 mod q_k, k < L
     const int *t2_src = nullptr, *t2_ellinv = nullptr, *t2_kid = nullptr;
-    const int *t3_src = nullptr, *t3_shift = nullptr;
     const int *kid_zero = nullptr;
     cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
     bool timed = false;
@@ -132,7 +131,7 @@ RingLayout ring_layout(int64_t N, int L) {
     r.consts = off;
     off = align_up(off + sizeof(uint64_t) * 6 * (L + 1));
     r.ints = off;
-    off = align_up(off + sizeof(int) * (5 * N + 1));
+    off = align_up(off + sizeof(int) * (3 * N + 1));
     r.total = off;
     return r;
 }
@@ -209,27 +208,54 @@ int tweak_pass_stages(int64_t half, int64_t size, int64_t N) {
     return 1;
 }
 
+// Where a Tweak's passes read first and write last.
+struct TweakIO {
+    const uint64_t *src = nullptr;  // the first pass reads here, through `in`, instead of a
+    TweakMap in;                    // input map of the first pass
+    uint64_t *dst = nullptr;        // the last pass writes here, through out_t3, instead of a / b
+    int out_t3 = 0;
+    uint64_t *land = nullptr;       // without dst: a or b, where the last pass must write
+};
+
+// The Tweak's passes on a batch of n ciphertexts (n / size independent Tweaks
+// of size ciphertexts each), ping-ponging between a and b; returns the buffer
+// holding the result.  Without io.src the first pass reads a (and writes b).
 uint64_t *tweak_stages(const modpp_ring_s *r, uint64_t *a, uint64_t *b, int64_t n, int64_t size,
-                       int L, cudaStream_t st, int *rc, int parts = 2) {
+                       int L, cudaStream_t st, int *rc, int parts = 2,
+                       const TweakIO &io = TweakIO{}) {
     *rc = MODPP_OK;
     const int N = static_cast<int>(r->N);
-    for (int64_t half = 1; half < size;) {
+    int passes = 0;
+    for (int64_t half = 1; half < size; ++passes) half <<= tweak_pass_stages(half, size, N);
+    const uint64_t *in = io.src ? io.src : a;
+    uint64_t *o = b;
+    if (io.land && io.src) o = ((passes - 1) % 2 == 0) ? io.land : (io.land == a ? b : a);
+    int p = 0;
+    for (int64_t half = 1; half < size; ++p) {
         cudaError_t e;
         const int k = tweak_pass_stages(half, size, N);
+        TweakMap mp{};
+        if (p == 0) mp = io.in;
+        uint64_t *dst = o;
+        if (p == passes - 1 && io.dst) {
+            dst = io.dst;
+            mp.out_t3 = io.out_t3;
+        }
         if (k == 3)
-            e = launch_tweak_radix8(a, b, n, L, N, half, r->tab, st, parts);
+            e = launch_tweak_radix8(in, dst, n, L, N, half, r->tab, st, parts, mp);
         else if (k == 2)
-            e = launch_tweak_radix4(a, b, n, L, N, half, r->tab, st, parts);
+            e = launch_tweak_radix4(in, dst, n, L, N, half, r->tab, st, parts, mp);
         else
-            e = launch_tweak_stage(a, b, n, L, N, half, r->tab, st, parts);
+            e = launch_tweak_stage(in, dst, n, L, N, half, r->tab, st, parts, mp);
         half <<= k;
         if (e != cudaSuccess) {
             *rc = MODPP_ERR_CUDA;
             return a;
         }
-        std::swap(a, b);
+        in = dst;
+        o = o == a ? b : a;
     }
-    return a;
+    return const_cast<uint64_t *>(in);
 }
 
 size_t transpose_scratch(const modpp_ring_s *r, int64_t groups) {
@@ -253,15 +279,14 @@ int transpose_run(const modpp_ring_s *r, const uint64_t *ct, uint64_t *out, int6
     uint64_t *x1 = reinterpret_cast<uint64_t *>(scratch);
     uint64_t *x2 = reinterpret_cast<uint64_t *>(scratch + bb);
     char *ks = scratch + 2 * bb;
-    // Step 1: aux = Tweak((X^i ct_i)_i): shift and bit-reverse, then the stages.
-    GatherTables t1{};
-    t1.per = N;
-    t1.brev_bits = r->logN;
-    t1.shift_src = 1;
-    if (launch_ct_gather(ct, x1, n, L, N, t1, r->tab, st, parts1) != cudaSuccess)
-        return MODPP_ERR_CUDA;
+    // Step 1: aux = Tweak((X^i ct_i)_i): the first pass reads ciphertext
+    // brev(i) times X^brev(i) for position i (the stages' bit-reversed input).
     int rc = MODPP_OK;
-    uint64_t *aux = tweak_stages(r, x1, x2, n, r->N, L, st, &rc, parts1);
+    TweakIO io1;
+    io1.src = ct;
+    io1.in.in_bits = r->logN;
+    io1.in.in_shift = 1;
+    uint64_t *aux = tweak_stages(r, x1, x2, n, r->N, L, st, &rc, parts1, io1);
     if (rc) return rc;
     uint64_t *other = aux == x1 ? x2 : x1;
     // Steps 2-5: aux'_j = Aut(N^-1 aux_{((2j+1)^-1 - 1)/2}, 2j+1), written in
@@ -276,16 +301,13 @@ int transpose_run(const modpp_ring_s *r, const uint64_t *ct, uint64_t *out, int6
         return MODPP_ERR_CUDA;
     rc = ks_run(r, other, n, n, other, n, aut_keys, r->t2_kid, N, b_zero ? 1 : 0, ks, st);
     if (rc) return rc;
-    // Step 6: ct'' = Tweak(aux').
-    uint64_t *ctpp = tweak_stages(r, other, aux, n, r->N, L, st, &rc);
-    if (rc) return rc;
-    // Steps 7-9: ct'_j = X^(2N-j) ct''_{N-j} (1 <= j < N), ct'_0 = ct''_0.
-    GatherTables t3{};
-    t3.per = N;
-    t3.src = r->t3_src;
-    t3.shift = r->t3_shift;
-    if (launch_ct_gather(ctpp, out, n, L, N, t3, r->tab, st) != cudaSuccess) return MODPP_ERR_CUDA;
-    return MODPP_OK;
+    // Step 6: ct'' = Tweak(aux'); steps 7-9 in its last pass:
+    // ct'_j = X^(2N-j) ct''_{N-j} (1 <= j < N), ct'_0 = ct''_0, written to out.
+    TweakIO io2;
+    io2.dst = out;
+    io2.out_t3 = 1;
+    tweak_stages(r, other, aux, n, r->N, L, st, &rc, 2, io2);
+    return rc;
 }
 
 struct CcLayout {
@@ -429,7 +451,6 @@ int modpp_ring_create(int64_t N, int L, const uint64_t *primes_host, void *mem, 
     auto *ints = reinterpret_cast<int *>(host.data() + lay.ints);
     const int *dints = reinterpret_cast<const int *>(r->mem + lay.ints);
     int *t2_src = ints, *t2_ellinv = ints + N, *t2_kid = ints + 2 * N;
-    int *t3_src = ints + 3 * N, *t3_shift = ints + 4 * N;
     const uint64_t twoN = 2 * static_cast<uint64_t>(N);
     for (int64_t c = 0; c < N; ++c) {
         // position c of the bit-reversed second Tweak input holds aux'_j, j = bitrev(c)
@@ -444,16 +465,12 @@ int modpp_ring_create(int64_t N, int L, const uint64_t *primes_host, void *mem, 
         t2_src[c] = static_cast<int>((inv - 1) / 2);
         t2_ellinv[c] = static_cast<int>(inv);
         t2_kid[c] = j == 0 ? -1 : static_cast<int>(j);
-        t3_src[c] = c == 0 ? 0 : static_cast<int>(N - c);
-        t3_shift[c] = c == 0 ? 0 : static_cast<int>(2 * N - c);
     }
-    ints[5 * N] = 0;
+    ints[3 * N] = 0;
     r->t2_src = dints;
     r->t2_ellinv = dints + N;
     r->t2_kid = dints + 2 * N;
-    r->t3_src = dints + 3 * N;
-    r->t3_shift = dints + 4 * N;
-    r->kid_zero = dints + 5 * N;
+    r->kid_zero = dints + 3 * N;
 
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     cudaError_t e = cudaMemcpyAsync(mem, host.data(), lay.total, cudaMemcpyHostToDevice, st);
@@ -516,20 +533,22 @@ int modpp_tweak(modpp_ring r, const uint64_t *ct, uint64_t *out, int64_t n, void
         return MODPP_ERR_WORKSPACE;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     uint64_t *w = static_cast<uint64_t *>(ws);
-    // The passes alternate buffers: start where the last one lands in out.
-    int passes = 0;
-    for (int64_t half = 1; half < n; ++passes)
-        half <<= tweak_pass_stages(half, n, r->N);
-    uint64_t *first = (passes % 2 == 1) ? w : out;
-    uint64_t *second = first == w ? out : w;
-    GatherTables t{};
-    t.per = static_cast<int>(n);
-    t.brev_bits = ln;
-    if (n == 1) t.brev_bits = 0;
-    if (launch_ct_gather(ct, first, n, r->L, static_cast<int>(r->N), t, r->tab, st) != cudaSuccess)
-        return MODPP_ERR_CUDA;
+    if (n == 1) {  // no stage: the Tweak of one ciphertext is itself
+        GatherTables t{};
+        t.per = 1;
+        return launch_ct_gather(ct, out, 1, r->L, static_cast<int>(r->N), t, r->tab, st) ==
+                       cudaSuccess
+                   ? MODPP_OK
+                   : MODPP_ERR_CUDA;
+    }
+    // The first pass reads the inputs in bit-reversed order; the passes
+    // alternate between the workspace and out so that the last lands in out.
     int rc = MODPP_OK;
-    tweak_stages(r, first, second, n, n, r->L, st, &rc);
+    TweakIO io;
+    io.src = ct;
+    io.in.in_bits = ln;
+    io.land = out;
+    tweak_stages(r, w, out, n, n, r->L, st, &rc, 2, io);
     return rc;
 }
 

@@ -73,13 +73,31 @@ cudaError_t launch_ks_moddown(const uint64_t *U, const uint64_t *ct, int64_t n, 
 cudaError_t launch_ct_gather(const uint64_t *in, uint64_t *out, int64_t n, int L, int N,
                              const GatherTables &t, const NttPlane *tab, cudaStream_t s,
                              int parts = 2);
+// Input and output maps of a Tweak pass, folding the gathers around the
+// Tweaks of Alg. 4 into the first and last passes:
+//   in_bits > 0: input ciphertext i of each group of 2^in_bits is read from
+//     the bit-reversed index si of the group, times X^si when in_shift
+//     (Alg. 4 step 1: aux = Tweak((X^i ct_i)_i) with the stages' input in
+//     bit-reversed order);
+//   out_t3: output ciphertext i of each group of N is written as ciphertext
+//     (N - i) mod N times X^(N + i) for i > 0 (Alg. 4 steps 7-9:
+//     ct'_j = X^(2N - j) ct''_(N - j), ct'_0 = ct''_0).
+struct TweakMap {
+    int in_bits = 0;
+    int in_shift = 0;
+    int out_t3 = 0;
+};
 cudaError_t launch_tweak_stage(const uint64_t *in, uint64_t *out, int64_t n, int L, int N,
-                               int64_t half, const NttPlane *tab, cudaStream_t s, int parts = 2);
+                               int64_t half, const NttPlane *tab, cudaStream_t s, int parts = 2,
+                               const TweakMap &mp = TweakMap{});
 // Stages half and 2 half in one pass (4 half <= N, n a multiple of 4 half).
 cudaError_t launch_tweak_radix4(const uint64_t *in, uint64_t *out, int64_t n, int L, int N,
-                                int64_t half, const NttPlane *tab, cudaStream_t s, int parts = 2);
+                                int64_t half, const NttPlane *tab, cudaStream_t s, int parts = 2,
+                                const TweakMap &mp = TweakMap{});
+// Stages half, 2 half and 4 half in one pass (8 half <= N, n a multiple of 8 half).
 cudaError_t launch_tweak_radix8(const uint64_t *in, uint64_t *out, int64_t n, int L, int N,
-                                int64_t half, const NttPlane *tab, cudaStream_t s, int parts = 2);
+                                int64_t half, const NttPlane *tab, cudaStream_t s, int parts = 2,
+                                const TweakMap &mp = TweakMap{});
 cudaError_t launch_add_planes(const uint64_t *x, const uint64_t *y, uint64_t *out, int parts, int L,
                               int64_t count, const NttPlane *tab, cudaStream_t s);
 cudaError_t launch_rescale(const uint64_t *in, uint64_t *out, int L, int64_t count,

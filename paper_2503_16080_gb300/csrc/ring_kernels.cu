@@ -304,15 +304,101 @@ cudaError_t launch_ct_gather(const uint64_t *in, uint64_t *out, int64_t n, int L
     return cudaGetLastError();
 }
 
+// ------------------------------------------------------------ Tweak passes
+// Input and output maps of a Tweak pass (TweakMap, ring_internal.h) fold the
+// gathers around the Tweaks of Alg. 4 into the first and last passes.
+__device__ __forceinline__ uint64_t neg_mod(uint64_t v, uint64_t q) { return v == 0 ? 0 : q - v; }
+
+// Coefficients m and m + 1 of X^t x, m and t even (t taken mod 2N): one
+// 16-byte load, negated when the window lies in the upper half.
+__device__ __forceinline__ ulonglong2 rot_load(const uint64_t *x, int m, int t, int N, uint64_t q) {
+    // coefficient m (and m + 1) of X^t x, m and t even (t taken mod 2N)
+    int e = (m - t) & (2 * N - 1);
+    const bool neg = e >= N;
+    e &= N - 1;
+    ulonglong2 v = *reinterpret_cast<const ulonglong2 *>(x + e);
+    if (neg) {
+        v.x = v.x == 0 ? 0 : q - v.x;
+        v.y = v.y == 0 ? 0 : q - v.y;
+    }
+    return v;
+}
+
+// Coefficients m and m + 1 of X^t x for any t (odd t included: the two
+// words are loaded separately and may sit on either side of the wrap).
+__device__ __forceinline__ ulonglong2 rot_load_any(const uint64_t *x, int m, int t, int N,
+                                                   uint64_t q) {
+    const int e0 = (m - t) & (2 * N - 1), e1 = (m + 1 - t) & (2 * N - 1);
+    ulonglong2 v;
+    v.x = x[e0 & (N - 1)];
+    v.y = x[e1 & (N - 1)];
+    if (e0 >= N) v.x = neg_mod(v.x, q);
+    if (e1 >= N) v.y = neg_mod(v.y, q);
+    return v;
+}
+
+// Where input ciphertext i of a pass is read: itself, or (input map) the
+// bit-reversed index si of its group of 2^in_bits, with an extra rotation
+// X^si when in_shift.
+template <bool MI>
+__device__ __forceinline__ const uint64_t *tw_src(const uint64_t *inp, int64_t i, int logN,
+                                                  const TweakMap &mp, int &rot) {
+    if constexpr (!MI) {
+        rot = 0;
+        return inp + (i << logN);
+    } else {
+        const int64_t mask = (int64_t(1) << mp.in_bits) - 1;
+        const int ci = static_cast<int>(i & mask);
+        const int si = static_cast<int>(__brev(static_cast<unsigned>(ci)) >> (32 - mp.in_bits));
+        rot = mp.in_shift ? si : 0;
+        return inp + (((i - ci) + si) << logN);
+    }
+}
+
+// Coefficients m, m + 1 of X^t times the source x (rotation rx of the map added).
+template <bool MI>
+__device__ __forceinline__ ulonglong2 tw_load(const uint64_t *x, int m, int t, int rx, int N,
+                                              uint64_t q) {
+    if constexpr (MI) return rot_load_any(x, m, t + rx, N, q);
+    else return rot_load(x, m, t, N, q);
+}
+template <bool MI>
+__device__ __forceinline__ ulonglong2 tw_load0(const uint64_t *x, int m, int rx, int N, uint64_t q) {
+    if constexpr (MI) return rot_load_any(x, m, rx, N, q);
+    else return *reinterpret_cast<const ulonglong2 *>(x + m);
+}
+
+// Stores coefficients m, m + 1 of output ciphertext o: in place, or (output
+// map) into ciphertext j = (N - i) mod N of o's group of N (i = o mod N)
+// times X^(N + i) for i > 0: ct'_j = X^(2N - j) ct''_(N - j), ct'_0 = ct''_0.
+template <bool MO>
+__device__ __forceinline__ void tw_store(uint64_t *outp, int64_t o, int m, ulonglong2 v, int logN,
+                                         uint64_t q) {
+    if constexpr (!MO) {
+        *reinterpret_cast<ulonglong2 *>(outp + (o << logN) + m) = v;
+    } else {
+        const int N = 1 << logN;
+        const int i = static_cast<int>(o & (N - 1));
+        const int64_t dst = (o - i) + ((N - i) & (N - 1));
+        const int rot = i == 0 ? 0 : N + i;
+        const int p0 = (m + rot) & (2 * N - 1), p1 = (m + 1 + rot) & (2 * N - 1);
+        uint64_t *d = outp + (dst << logN);
+        d[p0 & (N - 1)] = p0 >= N ? neg_mod(v.x, q) : v.x;
+        d[p1 & (N - 1)] = p1 >= N ? neg_mod(v.y, q) : v.y;
+    }
+}
+
 // One radix-2 stage of Tweak (an n-point DFT over R_q with omega = X^(2N/n)):
 // for pairs (lo, hi = lo + half) inside blocks of 2*half,
 //   out_lo = x_lo + X^t x_hi,  out_hi = x_lo - X^t x_hi,  t = (lo mod half) * N / half.
-// Input ciphertexts must be in bit-reversed order before the first stage.
+// Input ciphertexts must be in bit-reversed order before the first stage
+// (or the pass's input map bit-reverses them).
 // Each thread takes two neighbouring coefficients with 16-byte accesses; t is
 // even whenever half < N, so the rotated read stays 16-byte aligned.
+template <bool MI, bool MO>
 __global__ void tweak_stage_kernel(const uint64_t *__restrict__ in, uint64_t *__restrict__ out,
                                    int64_t n, int L, int logN, int lhalf,
-                                   const NttPlane *__restrict__ tab) {
+                                   const NttPlane *__restrict__ tab, TweakMap mp) {
     const int r = blockIdx.y;  // part * L + plane
     const uint64_t q = tab[r % L].q;
     const int N = 1 << logN;
@@ -328,20 +414,18 @@ __global__ void tweak_stage_kernel(const uint64_t *__restrict__ in, uint64_t *__
         const int64_t lo = ((pr >> lhalf) << (lhalf + 1)) + jj;
         const int64_t hi = lo + (int64_t(1) << lhalf);
         const int tt = static_cast<int>(jj << (logN - lhalf));
-        const ulonglong2 a = *reinterpret_cast<const ulonglong2 *>(inp + (lo << logN) + m);
-        int src = m - tt;
-        ulonglong2 y = *reinterpret_cast<const ulonglong2 *>(inp + (hi << logN) + (src & (N - 1)));
-        if (src < 0) {
-            y.x = y.x == 0 ? 0 : q - y.x;
-            y.y = y.y == 0 ? 0 : q - y.y;
-        }
+        int ra, rb;
+        const uint64_t *xl = tw_src<MI>(inp, lo, logN, mp, ra);
+        const uint64_t *xh = tw_src<MI>(inp, hi, logN, mp, rb);
+        const ulonglong2 a = tw_load0<MI>(xl, m, ra, N, q);
+        const ulonglong2 y = tw_load<MI>(xh, m, tt, rb, N, q);
         ulonglong2 o0, o1;
         o0.x = add_mod(a.x, y.x, q);
         o0.y = add_mod(a.y, y.y, q);
         o1.x = sub_mod(a.x, y.x, q);
         o1.y = sub_mod(a.y, y.y, q);
-        *reinterpret_cast<ulonglong2 *>(outp + (lo << logN) + m) = o0;
-        *reinterpret_cast<ulonglong2 *>(outp + (hi << logN) + m) = o1;
+        tw_store<MO>(outp, lo, m, o0, logN, q);
+        tw_store<MO>(outp, hi, m, o1, logN, q);
     }
 }
 
@@ -355,23 +439,13 @@ __global__ void tweak_stage_kernel(const uint64_t *__restrict__ in, uint64_t *__
 // (the second stage pairs (i1, i3) with twiddle X^(tB + N/2)).  Six rotated
 // reads of contiguous windows give four outputs, instead of eight reads and
 // eight writes for two radix-2 passes.  All rotations are even, so two
-// neighbouring coefficients move together in 16-byte accesses.
-__device__ __forceinline__ ulonglong2 rot_load(const uint64_t *x, int m, int t, int N, uint64_t q) {
-    // coefficient m (and m + 1) of X^t x, 0 <= t < 2N, m and t even
-    int e = (m - t) & (2 * N - 1);
-    const bool neg = e >= N;
-    e &= N - 1;
-    ulonglong2 v = *reinterpret_cast<const ulonglong2 *>(x + e);
-    if (neg) {
-        v.x = v.x == 0 ? 0 : q - v.x;
-        v.y = v.y == 0 ? 0 : q - v.y;
-    }
-    return v;
-}
+// neighbouring coefficients move together in 16-byte accesses (an input map
+// adds rotations of any parity; those reads take two 8-byte loads).
 
+template <bool MI, bool MO>
 __global__ void tweak_radix4_kernel(const uint64_t *__restrict__ in, uint64_t *__restrict__ out,
                                     int64_t n, int L, int logN, int lh,
-                                    const NttPlane *__restrict__ tab) {
+                                    const NttPlane *__restrict__ tab, TweakMap mp) {
     const int r = blockIdx.y;  // part * L + plane
     const uint64_t q = tab[r % L].q;
     const int N = 1 << logN;
@@ -389,16 +463,16 @@ __global__ void tweak_radix4_kernel(const uint64_t *__restrict__ in, uint64_t *_
         const int tA = static_cast<int>(jj << (logN - lh));
         const int tB = static_cast<int>(jj << (logN - lh - 1));
         const int halfN = N >> 1;
-        const uint64_t *x0 = inp + (i0 << logN);
-        const uint64_t *x1 = inp + ((i0 + h) << logN);
-        const uint64_t *x2 = inp + ((i0 + 2 * h) << logN);
-        const uint64_t *x3 = inp + ((i0 + 3 * h) << logN);
-        const ulonglong2 a = *reinterpret_cast<const ulonglong2 *>(x0 + m);
-        const ulonglong2 b = rot_load(x1, m, tA, N, q);
-        const ulonglong2 c0 = rot_load(x2, m, tB, N, q);
-        const ulonglong2 c1 = rot_load(x2, m, tB + halfN, N, q);
-        const ulonglong2 d0 = rot_load(x3, m, tA + tB, N, q);
-        const ulonglong2 d1 = rot_load(x3, m, tA + tB + halfN, N, q);
+        int rx[4];
+        const uint64_t *x[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) x[k] = tw_src<MI>(inp, i0 + k * h, logN, mp, rx[k]);
+        const ulonglong2 a = tw_load0<MI>(x[0], m, rx[0], N, q);
+        const ulonglong2 b = tw_load<MI>(x[1], m, tA, rx[1], N, q);
+        const ulonglong2 c0 = tw_load<MI>(x[2], m, tB, rx[2], N, q);
+        const ulonglong2 c1 = tw_load<MI>(x[2], m, tB + halfN, rx[2], N, q);
+        const ulonglong2 d0 = tw_load<MI>(x[3], m, tA + tB, rx[3], N, q);
+        const ulonglong2 d1 = tw_load<MI>(x[3], m, tA + tB + halfN, rx[3], N, q);
         ulonglong2 z0, z1, z2, z3;
         {
             const uint64_t p = add_mod(a.x, b.x, q), mm = sub_mod(a.x, b.x, q);
@@ -416,21 +490,32 @@ __global__ void tweak_radix4_kernel(const uint64_t *__restrict__ in, uint64_t *_
             z1.y = add_mod(mm, s1, q);
             z3.y = sub_mod(mm, s1, q);
         }
-        *reinterpret_cast<ulonglong2 *>(outp + (i0 << logN) + m) = z0;
-        *reinterpret_cast<ulonglong2 *>(outp + ((i0 + h) << logN) + m) = z1;
-        *reinterpret_cast<ulonglong2 *>(outp + ((i0 + 2 * h) << logN) + m) = z2;
-        *reinterpret_cast<ulonglong2 *>(outp + ((i0 + 3 * h) << logN) + m) = z3;
+        tw_store<MO>(outp, i0, m, z0, logN, q);
+        tw_store<MO>(outp, i0 + h, m, z1, logN, q);
+        tw_store<MO>(outp, i0 + 2 * h, m, z2, logN, q);
+        tw_store<MO>(outp, i0 + 3 * h, m, z3, logN, q);
     }
 }
 
+template <bool MI, bool MO>
+static void tweak_radix4_go(dim3 g, cudaStream_t s, const uint64_t *in, uint64_t *out, int64_t n,
+                            int L, int logN, int lh, const NttPlane *tab, const TweakMap &mp) {
+    tweak_radix4_kernel<MI, MO><<<g, 256, 0, s>>>(in, out, n, L, logN, lh, tab, mp);
+}
+
 cudaError_t launch_tweak_radix4(const uint64_t *in, uint64_t *out, int64_t n, int L, int N,
-                                int64_t half, const NttPlane *tab, cudaStream_t s, int parts) {
+                                int64_t half, const NttPlane *tab, cudaStream_t s, int parts,
+                                const TweakMap &mp) {
     const int logN = 31 - __builtin_clz(N);
     const int lh = 63 - __builtin_clzll(static_cast<unsigned long long>(half));
     const int64_t per_plane = (n >> 2) * (N >> 1);
     const int64_t bx = std::min<int64_t>((per_plane + 255) / 256, 152 * 8);
-    tweak_radix4_kernel<<<dim3(static_cast<unsigned>(bx), parts * L), 256, 0, s>>>(in, out, n, L,
-                                                                                   logN, lh, tab);
+    const dim3 g(static_cast<unsigned>(bx), parts * L);
+    const bool mi = mp.in_bits > 0, mo = mp.out_t3 != 0;
+    if (mi && mo) tweak_radix4_go<true, true>(g, s, in, out, n, L, logN, lh, tab, mp);
+    else if (mi) tweak_radix4_go<true, false>(g, s, in, out, n, L, logN, lh, tab, mp);
+    else if (mo) tweak_radix4_go<false, true>(g, s, in, out, n, L, logN, lh, tab, mp);
+    else tweak_radix4_go<false, false>(g, s, in, out, n, L, logN, lh, tab, mp);
     return cudaGetLastError();
 }
 
@@ -451,9 +536,10 @@ cudaError_t launch_tweak_radix4(const uint64_t *in, uint64_t *out, int64_t n, in
 // 22 rotated 16-byte reads (the re-reads of a window hit in L2) and eight
 // writes per thread replace three radix-2 passes' reads and writes of the
 // batch.  All rotations stay even (8h <= N), so coefficient pairs move together.
+template <bool MI, bool MO>
 __global__ void tweak_radix8_kernel(const uint64_t *__restrict__ in, uint64_t *__restrict__ out,
                                     int64_t n, int L, int logN, int lh,
-                                    const NttPlane *__restrict__ tab) {
+                                    const NttPlane *__restrict__ tab, TweakMap mp) {
     const int r = blockIdx.y;  // part * L + plane
     const uint64_t q = tab[r % L].q;
     const int N = 1 << logN;
@@ -472,16 +558,17 @@ __global__ void tweak_radix8_kernel(const uint64_t *__restrict__ in, uint64_t *_
         const int tA = static_cast<int>(jj << (logN - lh));
         const int tB = static_cast<int>(jj << (logN - lh - 1));
         const int tC = static_cast<int>(jj << (logN - lh - 2));
+        int rx[8];
         const uint64_t *x[8];
 #pragma unroll
-        for (int k = 0; k < 8; ++k) x[k] = inp + ((i0 + k * h) << logN);
+        for (int k = 0; k < 8; ++k) x[k] = tw_src<MI>(inp, i0 + k * h, logN, mp, rx[k]);
         // z0..z3: the first two stages on x0..x3
-        const ulonglong2 a = *reinterpret_cast<const ulonglong2 *>(x[0] + m);
-        const ulonglong2 b = rot_load(x[1], m, tA, N, q);
-        const ulonglong2 c0 = rot_load(x[2], m, tB, N, q);
-        const ulonglong2 c1 = rot_load(x[2], m, tB + halfN, N, q);
-        const ulonglong2 d0 = rot_load(x[3], m, tA + tB, N, q);
-        const ulonglong2 d1 = rot_load(x[3], m, tA + tB + halfN, N, q);
+        const ulonglong2 a = tw_load0<MI>(x[0], m, rx[0], N, q);
+        const ulonglong2 b = tw_load<MI>(x[1], m, tA, rx[1], N, q);
+        const ulonglong2 c0 = tw_load<MI>(x[2], m, tB, rx[2], N, q);
+        const ulonglong2 c1 = tw_load<MI>(x[2], m, tB + halfN, rx[2], N, q);
+        const ulonglong2 d0 = tw_load<MI>(x[3], m, tA + tB, rx[3], N, q);
+        const ulonglong2 d1 = tw_load<MI>(x[3], m, tA + tB + halfN, rx[3], N, q);
         ulonglong2 z[4];
         {
             const uint64_t p = add_mod(a.x, b.x, q), mm = sub_mod(a.x, b.x, q);
@@ -503,41 +590,52 @@ __global__ void tweak_radix8_kernel(const uint64_t *__restrict__ in, uint64_t *_
         for (int k = 0; k < 4; ++k) {
             const int c = tC + k * quarterN;
             const int tb = (k & 1) ? tB + halfN : tB;
-            const ulonglong2 e4 = rot_load(x[4], m, c, N, q);
-            const ulonglong2 e5 = rot_load(x[5], m, c + tA, N, q);
-            const ulonglong2 e6 = rot_load(x[6], m, c + tb, N, q);
-            const ulonglong2 e7 = rot_load(x[7], m, c + tA + tb, N, q);
+            const ulonglong2 e4 = tw_load<MI>(x[4], m, c, rx[4], N, q);
+            const ulonglong2 e5 = tw_load<MI>(x[5], m, c + tA, rx[5], N, q);
+            const ulonglong2 e6 = tw_load<MI>(x[6], m, c + tb, rx[6], N, q);
+            const ulonglong2 e7 = tw_load<MI>(x[7], m, c + tA + tb, rx[7], N, q);
             // u = e4 +- e5 +- e6 +- e7 with the signs of row k
             ulonglong2 u;
             {
                 const uint64_t p = (k & 1) ? sub_mod(e4.x, e5.x, q) : add_mod(e4.x, e5.x, q);
-                const uint64_t s = (k & 1) ? sub_mod(e6.x, e7.x, q) : add_mod(e6.x, e7.x, q);
-                u.x = (k & 2) ? sub_mod(p, s, q) : add_mod(p, s, q);
+                const uint64_t t = (k & 1) ? sub_mod(e6.x, e7.x, q) : add_mod(e6.x, e7.x, q);
+                u.x = (k & 2) ? sub_mod(p, t, q) : add_mod(p, t, q);
             }
             {
                 const uint64_t p = (k & 1) ? sub_mod(e4.y, e5.y, q) : add_mod(e4.y, e5.y, q);
-                const uint64_t s = (k & 1) ? sub_mod(e6.y, e7.y, q) : add_mod(e6.y, e7.y, q);
-                u.y = (k & 2) ? sub_mod(p, s, q) : add_mod(p, s, q);
+                const uint64_t t = (k & 1) ? sub_mod(e6.y, e7.y, q) : add_mod(e6.y, e7.y, q);
+                u.y = (k & 2) ? sub_mod(p, t, q) : add_mod(p, t, q);
             }
             ulonglong2 o0, o1;
             o0.x = add_mod(z[k].x, u.x, q);
             o0.y = add_mod(z[k].y, u.y, q);
             o1.x = sub_mod(z[k].x, u.x, q);
             o1.y = sub_mod(z[k].y, u.y, q);
-            *reinterpret_cast<ulonglong2 *>(outp + ((i0 + k * h) << logN) + m) = o0;
-            *reinterpret_cast<ulonglong2 *>(outp + ((i0 + (k + 4) * h) << logN) + m) = o1;
+            tw_store<MO>(outp, i0 + k * h, m, o0, logN, q);
+            tw_store<MO>(outp, i0 + (k + 4) * h, m, o1, logN, q);
         }
     }
 }
 
+template <bool MI, bool MO>
+static void tweak_radix8_go(dim3 g, cudaStream_t s, const uint64_t *in, uint64_t *out, int64_t n,
+                            int L, int logN, int lh, const NttPlane *tab, const TweakMap &mp) {
+    tweak_radix8_kernel<MI, MO><<<g, 256, 0, s>>>(in, out, n, L, logN, lh, tab, mp);
+}
+
 cudaError_t launch_tweak_radix8(const uint64_t *in, uint64_t *out, int64_t n, int L, int N,
-                                int64_t half, const NttPlane *tab, cudaStream_t s, int parts) {
+                                int64_t half, const NttPlane *tab, cudaStream_t s, int parts,
+                                const TweakMap &mp) {
     const int logN = 31 - __builtin_clz(N);
     const int lh = 63 - __builtin_clzll(static_cast<unsigned long long>(half));
     const int64_t per_plane = (n >> 3) * (N >> 1);
     const int64_t bx = std::min<int64_t>((per_plane + 255) / 256, 152 * 8);
-    tweak_radix8_kernel<<<dim3(static_cast<unsigned>(bx), parts * L), 256, 0, s>>>(in, out, n, L,
-                                                                                   logN, lh, tab);
+    const dim3 g(static_cast<unsigned>(bx), parts * L);
+    const bool mi = mp.in_bits > 0, mo = mp.out_t3 != 0;
+    if (mi && mo) tweak_radix8_go<true, true>(g, s, in, out, n, L, logN, lh, tab, mp);
+    else if (mi) tweak_radix8_go<true, false>(g, s, in, out, n, L, logN, lh, tab, mp);
+    else if (mo) tweak_radix8_go<false, true>(g, s, in, out, n, L, logN, lh, tab, mp);
+    else tweak_radix8_go<false, false>(g, s, in, out, n, L, logN, lh, tab, mp);
     return cudaGetLastError();
 }
 
@@ -570,17 +668,29 @@ __global__ void tweak_stage_scalar_kernel(const uint64_t *__restrict__ in,
     }
 }
 
+template <bool MI, bool MO>
+static void tweak_stage_go(dim3 g, cudaStream_t s, const uint64_t *in, uint64_t *out, int64_t n,
+                           int L, int logN, int lh, const NttPlane *tab, const TweakMap &mp) {
+    tweak_stage_kernel<MI, MO><<<g, 256, 0, s>>>(in, out, n, L, logN, lh, tab, mp);
+}
+
 cudaError_t launch_tweak_stage(const uint64_t *in, uint64_t *out, int64_t n, int L, int N,
-                               int64_t half, const NttPlane *tab, cudaStream_t s, int parts) {
+                               int64_t half, const NttPlane *tab, cudaStream_t s, int parts,
+                               const TweakMap &mp) {
     if (n < 2) return cudaSuccess;
     const int logN = 31 - __builtin_clz(N);
     const int lhalf = 63 - __builtin_clzll(static_cast<unsigned long long>(half));
     const int64_t per_plane = (n >> 1) * N;
+    const bool mi = mp.in_bits > 0, mo = mp.out_t3 != 0;
     if (lhalf < logN && N >= 2) {
         const int64_t bx = std::min<int64_t>((per_plane / 2 + 255) / 256, 152 * 8);
-        tweak_stage_kernel<<<dim3(static_cast<unsigned>(bx), parts * L), 256, 0, s>>>(
-            in, out, n, L, logN, lhalf, tab);
+        const dim3 g(static_cast<unsigned>(bx), parts * L);
+        if (mi && mo) tweak_stage_go<true, true>(g, s, in, out, n, L, logN, lhalf, tab, mp);
+        else if (mi) tweak_stage_go<true, false>(g, s, in, out, n, L, logN, lhalf, tab, mp);
+        else if (mo) tweak_stage_go<false, true>(g, s, in, out, n, L, logN, lhalf, tab, mp);
+        else tweak_stage_go<false, false>(g, s, in, out, n, L, logN, lhalf, tab, mp);
     } else {
+        if (mi || mo) return cudaErrorInvalidValue;  // the half = N stage takes no map
         const int64_t bx = std::min<int64_t>((per_plane + 255) / 256, 152 * 8);
         tweak_stage_scalar_kernel<<<dim3(static_cast<unsigned>(bx), parts * L), 256, 0, s>>>(
             in, out, n, L, logN, lhalf, tab);
