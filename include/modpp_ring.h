@@ -35,6 +35,9 @@
  * negative modpp_status before anything is enqueued, caller workspaces
  * (256-byte aligned) sized by the *_workspace queries, no device allocation
  * on the call path, outputs that do not overlap inputs unless stated.
+ * Ciphertext, key and output pointers must be 16-byte aligned (the kernels
+ * move neighbouring coefficient pairs in 16-byte accesses); a misaligned
+ * pointer returns MODPP_ERR_ARG before anything is enqueued.
  */
 #ifndef MODPP_RING_H
 #define MODPP_RING_H

@@ -339,6 +339,9 @@ CcLayout cc_layout(const modpp_ring_s *r) {
     return c;
 }
 
+// Ciphertext, key and output pointers: present and 16-byte aligned.
+bool a16(const void *p) { return p != nullptr && (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
 bool ws_ok(const void *ws, size_t have, size_t need) {
     if (need == 0) return true;
     return ws != nullptr && (reinterpret_cast<uintptr_t>(ws) & (kAlign - 1)) == 0 && have >= need;
@@ -495,7 +498,7 @@ int modpp_ring_destroy(modpp_ring ring) {
 }
 
 int modpp_ring_prepare_keys(modpp_ring r, uint64_t *keys, int64_t count, void *stream) {
-    if (r == nullptr || count < 0 || (count > 0 && keys == nullptr)) return MODPP_ERR_ARG;
+    if (r == nullptr || count < 0 || (count > 0 && !a16(keys))) return MODPP_ERR_ARG;
     const int Lp = r->L + 1;
     const int64_t polys = count * r->L * 2 * Lp;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
@@ -512,7 +515,7 @@ size_t modpp_keyswitch_workspace(modpp_ring r, int64_t n) {
 int modpp_keyswitch(modpp_ring r, const uint64_t *ct, uint64_t *out, int64_t n, const uint64_t *key,
                     void *ws, size_t ws_bytes, void *stream) {
     if (r == nullptr || n < 0) return MODPP_ERR_ARG;
-    if (n > 0 && (ct == nullptr || out == nullptr || key == nullptr)) return MODPP_ERR_ARG;
+    if (n > 0 && (!a16(ct) || !a16(out) || !a16(key))) return MODPP_ERR_ARG;
     if (!ws_ok(ws, ws_bytes, ks_scratch_bytes(r, n))) return MODPP_ERR_WORKSPACE;
     return ks_run(r, ct, n, n, out, n, key, r->kid_zero, 1, 0, static_cast<char *>(ws),
                   static_cast<cudaStream_t>(stream));
@@ -528,7 +531,7 @@ int modpp_tweak(modpp_ring r, const uint64_t *ct, uint64_t *out, int64_t n, void
     if (r == nullptr || n < 0) return MODPP_ERR_ARG;
     if (n == 0) return MODPP_OK;
     const int ln = log2_exact(n);
-    if (ln < 0 || n > 2 * r->N || ct == nullptr || out == nullptr) return MODPP_ERR_ARG;
+    if (ln < 0 || n > 2 * r->N || !a16(ct) || !a16(out)) return MODPP_ERR_ARG;
     if (!ws_ok(ws, ws_bytes, align_up(sizeof(uint64_t) * batch_words(r, n, r->L))))
         return MODPP_ERR_WORKSPACE;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
@@ -561,7 +564,7 @@ int modpp_transpose(modpp_ring r, const uint64_t *ct, uint64_t *out, int64_t gro
                     const uint64_t *aut_keys, void *ws, size_t ws_bytes, void *stream) {
     if (r == nullptr || groups < 0) return MODPP_ERR_ARG;
     if (groups == 0) return MODPP_OK;
-    if (ct == nullptr || out == nullptr || aut_keys == nullptr) return MODPP_ERR_ARG;
+    if (!a16(ct) || !a16(out) || !a16(aut_keys)) return MODPP_ERR_ARG;
     if (!ws_ok(ws, ws_bytes, transpose_scratch(r, groups))) return MODPP_ERR_WORKSPACE;
     return transpose_run(r, ct, out, groups, aut_keys, static_cast<char *>(ws),
                          static_cast<cudaStream_t>(stream));
@@ -570,7 +573,7 @@ int modpp_transpose(modpp_ring r, const uint64_t *ct, uint64_t *out, int64_t gro
 int modpp_rescale(modpp_ring r, const uint64_t *ct, uint64_t *out, int64_t n, void *stream) {
     if (r == nullptr || n < 0 || r->L < 2) return MODPP_ERR_ARG;
     if (n == 0) return MODPP_OK;
-    if (ct == nullptr || out == nullptr) return MODPP_ERR_ARG;
+    if (!a16(ct) || !a16(out)) return MODPP_ERR_ARG;
     return cuda_status(launch_rescale(ct, out, r->L, n * r->N, r->tab, r->qlinv, r->qlinv_s,
                                       static_cast<cudaStream_t>(stream)));
 }
@@ -583,7 +586,8 @@ size_t cc_mm_workspace(modpp_ring r) {
 int cc_mm(modpp_ring r, const uint64_t *ct1, const uint64_t *ct2, const uint64_t *aut_keys,
           const uint64_t *relin_key, uint64_t *out, void *ws, size_t ws_bytes, void *stream) {
     if (r == nullptr || r->L < 2) return MODPP_ERR_ARG;
-    if (!ct1 || !ct2 || !aut_keys || !relin_key || !out) return MODPP_ERR_ARG;
+    if (!a16(ct1) || !a16(ct2) || !a16(aut_keys) || !a16(relin_key) || !a16(out))
+        return MODPP_ERR_ARG;
     const CcLayout lay = cc_layout(r);
     if (!ws_ok(ws, ws_bytes, lay.total)) return MODPP_ERR_WORKSPACE;
     cudaStream_t st = static_cast<cudaStream_t>(stream);

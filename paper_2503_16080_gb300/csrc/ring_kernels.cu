@@ -142,14 +142,15 @@ __global__ void ks_multacc_kernel(const uint64_t *__restrict__ D, const uint64_t
                                   const int *__restrict__ kid, int kper, int L, int logN,
                                   int64_t c0, int64_t nb, const NttPlane *__restrict__ tab,
                                   uint64_t *__restrict__ U) {
+    // Two neighbouring coefficients per thread (16-byte accesses).
     const int Lp = L + 1;
     const int N = 1 << logN;
     const int64_t key_stride = static_cast<int64_t>(L) * 2 * Lp << logN;
-    const int64_t total = (nb * Lp) << logN;
+    const int64_t total = (nb * Lp) << (logN - 1);
     for (int64_t x = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; x < total;
          x += static_cast<int64_t>(gridDim.x) * blockDim.x) {
-        const int m = static_cast<int>(x) & (N - 1);
-        const int r = static_cast<int>(x >> logN);
+        const int m = (static_cast<int>(x) << 1) & (N - 1);
+        const int r = static_cast<int>(x >> (logN - 1));
         const int k = r % Lp;
         const int c = r / Lp;
         const int kc = kid[(c0 + c) % kper];
@@ -160,22 +161,37 @@ __global__ void ks_multacc_kernel(const uint64_t *__restrict__ D, const uint64_t
         const int64_t dstep = static_cast<int64_t>(Lp) << logN;     // next digit i
         const int64_t kstep = static_cast<int64_t>(2 * Lp) << logN; // next key digit i
         const int64_t kpart = static_cast<int64_t>(Lp) << logN;     // part 1 of a key digit
-        uint64_t u0 = 0, u1 = 0;
+        ulonglong2 u0 = make_ulonglong2(0, 0), u1 = make_ulonglong2(0, 0);
         for (int i = 0; i < L; ++i) {
-            const uint64_t di = d[i * dstep];
-            u0 = add_mod(u0, mont_mul(di, key[i * kstep], q, qinv), q);
-            u1 = add_mod(u1, mont_mul(di, key[i * kstep + kpart], q, qinv), q);
+            const ulonglong2 di = *reinterpret_cast<const ulonglong2 *>(d + i * dstep);
+            const ulonglong2 k0 = *reinterpret_cast<const ulonglong2 *>(key + i * kstep);
+            const ulonglong2 k1 = *reinterpret_cast<const ulonglong2 *>(key + i * kstep + kpart);
+            u0.x = add_mod(u0.x, mont_mul(di.x, k0.x, q, qinv), q);
+            u0.y = add_mod(u0.y, mont_mul(di.y, k0.y, q, qinv), q);
+            u1.x = add_mod(u1.x, mont_mul(di.x, k1.x, q, qinv), q);
+            u1.y = add_mod(u1.y, mont_mul(di.y, k1.y, q, qinv), q);
         }
         uint64_t *u = U + ((static_cast<int64_t>(c) * 2 * Lp + k) << logN) + m;
-        u[0] = u0;
-        u[kpart] = u1;
+        *reinterpret_cast<ulonglong2 *>(u) = u0;
+        *reinterpret_cast<ulonglong2 *>(u + kpart) = u1;
     }
 }
 
 // ModDown by P and accumulation: out_a = round(U_a / P), out_b = b + round(U_b / P),
 // with round(x / P) = (x_k - r) * P^-1 mod q_k, r = [x]_P centred.
 // Ciphertexts with kid < 0 are copied unchanged.  With b_zero the input
-// b-part is taken as 0 (Relin(D0, 0) in Alg. 8).  blockIdx.y = part * L + k.
+// b-part is taken as 0 (Relin(D0, 0) in Alg. 8).  One thread takes two
+// neighbouring coefficients of one (ciphertext, part) for every chain prime,
+// so the special prime's plane is read once.
+__device__ __forceinline__ uint64_t centred_mod(uint64_t up, uint64_t P, uint64_t q, uint64_t mu) {
+    // [up]_P centred (up - P if up > P/2), as a residue mod q
+    if (up > P / 2) {
+        const uint64_t mag = barrett_u64(P - up, q, mu);
+        return mag == 0 ? 0 : q - mag;
+    }
+    return barrett_u64(up, q, mu);
+}
+
 __global__ void ks_moddown_kernel(const uint64_t *__restrict__ U, const uint64_t *__restrict__ ct,
                                   int64_t n, int L, int logN, int64_t c0, int64_t nb,
                                   const int *__restrict__ kid, int kper, int b_zero,
@@ -185,34 +201,38 @@ __global__ void ks_moddown_kernel(const uint64_t *__restrict__ U, const uint64_t
                                   int64_t n_out) {
     const int Lp = L + 1;
     const int N = 1 << logN;
-    const int part = blockIdx.y / L;
-    const int k = blockIdx.y % L;
+    const int part = blockIdx.y;
     const uint64_t P = tab[L].q;
-    const uint64_t q = tab[k].q, mu = tab[k].mu, pv = pinv[k], pvs = pinv_s[k];
-    const uint64_t *ctp = ct + ((static_cast<int64_t>(part) * L + k) * n + c0) * N;
-    uint64_t *outp = out + ((static_cast<int64_t>(part) * L + k) * n_out + c0) * N;
-    const int64_t total = nb << logN;
+    const int64_t total = nb << (logN - 1);
     for (int64_t x = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; x < total;
          x += static_cast<int64_t>(gridDim.x) * blockDim.x) {
-        const int m = static_cast<int>(x) & (N - 1);
-        const int64_t c = x >> logN;
-        if (kid[(c0 + c) % kper] < 0) {
-            outp[x] = (part == 1 && b_zero) ? 0 : ctp[x];
-            continue;
-        }
+        const int m = (static_cast<int>(x) << 1) & (N - 1);
+        const int64_t c = x >> (logN - 1);
+        const bool copy = kid[(c0 + c) % kper] < 0;
         const int64_t ub = ((c * 2 + part) * Lp) << logN;
-        const uint64_t up = U[ub + (static_cast<int64_t>(L) << logN) + m];
-        const uint64_t uk = U[ub + (static_cast<int64_t>(k) << logN) + m];
-        // centred r: up - P if up > P/2; lift r into [0, q)
-        uint64_t rq;
-        if (up > P / 2) {
-            const uint64_t mag = barrett_u64(P - up, q, mu);
-            rq = mag == 0 ? 0 : q - mag;
-        } else {
-            rq = barrett_u64(up, q, mu);
+        ulonglong2 up = make_ulonglong2(0, 0);
+        if (!copy) up = *reinterpret_cast<const ulonglong2 *>(U + ub + (static_cast<int64_t>(L) << logN) + m);
+        for (int k = 0; k < L; ++k) {
+            const int64_t io = ((static_cast<int64_t>(part) * L + k) * n + c0 + c) * N + m;
+            const int64_t oo = ((static_cast<int64_t>(part) * L + k) * n_out + c0 + c) * N + m;
+            ulonglong2 v;
+            if (copy) {
+                v = (part == 1 && b_zero) ? make_ulonglong2(0, 0)
+                                          : *reinterpret_cast<const ulonglong2 *>(ct + io);
+            } else {
+                const uint64_t q = tab[k].q, mu = tab[k].mu, pv = pinv[k], pvs = pinv_s[k];
+                const ulonglong2 uk =
+                    *reinterpret_cast<const ulonglong2 *>(U + ub + (static_cast<int64_t>(k) << logN) + m);
+                v.x = shoup_mulmod(sub_mod(uk.x, centred_mod(up.x, P, q, mu), q), pv, pvs, q);
+                v.y = shoup_mulmod(sub_mod(uk.y, centred_mod(up.y, P, q, mu), q), pv, pvs, q);
+                if (part == 1 && !b_zero) {
+                    const ulonglong2 b = *reinterpret_cast<const ulonglong2 *>(ct + io);
+                    v.x = add_mod(b.x, v.x, q);
+                    v.y = add_mod(b.y, v.y, q);
+                }
+            }
+            *reinterpret_cast<ulonglong2 *>(out + oo) = v;
         }
-        const uint64_t v = shoup_mulmod(sub_mod(uk, rq, q), pv, pvs, q);
-        outp[x] = (part == 0 || b_zero) ? v : add_mod(ctp[x], v, q);
     }
 }
 
@@ -227,7 +247,7 @@ cudaError_t launch_ks_multacc(const uint64_t *D, const uint64_t *keys, const int
                               uint64_t *U, cudaStream_t s) {
     if (nb == 0) return cudaSuccess;
     const int logN = 31 - __builtin_clz(N);
-    const int64_t total = nb * (L + 1) * N;
+    const int64_t total = nb * (L + 1) * N / 2;
     const int64_t bx = std::min<int64_t>((total + 255) / 256, 152 * 16);
     ks_multacc_kernel<<<static_cast<unsigned>(bx), 256, 0, s>>>(D, keys, kid, kper, L, logN, c0, nb,
                                                                 tab, U);
@@ -239,8 +259,8 @@ cudaError_t launch_ks_moddown(const uint64_t *U, const uint64_t *ct, int64_t n, 
                               uint64_t *out, int64_t n_out, cudaStream_t s) {
     if (nb == 0) return cudaSuccess;
     const int logN = 31 - __builtin_clz(N);
-    const int64_t bx = std::min<int64_t>((nb * N + 255) / 256, 152 * 8);
-    ks_moddown_kernel<<<dim3(static_cast<unsigned>(bx), 2 * L), 256, 0, s>>>(
+    const int64_t bx = std::min<int64_t>((nb * N / 2 + 255) / 256, 152 * 8);
+    ks_moddown_kernel<<<dim3(static_cast<unsigned>(bx), 2), 256, 0, s>>>(
         U, ct, n, L, logN, c0, nb, kid, kper, b_zero, tab, pinv, pinv_s, out, n_out);
     return cudaGetLastError();
 }

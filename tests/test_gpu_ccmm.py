@@ -178,6 +178,22 @@ def test_ring_rejects_bad_arguments(lib_ready):
                     dev(np.zeros((16, 3, 2, 4, 16), dtype=np.uint64)))
 
 
+def test_ring_rejects_misaligned_pointers(lib_ready):
+    # The ring kernels move coefficient pairs in 16-byte accesses: pointers
+    # off a 16-byte boundary are refused on the host before any launch.
+    from paper_2503_16080_gb300.api import lib
+    N, L = 16, len(C.PR)
+    R = lib_ready.Ring(N, C.PRP)
+    buf = torch.zeros(2 * 2 * L * N + 4, dtype=torch.int64, device="cuda")
+    base = buf.data_ptr()
+    assert base % 16 == 0
+    out = base + 8 * (2 * L * N + 2)
+    assert lib().modpp_rescale(R._h, base + 8, out, 1, None) == -1
+    assert lib().modpp_rescale(R._h, base, out + 8, 1, None) == -1
+    assert lib().modpp_rescale(R._h, base, out, 1, None) == 0
+    torch.cuda.synchronize()
+
+
 @pytest.mark.parametrize("N", [2, 4, 8])
 def test_transpose_small_degrees(oracle_mod, lib_ready, N):
     s = synth.ternary(N, 7, N)
