@@ -55,57 +55,102 @@ __device__ __forceinline__ Limbs to_limbs(int64_t x) {
     return Limbs{static_cast<uint32_t>(m & 0x1fffffu), static_cast<uint32_t>((m >> 21) & 0x1fffffu),
                  static_cast<uint32_t>(m >> 42), x < 0};
 }
-// Balanced residue in [-(p-1)/2, (p-1)/2].
-__device__ __forceinline__ int bal_mod(const Limbs &l, const RnsPrime &pp) {
-    const uint32_t r = mod_small(l.m2 * pp.t42 + l.m1 * pp.t21 + l.m0, pp.p, pp.mag);
-    int v = static_cast<int>(r);
-    if (l.neg && v != 0) v = static_cast<int>(pp.p) - v;
+
+// Balanced residue of |x| in [-(p-1)/2, (p-1)/2] (the caller applies x's sign).
+__device__ __forceinline__ int bal_mod_abs(const Limbs &l, const RnsPrime &pp) {
+    int v = static_cast<int>(mod_small(l.m2 * pp.t42 + l.m1 * pp.t21 + l.m0, pp.p, pp.mag));
     if (2 * v > static_cast<int>(pp.p)) v -= static_cast<int>(pp.p);
     return v;
 }
 
+// f16 bits of two small integers |v| < 512, as a half2 word: 1536 + v lies
+// in [1024, 2048), where f16 values are the integers, so its bit pattern is
+// 0x6600 + v, and subtracting 1536 in f16 is exact.  sign: 0x8000 in the
+// half of each value to negate (a negated zero is -0, which multiplies and
+// adds as 0).
+__device__ __forceinline__ uint32_t small_half2(int v0, int v1, uint32_t sign) {
+    const uint32_t biased = static_cast<uint32_t>(0x6600 + v0) |
+                            (static_cast<uint32_t>(0x6600 + v1) << 16);
+    __half2 h = *reinterpret_cast<const __half2 *>(&biased);
+    h = __hsub2(h, __float2half2_rn(1536.0f));
+    return *reinterpret_cast<const uint32_t *>(&h) ^ sign;
+}
+
 // U (d x k residues mod q, leading dimension ldu) -> R planes of balanced
 // residues mod p_i as f16, plane i rows [i d, (i+1) d) of a (R d) x kp matrix
-// (zero padded for t >= k).
+// (zero padded for t >= k).  One thread takes 8 consecutive entries of a row
+// (kp is a multiple of 8) and writes one 16-byte word per prime.
 __global__ void __launch_bounds__(256) rns_split_u_kernel(const uint64_t *__restrict__ U,
                                                           int64_t ldu, int d, int k, int kp,
                                                           uint64_t q, RnsPrimes pr,
                                                           __half *__restrict__ U16) {
-    const int64_t total = static_cast<int64_t>(d) * kp;
+    const int gpr = kp >> 3;  // groups of 8 per row
+    const int64_t groups = static_cast<int64_t>(d) * gpr;
     const int64_t plane = static_cast<int64_t>(d) * kp;
     const uint64_t half_q = q >> 1;
-    for (int64_t e = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; e < total;
-         e += static_cast<int64_t>(gridDim.x) * blockDim.x) {
-        const int64_t r = e / kp;
-        const int t = static_cast<int>(e - r * kp);
-        int64_t x = 0;
-        if (t < k) {
-            const uint64_t u = U[r * ldu + t];
-            x = u > half_q ? static_cast<int64_t>(u) - static_cast<int64_t>(q)
-                           : static_cast<int64_t>(u);
+    const bool vec = (reinterpret_cast<uintptr_t>(U) & 15u) == 0 && (ldu & 1) == 0;
+    for (int64_t g = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; g < groups;
+         g += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        const int64_t r = g / gpr;
+        const int t = static_cast<int>(g - r * gpr) << 3;
+        const uint64_t *row = U + r * ldu + t;
+        uint64_t u[8];
+        if (vec && t + 8 <= k) {
+#pragma unroll
+            for (int j = 0; j < 8; j += 2) {
+                const ulonglong2 w = *reinterpret_cast<const ulonglong2 *>(row + j);
+                u[j] = w.x;
+                u[j + 1] = w.y;
+            }
+        } else {
+#pragma unroll
+            for (int j = 0; j < 8; ++j) u[j] = t + j < k ? row[j] : 0;
         }
-        const Limbs l = to_limbs(x);
-        for (int i = 0; i < pr.R; ++i) U16[i * plane + e] = __int2half_rn(bal_mod(l, pr.p[i]));
+        Limbs l[8];
+        uint32_t sign[4] = {0, 0, 0, 0};
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const int64_t x = u[j] > half_q ? static_cast<int64_t>(u[j]) - static_cast<int64_t>(q)
+                                            : static_cast<int64_t>(u[j]);
+            l[j] = to_limbs(x);
+            if (l[j].neg) sign[j >> 1] |= (j & 1) ? 0x80000000u : 0x8000u;
+        }
+        __half *out = U16 + r * kp + t;
+        for (int i = 0; i < pr.R; ++i) {
+            const RnsPrime pp = pr.p[i];
+            uint4 w;
+            w.x = small_half2(bal_mod_abs(l[0], pp), bal_mod_abs(l[1], pp), sign[0]);
+            w.y = small_half2(bal_mod_abs(l[2], pp), bal_mod_abs(l[3], pp), sign[1]);
+            w.z = small_half2(bal_mod_abs(l[4], pp), bal_mod_abs(l[5], pp), sign[2]);
+            w.w = small_half2(bal_mod_abs(l[6], pp), bal_mod_abs(l[7], pp), sign[3]);
+            *reinterpret_cast<uint4 *>(out + i * plane) = w;
+        }
     }
 }
 
 // A (k x n residues mod q, leading dimension lda) -> R K-major planes: row
 // (i * nblk + c / 256) * 256 + c % 256 holds column c of A's residues mod
-// p_i over the inner index (kp halves per row).  One block per 64 x 64 tile.
+// p_i over the inner index (kp halves per row).  One block per 64 x 64 tile:
+// thread (column cl, quarter tq) reads 16 consecutive inner indices of its
+// column (a warp reads 32 neighbouring columns of one row), packs their
+// residues into two 16-byte words of the transposed shared tile, and 8
+// threads per 128-byte row write the tile out along the inner index.
 __global__ void __launch_bounds__(256) rns_split_a_kernel(const uint64_t *__restrict__ A,
                                                           int64_t lda, int k, int n, int kp,
                                                           int nblk, uint64_t q, RnsPrimes pr,
                                                           __half *__restrict__ D) {
-    __shared__ __align__(16) __half tile[64 * (kRnsT + 8)];
+    constexpr int kRow = kRnsT + 8;  // padded tile row (halves): 144 bytes
+    __shared__ __align__(16) __half tile[64 * kRow];
     const int t0 = blockIdx.x * kRnsT;
     const int c0 = blockIdx.y * 64;
     const uint64_t half_q = q >> 1;
+    const int cl = threadIdx.x & 63;
+    const int tq = (threadIdx.x >> 6) * 16;
     Limbs x[16];
+    uint32_t sign[8] = {0, 0, 0, 0, 0, 0, 0, 0};
 #pragma unroll
     for (int s = 0; s < 16; ++s) {
-        const int e = threadIdx.x + 256 * s;  // 64 x 64 elements, column fastest
-        const int tl = e >> 6, cl = e & 63;
-        const int t = t0 + tl, c = c0 + cl;
+        const int t = t0 + tq + s, c = c0 + cl;
         int64_t v = 0;
         if (t < k && c < n) {
             const uint64_t a = A[static_cast<int64_t>(t) * lda + c];
@@ -113,23 +158,26 @@ __global__ void __launch_bounds__(256) rns_split_a_kernel(const uint64_t *__rest
                            : static_cast<int64_t>(a);
         }
         x[s] = to_limbs(v);
+        if (x[s].neg) sign[s >> 1] |= (s & 1) ? 0x80000000u : 0x8000u;
     }
     const int sub = threadIdx.x & 7;   // 8 threads per 128-byte row, 8 halves each
     const int t = t0 + 8 * sub;
+    uint4 *dst = reinterpret_cast<uint4 *>(&tile[cl * kRow + tq]);
     for (int i = 0; i < pr.R; ++i) {
+        const RnsPrime pp = pr.p[i];
+        uint32_t w[8];
 #pragma unroll
-        for (int s = 0; s < 16; ++s) {
-            const int e = threadIdx.x + 256 * s;
-            const int tl = e >> 6, cl = e & 63;
-            tile[cl * (kRnsT + 8) + tl] = __int2half_rn(bal_mod(x[s], pr.p[i]));
-        }
+        for (int j = 0; j < 8; ++j)
+            w[j] = small_half2(bal_mod_abs(x[2 * j], pp), bal_mod_abs(x[2 * j + 1], pp), sign[j]);
+        dst[0] = make_uint4(w[0], w[1], w[2], w[3]);
+        dst[1] = make_uint4(w[4], w[5], w[6], w[7]);
         __syncthreads();
         if (t < kp) {
             for (int row = threadIdx.x >> 3; row < 64; row += 32) {
                 const int c = c0 + row;
                 const int64_t drow =
                     (static_cast<int64_t>(i) * nblk + c / kRnsNC) * kRnsNC + (c % kRnsNC);
-                const uint4 v = *reinterpret_cast<const uint4 *>(&tile[row * (kRnsT + 8) + 8 * sub]);
+                const uint4 v = *reinterpret_cast<const uint4 *>(&tile[row * kRow + 8 * sub]);
                 *reinterpret_cast<uint4 *>(D + drow * kp + t) = v;
             }
         }
@@ -137,27 +185,36 @@ __global__ void __launch_bounds__(256) rns_split_a_kernel(const uint64_t *__rest
     }
 }
 
-// C[r][c] = X mod q from the R balanced residues res[ch][i][r][c] (int8,
-// plane stride d * n, row stride n; the chunks' residues of one prime add).
-// Per small prime, y = r c_i mod p_i and
-// y / p_i come from shared-memory tables indexed by r; the sum
-// S = sum_i y_i w_i is kept as two 64-bit halves, S = S_hi 2^32 + S_lo with
-// w_i = w_hi 2^32 + w_lo (y_i w_lo < 2^40, y_i w_hi < 2^38: no overflow for
-// R <= 32), and reduced modulo q once.  Four consecutive outputs per thread
+// C[r][c] = X mod q from the R balanced residues res[i][r][c] (int8, plane
+// stride d * n, row stride n).  Per small prime one shared-memory word,
+// indexed by the residue r, holds y = r c_i mod p_i in its top 8 bits and
+// y / p_i in 0.24 fixed point below (one table read per prime: the reads
+// are at data-dependent addresses, so bank conflicts make them the cost).
+// The sum S = sum_i y_i w_i (w_i = (M / p_i) mod q) is one 64-bit word when
+// R (p_max - 1) (q - 1) < 2^64 (ONE: 50-bit chain primes), else two 64-bit
+// halves, S = S_hi 2^32 + S_lo with w_i = w_hi 2^32 + w_lo (y_i w_lo < 2^40,
+// y_i w_hi < 2^38: no overflow for R <= 32); either way it is reduced modulo
+// q once.  alpha = round(sum_i
+// y_i / p_i) from the fixed-point parts (rounding error below 2^-19 against
+// the 0.14 margin of |X| / M < 0.36).  Four consecutive outputs per thread
 // (n % 4 == 0) with 32-bit residue loads; one otherwise.
-template <int V>
+template <int V, bool ONE>
 __global__ void __launch_bounds__(256) rns_crt_kernel(const int8_t *__restrict__ res, int d, int n,
                                                       RnsCrt cr, uint64_t *__restrict__ C,
                                                       int64_t ldc) {
-    __shared__ uint8_t ytab[kMaxRnsPrimes][256];
-    __shared__ float ftab[kMaxRnsPrimes][256];
+    __shared__ uint32_t ytab[kMaxRnsPrimes][256];
     for (int e = threadIdx.x; e < cr.R * 256; e += blockDim.x) {
         const int i = e >> 8, r = (e & 255) - 128;  // residue r in [-128, 127]
         const int p = cr.p[i];
         int y = (r * cr.c[i]) % p;
         if (y < 0) y += p;
-        ytab[i][e & 255] = static_cast<uint8_t>(y);
-        ftab[i][e & 255] = static_cast<float>(y) * cr.pinv[i];
+        const uint32_t frac = static_cast<uint32_t>(
+            (static_cast<uint64_t>(y) << 24) / static_cast<uint64_t>(p) +
+            ((((static_cast<uint64_t>(y) << 24) % static_cast<uint64_t>(p)) * 2 >=
+              static_cast<uint64_t>(p))
+                 ? 1u
+                 : 0u));
+        ytab[i][e & 255] = (static_cast<uint32_t>(y) << 24) | frac;
     }
     __syncthreads();
     const uint64_t q = cr.q;
@@ -167,12 +224,12 @@ __global__ void __launch_bounds__(256) rns_crt_kernel(const int8_t *__restrict__
          g += static_cast<int64_t>(gridDim.x) * blockDim.x) {
         const int64_t e0 = g * V;
         uint64_t slo[V], shi[V];
-        float F[V];
+        uint32_t F[V];
 #pragma unroll
         for (int v = 0; v < V; ++v) {
             slo[v] = 0;
             shi[v] = 0;
-            F[v] = 0.f;
+            F[v] = 0;
         }
         // Residue words in batches of 8 primes: eight loads in flight, then
         // their sums.
@@ -191,26 +248,44 @@ __global__ void __launch_bounds__(256) rns_crt_kernel(const int8_t *__restrict__
                 const int i = i0 + u;
                 if (i >= cr.R) break;
                 const uint32_t wl = cr.wlo[i], wh = cr.whi[i];
+                const uint64_t w = (static_cast<uint64_t>(wh) << 32) | wl;
 #pragma unroll
                 for (int v = 0; v < V; ++v) {
-                    const int idx = static_cast<int8_t>((words[u] >> (8 * v)) & 0xffu) + 128;
-                    const uint32_t y = ytab[i][idx];
-                    slo[v] += static_cast<uint64_t>(y) * wl;
-                    shi[v] += static_cast<uint64_t>(y) * wh;
-                    F[v] += ftab[i][idx];
+                    const uint32_t idx = ((words[u] >> (8 * v)) & 0xffu) ^ 0x80u;  // r + 128
+                    const uint32_t t = ytab[i][idx];
+                    const uint32_t y = t >> 24;
+                    if constexpr (ONE) {
+                        slo[v] += y * w;
+                    } else {
+                        slo[v] += static_cast<uint64_t>(y) * wl;
+                        shi[v] += static_cast<uint64_t>(y) * wh;
+                    }
+                    F[v] += t & 0xffffffu;
                 }
             }
         }
+        // The V outputs share one row (n % V == 0): one division per thread.
+        const int64_t row = e0 / n;
+        uint64_t *out = C + row * ldc + (e0 - row * n);
+        uint64_t x[V];
 #pragma unroll
         for (int v = 0; v < V; ++v) {
-            // S mod q = (S_hi mod q) 2^32 + S_lo (mod q)
-            uint64_t x = shoup_mulmod(barrett_u64(shi[v], q, cr.mu), cr.t32, cr.t32s, q);
-            x = add_mod(x, barrett_u64(slo[v], q, cr.mu), q);
-            const uint64_t alpha = static_cast<uint64_t>(__float2int_rn(F[v]));
-            x = sub_mod(x, shoup_mulmod(alpha, cr.mq, cr.mqs, q), q);
-            const int64_t e = e0 + v;
-            const int64_t row = e / n;
-            C[row * ldc + (e - row * n)] = x;
+            if constexpr (ONE) {
+                x[v] = barrett_u64(slo[v], q, cr.mu);  // S itself fits 64 bits
+            } else {
+                // S mod q = (S_hi mod q) 2^32 + S_lo (mod q)
+                x[v] = shoup_mulmod(barrett_u64(shi[v], q, cr.mu), cr.t32, cr.t32s, q);
+                x[v] = add_mod(x[v], barrett_u64(slo[v], q, cr.mu), q);
+            }
+            const uint64_t alpha = (F[v] + (1u << 23)) >> 24;
+            x[v] = sub_mod(x[v], shoup_mulmod(alpha, cr.mq, cr.mqs, q), q);
+        }
+        if (V == 4 && (reinterpret_cast<uintptr_t>(out) & 15u) == 0) {
+            *reinterpret_cast<ulonglong2 *>(out) = make_ulonglong2(x[0], x[1 % V]);
+            *reinterpret_cast<ulonglong2 *>(out + 2) = make_ulonglong2(x[2 % V], x[3 % V]);
+        } else {
+#pragma unroll
+            for (int v = 0; v < V; ++v) out[v] = x[v];
         }
     }
 }
@@ -323,7 +398,6 @@ RnsCrt rns_crt_consts(const RnsPrimes &pr, uint64_t q) {
         c.c[i] = static_cast<int>(host_powmod_u(wp, p - 2, p));  // (M/p_i)^-1 mod p_i
         c.wlo[i] = static_cast<uint32_t>(wq & 0xffffffffu);
         c.whi[i] = static_cast<uint32_t>(wq >> 32);
-        c.pinv[i] = 1.0f / static_cast<float>(p);
     }
     return c;
 }
@@ -353,7 +427,7 @@ int rns_split(int64_t d, int64_t k, int64_t n, const uint64_t *U, int64_t ldu, c
     __half *U16 = reinterpret_cast<__half *>(ws + lay.off_u16);
     __half *D = reinterpret_cast<__half *>(ws + lay.off_d);
     if (split_u) {
-        const int64_t total = d * lay.kp;
+        const int64_t total = d * (lay.kp / 8);
         const int blocks = static_cast<int>(std::min<int64_t>((total + 255) / 256, 152 * 16));
         rns_split_u_kernel<<<blocks, 256, 0, st>>>(U, ldu, static_cast<int>(d), static_cast<int>(k),
                                                    static_cast<int>(lay.kp), q, pr, U16);
@@ -416,12 +490,21 @@ int rns_crt(int64_t d, int64_t n, uint64_t *C, int64_t ldc, uint64_t q, const Rn
     const int V = n % 4 == 0 ? 4 : 1;
     const int blocks =
         static_cast<int>(std::min<int64_t>((total / V + 255) / 256, 152 * 8));
-    if (V == 4)
-        rns_crt_kernel<4><<<blocks, 256, 0, st>>>(res, static_cast<int>(d), static_cast<int>(n), cr,
-                                                  C, ldc);
+    // One 64-bit sum when R (p_max - 1) (q - 1) < 2^64.
+    uint32_t pmax = 0;
+    for (int i = 0; i < pr.R; ++i) pmax = std::max(pmax, pr.p[i].p);
+    const unsigned __int128 bound =
+        static_cast<unsigned __int128>(pr.R) * (pmax - 1) * (q - 1);
+    const bool one = bound < (static_cast<unsigned __int128>(1) << 64);
+    const int di = static_cast<int>(d), ni = static_cast<int>(n);
+    if (V == 4 && one)
+        rns_crt_kernel<4, true><<<blocks, 256, 0, st>>>(res, di, ni, cr, C, ldc);
+    else if (V == 4)
+        rns_crt_kernel<4, false><<<blocks, 256, 0, st>>>(res, di, ni, cr, C, ldc);
+    else if (one)
+        rns_crt_kernel<1, true><<<blocks, 256, 0, st>>>(res, di, ni, cr, C, ldc);
     else
-        rns_crt_kernel<1><<<blocks, 256, 0, st>>>(res, static_cast<int>(d), static_cast<int>(n), cr,
-                                                  C, ldc);
+        rns_crt_kernel<1, false><<<blocks, 256, 0, st>>>(res, di, ni, cr, C, ldc);
     return cudaGetLastError() == cudaSuccess ? 0 : -5;
 }
 

@@ -31,7 +31,6 @@ struct RnsCrt {
     uint64_t mq, mqs;             // M mod q and its Shoup quotient
     int p[kMaxRnsPrimes];
     int c[kMaxRnsPrimes];         // (M / p_i)^-1 mod p_i
-    float pinv[kMaxRnsPrimes];    // 1 / p_i
     uint32_t wlo[kMaxRnsPrimes];  // (M / p_i) mod q, low and high 32 bits
     uint32_t whi[kMaxRnsPrimes];
     uint64_t mu;                  // Barrett constant of q
