@@ -768,6 +768,52 @@ def run_secondary(args):
             torch.cuda.synchronize()
             line["fp64_matmul_ms"] = f0.elapsed_time(f1)
             line["slowdown_vs_fp64_matmul"] = ms / line["fp64_matmul_ms"]
+    elif args.workload == "hostlink":
+        # Pinned host <-> device copy rates (the bound of the end-to-end
+        # numbers): one direction at a time, and both at once on separate
+        # streams; 400 MB per copy, CUDA events around each timed batch.
+        nbytes = 400 << 20
+        hb = [torch.empty(nbytes // 8, dtype=torch.int64).pin_memory() for _ in range(2)]
+        db = [torch.empty(nbytes // 8, dtype=torch.int64, device=dev) for _ in range(2)]
+        s_in, s_out = torch.cuda.Stream(), torch.cuda.Stream()
+
+        def rate(copies, reps=5):
+            for _ in range(2):
+                copies()
+            torch.cuda.synchronize()
+            t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            t0.record(stream)
+            for _ in range(reps):
+                s_in.wait_stream(stream)
+                s_out.wait_stream(stream)
+                copies()
+                stream.wait_stream(s_in)
+                stream.wait_stream(s_out)
+            t1.record(stream)
+            torch.cuda.synchronize()
+            return t0.elapsed_time(t1) / reps
+
+        def h2d():
+            with torch.cuda.stream(s_in):
+                db[0].copy_(hb[0], non_blocking=True)
+
+        def d2h():
+            with torch.cuda.stream(s_out):
+                hb[1].copy_(db[1], non_blocking=True)
+
+        def both():
+            h2d()
+            d2h()
+
+        ms_in, ms_out, ms_both = rate(h2d), rate(d2h), rate(both)
+        step_in, step_out = 822083584, 805306368  # bytes per PC-MM n=4096 step (e2e)
+        bidir = 2 * nbytes / (ms_both * 1e-3) / 1e9
+        line.update({"workload": "hostlink", "unit": "GB/s", "value": bidir,
+                     "config": {"workload": "pinned host <-> device copies, 400 MB each"},
+                     "h2d_gbs": nbytes / (ms_in * 1e-3) / 1e9,
+                     "d2h_gbs": nbytes / (ms_out * 1e-3) / 1e9,
+                     "bidirectional_gbs": bidir,
+                     "pcmm4096_e2e_bound_ms": (step_in + step_out) / (bidir * 1e9) * 1e3})
     elif args.workload == "umma_sweep":
         # Tensor throughput of the digit GEMM against UMMA N: one plane of
         # 8192^3 with primes of 9, 18, 27, 36, 45 and 50 bits gives L = 1..6
@@ -1036,7 +1082,7 @@ def main():
                     help="digit width of the f16 path (8, 9, 10; 0 = library default)")
     ap.add_argument("--workload", default="pcmm4096",
                     choices=["pcmm4096", "pcmm16384", "pcmv", "grouped", "ccmm8192",
-                             "umma_sweep"],
+                             "umma_sweep", "hostlink"],
                     help="pcmm4096 (default, the benchmark line); the others are recorded "
                          "beside it")
     ap.add_argument("--n", type=int, default=4096,
