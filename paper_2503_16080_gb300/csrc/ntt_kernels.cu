@@ -357,6 +357,9 @@ cudaError_t launch_fast(const NttFastArgs &a, int64_t npolys, cudaStream_t s) {
 
 }  // namespace
 
+// Coefficients per thread of the fused key switch (N / kKsE threads per CTA).
+constexpr int kKsE = 8;
+
 bool ks_fused_supported(int N) { return N >= 1024 && N <= 8192 && (N & (N - 1)) == 0; }
 
 cudaError_t launch_ks_fused(const uint64_t *ct, int64_t n, int L, int N, int64_t c0, int64_t nb,
@@ -376,11 +379,11 @@ cudaError_t launch_ks_fused(const uint64_t *ct, int64_t n, int L, int N, int64_t
     a.kper = kper;
     a.U = U;
     const size_t smem = 3 * static_cast<size_t>(N + N / 32) * sizeof(uint64_t);
-    cudaError_t e = cudaFuncSetAttribute(ks_fused_kernel<16>,
+    cudaError_t e = cudaFuncSetAttribute(ks_fused_kernel<kKsE>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          static_cast<int>(smem));
     if (e != cudaSuccess) return e;
-    ks_fused_kernel<16><<<static_cast<unsigned>(nb * (L + 1)), N / 16, smem, s>>>(a);
+    ks_fused_kernel<kKsE><<<static_cast<unsigned>(nb * (L + 1)), N / kKsE, smem, s>>>(a);
     return cudaGetLastError();
 }
 
