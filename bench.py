@@ -995,11 +995,21 @@ def run_ccmm(args):
     h1.copy_(ct1)
     h2.copy_(ct2)
 
-    def e2e_step():
+    marks = []
+
+    def e2e_step(record=False):
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)] if record else None
         ct1.copy_(h1, non_blocking=True)
         ct2.copy_(h2, non_blocking=True)
+        if record:
+            ev[0].record(stream)
         step()
+        if record:
+            ev[1].record(stream)
         ho.copy_(out, non_blocking=True)
+        if record:
+            ev[2].record(stream)
+            marks.append(ev)
 
     e2e_step()
     torch.cuda.synchronize()
@@ -1007,10 +1017,17 @@ def run_ccmm(args):
     e2e_steps = max(1, min(args.steps, 3))
     g0.record(stream)
     for _ in range(e2e_steps):
-        e2e_step()
+        e2e_step(record=True)
     g1.record(stream)
     torch.cuda.synchronize()
     e2e_ms = g0.elapsed_time(g1) / e2e_steps
+    # Per part: copy-in (from the previous step's end), product, copy-out.
+    starts = [g0] + [m[2] for m in marks[:-1]]
+    e2e_parts = {
+        "h2d_ms": sum(a.elapsed_time(m[0]) for a, m in zip(starts, marks)) / e2e_steps,
+        "cc_mm_ms": sum(m[0].elapsed_time(m[1]) for m in marks) / e2e_steps,
+        "d2h_ms": sum(m[1].elapsed_time(m[2]) for m in marks) / e2e_steps,
+    }
 
     # CPU oracle on a small ring (N=512): the whole CC-MM, and its Mod-PP-MM
     # part alone; the products extrapolate by N^3, the rest (transposes, key
@@ -1062,7 +1079,8 @@ def run_ccmm(args):
             "fp64_matmul_ms": dgemm_ms, "slowdown_vs_fp64_matmul": ms / dgemm_ms,
             "decrypt": dec,
             "e2e": {"value": e2e_ms, "unit": "ms per CC-MM", "h2d_bytes_per_step":
-                    8 * (h1.numel() + h2.numel()), "d2h_bytes_per_step": 8 * ho.numel()},
+                    8 * (h1.numel() + h2.numel()), "d2h_bytes_per_step": 8 * ho.numel(),
+                    "parts": e2e_parts},
             "cpu_baseline": cpu, "clocks": clk}
     ring.close()
     print(json.dumps(line))
