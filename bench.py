@@ -539,6 +539,7 @@ def run_ours(args):
         del Ud, Md
 
         fp64_ms = None
+        fp64_tight_ms = None
         fp64_identical = None
         if not args.no_fp64:
             pkg.pc_mm(U, A, B, primes, out=(Aout, Bout), path="fp64")
@@ -551,6 +552,18 @@ def run_ours(args):
             fp64_ms = g0.elapsed_time(g1)
             fp64_identical = bool(torch.equal(Aout.view(torch.int64), ref_out[0]) and
                                   torch.equal(Bout.view(torch.int64), ref_out[1]))
+            # The tight asymmetric split: U is one digit (|U| <= 128), so A's base can be
+            # 2^53 / (128 k), two digits per residue at k = 4096 instead of three.
+            pkg.pc_mm(U, A, B, primes, out=(Aout, Bout), path="fp64_tight")
+            torch.cuda.synchronize()
+            g0.record(stream)
+            pkg.pc_mm(U, A, B, primes, out=(Aout, Bout), path="fp64_tight")
+            g1.record(stream)
+            torch.cuda.synchronize()
+            fp64_tight_ms = g0.elapsed_time(g1)
+            fp64_identical = fp64_identical and bool(
+                torch.equal(Aout.view(torch.int64), ref_out[0]) and
+                torch.equal(Bout.view(torch.int64), ref_out[1]))
         del ref_out
 
         # End to end through the public call with host buffers: every step
@@ -654,6 +667,7 @@ def run_ours(args):
             "fp64_matmul_ms": dgemm_ms,
             "slowdown_vs_fp64_matmul": ms_per_step / dgemm_ms,
             "fp64_limb_pc_mm_ms": fp64_ms,
+            "fp64_limb_tight_pc_mm_ms": fp64_tight_ms,
             "fp64_limb_outputs_identical": fp64_identical,
             "decrypt": dec,
             "int8_limb": "unavailable: tcgen05.mma kind::i8 is not supported on sm_103a (ptxas)",

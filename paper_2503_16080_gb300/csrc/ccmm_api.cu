@@ -536,14 +536,11 @@ int modpp_tweak(modpp_ring r, const uint64_t *ct, uint64_t *out, int64_t n, void
         return MODPP_ERR_WORKSPACE;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     uint64_t *w = static_cast<uint64_t *>(ws);
-    if (n == 1) {  // no stage: the Tweak of one ciphertext is itself
-        GatherTables t{};
-        t.per = 1;
-        return launch_ct_gather(ct, out, 1, r->L, static_cast<int>(r->N), t, r->tab, st) ==
-                       cudaSuccess
+    if (n == 1)  // no stage: the Tweak of one ciphertext is itself
+        return cudaMemcpyAsync(out, ct, sizeof(uint64_t) * batch_words(r, 1, r->L),
+                               cudaMemcpyDeviceToDevice, st) == cudaSuccess
                    ? MODPP_OK
                    : MODPP_ERR_CUDA;
-    }
     // The first pass reads the inputs in bit-reversed order; the passes
     // alternate between the workspace and out so that the last lands in out.
     int rc = MODPP_OK;

@@ -24,19 +24,13 @@ struct NttPlane {
 // Per-ciphertext tables of a gather: every table has period `per` over the
 // batch (ciphertext c reads entry c mod per; source indices are relative to
 // the period block of c, and per is a power of two).  Null tables mean
-// identity source, shift 0, ell 1.
-// brev_bits > 0 takes the source index as the bit reversal of (c mod per)
-// over brev_bits bits instead of src; shift_src takes the shift equal to the
-// source index (the X^i ct_i of Alg. 4, step 1).
+// identity source and ell 1.
 struct GatherTables {
     const int *src;
-    const int *shift;
     const int *ellinv;        // ell^-1 mod 2N of the automorphism, or null (ell = 1)
     const uint64_t *scale;    // per plane, or null
     const uint64_t *scale_s;
     int per;
-    int brev_bits;
-    int shift_src;
 };
 
 // Negacyclic NTT of npolys polynomials in place; polynomial p uses the

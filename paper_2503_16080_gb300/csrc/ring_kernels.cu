@@ -269,14 +269,13 @@ cudaError_t launch_ks_moddown(const uint64_t *U, const uint64_t *ct, int64_t n, 
 // Batches have power-of-two N (and, for Tweak, n and the table period), so
 // every index below is a shift or a mask; blockIdx.y selects the (part,
 // prime) plane: 2L of them, or the L a-part planes only (parts = 1).
-__device__ __forceinline__ int ilog2(int x) { return 31 - __clz(x); }
 
-// out[c] = scale * X^shift(c) * sigma_ell(c)(in[src(c)]) for every part and
-// plane; the tables repeat with period t.per (ciphertext c reads entry c mod
-// per, and src is relative to the block of `per` ciphertexts holding c).
-// X^t multiplies by a signed rotation (X^N = -1); sigma_ell maps X^i to
-// X^(i*ell mod 2N).  One thread per output coefficient: it reads input
-// coefficient i = (pos - shift) * ell^-1 mod 2N.
+// out[c] = scale * sigma_ell(c)(in[src(c)]) for every part and plane (the
+// N^-1, source permutation and Aut before the key switches of Alg. 4); the
+// tables repeat with period t.per (ciphertext c reads entry c mod per, and
+// src is relative to the block of `per` ciphertexts holding c).  sigma_ell
+// maps X^i to X^(i*ell mod 2N) (X^N = -1).  One thread per output
+// coefficient: it reads input coefficient i = pos * ell^-1 mod 2N.
 __global__ void ct_gather_kernel(const uint64_t *__restrict__ in, uint64_t *__restrict__ out,
                                  int64_t n, int L, int logN, GatherTables t,
                                  const NttPlane *__restrict__ tab) {
@@ -299,11 +298,8 @@ __global__ void ct_gather_kernel(const uint64_t *__restrict__ in, uint64_t *__re
         const int pos = static_cast<int>(x) & (N - 1);
         const int64_t c = x >> logN;
         const int ci = static_cast<int>(c) & per_mask;
-        const int si = t.brev_bits > 0 ? static_cast<int>(__brev(static_cast<unsigned>(ci)) >>
-                                                          (32 - t.brev_bits))
-                                       : (t.src ? t.src[ci] : ci);
-        const int sh = t.shift_src ? si : (t.shift ? t.shift[ci] : 0);
-        int e = (pos - sh) & twoN_mask;
+        const int si = t.src ? t.src[ci] : ci;
+        int e = pos;
         if (t.ellinv) e = static_cast<int>((static_cast<int64_t>(e) * t.ellinv[ci]) & twoN_mask);
         const bool neg = e >= N;
         e &= N - 1;
