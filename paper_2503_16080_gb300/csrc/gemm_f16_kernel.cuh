@@ -427,14 +427,22 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
                     for (int k4 = 0; k4 < 4; ++k4) {
                         const int c = c0 + k4;
-                        uint64_t x = smod_i64(grp[0][c], pc.q, pc.mu);
+                        // |grp| < 2^57: adding qoff (a multiple of q) makes each
+                        // sum a non-negative word with the same residue, so one
+                        // Barrett (group 0) or Shoup (groups 1, 2, times their
+                        // weight) reduction needs no sign handling.  This
+                        // per-tile reduction overlaps the next tile's MMAs only
+                        // while it is shorter than about two K chunks, so its
+                        // length shows in the GEMM time.
+                        uint64_t x = barrett_u64(static_cast<uint64_t>(grp[0][c]) + pc.qoff,
+                                                 pc.q, pc.mu);
                         if constexpr (G > 1)
-                            x = add_mod(x, shoup_mulmod(smod_i64(grp[1][c], pc.q, pc.mu), pc.wg1,
-                                                        pc.wg1s, pc.q),
+                            x = add_mod(x, shoup_mulmod(static_cast<uint64_t>(grp[1][c]) + pc.qoff,
+                                                        pc.wg1, pc.wg1s, pc.q),
                                         pc.q);
                         if constexpr (G > 2)
-                            x = add_mod(x, shoup_mulmod(smod_i64(grp[2][c], pc.q, pc.mu), pc.wg2,
-                                                        pc.wg2s, pc.q),
+                            x = add_mod(x, shoup_mulmod(static_cast<uint64_t>(grp[2][c]) + pc.qoff,
+                                                        pc.wg2, pc.wg2s, pc.q),
                                         pc.q);
                         if (pc.accumulate) {  // C <- C + wout * x  (wide products)
                             x = shoup_mulmod(x, pc.wout, pc.wouts, pc.q);

@@ -55,6 +55,7 @@ struct PlaneConst {
     uint64_t wg2s;
     uint64_t *C;    // output plane, d x n, leading dimension ldc
     int64_t ldc;
+    uint64_t qoff;  // a multiple of q >= 2^57: g + qoff lies in [0, 2^64) for |g| < 2^57
     uint64_t wout;  // accumulate mode: C <- C + wout * (U*A) mod q
     uint64_t wouts; // Shoup quotient of wout
     int accumulate; // 0: C <- U*A mod q
@@ -157,6 +158,7 @@ inline PlaneConst make_plane_const(uint64_t q, int b, uint64_t *C, int64_t ldc) 
     p.wg1s = host_shoup(p.wg1, q);
     p.wg2 = host_pow2_mod(6 * b, q);
     p.wg2s = host_shoup(p.wg2, q);
+    p.qoff = static_cast<uint64_t>(((static_cast<unsigned __int128>(1) << 57) + q - 1) / q * q);
     p.C = C;
     p.ldc = ldc;
     p.wout = 1 % q;
