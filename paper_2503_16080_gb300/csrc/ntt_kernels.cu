@@ -177,6 +177,13 @@ __device__ __forceinline__ void ntt_pass(uint64_t *sa, const uint64_t *gin, uint
     if (!last) __syncthreads();
 }
 
+// Stages of pass pi when logN stages run in `passes` passes: as even as
+// possible, the longer passes first (13 stages in 4 passes: 4, 3, 3, 3).
+__device__ __forceinline__ int pass_stages(int logN, int passes, int pi) {
+    const int base = logN / passes, extra = logN % passes;
+    return base + (pi < extra ? 1 : 0);
+}
+
 // E coefficients per thread (N / E threads), passes of up to log2(E) stages.
 template <int E>
 struct NttShape {
@@ -214,10 +221,11 @@ __global__ void __launch_bounds__(NttShape<E>::kMaxThreads, 1) ntt_e_kernel(NttF
     const bool reduce_in = a.ks_ct != nullptr;
     uint64_t *gout = a.polys + p * N;
     const int logN = a.logN;
+    const int passes = (logN + SM - 1) / SM;
     int done = 0;
     bool first = true;
-    while (done < logN) {
-        const int s = logN - done < SM ? logN - done : SM;
+    for (int pi = 0; done < logN; ++pi) {
+        const int s = pass_stages(logN, passes, pi);
         const bool last = done + s == logN;
         // forward: distances fall from N/2; inverse: they rise from 1
         const int lu = FWD ? logN - done - s : done;
@@ -244,10 +252,11 @@ __device__ __forceinline__ void ntt_run(uint64_t *sa, const uint64_t *gin, uint6
                                         bool reduce_in, int N, int logN, const PlaneRegs &pr,
                                         bool from_smem, const MacSink *mk) {
     constexpr int SM = NttShape<E>::kLogE;
+    const int passes = (logN + SM - 1) / SM;
     int done = 0;
     bool first = !from_smem;
-    while (done < logN) {
-        const int s = logN - done < SM ? logN - done : SM;
+    for (int pi = 0; done < logN; ++pi) {
+        const int s = pass_stages(logN, passes, pi);
         const bool last = done + s == logN;
         const int lu = FWD ? logN - done - s : done;
         if (s == SM) {
