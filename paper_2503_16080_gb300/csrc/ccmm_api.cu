@@ -195,10 +195,8 @@ int ks_run(const modpp_ring_s *r, const uint64_t *ct, int64_t n, int64_t count, 
     return MODPP_OK;
 }
 
-// log2(size) radix-2 Tweak stages on a batch of n ciphertexts (n / size
-// independent DFTs of length size), each block of `size` already in
-// bit-reversed order in `a`, ping-ponging with `b`; returns the buffer
-// holding the result.
+// A Tweak is log2(size) radix-2 stages (Alg. 3) over blocks of `size`
+// ciphertexts in bit-reversed order; its passes run one to three stages each.
 // Stages the next Tweak pass takes at stage half `half`: three (radix 8) or
 // two (radix 4) while the group of 8h or 4h ciphertexts fits both the Tweak's
 // size and the ring degree (even rotations), else one.
@@ -265,7 +263,7 @@ size_t transpose_scratch(const modpp_ring_s *r, int64_t groups) {
 
 // Alg. 4 on `groups` matrices of N ciphertexts; scratch of transpose_scratch bytes.
 // b_zero: every input b-part is zero (the (C00, 0) and (C10, 0) of Alg. 8):
-// the first Tweak and the gathers before the key switches then run on the
+// the first Tweak and the gather before the key switches then run on the
 // a-parts only (a Tweak and Aut of zero are zero), the input's b-parts are
 // never read, and the key switches produce the b-parts.
 int transpose_run(const modpp_ring_s *r, const uint64_t *ct, uint64_t *out, int64_t groups,
