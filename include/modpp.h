@@ -337,6 +337,18 @@ int modpp_mm_static(int64_t d, int64_t k, int64_t n, const void *U, int ukind, i
  */
 int modpp_status_read(void *ws, void *stream);
 
+/*
+ * Self-test of the failure path of the bounded device waits (every spin on
+ * an mbarrier in the library's kernels gives up after a time limit, records
+ * MODPP_ERR_TIMEOUT in the status word and returns).  Enqueues one small
+ * kernel whose wait nothing ever satisfies, limited to limit_ns (1 ns to
+ * 10 s); the status word at the start of `ws` (device, 256-byte aligned, at
+ * least 256 bytes) then reads MODPP_ERR_TIMEOUT through modpp_status_read,
+ * and the context stays usable.  Returns MODPP_OK once enqueued,
+ * MODPP_ERR_ARG for a bad workspace or limit, MODPP_ERR_CUDA.
+ */
+int modpp_selftest_bounded_wait(void *ws, uint64_t limit_ns, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -73,6 +73,7 @@ def lib() -> ctypes.CDLL:
         L.pc_mm.argtypes = [I64, I64, I64, P, P, P, P, P, P, I, I, P, SZ, P]
         L.pc_mv.argtypes = [I64, I64, I64, P, P, P, P, P, P, I, I, P, SZ, P]
         L.modpp_status_read.argtypes = [P, P]
+        L.modpp_selftest_bounded_wait.argtypes = [P, ctypes.c_uint64, P]
         L.modpp_mm_wide_workspace.argtypes = [I64, I64, I64, P, I]
         L.modpp_mm_wide_workspace.restype = SZ
         L.modpp_mm_wide.argtypes = [I64, I64, I64, P, I64, I64, P, I64, I64, P, I64, I64, P, I, P,
@@ -172,6 +173,20 @@ def last_status(device: torch.device | int | None = None, stream=None,
             return 0
     return int(lib().modpp_status_read(ctypes.c_void_p(workspace.data_ptr()),
                                        ctypes.c_void_p(_stream_handle(stream))))
+
+
+def selftest_bounded_wait(limit_ms: float = 10.0, device=None) -> int:
+    """Runs the library's bounded-wait self-test (a device wait that nothing
+    satisfies, limited to limit_ms) and returns the status word it leaves:
+    MODPP_ERR_TIMEOUT (-7) when the wait gave up as designed."""
+    dev = torch.device("cuda", torch.cuda.current_device() if device is None else device)
+    ws = torch.zeros(256, dtype=torch.uint8, device=dev)
+    st = torch.cuda.current_stream(dev)
+    _check(lib().modpp_selftest_bounded_wait(ctypes.c_void_p(ws.data_ptr()),
+                                             int(limit_ms * 1e6), ctypes.c_void_p(st.cuda_stream)),
+           "modpp_selftest_bounded_wait")
+    return int(lib().modpp_status_read(ctypes.c_void_p(ws.data_ptr()),
+                                       ctypes.c_void_p(st.cuda_stream)))
 
 
 KERNEL_GEMM, KERNEL_SPLIT, KERNEL_U16 = 0, 1, 2

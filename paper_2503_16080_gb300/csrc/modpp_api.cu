@@ -15,6 +15,7 @@
 
 #include "modpp.h"
 #include "modpp_internal.h"
+#include "ptx_sm103.cuh"
 #include "rns_wide.h"
 
 using namespace modpp;
@@ -628,6 +629,24 @@ int pc_common(int64_t d, int64_t kct, int64_t N, const int8_t *U, const uint64_t
 }  // namespace
 
 // ====================================================================== ABI
+namespace modpp {
+// Self-test of the bounded device waits: one thread waits on an mbarrier
+// that nothing ever arrives at; the wait must give up after limit_ns and the
+// kernel must return, recording MODPP_ERR_TIMEOUT in the status word.
+__global__ void bounded_wait_selftest_kernel(int *status, uint64_t limit_ns) {
+    __shared__ __align__(8) uint64_t bar;
+    __shared__ int abort_flag;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        abort_flag = 0;
+        fence_mbar_init();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0 && !mbar_wait_bounded(&bar, 0, &abort_flag, limit_ns))
+        atomicExch(status, MODPP_ERR_TIMEOUT);
+}
+}  // namespace modpp
+
 extern "C" {
 
 const char *modpp_status_string(int status) {
@@ -820,6 +839,17 @@ int modpp_mm_wide_pair(int64_t d, int64_t k, int64_t n, const uint64_t *U, int64
     if (cudaMemsetAsync(w, 0, sizeof(int), st) != cudaSuccess) return MODPP_ERR_CUDA;
     return run_rns_wide(d, k, n, U, ldu, strideU, A1, A2, lda, strideA, C1, C2, ldc, strideC,
                         primes_host, P, wl, w, st);
+}
+
+int modpp_selftest_bounded_wait(void *ws, uint64_t limit_ns, void *stream) {
+    if (ws == nullptr || (reinterpret_cast<uintptr_t>(ws) & 255u) != 0 || limit_ns == 0 ||
+        limit_ns > uint64_t(10) * 1000000000ull)
+        return MODPP_ERR_ARG;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    int *status = static_cast<int *>(ws);
+    if (cudaMemsetAsync(status, 0, sizeof(int), st) != cudaSuccess) return MODPP_ERR_CUDA;
+    bounded_wait_selftest_kernel<<<1, 32, 0, st>>>(status, limit_ns);
+    return cuda_status(cudaGetLastError());
 }
 
 int modpp_status_read(void *ws, void *stream) {

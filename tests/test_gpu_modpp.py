@@ -196,3 +196,14 @@ def test_wide_crt_largest_products(mp, oracle_mod, k):
         assert int(got[0, 0, 1]) == (-X) % q
     finally:
         mp.set_wide_path("auto")
+
+
+def test_bounded_wait_gives_up_and_context_survives(mp, oracle_mod):
+    # A device wait that nothing satisfies gives up after its limit and
+    # reports MODPP_ERR_TIMEOUT through the status word; the context is still
+    # usable afterwards (the next product is exact).
+    assert mp.selftest_bounded_wait(5.0) == -7
+    assert mp.selftest_bounded_wait(20.0) == -7
+    U = synth.uniform_int8(61, 1, (130, 200))
+    A = synth.uniform_mod(61, 2, (1, 200, 70), P50[0])
+    run_and_compare(mp, oracle_mod, U, A, [P50[0]])
