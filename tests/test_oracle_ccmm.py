@@ -20,6 +20,23 @@ def test_tweak_algorithm_equals_definition(oracle_mod, n, N):
     assert np.array_equal(oracle_mod.tweak_alg(cts, PR[:2]), oracle_mod.tweak_def(cts, PR[:2]))
 
 
+@pytest.mark.parametrize("n,N", [(2, 8), (4, 8), (8, 8), (16, 8), (8, 32), (64, 32)])
+def test_tweak_twice_is_n_times_index_negation(oracle_mod, n, N):
+    # Tweak is the n-point DFT over R_q with omega = X^(2N/n), a primitive
+    # n-th root of unity there (X^t - 1 is invertible for 0 < t < 2N when q
+    # splits X^N + 1), so applying it twice gives n * ct_(-j mod n): the DFT
+    # inversion theorem, independent of how Tweak is computed.
+    primes = PR[:2]
+    cts = rand_cts(3 * n + N, n, N, primes)
+    for f in (oracle_mod.tweak_def, oracle_mod.tweak_alg):
+        if f is oracle_mod.tweak_alg and n > 2 * N:
+            continue
+        twice = f(f(cts, primes), primes)
+        for pl, q in enumerate(primes):
+            want = (cts[(-np.arange(n)) % n, :, pl, :].astype(object) * n) % q
+            assert np.array_equal(twice[:, :, pl, :], want.astype(np.uint64)), (f.__name__, pl)
+
+
 def test_tweak_n2_by_hand(oracle_mod):
     # n = 2: ct'_0 = ct_0 + ct_1 and ct'_1 = ct_0 + X^N ct_1 = ct_0 - ct_1.
     q = PR[0]
