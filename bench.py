@@ -47,8 +47,7 @@ WORKLOAD = ("PC-MM n=4096: U 4096x4096 int8 (N(0,1)*2^5) x row-RLWE ciphertext m
 
 
 # DRAM bytes (read + write) of one gemm_f16_kernel launch of this workload, from
-# one ncu capture of the current kernel (profiles/gemm_f16_pcmm_n4096_traffic.md):
-# 1273489664 read + 792201472 written.
+# one ncu capture of the current kernel: 1273489664 read + 792201472 written.
 GEMM_TRAFFIC_N4096 = 1273489664 + 792201472
 
 
@@ -692,8 +691,7 @@ def run_ours(args):
 
 
 # ----------------------------------------------------------------- secondary workloads
-# Recorded beside the benchmark line (profiles/); the default line
-# is the default PC-MM n=4096 workload above.
+# Workloads measured beside the default PC-MM n=4096 line above.
 
 def _timed(step, steps, warmup, stream, pkg):
     import torch

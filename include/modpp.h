@@ -308,19 +308,24 @@ int modpp_profile_read(int kernel, double *total_ms, int64_t *launches);
  *
  * - The first call on each device looks up the array's device address
  *   (cudaGetSymbolAddress) with that device current, and caches it.  Make
- *   that first call before any stream capture on the device.
- * - A request whose scratch need, modpp_mm_workspace(d, k, n, primes, P,
- *   MODPP_PATH_F16), exceeds MODPP_STATIC_SCRATCH_BYTES is rejected with
- *   MODPP_ERR_WORKSPACE before anything is enqueued.  Invalid sizes or primes
- *   return MODPP_ERR_ARG / MODPP_ERR_PRIME as in modpp_mm.
+ *   that first call before any stream capture on the device.  A
+ *   cudaDeviceReset unloads the library's device code; calls after one are
+ *   not supported.
+ * - Argument errors return the codes of modpp_mm (MODPP_ERR_ARG,
+ *   MODPP_ERR_PRIME) before any CUDA call.  A request whose scratch need,
+ *   modpp_mm_workspace(d, k, n, primes, P, MODPP_PATH_F16), exceeds
+ *   MODPP_STATIC_SCRATCH_BYTES is then rejected with MODPP_ERR_WORKSPACE
+ *   before anything is enqueued.
  * - It calls no cudaMalloc, cudaFree or other allocating routine.
  * - All calls on a device share the one array, which keeps the last call's
  *   contents.  Each call clears what must start at zero (the status word)
  *   and overwrites the rest before reading it.  Calls whose execution can
  *   overlap on the GPU (different streams without ordering, or several host
  *   threads) race on the array and give unspecified results: serialise them.
- * - Device-side status: modpp_status_read() is not available for this entry
- *   point (the status word lives in the static array).
+ * - Device-side status: the status word lives in the static array.
+ *   modpp_mm_static_status(stream) waits for `stream`, reads and clears it
+ *   on the current device: MODPP_OK, or MODPP_ERR_TIMEOUT when a bounded
+ *   device wait of the last call gave up (its outputs are then unspecified).
  */
 #define MODPP_STATIC_SCRATCH_BYTES ((size_t)64 << 20)
 
@@ -328,6 +333,7 @@ size_t modpp_mm_static_capacity(void);
 int modpp_mm_static(int64_t d, int64_t k, int64_t n, const void *U, int ukind, int64_t ldu,
                     const uint64_t *A, int64_t lda, int64_t strideA, uint64_t *C, int64_t ldc,
                     int64_t strideC, const uint64_t *primes_host, int P, void *stream);
+int modpp_mm_static_status(void *stream);
 
 /*
  * Waits for `stream`, reads and clears the device status word kept in the

@@ -87,6 +87,22 @@ int modpp_keyswitch(modpp_ring ring, const uint64_t *ct, uint64_t *out, int64_t 
                     const uint64_t *key, void *ws, size_t ws_bytes, void *stream);
 
 /*
+ * KeySwitch (Sec. 2.2) of a batch of n ciphertexts, each with its own key:
+ * ciphertext c is switched with keys[key_index[c]] (prepared keys,
+ * [count][L][2][L+1][N]); key_index[c] < 0 copies ciphertext c unchanged.
+ * This is the key switch that follows each automorphism in Alg. 4 (steps
+ * 2-5), where ciphertext j needs the key of s(X^(2j+1)) -> s.
+ *   key_index  DEVICE array of n int32, read by the kernels; every
+ *              non-negative entry must be a valid key index (not checked).
+ * Workspace: modpp_keyswitch_workspace(ring, n).  out may equal ct.
+ * n = 1 runs the single-key kernel; n >= 2 the streaming key-product kernels
+ * that modpp_transpose uses.
+ */
+int modpp_keyswitch_indexed(modpp_ring ring, const uint64_t *ct, uint64_t *out, int64_t n,
+                            const uint64_t *keys, const int *key_index, void *ws, size_t ws_bytes,
+                            void *stream);
+
+/*
  * Tweak (Alg. 3): out_j = sum_{i<n} X^(2 i j N / n) * ct_i for a batch of n
  * ciphertexts, n a power of two dividing 2N (an n-point DFT over R_q with
  * root X^(2N/n)), computed by log2(n) radix-2 stages.  [2][L][n][N]; out must

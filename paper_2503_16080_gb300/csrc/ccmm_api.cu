@@ -519,6 +519,17 @@ int modpp_keyswitch(modpp_ring r, const uint64_t *ct, uint64_t *out, int64_t n, 
                   static_cast<cudaStream_t>(stream));
 }
 
+int modpp_keyswitch_indexed(modpp_ring r, const uint64_t *ct, uint64_t *out, int64_t n,
+                            const uint64_t *keys, const int *key_index, void *ws, size_t ws_bytes,
+                            void *stream) {
+    if (r == nullptr || n < 0 || n > (int64_t(1) << 30)) return MODPP_ERR_ARG;
+    if (n == 0) return MODPP_OK;
+    if (!a16(ct) || !a16(out) || !a16(keys) || key_index == nullptr) return MODPP_ERR_ARG;
+    if (!ws_ok(ws, ws_bytes, ks_scratch_bytes(r, n))) return MODPP_ERR_WORKSPACE;
+    return ks_run(r, ct, n, n, out, n, keys, key_index, static_cast<int>(n), 0,
+                  static_cast<char *>(ws), static_cast<cudaStream_t>(stream));
+}
+
 size_t modpp_tweak_workspace(modpp_ring r, int64_t n) {
     if (r == nullptr || n < 0) return 0;
     return std::max<size_t>(kAlign, align_up(sizeof(uint64_t) * batch_words(r, n, r->L)));

@@ -645,6 +645,22 @@ __global__ void bounded_wait_selftest_kernel(int *status, uint64_t limit_ns) {
     if (threadIdx.x == 0 && !mbar_wait_bounded(&bar, 0, &abort_flag, limit_ns))
         atomicExch(status, MODPP_ERR_TIMEOUT);
 }
+
+int mm_check_args(int64_t d, int64_t k, int64_t n, const void *U, int ukind, int64_t ldu,
+                  const uint64_t *A, int64_t lda, int64_t strideA, const uint64_t *C, int64_t ldc,
+                  int64_t strideC, const uint64_t *primes_host, int P) {
+    int rc = check_sizes(d, k, n);
+    if (rc) return rc;
+    rc = check_primes(primes_host, P, kMaxPlanes);
+    if (rc) return rc;
+    if (ukind != MODPP_U_I8 && ukind != MODPP_U_I32) return MODPP_ERR_ARG;
+    const bool work = d > 0 && n > 0;
+    if (work && C == nullptr) return MODPP_ERR_ARG;
+    if (work && k > 0 && (U == nullptr || A == nullptr)) return MODPP_ERR_ARG;
+    if (ldu < k || lda < n || ldc < n) return MODPP_ERR_ARG;
+    if (P > 1 && (strideA < k * lda || strideC < d * ldc)) return MODPP_ERR_ARG;
+    return MODPP_OK;
+}
 }  // namespace modpp
 
 extern "C" {
@@ -722,16 +738,10 @@ int modpp_mm(int64_t d, int64_t k, int64_t n, const void *U, int ukind, int64_t 
              const uint64_t *A, int64_t lda, int64_t strideA, uint64_t *C, int64_t ldc,
              int64_t strideC, const uint64_t *primes_host, int P, int path, void *ws,
              size_t ws_bytes, void *stream) {
-    int rc = check_sizes(d, k, n);
+    if (!path_ok(path)) return MODPP_ERR_ARG;
+    const int rc = modpp::mm_check_args(d, k, n, U, ukind, ldu, A, lda, strideA, C, ldc, strideC,
+                                        primes_host, P);
     if (rc) return rc;
-    rc = check_primes(primes_host, P, kMaxPlanes);
-    if (rc) return rc;
-    if (!path_ok(path) || (ukind != MODPP_U_I8 && ukind != MODPP_U_I32)) return MODPP_ERR_ARG;
-    const bool work = d > 0 && n > 0;
-    if (work && C == nullptr) return MODPP_ERR_ARG;
-    if (work && k > 0 && (U == nullptr || A == nullptr)) return MODPP_ERR_ARG;
-    if (ldu < k || lda < n || ldc < n) return MODPP_ERR_ARG;
-    if (P > 1 && (strideA < k * lda || strideC < d * ldc)) return MODPP_ERR_ARG;
     PlaneIn pl[kMaxPlanes];
     for (int j = 0; j < P; ++j)
         pl[j] = PlaneIn{A + static_cast<int64_t>(j) * strideA, lda, primes_host[j],

@@ -224,4 +224,11 @@ struct Fp64RecombineParams {
 };
 cudaError_t launch_fp64_recombine(const Fp64RecombineParams &p, cudaStream_t s);
 
+// Host-side argument checks of modpp_mm other than the path and the
+// workspace: sizes, primes, U kind, null pointers, leading dimensions and
+// plane strides.  Returns MODPP_OK or the negative status modpp_mm returns.
+int mm_check_args(int64_t d, int64_t k, int64_t n, const void *U, int ukind, int64_t ldu,
+                  const uint64_t *A, int64_t lda, int64_t strideA, const uint64_t *C, int64_t ldc,
+                  int64_t strideC, const uint64_t *primes_host, int P);
+
 }  // namespace modpp

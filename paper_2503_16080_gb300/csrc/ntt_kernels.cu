@@ -1,15 +1,16 @@
-// Negacyclic NTT of degree N >= 1024 with 16 coefficients per thread.
+// Negacyclic NTT of degree N >= 1024, E coefficients per thread in registers.
 //
 // Same transform as the per-stage kernel in ring_kernels.cu (Cooley-Tukey
 // forward / Gentleman-Sande inverse with bit-reversed powers of psi, Longa and
-// Naehrig, CANS 2016), organised for the GPU: each thread holds 16
-// coefficients in registers and runs up to four butterfly stages on them
-// before the coefficients go back to shared memory, so log2(N) stages take
-// ceil(log2(N) / 4) shared-memory round trips.  The first pass reads global
-// memory and the last writes it.  Butterflies keep values lazily reduced
-// (D. Harvey, "Faster arithmetic for number-theoretic transforms", J. Symb.
-// Comp. 2014): forward values live in [0, 4q), inverse ones in [0, 2q), which
-// needs 4q < 2^64 (q < 2^62).
+// Naehrig, CANS 2016), organised for the GPU: each thread holds E = 8
+// coefficients (16 or 32 selectable) in registers and runs up to log2(E)
+// butterfly stages on them before the coefficients go back to shared memory;
+// the log2(N) stages are spread as evenly as possible over
+// ceil(log2(N) / log2(E)) shared-memory round trips.  The first pass reads
+// global memory and the last writes it.  Butterflies keep values lazily
+// reduced (D. Harvey, "Faster arithmetic for number-theoretic transforms",
+// J. Symb. Comp. 2014): forward values live in [0, 4q), inverse ones in
+// [0, 2q), which needs 4q < 2^64 (q < 2^62).
 //
 // The forward transform can also read its input from the a-part of a
 // ciphertext batch and reduce it modulo the target prime on the fly: the

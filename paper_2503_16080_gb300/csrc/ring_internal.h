@@ -34,7 +34,7 @@ struct GatherTables {
 };
 
 // Negacyclic NTT of npolys polynomials in place; polynomial p uses the
-// tables of plane (p / inner) % nplanes.  N >= 1024 runs the 16-per-thread
+// tables of plane (p / inner) % nplanes.  N >= 1024 runs the register-blocked
 // kernel of ntt_kernels.cu, smaller N the per-stage kernel.
 cudaError_t launch_ntt(uint64_t *polys, int64_t npolys, int N, int64_t inner, int nplanes,
                        const NttPlane *tab, bool inverse, cudaStream_t s);

@@ -36,6 +36,7 @@ def _register():
     L.modpp_keyswitch_workspace.argtypes = [P, I64]
     L.modpp_keyswitch_workspace.restype = SZ
     L.modpp_keyswitch.argtypes = [P, P, P, I64, P, P, SZ, P]
+    L.modpp_keyswitch_indexed.argtypes = [P, P, P, I64, P, P, P, SZ, P]
     L.modpp_tweak_workspace.argtypes = [P, I64]
     L.modpp_tweak_workspace.restype = SZ
     L.modpp_tweak.argtypes = [P, P, P, I64, P, SZ, P]
@@ -120,6 +121,24 @@ class Ring:
         wp, wl = _workspace(need, ct.device, workspace)
         _check(lib().modpp_keyswitch(self._h, ct.data_ptr(), out.data_ptr(), n, key.data_ptr(),
                                      wp, wl, _stream_handle(stream)), "modpp_keyswitch")
+        return out
+
+    def keyswitch_indexed(self, ct: torch.Tensor, keys: torch.Tensor, key_index: torch.Tensor,
+                          out=None, stream=None, workspace=None) -> torch.Tensor:
+        """Ciphertext c switched with keys[key_index[c]]; key_index[c] < 0 copies it."""
+        n = self._batch(ct, "ct")
+        count = self._keys(keys, "keys")
+        if not (key_index.is_cuda and key_index.dtype == torch.int32 and key_index.is_contiguous()
+                and key_index.numel() == n):
+            raise TypeError("key_index must be a contiguous int32 CUDA tensor of n entries")
+        if n and int(key_index.max()) >= count:
+            raise ValueError("key_index refers past the last key")
+        out = torch.empty_like(ct) if out is None else out
+        need = int(lib().modpp_keyswitch_workspace(self._h, n))
+        wp, wl = _workspace(need, ct.device, workspace)
+        _check(lib().modpp_keyswitch_indexed(self._h, ct.data_ptr(), out.data_ptr(), n,
+                                             keys.data_ptr(), key_index.data_ptr(), wp, wl,
+                                             _stream_handle(stream)), "modpp_keyswitch_indexed")
         return out
 
     def tweak(self, ct: torch.Tensor, out=None, stream=None, workspace=None) -> torch.Tensor:

@@ -137,6 +137,27 @@ def test_argument_errors_before_any_launch(api):
     assert _call(api, ws_bytes=16) == WS     # too small
 
 
+def test_static_entry_point_argument_errors_before_any_cuda_call(api):
+    # modpp_mm_static checks its arguments with modpp_mm's codes before it
+    # looks up its scratch array (no GPU here: a CUDA call would fail).
+    L = api.lib()
+    fn = L.modpp_mm_static
+    I64, P = ctypes.c_int64, ctypes.c_void_p
+    fn.argtypes = [I64, I64, I64, P, ctypes.c_int, I64, P, I64, I64, P, I64, I64, P,
+                   ctypes.c_int, P]
+
+    def call(d=4, k=4, n=4, primes=(97,), U=1, ldc=None):
+        pr = np.ascontiguousarray(primes, dtype=np.uint64)
+        return fn(d, k, n, U, 0, k, 1, n, k * n, 1, n if ldc is None else ldc, d * n,
+                  pr.ctypes.data, len(pr), None)
+    assert call(d=-1) == -1
+    assert call(U=None) == -1
+    assert call(ldc=3) == -1
+    assert call(primes=(98,)) == -2
+    assert call(primes=(97, 1 << 40)) == -2
+    assert call(d=8192, k=8192, n=8192) == -3     # needs more than the 64 MiB array
+
+
 def test_pc_argument_errors(api):
     L = api.lib()
     pr = np.ascontiguousarray([97] * 17, dtype=np.uint64)
