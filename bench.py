@@ -13,8 +13,13 @@ Metric: exact Mod-PP-MM throughput in TOPS, counting 2*d*k*n multiply-adds
 mod q per (prime, part) plane (so one step is 2 * 4096^3 * 6 = 8.2e11 ops).
 Also reported: PC-MM time, cuBLAS FP64 DGEMM time for U*M at the same n and
 the ratio ("slowdown vs FP64 matmul"), the FP64-limb path (Strategy 1 on
-cuBLAS DGEMM), the roofline of the dominant kernel, an end-to-end number with
-host buffers, and the CPU oracle as a baseline.
+cuBLAS DGEMM) and its fraction of the measured DGEMM rate, the roofline of
+the dominant kernel, an end-to-end number with host buffers, and the CPU
+oracle as a baseline.  After the line's own timed region the default run also
+measures the rest of the metric as sub-objects of the same line: "config1"
+(the 256^3 one-prime product: launch latency in microseconds), "pcmm16384"
+(PC-MM n=16384, L=4) and "ccmm" (CC-MM n=8192, Alg. 8, with real keys; stage
+split, slowdown vs the 8192^3 DGEMM, decrypted error, CRT GEMM roofline).
 
 python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 Under torchrun each rank runs the same workload on its own GPU (independent
@@ -91,7 +96,9 @@ def load_peaks():
 
 
 class ClockSampler:
-    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed
+    region.  start() returns once the first sample has arrived (or after 3 s),
+    so that sampling covers the region that follows; samples come every 50 ms."""
 
     QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -100,28 +107,54 @@ class ClockSampler:
     def __init__(self, gpu_index: int):
         self.gpu = gpu_index
         self.proc = None
+        self.lines = []
+        self.reader = None
+        self.t_mark = None
 
     def start(self):
+        import threading
+        self.lines = []
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--query-gpu={self.QUERY}", "--format=csv,noheader,nounits",
-                 "-i", str(self.gpu), "-lms", "200"],
+                 "-i", str(self.gpu), "-lms", "50"],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except OSError:
             self.proc = None
+            return
+        first = threading.Event()
+
+        def read():
+            for line in self.proc.stdout:
+                self.lines.append((time.perf_counter(), line))
+                first.set()
+        self.reader = threading.Thread(target=read, daemon=True)
+        self.reader.start()
+        first.wait(3.0)
+
+    def mark(self):
+        """Start of the timed region: samples before it are dropped, except the
+        last one (the clock state the region starts in)."""
+        self.t_mark = time.perf_counter()
 
     def stop(self):
         if self.proc is None:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
         self.proc.terminate()
         try:
-            out, _ = self.proc.communicate(timeout=5)
+            self.proc.wait(timeout=5)
         except subprocess.TimeoutExpired:
             self.proc.kill()
-            out, _ = self.proc.communicate()
+            self.proc.wait()
+        if self.reader is not None:
+            self.reader.join(timeout=5)
+        rows = self.lines
+        if self.t_mark is not None:
+            before = [r for r in rows if r[0] < self.t_mark]
+            rows = before[-1:] + [r for r in rows if r[0] >= self.t_mark]
         sm, smax, reasons, power = [], [], set(), []
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for line in out.splitlines():
+        for _, line in rows:
             parts = [p.strip() for p in line.split(",")]
             if len(parts) < 9:
                 continue
@@ -138,6 +171,16 @@ class ClockSampler:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "samples": len(sm),
                 "power_w_max": max(power) if power else None, "reasons": sorted(reasons)}
+
+
+def tensor_peak(peaks: dict, region_ms: float):
+    """Measured bf16 dense peak that a kernel timed in a region of region_ms
+    is held to: the burst figure for a region shorter than one second (the
+    clocks stay at their maximum), the sustained one (seconds under the power
+    cap) for longer regions.  f16 runs at the bf16 rate on kind::f16."""
+    if region_ms < 1000.0:
+        return peaks["bf16_tflops"], "burst"
+    return peaks["bf16_tflops_sustained"], "sustained"
 
 
 DELTA = 2.0 ** 40     # CKKS scale of the encrypted message matrix
@@ -414,6 +457,9 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
             "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": mod_ops_per_step() / (value * 1e12) * 1e3,
+            "ms_per_step_extrapolated": True,
+            "ms_per_step_note": (f"a whole step extrapolated from the timed {rows}-row sample "
+                                 f"({dt * 1e3:.0f} ms of wall time per sample step)"),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int128",
             "data": "synthetic", "config": {"workload": WORKLOAD, "d": D, "k": K, "N": N,
                                             "primes": NPRIMES, "prime_bits": PRIME_BITS},
@@ -470,6 +516,7 @@ def run_ours(args):
     barrier()
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    clocks.mark()
     e0.record(stream)
     for _ in range(args.steps):
         step()
@@ -513,7 +560,7 @@ def run_ours(args):
         gemm_bytes = (planes * K * digits * N * 2 + gemm_per_step * D * kp * 2 + planes * D * N * 8)
         gemm_step_s = gemm_ms / args.steps * 1e-3
         achieved = gemm_flops / gemm_step_s / 1e12
-        peak = peaks["bf16_tflops_sustained"]
+        peak, peak_kind = tensor_peak(peaks, elapsed_ms)
         split_bytes = planes * K * N * 8 + planes * (n_pad // 32) * digits * 32 * kp * 2
         split_gbs = split_bytes / (split_ms / args.steps * 1e-3) / 1e9
 
@@ -540,6 +587,7 @@ def run_ours(args):
         fp64_ms = None
         fp64_tight_ms = None
         fp64_identical = None
+        fp64_roof = None
         if not args.no_fp64:
             pkg.pc_mm(U, A, B, primes, out=(Aout, Bout), path="fp64")
             torch.cuda.synchronize()
@@ -564,6 +612,23 @@ def run_ours(args):
                 torch.equal(Aout.view(torch.int64), ref_out[0]) and
                 torch.equal(Bout.view(torch.int64), ref_out[1]))
         del ref_out
+        # The FP64-limb path against the FP64 peak: its DGEMMs (k1 * k2 per
+        # (prime, part) plane, each 2*d*k*n FLOPs) over its time, divided by
+        # the rate of the plain cuBLAS DGEMM measured above (the FP64 peak
+        # this GPU delivers; the nominal dense FP64 rate is 1.25 TFLOP/s).
+        dgemm_tflops = 2.0 * D * K * N / (dgemm_ms * 1e-3) / 1e12
+        fp64_roof = {"peak": dgemm_tflops, "peak_source": "measured cuBLAS DGEMM U*M, same n",
+                     "nominal_fp64_tflops": 1.25, "unit": "TFLOP/s"}
+        for name, ms_, tight in (("paper_split", fp64_ms, False), ("tight_split", fp64_tight_ms, True)):
+            if ms_ is None:
+                continue
+            info = pkg.plan_info(K, primes[0], "fp64_tight" if tight else "fp64")
+            prods = info["digits"] * 1 * planes  # U is one base-K digit (|U| <= 128 < K)
+            fl = 2.0 * D * K * N * prods
+            fp64_roof[name] = {"dgemms": prods, "flops": fl,
+                               "achieved": fl / (ms_ * 1e-3) / 1e12,
+                               "frac": fl / (ms_ * 1e-3) / 1e12 / dgemm_tflops,
+                               "exact_tops": mod_ops_per_step() / (ms_ * 1e-3) / 1e12}
 
         # End to end through the public call with host buffers: every step
         # copies its inputs in from pinned host memory, runs pc_mm and copies
@@ -652,7 +717,11 @@ def run_ours(args):
                        "parallelism": f"replicas x{ws}"},
             "roofline": {"kernel": "gemm_f16_kernel", "bound": "tensor", "achieved": achieved,
                          "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                         "peak_source": f"{peak_src} bf16 dense sustained (f16 same rate)",
+                         "peak_kind": peak_kind,
+                         "peak_source": (f"{peak_src} bf16 dense {peak_kind} (f16 same rate); "
+                                         f"burst for a timed region under 1 s "
+                                         f"({elapsed_ms:.0f} ms here), sustained above"),
+                         "frac_of_sustained": achieved / peaks["bf16_tflops_sustained"],
                          "traffic": GEMM_TRAFFIC_N4096 if (D, K, N) == (4096, 4096, 4096) else None,
                          "traffic_algorithmic": gemm_bytes / gemm_per_step,
                          "avg_launch_ms": gemm_step_s * 1e3 / gemm_per_step,
@@ -668,6 +737,7 @@ def run_ours(args):
             "fp64_limb_pc_mm_ms": fp64_ms,
             "fp64_limb_tight_pc_mm_ms": fp64_tight_ms,
             "fp64_limb_outputs_identical": fp64_identical,
+            "fp64_limb_roofline": fp64_roof,
             "decrypt": dec,
             "int8_limb": "unavailable: tcgen05.mma kind::i8 is not supported on sm_103a (ptxas)",
             "cpu_baseline": {"value": cpu_tops, "unit": UNIT, "cores": cpu_threads,
@@ -682,6 +752,17 @@ def run_ours(args):
             "gpu_launches": (gemm_n + split_n + u16_n),
             "clocks": clk,
         }
+        if not args.no_extra:
+            # The rest of the metric, each with its own timed region after the
+            # line's: the latency-bound 256^3 case, PC-MM at n=16384 and CC-MM
+            # at n=8192.  The n=4096 buffers are released first.
+            del dev_sets, U, A, B, Aout, Bout, U_h, A_h, B_h, outs_h
+            torch.cuda.synchronize()
+            torch.cuda.empty_cache()
+            line["config1"] = measure_config1(pkg, dev, stream)
+            line["pcmm16384"] = measure_pc_large(pkg, dev, stream, "pcmm16384", 5, 3, peaks)
+            line["ccmm"] = measure_ccmm(pkg, dev, stream, 8192, 5, 3, peaks, e2e=True,
+                                        cpu_leg=False)
     if ws > 1:
         dist.barrier()
         dist.destroy_process_group()
@@ -711,6 +792,122 @@ def _timed(step, steps, warmup, stream, pkg):
     return e0.elapsed_time(e1) / steps, kern
 
 
+def measure_pc_large(pkg, dev, stream, workload: str, steps: int, warmup: int, peaks: dict):
+    """PC-MM n=16384 (d = k = N = 16384, L = 4 primes of 50 bits) or PC-Mv
+    (16384^2 int8 U times a batch of 32), inputs uniform on the device: time per
+    step, exact TOPS, the GEMM's fraction of the tensor peak and, for PC-MM,
+    the cuBLAS FP64 DGEMM of the same n and the slowdown against it."""
+    import torch
+    from paper_2503_16080_gb300 import synth
+    d = k = 16384
+    n = 16384 if workload == "pcmm16384" else 32
+    P = 4
+    primes = synth.ntt_primes(50, P)
+    U = synth.uniform_int8_torch(SEED, 1, (d, k), dev)
+    A = torch.stack([synth.uniform_mod_torch(SEED, 10 + j, (k, n), q, dev)
+                     for j, q in enumerate(primes)])
+    B = torch.stack([synth.uniform_mod_torch(SEED, 20 + j, (k, n), q, dev)
+                     for j, q in enumerate(primes)])
+    Ao = torch.empty((P, d, n), dtype=torch.uint64, device=dev)
+    Bo = torch.empty_like(Ao)
+    fn = pkg.pc_mm if workload == "pcmm16384" else pkg.pc_mv
+    clocks = ClockSampler(dev.index or 0)
+    clocks.start()
+    clocks.mark()
+    ms, kern = _timed(lambda: fn(U, A, B, primes, out=(Ao, Bo)), steps, warmup, stream, pkg)
+    clk = clocks.stop()
+    ops = 2.0 * d * k * n * 2 * P
+    L = pkg.plan_info(k, primes[0])["digits"]
+    g_ms = kern["gemm"][0] / steps  # GEMM time per step (all launches of a step)
+    gflops = ops * L
+    peak, kind = tensor_peak(peaks, ms * steps)
+    out = {
+        "workload": workload, "value": ops / (ms * 1e-3) / 1e12, "ms_per_step": ms,
+        "steps": steps, "warmup": warmup,
+        "config": {"workload": (f"PC-MM n=16384: U 16384^2 int8 x 16384 row-RLWE cts of degree "
+                                f"16384, L=4 primes of 50 bits" if n > 32 else
+                                "PC-Mv: U 16384^2 int8 x batch of 32, L=4 primes of 50 bits"),
+                   "d": d, "k": k, "n": n, "primes": P, "digits": L,
+                   "digit_bits": pkg.get_digit_bits()},
+        "roofline": {"kernel": "gemm_f16_kernel", "bound": "tensor",
+                     "achieved": gflops / (g_ms * 1e-3) / 1e12, "peak": peak,
+                     "peak_kind": kind, "unit": "TFLOP/s",
+                     "frac": gflops / (g_ms * 1e-3) / 1e12 / peak,
+                     "gemm_ms_per_step": g_ms,
+                     "launches_per_step": kern["gemm"][1] / steps},
+        "kernels_ms_per_step": {kname: v[0] / steps for kname, v in kern.items()},
+        "hbm_gbs_U_stream": d * k * 2 / (g_ms * 1e-3) / 1e9,
+        "fp64_matmul_ms": None, "clocks": clk}
+    del A, B, Ao, Bo
+    if workload == "pcmm16384":
+        Ud = U.to(torch.float64)
+        del U
+        Md = torch.empty((k, n), dtype=torch.float64, device=dev).uniform_(-1, 1)
+        torch.matmul(Ud[:1024], Md)
+        torch.cuda.synchronize()
+        f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        f0.record(stream)
+        torch.matmul(Ud, Md)
+        f1.record(stream)
+        torch.cuda.synchronize()
+        out["fp64_matmul_ms"] = f0.elapsed_time(f1)
+        out["slowdown_vs_fp64_matmul"] = ms / out["fp64_matmul_ms"]
+        del Ud, Md
+    torch.cuda.empty_cache()
+    return out
+
+
+def measure_config1(pkg, dev, stream, calls: int = 200):
+    """The 256^3 Mod-PP-MM with one 50-bit prime and int32 U (values in
+    [-128, 127]): the latency-bound case.  Reports the device time per call
+    of back-to-back calls (CUDA events), the time of one call followed by a
+    synchronisation (median), and the host time spent enqueueing one call."""
+    import numpy as np
+    import torch
+    from paper_2503_16080_gb300 import synth
+    n = 256
+    q = synth.ntt_primes(50, 1)
+    U = torch.from_numpy(synth.uniform_int8(1, 1, (n, n)).astype(np.int32)).to(dev)
+    A = synth.uniform_mod_torch(1, 2, (1, n, n), q[0], dev)
+    C = torch.empty((1, n, n), dtype=torch.uint64, device=dev)
+    ws = torch.empty(pkg.workspace_bytes(n, n, n, q), dtype=torch.uint8, device=dev)
+
+    def call():
+        pkg.modpp_mm(U, A, q, out=C, workspace=ws)
+
+    for _ in range(20):
+        call()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    t0 = time.perf_counter()
+    for _ in range(calls):
+        call()
+    t_enq = time.perf_counter() - t0
+    e1.record(stream)
+    torch.cuda.synchronize()
+    back_to_back = e0.elapsed_time(e1) / calls
+    sync = []
+    for _ in range(50):
+        t0 = time.perf_counter()
+        call()
+        torch.cuda.synchronize()
+        sync.append(time.perf_counter() - t0)
+    pkg.profile_enable(True)
+    call()
+    launches = sum(pkg.profile_read(kid)[1]
+                   for kid in (pkg.KERNEL_GEMM, pkg.KERNEL_SPLIT, pkg.KERNEL_U16))
+    pkg.profile_enable(False)
+    return {"workload": "Mod-PP-MM 256^3, one 50-bit prime, int32 U in [-128,127] "
+                        "(uniform), A uniform mod q",
+            "d": n, "k": n, "n": n, "primes": 1,
+            "us_per_call_back_to_back": back_to_back * 1e3,
+            "us_per_call_with_sync": statistics.median(sync) * 1e6,
+            "host_enqueue_us_per_call": t_enq / calls * 1e6,
+            "launches_per_call": launches,
+            "tops_back_to_back": 2.0 * n ** 3 / (back_to_back * 1e-3) / 1e12}
+
+
 def run_secondary(args):
     import numpy as np
     import torch
@@ -731,55 +928,8 @@ def run_secondary(args):
             "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f16", "data": "synthetic"}
     if args.workload in ("pcmm16384", "pcmv"):
-        d = k = 16384
-        n = 16384 if args.workload == "pcmm16384" else 32
-        P = 4
-        primes = synth.ntt_primes(50, P)
-        U = synth.uniform_int8_torch(SEED, 1, (d, k), dev)
-        A = torch.stack([synth.uniform_mod_torch(SEED, 10 + j, (k, n), q, dev)
-                         for j, q in enumerate(primes)])
-        B = torch.stack([synth.uniform_mod_torch(SEED, 20 + j, (k, n), q, dev)
-                         for j, q in enumerate(primes)])
-        Ao = torch.empty((P, d, n), dtype=torch.uint64, device=dev)
-        Bo = torch.empty_like(Ao)
-        fn = pkg.pc_mm if args.workload == "pcmm16384" else pkg.pc_mv
-        clocks.start()
-        ms, kern = _timed(lambda: fn(U, A, B, primes, out=(Ao, Bo)), args.steps, args.warmup,
-                          stream, pkg)
-        clk = clocks.stop()
-        ops = 2.0 * d * k * n * 2 * P
-        L = pkg.plan_info(k, primes[0])["digits"]
-        # GEMM time per step (all launches of a step).
-        g_ms = kern["gemm"][0] / args.steps
-        gflops = ops * L
-        line.update({
-            "workload": args.workload, "value": ops / (ms * 1e-3) / 1e12, "ms_per_step": ms,
-            "config": {"workload": (f"PC-MM n=16384: U 16384^2 int8 x 16384 row-RLWE cts of degree "
-                                    f"16384, L=4 primes of 50 bits" if n > 32 else
-                                    "PC-Mv: U 16384^2 int8 x batch of 32, L=4 primes of 50 bits"),
-                       "d": d, "k": k, "n": n, "primes": P, "digits": L,
-                       "digit_bits": pkg.get_digit_bits()},
-            "roofline": {"kernel": "gemm_f16_kernel", "bound": "tensor",
-                         "achieved": gflops / (g_ms * 1e-3) / 1e12,
-                         "peak": peaks["bf16_tflops_sustained"], "unit": "TFLOP/s",
-                         "frac": gflops / (g_ms * 1e-3) / 1e12 / peaks["bf16_tflops_sustained"],
-                         "gemm_ms_per_step": g_ms,
-                         "launches_per_step": kern["gemm"][1] / args.steps},
-            "kernels_ms_per_step": {kname: v[0] / args.steps for kname, v in kern.items()},
-            "hbm_gbs_U_stream": d * k * 2 / (g_ms * 1e-3) / 1e9,
-            "fp64_matmul_ms": None, "clocks": clk})
-        if args.workload == "pcmm16384":
-            Ud = U.to(torch.float64)
-            Md = torch.empty((k, n), dtype=torch.float64, device=dev).uniform_(-1, 1)
-            torch.matmul(Ud[:1024], Md)
-            torch.cuda.synchronize()
-            f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            f0.record(stream)
-            torch.matmul(Ud, Md)
-            f1.record(stream)
-            torch.cuda.synchronize()
-            line["fp64_matmul_ms"] = f0.elapsed_time(f1)
-            line["slowdown_vs_fp64_matmul"] = ms / line["fp64_matmul_ms"]
+        line.update(measure_pc_large(pkg, dev, stream, args.workload, args.steps, args.warmup,
+                                     peaks))
     elif args.workload == "hostlink":
         # Pinned host <-> device copy rates (the bound of the end-to-end
         # numbers): one direction at a time, and both at once on separate
@@ -908,19 +1058,16 @@ CC_WORKLOAD = ("CC-MM n=8192 (Alg. 8): two column-wise encrypted 8192x8192 matri
                "encryptions of M1, M2 uniform in [-1,1] at scale 2^40 under a ternary secret")
 
 
-def run_ccmm(args):
+def measure_ccmm(pkg, dev, stream, Nr: int, steps: int, warmup: int, peaks: dict,
+                 e2e: bool = True, cpu_leg: bool = True):
+    """CC-MM (Alg. 8) at ring degree Nr, L = 4: harness (real encryptions and
+    keys), timed steps, stage split, CRT GEMM roofline, FP64 DGEMM of the same
+    n, decrypted error; optionally the end-to-end form from host memory and
+    the CPU oracle's extrapolated time.  Returns the measurement as a dict."""
     import numpy as np
     import torch
-
-    import __graft_entry__
-    __graft_entry__.build()
-    import paper_2503_16080_gb300 as pkg
     from paper_2503_16080_gb300 import synth
 
-    torch.cuda.set_device(0)
-    dev = torch.device("cuda", 0)
-    stream = torch.cuda.current_stream()
-    Nr = args.ccmm_n
     L = 4
     primes = synth.ntt_primes(50, L)
     prp = primes + synth.ntt_primes(60, 1)
@@ -929,11 +1076,16 @@ def run_ccmm(args):
     # Real inputs: column-wise encryptions of M1 and M2 under a ternary secret,
     # valid automorphism and relinearisation keys (the kernels' work does not
     # depend on the values; the decrypted product is checked after timing).
+    t_h = time.perf_counter()
     inp = ccmm_inputs(Nr, primes, prp, dev)
+    torch.cuda.synchronize()
+    harness_s = time.perf_counter() - t_h
     ct1, ct2 = inp["ct1"], inp["ct2"]
+    t_k = time.perf_counter()
     keys = ring.prepare_keys(inp["keys"])   # in place: evaluation-domain Montgomery form
     rkey = ring.prepare_keys(inp["rkey"])
     torch.cuda.synchronize()
+    prepare_s = time.perf_counter() - t_k
     out = torch.empty((2, L - 1, Nr, Nr), dtype=torch.uint64, device=dev)
     ws_bytes = ring.cc_mm_workspace_bytes()
     ws = torch.empty(ws_bytes, dtype=torch.uint8, device=dev)
@@ -941,19 +1093,21 @@ def run_ccmm(args):
     def step():
         ring.cc_mm(ct1, ct2, keys, rkey, out=out, workspace=ws)
 
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         step()
     torch.cuda.synchronize()
-    clocks = ClockSampler(0)
+    clocks = ClockSampler(dev.index or 0)
     clocks.start()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    clocks.mark()
     e0.record(stream)
-    for _ in range(args.steps):
+    for _ in range(steps):
         step()
     e1.record(stream)
     torch.cuda.synchronize()
     clk = clocks.stop()
-    ms = e0.elapsed_time(e1) / args.steps
+    region_ms = e0.elapsed_time(e1)
+    ms = region_ms / steps
     dec = ccmm_decrypt_error(inp, out, primes)
 
     # Stage split and GEMM launches (one extra, separately timed call).
@@ -965,7 +1119,6 @@ def run_ccmm(args):
     post_ms, post_n = pkg.profile_read(pkg.KERNEL_U16)
     pkg.profile_enable(False)
 
-    peaks, peak_src = load_peaks()
     crt_primes = pkg.wide_plan_info(Nr, primes)
     if crt_primes:
         # CRT form: R small-prime products of [A;B] (2N x N) times an N x N
@@ -983,7 +1136,7 @@ def run_ccmm(args):
     gemm_flops = total_flops / max(gemm_n, 1)
     g_avg = gemm_ms / max(gemm_n, 1)
     achieved = total_flops / (gemm_ms * 1e-3) / 1e12
-    peak = peaks["bf16_tflops_sustained"]
+    peak, kind = tensor_peak(peaks, region_ms)
     modops = 2.0 * (2 * Nr) * Nr * (2 * Nr) * L
 
     # FP64 matmul of the same n.
@@ -999,53 +1152,56 @@ def run_ccmm(args):
     dgemm_ms = f0.elapsed_time(f1)
     del Ad, Bd
 
-    # End to end: both ciphertext matrices from pinned host memory, the
-    # product, and the result back, every step (keys stay resident).
-    h1 = torch.empty(ct1.shape, dtype=torch.uint64).pin_memory()
-    h2 = torch.empty(ct2.shape, dtype=torch.uint64).pin_memory()
-    ho = torch.empty(out.shape, dtype=torch.uint64).pin_memory()
-    h1.copy_(ct1)
-    h2.copy_(ct2)
+    e2e_out = None
+    if e2e:
+        # End to end: both ciphertext matrices from pinned host memory, the
+        # product, and the result back, every step (keys stay resident).
+        h1 = torch.empty(ct1.shape, dtype=torch.uint64).pin_memory()
+        h2 = torch.empty(ct2.shape, dtype=torch.uint64).pin_memory()
+        ho = torch.empty(out.shape, dtype=torch.uint64).pin_memory()
+        h1.copy_(ct1)
+        h2.copy_(ct2)
+        marks = []
 
-    marks = []
+        def e2e_step(record=False):
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)] if record else None
+            ct1.copy_(h1, non_blocking=True)
+            ct2.copy_(h2, non_blocking=True)
+            if record:
+                ev[0].record(stream)
+            step()
+            if record:
+                ev[1].record(stream)
+            ho.copy_(out, non_blocking=True)
+            if record:
+                ev[2].record(stream)
+                marks.append(ev)
 
-    def e2e_step(record=False):
-        ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)] if record else None
-        ct1.copy_(h1, non_blocking=True)
-        ct2.copy_(h2, non_blocking=True)
-        if record:
-            ev[0].record(stream)
-        step()
-        if record:
-            ev[1].record(stream)
-        ho.copy_(out, non_blocking=True)
-        if record:
-            ev[2].record(stream)
-            marks.append(ev)
-
-    e2e_step()
-    torch.cuda.synchronize()
-    g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e2e_steps = max(1, min(args.steps, 3))
-    g0.record(stream)
-    for _ in range(e2e_steps):
-        e2e_step(record=True)
-    g1.record(stream)
-    torch.cuda.synchronize()
-    e2e_ms = g0.elapsed_time(g1) / e2e_steps
-    # Per part: copy-in (from the previous step's end), product, copy-out.
-    starts = [g0] + [m[2] for m in marks[:-1]]
-    e2e_parts = {
-        "h2d_ms": sum(a.elapsed_time(m[0]) for a, m in zip(starts, marks)) / e2e_steps,
-        "cc_mm_ms": sum(m[0].elapsed_time(m[1]) for m in marks) / e2e_steps,
-        "d2h_ms": sum(m[1].elapsed_time(m[2]) for m in marks) / e2e_steps,
-    }
+        e2e_step()
+        torch.cuda.synchronize()
+        g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e2e_steps = max(1, min(steps, 3))
+        g0.record(stream)
+        for _ in range(e2e_steps):
+            e2e_step(record=True)
+        g1.record(stream)
+        torch.cuda.synchronize()
+        e2e_ms = g0.elapsed_time(g1) / e2e_steps
+        # Per part: copy-in (from the previous step's end), product, copy-out.
+        starts = [g0] + [m[2] for m in marks[:-1]]
+        e2e_out = {"value": e2e_ms, "unit": "ms per CC-MM",
+                   "h2d_bytes_per_step": 8 * (h1.numel() + h2.numel()),
+                   "d2h_bytes_per_step": 8 * ho.numel(),
+                   "parts": {
+                       "h2d_ms": sum(a.elapsed_time(m[0]) for a, m in zip(starts, marks)) / e2e_steps,
+                       "cc_mm_ms": sum(m[0].elapsed_time(m[1]) for m in marks) / e2e_steps,
+                       "d2h_ms": sum(m[1].elapsed_time(m[2]) for m in marks) / e2e_steps}}
 
     # CPU oracle on a small ring (N=512): the whole CC-MM, and its Mod-PP-MM
     # part alone; the products extrapolate by N^3, the rest (transposes, key
     # switches, relin) by N^2 log N.
     cpu = None
-    if not args.quick:
+    if cpu_leg:
         import oracle
         oracle.build()
         n0 = 512
@@ -1070,31 +1226,50 @@ def run_ccmm(args):
                          f"step-2 products); products scaled by (N/{n0})^3, the rest by "
                          f"(N/{n0})^2 log N"}
 
-    line = {"metric": METRIC, "workload": "ccmm8192" if Nr == 8192 else f"ccmm{Nr}",
-            "value": ms, "unit": "ms per CC-MM", "higher_is_better": False, "n_gpus": 1,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "scaling": "weak",
-            "vs_baseline": None, "dtype": "u64 residues (f16 digits on tcgen05)",
-            "data": "synthetic",
-            "config": {"workload": CC_WORKLOAD.replace("8192", str(Nr)), "N": Nr, "L": L,
-                       "prime_bits": 50, "special_prime_bits": 60,
-                       "l2": "inputs larger than L2", "key_bytes": keys.numel() * 8,
-                       "workspace_bytes": ws_bytes},
-            "stages_ms": {"transpose_ct2": stages[0], "mod_pp_mm_x2": stages[1],
-                          "transpose_C00_C10": stages[2], "relin_finish": stages[3]},
-            "mod_pp_mm_tops": modops / (stages[1] * 1e-3) / 1e12,
-            "roofline": {"kernel": "gemm_f16_kernel", "bound": "tensor", "achieved": achieved,
-                         "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                         "peak_source": f"{peak_src} bf16 dense sustained (f16 same rate)",
-                         "avg_launch_ms": g_avg, "launches_per_cc_mm": gemm_n,
-                         "flops_per_launch": gemm_flops, **form},
-            "wide_passes_ms": {"gemm": gemm_ms, "residue_split": pre_ms, "crt_or_u16": post_ms},
-            "fp64_matmul_ms": dgemm_ms, "slowdown_vs_fp64_matmul": ms / dgemm_ms,
-            "decrypt": dec,
-            "e2e": {"value": e2e_ms, "unit": "ms per CC-MM", "h2d_bytes_per_step":
-                    8 * (h1.numel() + h2.numel()), "d2h_bytes_per_step": 8 * ho.numel(),
-                    "parts": e2e_parts},
-            "cpu_baseline": cpu, "clocks": clk}
+    res = {"workload": "ccmm8192" if Nr == 8192 else f"ccmm{Nr}",
+           "value": ms, "unit": "ms per CC-MM", "higher_is_better": False,
+           "steps": steps, "warmup": warmup, "ms_per_step": ms,
+           "dtype": "u64 residues (f16 digits on tcgen05)",
+           "config": {"workload": CC_WORKLOAD.replace("8192", str(Nr)), "N": Nr, "L": L,
+                      "prime_bits": 50, "special_prime_bits": 60,
+                      "l2": "inputs larger than L2", "key_bytes": keys.numel() * 8,
+                      "workspace_bytes": ws_bytes},
+           "stages_ms": {"transpose_ct2": stages[0], "mod_pp_mm_x2": stages[1],
+                         "transpose_C00_C10": stages[2], "relin_finish": stages[3]},
+           "mod_pp_mm_tops": modops / (stages[1] * 1e-3) / 1e12,
+           "roofline": {"kernel": "gemm_f16_kernel", "bound": "tensor", "achieved": achieved,
+                        "peak": peak, "peak_kind": kind, "unit": "TFLOP/s",
+                        "frac": achieved / peak,
+                        "frac_of_sustained": achieved / peaks["bf16_tflops_sustained"],
+                        "avg_launch_ms": g_avg, "launches_per_cc_mm": gemm_n,
+                        "flops_per_launch": gemm_flops, "flops_per_cc_mm": total_flops, **form},
+           "wide_passes_ms": {"gemm": gemm_ms, "residue_split": pre_ms, "crt_or_u16": post_ms},
+           "fp64_matmul_ms": dgemm_ms, "slowdown_vs_fp64_matmul": ms / dgemm_ms,
+           "decrypt": dec,
+           "harness_s": {"encrypt_and_keygen": harness_s, "prepare_keys": prepare_s,
+                         "note": "not in the timed region"},
+           "e2e": e2e_out, "cpu_baseline": cpu, "clocks": clk}
     ring.close()
+    del inp, keys, rkey, ct1, ct2, out, ws
+    torch.cuda.empty_cache()
+    return res
+
+
+def run_ccmm(args):
+    import torch
+
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2503_16080_gb300 as pkg
+
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream()
+    peaks, _ = load_peaks()
+    res = measure_ccmm(pkg, dev, stream, args.ccmm_n, args.steps, args.warmup, peaks,
+                       e2e=True, cpu_leg=not args.quick)
+    line = {"metric": METRIC, **res, "n_gpus": 1, "scaling": "weak", "vs_baseline": None,
+            "data": "synthetic"}
     print(json.dumps(line))
     return 0
 
@@ -1106,6 +1281,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64-limb comparison")
+    ap.add_argument("--no-extra", action="store_true",
+                    help="default workload: skip the config-1, n=16384 and CC-MM sub-objects")
     ap.add_argument("--quick", action="store_true",
                     help="timed loop only (no FP64, e2e or CPU legs): for profiler runs")
     ap.add_argument("--digit-bits", type=int, default=0,
