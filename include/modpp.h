@@ -32,6 +32,10 @@
  *   device (a bounded wait that timed out) is recorded in the workspace's
  *   status word and read back with modpp_status_read().
  * - Output buffers must not overlap inputs.
+ * - Value ranges (residues canonical, U in [-128, 127]) are preconditions the
+ *   host cannot see.  They are checked only in debug mode
+ *   (modpp_set_debug_checks); otherwise an input outside its range gives
+ *   unspecified outputs.
  */
 #ifndef MODPP_H
 #define MODPP_H
@@ -50,7 +54,7 @@ typedef enum {
     MODPP_ERR_WORKSPACE = -3,   /* workspace null, misaligned or too small */
     MODPP_ERR_UNSUPPORTED = -4, /* valid request this build does not serve */
     MODPP_ERR_CUDA = -5,        /* a CUDA runtime, driver or cuBLAS call failed */
-    MODPP_ERR_RANGE = -6,       /* reserved: input values outside their documented range */
+    MODPP_ERR_RANGE = -6,       /* debug checks: an input value outside its range (status word) */
     MODPP_ERR_TIMEOUT = -7      /* a bounded device-side wait gave up (status word) */
 } modpp_status;
 
@@ -75,6 +79,24 @@ typedef enum {
     MODPP_U_I8 = 0,  /* int8_t entries */
     MODPP_U_I32 = 1  /* int32_t entries, values in [-128, 127] */
 } modpp_u_kind;
+
+/*
+ * Debug mode: value-range checks of the inputs on the device (the
+ * preconditions on input values, which the host cannot see).
+ * While on, every product entry point (modpp_mm, pc_mm, pc_mv, the wide
+ * products, grouped runs) enqueues, after its own launches, a pass over its
+ * residue inputs checking 0 <= A_j[t][c] < q_j (and U_j for the wide
+ * products) and, for MODPP_U_I32, -128 <= U <= 127.  A violation writes
+ * MODPP_ERR_RANGE into the call's status word (modpp_status_read), unless
+ * the word already holds an error.  The ring entry points of modpp_ring.h
+ * check their ciphertext and key inputs before their launches and report
+ * in the ring's status word (modpp_ring_status_read).  The products still
+ * run; their outputs are unspecified when a check fails.  The setting is
+ * process-wide (host only); the environment variable MODPP_DEBUG_CHECKS=1
+ * turns it on at load time.  on: 0 or 1, else MODPP_ERR_ARG.
+ */
+int modpp_set_debug_checks(int on);
+int modpp_get_debug_checks(void);
 
 /* Human-readable name of a modpp_status value (static string). */
 const char *modpp_status_string(int status);

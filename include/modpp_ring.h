@@ -151,6 +151,17 @@ size_t cc_mm_workspace(modpp_ring ring);
 int cc_mm(modpp_ring ring, const uint64_t *ct1, const uint64_t *ct2, const uint64_t *aut_keys,
           const uint64_t *relin_key, uint64_t *out, void *ws, size_t ws_bytes, void *stream);
 
+/*
+ * Waits for `stream`, then reads and clears the ring's status word (a word
+ * in the ring's table memory): MODPP_OK, or MODPP_ERR_RANGE when, in debug
+ * mode (modpp_set_debug_checks), an entry point of this ring was given a
+ * ciphertext coefficient or key coefficient not below its prime since the
+ * last read.  The word is sticky until read.  Device waits of the wide
+ * products inside cc_mm report in the status word at the start of cc_mm's
+ * workspace (modpp_status_read).
+ */
+int modpp_ring_status_read(modpp_ring ring, void *stream);
+
 /* Device time (ms) of the stages of the last cc_mm call on this ring, when
  * timing is switched on with modpp_profile_enable(1); stage 0 = transpose of
  * ct2, 1 = the two Mod-PP-MMs, 2 = transpose of C00 | C10, 3 = relin and

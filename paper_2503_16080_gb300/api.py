@@ -91,6 +91,8 @@ def lib() -> ctypes.CDLL:
         L.modpp_set_wide_path.argtypes = [I]
         L.modpp_get_wide_path.restype = I
         L.modpp_wide_plan_info.argtypes = [I64, P, I, P]
+        L.modpp_set_debug_checks.argtypes = [I]
+        L.modpp_get_debug_checks.restype = I
         L.modpp_profile_enable.argtypes = [I]
         L.modpp_profile_read.argtypes = [I, P, P]
         _lib = L
@@ -214,6 +216,16 @@ def wide_plan_info(k: int, primes: Sequence[int]) -> int:
     _check(lib().modpp_wide_plan_info(int(k), pr.ctypes.data, len(pr), ctypes.byref(out)),
            "modpp_wide_plan_info")
     return out.value
+
+
+def set_debug_checks(on: bool) -> None:
+    """Debug mode: device-side value-range checks of every call's inputs,
+    reported as MODPP_ERR_RANGE in the call's status word (process-wide)."""
+    _check(lib().modpp_set_debug_checks(1 if on else 0), "modpp_set_debug_checks")
+
+
+def get_debug_checks() -> bool:
+    return bool(lib().modpp_get_debug_checks())
 
 
 def get_digit_bits() -> int:

@@ -29,6 +29,7 @@ struct modpp_ring_s {
     const uint64_t *ninv = nullptr, *ninv_s = nullptr;    // N^-1 mod q_k, k < L
     const int *t2_src = nullptr, *t2_ellinv = nullptr, *t2_kid = nullptr;
     const int *kid_zero = nullptr;
+    int *status = nullptr;         // status word of the ring (debug range checks)
     cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
     bool timed = false;
 };
@@ -119,7 +120,7 @@ int log2_exact(int64_t x) {
 
 // Layout of the ring tables inside the caller's memory.
 struct RingLayout {
-    size_t tab, tables, consts, ints, total;
+    size_t tab, tables, consts, ints, status, total;
 };
 RingLayout ring_layout(int64_t N, int L) {
     RingLayout r{};
@@ -132,6 +133,8 @@ RingLayout ring_layout(int64_t N, int L) {
     off = align_up(off + sizeof(uint64_t) * 6 * (L + 1));
     r.ints = off;
     off = align_up(off + sizeof(int) * (3 * N + 1));
+    r.status = off;
+    off = align_up(off + sizeof(int));
     r.total = off;
     return r;
 }
@@ -345,6 +348,22 @@ bool ws_ok(const void *ws, size_t have, size_t need) {
     return ws != nullptr && (reinterpret_cast<uintptr_t>(ws) & (kAlign - 1)) == 0 && have >= need;
 }
 
+// Debug-mode range checks of ring inputs (off unless debug_checks_on()): a
+// batch [2][Lc][n][N] of coefficients below the chain primes, and switching
+// keys [count][L][2][L+1][N] below q_0 .. q_{L-1}, P.  A violation sets
+// MODPP_ERR_RANGE in the ring's status word (sticky until read).
+int check_batch(const modpp_ring_s *r, const uint64_t *ct, int64_t n, int Lc, cudaStream_t st) {
+    if (!debug_checks_on() || n == 0) return MODPP_OK;
+    const int64_t plane = n * r->N;
+    return cuda_status(range_planes(ct, 2 * Lc, 1, plane, plane, plane, r->primes.data(), Lc,
+                                    r->status, st));
+}
+int check_keys(const modpp_ring_s *r, const uint64_t *keys, int64_t count, cudaStream_t st) {
+    if (!debug_checks_on() || count == 0) return MODPP_OK;
+    return cuda_status(range_planes(keys, count * r->L * 2 * (r->L + 1), 1, r->N, r->N, r->N,
+                                    r->primes.data(), r->L + 1, r->status, st));
+}
+
 
 }  // namespace
 
@@ -472,6 +491,7 @@ int modpp_ring_create(int64_t N, int L, const uint64_t *primes_host, void *mem, 
     r->t2_ellinv = dints + N;
     r->t2_kid = dints + 2 * N;
     r->kid_zero = dints + 3 * N;
+    r->status = reinterpret_cast<int *>(r->mem + lay.status);
 
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     cudaError_t e = cudaMemcpyAsync(mem, host.data(), lay.total, cudaMemcpyHostToDevice, st);
@@ -500,6 +520,8 @@ int modpp_ring_prepare_keys(modpp_ring r, uint64_t *keys, int64_t count, void *s
     const int Lp = r->L + 1;
     const int64_t polys = count * r->L * 2 * Lp;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const int rc = check_keys(r, keys, count, st);
+    if (rc) return rc;
     cudaError_t e = launch_ntt(keys, polys, static_cast<int>(r->N), 1, Lp, r->tab, false, st);
     if (e == cudaSuccess) e = launch_to_montgomery(keys, polys, static_cast<int>(r->N), 1, Lp, r->tab, st);
     return cuda_status(e);
@@ -515,8 +537,11 @@ int modpp_keyswitch(modpp_ring r, const uint64_t *ct, uint64_t *out, int64_t n, 
     if (r == nullptr || n < 0) return MODPP_ERR_ARG;
     if (n > 0 && (!a16(ct) || !a16(out) || !a16(key))) return MODPP_ERR_ARG;
     if (!ws_ok(ws, ws_bytes, ks_scratch_bytes(r, n))) return MODPP_ERR_WORKSPACE;
-    return ks_run(r, ct, n, n, out, n, key, r->kid_zero, 1, 0, static_cast<char *>(ws),
-                  static_cast<cudaStream_t>(stream));
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    int rc = check_batch(r, ct, n, r->L, st);
+    if (rc == MODPP_OK && n > 0) rc = check_keys(r, key, 1, st);
+    if (rc) return rc;
+    return ks_run(r, ct, n, n, out, n, key, r->kid_zero, 1, 0, static_cast<char *>(ws), st);
 }
 
 int modpp_keyswitch_indexed(modpp_ring r, const uint64_t *ct, uint64_t *out, int64_t n,
@@ -526,8 +551,11 @@ int modpp_keyswitch_indexed(modpp_ring r, const uint64_t *ct, uint64_t *out, int
     if (n == 0) return MODPP_OK;
     if (!a16(ct) || !a16(out) || !a16(keys) || key_index == nullptr) return MODPP_ERR_ARG;
     if (!ws_ok(ws, ws_bytes, ks_scratch_bytes(r, n))) return MODPP_ERR_WORKSPACE;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const int rc = check_batch(r, ct, n, r->L, st);
+    if (rc) return rc;
     return ks_run(r, ct, n, n, out, n, keys, key_index, static_cast<int>(n), 0,
-                  static_cast<char *>(ws), static_cast<cudaStream_t>(stream));
+                  static_cast<char *>(ws), st);
 }
 
 size_t modpp_tweak_workspace(modpp_ring r, int64_t n) {
@@ -544,6 +572,8 @@ int modpp_tweak(modpp_ring r, const uint64_t *ct, uint64_t *out, int64_t n, void
     if (!ws_ok(ws, ws_bytes, align_up(sizeof(uint64_t) * batch_words(r, n, r->L))))
         return MODPP_ERR_WORKSPACE;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const int crc = check_batch(r, ct, n, r->L, st);
+    if (crc) return crc;
     uint64_t *w = static_cast<uint64_t *>(ws);
     if (n == 1)  // no stage: the Tweak of one ciphertext is itself
         return cudaMemcpyAsync(out, ct, sizeof(uint64_t) * batch_words(r, 1, r->L),
@@ -572,16 +602,21 @@ int modpp_transpose(modpp_ring r, const uint64_t *ct, uint64_t *out, int64_t gro
     if (groups == 0) return MODPP_OK;
     if (!a16(ct) || !a16(out) || !a16(aut_keys)) return MODPP_ERR_ARG;
     if (!ws_ok(ws, ws_bytes, transpose_scratch(r, groups))) return MODPP_ERR_WORKSPACE;
-    return transpose_run(r, ct, out, groups, aut_keys, static_cast<char *>(ws),
-                         static_cast<cudaStream_t>(stream));
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    int rc = check_batch(r, ct, groups * r->N, r->L, st);
+    if (rc == MODPP_OK) rc = check_keys(r, aut_keys, r->N, st);
+    if (rc) return rc;
+    return transpose_run(r, ct, out, groups, aut_keys, static_cast<char *>(ws), st);
 }
 
 int modpp_rescale(modpp_ring r, const uint64_t *ct, uint64_t *out, int64_t n, void *stream) {
     if (r == nullptr || n < 0 || r->L < 2) return MODPP_ERR_ARG;
     if (n == 0) return MODPP_OK;
     if (!a16(ct) || !a16(out)) return MODPP_ERR_ARG;
-    return cuda_status(launch_rescale(ct, out, r->L, n * r->N, r->tab, r->qlinv, r->qlinv_s,
-                                      static_cast<cudaStream_t>(stream)));
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const int rc = check_batch(r, ct, n, r->L, st);
+    if (rc) return rc;
+    return cuda_status(launch_rescale(ct, out, r->L, n * r->N, r->tab, r->qlinv, r->qlinv_s, st));
 }
 
 size_t cc_mm_workspace(modpp_ring r) {
@@ -606,6 +641,13 @@ int cc_mm(modpp_ring r, const uint64_t *ct1, const uint64_t *ct2, const uint64_t
     uint64_t *y = reinterpret_cast<uint64_t *>(base + lay.y);
     uint64_t *z = reinterpret_cast<uint64_t *>(base + lay.z);
     char *scratch = base + lay.scratch;
+    {
+        int rc = check_batch(r, ct1, N, L, st);
+        if (rc == MODPP_OK) rc = check_batch(r, ct2, N, L, st);
+        if (rc == MODPP_OK) rc = check_keys(r, aut_keys, N, st);
+        if (rc == MODPP_OK) rc = check_keys(r, relin_key, 1, st);
+        if (rc) return rc;
+    }
     const bool timed = profile_active();
     r->timed = timed;
     auto mark = [&](int i) {
@@ -651,6 +693,11 @@ int cc_mm(modpp_ring r, const uint64_t *ct1, const uint64_t *ct2, const uint64_t
     if (launch_cc_finish(fp, st) != cudaSuccess) return MODPP_ERR_CUDA;
     mark(4);
     return MODPP_OK;
+}
+
+int modpp_ring_status_read(modpp_ring r, void *stream) {
+    if (r == nullptr) return MODPP_ERR_ARG;
+    return modpp_status_read(r->status, stream);
 }
 
 int cc_mm_stage_ms(modpp_ring r, double ms[4]) {

@@ -541,6 +541,18 @@ int plan_enqueue(modpp_group_plan *pl, cudaStream_t st) {
         }
         if (e != cudaSuccess) return MODPP_ERR_CUDA;
     }
+    // Debug mode: every problem's residues A bounded by its primes (the
+    // status word of the plan's workspace; in a captured graph the setting
+    // at capture time holds).
+    if (debug_checks_on()) {
+        for (const auto &pc : pl->probs) {
+            const modpp_problem &p = pc.p;
+            if (p.k == 0 || p.d == 0 || p.n == 0) continue;
+            if (range_planes(p.A, p.P, p.k, p.n, p.lda, p.strideA, pc.primes.data(), p.P,
+                             reinterpret_cast<int *>(w), st) != cudaSuccess)
+                return MODPP_ERR_CUDA;
+        }
+    }
     return MODPP_OK;
 }
 

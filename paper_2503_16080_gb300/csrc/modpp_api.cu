@@ -590,6 +590,34 @@ int run_f16_wide(int64_t d, int64_t k, int64_t n, const uint64_t *U, int64_t ldu
     return MODPP_OK;
 }
 
+// Debug-mode value checks of a product's inputs, after its launches (the
+// inputs are read-only and the call's status word was cleared at its start):
+// the residue planes of A bounded by their primes and, for int32 U, the
+// plaintext range [-128, 127].  Off unless debug_checks_on().
+int debug_check_inputs(int64_t d, int64_t k, int64_t n, const void *U, int ukind, int64_t ldu,
+                       const uint64_t *A, int64_t lda, int64_t strideA, const uint64_t *primes,
+                       int P, void *ws, cudaStream_t st) {
+    if (!debug_checks_on() || d == 0 || n == 0 || k == 0) return MODPP_OK;
+    int *status = static_cast<int *>(ws);
+    cudaError_t e = range_planes(A, P, k, n, lda, strideA, primes, P, status, st);
+    if (e == cudaSuccess && ukind == MODPP_U_I32)
+        e = launch_range_i32(static_cast<const int32_t *>(U), d, k, ldu, status, st);
+    return cuda_status(e);
+}
+
+// The same for wide products: U_j and A_j (and A2_j) residues mod q_j.
+int debug_check_wide(int64_t d, int64_t k, int64_t n, const uint64_t *U, int64_t ldu,
+                     int64_t strideU, const uint64_t *A1, const uint64_t *A2, int64_t lda,
+                     int64_t strideA, const uint64_t *primes, int P, void *ws, cudaStream_t st) {
+    if (!debug_checks_on() || d == 0 || n == 0 || k == 0) return MODPP_OK;
+    int *status = static_cast<int *>(ws);
+    cudaError_t e = cudaSuccess;
+    if (U) e = range_planes(U, P, d, k, ldu, strideU, primes, P, status, st);
+    if (e == cudaSuccess && A1) e = range_planes(A1, P, k, n, lda, strideA, primes, P, status, st);
+    if (e == cudaSuccess && A2) e = range_planes(A2, P, k, n, lda, strideA, primes, P, status, st);
+    return cuda_status(e);
+}
+
 size_t layout_bytes(int64_t d, int64_t k, int64_t n, const uint64_t *qs, int planes, int path) {
     if (path == MODPP_PATH_F16) return f16_layout(d, k, n, qs, planes).total;
     return fp64_layout(d, k, n, qs, planes, path == MODPP_PATH_FP64_TIGHT).total;
@@ -623,7 +651,12 @@ int pc_common(int64_t d, int64_t kct, int64_t N, const int8_t *U, const uint64_t
         pl[P + j] = PlaneIn{B + static_cast<int64_t>(j) * kct * N, N, primes[j],
                             Bout + static_cast<int64_t>(j) * d * N, N};
     }
-    return dispatch(d, kct, N, U, MODPP_U_I8, kct, pl, 2 * P, path, ws, ws_bytes, stream);
+    rc = dispatch(d, kct, N, U, MODPP_U_I8, kct, pl, 2 * P, path, ws, ws_bytes, stream);
+    if (rc) return rc;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    rc = debug_check_inputs(d, kct, N, U, MODPP_U_I8, kct, A, N, kct * N, primes, P, ws, st);
+    if (rc) return rc;
+    return debug_check_inputs(d, kct, N, U, MODPP_U_I8, kct, B, N, kct * N, primes, P, ws, st);
 }
 
 }  // namespace
@@ -746,7 +779,10 @@ int modpp_mm(int64_t d, int64_t k, int64_t n, const void *U, int ukind, int64_t 
     for (int j = 0; j < P; ++j)
         pl[j] = PlaneIn{A + static_cast<int64_t>(j) * strideA, lda, primes_host[j],
                         C + static_cast<int64_t>(j) * strideC, ldc};
-    return dispatch(d, k, n, U, ukind, ldu, pl, P, path, ws, ws_bytes, stream);
+    const int rc2 = dispatch(d, k, n, U, ukind, ldu, pl, P, path, ws, ws_bytes, stream);
+    if (rc2) return rc2;
+    return debug_check_inputs(d, k, n, U, ukind, ldu, A, lda, strideA, primes_host, P, ws,
+                              static_cast<cudaStream_t>(stream));
 }
 
 size_t pc_mm_workspace(int64_t d, int64_t kct, int64_t N, const uint64_t *primes_host, int P,
@@ -817,8 +853,12 @@ int modpp_mm_wide(int64_t d, int64_t k, int64_t n, const uint64_t *U, int64_t ld
     if (P > 1 && (strideU < d * ldu || strideA < k * lda || strideC < d * ldc)) return MODPP_ERR_ARG;
     if (ws == nullptr || (reinterpret_cast<uintptr_t>(ws) & (kAlign - 1)) != 0)
         return MODPP_ERR_WORKSPACE;
-    return run_f16_wide(d, k, n, U, ldu, strideU, A, lda, strideA, C, ldc, strideC, primes_host, P,
-                        ws, ws_bytes, static_cast<cudaStream_t>(stream));
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    rc = run_f16_wide(d, k, n, U, ldu, strideU, A, lda, strideA, C, ldc, strideC, primes_host, P,
+                      ws, ws_bytes, st);
+    if (rc) return rc;
+    return debug_check_wide(d, k, n, U, ldu, strideU, A, nullptr, lda, strideA, primes_host, P,
+                            ws, st);
 }
 
 int modpp_mm_wide_pair(int64_t d, int64_t k, int64_t n, const uint64_t *U, int64_t ldu,
@@ -835,8 +875,12 @@ int modpp_mm_wide_pair(int64_t d, int64_t k, int64_t n, const uint64_t *U, int64
         rc = modpp_mm_wide(d, k, n, U, ldu, strideU, A1, lda, strideA, C1, ldc, strideC,
                            primes_host, P, ws, ws_bytes, stream);
         if (rc) return rc;
-        return modpp_mm_wide(d, k, n, U, ldu, strideU, A2, lda, strideA, C2, ldc, strideC,
-                             primes_host, P, ws, ws_bytes, stream);
+        rc = modpp_mm_wide(d, k, n, U, ldu, strideU, A2, lda, strideA, C2, ldc, strideC,
+                           primes_host, P, ws, ws_bytes, stream);
+        if (rc) return rc;
+        // The second call cleared the status word: check the first operand again.
+        return debug_check_wide(d, k, n, nullptr, ldu, strideU, A1, nullptr, lda, strideA,
+                                primes_host, P, ws, static_cast<cudaStream_t>(stream));
     }
     if (!U || !A1 || !A2 || !C1 || !C2) return MODPP_ERR_ARG;
     if (ldu < k || lda < n || ldc < n) return MODPP_ERR_ARG;
@@ -847,8 +891,11 @@ int modpp_mm_wide_pair(int64_t d, int64_t k, int64_t n, const uint64_t *U, int64
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     uint8_t *w = static_cast<uint8_t *>(ws);
     if (cudaMemsetAsync(w, 0, sizeof(int), st) != cudaSuccess) return MODPP_ERR_CUDA;
-    return run_rns_wide(d, k, n, U, ldu, strideU, A1, A2, lda, strideA, C1, C2, ldc, strideC,
-                        primes_host, P, wl, w, st);
+    rc = run_rns_wide(d, k, n, U, ldu, strideU, A1, A2, lda, strideA, C1, C2, ldc, strideC,
+                      primes_host, P, wl, w, st);
+    if (rc) return rc;
+    return debug_check_wide(d, k, n, U, ldu, strideU, A1, A2, lda, strideA, primes_host, P, ws,
+                            st);
 }
 
 int modpp_selftest_bounded_wait(void *ws, uint64_t limit_ns, void *stream) {

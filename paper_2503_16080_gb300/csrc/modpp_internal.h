@@ -224,6 +224,25 @@ struct Fp64RecombineParams {
 };
 cudaError_t launch_fp64_recombine(const Fp64RecombineParams &p, cudaStream_t s);
 
+// Value-range checks of the inputs (debug mode, range_checks.cu).
+constexpr int kMaxRangeQ = 40;
+struct RangeCheckU64 {
+    const uint64_t *base;
+    int64_t planes, rows, cols, ld, plane_stride;
+    int nq;                // plane p is bounded by q[p % nq]
+    uint64_t q[kMaxRangeQ];
+    int *status;           // MODPP_ERR_RANGE is written here on a violation
+};
+bool debug_checks_on();
+cudaError_t launch_range_u64(const RangeCheckU64 &a, cudaStream_t s);
+cudaError_t launch_range_i32(const int32_t *U, int64_t rows, int64_t cols, int64_t ld, int *status,
+                             cudaStream_t s);
+// Planes p < planes of rows x cols (leading dimension ld, plane stride
+// plane_stride) bounded by q[p % nq].
+cudaError_t range_planes(const uint64_t *base, int64_t planes, int64_t rows, int64_t cols,
+                         int64_t ld, int64_t plane_stride, const uint64_t *q, int nq, int *status,
+                         cudaStream_t s);
+
 // Host-side argument checks of modpp_mm other than the path and the
 // workspace: sizes, primes, U kind, null pointers, leading dimensions and
 // plane strides.  Returns MODPP_OK or the negative status modpp_mm returns.

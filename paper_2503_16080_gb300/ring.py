@@ -48,6 +48,7 @@ def _register():
     L.cc_mm_workspace.restype = SZ
     L.cc_mm.argtypes = [P, P, P, P, P, P, P, SZ, P]
     L.cc_mm_stage_ms.argtypes = [P, P]
+    L.modpp_ring_status_read.argtypes = [P, P]
     _registered = True
     return L
 
@@ -197,6 +198,12 @@ class Ring:
                            relin_key.data_ptr(), out.data_ptr(), wp, wl, _stream_handle(stream)),
                "cc_mm")
         return out
+
+    def status(self, stream=None) -> int:
+        """Reads and clears the ring's status word (syncs the stream):
+        0, or MODPP_ERR_RANGE (-6) when debug checks found an input
+        coefficient not below its prime since the last read."""
+        return int(lib().modpp_ring_status_read(self._h, _stream_handle(stream)))
 
     def cc_mm_stage_ms(self) -> list[float]:
         """Stage times of the last cc_mm while profiling is on: transpose of ct2,

@@ -158,6 +158,18 @@ def test_static_entry_point_argument_errors_before_any_cuda_call(api):
     assert call(d=8192, k=8192, n=8192) == -3     # needs more than the 64 MiB array
 
 
+def test_debug_checks_setting(api):
+    assert not api.get_debug_checks()
+    api.set_debug_checks(True)
+    try:
+        assert api.get_debug_checks()
+    finally:
+        api.set_debug_checks(False)
+    assert not api.get_debug_checks()
+    assert api.lib().modpp_set_debug_checks(2) == -1
+    assert api.lib().modpp_ring_status_read(None, None) == -1
+
+
 def test_pc_argument_errors(api):
     L = api.lib()
     pr = np.ascontiguousarray([97] * 17, dtype=np.uint64)
