@@ -18,8 +18,8 @@ computes:
                      textbook coefficient-encoded CKKS (Sec. 2.2).
 * ``toeplitz``       Toep(m) of Sec. 2 (the matrix of u -> u*m).
 * ``tweak_*``, ``automorphism``, ``ks_keygen``, ``keyswitch``, ``rescale``,
-  ``transpose``, ``cc_mm``: the ring operations of the ciphertext-ciphertext
-  product, Alg. 3 (Tweak), Alg. 4 (Transpose) and Alg. 8 (CC-MM), in the
+  ``transpose``, ``cc_mm``, ``cc_mm_rowwise``: the ring operations of the
+  ciphertext-ciphertext product, Alg. 3 (Tweak), Alg. 4 (Transpose) and Alg. 8 (CC-MM), in the
   paper's order (``ccmm_oracle.c`` plus the compositions below).
 
 Pins against things other than itself live in ``tests/test_oracle_*.py``.
@@ -488,16 +488,30 @@ def cc_mm(ct1, ct2, aut_keys, relin_key, primes_with_P):
     """Alg. 8 (CC-MM) on column-wise encryptions [N, 2, L, N] (ciphertext j is
     column j of the matrix).  Returns the column-wise encryption of M1*M2 after
     Rescale by q_{L-1}, [N, 2, L-1, N], and the intermediate blocks."""
+    rw = transpose(ct2, aut_keys, primes_with_P)                     # Step 1
+    out, blocks = cc_mm_rowwise(ct1, rw, aut_keys, relin_key, primes_with_P)
+    blocks["row_wise"] = rw
+    return out, blocks
+
+
+def cc_mm_rowwise(ct1, rw, aut_keys, relin_key, primes_with_P):
+    """Alg. 8 with Step 1 omitted, for a row-wise encrypted right operand (the
+    "row or column" remark after Thm th:ccmm): ct1 holds n column-wise
+    encryptions [n, 2, L, N] of an N x n matrix M (ciphertext j is column j),
+    rw holds n row-wise encryptions [n, 2, L, N] of an n x N matrix M'
+    (ciphertext t is row t), 1 <= n <= N.  Steps 2-5 as in Alg. 8; returns the
+    column-wise encryption of M*M' (N x N) after Rescale, [N, 2, L-1, N], and
+    the intermediate blocks."""
     ct1 = _u64(ct1)
-    N, _, L, _ = ct1.shape
+    rw = _u64(rw)
+    n, _, L, N = ct1.shape
+    assert rw.shape == (n, 2, L, N)
     primes = list(primes_with_P[:L])
-    # Step 1: row-wise encryption of M2.
-    rw = transpose(ct2, aut_keys, primes_with_P)
     C = np.empty((L, 2 * N, 2 * N), dtype=np.uint64)
     for pl, q in enumerate(primes):
-        # [A; B]: row r of A holds coefficient r of every column ciphertext.
+        # [A; B] (2N x n): row r of A holds coefficient r of every column ciphertext.
         Ub = np.concatenate([ct1[:, 0, pl, :].T, ct1[:, 1, pl, :].T])
-        # [A~' B~']: row t is the row-wise ciphertext t (a-part then b-part).
+        # [A~' B~'] (n x 2N): row t is the row-wise ciphertext t (a-part then b-part).
         Wb = np.concatenate([rw[:, 0, pl, :], rw[:, 1, pl, :]], axis=1)
         C[pl] = mod_pp_mm_residues(Ub, Wb, q)                      # Step 2
     C00, C01 = C[:, :N, :N], C[:, :N, N:]
@@ -520,4 +534,4 @@ def cc_mm(ct1, ct2, aut_keys, relin_key, primes_with_P):
         extra[0] = ct_add(extra[0], C01[:, :, j], primes)            # + C01 (column j)
         extra[1] = ct_add(D23[j, 1], C11[:, :, j], primes)           # D3 + C11
         out[j] = rescale(ct_add(rl, extra, primes), primes)
-    return out, {"row_wise": rw, "C": C, "D01": D01, "D23": D23}
+    return out, {"C": C, "D01": D01, "D23": D23}

@@ -57,6 +57,21 @@ def encrypt_columns(oracle_mod, M, s, delta, seed, primes=PR):
     return cts, m, e
 
 
+def encrypt_rows(oracle_mod, X, s, delta, seed, primes=PR):
+    """Ciphertext t encrypts row t of X (rows x N): the row-wise encryption of
+    X, or the column-wise encryption of X^T."""
+    rows, N = X.shape
+    L = len(primes)
+    m = oracle_mod.ckks_encode(np.ascontiguousarray(X), delta)
+    a = np.stack([synth.uniform_mod(seed, 30 + pl, (rows, N), q) for pl, q in enumerate(primes)])
+    e = synth.rounded_gaussian(seed, 40, (rows, N))
+    b = oracle_mod.rlwe_encrypt_rows(a, s, m, e, primes)
+    cts = np.empty((rows, 2, L, N), dtype=np.uint64)
+    cts[:, 0] = np.transpose(a, (1, 0, 2))
+    cts[:, 1] = np.transpose(b, (1, 0, 2))
+    return cts, m, e
+
+
 def to_batch(cts):
     """[n, 2, L, N] -> the library's part-major batch [2, L, n, N]."""
     return np.ascontiguousarray(np.transpose(cts, (1, 2, 0, 3)))

@@ -189,3 +189,52 @@ def test_cc_mm_decrypts_to_product(oracle_mod):
     for j in range(N):
         dec = _decrypt_centered(oracle_mod, out[j], s, PR[:-1]).astype(np.float64) / scale
         assert np.max(np.abs(dec - ref[:, j])) <= 2.0 ** -20
+
+
+@pytest.mark.parametrize("n", [1, 4, 16])
+def test_cc_mm_rowwise_trivial_is_exact(oracle_mod, n):
+    # Alg. 8 without Step 1 on noise-free ciphertexts (0, m): every a-part
+    # product is 0, so the result is exactly (0, Rescale(M * M')) with the
+    # rescale rounding x -> (x - [x]_q)/q, [x]_q centred -- computed here
+    # with Python integers from M (N x n) and M' (n x N).
+    N, L = 16, len(PR)
+    keys = _aut_keys(oracle_mod, synth.ternary(17, 1, N), N, 7000)
+    relin = ckks_inputs.relin_key(oracle_mod, synth.ternary(17, 1, N), N, 71)
+    M = synth.uniform_mod(17, 2, (N, n), 1 << 36).astype(object) - (1 << 35)
+    Mp = synth.uniform_mod(17, 3, (n, N), 1 << 36).astype(object) - (1 << 35)
+    c1 = np.zeros((n, 2, L, N), dtype=np.uint64)
+    rw = np.zeros((n, 2, L, N), dtype=np.uint64)
+    for pl, q in enumerate(PR):
+        c1[:, 1, pl, :] = (M.T % q).astype(np.uint64)     # ciphertext j holds column j of M
+        rw[:, 1, pl, :] = (Mp % q).astype(np.uint64)      # ciphertext t holds row t of M'
+    out, _ = oracle_mod.cc_mm_rowwise(c1, rw, keys, relin, PRP)
+    assert out.shape == (N, 2, L - 1, N)
+    assert np.all(out[:, 0] == 0)
+    X = M.dot(Mp)                                          # exact integers
+    ql = PR[-1]
+    r = X % ql
+    r = np.where(2 * r > ql, r - ql, r)
+    t = (X - r) // ql
+    for pl, q in enumerate(PR[:-1]):
+        assert np.array_equal(out[:, 1, pl, :], (t.T % q).astype(np.uint64))
+
+
+@pytest.mark.parametrize("n", [4, 16])
+def test_cc_mm_rowwise_decrypts_to_product(oracle_mod, n):
+    # Column-wise M (N x n) times row-wise M' (n x N): decrypts to M * M'
+    # within 2^-20 at scale Delta^2 / q_{L-1}.
+    N = 16
+    s = synth.ternary(19, 1, N)
+    keys = _aut_keys(oracle_mod, s, N, 8000)
+    relin = ckks_inputs.relin_key(oracle_mod, s, N, 81)
+    delta = 2.0 ** 40
+    M = synth.uniform_unit(19, 2, (N, n))
+    Mp = synth.uniform_unit(19, 3, (n, N))
+    c1, _, _ = ckks_inputs.encrypt_rows(oracle_mod, np.ascontiguousarray(M.T), s, delta, 21)
+    rw, _, _ = ckks_inputs.encrypt_rows(oracle_mod, Mp, s, delta, 22)
+    out, _ = oracle_mod.cc_mm_rowwise(c1, rw, keys, relin, PRP)
+    scale = delta * delta / PR[-1]
+    ref = M @ Mp
+    for j in range(N):
+        dec = _decrypt_centered(oracle_mod, out[j], s, PR[:-1]).astype(np.float64) / scale
+        assert np.max(np.abs(dec - ref[:, j])) <= 2.0 ** -20
