@@ -152,6 +152,28 @@ int cc_mm(modpp_ring ring, const uint64_t *ct1, const uint64_t *ct2, const uint6
           const uint64_t *relin_key, uint64_t *out, void *ws, size_t ws_bytes, void *stream);
 
 /*
+ * CC-MM with a choice of encoding for the right operand (the remark on row
+ * or column encodings after Thm th:ccmm, Sec. 5):
+ *   flags = 0: as cc_mm; n must equal N.
+ *   flags = MODPP_CC_M2_ROWWISE: ct2 is a ROW-wise encryption of an n x N
+ *     matrix M2 (ciphertext t encrypts row t; [2][L][n][N]) and ct1 the
+ *     column-wise encryption of an N x n matrix M1 (ciphertext j encrypts
+ *     column j; [2][L][n][N]), 1 <= n <= N.  Step 1 of Alg. 8 (the
+ *     Transpose of ct2) is skipped: two Transposes instead of three, and the
+ *     wide products have inner dimension n.
+ * out: [2][L-1][N][N], the column-wise encryption of M1 * M2 (N x N).
+ * out_scale_mult (host, may be null) receives 1 / q_{L-1}: the output's
+ * scale is the product of the inputs' scales times this factor (Delta^2 /
+ * q_{L-1} for two inputs at scale Delta).  Workspace: cc_mm_ex_workspace
+ * (0 for an invalid n or flags).  Other conventions as cc_mm.
+ */
+#define MODPP_CC_M2_ROWWISE 1
+size_t cc_mm_ex_workspace(modpp_ring ring, int64_t n, int flags);
+int cc_mm_ex(modpp_ring ring, int64_t n, const uint64_t *ct1, const uint64_t *ct2,
+             const uint64_t *aut_keys, const uint64_t *relin_key, int flags, uint64_t *out,
+             double *out_scale_mult, void *ws, size_t ws_bytes, void *stream);
+
+/*
  * Waits for `stream`, then reads and clears the ring's status word (a word
  * in the ring's table memory): MODPP_OK, or MODPP_ERR_RANGE when, in debug
  * mode (modpp_set_debug_checks), an entry point of this ring was given a

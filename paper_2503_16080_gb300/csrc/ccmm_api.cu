@@ -314,11 +314,12 @@ int transpose_run(const modpp_ring_s *r, const uint64_t *ct, uint64_t *out, int6
 struct CcLayout {
     size_t wide, scratch, rw, ut, x, y, z, total;
 };
-CcLayout cc_layout(const modpp_ring_s *r) {
+// Workspace of CC-MM with inner dimension n (n = N for Alg. 8 as printed).
+CcLayout cc_layout(const modpp_ring_s *r, int64_t n) {
     CcLayout c{};
     const int64_t N = r->N;
     const int L = r->L;
-    const size_t wide = modpp_mm_wide_workspace(2 * N, N, N, r->primes.data(), L);
+    const size_t wide = modpp_mm_wide_workspace(2 * N, n, N, r->primes.data(), L);
     const size_t tr = transpose_scratch(r, 2);
     size_t off = 0;
     // The Mod-PP-MM workspace (whose first word is the status word) and the
@@ -326,10 +327,10 @@ CcLayout cc_layout(const modpp_ring_s *r) {
     c.wide = off;
     c.scratch = off;
     off = align_up(off + std::max(wide, tr));
-    c.rw = off;  // row-wise encryption of M2; later the relinearised D0
+    c.rw = off;  // row-wise encryption of M2 (column-wise input); later the relinearised D0
     off = align_up(off + sizeof(uint64_t) * batch_words(r, N, L));
-    c.ut = off;  // [L][2N][N]: [A; B] of ct1 per prime
-    off = align_up(off + sizeof(uint64_t) * L * 2 * N * N);
+    c.ut = off;  // [L][2N][n]: [A; B] of ct1 per prime
+    off = align_up(off + sizeof(uint64_t) * L * 2 * N * n);
     c.x = off;   // batch of 2N: a-parts [C00; C10]; b-parts zero (never written or read)
     off = align_up(off + sizeof(uint64_t) * batch_words(r, 2 * N, L));
     c.y = off;   // [L][2N][N]: [C01; C11]
@@ -619,22 +620,31 @@ int modpp_rescale(modpp_ring r, const uint64_t *ct, uint64_t *out, int64_t n, vo
     return cuda_status(launch_rescale(ct, out, r->L, n * r->N, r->tab, r->qlinv, r->qlinv_s, st));
 }
 
-size_t cc_mm_workspace(modpp_ring r) {
-    if (r == nullptr || r->L < 2) return 0;
-    return cc_layout(r).total;
+size_t cc_mm_ex_workspace(modpp_ring r, int64_t n, int flags) {
+    if (r == nullptr || r->L < 2 || (flags & ~MODPP_CC_M2_ROWWISE) != 0) return 0;
+    if ((flags & MODPP_CC_M2_ROWWISE) ? (n < 1 || n > r->N) : n != r->N) return 0;
+    return cc_layout(r, n).total;
 }
 
-int cc_mm(modpp_ring r, const uint64_t *ct1, const uint64_t *ct2, const uint64_t *aut_keys,
-          const uint64_t *relin_key, uint64_t *out, void *ws, size_t ws_bytes, void *stream) {
-    if (r == nullptr || r->L < 2) return MODPP_ERR_ARG;
+size_t cc_mm_workspace(modpp_ring r) {
+    if (r == nullptr) return 0;
+    return cc_mm_ex_workspace(r, r->N, 0);
+}
+
+int cc_mm_ex(modpp_ring r, int64_t n, const uint64_t *ct1, const uint64_t *ct2,
+             const uint64_t *aut_keys, const uint64_t *relin_key, int flags, uint64_t *out,
+             double *out_scale_mult, void *ws, size_t ws_bytes, void *stream) {
+    if (r == nullptr || r->L < 2 || (flags & ~MODPP_CC_M2_ROWWISE) != 0) return MODPP_ERR_ARG;
+    const bool rowwise = (flags & MODPP_CC_M2_ROWWISE) != 0;
+    if (rowwise ? (n < 1 || n > r->N) : n != r->N) return MODPP_ERR_ARG;
     if (!a16(ct1) || !a16(ct2) || !a16(aut_keys) || !a16(relin_key) || !a16(out))
         return MODPP_ERR_ARG;
-    const CcLayout lay = cc_layout(r);
+    const CcLayout lay = cc_layout(r, n);
     if (!ws_ok(ws, ws_bytes, lay.total)) return MODPP_ERR_WORKSPACE;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     char *base = static_cast<char *>(ws);
     const int L = r->L;
-    const int64_t N = r->N, NN = N * N;
+    const int64_t N = r->N, NN = N * N, nN = n * N;
     uint64_t *rw = reinterpret_cast<uint64_t *>(base + lay.rw);
     uint64_t *ut = reinterpret_cast<uint64_t *>(base + lay.ut);
     uint64_t *x = reinterpret_cast<uint64_t *>(base + lay.x);
@@ -642,8 +652,8 @@ int cc_mm(modpp_ring r, const uint64_t *ct1, const uint64_t *ct2, const uint64_t
     uint64_t *z = reinterpret_cast<uint64_t *>(base + lay.z);
     char *scratch = base + lay.scratch;
     {
-        int rc = check_batch(r, ct1, N, L, st);
-        if (rc == MODPP_OK) rc = check_batch(r, ct2, N, L, st);
+        int rc = check_batch(r, ct1, n, L, st);
+        if (rc == MODPP_OK) rc = check_batch(r, ct2, n, L, st);
         if (rc == MODPP_OK) rc = check_keys(r, aut_keys, N, st);
         if (rc == MODPP_OK) rc = check_keys(r, relin_key, 1, st);
         if (rc) return rc;
@@ -654,22 +664,27 @@ int cc_mm(modpp_ring r, const uint64_t *ct1, const uint64_t *ct2, const uint64_t
         if (timed) cudaEventRecord(r->ev[i], st);
     };
     mark(0);
-    // Step 1: row-wise encryption of M2.
-    int rc = transpose_run(r, ct2, rw, 1, aut_keys, scratch, st);
-    if (rc) return rc;
+    // Step 1: row-wise encryption of M2, unless it is given row-wise (the
+    // row-or-column remark after Thm th:ccmm: Step 1 is skipped).
+    const uint64_t *m2 = ct2;
+    if (!rowwise) {
+        const int rc = transpose_run(r, ct2, rw, 1, aut_keys, scratch, st);
+        if (rc) return rc;
+        m2 = rw;
+    }
     mark(1);
-    // Step 2: [A; B] per prime (row r of A: coefficient r of every column
-    // ciphertext), then C[:, :N] = [A; B] * A~' and C[:, N:] = [A; B] * B~'.
-    cudaError_t e = launch_transpose_u64(ct1, ut, static_cast<int>(N), static_cast<int>(N), N, N,
-                                         NN, 2 * NN, L, st);
+    // Step 2: [A; B] per prime (2N x n; row r of A: coefficient r of every
+    // column ciphertext), then C[:, :N] = [A; B] * A~' and C[:, N:] = [A; B] * B~'.
+    cudaError_t e = launch_transpose_u64(ct1, ut, static_cast<int>(n), static_cast<int>(N), N, n,
+                                         nN, 2 * N * n, L, st);
     if (e == cudaSuccess)
-        e = launch_transpose_u64(ct1 + L * NN, ut + NN, static_cast<int>(N), static_cast<int>(N), N,
-                                 N, NN, 2 * NN, L, st);
+        e = launch_transpose_u64(ct1 + L * nN, ut + N * n, static_cast<int>(n),
+                                 static_cast<int>(N), N, n, nN, 2 * N * n, L, st);
     if (e != cudaSuccess) return MODPP_ERR_CUDA;
-    const size_t wide_bytes = modpp_mm_wide_workspace(2 * N, N, N, r->primes.data(), L);
+    const size_t wide_bytes = modpp_mm_wide_workspace(2 * N, n, N, r->primes.data(), L);
     void *wws = base + lay.wide;
-    rc = modpp_mm_wide_pair(2 * N, N, N, ut, N, 2 * NN, rw, rw + L * NN, N, NN, x, y, N, 2 * NN,
-                            r->primes.data(), L, wws, wide_bytes, st);
+    int rc = modpp_mm_wide_pair(2 * N, n, N, ut, n, 2 * N * n, m2, m2 + L * nN, N, nN, x, y, N,
+                                2 * NN, r->primes.data(), L, wws, wide_bytes, st);
     if (rc) return rc;
     mark(2);
     // Steps 3-4: Transpose((C00, 0)) and Transpose((C10, 0)) as one batch.
@@ -692,7 +707,14 @@ int cc_mm(modpp_ring r, const uint64_t *ct1, const uint64_t *ct2, const uint64_t
     fp.qlinv_s = r->qlinv_s;
     if (launch_cc_finish(fp, st) != cudaSuccess) return MODPP_ERR_CUDA;
     mark(4);
+    if (out_scale_mult) *out_scale_mult = 1.0 / static_cast<double>(r->primes[L - 1]);
     return MODPP_OK;
+}
+
+int cc_mm(modpp_ring r, const uint64_t *ct1, const uint64_t *ct2, const uint64_t *aut_keys,
+          const uint64_t *relin_key, uint64_t *out, void *ws, size_t ws_bytes, void *stream) {
+    if (r == nullptr) return MODPP_ERR_ARG;
+    return cc_mm_ex(r, r->N, ct1, ct2, aut_keys, relin_key, 0, out, nullptr, ws, ws_bytes, stream);
 }
 
 int modpp_ring_status_read(modpp_ring r, void *stream) {

@@ -49,6 +49,9 @@ def _register():
     L.cc_mm.argtypes = [P, P, P, P, P, P, P, SZ, P]
     L.cc_mm_stage_ms.argtypes = [P, P]
     L.modpp_ring_status_read.argtypes = [P, P]
+    L.cc_mm_ex_workspace.argtypes = [P, I64, I]
+    L.cc_mm_ex_workspace.restype = SZ
+    L.cc_mm_ex.argtypes = [P, I64, P, P, P, P, I, P, P, P, SZ, P]
     _registered = True
     return L
 
@@ -198,6 +201,36 @@ class Ring:
                            relin_key.data_ptr(), out.data_ptr(), wp, wl, _stream_handle(stream)),
                "cc_mm")
         return out
+
+    def cc_mm_ex(self, ct1: torch.Tensor, ct2: torch.Tensor, aut_keys: torch.Tensor,
+                 relin_key: torch.Tensor, m2_rowwise: bool = False, out=None, stream=None,
+                 workspace=None):
+        """Alg. 8 with the right operand column-wise (as cc_mm) or, with
+        m2_rowwise, row-wise and Step 1 skipped: ct1 (2, L, n, N) encrypts the
+        columns of an N x n matrix, ct2 (2, L, n, N) the rows of an n x N
+        matrix, 1 <= n <= N.  Returns (out (2, L-1, N, N), scale multiplier
+        1/q_{L-1} of the output)."""
+        n = self._batch(ct1, "ct1")
+        if self._batch(ct2, "ct2") != n:
+            raise ValueError("ct1 and ct2 must hold the same number of ciphertexts")
+        if not m2_rowwise and n != self.N:
+            raise ValueError("a column-wise ct2 needs N ciphertexts")
+        if self._keys(aut_keys, "aut_keys") != self.N:
+            raise ValueError("aut_keys must hold N keys")
+        self._keys(relin_key, "relin_key")
+        flags = 1 if m2_rowwise else 0
+        if out is None:
+            out = torch.empty((2, self.L - 1, self.N, self.N), dtype=torch.uint64,
+                              device=ct1.device)
+        need = int(lib().cc_mm_ex_workspace(self._h, n, flags))
+        if need == 0:
+            raise ModppError(-1, "cc_mm_ex_workspace")
+        wp, wl = _workspace(need, ct1.device, workspace)
+        mult = ctypes.c_double()
+        _check(lib().cc_mm_ex(self._h, n, ct1.data_ptr(), ct2.data_ptr(), aut_keys.data_ptr(),
+                              relin_key.data_ptr(), flags, out.data_ptr(), ctypes.byref(mult),
+                              wp, wl, _stream_handle(stream)), "cc_mm_ex")
+        return out, mult.value
 
     def status(self, stream=None) -> int:
         """Reads and clears the ring's status word (syncs the stream):

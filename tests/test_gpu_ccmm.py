@@ -222,3 +222,53 @@ def test_cc_mm_two_prime_chain(oracle_mod, lib_ready):
     got = C.from_batch(host(R.cc_mm(dev(C.to_batch(c1)), dev(C.to_batch(c2)), dkeys, drk)))
     assert got.shape == (N, 2, 1, N)
     assert np.array_equal(got, want)
+
+
+@pytest.mark.parametrize("N,n", [(16, 16), (16, 4), (16, 1), (64, 24), (256, 256), (256, 100)])
+def test_cc_mm_rowwise_bit_exact_and_decrypts(oracle_mod, lib_ready, N, n):
+    # Alg. 8 with Step 1 skipped: column-wise M1 (N x n) times row-wise M2 (n x N).
+    R, s, keys, rk, dkeys, drk = setup(oracle_mod, lib_ready, N)
+    delta = 2.0 ** 40
+    M1 = synth.uniform_unit(N + n, 6, (N, n))
+    M2 = synth.uniform_unit(N + n, 7, (n, N))
+    c1, _, _ = C.encrypt_rows(oracle_mod, np.ascontiguousarray(M1.T), s, delta, 31)
+    rw, _, _ = C.encrypt_rows(oracle_mod, M2, s, delta, 32)
+    want, _ = oracle_mod.cc_mm_rowwise(c1, rw, keys, rk, C.PRP)
+    got, mult = R.cc_mm_ex(dev(C.to_batch(c1)), dev(C.to_batch(rw)), dkeys, drk, m2_rowwise=True)
+    got = C.from_batch(host(got))
+    assert mult == 1.0 / C.PR[-1]
+    assert np.array_equal(got, want)
+    scale = delta * delta * mult
+    ref = M1 @ M2
+    for j in range(0, N, max(1, N // 8)):
+        dec = oracle_mod.rlwe_decrypt_rows(got[j, 0][:, None, :], got[j, 1][:, None, :], s,
+                                           C.PR[:-1])[:, 0]
+        val = oracle_mod.crt2(dec[0], dec[1], C.PR[0], C.PR[1]).astype(np.float64) / scale
+        assert np.max(np.abs(val - ref[:, j])) <= 2.0 ** -20
+
+
+def test_cc_mm_rowwise_equals_cc_mm_after_transpose(oracle_mod, lib_ready):
+    # Giving Alg. 8 the transposed (row-wise) right operand and skipping Step 1
+    # is the same computation as the column-wise call.
+    N = 64
+    R, s, keys, rk, dkeys, drk = setup(oracle_mod, lib_ready, N)
+    c1 = dev(C.to_batch(C.rand_cts(51, N, N, C.PR)))
+    c2 = dev(C.to_batch(C.rand_cts(52, N, N, C.PR)))
+    full = host(R.cc_mm(c1, c2, dkeys, drk))
+    rw = R.transpose(c2, dkeys)
+    part, _ = R.cc_mm_ex(c1, rw, dkeys, drk, m2_rowwise=True)
+    assert np.array_equal(host(part), full)
+    col, _ = R.cc_mm_ex(c1, c2, dkeys, drk)
+    assert np.array_equal(host(col), full)
+
+
+def test_cc_mm_ex_rejects_bad_shapes(lib_ready):
+    from paper_2503_16080_gb300.api import lib
+    N = 16
+    R = lib_ready.Ring(N, C.PRP)
+    assert lib().cc_mm_ex_workspace(R._h, 8, 0) == 0       # column-wise needs n = N
+    assert lib().cc_mm_ex_workspace(R._h, 0, 1) == 0
+    assert lib().cc_mm_ex_workspace(R._h, N + 1, 1) == 0
+    assert lib().cc_mm_ex_workspace(R._h, 4, 2) == 0       # unknown flag
+    assert lib().cc_mm_ex_workspace(R._h, 4, 1) > 0
+    assert lib().cc_mm_ex_workspace(R._h, N, 0) == lib().cc_mm_workspace(R._h)

@@ -11,7 +11,8 @@ exactly that sequence:
   N = 1024 and 8192;
 - Transpose (Alg. 4) at N = 1024 and 2048;
 - CC-MM (Alg. 8) at N = 1024, whose second transpose also runs the zero-b
-  form and whose relinearisation runs the single-key kernel."""
+  form and whose relinearisation runs the single-key kernel, and its form
+  with a row-wise right operand (Step 1 skipped, inner dimension 256)."""
 import numpy as np
 import pytest
 import torch
@@ -107,3 +108,17 @@ def test_cc_mm_bit_exact_n1024(oracle_mod, ring_mod):
                                            C.PR[:-1])[:, 0]
         val = oracle_mod.crt2(dec[0], dec[1], C.PR[0], C.PR[1]).astype(np.float64) / scale
         assert np.max(np.abs(val - ref[:, j])) <= 2.0 ** -20
+
+
+def test_cc_mm_rowwise_bit_exact_n1024(oracle_mod, ring_mod):
+    # Alg. 8 without Step 1 at N = 1024, inner dimension n = 256.
+    N, n = 1024, 256
+    R, s, keys, rk, dkeys, drk = setup(oracle_mod, ring_mod, N)
+    delta = 2.0 ** 40
+    M1 = synth.uniform_unit(N, 14, (N, n))
+    M2 = synth.uniform_unit(N, 15, (n, N))
+    c1, _, _ = C.encrypt_rows(oracle_mod, np.ascontiguousarray(M1.T), s, delta, 41)
+    rw, _, _ = C.encrypt_rows(oracle_mod, M2, s, delta, 42)
+    want, _ = oracle_mod.cc_mm_rowwise(c1, rw, keys, rk, C.PRP)
+    got, mult = R.cc_mm_ex(dev(C.to_batch(c1)), dev(C.to_batch(rw)), dkeys, drk, m2_rowwise=True)
+    assert np.array_equal(C.from_batch(host(got)), want)
