@@ -13,6 +13,10 @@ computes:
 * ``strategy1_*``    Strategy 1 of Sec. 6.1 (Lemma le:strategy1, Eq. decomp):
                      base-K signed digits, k1*k2 binary64 products, integer
                      recombination.  The FP64-limb path computes this.
+* ``strategy2_*``    Strategy 2 of Sec. 6.1 (truncation): the product with the
+                     high-order bits of the residue operand (an approximate
+                     Mod-PP-MM for one modulus), in binary64 as printed and
+                     as a rounding to a multiple of 2^s.
 * ``negacyclic_mul`` products in R_q = Z_q[X]/(X^N+1) (Sec. 2).
 * ``ckks_encode`` / ``rlwe_encrypt_rows`` / ``rlwe_decrypt_rows`` / ``crt2``:
                      textbook coefficient-encoded CKKS (Sec. 2.2).
@@ -222,6 +226,48 @@ def strategy1_mod_pp_mm(U: np.ndarray, A: np.ndarray, q: int) -> tuple[np.ndarra
             total = total + prod.astype(np.int64).astype(object) * (K ** (i + j))
     C = np.asarray(total % q, dtype=np.uint64)
     return C, {"K": K, "k1": k1, "k2": k2, "products": k1 * k2}
+
+
+# --------------------------------------------------------------------------
+# Strategy 2 of Sec. 6.1 (truncation): an approximate product from the
+# high-order bits of the residue operand, for one modulus q
+# --------------------------------------------------------------------------
+
+def strategy2_round_high(B: np.ndarray, q: int, s: int) -> np.ndarray:
+    """The residues' high-order bits: each entry of B (mod q) taken as its
+    centred representative x in (-q/2, q/2] and rounded to the nearest
+    multiple of 2^s, ties upward: 2^s * floor((x + 2^(s-1)) / 2^s).  s = 0
+    keeps x.  Python integers (object array)."""
+    x = centered(B, q)
+    if s == 0:
+        return x
+    return ((x + (1 << (s - 1))) // (1 << s)) * (1 << s)
+
+
+def strategy2_trunc(U: np.ndarray, B: np.ndarray, q: int, s: int) -> np.ndarray:
+    """Mod-PP-MM of U with B's high-order bits (the truncation of Sec. 6.1
+    with the decomposition of Eq. decomp started from the top, keeping the
+    bits above 2^s): C = U * strategy2_round_high(B, q, s) mod q, canonical.
+    Every entry differs from the exact (U * B mod q) by at most
+    k * max|U| * 2^(s-1) (centred)."""
+    Bs = strategy2_round_high(B, q, s)
+    return mod_pp_mm(np.asarray(U), np.asarray(Bs % q, dtype=np.uint64)[None], [q])[0]
+
+
+def strategy2_fp64(U: np.ndarray, B: np.ndarray, q: int) -> np.ndarray:
+    """Strategy 2 as the paper states it for binary64: B's centred entries
+    rounded to 53 bits (the nearest double), one floating-point product with
+    U, and the product's value reduced modulo q.  The double products are
+    integers; their residues are taken exactly, so the only errors are the
+    rounding of B and of the floating-point sums (the paper's bound:
+    about 2^-50 * k * ||U|| * ||B||)."""
+    Bf = np.array([[float(v) for v in row] for row in centered(B, q)], dtype=np.float64) \
+        if B.size else np.zeros(B.shape)
+    P = np.asarray(U, dtype=np.float64) @ Bf
+    out = np.empty(P.shape, dtype=np.uint64)
+    for idx, v in np.ndenumerate(P):
+        out[idx] = int(v) % q
+    return out
 
 
 # --------------------------------------------------------------------------
