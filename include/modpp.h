@@ -154,6 +154,35 @@ int modpp_mm(int64_t d, int64_t k, int64_t n, const void *U, int ukind, int64_t 
              size_t ws_bytes, void *stream);
 
 /*
+ * Approximate Mod-PP-MM of ONE modulus from the high-order bits of the
+ * residue operand: Strategy 2 of Sec. 6.1 ("truncation").  The paper uses
+ * it for the b-part of PC-MM, where an error e on the product becomes an
+ * error of about e / Delta on the decoded message.  q: one odd modulus,
+ * 3 <= q < 2^62 (it need not be prime).  B (k x n, leading dimension ldb)
+ * holds residues in [0, q); each entry is read as its centred representative
+ * x in (-q/2, q/2].  C (d x n, ldc) receives canonical residues.
+ *   MODPP_PATH_F16, drop_bits = s >= 0 (s <= bits(q)): x is rounded to the
+ *     nearest multiple of 2^s (ties upward), x_s = 2^s floor((x + 2^(s-1))
+ *     / 2^s), and C = U * x_s mod q exactly, on the f16 digits of x_s / 2^s
+ *     (fewer digit products than the exact product when s drops whole
+ *     digits).  U int8, or int32 with values in [-128, 127].
+ *     |C - U * B|  <=  k * max|U| * 2^(s-1)   (centred, per entry).
+ *     s = 0 is the exact product.
+ *   MODPP_PATH_FP64, drop_bits = 0: as printed, x rounded to the nearest
+ *     double (53 significant bits), one binary64 product with U (cuBLAS
+ *     DGEMM; any int32 U is exact in binary64), and the exact residue of
+ *     each (integer-valued) double product.  The paper's bound:
+ *     |C - U * B| <~ 2^-50 * k * max|U| * max|x|.
+ * Sizes and errors as modpp_mm; other paths or a drop_bits outside the
+ * range return MODPP_ERR_ARG.  Workspace from modpp_mm_trunc_workspace.
+ */
+size_t modpp_mm_trunc_workspace(int64_t d, int64_t k, int64_t n, uint64_t q, int path,
+                                int drop_bits);
+int modpp_mm_trunc(int64_t d, int64_t k, int64_t n, const void *U, int ukind, int64_t ldu,
+                   const uint64_t *B, int64_t ldb, uint64_t *C, int64_t ldc, uint64_t q, int path,
+                   int drop_bits, void *ws, size_t ws_bytes, void *stream);
+
+/*
  * Mod-PP-MM of two residue matrices (the products of two ciphertext
  * matrices in Alg. 8, step 2):
  *   C_j = U_j * A_j mod q_j,   0 <= j < P,

@@ -16,7 +16,7 @@ _API_NAMES = (
     "ModppError", "lib", "library_path", "profile_enable", "profile_read", "KERNEL_GEMM",
     "KERNEL_SPLIT", "KERNEL_U16", "set_digit_bits", "get_digit_bits", "GroupedPlan",
     "modpp_mm_grouped", "modpp_mm_wide", "set_wide_path", "get_wide_path", "wide_plan_info",
-    "selftest_bounded_wait", "set_debug_checks", "get_debug_checks",
+    "selftest_bounded_wait", "set_debug_checks", "get_debug_checks", "modpp_mm_trunc",
 )
 _RING_NAMES = ("Ring",)
 

@@ -91,6 +91,10 @@ def lib() -> ctypes.CDLL:
         L.modpp_set_wide_path.argtypes = [I]
         L.modpp_get_wide_path.restype = I
         L.modpp_wide_plan_info.argtypes = [I64, P, I, P]
+        L.modpp_mm_trunc_workspace.argtypes = [I64, I64, I64, U64, I, I]
+        L.modpp_mm_trunc_workspace.restype = SZ
+        L.modpp_mm_trunc.argtypes = [I64, I64, I64, P, I, I64, P, I64, P, I64, U64, I, I, P, SZ,
+                                     P]
         L.modpp_set_debug_checks.argtypes = [I]
         L.modpp_get_debug_checks.restype = I
         L.modpp_profile_enable.argtypes = [I]
@@ -318,6 +322,40 @@ def modpp_mm_wide(U: torch.Tensor, A: torch.Tensor, primes: Sequence[int], *,
     _check(lib().modpp_mm_wide(d, k, n, U.data_ptr(), lu, su, A.data_ptr(), la, sa,
                                out.data_ptr(), lc, sc, pr.ctypes.data, P, ws_ptr, ws_len,
                                _stream_handle(stream)), "modpp_mm_wide")
+    return out
+
+
+def modpp_mm_trunc(U: torch.Tensor, B: torch.Tensor, q: int, *, path="f16", drop_bits: int = 0,
+                   out: torch.Tensor | None = None, stream=None,
+                   workspace: torch.Tensor | None = None) -> torch.Tensor:
+    """Strategy 2 of Sec. 6.1: C ~ U @ B mod q for one odd modulus q from the
+    high-order bits of B.  path "f16": B rounded to multiples of 2^drop_bits,
+    exact product of the rounded operand; path "fp64": B rounded to 53 bits,
+    one DGEMM (drop_bits 0).  U: (d, k) int8/int32; B: (k, n) uint64 residues.
+    Returns (d, n) uint64."""
+    _check_residues(B, "B")
+    if not U.is_cuda or U.dtype not in (torch.int8, torch.int32) or U.dim() != 2 or B.dim() != 2:
+        raise TypeError("U must be 2-D int8/int32 and B 2-D uint64 CUDA tensors")
+    if U.shape[1] != B.shape[0]:
+        raise ValueError("inner dimensions differ")
+    d, k = U.shape
+    n = B.shape[1]
+    if (U.numel() and U.stride(1) != 1) or (B.numel() and B.stride(1) != 1):
+        raise ValueError("unit stride along the last dimension required")
+    if out is None:
+        out = torch.empty((d, n), dtype=torch.uint64, device=B.device)
+    p = _path(path)
+    need = int(lib().modpp_mm_trunc_workspace(d, k, n, int(q), p, int(drop_bits)))
+    if need == 0:
+        raise ModppError(-1, "modpp_mm_trunc_workspace")
+    ws_ptr, ws_len = _workspace(need, B.device, workspace)
+    ldu = U.stride(0) if U.numel() else k
+    ldb = B.stride(0) if B.numel() else n
+    ldc = out.stride(0) if out.numel() else n
+    _check(lib().modpp_mm_trunc(d, k, n, U.data_ptr(), 0 if U.dtype == torch.int8 else 1, ldu,
+                                B.data_ptr(), ldb, out.data_ptr(), ldc, int(q), p,
+                                int(drop_bits), ws_ptr, ws_len, _stream_handle(stream)),
+           "modpp_mm_trunc")
     return out
 
 

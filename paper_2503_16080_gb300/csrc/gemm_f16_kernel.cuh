@@ -444,9 +444,9 @@ __global__ void __launch_bounds__(kThreads, 1)
                             x = add_mod(x, shoup_mulmod(static_cast<uint64_t>(grp[2][c]) + pc.qoff,
                                                         pc.wg2, pc.wg2s, pc.q),
                                         pc.q);
-                        if (pc.accumulate) {  // C <- C + wout * x  (wide products)
-                            x = shoup_mulmod(x, pc.wout, pc.wouts, pc.q);
-                            if (col0 + c < j.n) x = add_mod(x, out[c], pc.q);
+                        if (pc.accumulate) {  // C <- C + wout * x (wide products), or
+                            x = shoup_mulmod(x, pc.wout, pc.wouts, pc.q);  // wout * x (2)
+                            if (pc.accumulate == 1 && col0 + c < j.n) x = add_mod(x, out[c], pc.q);
                         }
                         v[k4] = x;
                     }

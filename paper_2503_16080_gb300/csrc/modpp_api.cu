@@ -618,6 +618,190 @@ int debug_check_wide(int64_t d, int64_t k, int64_t n, const uint64_t *U, int64_t
     return cuda_status(e);
 }
 
+// ------------------------------------------------------------ Strategy 2
+// Approximate Mod-PP-MM of one modulus from the high-order bits of the
+// residue operand (Sec. 6.1, "Strategy 2: truncation").
+//
+// F16 form: each centred residue x of B is rounded to the nearest multiple
+// of 2^s, y = floor((x + 2^(s-1)) / 2^s); C = 2^s * (U * y) mod q exactly
+// (the digit GEMM on y's balanced digits, whose epilogue multiplies by 2^s).
+// Balanced b-bit digits of y: the fewest L whose window
+// [-2^(b-1) S_L, (2^(b-1) - 1) S_L], S_L = sum_{i<L} 2^(b i), holds every y.
+struct TruncF16Layout {
+    F16Layout f16;
+    int64_t ymin = 0, ymax = 0;
+};
+TruncF16Layout trunc_f16_layout(int64_t d, int64_t k, int64_t n, uint64_t q, int s) {
+    TruncF16Layout t;
+    const int64_t half = static_cast<int64_t>((q - 1) / 2);
+    const int64_t rnd = s > 0 ? (int64_t(1) << (s - 1)) : 0;
+    t.ymax = (half + rnd) >> s;
+    t.ymin = (-half + rnd) >> s;  // arithmetic shift: floor
+    F16Layout &lay = t.f16;
+    lay.b = current_digit_bits();
+    lay.L = 0;
+    for (int L = 1; L <= kMaxDigits; ++L) {
+        unsigned __int128 S = 0;
+        for (int i = 0; i < L; ++i) S += static_cast<unsigned __int128>(1) << (lay.b * i);
+        const unsigned __int128 lo = S << (lay.b - 1);
+        const unsigned __int128 hi = S * ((1u << (lay.b - 1)) - 1u);
+        if (static_cast<unsigned __int128>(-t.ymin) <= lo &&
+            static_cast<unsigned __int128>(t.ymax) <= hi) {
+            lay.L = L;
+            break;
+        }
+    }
+    if (lay.L == 0) return t;
+    const int nc = tile_cols_for(lay.L, n);
+    lay.nc = nc;
+    lay.kp = (k + 7) / 8 * 8;
+    lay.n_blocks = (n + nc - 1) / nc;
+    lay.rows = lay.n_blocks * lay.L * nc;
+    lay.off_u16 = kHeaderBytes;
+    lay.off_d = lay.off_u16 + align_up(static_cast<size_t>(d) * lay.kp * 2);
+    lay.total = lay.off_d + align_up(static_cast<size_t>(lay.rows) * lay.kp * 2);
+    return t;
+}
+
+int run_f16_trunc(int64_t d, int64_t k, int64_t n, const void *U, int ukind, int64_t ldu,
+                  const uint64_t *B, int64_t ldb, uint64_t *C, int64_t ldc, uint64_t q, int s,
+                  void *ws, size_t ws_bytes, cudaStream_t st) {
+    const TruncF16Layout tl = trunc_f16_layout(d, k, n, q, s);
+    const F16Layout &lay = tl.f16;
+    if (lay.L == 0) return MODPP_ERR_UNSUPPORTED;
+    if (ws_bytes < lay.total) return MODPP_ERR_WORKSPACE;
+    if (lay.rows >= (int64_t(1) << 31)) return MODPP_ERR_UNSUPPORTED;
+    uint8_t *w = static_cast<uint8_t *>(ws);
+    int *status = reinterpret_cast<int *>(w);
+    if (cudaMemsetAsync(status, 0, sizeof(int), st) != cudaSuccess) return MODPP_ERR_CUDA;
+    PlaneIn pl{B, ldb, q, C, ldc};
+    if (d == 0 || n == 0) return MODPP_OK;
+    if (k == 0) return zero_outputs(d, n, &pl, 1, st);
+
+    __half *U16 = reinterpret_cast<__half *>(w + lay.off_u16);
+    __half *D = reinterpret_cast<__half *>(w + lay.off_d);
+    int rc = cuda_status(launch_u_to_f16(U, ukind, ldu, static_cast<int>(d), static_cast<int>(k),
+                                         static_cast<int>(lay.kp), U16, st));
+    if (rc) return rc;
+    SplitParams sp{};
+    sp.k = static_cast<int>(k);
+    sp.n = static_cast<int>(n);
+    sp.kp = static_cast<int>(lay.kp);
+    sp.n_blocks = static_cast<int>(lay.n_blocks);
+    sp.planes = 1;
+    sp.digits = lay.L;
+    sp.digit_bits = lay.b;
+    sp.nc = lay.nc;
+    sp.D = D;
+    // Centred lift (values above (q-1)/2 become x - q), then the rounding shift.
+    sp.sp[0] = SplitPlane{B, ldb, q, (q - 1) / 2, s};
+    rc = cuda_status(launch_split_digits(sp, st));
+    if (rc) return rc;
+
+    CUtensorMap tmU, tmD;
+    if (!make_map_f16(&tmU, U16, static_cast<uint64_t>(lay.kp), static_cast<uint64_t>(d), kBK, kBM) ||
+        !make_map_f16(&tmD, D, static_cast<uint64_t>(lay.kp), static_cast<uint64_t>(lay.rows), kBK,
+                      static_cast<uint32_t>(lay.L * lay.nc)))
+        return MODPP_ERR_CUDA;
+    GemmParams gp{};
+    gp.d = static_cast<int>(d);
+    gp.n = static_cast<int>(n);
+    gp.k = static_cast<int>(k);
+    gp.m_blocks = static_cast<int>((d + kBM - 1) / kBM);
+    gp.n_blocks = static_cast<int>(lay.n_blocks);
+    gp.planes = 1;
+    gp.kb_total = static_cast<int>((k + kBK - 1) / kBK);
+    const int64_t tiles = static_cast<int64_t>(gp.m_blocks) * gp.n_blocks;
+    if (tiles >= (int64_t(1) << 31)) return MODPP_ERR_UNSUPPORTED;
+    gp.num_tiles = static_cast<int>(tiles);
+    gp.band_m = band_rows(gp.m_blocks, lay.kp);
+    gp.status = status;
+    gp.timeout_ns = wait_limit_ns();
+    gp.pc[0] = make_plane_const(q, lay.b, C, ldc);
+    if (s > 0) {  // C <- 2^s * (U * y) mod q
+        gp.pc[0].accumulate = 2;
+        gp.pc[0].wout = host_pow2_mod(s, q);
+        gp.pc[0].wouts = host_shoup(gp.pc[0].wout, q);
+    }
+    const int sms = device_sms();
+    if (sms <= 0) return MODPP_ERR_CUDA;
+    EventPair *ev = timer_begin(MODPP_KERNEL_GEMM, st);
+    rc = cuda_status(launch_gemm_f16(tmU, tmD, gp, lay.L, lay.b, sms, st, lay.nc));
+    timer_end(ev, st);
+    return rc;
+}
+
+// FP64 form, as printed: the centred entries of B rounded to the nearest
+// double (53 bits), one cuBLAS DGEMM with U, and the exact residue of every
+// integer-valued double product.
+struct TruncFp64Layout {
+    size_t off_u = 0, off_b = 0, off_p = 0, off_cublas = 0, total = 0;
+};
+TruncFp64Layout trunc_fp64_layout(int64_t d, int64_t k, int64_t n) {
+    TruncFp64Layout lay;
+    lay.off_u = kHeaderBytes;
+    lay.off_b = lay.off_u + align_up(static_cast<size_t>(d) * k * 8);
+    lay.off_p = lay.off_b + align_up(static_cast<size_t>(k) * n * 8);
+    lay.off_cublas = lay.off_p + align_up(static_cast<size_t>(d) * n * 8);
+    lay.total = lay.off_cublas + kCublasWsBytes;
+    return lay;
+}
+
+int run_fp64_trunc(int64_t d, int64_t k, int64_t n, const void *U, int ukind, int64_t ldu,
+                   const uint64_t *B, int64_t ldb, uint64_t *C, int64_t ldc, uint64_t q, void *ws,
+                   size_t ws_bytes, cudaStream_t st) {
+    const TruncFp64Layout lay = trunc_fp64_layout(d, k, n);
+    if (ws_bytes < lay.total) return MODPP_ERR_WORKSPACE;
+    uint8_t *w = static_cast<uint8_t *>(ws);
+    int *status = reinterpret_cast<int *>(w);
+    if (cudaMemsetAsync(status, 0, sizeof(int), st) != cudaSuccess) return MODPP_ERR_CUDA;
+    PlaneIn pl{B, ldb, q, C, ldc};
+    if (d == 0 || n == 0) return MODPP_OK;
+    if (k == 0) return zero_outputs(d, n, &pl, 1, st);
+    if (d >= (int64_t(1) << 31) || n >= (int64_t(1) << 31)) return MODPP_ERR_UNSUPPORTED;
+
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev >= kMaxDevices) return MODPP_ERR_CUDA;
+    std::lock_guard<std::mutex> lock(g_cublas_mu);
+    if (!g_cublas[dev] && cublasCreate(&g_cublas[dev]) != CUBLAS_STATUS_SUCCESS)
+        return MODPP_ERR_CUDA;
+    cublasHandle_t h = g_cublas[dev];
+    if (cublasSetStream(h, st) != CUBLAS_STATUS_SUCCESS ||
+        cublasSetWorkspace(h, w + lay.off_cublas, kCublasWsBytes) != CUBLAS_STATUS_SUCCESS ||
+        cublasSetMathMode(h, CUBLAS_DEFAULT_MATH) != CUBLAS_STATUS_SUCCESS)
+        return MODPP_ERR_CUDA;
+    double *Ud = reinterpret_cast<double *>(w + lay.off_u);
+    double *Bd = reinterpret_cast<double *>(w + lay.off_b);
+    double *Pd = reinterpret_cast<double *>(w + lay.off_p);
+    int rc = cuda_status(
+        launch_u_to_f64(U, ukind, ldu, static_cast<int>(d), static_cast<int>(k), Ud, st));
+    if (rc) return rc;
+    // One signed "digit" of base 2^63: the centred residue itself, converted
+    // to the nearest double.
+    Fp64SplitParams sp{B, ldb, static_cast<int>(k), static_cast<int>(n), 1, q,
+                       uint64_t(1) << 63, Bd};
+    rc = cuda_status(launch_fp64_split(sp, st));
+    if (rc) return rc;
+    const double one = 1.0, zero = 0.0;
+    if (cublasDgemm(h, CUBLAS_OP_N, CUBLAS_OP_N, static_cast<int>(n), static_cast<int>(d),
+                    static_cast<int>(k), &one, Bd, static_cast<int>(n), Ud, static_cast<int>(k),
+                    &zero, Pd, static_cast<int>(n)) != CUBLAS_STATUS_SUCCESS)
+        return MODPP_ERR_CUDA;
+    Fp64ResidueParams rp{};
+    rp.P = Pd;
+    rp.d = static_cast<int>(d);
+    rp.n = static_cast<int>(n);
+    rp.q = q;
+    rp.mu = host_barrett_mu(q);
+    for (int e = 0; e < kMaxPow2Shift; ++e) {
+        rp.pow2[e] = host_pow2_mod(e, q);
+        rp.pow2s[e] = host_shoup(rp.pow2[e], q);
+    }
+    rp.C = C;
+    rp.ldc = ldc;
+    return cuda_status(launch_fp64_residue(rp, st));
+}
+
 size_t layout_bytes(int64_t d, int64_t k, int64_t n, const uint64_t *qs, int planes, int path) {
     if (path == MODPP_PATH_F16) return f16_layout(d, k, n, qs, planes).total;
     return fp64_layout(d, k, n, qs, planes, path == MODPP_PATH_FP64_TIGHT).total;
@@ -896,6 +1080,42 @@ int modpp_mm_wide_pair(int64_t d, int64_t k, int64_t n, const uint64_t *U, int64
     if (rc) return rc;
     return debug_check_wide(d, k, n, U, ldu, strideU, A1, A2, lda, strideA, primes_host, P, ws,
                             st);
+}
+
+size_t modpp_mm_trunc_workspace(int64_t d, int64_t k, int64_t n, uint64_t q, int path,
+                                int drop_bits) {
+    if (check_sizes(d, k, n) || !prime_ok(q)) return 0;
+    if (path == MODPP_PATH_F16) {
+        if (drop_bits < 0 || drop_bits > bit_length(q)) return 0;
+        const TruncF16Layout t = trunc_f16_layout(d, k, n, q, drop_bits);
+        return t.f16.L == 0 ? 0 : t.f16.total;
+    }
+    if (path == MODPP_PATH_FP64 && drop_bits == 0) return trunc_fp64_layout(d, k, n).total;
+    return 0;
+}
+
+int modpp_mm_trunc(int64_t d, int64_t k, int64_t n, const void *U, int ukind, int64_t ldu,
+                   const uint64_t *B, int64_t ldb, uint64_t *C, int64_t ldc, uint64_t q, int path,
+                   int drop_bits, void *ws, size_t ws_bytes, void *stream) {
+    if (path != MODPP_PATH_F16 && path != MODPP_PATH_FP64) return MODPP_ERR_ARG;
+    if (path == MODPP_PATH_F16 ? (drop_bits < 0 || (q >= 3 && drop_bits > bit_length(q)))
+                               : drop_bits != 0)
+        return MODPP_ERR_ARG;
+    const int rc = modpp::mm_check_args(d, k, n, U, ukind, ldu, B, ldb, 0, C, ldc, 0, &q, 1);
+    if (rc) return rc;
+    if (ws == nullptr || (reinterpret_cast<uintptr_t>(ws) & (kAlign - 1)) != 0)
+        return MODPP_ERR_WORKSPACE;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const int rc2 = path == MODPP_PATH_F16
+                        ? run_f16_trunc(d, k, n, U, ukind, ldu, B, ldb, C, ldc, q, drop_bits, ws,
+                                        ws_bytes, st)
+                        : run_fp64_trunc(d, k, n, U, ukind, ldu, B, ldb, C, ldc, q, ws, ws_bytes,
+                                         st);
+    if (rc2) return rc2;
+    // Debug mode: B canonical; int32 U in [-128, 127] on the f16 path only
+    // (the binary64 form takes any int32 plaintext).
+    return debug_check_inputs(d, k, n, U, path == MODPP_PATH_F16 ? ukind : MODPP_U_I8, ldu, B,
+                              ldb, 0, &q, 1, ws, st);
 }
 
 int modpp_selftest_bounded_wait(void *ws, uint64_t limit_ns, void *stream) {

@@ -58,7 +58,7 @@ struct PlaneConst {
     uint64_t qoff;  // a multiple of q >= 2^57: g + qoff lies in [0, 2^64) for |g| < 2^57
     uint64_t wout;  // accumulate mode: C <- C + wout * (U*A) mod q
     uint64_t wouts; // Shoup quotient of wout
-    int accumulate; // 0: C <- U*A mod q
+    int accumulate; // 0: C <- U*A mod q;  1: C <- C + wout * (U*A);  2: C <- wout * (U*A)
 };
 
 // One (problem, prime) plane of a grouped launch.  Planes are stored in tile
@@ -99,6 +99,7 @@ struct SplitPlane {
     int64_t lda;
     uint64_t q;
     uint64_t thresh;    // residues above thresh are lifted to a - q (balanced window)
+    int shift = 0;      // > 0: lifted value rounded to floor((x + 2^(s-1)) / 2^s) first
 };
 
 struct SplitParams {
@@ -223,6 +224,18 @@ struct Fp64RecombineParams {
     int64_t ldc;
 };
 cudaError_t launch_fp64_recombine(const Fp64RecombineParams &p, cudaStream_t s);
+// Exact residues of integer-valued double products (Strategy 2).
+constexpr int kMaxPow2Shift = 72;
+struct Fp64ResidueParams {
+    const double *P;  // d x n, leading dimension n
+    int d, n;
+    uint64_t q, mu;
+    uint64_t pow2[kMaxPow2Shift];   // 2^e mod q
+    uint64_t pow2s[kMaxPow2Shift];  // Shoup quotients
+    uint64_t *C;
+    int64_t ldc;
+};
+cudaError_t launch_fp64_residue(const Fp64ResidueParams &p, cudaStream_t s);
 
 // Value-range checks of the inputs (debug mode, range_checks.cu).
 constexpr int kMaxRangeQ = 40;

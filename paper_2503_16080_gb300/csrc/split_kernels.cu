@@ -107,7 +107,7 @@ __global__ void __launch_bounds__(256) split_digits_kernel(const __grid_constant
     __half *Dblock =
         p.D + (static_cast<int64_t>(plane) * p.n_blocks + nb) * L * NC * static_cast<int64_t>(p.kp);
     split_digit_tile<L, DB, NC>(tile, sp.A, sp.lda, sp.q, sp.thresh, p.k, p.n, p.kp, L,
-                                blockIdx.x * kSplitT, nb * NC, Dblock);
+                                blockIdx.x * kSplitT, nb * NC, Dblock, sp.shift);
 }
 
 template <int DB>
@@ -221,6 +221,39 @@ __global__ void fp64_recombine_kernel(const __grid_constant__ Fp64RecombineParam
         }
         p.C[r * p.ldc + c] = acc;
     }
+}
+
+// Exact residue modulo q of integer-valued binary64 products (Strategy 2 of
+// Sec. 6.1): v = m * 2^e with an integer mantissa |m| < 2^53; for e > 0 the
+// residue is (m mod q) * (2^e mod q).
+__global__ void fp64_residue_kernel(const __grid_constant__ Fp64ResidueParams p) {
+    const int64_t total = static_cast<int64_t>(p.d) * p.n;
+    for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < total;
+         i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        const int64_t r = i / p.n;
+        const int64_t c = i - r * p.n;
+        const double v = p.P[r * p.n + c];
+        int e = 0;
+        const double f = frexp(v, &e);  // v = f * 2^e, 0.5 <= |f| < 1
+        uint64_t res;
+        if (e <= 53) {
+            res = smod_i64(__double2ll_rn(v), p.q, p.mu);  // |v| < 2^53: exact
+        } else {
+            const int64_t m = __double2ll_rn(ldexp(f, 53));  // exact integer mantissa
+            const int sh = e - 53;
+            res = shoup_mulmod(smod_i64(m, p.q, p.mu), p.pow2[sh], p.pow2s[sh], p.q);
+        }
+        p.C[r * p.ldc + c] = res;
+    }
+}
+
+cudaError_t launch_fp64_residue(const Fp64ResidueParams &p, cudaStream_t s) {
+    const int64_t total = static_cast<int64_t>(p.d) * p.n;
+    if (total == 0) return cudaSuccess;
+    int blocks = static_cast<int>((total + 255) / 256);
+    if (blocks > 152 * 32) blocks = 152 * 32;
+    fp64_residue_kernel<<<blocks, 256, 0, s>>>(p);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_fp64_recombine(const Fp64RecombineParams &p, cudaStream_t s) {

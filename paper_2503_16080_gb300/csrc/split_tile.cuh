@@ -31,6 +31,9 @@ __device__ __forceinline__ uint32_t digit_half2(int v0, int v1) {
 // Lifts residue a (in [0, q)) into the balanced window of Lp digits (values
 // above `thresh` become a - q), then peels digits from the bottom:
 // d = ((x + 2^(b-1)) mod 2^b) - 2^(b-1), x <- (x - d) / 2^b (exact).
+// With shift s > 0 the lifted value is first rounded to its high-order
+// bits, x <- floor((x + 2^(s-1)) / 2^s) (the truncation of Strategy 2,
+// Sec. 6.1; the caller multiplies the product by 2^s).
 // Phase 1: a thread takes four consecutive inner indices of one column
 // (loads coalesced along the columns) and writes each digit's four values as
 // one 8-byte word of the tile's row (row stride 136 bytes: a half-warp's
@@ -38,7 +41,8 @@ __device__ __forceinline__ uint32_t digit_half2(int v0, int v1) {
 template <int LMAX, int DB, int NC>
 __device__ __forceinline__ void split_digit_tile(__half *tile, const uint64_t *A, int64_t lda,
                                                  uint64_t q, uint64_t thresh, int k, int n, int kp,
-                                                 int Lp, int t0, int c0, __half *Dblock) {
+                                                 int Lp, int t0, int c0, __half *Dblock,
+                                                 int shift = 0) {
     static_assert(DB <= 10, "digits must satisfy |d| < 512 for the f16 packing");
     constexpr int64_t kHalf = int64_t(1) << (DB - 1);
     constexpr int64_t kMask = (int64_t(1) << DB) - 1;
@@ -53,6 +57,7 @@ __device__ __forceinline__ void split_digit_tile(__half *tile, const uint64_t *A
             uint64_t a = 0;
             if (t < k && c < n) a = A[static_cast<int64_t>(t) * lda + c];
             x[s4] = a > thresh ? static_cast<int64_t>(a - q) : static_cast<int64_t>(a);
+            if (shift > 0) x[s4] = (x[s4] + (int64_t(1) << (shift - 1))) >> shift;
         }
 #pragma unroll
         for (int l = 0; l < LMAX; ++l) {
