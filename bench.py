@@ -760,6 +760,7 @@ def run_ours(args):
             torch.cuda.synchronize()
             torch.cuda.empty_cache()
             line["config1"] = measure_config1(pkg, dev, stream)
+            line["strategy2"] = measure_strategy2(pkg, dev, stream, peaks)
             line["pcmm16384"] = measure_pc_large(pkg, dev, stream, "pcmm16384", 5, 3, peaks)
             line["ccmm"] = measure_ccmm(pkg, dev, stream, 8192, 5, 3, peaks, e2e=True,
                                         cpu_leg=False)
@@ -857,6 +858,55 @@ def measure_pc_large(pkg, dev, stream, workload: str, steps: int, warmup: int, p
     return out
 
 
+def measure_strategy2(pkg, dev, stream, peaks: dict, steps: int = 5, warmup: int = 3):
+    """Strategy 2 of Sec. 6.1 (truncation) in the paper's single-modulus
+    setting: one 54-bit modulus, d = k = n = 4096, U the benchmark's int8
+    plaintext, B uniform residues (an RLWE b-part is indistinguishable from
+    uniform).  Times the exact product (f16 digits), the f16 truncation with
+    s = 9 and 18 dropped bits (one and two fewer digit products) and the
+    binary64 form as printed (one DGEMM); reports each result's largest
+    centred deviation from the exact product against its bound."""
+    import torch
+    from paper_2503_16080_gb300 import synth
+    n = 4096
+    q = synth.ntt_primes(54, 1)[0]
+    U = torch.from_numpy(synth.quantised_normal_int8(SEED, 1, (n, n))).to(dev)
+    B = synth.uniform_mod_torch(SEED, 40, (n, n), q, dev)
+    exact = torch.empty((n, n), dtype=torch.uint64, device=dev)
+    out = torch.empty_like(exact)
+    normU = int(U.abs().max())
+    normB = (q - 1) // 2
+    res = {"workload": "one modulus q ~ 2^54 (54-bit prime), d = k = n = 4096, U int8 "
+                       "(N(0,1)*2^5), B uniform mod q", "q_bits": q.bit_length(), "forms": []}
+    ops = 2.0 * n ** 3
+    forms = [("f16 exact", "f16", 0), ("f16 trunc s=9", "f16", 9), ("f16 trunc s=18", "f16", 18),
+             ("fp64 as printed", "fp64", 0)]
+    for name, path, sbits in forms:
+        dst = exact if name == "f16 exact" else out
+        ms, kern = _timed(lambda: pkg.modpp_mm_trunc(U, B, q, path=path, drop_bits=sbits, out=dst),
+                          steps if path == "f16" else 2, warmup if path == "f16" else 1, stream, pkg)
+        row = {"form": name, "ms": ms, "tops": ops / (ms * 1e-3) / 1e12}
+        if path == "f16":
+            wsb = int(pkg.lib().modpp_mm_trunc_workspace(n, n, n, q, 0, sbits))
+            row["gemm_ms"] = kern["gemm"][0] / max(kern["gemm"][1], 1)
+            row["workspace_bytes"] = wsb
+            row["bound"] = n * normU * 2 ** (sbits - 1) if sbits else 0
+        else:
+            row["bound"] = 2.0 ** -50 * n * normU * normB
+            row["fp64_tflops"] = ops / (ms * 1e-3) / 1e12
+        if name != "f16 exact":
+            d = (out.view(torch.int64) - exact.view(torch.int64))
+            d = torch.remainder(d, q)
+            d = torch.where(d > q // 2, d - q, d)
+            row["max_abs_err"] = int(d.abs().max())
+            row["within_bound"] = row["max_abs_err"] <= row["bound"]
+            row["err_over_scale_2^45"] = row["max_abs_err"] / 2.0 ** 45
+        res["forms"].append(row)
+    del U, B, exact, out
+    torch.cuda.empty_cache()
+    return res
+
+
 def measure_config1(pkg, dev, stream, calls: int = 200):
     """The 256^3 Mod-PP-MM with one 50-bit prime and int32 U (values in
     [-128, 127]): the latency-bound case.  Reports the device time per call
@@ -930,6 +980,9 @@ def run_secondary(args):
     if args.workload in ("pcmm16384", "pcmv"):
         line.update(measure_pc_large(pkg, dev, stream, args.workload, args.steps, args.warmup,
                                      peaks))
+    elif args.workload == "strategy2":
+        line.update({"workload": "strategy2", **measure_strategy2(pkg, dev, stream, peaks,
+                                                                  args.steps, args.warmup)})
     elif args.workload == "hostlink":
         # Pinned host <-> device copy rates (the bound of the end-to-end
         # numbers): one direction at a time, and both at once on separate
@@ -1289,7 +1342,7 @@ def main():
                     help="digit width of the f16 path (8, 9, 10; 0 = library default)")
     ap.add_argument("--workload", default="pcmm4096",
                     choices=["pcmm4096", "pcmm16384", "pcmv", "grouped", "ccmm8192",
-                             "umma_sweep", "hostlink"],
+                             "umma_sweep", "hostlink", "strategy2"],
                     help="pcmm4096 (default, the benchmark line); the others are recorded "
                          "beside it")
     ap.add_argument("--n", type=int, default=4096,
