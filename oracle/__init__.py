@@ -23,8 +23,11 @@ computes:
 * ``toeplitz``       Toep(m) of Sec. 2 (the matrix of u -> u*m).
 * ``tweak_*``, ``automorphism``, ``ks_keygen``, ``keyswitch``, ``rescale``,
   ``transpose``, ``cc_mm``, ``cc_mm_rowwise``: the ring operations of the
-  ciphertext-ciphertext product, Alg. 3 (Tweak), Alg. 4 (Transpose) and Alg. 8 (CC-MM), in the
-  paper's order (``ccmm_oracle.c`` plus the compositions below).
+  ciphertext-ciphertext product, Alg. 3 (Tweak), Alg. 4 (Transpose) and
+  Alg. 8 (CC-MM), in the paper's order (``ccmm_oracle.c`` plus the
+  compositions below).
+* ``pcmm_precomp``   Alg. 7 (CP-MM with precomputation) on a shared-a
+                     encryption, then the key switches back to one secret.
 
 Pins against things other than itself live in ``tests/test_oracle_*.py``.
 """
@@ -581,3 +584,39 @@ def cc_mm_rowwise(ct1, rw, aut_keys, relin_key, primes_with_P):
         extra[1] = ct_add(D23[j, 1], C11[:, :, j], primes)           # D3 + C11
         out[j] = rescale(ct_add(rl, extra, primes), primes)
     return out, {"C": C, "D01": D01, "D23": D23}
+
+
+def pcmm_precomp(cts, U, keys, primes_with_P, rescale_out: bool = False):
+    """Alg. 7 (CP-MM with precomputation) on a shared-a RLWE encryption,
+    followed by the key switches back to one secret (Thm th:pcmm-with-precomp
+    and the remark after it: switching before Rescale keeps more precision).
+
+    cts: [d2, 2, L, N] ciphertexts (a, b_j) that share one a-part; ciphertext
+         j encrypts column j of M under the secret s_j (column j of S), so
+         Toep(a) * S + B = Delta * M + E with B's columns the b_j.
+    U:   (d2, d3) integers, the plaintext known beforehand.
+    keys: d3 switching keys [L, 2, L+1, N]; key k switches
+         s'_k = sum_j U[j, k] s_j (column k of S * U) to the target secret.
+    Step 1 (Alg. 7): B' = B * U mod q, so that Toep(a) * (S * U) + B' =
+    Delta * M * U + E * U: ciphertext k, (a, column k of B'), encrypts column
+    k of M * U under s'_k.  Then each (a, b'_k) is key-switched with key k,
+    and Rescale by q_{L-1} is applied when rescale_out is set.
+    Returns (out [d3, 2, L or L-1, N], {"B1": B' as [d3, L, N]})."""
+    cts = _u64(cts)
+    d2, _, L, N = cts.shape
+    primes = list(primes_with_P[:L])
+    a = cts[0, 0]
+    if not all(np.array_equal(cts[j, 0], a) for j in range(d2)):
+        raise ValueError("the ciphertexts must share one a-part")
+    U = np.asarray(U)
+    d3 = U.shape[1]
+    Bt = np.ascontiguousarray(np.transpose(cts[:, 1], (1, 0, 2)))    # [L, d2, N]: row j = b_j
+    B1 = mod_pp_mm(np.ascontiguousarray(U.T), Bt, primes)           # row k = sum_j U[j,k] b_j
+    out = np.empty((d3, 2, L - 1 if rescale_out else L, N), dtype=np.uint64)
+    for k in range(d3):
+        ct = np.empty((2, L, N), dtype=np.uint64)
+        ct[0] = a
+        ct[1] = B1[:, k, :]
+        sw = keyswitch(ct, keys[k], primes_with_P)
+        out[k] = rescale(sw, primes) if rescale_out else sw
+    return out, {"B1": np.ascontiguousarray(np.transpose(B1, (1, 0, 2)))}

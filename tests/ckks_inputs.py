@@ -72,6 +72,31 @@ def encrypt_rows(oracle_mod, X, s, delta, seed, primes=PR):
     return cts, m, e
 
 
+def encrypt_shared_a(oracle_mod, M, secrets, delta, seed, primes=PR):
+    """Shared-a encryption of M (N x d2): column j as (a, b_j) under its own
+    secret secrets[j], one uniform a for every column.  Returns the ciphertexts
+    [d2, 2, L, N], the encoded message (d2 x N) and the errors (d2 x N)."""
+    N, d2 = M.shape
+    L = len(primes)
+    m = oracle_mod.ckks_encode(np.ascontiguousarray(M.T), delta)       # row j = column j
+    a = np.stack([synth.uniform_mod(seed, 30 + pl, (1, N), q) for pl, q in enumerate(primes)])
+    e = synth.rounded_gaussian(seed, 40, (d2, N))
+    cts = np.empty((d2, 2, L, N), dtype=np.uint64)
+    for j in range(d2):
+        b = oracle_mod.rlwe_encrypt_rows(a, secrets[j], m[j:j + 1], e[j:j + 1], primes)
+        cts[j, 0] = a[:, 0, :]
+        cts[j, 1] = b[:, 0, :]
+    return cts, m, e
+
+
+def precomp_keys(oracle_mod, secrets, U, s_new, N, seed, primes_with_P=PRP):
+    """Key k switches s'_k = sum_j U[j, k] s_j (column k of S * U) to s_new."""
+    S = np.stack([np.asarray(x, dtype=np.int64) for x in secrets])      # d2 x N
+    SU = (U.astype(np.int64).T @ S)                                      # d3 x N: row k = s'_k
+    return [switching_key(oracle_mod, SU[k], s_new, N, seed + k, primes_with_P)
+            for k in range(U.shape[1])], SU
+
+
 def to_batch(cts):
     """[n, 2, L, N] -> the library's part-major batch [2, L, n, N]."""
     return np.ascontiguousarray(np.transpose(cts, (1, 2, 0, 3)))
