@@ -174,6 +174,38 @@ int cc_mm_ex(modpp_ring ring, int64_t n, const uint64_t *ct1, const uint64_t *ct
              double *out_scale_mult, void *ws, size_t ws_bytes, void *stream);
 
 /*
+ * CP-MM with precomputation (Alg. 7, Thm th:pcmm-with-precomp), followed by
+ * the key switches back to one secret (before the optional Rescale, the
+ * order the remark after Thm th:pcmm-with-precomp recommends for precision).
+ *
+ * Input: a shared-a encryption of an N x d2 matrix M: d2 ciphertexts
+ * (a, b_j) with ONE common a-part, ciphertext j encrypting column j of M
+ * under its own secret s_j (column j of S): Toep(a) * S + B = Delta M + E.
+ * U (d2 x d3, int8) is the plaintext known beforehand; key k (prepared)
+ * switches s'_k = sum_j U[j][k] s_j (column k of S * U) to the target
+ * secret s -- the precomputation of Alg. 7.
+ *   1. B' = B * U mod q_j: ONE Mod-PP-MM per chain prime (Alg. 6 needs two);
+ *      (a, column k of B') encrypts column k of M * U under s'_k.
+ *   2. KeySwitch of (a, b'_k) with key k for every k < d3.  The a-part is
+ *      shared, so its digits and their forward transforms are computed once
+ *      for the whole batch.
+ *   3. with MODPP_PRECOMP_RESCALE: Rescale by q_{L-1}.
+ *   Ut    d3 x d2 int8, contiguous: row k is column k of U.
+ *   a     [L][N], the shared a-part.
+ *   B     [L][d2][N]: the b-parts, row j = b_j (the b-part planes of a batch).
+ *   keys  [d3][L][2][L+1][N], prepared (modpp_ring_prepare_keys).
+ *   out   [2][L][d3][N] (with Rescale: [2][L-1][d3][N]): ciphertext k
+ *         encrypts column k of M * U under s (at scale Delta * scale(U),
+ *         divided by q_{L-1} with Rescale).
+ * 1 <= d2 <= 2^20, 1 <= d3 < 2^31.  Workspace: pc_mm_precomp_workspace.
+ */
+#define MODPP_PRECOMP_RESCALE 1
+size_t pc_mm_precomp_workspace(modpp_ring ring, int64_t d2, int64_t d3, int flags);
+int pc_mm_precomp(modpp_ring ring, int64_t d2, int64_t d3, const int8_t *Ut, const uint64_t *a,
+                  const uint64_t *B, const uint64_t *keys, int flags, uint64_t *out, void *ws,
+                  size_t ws_bytes, void *stream);
+
+/*
  * Waits for `stream`, then reads and clears the ring's status word (a word
  * in the ring's table memory): MODPP_OK, or MODPP_ERR_RANGE when, in debug
  * mode (modpp_set_debug_checks), an entry point of this ring was given a

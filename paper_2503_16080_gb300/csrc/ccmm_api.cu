@@ -717,6 +717,103 @@ int cc_mm(modpp_ring r, const uint64_t *ct1, const uint64_t *ct2, const uint64_t
     return cc_mm_ex(r, r->N, ct1, ct2, aut_keys, relin_key, 0, out, nullptr, ws, ws_bytes, stream);
 }
 
+// ---------------------------------------------------------------- Alg. 7
+// CP-MM with precomputation on a shared-a encryption, then the key switches
+// back to one secret.  Workspace: the Mod-PP-MM workspace (status word
+// first), the shared digits D of a (L * (L+1) transforms), key-switch
+// products for a chunk of output ciphertexts, and, with the Rescale flag,
+// the unrescaled batch.
+struct PrecompLayout {
+    size_t mm = 0, dig = 0, u = 0, x = 0, total = 0;
+    int64_t chunk = 0;
+};
+PrecompLayout precomp_layout(const modpp_ring_s *r, int64_t d2, int64_t d3, int flags) {
+    PrecompLayout p{};
+    const int L = r->L, Lp = L + 1;
+    const int64_t N = r->N;
+    size_t off = 0;
+    p.mm = off;
+    off = align_up(off + modpp_mm_workspace(d3, d2, N, r->primes.data(), L, MODPP_PATH_F16));
+    p.dig = off;
+    off = align_up(off + sizeof(uint64_t) * L * Lp * N);
+    const int64_t per_ct = 2 * static_cast<int64_t>(Lp) * N;
+    p.chunk = std::max<int64_t>(1, std::min<int64_t>(d3, static_cast<int64_t>(ks_chunk_budget() / 8) / per_ct));
+    p.u = off;
+    off = align_up(off + sizeof(uint64_t) * p.chunk * per_ct);
+    p.x = off;
+    if (flags & MODPP_PRECOMP_RESCALE) off = align_up(off + sizeof(uint64_t) * batch_words(r, d3, L));
+    p.total = off;
+    return p;
+}
+
+size_t pc_mm_precomp_workspace(modpp_ring r, int64_t d2, int64_t d3, int flags) {
+    if (r == nullptr || d2 < 1 || d3 < 1 || d2 > (int64_t(1) << 20) || d3 >= (int64_t(1) << 31) ||
+        (flags & ~MODPP_PRECOMP_RESCALE) != 0 || ((flags & MODPP_PRECOMP_RESCALE) && r->L < 2))
+        return 0;
+    return precomp_layout(r, d2, d3, flags).total;
+}
+
+int pc_mm_precomp(modpp_ring r, int64_t d2, int64_t d3, const int8_t *Ut, const uint64_t *a,
+                  const uint64_t *B, const uint64_t *keys, int flags, uint64_t *out, void *ws,
+                  size_t ws_bytes, void *stream) {
+    if (r == nullptr || d2 < 1 || d3 < 1 || d2 > (int64_t(1) << 20) || d3 >= (int64_t(1) << 31) ||
+        (flags & ~MODPP_PRECOMP_RESCALE) != 0)
+        return MODPP_ERR_ARG;
+    const bool resc = (flags & MODPP_PRECOMP_RESCALE) != 0;
+    if (resc && r->L < 2) return MODPP_ERR_ARG;
+    if (Ut == nullptr || !a16(a) || !a16(B) || !a16(keys) || !a16(out)) return MODPP_ERR_ARG;
+    const PrecompLayout lay = precomp_layout(r, d2, d3, flags);
+    if (!ws_ok(ws, ws_bytes, lay.total)) return MODPP_ERR_WORKSPACE;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const int L = r->L, Lp = L + 1;
+    const int N = static_cast<int>(r->N);
+    char *base = static_cast<char *>(ws);
+    int rc = MODPP_OK;
+    if (debug_checks_on()) {  // a and B below their primes; the keys
+        rc = cuda_status(range_planes(a, L, 1, N, N, N, r->primes.data(), L, r->status, st));
+        if (rc == MODPP_OK)
+            rc = cuda_status(range_planes(B, L, 1, d2 * N, d2 * N, d2 * N, r->primes.data(), L,
+                                          r->status, st));
+        if (rc == MODPP_OK) rc = check_keys(r, keys, d3, st);
+        if (rc) return rc;
+    }
+    // Step 1 (Alg. 7): B' = B * U, i.e. row k of B'^T = sum_j U[j][k] b_j for
+    // every chain prime: one Mod-PP-MM of U^T (d3 x d2, int8) times the b-parts
+    // (d2 x N per prime), written as the b-parts of the output batch.
+    uint64_t *X = resc ? reinterpret_cast<uint64_t *>(base + lay.x) : out;
+    const int64_t plane = d3 * static_cast<int64_t>(N);
+    const size_t mm_bytes = modpp_mm_workspace(d3, d2, N, r->primes.data(), L, MODPP_PATH_F16);
+    rc = modpp_mm(d3, d2, N, Ut, MODPP_U_I8, d2, B, N, d2 * static_cast<int64_t>(N), X + L * plane,
+                  N, plane, r->primes.data(), L, MODPP_PATH_F16, base + lay.mm, mm_bytes, st);
+    if (rc) return rc;
+    // Key switches of (a, b'_k) with key k, k < d3: the digits of the shared
+    // a-part and their forward transforms once, then per chunk the key
+    // products, the inverse transforms and ModDown (in place on X).
+    uint64_t *D = reinterpret_cast<uint64_t *>(base + lay.dig);
+    uint64_t *Ubuf = reinterpret_cast<uint64_t *>(base + lay.u);
+    cudaError_t e;
+    if (ntt_fast_supported(N)) {
+        e = launch_ks_digits_ntt(a, 1, L, N, 0, 1, r->tab, D, st);
+    } else {
+        e = launch_ks_decompose(a, 1, L, N, 0, 1, r->tab, D, st);
+        if (e == cudaSuccess) e = launch_ntt(D, L * Lp, N, 1, Lp, r->tab, false, st);
+    }
+    if (e != cudaSuccess) return MODPP_ERR_CUDA;
+    for (int64_t c0 = 0; c0 < d3; c0 += lay.chunk) {
+        const int64_t m = std::min(lay.chunk, d3 - c0);
+        e = launch_ks_multacc(D, keys, nullptr, 1, L, N, c0, m, r->tab, Ubuf, st, /*d_shared=*/1);
+        if (e == cudaSuccess) e = launch_ntt(Ubuf, m * 2 * Lp, N, 1, Lp, r->tab, true, st);
+        if (e == cudaSuccess)
+            e = launch_ks_moddown(Ubuf, X, d3, L, N, c0, m, nullptr, 1, 0, r->tab, r->pinv,
+                                  r->pinv_s, X, d3, st);
+        if (e != cudaSuccess) return MODPP_ERR_CUDA;
+    }
+    if (resc)
+        return cuda_status(launch_rescale(X, out, L, d3 * static_cast<int64_t>(N), r->tab,
+                                          r->qlinv, r->qlinv_s, st));
+    return MODPP_OK;
+}
+
 int modpp_ring_status_read(modpp_ring r, void *stream) {
     if (r == nullptr) return MODPP_ERR_ARG;
     return modpp_status_read(r->status, stream);

@@ -55,10 +55,13 @@ cudaError_t launch_to_montgomery(uint64_t *polys, int64_t npolys, int N, int64_t
                                  int nplanes, const NttPlane *tab, cudaStream_t s);
 cudaError_t launch_ks_decompose(const uint64_t *ct, int64_t n, int L, int N, int64_t c0,
                                 int64_t nb, const NttPlane *tab, uint64_t *D, cudaStream_t s);
+// kid null: ciphertext c takes key c.  d_shared: one set of digits D[0] for
+// every ciphertext (a batch sharing one a-part).
 cudaError_t launch_ks_multacc(const uint64_t *D, const uint64_t *keys, const int *kid, int kper,
                               int L, int N, int64_t c0, int64_t nb, const NttPlane *tab,
-                              uint64_t *U, cudaStream_t s);
-// Writes ciphertext c0 + c of the chunk to plane stride n_out of `out`.
+                              uint64_t *U, cudaStream_t s, int d_shared = 0);
+// Writes ciphertext c0 + c of the chunk to plane stride n_out of `out`; kid
+// null: no ciphertext is copied unchanged.
 cudaError_t launch_ks_moddown(const uint64_t *U, const uint64_t *ct, int64_t n, int L, int N,
                               int64_t c0, int64_t nb, const int *kid, int kper, int b_zero,
                               const NttPlane *tab, const uint64_t *pinv, const uint64_t *pinv_s,

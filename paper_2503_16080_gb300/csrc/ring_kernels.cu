@@ -137,11 +137,13 @@ __global__ void ks_decompose_kernel(const uint64_t *__restrict__ ct, int64_t n, 
 
 // U[c][part][k] = sum_i D[c][i][k] * key[kid(c)][i][part][k] in the evaluation
 // domain (keys in Montgomery form, digits plain: the product is plain).
+// kid null: ciphertext c0 + c takes key c0 + c.  d_shared: every ciphertext
+// shares the digits D[0] (one a-part for the whole batch).
 // nb * (L+1) < 2^31 and N = 2^logN.
 __global__ void ks_multacc_kernel(const uint64_t *__restrict__ D, const uint64_t *__restrict__ keys,
                                   const int *__restrict__ kid, int kper, int L, int logN,
                                   int64_t c0, int64_t nb, const NttPlane *__restrict__ tab,
-                                  uint64_t *__restrict__ U) {
+                                  uint64_t *__restrict__ U, int d_shared) {
     // Two neighbouring coefficients per thread (16-byte accesses).
     const int Lp = L + 1;
     const int N = 1 << logN;
@@ -153,11 +155,12 @@ __global__ void ks_multacc_kernel(const uint64_t *__restrict__ D, const uint64_t
         const int r = static_cast<int>(x >> (logN - 1));
         const int k = r % Lp;
         const int c = r / Lp;
-        const int kc = kid[(c0 + c) % kper];
+        const int kc = kid ? kid[(c0 + c) % kper] : static_cast<int>(c0 + c);
         if (kc < 0) continue;
         const uint64_t q = tab[k].q, qinv = tab[k].qinv_neg;
         const uint64_t *key = keys + kc * key_stride + (static_cast<int64_t>(k) << logN) + m;
-        const uint64_t *d = D + ((static_cast<int64_t>(c) * L * Lp + k) << logN) + m;
+        const uint64_t *d =
+            D + ((static_cast<int64_t>(d_shared ? 0 : c) * L * Lp + k) << logN) + m;
         const int64_t dstep = static_cast<int64_t>(Lp) << logN;     // next digit i
         const int64_t kstep = static_cast<int64_t>(2 * Lp) << logN; // next key digit i
         const int64_t kpart = static_cast<int64_t>(Lp) << logN;     // part 1 of a key digit
@@ -208,7 +211,7 @@ __global__ void ks_moddown_kernel(const uint64_t *__restrict__ U, const uint64_t
          x += static_cast<int64_t>(gridDim.x) * blockDim.x) {
         const int m = (static_cast<int>(x) << 1) & (N - 1);
         const int64_t c = x >> (logN - 1);
-        const bool copy = kid[(c0 + c) % kper] < 0;
+        const bool copy = kid != nullptr && kid[(c0 + c) % kper] < 0;
         const int64_t ub = ((c * 2 + part) * Lp) << logN;
         ulonglong2 up = make_ulonglong2(0, 0);
         if (!copy) up = *reinterpret_cast<const ulonglong2 *>(U + ub + (static_cast<int64_t>(L) << logN) + m);
@@ -244,13 +247,13 @@ cudaError_t launch_ks_decompose(const uint64_t *ct, int64_t n, int L, int N, int
 }
 cudaError_t launch_ks_multacc(const uint64_t *D, const uint64_t *keys, const int *kid, int kper,
                               int L, int N, int64_t c0, int64_t nb, const NttPlane *tab,
-                              uint64_t *U, cudaStream_t s) {
+                              uint64_t *U, cudaStream_t s, int d_shared) {
     if (nb == 0) return cudaSuccess;
     const int logN = 31 - __builtin_clz(N);
     const int64_t total = nb * (L + 1) * N / 2;
     const int64_t bx = std::min<int64_t>((total + 255) / 256, 152 * 16);
     ks_multacc_kernel<<<static_cast<unsigned>(bx), 256, 0, s>>>(D, keys, kid, kper, L, logN, c0, nb,
-                                                                tab, U);
+                                                                tab, U, d_shared);
     return cudaGetLastError();
 }
 cudaError_t launch_ks_moddown(const uint64_t *U, const uint64_t *ct, int64_t n, int L, int N,

@@ -52,6 +52,9 @@ def _register():
     L.cc_mm_ex_workspace.argtypes = [P, I64, I]
     L.cc_mm_ex_workspace.restype = SZ
     L.cc_mm_ex.argtypes = [P, I64, P, P, P, P, I, P, P, P, SZ, P]
+    L.pc_mm_precomp_workspace.argtypes = [P, I64, I64, I]
+    L.pc_mm_precomp_workspace.restype = SZ
+    L.pc_mm_precomp.argtypes = [P, I64, I64, P, P, P, P, I, P, P, SZ, P]
     _registered = True
     return L
 
@@ -231,6 +234,36 @@ class Ring:
                               relin_key.data_ptr(), flags, out.data_ptr(), ctypes.byref(mult),
                               wp, wl, _stream_handle(stream)), "cc_mm_ex")
         return out, mult.value
+
+    def pc_mm_precomp(self, Ut: torch.Tensor, a: torch.Tensor, B: torch.Tensor,
+                      keys: torch.Tensor, rescale: bool = False, out=None, stream=None,
+                      workspace=None) -> torch.Tensor:
+        """Alg. 7 on a shared-a encryption, then the key switches back to one
+        secret: Ut (d3, d2) int8 = U^T; a (L, N) the shared a-part; B (L, d2, N)
+        the b-parts; keys (d3, L, 2, L+1, N) prepared, key k from column k of
+        S*U.  Returns the batch (2, L or L-1, d3, N)."""
+        if not (Ut.is_cuda and Ut.dtype == torch.int8 and Ut.dim() == 2 and Ut.is_contiguous()):
+            raise TypeError("Ut must be a contiguous 2-D int8 CUDA tensor")
+        d3, d2 = Ut.shape
+        for t, nm, shp in ((a, "a", (self.L, self.N)), (B, "B", (self.L, d2, self.N))):
+            if not (t.is_cuda and t.dtype == torch.uint64 and t.is_contiguous()):
+                raise TypeError(f"{nm} must be a contiguous uint64 CUDA tensor")
+            if tuple(t.shape) != shp:
+                raise ValueError(f"{nm} must have shape {shp}")
+        if self._keys(keys, "keys") != d3:
+            raise ValueError("keys must hold d3 keys")
+        flags = 1 if rescale else 0
+        Lo = self.L - 1 if rescale else self.L
+        if out is None:
+            out = torch.empty((2, Lo, d3, self.N), dtype=torch.uint64, device=B.device)
+        need = int(lib().pc_mm_precomp_workspace(self._h, d2, d3, flags))
+        if need == 0:
+            raise ModppError(-1, "pc_mm_precomp_workspace")
+        wp, wl = _workspace(need, B.device, workspace)
+        _check(lib().pc_mm_precomp(self._h, d2, d3, Ut.data_ptr(), a.data_ptr(), B.data_ptr(),
+                                   keys.data_ptr(), flags, out.data_ptr(), wp, wl,
+                                   _stream_handle(stream)), "pc_mm_precomp")
+        return out
 
     def status(self, stream=None) -> int:
         """Reads and clears the ring's status word (syncs the stream):
