@@ -761,6 +761,7 @@ def run_ours(args):
             torch.cuda.empty_cache()
             line["config1"] = measure_config1(pkg, dev, stream)
             line["strategy2"] = measure_strategy2(pkg, dev, stream, peaks)
+            line["precomp"] = [measure_precomp(pkg, dev, stream, d3) for d3 in (4096, 32)]
             line["pcmm16384"] = measure_pc_large(pkg, dev, stream, "pcmm16384", 5, 3, peaks)
             line["ccmm"] = measure_ccmm(pkg, dev, stream, 8192, 5, 3, peaks, e2e=True,
                                         cpu_leg=False)
@@ -907,6 +908,57 @@ def measure_strategy2(pkg, dev, stream, peaks: dict, steps: int = 5, warmup: int
     return res
 
 
+def measure_precomp(pkg, dev, stream, d3: int, steps: int = 5, warmup: int = 3):
+    """Alg. 7 (CP-MM with precomputation) with the key switches back to one
+    secret, against Alg. 6 (pc_mm, two Mod-PP-MMs) on the same shape: ring
+    degree N = d2 = 4096, d3 output columns, L = 3 primes of 50 bits and a
+    60-bit special prime.  Inputs uniform mod q (RLWE parts and keys are
+    indistinguishable from uniform; the kernels' work does not depend on the
+    values)."""
+    import torch
+    from paper_2503_16080_gb300 import synth
+    N = d2 = 4096
+    L = 3
+    primes = synth.ntt_primes(50, L)
+    prp = primes + synth.ntt_primes(60, 1)
+    ring = pkg.Ring(N, prp)
+    Ut = torch.from_numpy(synth.quantised_normal_int8(SEED, 1, (d3, d2))).to(dev)
+    a = torch.stack([synth.uniform_mod_torch(SEED, 50 + j, (N,), q, dev) for j, q in enumerate(primes)])
+    B = torch.stack([synth.uniform_mod_torch(SEED, 60 + j, (d2, N), q, dev)
+                     for j, q in enumerate(primes)])
+    keys = torch.empty((d3, L, 2, L + 1, N), dtype=torch.uint64, device=dev)
+    kv = keys.view(torch.int64)
+    for k, q in enumerate(prp):
+        kv[:, :, :, k, :] = synth.uniform_mod_torch(SEED, 70 + k, (d3, L, 2, N), q, dev).view(torch.int64)
+    ring.prepare_keys(keys)
+    out = torch.empty((2, L, d3, N), dtype=torch.uint64, device=dev)
+    ws = torch.empty(int(pkg.lib().pc_mm_precomp_workspace(ring._h, d2, d3, 0)), dtype=torch.uint8,
+                     device=dev)
+    ms7, kern = _timed(lambda: ring.pc_mm_precomp(Ut, a, B, keys, out=out, workspace=ws),
+                       steps, warmup, stream, pkg)
+    gemm7 = kern["gemm"][0] / steps
+    # Alg. 6 on the same shape: both parts (a-parts A and b-parts B) times U^T.
+    A = torch.stack([synth.uniform_mod_torch(SEED, 80 + j, (d2, N), q, dev)
+                     for j, q in enumerate(primes)])
+    Ao = torch.empty((L, d3, N), dtype=torch.uint64, device=dev)
+    Bo = torch.empty_like(Ao)
+    ms6, kern6 = _timed(lambda: pkg.pc_mm(Ut, A, B, primes, out=(Ao, Bo)), steps, warmup,
+                        stream, pkg)
+    res = {"workload": f"Alg. 7 with key switches vs Alg. 6: N = d2 = 4096, d3 = {d3}, L = 3 "
+                       "(50-bit) + 60-bit special prime, U int8",
+           "d2": d2, "d3": d3, "N": N,
+           "alg7_ms": ms7, "alg7_gemm_ms": gemm7, "alg7_keyswitch_ms": ms7 - gemm7
+           - kern["split"][0] / steps - kern["u16"][0] / steps,
+           "alg6_pc_mm_ms": ms6, "alg6_gemm_ms": kern6["gemm"][0] / steps,
+           "mod_ops": 2.0 * d3 * d2 * N * L,
+           "alg7_exact_tops_of_product": 2.0 * d3 * d2 * N * L / (gemm7 * 1e-3) / 1e12,
+           "key_bytes": keys.numel() * 8}
+    ring.close()
+    del keys, A, B, out, ws, Ao, Bo
+    torch.cuda.empty_cache()
+    return res
+
+
 def measure_config1(pkg, dev, stream, calls: int = 200):
     """The 256^3 Mod-PP-MM with one 50-bit prime and int32 U (values in
     [-128, 127]): the latency-bound case.  Reports the device time per call
@@ -983,6 +1035,10 @@ def run_secondary(args):
     elif args.workload == "strategy2":
         line.update({"workload": "strategy2", **measure_strategy2(pkg, dev, stream, peaks,
                                                                   args.steps, args.warmup)})
+    elif args.workload == "precomp":
+        line.update({"workload": "precomp",
+                     "rows": [measure_precomp(pkg, dev, stream, d3, args.steps, args.warmup)
+                              for d3 in (4096, 256, 32)]})
     elif args.workload == "hostlink":
         # Pinned host <-> device copy rates (the bound of the end-to-end
         # numbers): one direction at a time, and both at once on separate
@@ -1342,7 +1398,7 @@ def main():
                     help="digit width of the f16 path (8, 9, 10; 0 = library default)")
     ap.add_argument("--workload", default="pcmm4096",
                     choices=["pcmm4096", "pcmm16384", "pcmv", "grouped", "ccmm8192",
-                             "umma_sweep", "hostlink", "strategy2"],
+                             "umma_sweep", "hostlink", "strategy2", "precomp"],
                     help="pcmm4096 (default, the benchmark line); the others are recorded "
                          "beside it")
     ap.add_argument("--n", type=int, default=4096,
