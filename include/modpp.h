@@ -116,6 +116,21 @@ int modpp_set_digit_bits(int bits);
 int modpp_get_digit_bits(void);
 
 /*
+ * Tensor-core kernel form of the f16 path for single-problem products
+ * (modpp_mm, pc_mm, pc_mv; process-wide tuning setting, host only):
+ *   0  one CTA per 128-row tile (tcgen05.mma.cta_group::1, M = 128);
+ *   1  CTA pairs: clusters of two CTAs compute 256-row tiles with
+ *      tcgen05.mma.cta_group::2 (M = 256), each CTA staging its own 128 rows
+ *      of U and half of the digit tile, for outputs of at least 256 rows and
+ *      more than 64 columns (others keep the one-CTA form).
+ * The results are identical.  The environment variable MODPP_GEMM_PAIR sets
+ * the initial value.  Workspace queries made before a change do not apply
+ * after it.  Returns MODPP_OK or MODPP_ERR_ARG.
+ */
+int modpp_set_gemm_pair(int on);
+int modpp_get_gemm_pair(void);
+
+/*
  * Planning query (host only, no GPU needed).  For a product with inner
  * dimension k modulo q on `path`, reports how the operands are split:
  *   digits      number of residue digits (F16: ceil(bits(q)/b) balanced

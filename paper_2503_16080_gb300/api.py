@@ -95,6 +95,8 @@ def lib() -> ctypes.CDLL:
         L.modpp_mm_trunc_workspace.restype = SZ
         L.modpp_mm_trunc.argtypes = [I64, I64, I64, P, I, I64, P, I64, P, I64, U64, I, I, P, SZ,
                                      P]
+        L.modpp_set_gemm_pair.argtypes = [I]
+        L.modpp_get_gemm_pair.restype = I
         L.modpp_set_debug_checks.argtypes = [I]
         L.modpp_get_debug_checks.restype = I
         L.modpp_profile_enable.argtypes = [I]
@@ -220,6 +222,16 @@ def wide_plan_info(k: int, primes: Sequence[int]) -> int:
     _check(lib().modpp_wide_plan_info(int(k), pr.ctypes.data, len(pr), ctypes.byref(out)),
            "modpp_wide_plan_info")
     return out.value
+
+
+def set_gemm_pair(on: bool) -> None:
+    """Kernel form of the f16 path for single-problem products: CTA pairs
+    (tcgen05 cta_group::2, 256-row tiles) or one CTA per 128-row tile."""
+    _check(lib().modpp_set_gemm_pair(1 if on else 0), "modpp_set_gemm_pair")
+
+
+def get_gemm_pair() -> bool:
+    return bool(lib().modpp_get_gemm_pair())
 
 
 def set_debug_checks(on: bool) -> None:

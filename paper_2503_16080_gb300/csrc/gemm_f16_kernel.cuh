@@ -30,6 +30,18 @@
 // Two TMEM accumulators (columns 0.. and 256..) alternate between chunks, so
 // the epilogue drains one while the tensor cores fill the other.
 //
+// CTAS = 2: a cluster of two CTAs computes tiles of 256 rows with
+// tcgen05.mma.cta_group::2 (M = 256): each CTA loads its own 128 rows of U
+// and half of the digit tile (N / 2 rows) into its shared memory, the even
+// CTA (the leader) issues the MMAs, and each CTA's tensor memory receives
+// the accumulators of its 128 rows.  Half of B per CTA means a stage of
+// (128 + N/2) x 64 halves instead of (128 + N) x 64, so the ring holds more
+// stages in flight.  TMA completions of both CTAs are counted on the
+// leader's `full` barrier; MMA completions are multicast to both CTAs'
+// `empty`, `tfull` and `drain` barriers; both CTAs' epilogue warps arrive on
+// the leader's `tempty`.  Every wait stays bounded, and both CTAs meet at a
+// cluster barrier before the tensor memory is released and the CTAs exit.
+//
 // GROUPED = false: one problem; all planes share U, the sizes and the digit
 // count L, and the tensor maps are kernel parameters.  GROUPED = true: the
 // tiles of many problems are concatenated; each tile looks up its plane's
@@ -43,11 +55,11 @@
 
 namespace modpp {
 
-template <int L, int NC>
+template <int L, int NC, int CTAS = 1>
 struct GemmCfg {
     static constexpr int BN = L * NC;  // largest UMMA N (all L digits)
     static constexpr int A_BYTES = kBM * kBK * 2;
-    static constexpr int B_BYTES = BN * kBK * 2;
+    static constexpr int B_BYTES = BN / CTAS * kBK * 2;  // a CTA pair holds half of B each
     static constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
     static constexpr int SMEM_LIMIT = 232448;  // opt-in dynamic shared memory per CTA
     static constexpr int RESERVED = 1024 + 256;
@@ -56,7 +68,7 @@ struct GemmCfg {
     static constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + RESERVED;
     static constexpr uint32_t TMEM_COLS = 512;
     static constexpr uint32_t ACC_STRIDE = 256;
-    static_assert(BN % 16 == 0 && BN <= 256, "UMMA N for M = 128");
+    static_assert(BN % (16 * CTAS) == 0 && BN <= 256, "UMMA N for M = 128 (one CTA) or 256 (pair)");
     static_assert(STAGES >= 2, "pipeline depth");
 };
 
@@ -147,13 +159,15 @@ __device__ __forceinline__ TileJob tile_job(int tile, const CUtensorMap *tmU,
 // rns_wide.cu).  Each plane then has its own U rows (p.u_per_plane).  With
 // the plane's `accumulate` set, the residues already stored are added (the
 // inner dimension in chunks).
-template <int L, int DB, int NC, bool GROUPED, int MODE = 0>
+template <int L, int DB, int NC, bool GROUPED, int MODE = 0, int CTAS = 1>
 __global__ void __launch_bounds__(kThreads, 1)
     gemm_f16_kernel(const __grid_constant__ CUtensorMap tmU_param,
                     const __grid_constant__ CUtensorMap tmD_param,
                     const __grid_constant__ GemmParams p) {
-    using Cfg = GemmCfg<L, NC>;
+    static_assert(CTAS == 1 || (CTAS == 2 && MODE == 0 && !GROUPED), "pairs: single-problem digits");
+    using Cfg = GemmCfg<L, NC, CTAS>;
     constexpr int STAGES = Cfg::STAGES;
+    constexpr int kRowsPerTile = kBM * CTAS;
     extern __shared__ uint8_t smem_raw[];
     const uint32_t raw = smem_u32(smem_raw);
     uint8_t *smem = smem_raw + (((raw + 1023u) & ~1023u) - raw);
@@ -168,6 +182,11 @@ __global__ void __launch_bounds__(kThreads, 1)
 
     const int warp = threadIdx.x >> 5;
     const int lane = threadIdx.x & 31;
+    // Pair: rank 0 leads; tiles are distributed over clusters.
+    const uint32_t rank = CTAS == 2 ? cluster_ctarank() : 0u;
+    const bool leader = rank == 0;
+    const int tile0 = CTAS == 2 ? static_cast<int>(cluster_id_x()) : static_cast<int>(blockIdx.x);
+    const int tstep = CTAS == 2 ? static_cast<int>(cluster_count_x()) : static_cast<int>(gridDim.x);
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < STAGES; ++s) {
@@ -176,7 +195,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
         for (int b = 0; b < 2; ++b) {
             mbar_init(&tfull[b], 1);
-            mbar_init(&tempty[b], kEpiWarps);
+            mbar_init(&tempty[b], kEpiWarps * CTAS);
         }
         mbar_init(drain, 1);
         *abort_flag = 0;
@@ -188,11 +207,19 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
     }
     if (warp == 1) {
-        tmem_alloc(tmem_slot, Cfg::TMEM_COLS);
-        tmem_relinquish();
+        if constexpr (CTAS == 2) {
+            tmem_alloc_pair(tmem_slot, Cfg::TMEM_COLS);
+            tmem_relinquish_pair();
+        } else {
+            tmem_alloc(tmem_slot, Cfg::TMEM_COLS);
+            tmem_relinquish();
+        }
     }
     tc_fence_before();
     __syncthreads();
+    // Pair: both CTAs' barriers initialised and tensor memory allocated
+    // before either CTA signals the other.
+    if constexpr (CTAS == 2) cluster_sync_all();
     tc_fence_after();
     const uint32_t tmem_base = *tmem_slot;
     constexpr int kChunkKB = MODE == 1 ? (1 << 20) / kBK : chunk_k(DB) / kBK;
@@ -203,7 +230,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             uint32_t it = 0;
             bool ok = true;
             const CUtensorMap *last_map = nullptr;
-            for (int tile = blockIdx.x; ok && tile < p.num_tiles; tile += gridDim.x) {
+            for (int tile = tile0; ok && tile < p.num_tiles; tile += tstep) {
                 const TileJob j = tile_job<L, NC, GROUPED>(tile, &tmU_param, &tmD_param, p);
                 if constexpr (GROUPED) {
                     if (j.tmD != last_map) {
@@ -213,8 +240,10 @@ __global__ void __launch_bounds__(kThreads, 1)
                         last_map = j.tmD;
                     }
                 }
-                const int ay = j.uy + j.mb * kBM;
-                const uint32_t bytes = Cfg::A_BYTES + static_cast<uint32_t>(j.Lp * NC * kBK * 2);
+                const int ay = j.uy + j.mb * kRowsPerTile + static_cast<int>(rank) * kBM;
+                const int by = j.by + static_cast<int>(rank) * (j.Lp * NC / CTAS);
+                const uint32_t bytes =
+                    Cfg::A_BYTES + static_cast<uint32_t>(j.Lp * NC / CTAS * kBK * 2);
                 for (int kb = 0; kb < j.kb_total; ++kb, ++it) {
                     const int s = static_cast<int>(it % STAGES);
                     const uint32_t ph = (it / STAGES) & 1u;
@@ -223,23 +252,36 @@ __global__ void __launch_bounds__(kThreads, 1)
                         break;
                     }
                     uint8_t *sa = smem + s * Cfg::STAGE_BYTES;
-                    mbar_arrive_expect_tx(&full[s], bytes);
-                    tma_load_2d(sa, j.tmU, &full[s], kb * kBK, ay);
-                    tma_load_2d(sa + Cfg::A_BYTES, j.tmD, &full[s], kb * kBK, j.by);
+                    if constexpr (CTAS == 2) {
+                        // Both CTAs' loads complete on the leader's full[s],
+                        // which expects the bytes of the pair.
+                        if (leader) mbar_arrive_expect_tx(&full[s], bytes * CTAS);
+                        const uint32_t fb = mapa_shared(&full[s], 0);
+                        tma_load_2d_pair(sa, j.tmU, fb, kb * kBK, ay);
+                        tma_load_2d_pair(sa + Cfg::A_BYTES, j.tmD, fb, kb * kBK, by);
+                    } else {
+                        mbar_arrive_expect_tx(&full[s], bytes);
+                        tma_load_2d(sa, j.tmU, &full[s], kb * kBK, ay);
+                        tma_load_2d(sa + Cfg::A_BYTES, j.tmD, &full[s], kb * kBK, by);
+                    }
                 }
             }
-            // Every issued load must land before the CTA may exit.
-            for (uint32_t q = it > static_cast<uint32_t>(STAGES) ? it - STAGES : 0u; q < it; ++q)
-                mbar_wait_bounded(&full[q % STAGES], (q / STAGES) & 1u, drain_abort, p.timeout_ns);
+            // Every issued load must land before the CTA may exit.  A pair's
+            // loads are counted on the leader's barriers: the leader drains
+            // them, and the final cluster barrier holds the peer until then.
+            if (leader)
+                for (uint32_t q = it > static_cast<uint32_t>(STAGES) ? it - STAGES : 0u; q < it; ++q)
+                    mbar_wait_bounded(&full[q % STAGES], (q / STAGES) & 1u, drain_abort,
+                                      p.timeout_ns);
         }
     } else if (warp == 1) {
         // ------------------------------------------------ MMA issuer
-        if (lane == 0) {
+        if (lane == 0 && leader) {
             uint32_t it = 0, g = 0;
             bool ok = true;
-            for (int tile = blockIdx.x; ok && tile < p.num_tiles; tile += gridDim.x) {
+            for (int tile = tile0; ok && tile < p.num_tiles; tile += tstep) {
                 const TileJob j = tile_job<L, NC, GROUPED>(tile, &tmU_param, &tmD_param, p);
-                const uint32_t idesc = idesc_f16_f32(kBM, j.Lp * NC);
+                const uint32_t idesc = idesc_f16_f32(kRowsPerTile, j.Lp * NC);
                 const int n_chunks = (j.kb_total + kChunkKB - 1) / kChunkKB;
                 for (int ch = 0; ok && ch < n_chunks; ++ch, ++g) {
                     const uint32_t buf = g & 1u, use = g >> 1;
@@ -264,17 +306,34 @@ __global__ void __launch_bounds__(kThreads, 1)
                         const uint32_t b_addr = a_addr + Cfg::A_BYTES;
 #pragma unroll
                         for (int ks = 0; ks < kBK / 16; ++ks) {
-                            umma_f16_ss(dtm, sdesc_kmajor<kRowBytes>(a_addr + ks * 32),
-                                        sdesc_kmajor<kRowBytes>(b_addr + ks * 32), idesc,
-                                        (kb > kb0 || ks > 0) ? 1u : 0u);
+                            const uint64_t ad = sdesc_kmajor<kRowBytes>(a_addr + ks * 32);
+                            const uint64_t bd = sdesc_kmajor<kRowBytes>(b_addr + ks * 32);
+                            const uint32_t acc = (kb > kb0 || ks > 0) ? 1u : 0u;
+                            if constexpr (CTAS == 2)
+                                umma_f16_ss_pair(dtm, ad, bd, idesc, acc);
+                            else
+                                umma_f16_ss(dtm, ad, bd, idesc, acc);
                         }
-                        umma_commit(&empty[s]);
+                        if constexpr (CTAS == 2)
+                            umma_commit_pair_mc(&empty[s], 0x3);
+                        else
+                            umma_commit(&empty[s]);
                     }
                     if (!ok) break;
-                    umma_commit(&tfull[buf]);
+                    if constexpr (CTAS == 2)
+                        umma_commit_pair_mc(&tfull[buf], 0x3);
+                    else
+                        umma_commit(&tfull[buf]);
                 }
             }
-            umma_commit(drain);
+            if constexpr (CTAS == 2)
+                umma_commit_pair_mc(drain, 0x3);
+            else
+                umma_commit(drain);
+            mbar_wait_bounded(drain, 0, drain_abort, p.timeout_ns);
+        } else if (CTAS == 2 && lane == 0) {
+            // The peer issues no MMAs: it waits until the leader's last ones
+            // (which write its tensor memory and read its shared memory) are done.
             mbar_wait_bounded(drain, 0, drain_abort, p.timeout_ns);
         }
     } else {
@@ -358,7 +417,18 @@ __global__ void __launch_bounds__(kThreads, 1)
             }
         } else {
         constexpr int G = (L + 2) / 3;       // digit groups: digits 3g, 3g+1, 3g+2
-        constexpr int CW = (L >= 7 || NCH % 8 != 0) ? 4 : 8;  // columns per TMEM load group
+        // The TMEM round trips of a chunk's drain (load, then one wait) bound
+        // it, not the conversions.  Two ways to batch the loads:
+        //   by columns: all L digits of CW columns per wait, NCH / CW waits;
+        //   by digits:  DPB digits of all NCH columns per wait, ceil(L / DPB)
+        //               waits (DPB * NCH <= 64 registers; used with at most
+        //               two digit groups, where the accumulators leave room).
+        constexpr int CW = (L >= 7 || NCH % 8 != 0) ? 4 : 8;
+        constexpr int DPB = NCH * 3 <= 64 ? 3 : (NCH * 2 <= 64 ? 2 : 1);
+        // (load registers DPB * NCH plus int64 accumulators 2 * G * NCH kept
+        // within 140 of the 168 a thread has: no spills)
+        constexpr bool kByDigits =
+            G <= 2 && (L + DPB - 1) / DPB < NCH / CW && DPB * NCH + 2 * G * NCH <= 140;
         constexpr int kDigitWeight[3] = {1, 1 << DB, 1 << (2 * DB)};
         const int ew = warp - 2;
         const int quarter = warp & 3;  // TMEM lane quarter this warp may access
@@ -370,7 +440,11 @@ __global__ void __launch_bounds__(kThreads, 1)
         int64_t grp[G][NCH];
         uint32_t g = 0;
         bool ok = true;
-        for (int tile = blockIdx.x; ok && tile < p.num_tiles; tile += gridDim.x) {
+        // Pair: both CTAs' epilogue warps release a drained accumulator on
+        // the leader's tempty (which the leader's MMA thread waits on).
+        const uint32_t tempty_leader0 = CTAS == 2 ? mapa_shared(&tempty[0], 0) : 0u;
+        const uint32_t tempty_leader1 = CTAS == 2 ? mapa_shared(&tempty[1], 0) : 0u;
+        for (int tile = tile0; ok && tile < p.num_tiles; tile += tstep) {
             const TileJob j = tile_job<L, NC, GROUPED>(tile, &tmU_param, &tmD_param, p);
             const int Lp = GROUPED ? j.Lp : L;
             const int n_chunks = (j.kb_total + kChunkKB - 1) / kChunkKB;
@@ -387,32 +461,57 @@ __global__ void __launch_bounds__(kThreads, 1)
                 }
                 tc_fence_after();
                 const uint32_t base = tmem_base + lane_off + buf * Cfg::ACC_STRIDE + half * NCH;
-                // All digits of a group of CW columns are loaded before one
-                // wait, so a chunk costs NCH / CW TMEM round trips, not L.
+                if constexpr (kByDigits) {
 #pragma unroll
-                for (int c0 = 0; c0 < NCH; c0 += CW) {
-                    uint32_t r[L][CW];
+                    for (int l0 = 0; l0 < L; l0 += DPB) {
+                        uint32_t r[DPB][NCH];
 #pragma unroll
-                    for (int l = 0; l < L; ++l)
-                        if (l < Lp) tmem_ld_group<CW>(base + l * NC + c0, r[l]);
-                    tmem_wait_ld();
+                        for (int j = 0; j < DPB; ++j)
+                            if (l0 + j < L && l0 + j < Lp)
+                                tmem_ld_cols<NCH>(base + (l0 + j) * NC, r[j]);
+                        tmem_wait_ld();
 #pragma unroll
-                    for (int l = 0; l < L; ++l) {
-                        if (l >= Lp) continue;
+                        for (int j = 0; j < DPB; ++j) {
+                            const int l = l0 + j;
+                            if (l >= L || l >= Lp) continue;
 #pragma unroll
-                        for (int c = 0; c < CW; ++c)
-                            grp[l / 3][c0 + c] = mad_wide_s32(
-                                __float2int_rn(__uint_as_float(r[l][c])), kDigitWeight[l % 3],
-                                grp[l / 3][c0 + c]);
+                            for (int c = 0; c < NCH; ++c)
+                                grp[l / 3][c] =
+                                    mad_wide_s32(__float2int_rn(__uint_as_float(r[j][c])),
+                                                 kDigitWeight[l % 3], grp[l / 3][c]);
+                        }
+                    }
+                } else {
+#pragma unroll
+                    for (int c0 = 0; c0 < NCH; c0 += CW) {
+                        uint32_t r[L][CW];
+#pragma unroll
+                        for (int l = 0; l < L; ++l)
+                            if (l < Lp) tmem_ld_group<CW>(base + l * NC + c0, r[l]);
+                        tmem_wait_ld();
+#pragma unroll
+                        for (int l = 0; l < L; ++l) {
+                            if (l >= Lp) continue;
+#pragma unroll
+                            for (int c = 0; c < CW; ++c)
+                                grp[l / 3][c0 + c] = mad_wide_s32(
+                                    __float2int_rn(__uint_as_float(r[l][c])), kDigitWeight[l % 3],
+                                    grp[l / 3][c0 + c]);
+                        }
                     }
                 }
                 tc_fence_before();
                 __syncwarp();
-                if (lane == 0) mbar_arrive(&tempty[buf]);
+                if (lane == 0) {
+                    if constexpr (CTAS == 2)
+                        mbar_arrive_cluster(buf ? tempty_leader1 : tempty_leader0);
+                    else
+                        mbar_arrive(&tempty[buf]);
+                }
             }
             if (!ok) break;
             // value = grp0 + 2^(3b) grp1 + 2^(6b) grp2  (mod q)
-            const int row = j.mb * kBM + quarter * 32 + lane;
+            const int row = j.mb * kRowsPerTile + static_cast<int>(rank) * kBM + quarter * 32 + lane;
             const int col0 = j.nb * NC + half * NCH;
             if (row < j.d) {
                 const PlaneConst &pc = *j.pc;
@@ -465,9 +564,15 @@ __global__ void __launch_bounds__(kThreads, 1)
 
     tc_fence_before();
     __syncthreads();
+    // Pair: neither CTA releases its tensor memory or exits while the other
+    // may still signal its barriers or have the leader's MMAs use its memory.
+    if constexpr (CTAS == 2) cluster_sync_all();
     if (warp == 1) {
         tc_fence_after();
-        tmem_dealloc(tmem_base, Cfg::TMEM_COLS);
+        if constexpr (CTAS == 2)
+            tmem_dealloc_pair(tmem_base, Cfg::TMEM_COLS);
+        else
+            tmem_dealloc(tmem_base, Cfg::TMEM_COLS);
     }
     if (threadIdx.x == 0 && (*abort_flag || *drain_abort)) atomicExch(p.status, -7);
 }

@@ -70,19 +70,32 @@ struct PlaneIn {
 struct F16Layout {
     int b = 0;
     int L = 0;
+    bool pair = false;  // CTA-pair GEMM
     int nc = 0;  // tile columns
     int64_t kp = 0, n_blocks = 0, rows = 0;
     size_t off_u16 = 0, off_d = 0, total = 0;
 };
 
-F16Layout f16_layout(int64_t d, int64_t k, int64_t n, const uint64_t *qs, int planes) {
+// CTA-pair GEMM (tiles of 256 rows, cta_group::2) for single-problem
+// products: chosen process-wide (modpp_set_gemm_pair, MODPP_GEMM_PAIR), for
+// outputs of at least 256 rows and more than 64 columns (thin outputs keep
+// the one-CTA kernel's plane-fastest order).
+std::atomic<int> g_gemm_pair{[] {
+    const char *v = std::getenv("MODPP_GEMM_PAIR");
+    return (v != nullptr && v[0] != '\0') ? (v[0] != '0' ? 1 : 0) : 0;
+}()};
+bool use_pair(int64_t d, int64_t n) { return g_gemm_pair.load() != 0 && d >= 2 * kBM && n > 64; }
+
+F16Layout f16_layout(int64_t d, int64_t k, int64_t n, const uint64_t *qs, int planes,
+                     bool pair_ok = false) {
     F16Layout lay;
     lay.b = current_digit_bits();
     for (int i = 0; i < planes; ++i) {
         const int l = f16_digit_count(qs[i], lay.b);
         if (l > lay.L) lay.L = l;
     }
-    const int nc = tile_cols_for(lay.L, n);
+    lay.pair = pair_ok && use_pair(d, n);
+    const int nc = lay.pair ? pair_tile_cols(lay.L) : tile_cols_for(lay.L, n);
     lay.nc = nc;
     lay.kp = (k + 7) / 8 * 8;
     lay.n_blocks = (n + nc - 1) / nc;
@@ -258,7 +271,7 @@ int run_f16(int64_t d, int64_t k, int64_t n, const void *U, int ukind, int64_t l
             const PlaneIn *pl, int planes, void *ws, size_t ws_bytes, cudaStream_t st) {
     uint64_t qs[kMaxPlanes];
     for (int i = 0; i < planes; ++i) qs[i] = pl[i].q;
-    const F16Layout lay = f16_layout(d, k, n, qs, planes);
+    const F16Layout lay = f16_layout(d, k, n, qs, planes, /*pair_ok=*/true);
     if (ws_bytes < lay.total) return MODPP_ERR_WORKSPACE;
     if (lay.rows >= (int64_t(1) << 31)) return MODPP_ERR_UNSUPPORTED;
     uint8_t *w = static_cast<uint8_t *>(ws);
@@ -295,15 +308,18 @@ int run_f16(int64_t d, int64_t k, int64_t n, const void *U, int ukind, int64_t l
     CUtensorMap tmU, tmD;
     if (!make_map_f16(&tmU, U16, static_cast<uint64_t>(lay.kp), static_cast<uint64_t>(d), kBK, kBM))
         return MODPP_ERR_CUDA;
+    // One box is one CTA's share of a tile's digit rows: all L * nc of them,
+    // or half of them for a CTA pair (each CTA stages N / 2 rows of B).
     if (!make_map_f16(&tmD, D, static_cast<uint64_t>(lay.kp), static_cast<uint64_t>(lay.rows), kBK,
-                      static_cast<uint32_t>(lay.L * lay.nc)))
+                      static_cast<uint32_t>(lay.pair ? lay.L * lay.nc / 2 : lay.L * lay.nc)))
         return MODPP_ERR_CUDA;
 
     GemmParams gp{};
     gp.d = static_cast<int>(d);
     gp.n = static_cast<int>(n);
     gp.k = static_cast<int>(k);
-    gp.m_blocks = static_cast<int>((d + kBM - 1) / kBM);
+    const int rows_per_tile = lay.pair ? 2 * kBM : kBM;
+    gp.m_blocks = static_cast<int>((d + rows_per_tile - 1) / rows_per_tile);
     gp.n_blocks = static_cast<int>(lay.n_blocks);
     gp.planes = planes;
     gp.kb_total = static_cast<int>((k + kBK - 1) / kBK);
@@ -312,11 +328,13 @@ int run_f16(int64_t d, int64_t k, int64_t n, const void *U, int ukind, int64_t l
     gp.num_tiles = static_cast<int>(tiles);
     // U larger than a slice of L2 and few column blocks: run the planes of a
     // row block together so each U block is read from HBM once.
-    gp.plane_fastest = (static_cast<int64_t>(d) * lay.kp * 2 > (int64_t(48) << 20) &&
+    gp.plane_fastest = (!lay.pair && static_cast<int64_t>(d) * lay.kp * 2 > (int64_t(48) << 20) &&
                         lay.n_blocks <= 2 && planes > 1)
                            ? 1
                            : 0;
-    gp.band_m = band_rows(gp.m_blocks, lay.kp);
+    // Bands of row blocks whose U rows fit the L2 budget (a pair block is
+    // twice as tall).
+    gp.band_m = band_rows(gp.m_blocks, lay.pair ? 2 * lay.kp : lay.kp);
     gp.status = status;
     gp.timeout_ns = wait_limit_ns();
     for (int i = 0; i < planes; ++i)
@@ -324,7 +342,8 @@ int run_f16(int64_t d, int64_t k, int64_t n, const void *U, int ukind, int64_t l
     const int sms = device_sms();
     if (sms <= 0) return MODPP_ERR_CUDA;
     ev = timer_begin(MODPP_KERNEL_GEMM, st);
-    rc = cuda_status(launch_gemm_f16(tmU, tmD, gp, lay.L, lay.b, sms, st, lay.nc));
+    rc = cuda_status(lay.pair ? launch_gemm_f16_pair(tmU, tmD, gp, lay.L, lay.b, st)
+                              : launch_gemm_f16(tmU, tmD, gp, lay.L, lay.b, sms, st, lay.nc));
     timer_end(ev, st);
     return rc;
 }
@@ -803,7 +822,7 @@ int run_fp64_trunc(int64_t d, int64_t k, int64_t n, const void *U, int ukind, in
 }
 
 size_t layout_bytes(int64_t d, int64_t k, int64_t n, const uint64_t *qs, int planes, int path) {
-    if (path == MODPP_PATH_F16) return f16_layout(d, k, n, qs, planes).total;
+    if (path == MODPP_PATH_F16) return f16_layout(d, k, n, qs, planes, /*pair_ok=*/true).total;
     return fp64_layout(d, k, n, qs, planes, path == MODPP_PATH_FP64_TIGHT).total;
 }
 
@@ -905,6 +924,14 @@ int modpp_set_digit_bits(int bits) {
 }
 
 int modpp_get_digit_bits(void) { return current_digit_bits(); }
+
+int modpp_set_gemm_pair(int on) {
+    if (on != 0 && on != 1) return MODPP_ERR_ARG;
+    g_gemm_pair.store(on);
+    return MODPP_OK;
+}
+
+int modpp_get_gemm_pair(void) { return g_gemm_pair.load(); }
 
 int modpp_set_wide_path(int mode) {
     if (mode < 0 || mode > 2) return MODPP_ERR_ARG;

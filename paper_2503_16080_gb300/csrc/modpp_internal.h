@@ -33,6 +33,12 @@ __host__ __device__ constexpr int tile_cols_for(int L, long long n) {
 __host__ __device__ constexpr int grouped_tile_cols(int L) {
     return L <= 3 ? 64 : (L <= 5 ? 48 : 32);
 }
+// Tile columns of the CTA-pair GEMM (gemm_f16_kernel with CTAS = 2): the
+// pair's UMMA N = L * cols must be a multiple of 32 (each CTA holds N / 2
+// rows of B in whole swizzle atoms) and at most 256.
+__host__ __device__ constexpr int pair_tile_cols(int L) {
+    return L <= 3 ? 64 : (L == 4 ? 48 : 32);
+}
 constexpr int kMaxTileCols = 64;
 constexpr int kBK = 64;              // f16 elements per K block: one 128-byte row
 constexpr int kRowBytes = kBK * 2;   // swizzle span of the operand tiles (64 or 128)
@@ -202,6 +208,12 @@ cudaError_t launch_split_digits(const SplitParams &p, cudaStream_t s);
 cudaError_t launch_gemm_f16(const CUtensorMap &tmU, const CUtensorMap &tmD, const GemmParams &p,
                             int digits, int digit_bits, int num_sms, cudaStream_t s,
                             int nc = 0);  // 0: tile_cols(digits)
+// The CTA-pair GEMM (tiles of 256 rows x pair_tile_cols(digits) columns;
+// p.m_blocks counts 256-row blocks), launched as clusters of two CTAs, as
+// many clusters as can be resident at once.
+cudaError_t launch_gemm_f16_pair(const CUtensorMap &tmU, const CUtensorMap &tmD,
+                                 const GemmParams &p, int digits, int digit_bits, cudaStream_t s);
+
 
 // FP64-limb (Strategy 1) helpers.
 struct Fp64SplitParams {

@@ -158,6 +158,23 @@ def test_static_entry_point_argument_errors_before_any_cuda_call(api):
     assert call(d=8192, k=8192, n=8192) == -3     # needs more than the 64 MiB array
 
 
+def test_gemm_pair_setting(api):
+    assert api.get_gemm_pair() in (False, True)
+    old = api.get_gemm_pair()
+    try:
+        api.set_gemm_pair(True)
+        assert api.get_gemm_pair()
+        q = synth.ntt_primes(50, 3)
+        # the pair tiles (32 columns at 6 digits) change the workspace layout
+        assert api.workspace_bytes(4096, 4096, 4096, q) == 256 + 4096 * 4096 * 2 + \
+            3 * 128 * 6 * 32 * 4096 * 2
+        api.set_gemm_pair(False)
+        assert not api.get_gemm_pair()
+    finally:
+        api.set_gemm_pair(old)
+    assert api.lib().modpp_set_gemm_pair(2) == -1
+
+
 def test_debug_checks_setting(api):
     assert not api.get_debug_checks()
     api.set_debug_checks(True)
