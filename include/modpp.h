@@ -282,6 +282,28 @@ int pc_mv(int64_t d, int64_t kct, int64_t nvec, const int8_t *U, const uint64_t 
           int path, void *ws, size_t ws_bytes, void *stream);
 
 /*
+ * Prepared plaintext.  The f16 path first converts U into an f16 matrix of d
+ * rows of kp = k rounded up to 8 halves (zero padded), which the tensor cores
+ * read.  For a plaintext reused over many products (the setting of Sec. 5.2,
+ * where U is known beforehand) that conversion can be done once:
+ *   modpp_u16_bytes(d, k)     bytes of the prepared matrix (0 for bad sizes);
+ *   modpp_u_to_f16(...)       writes it to U16 (device, 16-byte aligned),
+ *                             from U (int8, or int32 in [-128, 127]; d x k,
+ *                             leading dimension ldu);
+ *   pc_mm_u16(...)            PC-MM / PC-Mv exactly as pc_mm / pc_mv on
+ *                             MODPP_PATH_F16, with the prepared U16 (d x kct)
+ *                             instead of U; workspace from pc_mm_workspace.
+ * Results are identical to pc_mm / pc_mv with the same U.  Debug range checks
+ * do not inspect a prepared U16.
+ */
+size_t modpp_u16_bytes(int64_t d, int64_t k);
+int modpp_u_to_f16(int64_t d, int64_t k, const void *U, int ukind, int64_t ldu, void *U16,
+                   void *stream);
+int pc_mm_u16(int64_t d, int64_t kct, int64_t N, const void *U16, const uint64_t *A,
+              const uint64_t *B, uint64_t *Aout, uint64_t *Bout, const uint64_t *primes_host, int P,
+              void *ws, size_t ws_bytes, void *stream);
+
+/*
  * Grouped Mod-PP-MM: many independent products of uneven sizes, each with its
  * own prime list, computed by a few launches for the whole group: one U
  * conversion, then one digit split and one persistent tensor-core GEMM per

@@ -17,7 +17,7 @@ _API_NAMES = (
     "KERNEL_SPLIT", "KERNEL_U16", "set_digit_bits", "get_digit_bits", "GroupedPlan",
     "modpp_mm_grouped", "modpp_mm_wide", "set_wide_path", "get_wide_path", "wide_plan_info",
     "selftest_bounded_wait", "set_debug_checks", "get_debug_checks", "modpp_mm_trunc",
-    "set_gemm_pair", "get_gemm_pair",
+    "set_gemm_pair", "get_gemm_pair", "PreparedU",
 )
 _RING_NAMES = ("Ring",)
 

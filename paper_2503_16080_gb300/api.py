@@ -72,6 +72,10 @@ def lib() -> ctypes.CDLL:
         L.pc_mm_workspace.restype = SZ
         L.pc_mm.argtypes = [I64, I64, I64, P, P, P, P, P, P, I, I, P, SZ, P]
         L.pc_mv.argtypes = [I64, I64, I64, P, P, P, P, P, P, I, I, P, SZ, P]
+        L.modpp_u16_bytes.argtypes = [I64, I64]
+        L.modpp_u16_bytes.restype = SZ
+        L.modpp_u_to_f16.argtypes = [I64, I64, P, I, I64, P, P]
+        L.pc_mm_u16.argtypes = [I64, I64, I64, P, P, P, P, P, P, I, P, SZ, P]
         L.modpp_status_read.argtypes = [P, P]
         L.modpp_selftest_bounded_wait.argtypes = [P, ctypes.c_uint64, P]
         L.modpp_mm_wide_workspace.argtypes = [I64, I64, I64, P, I]
@@ -371,10 +375,39 @@ def modpp_mm_trunc(U: torch.Tensor, B: torch.Tensor, q: int, *, path="f16", drop
     return out
 
 
+class PreparedU:
+    """A plaintext U (d x k) converted once into the f16 layout the tensor
+    cores read (modpp_u_to_f16), for reuse over many pc_mm / pc_mv calls."""
+
+    def __init__(self, U: torch.Tensor, stream=None):
+        if not U.is_cuda or U.dtype not in (torch.int8, torch.int32) or U.dim() != 2:
+            raise TypeError("U must be a 2-D CUDA int8 or int32 tensor")
+        if U.numel() and U.stride(1) != 1:
+            raise ValueError("U needs unit stride along k")
+        self.shape = tuple(U.shape)
+        d, k = self.shape
+        nbytes = int(lib().modpp_u16_bytes(d, k))
+        self.data = torch.empty(max(nbytes, 16), dtype=torch.uint8, device=U.device)
+        _check(lib().modpp_u_to_f16(d, k, U.data_ptr(), 0 if U.dtype == torch.int8 else 1,
+                                    U.stride(0) if U.numel() else k, self.data.data_ptr(),
+                                    _stream_handle(stream)), "modpp_u_to_f16")
+
+    @property
+    def is_cuda(self):
+        return True
+
+    def data_ptr(self):
+        return self.data.data_ptr()
+
+
 def _pc(fn_name: str, U, A, B, primes, path, out, stream, workspace):
     _check_residues(A, "A")
     _check_residues(B, "B")
-    if not U.is_cuda or U.dtype != torch.int8 or U.dim() != 2 or not U.is_contiguous():
+    prepared = isinstance(U, PreparedU)
+    if prepared:
+        if _path(path) != Path.F16:
+            raise ValueError("a prepared U serves the f16 path only")
+    elif not U.is_cuda or U.dtype != torch.int8 or U.dim() != 2 or not U.is_contiguous():
         raise TypeError("U must be a contiguous 2-D CUDA int8 tensor")
     if not (A.is_contiguous() and B.is_contiguous()) or A.shape != B.shape or A.dim() != 3:
         raise ValueError("A and B must be contiguous (P, kct, N) tensors of equal shape")
@@ -395,6 +428,12 @@ def _pc(fn_name: str, U, A, B, primes, path, out, stream, workspace):
     if need == 0:
         raise ModppError(-1, "pc_mm_workspace")
     ws_ptr, ws_len = _workspace(need, A.device, workspace)
+    if prepared:
+        rc = lib().pc_mm_u16(d, kct, N, U.data_ptr(), A.data_ptr(), B.data_ptr(),
+                             Aout.data_ptr(), Bout.data_ptr(), pr.ctypes.data, P, ws_ptr, ws_len,
+                             _stream_handle(stream))
+        _check(rc, "pc_mm_u16")
+        return Aout, Bout
     rc = getattr(lib(), fn_name)(d, kct, N, U.data_ptr(), A.data_ptr(), B.data_ptr(),
                                  Aout.data_ptr(), Bout.data_ptr(), pr.ctypes.data, P, p, ws_ptr,
                                  ws_len, _stream_handle(stream))

@@ -581,9 +581,10 @@ template <int L, int DB, int NC, bool GROUPED, int MODE = 0>
 cudaError_t launch_gemm_kernel(const CUtensorMap &tmU, const CUtensorMap &tmD, const GemmParams &p,
                                int num_sms, cudaStream_t s) {
     using Cfg = GemmCfg<L, NC>;
-    cudaError_t e = cudaFuncSetAttribute(gemm_f16_kernel<L, DB, NC, GROUPED, MODE>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         Cfg::SMEM_BYTES);
+    static std::atomic<unsigned long long> smem_set{0};
+    cudaError_t e = set_smem_limit_once(
+        reinterpret_cast<const void *>(gemm_f16_kernel<L, DB, NC, GROUPED, MODE>), Cfg::SMEM_BYTES,
+        smem_set);
     if (e != cudaSuccess) return e;
     const int grid = p.num_tiles < num_sms ? p.num_tiles : num_sms;
     gemm_f16_kernel<L, DB, NC, GROUPED, MODE><<<grid, kThreads, Cfg::SMEM_BYTES, s>>>(tmU, tmD, p);

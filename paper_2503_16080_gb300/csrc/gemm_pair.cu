@@ -12,8 +12,9 @@ cudaError_t launch_pair(const CUtensorMap &tmU, const CUtensorMap &tmD, const Ge
     constexpr int NC = pair_tile_cols(L);
     using Cfg = GemmCfg<L, NC, 2>;
     auto kern = gemm_f16_kernel<L, DB, NC, false, 0, 2>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         Cfg::SMEM_BYTES);
+    static std::atomic<unsigned long long> smem_set{0};
+    cudaError_t e =
+        set_smem_limit_once(reinterpret_cast<const void *>(kern), Cfg::SMEM_BYTES, smem_set);
     if (e != cudaSuccess) return e;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeClusterDimension;

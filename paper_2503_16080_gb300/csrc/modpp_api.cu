@@ -27,6 +27,8 @@ constexpr size_t kHeaderBytes = 256;        // status word + reserve
 constexpr size_t kCublasWsBytes = 32u << 20;  // cuBLAS scratch inside the workspace
 constexpr int64_t kMaxK = int64_t(1) << 20;
 constexpr int kMaxDevices = 64;
+// Internal U kind: U is a prepared f16 plaintext (modpp_u_to_f16).
+constexpr int kUPrepared = 16;
 
 size_t align_up(size_t x) { return (x + kAlign - 1) & ~(kAlign - 1); }
 
@@ -280,13 +282,21 @@ int run_f16(int64_t d, int64_t k, int64_t n, const void *U, int ukind, int64_t l
     if (d == 0 || n == 0) return MODPP_OK;
     if (k == 0) return zero_outputs(d, n, pl, planes, st);
 
-    __half *U16 = reinterpret_cast<__half *>(w + lay.off_u16);
+    // A prepared plaintext (kUPrepared: U is already the f16 layout, d rows
+    // of kp halves) is read in place; otherwise U is converted into the
+    // workspace.
+    __half *U16 = ukind == kUPrepared ? static_cast<__half *>(const_cast<void *>(U))
+                                      : reinterpret_cast<__half *>(w + lay.off_u16);
     __half *D = reinterpret_cast<__half *>(w + lay.off_d);
-    EventPair *ev = timer_begin(MODPP_KERNEL_U16, st);
-    int rc = cuda_status(launch_u_to_f16(U, ukind, ldu, static_cast<int>(d), static_cast<int>(k),
+    EventPair *ev = nullptr;
+    int rc = MODPP_OK;
+    if (ukind != kUPrepared) {
+        ev = timer_begin(MODPP_KERNEL_U16, st);
+        rc = cuda_status(launch_u_to_f16(U, ukind, ldu, static_cast<int>(d), static_cast<int>(k),
                                          static_cast<int>(lay.kp), U16, st));
-    timer_end(ev, st);
-    if (rc) return rc;
+        timer_end(ev, st);
+        if (rc) return rc;
+    }
 
     SplitParams sp{};
     sp.k = static_cast<int>(k);
@@ -836,9 +846,9 @@ int dispatch(int64_t d, int64_t k, int64_t n, const void *U, int ukind, int64_t 
                     path == MODPP_PATH_FP64_TIGHT);
 }
 
-int pc_common(int64_t d, int64_t kct, int64_t N, const int8_t *U, const uint64_t *A,
+int pc_common(int64_t d, int64_t kct, int64_t N, const void *U, const uint64_t *A,
               const uint64_t *B, uint64_t *Aout, uint64_t *Bout, const uint64_t *primes, int P,
-              int path, void *ws, size_t ws_bytes, void *stream) {
+              int path, void *ws, size_t ws_bytes, void *stream, int ukind = MODPP_U_I8) {
     int rc = check_sizes(d, kct, N);
     if (rc) return rc;
     rc = check_primes(primes, P, kMaxPlanes / 2);
@@ -854,7 +864,7 @@ int pc_common(int64_t d, int64_t kct, int64_t N, const int8_t *U, const uint64_t
         pl[P + j] = PlaneIn{B + static_cast<int64_t>(j) * kct * N, N, primes[j],
                             Bout + static_cast<int64_t>(j) * d * N, N};
     }
-    rc = dispatch(d, kct, N, U, MODPP_U_I8, kct, pl, 2 * P, path, ws, ws_bytes, stream);
+    rc = dispatch(d, kct, N, U, ukind, kct, pl, 2 * P, path, ws, ws_bytes, stream);
     if (rc) return rc;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     rc = debug_check_inputs(d, kct, N, U, MODPP_U_I8, kct, A, N, kct * N, primes, P, ws, st);
@@ -1009,6 +1019,34 @@ int pc_mm(int64_t d, int64_t kct, int64_t N, const int8_t *U, const uint64_t *A,
           const uint64_t *B, uint64_t *Aout, uint64_t *Bout, const uint64_t *primes_host, int P,
           int path, void *ws, size_t ws_bytes, void *stream) {
     return pc_common(d, kct, N, U, A, B, Aout, Bout, primes_host, P, path, ws, ws_bytes, stream);
+}
+
+size_t modpp_u16_bytes(int64_t d, int64_t k) {
+    if (d < 0 || k < 0 || d >= (int64_t(1) << 31) || k > kMaxK) return 0;
+    return align_up(static_cast<size_t>(d) * static_cast<size_t>((k + 7) / 8 * 8) * 2);
+}
+
+int modpp_u_to_f16(int64_t d, int64_t k, const void *U, int ukind, int64_t ldu, void *U16,
+                   void *stream) {
+    if (d < 0 || k < 0 || d >= (int64_t(1) << 31) || k > kMaxK || ldu < k) return MODPP_ERR_ARG;
+    if (ukind != MODPP_U_I8 && ukind != MODPP_U_I32) return MODPP_ERR_ARG;
+    if (d == 0 || k == 0) return MODPP_OK;
+    if (U == nullptr || U16 == nullptr || (reinterpret_cast<uintptr_t>(U16) & 15u) != 0)
+        return MODPP_ERR_ARG;
+    return cuda_status(launch_u_to_f16(U, ukind, ldu, static_cast<int>(d), static_cast<int>(k),
+                                       static_cast<int>((k + 7) / 8 * 8),
+                                       static_cast<__half *>(U16),
+                                       static_cast<cudaStream_t>(stream)));
+}
+
+int pc_mm_u16(int64_t d, int64_t kct, int64_t N, const void *U16, const uint64_t *A,
+              const uint64_t *B, uint64_t *Aout, uint64_t *Bout, const uint64_t *primes_host, int P,
+              void *ws, size_t ws_bytes, void *stream) {
+    if (d > 0 && kct > 0 && N > 0 &&
+        (U16 == nullptr || (reinterpret_cast<uintptr_t>(U16) & 15u) != 0))
+        return MODPP_ERR_ARG;
+    return pc_common(d, kct, N, U16, A, B, Aout, Bout, primes_host, P, MODPP_PATH_F16, ws,
+                     ws_bytes, stream, kUPrepared);
 }
 
 int pc_mv(int64_t d, int64_t kct, int64_t nvec, const int8_t *U, const uint64_t *A,

@@ -5,6 +5,7 @@
 #include <cuda.h>
 #include <cuda_runtime.h>
 #include <cuda_fp16.h>
+#include <atomic>
 #include <cstddef>
 #include <cstdint>
 
@@ -194,6 +195,22 @@ inline int band_rows(int m_blocks, int64_t kp) {
     int64_t b = kBandBytes / (per_block > 0 ? per_block : 1);
     if (b < 1) b = 1;
     return b >= m_blocks ? m_blocks : static_cast<int>(b);
+}
+
+// Raises a kernel's dynamic shared-memory limit to `bytes` once per device
+// (the setting stays with the kernel on that device), so repeated launches
+// skip the driver call.  `done` holds one bit per device (devices >= 64 set
+// it every time).
+inline cudaError_t set_smem_limit_once(const void *kernel, int bytes,
+                                       std::atomic<unsigned long long> &done) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    const unsigned long long bit = dev >= 0 && dev < 64 ? (1ull << dev) : 0ull;
+    if (bit != 0 && (done.load(std::memory_order_acquire) & bit) != 0) return cudaSuccess;
+    e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e == cudaSuccess && bit != 0) done.fetch_or(bit, std::memory_order_acq_rel);
+    return e;
 }
 
 // ------------------------------------------------------------ launchers
