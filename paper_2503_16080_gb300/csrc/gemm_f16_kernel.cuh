@@ -279,6 +279,12 @@ __global__ void __launch_bounds__(kThreads, 1)
         if (lane == 0 && leader) {
             uint32_t it = 0, g = 0;
             bool ok = true;
+            // Descriptors of stage 0's operand tiles; stage s adds
+            // s * STAGE_BYTES and sub-block ks adds 32 bytes (the start address
+            // field holds the address >> 4; shared addresses stay below 2^18, so
+            // the additions never carry out of the field).
+            const uint64_t adesc0 = sdesc_kmajor<kRowBytes>(smem_u32(smem));
+            const uint64_t bdesc0 = sdesc_kmajor<kRowBytes>(smem_u32(smem) + Cfg::A_BYTES);
             for (int tile = tile0; ok && tile < p.num_tiles; tile += tstep) {
                 const TileJob j = tile_job<L, NC, GROUPED>(tile, &tmU_param, &tmD_param, p);
                 const uint32_t idesc = idesc_f16_f32(kRowsPerTile, j.Lp * NC);
@@ -302,12 +308,11 @@ __global__ void __launch_bounds__(kThreads, 1)
                             break;
                         }
                         tc_fence_after();
-                        const uint32_t a_addr = smem_u32(smem + s * Cfg::STAGE_BYTES);
-                        const uint32_t b_addr = a_addr + Cfg::A_BYTES;
+                        const uint64_t soff = static_cast<uint64_t>(s) * (Cfg::STAGE_BYTES >> 4);
 #pragma unroll
                         for (int ks = 0; ks < kBK / 16; ++ks) {
-                            const uint64_t ad = sdesc_kmajor<kRowBytes>(a_addr + ks * 32);
-                            const uint64_t bd = sdesc_kmajor<kRowBytes>(b_addr + ks * 32);
+                            const uint64_t ad = adesc0 + soff + static_cast<uint64_t>(ks * 2);
+                            const uint64_t bd = bdesc0 + soff + static_cast<uint64_t>(ks * 2);
                             const uint32_t acc = (kb > kb0 || ks > 0) ? 1u : 0u;
                             if constexpr (CTAS == 2)
                                 umma_f16_ss_pair(dtm, ad, bd, idesc, acc);
