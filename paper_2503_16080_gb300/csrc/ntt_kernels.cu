@@ -180,9 +180,8 @@ __device__ __forceinline__ void ntt_pass(uint64_t *sa, const uint64_t *gin, uint
 
 // Stages of pass pi when logN stages run in `passes` passes: as even as
 // possible, the longer passes first (13 stages in 4 passes: 4, 3, 3, 3).
-__device__ __forceinline__ int pass_stages(int logN, int passes, int pi) {
-    const int base = logN / passes, extra = logN % passes;
-    return base + (pi < extra ? 1 : 0);
+__host__ __device__ constexpr int pass_stages(int logN, int passes, int pi) {
+    return logN / passes + (pi < logN % passes ? 1 : 0);
 }
 
 // E coefficients per thread (N / E threads), passes of up to log2(E) stages.
@@ -192,7 +191,29 @@ struct NttShape {
     static constexpr int kMaxThreads = E == 8 ? 1024 : 512;
 };
 
-template <int E, bool FWD>
+// The passes of one transform with the degree fixed at compile time
+// (N = 2^LOGN): each pass's stage count, distance and first/last role are
+// constants, so the index arithmetic of ntt_pass folds away.  Same passes
+// and arithmetic as ntt_run.
+template <int E, bool FWD, bool MAC, int LOGN, int PI = 0, int DONE = 0>
+__device__ __forceinline__ void ntt_run_c(uint64_t *sa, const uint64_t *gin, uint64_t *gout,
+                                          bool reduce_in, const PlaneRegs &pr, bool from_smem,
+                                          const MacSink *mk) {
+    constexpr int SM = NttShape<E>::kLogE;
+    constexpr int PASSES = (LOGN + SM - 1) / SM;
+    constexpr int S = pass_stages(LOGN, PASSES, PI);
+    constexpr bool LAST = DONE + S == LOGN;
+    constexpr int LU = FWD ? LOGN - DONE - S : DONE;
+    ntt_pass<E, S, FWD, MAC>(sa, gin, gout, reduce_in, 1 << LOGN, LOGN, LU,
+                             PI == 0 && !from_smem, LAST, pr, mk);
+    if constexpr (!LAST)
+        ntt_run_c<E, FWD, MAC, LOGN, PI + 1, DONE + S>(sa, gin, gout, reduce_in, pr, from_smem,
+                                                       mk);
+}
+
+// LOGN > 0: the degree is 2^LOGN, known at compile time (ntt_run_c); 0: a.N
+// at run time.
+template <int E, bool FWD, int LOGN = 0>
 __global__ void __launch_bounds__(NttShape<E>::kMaxThreads, 1) ntt_e_kernel(NttFastArgs a) {
     constexpr int SM = NttShape<E>::kLogE;
     extern __shared__ uint64_t sa[];
@@ -221,6 +242,10 @@ __global__ void __launch_bounds__(NttShape<E>::kMaxThreads, 1) ntt_e_kernel(NttF
     pr.tw = FWD ? tp.fwd2 : tp.inv2;
     const bool reduce_in = a.ks_ct != nullptr;
     uint64_t *gout = a.polys + p * N;
+    if constexpr (LOGN > 0) {
+        ntt_run_c<E, FWD, false, LOGN>(sa, gin, gout, reduce_in, pr, false, nullptr);
+        return;
+    }
     const int logN = a.logN;
     const int passes = (logN + SM - 1) / SM;
     int done = 0;
@@ -294,7 +319,7 @@ struct KsFusedArgs {
 // transform of (a_i mod q_k), multiplied in its last pass by key i (both
 // parts) and summed into two accumulators; then both inverse transforms,
 // written to U.  Shared memory: three padded polynomials (N <= 8192).
-template <int E>
+template <int E, int LOGN = 0>
 __global__ void __launch_bounds__(NttShape<E>::kMaxThreads, 1) ks_fused_kernel(KsFusedArgs a) {
     extern __shared__ uint64_t smem[];
     const int N = a.N;
@@ -321,7 +346,10 @@ __global__ void __launch_bounds__(NttShape<E>::kMaxThreads, 1) ks_fused_kernel(K
         MacSink mk{acc0, acc1, key + (static_cast<int64_t>(i * 2 + 0) * Lp + k) * N,
                    key + (static_cast<int64_t>(i * 2 + 1) * Lp + k) * N, tp.qinv_neg, i == 0};
 
-        ntt_run<E, true, true>(sa, gin, nullptr, true, N, a.logN, fw, false, &mk);
+        if constexpr (LOGN > 0)
+            ntt_run_c<E, true, true, LOGN>(sa, gin, nullptr, true, fw, false, &mk);
+        else
+            ntt_run<E, true, true>(sa, gin, nullptr, true, N, a.logN, fw, false, &mk);
         __syncthreads();  // sa is rewritten by the next digit; acc read by the inverse
     }
     uint64_t *u0 = a.U + ((c * 2 + 0) * Lp + k) * N;
@@ -344,16 +372,35 @@ int ntt_e_for(int N) {
     return e;
 }
 
-template <int E, bool FWD>
-cudaError_t launch_e(const NttFastArgs &a, int64_t npolys, cudaStream_t s) {
+template <int E, bool FWD, int LOGN>
+cudaError_t launch_e_kernel(const NttFastArgs &a, int64_t npolys, cudaStream_t s) {
     const int threads = a.N / E;
     const size_t smem = static_cast<size_t>(a.N + a.N / 32) * sizeof(uint64_t);
-    cudaError_t e = cudaFuncSetAttribute(ntt_e_kernel<E, FWD>,
+    cudaError_t e = cudaFuncSetAttribute(ntt_e_kernel<E, FWD, LOGN>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          static_cast<int>(smem));
     if (e != cudaSuccess) return e;
-    ntt_e_kernel<E, FWD><<<static_cast<unsigned>(npolys), threads, smem, s>>>(a);
+    ntt_e_kernel<E, FWD, LOGN><<<static_cast<unsigned>(npolys), threads, smem, s>>>(a);
     return cudaGetLastError();
+}
+
+// The degree as a compile-time constant for the default shapes (8
+// coefficients per thread up to 2^13, 32 at 2^14); the run-time kernel
+// otherwise.
+template <int E, bool FWD>
+cudaError_t launch_e(const NttFastArgs &a, int64_t npolys, cudaStream_t s) {
+    if constexpr (E == 8) {
+        switch (a.logN) {
+            case 10: return launch_e_kernel<8, FWD, 10>(a, npolys, s);
+            case 11: return launch_e_kernel<8, FWD, 11>(a, npolys, s);
+            case 12: return launch_e_kernel<8, FWD, 12>(a, npolys, s);
+            case 13: return launch_e_kernel<8, FWD, 13>(a, npolys, s);
+            default: break;
+        }
+    }
+    if constexpr (E == 32)
+        if (a.logN == 14) return launch_e_kernel<32, FWD, 14>(a, npolys, s);
+    return launch_e_kernel<E, FWD, 0>(a, npolys, s);
 }
 
 template <bool FWD>
@@ -389,12 +436,21 @@ cudaError_t launch_ks_fused(const uint64_t *ct, int64_t n, int L, int N, int64_t
     a.kper = kper;
     a.U = U;
     const size_t smem = 3 * static_cast<size_t>(N + N / 32) * sizeof(uint64_t);
-    cudaError_t e = cudaFuncSetAttribute(ks_fused_kernel<kKsE>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         static_cast<int>(smem));
-    if (e != cudaSuccess) return e;
-    ks_fused_kernel<kKsE><<<static_cast<unsigned>(nb * (L + 1)), N / kKsE, smem, s>>>(a);
-    return cudaGetLastError();
+    const dim3 grid(static_cast<unsigned>(nb * (L + 1)));
+    auto go = [&](auto kernel) {
+        cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             static_cast<int>(smem));
+        if (e != cudaSuccess) return e;
+        kernel<<<grid, N / kKsE, smem, s>>>(a);
+        return cudaGetLastError();
+    };
+    switch (a.logN) {  // the degree as a compile-time constant (1024 <= N <= 8192)
+        case 10: return go(ks_fused_kernel<kKsE, 10>);
+        case 11: return go(ks_fused_kernel<kKsE, 11>);
+        case 12: return go(ks_fused_kernel<kKsE, 12>);
+        case 13: return go(ks_fused_kernel<kKsE, 13>);
+        default: return go(ks_fused_kernel<kKsE, 0>);
+    }
 }
 
 bool ntt_fast_supported(int N) { return N >= 1024 && N <= 16384 && (N & (N - 1)) == 0; }

@@ -47,7 +47,8 @@ def setup(oracle_mod, ring_mod, N, seed=1):
     return _cache[N]
 
 
-@pytest.mark.parametrize("N,n", [(16, 1), (16, 5), (64, 7), (1024, 3), (2048, 2), (8192, 2)])
+@pytest.mark.parametrize("N,n", [(16, 1), (16, 5), (64, 7), (1024, 3), (2048, 2), (4096, 1), (8192, 2),
+                                 (16384, 1)])
 def test_keyswitch_bit_exact(oracle_mod, lib_ready, N, n):
     L = len(C.PR)
     s_old, s_new = synth.ternary(N, 1, N), synth.ternary(N, 2, N)
