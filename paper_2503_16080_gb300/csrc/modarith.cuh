@@ -41,7 +41,8 @@ __device__ __forceinline__ uint64_t add_mod(uint64_t a, uint64_t b, uint64_t q) 
     return s >= q ? s - q : s;
 }
 
-// Montgomery product a * b * 2^-64 mod q for a < q, b < q, q odd < 2^62;
+// Montgomery product a * b * 2^-64 mod q for any 64-bit a and b < q, q odd
+// < 2^62 (a * b + t * q < 2^65 q, so one subtraction reaches [0, q));
 // qinv = -q^-1 mod 2^64.
 __device__ __forceinline__ uint64_t mont_mul(uint64_t a, uint64_t b, uint64_t q, uint64_t qinv) {
     const uint64_t lo = a * b;

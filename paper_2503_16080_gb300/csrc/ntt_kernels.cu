@@ -34,6 +34,18 @@ __device__ __forceinline__ uint64_t shoup_lazy(uint64_t a, uint64_t w, uint64_t 
     return a * w - __umul64hi(a, ws) * q;
 }
 
+// a * w mod q up to three multiples of q, [0, 4q), for any 64-bit a: Shoup's
+// quotient from three of the four 32 x 32-bit partial products of a * ws.
+// The low product and the low halves of the two middle ones are each below
+// 2^64 after scaling, so the quotient falls short of floor(a * ws / 2^64) by
+// at most 2, and the remainder of the exact quotient is below 2q.
+__device__ __forceinline__ uint64_t shoup_lazy3(uint64_t a, uint64_t w, uint64_t ws, uint64_t q) {
+    const uint32_t a0 = static_cast<uint32_t>(a), a1 = static_cast<uint32_t>(a >> 32);
+    const uint32_t s0 = static_cast<uint32_t>(ws), s1 = static_cast<uint32_t>(ws >> 32);
+    const uint64_t qh = static_cast<uint64_t>(a1) * s1 + __umulhi(a1, s0) + __umulhi(a0, s1);
+    return a * w - qh * q;
+}
+
 struct NttFastArgs {
     uint64_t *polys;
     int N, logN;
@@ -50,7 +62,7 @@ struct NttFastArgs {
 
 // Constants of the polynomial's prime, held in registers.
 struct PlaneRegs {
-    uint64_t q, q2, mu, ninv, ninv_s;
+    uint64_t q, q2, q4, mu, ninv, ninv_s;
     const ulonglong2 *tw;  // (twiddle, Shoup quotient) pairs: fwd2 (forward) or inv2 (inverse)
 };
 
@@ -81,7 +93,42 @@ struct MacSink {
     bool assign;    // first digit: the accumulators take the products
 };
 
-template <int E, int S, bool FWD, bool MAC = false>
+// Value ranges.  GROW = false: Harvey's lazy butterflies with Shoup
+// products in [0, 2q); every value stays in [0, 4q) (forward) or [0, 2q)
+// (inverse) between stages, for q < 2^62.  GROW = true drops the per-stage
+// conditional subtractions and lets the bound grow instead, for the primes
+// where 64-bit words have room, with the three-product Shoup quotient
+// (products in [0, 4q)):
+//   forward: the sum and the difference (taken against 4q) each add less
+//            than 4q per stage, so after m stages every value is below
+//            B0 + 4mq, B0 the input bound: q, or the largest chain prime
+//            when the key-switch digits are transformed without reduction;
+//   inverse: before stage m (m stages done) values are below 2^(m+1) q
+//            (q for m = 0): the sum doubles the bound, the product stays
+//            below 4q, and the difference is taken against that bound.
+// Shoup's products accept any 64-bit multiplicand, and the Montgomery
+// product of the key sink any 64-bit a times b < q, so only the plain
+// forward output needs a full reduction (Barrett).
+__host__ __device__ constexpr bool ntt_grow_ok_fwd(uint64_t q, uint64_t in_max, int logN) {
+    // B0 + 4 * logN * q < 2^57 + 64 * 2^57 < 2^64 for logN <= 16
+    return logN <= 16 && q < (1ull << 57) && in_max < (1ull << 57);
+}
+__host__ __device__ constexpr bool ntt_grow_ok_inv(uint64_t q, int logN) {
+    // the last stage's sum is below 2^(logN + 1) q
+    return logN <= 62 && q <= (~0ull >> (logN + 1));
+}
+// Difference offset of inverse stage m under GROW: the bound of its inputs.
+__device__ __forceinline__ uint64_t grow_inv_bound(uint64_t q, int m) {
+    return m == 0 ? q : q << (m + 1);
+}
+
+// Shared-memory index of coefficient j0 + k * 2^lu of a group: groups start
+// at (blk << (lu + S)) + r with r < 2^lu, so adding k * 2^lu never carries
+// across a multiple of 32 except through k * 2^lu itself, and the padded
+// index is pad_idx(j0) plus a constant of k and lu.
+__device__ __forceinline__ int pad_off(int k, int lu) { return (k << lu) + ((k << lu) >> 5); }
+
+template <int E, int S, bool FWD, bool MAC = false, bool GROW = false>
 __device__ __forceinline__ void ntt_pass(uint64_t *sa, const uint64_t *gin, uint64_t *gout,
                                          bool reduce_in, int N, int logN, int lu, bool first,
                                          bool last, const PlaneRegs &pr,
@@ -94,15 +141,15 @@ __device__ __forceinline__ void ntt_pass(uint64_t *sa, const uint64_t *gin, uint
 #pragma unroll
     for (int gi = 0; gi < G; ++gi) {
         const int j0 = group_start<S>(threadIdx.x + T * gi, lu, lnb);
+        const int p0 = pad_idx(j0);
 #pragma unroll
         for (int k = 0; k < W; ++k) {
-            const int j = j0 + (k << lu);
             uint64_t x;
             if (first) {
-                x = gin[j];
+                x = gin[j0 + (k << lu)];
                 if (reduce_in) x = barrett_u64(x, pr.q, pr.mu);
             } else {
-                x = sa[pad_idx(j)];
+                x = sa[p0 + pad_off(k, lu)];
             }
             v[gi * W + k] = x;
         }
@@ -131,16 +178,28 @@ __device__ __forceinline__ void ntt_pass(uint64_t *sa, const uint64_t *gin, uint
                 const ulonglong2 tw = pr.tw[ti];
                 const uint64_t w = tw.x, ws = tw.y;
                 if (FWD) {
-                    const uint64_t xa = min(x, x - pr.q2);  // x - 2q when x >= 2q
-                    const uint64_t t = shoup_lazy(y, w, ws, pr.q);
-                    x = xa + t;
-                    y = xa - t + pr.q2;
+                    if (GROW) {
+                        const uint64_t t = shoup_lazy3(y, w, ws, pr.q);
+                        y = x - t + pr.q4;
+                        x = x + t;
+                    } else {
+                        const uint64_t xa = min(x, x - pr.q2);  // x - 2q when x >= 2q
+                        const uint64_t t = shoup_lazy(y, w, ws, pr.q);
+                        x = xa + t;
+                        y = xa - t + pr.q2;
+                    }
                 } else {
-                    uint64_t sm = x + y;
-                    sm = min(sm, sm - pr.q2);
-                    const uint64_t d = x - y + pr.q2;
-                    x = sm;
-                    y = shoup_lazy(d, w, ws, pr.q);
+                    if (GROW) {
+                        const uint64_t d = x - y + grow_inv_bound(pr.q, lu + st);
+                        x = x + y;
+                        y = shoup_lazy3(d, w, ws, pr.q);
+                    } else {
+                        uint64_t sm = x + y;
+                        sm = min(sm, sm - pr.q2);
+                        const uint64_t d = x - y + pr.q2;
+                        x = sm;
+                        y = shoup_lazy(d, w, ws, pr.q);
+                    }
                 }
             }
         }
@@ -150,28 +209,34 @@ __device__ __forceinline__ void ntt_pass(uint64_t *sa, const uint64_t *gin, uint
 #pragma unroll
     for (int gi = 0; gi < G; ++gi) {
         const int j0 = group_start<S>(threadIdx.x + T * gi, lu, lnb);
+        const int p0 = pad_idx(j0);
 #pragma unroll
         for (int k = 0; k < W; ++k) {
             const int j = j0 + (k << lu);
+            const int idx = p0 + pad_off(k, lu);
             uint64_t x = v[gi * W + k];
             if (last) {
-                if (FWD) {
-                    x = x >= pr.q2 ? x - pr.q2 : x;
-                    x = x >= pr.q ? x - pr.q : x;
-                } else {
-                    x = shoup_mulmod(x, pr.ninv, pr.ninv_s, pr.q);
-                }
                 if constexpr (MAC) {
-                    const int idx = pad_idx(j);
-                    const uint64_t p0 = mont_mul(x, mk->k0[j], pr.q, mk->qinv);
-                    const uint64_t p1 = mont_mul(x, mk->k1[j], pr.q, mk->qinv);
-                    mk->acc0[idx] = mk->assign ? p0 : add_mod(mk->acc0[idx], p0, pr.q);
-                    mk->acc1[idx] = mk->assign ? p1 : add_mod(mk->acc1[idx], p1, pr.q);
+                    // any representative: the Montgomery product reduces it
+                    const uint64_t m0 = mont_mul(x, mk->k0[j], pr.q, mk->qinv);
+                    const uint64_t m1 = mont_mul(x, mk->k1[j], pr.q, mk->qinv);
+                    mk->acc0[idx] = mk->assign ? m0 : add_mod(mk->acc0[idx], m0, pr.q);
+                    mk->acc1[idx] = mk->assign ? m1 : add_mod(mk->acc1[idx], m1, pr.q);
                 } else {
+                    if (FWD) {
+                        if (GROW) {
+                            x = barrett_u64(x, pr.q, pr.mu);
+                        } else {
+                            x = x >= pr.q2 ? x - pr.q2 : x;
+                            x = x >= pr.q ? x - pr.q : x;
+                        }
+                    } else {
+                        x = shoup_mulmod(x, pr.ninv, pr.ninv_s, pr.q);
+                    }
                     gout[j] = x;
                 }
             } else {
-                sa[pad_idx(j)] = x;
+                sa[idx] = x;
             }
         }
     }
@@ -195,7 +260,7 @@ struct NttShape {
 // (N = 2^LOGN): each pass's stage count, distance and first/last role are
 // constants, so the index arithmetic of ntt_pass folds away.  Same passes
 // and arithmetic as ntt_run.
-template <int E, bool FWD, bool MAC, int LOGN, int PI = 0, int DONE = 0>
+template <int E, bool FWD, bool MAC, bool GROW, int LOGN, int PI = 0, int DONE = 0>
 __device__ __forceinline__ void ntt_run_c(uint64_t *sa, const uint64_t *gin, uint64_t *gout,
                                           bool reduce_in, const PlaneRegs &pr, bool from_smem,
                                           const MacSink *mk) {
@@ -204,11 +269,11 @@ __device__ __forceinline__ void ntt_run_c(uint64_t *sa, const uint64_t *gin, uin
     constexpr int S = pass_stages(LOGN, PASSES, PI);
     constexpr bool LAST = DONE + S == LOGN;
     constexpr int LU = FWD ? LOGN - DONE - S : DONE;
-    ntt_pass<E, S, FWD, MAC>(sa, gin, gout, reduce_in, 1 << LOGN, LOGN, LU,
-                             PI == 0 && !from_smem, LAST, pr, mk);
+    ntt_pass<E, S, FWD, MAC, GROW>(sa, gin, gout, reduce_in, 1 << LOGN, LOGN, LU,
+                                   PI == 0 && !from_smem, LAST, pr, mk);
     if constexpr (!LAST)
-        ntt_run_c<E, FWD, MAC, LOGN, PI + 1, DONE + S>(sa, gin, gout, reduce_in, pr, from_smem,
-                                                       mk);
+        ntt_run_c<E, FWD, MAC, GROW, LOGN, PI + 1, DONE + S>(sa, gin, gout, reduce_in, pr,
+                                                             from_smem, mk);
 }
 
 // LOGN > 0: the degree is 2^LOGN, known at compile time (ntt_run_c); 0: a.N
@@ -236,6 +301,7 @@ __global__ void __launch_bounds__(NttShape<E>::kMaxThreads, 1) ntt_e_kernel(NttF
     PlaneRegs pr;
     pr.q = tp.q;
     pr.q2 = 2 * tp.q;
+    pr.q4 = 4 * tp.q;
     pr.mu = tp.mu;
     pr.ninv = tp.ninv;
     pr.ninv_s = tp.ninv_s;
@@ -243,7 +309,17 @@ __global__ void __launch_bounds__(NttShape<E>::kMaxThreads, 1) ntt_e_kernel(NttF
     const bool reduce_in = a.ks_ct != nullptr;
     uint64_t *gout = a.polys + p * N;
     if constexpr (LOGN > 0) {
-        ntt_run_c<E, FWD, false, LOGN>(sa, gin, gout, reduce_in, pr, false, nullptr);
+        // Uniform per CTA (one plane, one modulus).  Key-switch digits are
+        // residues mod the chain primes: unreduced they are below the
+        // largest of them.
+        uint64_t in_max = 0;
+        if (reduce_in)
+            for (int i = 0; i < a.ks_L; ++i) in_max = max(in_max, a.tab[i].q);
+        const bool grow = FWD ? ntt_grow_ok_fwd(pr.q, in_max, LOGN) : ntt_grow_ok_inv(pr.q, LOGN);
+        if (grow)
+            ntt_run_c<E, FWD, false, true, LOGN>(sa, gin, gout, false, pr, false, nullptr);
+        else
+            ntt_run_c<E, FWD, false, false, LOGN>(sa, gin, gout, reduce_in, pr, false, nullptr);
         return;
     }
     const int logN = a.logN;
@@ -273,7 +349,7 @@ __global__ void __launch_bounds__(NttShape<E>::kMaxThreads, 1) ntt_e_kernel(NttF
 
 // All passes of one transform held in `sa`: the first reads gin (or `sa`
 // itself when from_smem), the last writes gout (or the MAC sink).
-template <int E, bool FWD, bool MAC>
+template <int E, bool FWD, bool MAC, bool GROW = false>
 __device__ __forceinline__ void ntt_run(uint64_t *sa, const uint64_t *gin, uint64_t *gout,
                                         bool reduce_in, int N, int logN, const PlaneRegs &pr,
                                         bool from_smem, const MacSink *mk) {
@@ -286,17 +362,17 @@ __device__ __forceinline__ void ntt_run(uint64_t *sa, const uint64_t *gin, uint6
         const bool last = done + s == logN;
         const int lu = FWD ? logN - done - s : done;
         if (s == SM) {
-            ntt_pass<E, SM, FWD, MAC>(sa, gin, gout, reduce_in, N, logN, lu, first, last, pr, mk);
+            ntt_pass<E, SM, FWD, MAC, GROW>(sa, gin, gout, reduce_in, N, logN, lu, first, last, pr, mk);
         } else if (s == 4) {
-            ntt_pass<E, (SM > 4 ? 4 : 1), FWD, MAC>(sa, gin, gout, reduce_in, N, logN, lu, first,
+            ntt_pass<E, (SM > 4 ? 4 : 1), FWD, MAC, GROW>(sa, gin, gout, reduce_in, N, logN, lu, first,
                                                     last, pr, mk);
         } else if (s == 3) {
-            ntt_pass<E, (SM > 3 ? 3 : 1), FWD, MAC>(sa, gin, gout, reduce_in, N, logN, lu, first,
+            ntt_pass<E, (SM > 3 ? 3 : 1), FWD, MAC, GROW>(sa, gin, gout, reduce_in, N, logN, lu, first,
                                                     last, pr, mk);
         } else if (s == 2) {
-            ntt_pass<E, 2, FWD, MAC>(sa, gin, gout, reduce_in, N, logN, lu, first, last, pr, mk);
+            ntt_pass<E, 2, FWD, MAC, GROW>(sa, gin, gout, reduce_in, N, logN, lu, first, last, pr, mk);
         } else {
-            ntt_pass<E, 1, FWD, MAC>(sa, gin, gout, reduce_in, N, logN, lu, first, last, pr, mk);
+            ntt_pass<E, 1, FWD, MAC, GROW>(sa, gin, gout, reduce_in, N, logN, lu, first, last, pr, mk);
         }
         done += s;
         first = false;
@@ -334,6 +410,7 @@ __global__ void __launch_bounds__(NttShape<E>::kMaxThreads, 1) ks_fused_kernel(K
     PlaneRegs fw, iv;
     fw.q = iv.q = tp.q;
     fw.q2 = iv.q2 = 2 * tp.q;
+    fw.q4 = iv.q4 = 4 * tp.q;
     fw.mu = iv.mu = tp.mu;
     fw.ninv = iv.ninv = tp.ninv;
     fw.ninv_s = iv.ninv_s = tp.ninv_s;
@@ -341,21 +418,33 @@ __global__ void __launch_bounds__(NttShape<E>::kMaxThreads, 1) ks_fused_kernel(K
     iv.tw = tp.inv2;
     const int64_t key_stride = static_cast<int64_t>(a.L) * 2 * Lp * N;
     const uint64_t *key = a.keys + kc * key_stride;
+    uint64_t in_max = 0;  // digits are residues mod the chain primes
+    for (int i = 0; i < a.L; ++i) in_max = max(in_max, a.tab[i].q);
+    const bool grow_f = ntt_grow_ok_fwd(tp.q, in_max, a.logN);
     for (int i = 0; i < a.L; ++i) {
         const uint64_t *gin = a.ct + (static_cast<int64_t>(i) * a.n + a.c0 + c) * N;
         MacSink mk{acc0, acc1, key + (static_cast<int64_t>(i * 2 + 0) * Lp + k) * N,
                    key + (static_cast<int64_t>(i * 2 + 1) * Lp + k) * N, tp.qinv_neg, i == 0};
 
-        if constexpr (LOGN > 0)
-            ntt_run_c<E, true, true, LOGN>(sa, gin, nullptr, true, fw, false, &mk);
-        else
+        if constexpr (LOGN > 0) {
+            if (grow_f)  // unreduced digits
+                ntt_run_c<E, true, true, true, LOGN>(sa, gin, nullptr, false, fw, false, &mk);
+            else
+                ntt_run_c<E, true, true, false, LOGN>(sa, gin, nullptr, true, fw, false, &mk);
+        } else {
             ntt_run<E, true, true>(sa, gin, nullptr, true, N, a.logN, fw, false, &mk);
+        }
         __syncthreads();  // sa is rewritten by the next digit; acc read by the inverse
     }
     uint64_t *u0 = a.U + ((c * 2 + 0) * Lp + k) * N;
     uint64_t *u1 = a.U + ((c * 2 + 1) * Lp + k) * N;
-    ntt_run<E, false, false>(acc0, nullptr, u0, false, N, a.logN, iv, true, nullptr);
-    ntt_run<E, false, false>(acc1, nullptr, u1, false, N, a.logN, iv, true, nullptr);
+    if (LOGN > 0 && ntt_grow_ok_inv(tp.q, a.logN)) {
+        ntt_run<E, false, false, true>(acc0, nullptr, u0, false, N, a.logN, iv, true, nullptr);
+        ntt_run<E, false, false, true>(acc1, nullptr, u1, false, N, a.logN, iv, true, nullptr);
+    } else {
+        ntt_run<E, false, false>(acc0, nullptr, u0, false, N, a.logN, iv, true, nullptr);
+        ntt_run<E, false, false>(acc1, nullptr, u1, false, N, a.logN, iv, true, nullptr);
+    }
 }
 
 // Coefficients per thread for degree N: 8 up to N = 8192 (measured best of
