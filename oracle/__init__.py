@@ -96,8 +96,9 @@ def _load():
     lib.or_tweak_def.restype = None
     lib.or_tweak_alg.argtypes = [I, I, ctypes.c_int, P, P, P]
     lib.or_tweak_alg.restype = None
-    lib.or_ks_keygen.argtypes = [I, ctypes.c_int, P, P, P, P, P, P]
-    lib.or_keyswitch.argtypes = [I, ctypes.c_int, P, P, P, P]
+    C = ctypes.c_int
+    lib.or_ks_keygen_g.argtypes = [I, C, C, C, P, P, P, P, P, P]
+    lib.or_keyswitch_g.argtypes = [I, C, C, C, P, P, P, P]
     lib.or_rescale.argtypes = [I, ctypes.c_int, P, P, P]
     lib.or_rescale.restype = None
     _lib = lib
@@ -418,32 +419,49 @@ def tweak_alg(cts, primes) -> np.ndarray:
     return out
 
 
-def ks_keygen(s_old, s_new, primes_with_P, a, e) -> np.ndarray:
-    """Switching key s_old -> s_new modulo P*Q with the RNS gadget (one digit
-    per prime).  a: [L, L+1, N] uniform; e: [L, N] small.  Returns [L, 2, L+1, N]."""
-    L = len(primes_with_P) - 1
+def gadget_digits(L: int, dnum: int) -> list[range]:
+    """Chain primes of each digit of the RNS gadget with dnum digits:
+    consecutive groups of alpha = ceil(L / dnum) primes, the last one shorter."""
+    alpha = -(-L // dnum)
+    return [range(d * alpha, min(L, (d + 1) * alpha)) for d in range(dnum)]
+
+
+def ks_keygen(s_old, s_new, primes_with_P, a, e, L=None, dnum=None) -> np.ndarray:
+    """Switching key s_old -> s_new modulo P*Q with the RNS gadget of dnum
+    digits (SWKGen of Sec. 2.2 with gadget rank dnum).  primes_with_P: the L
+    chain primes, then the K special primes whose product is P (L defaults
+    to K = 1; dnum to L, one digit per chain prime).  a: [dnum, L+K, N]
+    uniform; e: [dnum, N] small.  Returns [dnum, 2, L+K, N]."""
+    Lp = len(primes_with_P)
+    L = Lp - 1 if L is None else L
+    dnum = L if dnum is None else dnum
     N = len(s_old)
-    key = np.empty((L, 2, L + 1, N), dtype=np.uint64)
+    key = np.empty((dnum, 2, Lp, N), dtype=np.uint64)
     pr = _u64(primes_with_P)
     so = np.ascontiguousarray(s_old, dtype=np.int64)
     sn = np.ascontiguousarray(s_new, dtype=np.int64)
     a64 = _u64(a)
     e64 = np.ascontiguousarray(e, dtype=np.int64)
-    _check(_load().or_ks_keygen(N, L, _ptr(pr), _ptr(so), _ptr(sn), _ptr(a64), _ptr(e64),
-                                _ptr(key)),
+    assert a64.shape == (dnum, Lp, N) and e64.shape == (dnum, N)
+    _check(_load().or_ks_keygen_g(N, L, Lp - L, dnum, _ptr(pr), _ptr(so), _ptr(sn), _ptr(a64),
+                                  _ptr(e64), _ptr(key)),
            "ks_keygen")
     return key
 
 
 def keyswitch(ct, key, primes_with_P) -> np.ndarray:
-    """KeySwitch: digits a mod q_i, sum digit_i * key_i mod PQ, divide by P (rounded)."""
+    """KeySwitch: digit d = [a]_{Q_d} (exact CRT lift of a's residues on the
+    digit's primes), sum digit_d * key_d mod PQ, divide by P (rounded).  The
+    gadget is read off the key: [dnum, 2, L+K, N]."""
     ct = _u64(ct)
     _, L, N = ct.shape
+    key64 = _u64(key)
+    dnum, _, Lp, _ = key64.shape
+    assert len(primes_with_P) == Lp
     out = np.empty_like(ct)
     pr = _u64(primes_with_P)
-    key64 = _u64(key)
-    _check(_load().or_keyswitch(N, L, _ptr(pr), _ptr(key64), _ptr(ct),
-                                _ptr(out)), "keyswitch")
+    _check(_load().or_keyswitch_g(N, L, Lp - L, dnum, _ptr(pr), _ptr(key64), _ptr(ct),
+                                  _ptr(out)), "keyswitch")
     return out
 
 

@@ -3,7 +3,11 @@ switching keys (generated by the oracle's key generator from seeded secrets,
 masks and errors), and column-wise encryptions of real matrices.
 
 Oracle layout throughout: a ciphertext batch is [n, 2, L, N] (ciphertext,
-part a/b, prime, coefficient); a switching key is [L, 2, L+1, N]."""
+part a/b, prime, coefficient); a switching key is [dnum, 2, L+K, N] (dnum
+digits; L chain primes and K special primes).  The default gadget is one
+digit per chain prime and one special prime; PR4/SP2 give the paper's
+experimental gadget of two digits (two chain primes each) and two special
+primes."""
 import numpy as np
 
 from paper_2503_16080_gb300 import synth
@@ -11,6 +15,8 @@ from paper_2503_16080_gb300 import synth
 PR = synth.ntt_primes(50, 3)
 SP = synth.ntt_primes(60, 1)[0]
 PRP = PR + [SP]
+PR4 = synth.ntt_primes(50, 4)
+SP2 = synth.ntt_primes(60, 2)
 
 
 def rand_cts(seed, n, N, primes):
@@ -21,26 +27,30 @@ def rand_cts(seed, n, N, primes):
     return cts
 
 
-def switching_key(oracle_mod, s_old, s_new, N, seed, primes_with_P=PRP):
-    L = len(primes_with_P) - 1
+def switching_key(oracle_mod, s_old, s_new, N, seed, primes_with_P=PRP, L=None, dnum=None):
+    """Key s_old -> s_new; primes_with_P = L chain primes then the special ones
+    (L defaults to one special prime), dnum digits (default L)."""
+    L = len(primes_with_P) - 1 if L is None else L
+    dnum = L if dnum is None else dnum
     a = np.stack([np.stack([synth.uniform_mod(seed, 100 + 10 * i + k, (N,), q)
-                            for k, q in enumerate(primes_with_P)]) for i in range(L)])
-    e = synth.rounded_gaussian(seed, 200, (L, N))
-    return oracle_mod.ks_keygen(s_old, s_new, primes_with_P, a, e)
+                            for k, q in enumerate(primes_with_P)]) for i in range(dnum)])
+    e = synth.rounded_gaussian(seed, 200, (dnum, N))
+    return oracle_mod.ks_keygen(s_old, s_new, primes_with_P, a, e, L=L, dnum=dnum)
 
 
-def aut_keys(oracle_mod, s, N, seed, primes_with_P=PRP):
+def aut_keys(oracle_mod, s, N, seed, primes_with_P=PRP, L=None, dnum=None):
     """Key j switches s(X^(2j+1)) -> s, 1 <= j < N; entry 0 is None."""
     keys = [None]
     for j in range(1, N):
         keys.append(switching_key(oracle_mod, oracle_mod.aut_key_secret(s, 2 * j + 1), s, N,
-                                  seed + j, primes_with_P))
+                                  seed + j, primes_with_P, L, dnum))
     return keys
 
 
-def relin_key(oracle_mod, s, N, seed, primes_with_P=PRP):
+def relin_key(oracle_mod, s, N, seed, primes_with_P=PRP, L=None, dnum=None):
     """Switches s^2 -> s."""
-    return switching_key(oracle_mod, oracle_mod.negacyclic_int(s, s), s, N, seed, primes_with_P)
+    return switching_key(oracle_mod, oracle_mod.negacyclic_int(s, s), s, N, seed, primes_with_P,
+                         L, dnum)
 
 
 def encrypt_columns(oracle_mod, M, s, delta, seed, primes=PR):
@@ -107,8 +117,11 @@ def from_batch(b):
 
 
 def stack_keys(keys, N, L):
-    """List of keys (None for unused slots) -> [count, L, 2, L+1, N]."""
-    out = np.zeros((len(keys), L, 2, L + 1, N), dtype=np.uint64)
+    """List of keys (None for unused slots) -> [count, dnum, 2, L+K, N] (the
+    shape of the first key present; N and L are checked against it)."""
+    shape = next(k.shape for k in keys if k is not None)
+    assert shape[3] == N and shape[2] > L
+    out = np.zeros((len(keys),) + shape, dtype=np.uint64)
     for i, k in enumerate(keys):
         if k is not None:
             out[i] = k

@@ -11,7 +11,7 @@ import pytest
 from paper_2503_16080_gb300 import synth
 
 import ckks_inputs
-from ckks_inputs import PR, PRP, rand_cts
+from ckks_inputs import PR, PRP, SP, rand_cts
 
 
 @pytest.mark.parametrize("n,N", [(1, 8), (2, 8), (4, 8), (8, 8), (16, 8), (16, 32), (8, 64)])
@@ -238,3 +238,131 @@ def test_cc_mm_rowwise_decrypts_to_product(oracle_mod, n):
     for j in range(N):
         dec = _decrypt_centered(oracle_mod, out[j], s, PR[:-1]).astype(np.float64) / scale
         assert np.max(np.abs(dec - ref[:, j])) <= 2.0 ** -20
+
+
+# ---- KeySwitch with the RNS gadget of dnum digits and K special primes (the
+# gadget rank of Sec. 2.2's footnote; the experiments of Sec. 6 use dnum = 2).
+# Chain primes, special primes, dnum: one digit per prime; two digits of two
+# primes with two special primes (the paper's dnum); uneven digits (2 + 1);
+# four one-prime digits with two special primes; one digit of two primes;
+# two digits with a single special prime.
+GADGETS = [(PR, [SP], 3), (ckks_inputs.PR4, ckks_inputs.SP2, 2), (PR, ckks_inputs.SP2, 2),
+           (ckks_inputs.PR4, ckks_inputs.SP2, 4), (ckks_inputs.PR4[:2], ckks_inputs.SP2, 1),
+           (ckks_inputs.PR4, [SP], 2)]
+
+
+def _prod(xs):
+    out = 1
+    for x in xs:
+        out *= int(x)
+    return out
+
+
+def _garner(res, mods):
+    """The integer in [0, prod(mods)) with the given residues, by Garner's
+    mixed-radix digits (v_0 + m_0 (v_1 + m_1 (v_2 + ...)))."""
+    v, x, M = [], 0, 1
+    for r, m in zip(res, mods):
+        t = (int(r) - x) * pow(M, -1, int(m)) % int(m)
+        x += t * M
+        M *= int(m)
+    return x
+
+
+def _negacyclic_z(a, b, mod):
+    N = len(a)
+    out = [0] * N
+    for i in range(N):
+        for j in range(N):
+            if i + j < N:
+                out[i + j] += a[i] * b[j]
+            else:
+                out[i + j - N] -= a[i] * b[j]
+    return [v % mod for v in out]
+
+
+def _digit_primes(L, dnum):
+    alpha = -(-L // dnum)
+    return [list(range(d * alpha, min(L, (d + 1) * alpha))) for d in range(dnum)]
+
+
+@pytest.mark.parametrize("chain,special,dnum", GADGETS)
+def test_keyswitch_gadget_integer_route(oracle_mod, chain, special, dnum):
+    # The oracle works prime by prime (digit lifts reduced per prime, RNS
+    # products, ModDown by residues); here the same KeySwitch runs on whole
+    # integers: keys lifted to [0, PQ), digits to [0, Q_d), products in
+    # Z[X]/(X^N + 1) mod PQ, then the rounded division by P.
+    N, L = 16, len(chain)
+    prp = list(chain) + list(special)
+    Q, P = _prod(chain), _prod(special)
+    key = ckks_inputs.switching_key(oracle_mod, synth.ternary(5, 1, N), synth.ternary(5, 2, N),
+                                    N, 31, prp, L, dnum)
+    assert key.shape == (dnum, 2, L + len(special), N)
+    ct = rand_cts(41, 1, N, chain)[0]
+    got = oracle_mod.keyswitch(ct, key, prp)
+    U = [[0] * N for _ in range(2)]
+    for d, idx in enumerate(_digit_primes(L, dnum)):
+        x = [_garner([ct[0, j, c] for j in idx], [chain[j] for j in idx]) for c in range(N)]
+        assert all(0 <= v < _prod(chain[j] for j in idx) for v in x)
+        for part in range(2):
+            kd = [_garner(key[d, part, :, c], prp) for c in range(N)]
+            prod = _negacyclic_z(x, kd, P * Q)
+            U[part] = [(u + v) % (P * Q) for u, v in zip(U[part], prod)]
+    for part in range(2):
+        for c in range(N):
+            r = U[part][c] % P
+            if r > P // 2:
+                r -= P
+            v = (U[part][c] - r) // P
+            for k, q in enumerate(chain):
+                want = (v + (int(ct[1, k, c]) if part else 0)) % q
+                assert int(got[part, k, c]) == want, (part, c, k)
+
+
+@pytest.mark.parametrize("chain,special,dnum", GADGETS)
+def test_ks_keygen_gadget_identity(oracle_mod, chain, special, dnum):
+    # Key d satisfies b_d + a_d * s_new = e_d + P * g_d * s_old mod PQ with
+    # g_d = (Q/Q_d) * ((Q/Q_d)^-1 mod Q_d), and sum_d [a]_{Q_d} g_d = a mod Q.
+    N, L = 8, len(chain)
+    prp = list(chain) + list(special)
+    Q, P = _prod(chain), _prod(special)
+    s_old, s_new = synth.ternary(6, 1, N), synth.ternary(6, 2, N)
+    key = ckks_inputs.switching_key(oracle_mod, s_old, s_new, N, 37, prp, L, dnum)
+    e = synth.rounded_gaussian(37, 200, (dnum, N))
+    digits = _digit_primes(L, dnum)
+    g = []
+    for d, idx in enumerate(digits):
+        Qd = _prod(chain[j] for j in idx)
+        g.append((Q // Qd) * pow(Q // Qd, -1, Qd))
+        kb = [_garner(key[d, 1, :, c], prp) for c in range(N)]
+        ka = [_garner(key[d, 0, :, c], prp) for c in range(N)]
+        lhs = [(u + v) % (P * Q) for u, v in zip(kb, _negacyclic_z(ka, [int(x) for x in s_new], P * Q))]
+        rhs = [(int(e[d, c]) + P * g[d] * int(s_old[c])) % (P * Q) for c in range(N)]
+        assert lhs == rhs, d
+    a = [_garner(rand_cts(43, 1, N, chain)[0, 0, :, c], chain) for c in range(N)]
+    for c in range(N):
+        total = sum((a[c] % _prod(chain[j] for j in idx)) * g[d] for d, idx in enumerate(digits))
+        assert total % Q == a[c]
+
+
+@pytest.mark.parametrize("chain,special,dnum", GADGETS)
+def test_keyswitch_gadget_decrypts(oracle_mod, chain, special, dnum):
+    N, L = 32, len(chain)
+    prp = list(chain) + list(special)
+    s_old, s_new = synth.ternary(1, 1, N), synth.ternary(1, 2, N)
+    key = ckks_inputs.switching_key(oracle_mod, s_old, s_new, N, 4, prp, L, dnum)
+    triv = np.zeros((2, L, N), dtype=np.uint64)
+    triv[1] = rand_cts(2, 1, N, chain)[0, 1]
+    assert np.array_equal(oracle_mod.keyswitch(triv, key, prp), triv)
+    m = (synth.uniform_unit(3, 1, (1, N)) * 2.0 ** 40).astype(np.int64)
+    ea = np.stack([synth.uniform_mod(3, 2 + pl, (1, N), q) for pl, q in enumerate(chain)])
+    eb = oracle_mod.rlwe_encrypt_rows(ea, s_old, m, np.zeros_like(m), chain)
+    ct = np.stack([ea[:, 0, :], eb[:, 0, :]])
+    before = _decrypt_centered(oracle_mod, ct, s_old, chain)
+    assert np.array_equal(before, m[0])
+    after = _decrypt_centered(oracle_mod, oracle_mod.keyswitch(ct, key, prp), s_new, chain)
+    # digit d times e_d, summed and divided by P, plus the rounding (times s)
+    e = synth.rounded_gaussian(4, 200, (dnum, N))
+    Qd = max(_prod(chain[j] for j in idx) for idx in _digit_primes(L, dnum))
+    bound = dnum * N * Qd * int(np.max(np.abs(e))) // _prod(special) + N
+    assert np.max(np.abs(after.astype(object) - before.astype(object))) <= bound
