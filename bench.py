@@ -306,45 +306,52 @@ def decrypt_error(U, M, sec, Aout, Bout, primes, rows: int = 64):
             "reference": "FP64 U*M (numpy) on the same rows"}
 
 
-def _switching_keys(s_old, S32, prp, seed: int, stream: int):
-    """Switching keys s_old[r] -> s for every row r of s_old (K x N small int64),
-    in the library's key layout [K, L, 2, L+1, N] (digit, part a/b, prime):
-    a uniform, b = e - a*s + [prime == digit] P s_old mod each prime, with the
-    RNS gadget of one digit per chain prime and P the special prime (last)."""
+def _switching_keys(s_old, S32, prp, seed: int, stream: int, L: int, dnum: int):
+    """Switching keys s_old[r] -> s for every row r of s_old (count x N small
+    int64), in the library's key layout [count, dnum, 2, L+K, N] (digit, part
+    a/b, prime): a uniform, b = e - a*s + P s_old on the primes of the digit
+    (the RNS gadget of dnum digits of consecutive chain primes), with P the
+    product of the K special primes prp[L:]."""
     import torch
     from paper_2503_16080_gb300 import synth
-    K, n = s_old.shape
-    L = len(prp) - 1
-    P = int(prp[-1])
+    count, n = s_old.shape
+    Lp = len(prp)
+    alpha = -(-L // dnum)
     dev = s_old.device
-    keys = torch.empty((K, L, 2, L + 1, n), dtype=torch.uint64, device=dev)
+    keys = torch.empty((count, dnum, 2, Lp, n), dtype=torch.uint64, device=dev)
     kv = keys.view(torch.int64)
-    e = synth.rounded_gaussian_torch(seed, stream + 90, (K * L, n), dev)
+    e = synth.rounded_gaussian_torch(seed, stream + 90, (count * dnum, n), dev)
     for k, q in enumerate(prp):
-        a = synth.uniform_mod_torch(seed, stream + k, (K * L, n), q, dev).view(torch.int64)
-        kv[:, :, 0, k, :] = a.view(K, L, n)
+        a = synth.uniform_mod_torch(seed, stream + k, (count * dnum, n), q, dev).view(torch.int64)
+        kv[:, :, 0, k, :] = a.view(count, dnum, n)
         b = torch.remainder(e.to(torch.int64) - negacyclic_rows_mod(a, S32, q, 10), q)
         del a
-        b = b.view(K, L, n)
+        b = b.view(count, dnum, n)
         if k < L:  # |P mod q| < 2^50 and |s_old| <= N <= 2^13: the product fits int64
-            b[:, k, :] = torch.remainder(b[:, k, :] + (P % q) * s_old, q)
+            Pq = 1
+            for p in prp[L:]:
+                Pq = Pq * (int(p) % int(q)) % int(q)
+            d = k // alpha
+            b[:, d, :] = torch.remainder(b[:, d, :] + Pq * s_old, q)
         kv[:, :, 1, k, :] = b
         del b
     return keys
 
 
-def ccmm_inputs(n: int, primes, prp, dev, seed: int = SEED):
+def ccmm_inputs(n: int, primes, prp, dev, seed: int = SEED, dnum=None):
     """Real CKKS inputs for CC-MM at ring degree n (plain PyTorch harness):
     a ternary secret s; column-wise encryptions of M1 and M2 (uniform in
     [-1, 1], scale 2^40; ciphertext j encrypts column j); the automorphism
     keys (slot j switches s(X^(2j+1)) -> s) and the relinearisation key
-    (s^2 -> s).  The negacyclic products by s run as TF32 matrix products of
-    10-bit limbs (exact: every sum is an integer below 2^24), checked on two
-    rows against the FP64 form."""
+    (s^2 -> s) for the gadget of dnum digits (default one per chain prime)
+    and the special primes prp[len(primes):].  The negacyclic products by s
+    run as TF32 matrix products of 10-bit limbs (exact: every sum is an
+    integer below 2^24), checked on two rows against the FP64 form."""
     import numpy as np
     import torch
     from paper_2503_16080_gb300 import synth
     L = len(primes)
+    dnum = L if dnum is None else dnum
     s = torch.from_numpy(synth.ternary(seed, 800, n)).to(dev)
     S32 = negacyclic_matrix(s, torch.float32)
     probe = synth.uniform_mod_torch(seed, 801, (2, n), prp[-1], dev).view(torch.int64)
@@ -372,10 +379,10 @@ def ccmm_inputs(n: int, primes, prp, dev, seed: int = SEED):
     s_aut = torch.zeros((n, n), dtype=torch.int64, device=dev)
     s_aut.scatter_(1, torch.remainder(pos, n), sign * s[None, :])
     del pos, sign
-    keys = _switching_keys(s_aut, S32, prp, seed, 300)
+    keys = _switching_keys(s_aut, S32, prp, seed, 300, L, dnum)
     del s_aut
     s2 = torch.matmul(s.to(torch.float64)[None, :], negacyclic_matrix(s, torch.float64))
-    rkey = _switching_keys(s2.to(torch.int64), S32, prp, seed, 400)
+    rkey = _switching_keys(s2.to(torch.int64), S32, prp, seed, 400, L, dnum)
     return {"s": s, "S32": S32, "M1": M1, "M2": M2, "ct1": ct1, "ct2": ct2, "keys": keys,
             "rkey": rkey}
 
@@ -936,10 +943,11 @@ def measure_precomp(pkg, dev, stream, d3: int, steps: int = 5, warmup: int = 3):
     a = torch.stack([synth.uniform_mod_torch(SEED, 50 + j, (N,), q, dev) for j, q in enumerate(primes)])
     B = torch.stack([synth.uniform_mod_torch(SEED, 60 + j, (d2, N), q, dev)
                      for j, q in enumerate(primes)])
-    keys = torch.empty((d3, L, 2, L + 1, N), dtype=torch.uint64, device=dev)
+    keys = torch.empty((d3,) + ring.key_shape(), dtype=torch.uint64, device=dev)
     kv = keys.view(torch.int64)
     for k, q in enumerate(prp):
-        kv[:, :, :, k, :] = synth.uniform_mod_torch(SEED, 70 + k, (d3, L, 2, N), q, dev).view(torch.int64)
+        kv[:, :, :, k, :] = synth.uniform_mod_torch(SEED, 70 + k, (d3, L, 2, N), q,
+                                                    dev).view(torch.int64)
     ring.prepare_keys(keys)
     out = torch.empty((2, L, d3, N), dtype=torch.uint64, device=dev)
     ws = torch.empty(int(pkg.lib().pc_mm_precomp_workspace(ring._h, d2, d3, 0)), dtype=torch.uint8,
@@ -1172,31 +1180,40 @@ def run_secondary(args):
 # ----------------------------------------------------------------- CC-MM
 
 CC_WORKLOAD = ("CC-MM n=8192 (Alg. 8): two column-wise encrypted 8192x8192 matrices, ring degree "
-               "8192, L=4 primes of 50 bits + a 60-bit special prime, N automorphism keys and a "
-               "relinearisation key resident on the device; output rescaled by q_3; real "
+               "8192, L=4 primes of 50 bits, key switching with {gadget}, N automorphism keys "
+               "and a relinearisation key resident on the device; output rescaled by q_3; real "
                "encryptions of M1, M2 uniform in [-1,1] at scale 2^40 under a ternary secret")
+# Key-switching gadgets of the CC-MM workload: the paper's experimental
+# setting (Sec. 6: dnum = 2), two digits of two chain primes over two 60-bit
+# special primes; and one digit per chain prime over one special prime.
+CC_GADGETS = {"paper": (2, 2, "dnum=2 digits of two primes + two 60-bit special primes "
+                                "(the paper's dnum)"),
+              "prime": (None, 1, "dnum=L one-prime digits + one 60-bit special prime")}
 
 
 def measure_ccmm(pkg, dev, stream, Nr: int, steps: int, warmup: int, peaks: dict,
-                 e2e: bool = True, cpu_leg: bool = True):
-    """CC-MM (Alg. 8) at ring degree Nr, L = 4: harness (real encryptions and
-    keys), timed steps, stage split, CRT GEMM roofline, FP64 DGEMM of the same
-    n, decrypted error; optionally the end-to-end form from host memory and
-    the CPU oracle's extrapolated time.  Returns the measurement as a dict."""
+                 e2e: bool = True, cpu_leg: bool = True, gadget: str = "paper"):
+    """CC-MM (Alg. 8) at ring degree Nr, L = 4, with the key-switching gadget
+    CC_GADGETS[gadget]: harness (real encryptions and keys), timed steps,
+    stage split, CRT GEMM roofline, FP64 DGEMM of the same n, decrypted error;
+    optionally the end-to-end form from host memory and the CPU oracle's
+    extrapolated time.  Returns the measurement as a dict."""
     import numpy as np
     import torch
     from paper_2503_16080_gb300 import synth
 
     L = 4
+    dnum, K, gadget_text = CC_GADGETS[gadget]
+    dnum = L if dnum is None else dnum
     primes = synth.ntt_primes(50, L)
-    prp = primes + synth.ntt_primes(60, 1)
-    ring = pkg.Ring(Nr, prp)
+    prp = primes + synth.ntt_primes(60, K)
+    ring = pkg.Ring(Nr, prp, special=K, dnum=dnum)
 
     # Real inputs: column-wise encryptions of M1 and M2 under a ternary secret,
     # valid automorphism and relinearisation keys (the kernels' work does not
     # depend on the values; the decrypted product is checked after timing).
     t_h = time.perf_counter()
-    inp = ccmm_inputs(Nr, primes, prp, dev)
+    inp = ccmm_inputs(Nr, primes, prp, dev, dnum=dnum)
     torch.cuda.synchronize()
     harness_s = time.perf_counter() - t_h
     ct1, ct2 = inp["ct1"], inp["ct2"]
@@ -1324,12 +1341,12 @@ def measure_ccmm(pkg, dev, stream, Nr: int, steps: int, warmup: int, peaks: dict
         import oracle
         oracle.build()
         n0 = 512
-        kz = [None] + [np.zeros((L, 2, L + 1, n0), dtype=np.uint64)] * (n0 - 1)
+        kz = [None] + [np.zeros((dnum, 2, L + K, n0), dtype=np.uint64)] * (n0 - 1)
         c0 = np.zeros((n0, 2, L, n0), dtype=np.uint64)
         for j, q in enumerate(primes):
             c0[:, :, j, :] = synth.uniform_mod(SEED, 700 + j, (n0, 2, n0), q)
         t0 = time.perf_counter()
-        oracle.cc_mm(c0, c0, kz, np.zeros((L, 2, L + 1, n0), dtype=np.uint64), prp)
+        oracle.cc_mm(c0, c0, kz, np.zeros((dnum, 2, L + K, n0), dtype=np.uint64), prp)
         t_all = time.perf_counter() - t0
         Ub = np.concatenate([c0[:, 0, 0, :].T, c0[:, 1, 0, :].T])
         Wb = np.concatenate([c0[:, 0, 0, :], c0[:, 1, 0, :]], axis=1)
@@ -1349,7 +1366,8 @@ def measure_ccmm(pkg, dev, stream, Nr: int, steps: int, warmup: int, peaks: dict
            "value": ms, "unit": "ms per CC-MM", "higher_is_better": False,
            "steps": steps, "warmup": warmup, "ms_per_step": ms,
            "dtype": "u64 residues (f16 digits on tcgen05)",
-           "config": {"workload": CC_WORKLOAD.replace("8192", str(Nr)), "N": Nr, "L": L,
+           "config": {"workload": CC_WORKLOAD.format(gadget=gadget_text).replace("8192", str(Nr)),
+                      "N": Nr, "L": L, "dnum": dnum, "special_primes": K,
                       "prime_bits": 50, "special_prime_bits": 60,
                       "l2": "inputs larger than L2", "key_bytes": keys.numel() * 8,
                       "workspace_bytes": ws_bytes},
@@ -1386,6 +1404,7 @@ def run_ccmm(args):
     stream = torch.cuda.current_stream()
     peaks, _ = load_peaks()
     res = measure_ccmm(pkg, dev, stream, args.ccmm_n, args.steps, args.warmup, peaks,
+                       gadget=args.gadget,
                        e2e=True, cpu_leg=not args.quick)
     line = {"metric": METRIC, **res, "n_gpus": 1, "scaling": "weak", "vs_baseline": None,
             "data": "synthetic"}
@@ -1413,6 +1432,9 @@ def main():
                          "beside it")
     ap.add_argument("--n", type=int, default=4096,
                     help="square size d = k = N (default 4096, the benchmark workload)")
+    ap.add_argument("--gadget", default="paper", choices=sorted(CC_GADGETS),
+                    help="key-switching gadget of the ccmm8192 workload: paper (dnum=2, two "
+                         "special primes) or prime (one digit per chain prime, one special)")
     ap.add_argument("--ccmm-n", type=int, default=8192,
                     help="ring degree of the ccmm8192 workload (smaller for profiling)")
     args = ap.parse_args()

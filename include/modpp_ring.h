@@ -2,15 +2,16 @@
  * modpp_ring.h -- C ABI of the ciphertext-ciphertext matrix product (CC-MM,
  * Alg. 8 of "Fast Homomorphic Linear Algebra with BLAS", arXiv 2503.16080)
  * and the ring operations it is built from: Tweak (Alg. 3), Transpose
- * (Alg. 4), KeySwitch with a special prime (Sec. 2.2), and Rescale.
+ * (Alg. 4), KeySwitch with special primes (Sec. 2.2), and Rescale.
  *
  * Ring and ciphertexts
  * --------------------
  * R_q = Z_q[X]/(X^N + 1), N a power of two, 2 <= N <= 16384.  The RNS chain
  * is q_0 .. q_{L-1} (the ciphertext modulus Q is their product) and key
- * switching uses one special prime P.  Every prime is odd, < 2^62,
- * congruent to 1 mod 2N (the negacyclic NTT needs a primitive 2N-th root of
- * unity), and all L+1 primes are distinct.
+ * switching uses K special primes p_0 .. p_{K-1} (K = 1 or 2) whose product
+ * is P.  Every prime is odd, < 2^62, congruent to 1 mod 2N (the negacyclic
+ * NTT needs a primitive 2N-th root of unity), and all L+K primes are
+ * distinct.
  *
  * A batch of n ciphertexts is stored part-major, [2][L][n][N] uint64:
  * element ((part * L + j) * n + c) * N + m is coefficient m of part `part`
@@ -20,13 +21,20 @@
  * c: the column-wise and row-wise formats of a ciphertext matrix (Sec. 6) are
  * the same storage read along the other axis.
  *
- * Switching keys: [L][2][L+1][N] uint64 per key (digit i, part, plane over
- * q_0 .. q_{L-1}, P, coefficient).  Key i encrypts P * g_i * s_old under
- * s_new modulo P*Q with the RNS gadget g_i = 1 mod q_i, 0 mod q_k (k != i):
- * key[i][1] = -key[i][0] * s_new + e_i + P * g_i * s_old.  KeySwitch of
- * (a, b) computes (round(sum_i [a]_{q_i} * key[i][0] / P),
- * b + round(sum_i [a]_{q_i} * key[i][1] / P)) with the division by P
- * rounded as x -> (x - [x]_P) / P, [x]_P centred in (-P/2, P/2].
+ * Gadget (SWKGen with gadget rank D, the decomposition number of Sec. 2.2's
+ * footnote; the paper's experiments use D = 2): the chain primes fall into
+ * D digits of alpha = ceil(L / D) consecutive primes (the last digit may be
+ * shorter; alpha <= 2), digit d holding q_j for d*alpha <= j <
+ * min(L, (d+1)*alpha), with product Q_d.  Switching keys: [D][2][L+K][N]
+ * uint64 per key (digit d, part, plane over q_0 .. q_{L-1}, p_0 .. p_{K-1},
+ * coefficient).  Key d encrypts P * g_d * s_old under s_new modulo P*Q with
+ * g_d = (Q/Q_d) * ((Q/Q_d)^-1 mod Q_d), which is 1 mod the digit's primes and
+ * 0 mod the other q_k: key[d][1] = -key[d][0] * s_new + e_d + P * g_d * s_old.
+ * KeySwitch of (a, b) computes (round(sum_d [a]_{Q_d} * key[d][0] / P),
+ * b + round(sum_d [a]_{Q_d} * key[d][1] / P)), [a]_{Q_d} the exact lift of
+ * a's residues on the digit's primes to [0, Q_d), with the division by P
+ * rounded as x -> (x - [x]_P) / P, [x]_P centred in (-P/2, P/2].  The
+ * default ring (modpp_ring_create) has D = L one-prime digits and K = 1.
  * Keys are generated outside the library (the server never sees secrets)
  * and converted once, in place, by modpp_ring_prepare_keys.
  *
@@ -50,28 +58,37 @@ extern "C" {
 
 typedef struct modpp_ring_s *modpp_ring;
 
-/* Device bytes of the ring tables for degree N and L chain primes (0 for
- * invalid sizes). */
+/* Device bytes of the ring tables for degree N, L chain primes, K special
+ * primes and D = dnum gadget digits (0 for invalid sizes); modpp_ring_bytes
+ * is the same with K = 1, D = L. */
+size_t modpp_ring_bytes_ks(int64_t N, int L, int K, int dnum);
 size_t modpp_ring_bytes(int64_t N, int L);
 
 /*
  * Writes the NTT tables (powers of a primitive 2N-th root psi of every
  * prime in bit-reversed order and their Shoup quotients), the RNS constants
  * (P^-1 mod q_k, q_{L-1}^-1 mod q_k, N^-1 mod q_k) and the index tables of
- * Alg. 4 into `mem` (device, modpp_ring_bytes(N, L) bytes, owned by the
- * caller and kept alive until modpp_ring_destroy), and returns a host handle
- * in *ring.  primes_host: L+1 primes, the chain q_0 .. q_{L-1} then P.
- * 1 <= L <= 16.  Synchronises `stream` once (the tables are copied from host
- * memory).  Errors: MODPP_ERR_ARG (sizes, null pointers), MODPP_ERR_PRIME (a
- * prime that is even, >= 2^62, not 1 mod 2N, or repeated),
- * MODPP_ERR_WORKSPACE (mem too small or misaligned), MODPP_ERR_CUDA.
+ * Alg. 4, and the gadget's constants (Garner's lift of two-prime digits,
+ * the CRT lift of [x]_P for two special primes) into `mem` (device,
+ * modpp_ring_bytes_ks(N, L, K, dnum) bytes, owned by the caller and kept
+ * alive until modpp_ring_destroy), and returns a host handle in *ring.
+ * primes_host: L+K primes, the chain q_0 .. q_{L-1} then the special primes.
+ * 1 <= L <= 16, K in {1, 2}, 1 <= dnum <= L with ceil(L / dnum) <= 2 and
+ * every digit non-empty.  Synchronises `stream` once (the tables are copied
+ * from host memory).  Errors: MODPP_ERR_ARG (sizes, gadget, null pointers),
+ * MODPP_ERR_PRIME (a prime that is even, >= 2^62, not 1 mod 2N, or
+ * repeated), MODPP_ERR_WORKSPACE (mem too small or misaligned),
+ * MODPP_ERR_CUDA.  modpp_ring_create is the same with K = 1 and dnum = L
+ * (primes_host: L+1 primes, the chain then P).
  */
+int modpp_ring_create_ks(int64_t N, int L, int K, int dnum, const uint64_t *primes_host, void *mem,
+                         size_t mem_bytes, void *stream, modpp_ring *ring);
 int modpp_ring_create(int64_t N, int L, const uint64_t *primes_host, void *mem, size_t mem_bytes,
                       void *stream, modpp_ring *ring);
 int modpp_ring_destroy(modpp_ring ring);
 
 /*
- * Converts `count` switching keys ([count][L][2][L+1][N], contiguous) in
+ * Converts `count` switching keys ([count][D][2][L+K][N], contiguous) in
  * place from coefficients to the form the key-switching kernels read: the
  * negacyclic NTT of every polynomial, multiplied by 2^64 mod its prime
  * (Montgomery form).  Apply once per key; the other calls take prepared keys.
@@ -89,7 +106,7 @@ int modpp_keyswitch(modpp_ring ring, const uint64_t *ct, uint64_t *out, int64_t 
 /*
  * KeySwitch (Sec. 2.2) of a batch of n ciphertexts, each with its own key:
  * ciphertext c is switched with keys[key_index[c]] (prepared keys,
- * [count][L][2][L+1][N]); key_index[c] < 0 copies ciphertext c unchanged.
+ * [count][D][2][L+K][N]); key_index[c] < 0 copies ciphertext c unchanged.
  * This is the key switch that follows each automorphism in Alg. 4 (steps
  * 2-5), where ciphertext j needs the key of s(X^(2j+1)) -> s.
  *   key_index  DEVICE array of n int32, read by the kernels; every
@@ -193,7 +210,7 @@ int cc_mm_ex(modpp_ring ring, int64_t n, const uint64_t *ct1, const uint64_t *ct
  *   Ut    d3 x d2 int8, contiguous: row k is column k of U.
  *   a     [L][N], the shared a-part.
  *   B     [L][d2][N]: the b-parts, row j = b_j (the b-part planes of a batch).
- *   keys  [d3][L][2][L+1][N], prepared (modpp_ring_prepare_keys).
+ *   keys  [d3][D][2][L+K][N], prepared (modpp_ring_prepare_keys).
  *   out   [2][L][d3][N] (with Rescale: [2][L-1][d3][N]): ciphertext k
  *         encrypts column k of M * U under s (at scale Delta * scale(U),
  *         divided by q_{L-1} with Rescale).

@@ -20,10 +20,13 @@ using namespace modpp;
 struct modpp_ring_s {
     int64_t N = 0;
     int L = 0;
+    int K = 1;                     // special primes
+    int Dg = 0;                    // gadget digits (dnum)
     int logN = 0;
-    std::vector<uint64_t> primes;  // L + 1: chain, then P
+    std::vector<uint64_t> primes;  // L + K: chain, then the special primes
     char *mem = nullptr;           // caller's device memory holding the tables
-    const NttPlane *tab = nullptr; // [L + 1]
+    const NttPlane *tab = nullptr; // [L + K]
+    KsGadget g{};                  // the key-switching gadget (device pointers into mem)
     const uint64_t *pinv = nullptr, *pinv_s = nullptr;    // P^-1 mod q_k, k < L
     const uint64_t *qlinv = nullptr, *qlinv_s = nullptr;  // q_{L-1}^-1 mod q_k, k < L-1
     const uint64_t *ninv = nullptr, *ninv_s = nullptr;    // N^-1 mod q_k, k < L
@@ -120,17 +123,20 @@ int log2_exact(int64_t x) {
 
 // Layout of the ring tables inside the caller's memory.
 struct RingLayout {
-    size_t tab, tables, consts, ints, status, total;
+    size_t tab, tables, consts, gadget, ints, status, total;
 };
-RingLayout ring_layout(int64_t N, int L) {
+RingLayout ring_layout(int64_t N, int L, int K) {
     RingLayout r{};
+    const int Lp = L + K;
     size_t off = 0;
     r.tab = off;
-    off = align_up(off + sizeof(NttPlane) * (L + 1));
+    off = align_up(off + sizeof(NttPlane) * Lp);
     r.tables = off;
-    off = align_up(off + sizeof(uint64_t) * 8 * (L + 1) * N);
+    off = align_up(off + sizeof(uint64_t) * 8 * Lp * N);
     r.consts = off;
-    off = align_up(off + sizeof(uint64_t) * 6 * (L + 1));
+    off = align_up(off + sizeof(uint64_t) * 6 * Lp);
+    r.gadget = off;  // cq, cq_s [kMaxGadgetDigits][L+K]; p0k, p0k_s, Pk [L]
+    off = align_up(off + sizeof(uint64_t) * (2 * kMaxGadgetDigits * Lp + 3 * L));
     r.ints = off;
     off = align_up(off + sizeof(int) * (3 * N + 1));
     r.status = off;
@@ -141,10 +147,17 @@ RingLayout ring_layout(int64_t N, int L) {
 
 int64_t batch_words(const modpp_ring_s *r, int64_t n, int L) { return 2 * L * n * r->N; }
 
+// Planes of key switching: chain and special primes.
+int ks_planes(const modpp_ring_s *r) { return r->L + r->K; }
+// Words of one switching key: [D][2][L+K][N].
+int64_t key_words(const modpp_ring_s *r) {
+    return static_cast<int64_t>(r->Dg) * 2 * ks_planes(r) * r->N;
+}
+
 // Ciphertexts per key-switching chunk and the chunk's scratch words.
 int64_t ks_chunk(const modpp_ring_s *r, int64_t n) {
-    const int64_t per_ct = static_cast<int64_t>(r->L) * (r->L + 1) * r->N +
-                           2 * static_cast<int64_t>(r->L + 1) * r->N;
+    const int64_t Lp = ks_planes(r);
+    const int64_t per_ct = static_cast<int64_t>(r->Dg) * Lp * r->N + 2 * Lp * r->N;
     int64_t nb = static_cast<int64_t>(ks_chunk_budget() / 8) / per_ct;
     nb = std::max<int64_t>(1, std::min(nb, n));
     return nb;
@@ -152,8 +165,8 @@ int64_t ks_chunk(const modpp_ring_s *r, int64_t n) {
 size_t ks_scratch_bytes(const modpp_ring_s *r, int64_t n) {
     if (n == 0) return 0;
     const int64_t nb = ks_chunk(r, n);
-    const int64_t Lp = r->L + 1;
-    return align_up(sizeof(uint64_t) * nb * r->L * Lp * r->N) +
+    const int64_t Lp = ks_planes(r);
+    return align_up(sizeof(uint64_t) * nb * r->Dg * Lp * r->N) +
            align_up(sizeof(uint64_t) * nb * 2 * Lp * r->N);
 }
 
@@ -164,12 +177,12 @@ int ks_run(const modpp_ring_s *r, const uint64_t *ct, int64_t n, int64_t count, 
            int64_t n_out, const uint64_t *keys, const int *kid, int kper, int b_zero, char *scratch,
            cudaStream_t st) {
     if (count == 0) return MODPP_OK;
-    const int L = r->L, Lp = L + 1;
+    const int Lp = ks_planes(r);
     const int N = static_cast<int>(r->N);
     const int64_t nb = ks_chunk(r, count);
     uint64_t *D = reinterpret_cast<uint64_t *>(scratch);
     uint64_t *U = reinterpret_cast<uint64_t *>(
-        scratch + align_up(sizeof(uint64_t) * nb * L * Lp * r->N));
+        scratch + align_up(sizeof(uint64_t) * nb * r->Dg * Lp * r->N));
     for (int64_t c0 = 0; c0 < count; c0 += nb) {
         const int64_t m = std::min(nb, count - c0);
         cudaError_t e;
@@ -178,20 +191,21 @@ int ks_run(const modpp_ring_s *r, const uint64_t *ct, int64_t n, int64_t count, 
         // ciphertext (the automorphisms of Alg. 4): the streaming
         // multiply-accumulate kernel reads the keys at full bandwidth.
         if (kper == 1 && ks_fused_supported(N)) {
-            e = launch_ks_fused(ct, n, L, N, c0, m, r->tab, keys, kid, kper, U, st);
+            e = launch_ks_fused(ct, n, N, c0, m, r->tab, r->g, keys, kid, kper, U, st);
         } else {
             if (ntt_fast_supported(N)) {
-                e = launch_ks_digits_ntt(ct, n, L, N, c0, m, r->tab, D, st);
+                e = launch_ks_digits_ntt(ct, n, N, c0, m, r->tab, r->g, D, st);
             } else {
-                e = launch_ks_decompose(ct, n, L, N, c0, m, r->tab, D, st);
-                if (e == cudaSuccess) e = launch_ntt(D, m * L * Lp, N, 1, Lp, r->tab, false, st);
+                e = launch_ks_decompose(ct, n, N, c0, m, r->tab, r->g, D, st);
+                if (e == cudaSuccess)
+                    e = launch_ntt(D, m * r->Dg * Lp, N, 1, Lp, r->tab, false, st);
             }
             if (e == cudaSuccess)
-                e = launch_ks_multacc(D, keys, kid, kper, L, N, c0, m, r->tab, U, st);
+                e = launch_ks_multacc(D, keys, kid, kper, r->g, N, c0, m, r->tab, U, st);
             if (e == cudaSuccess) e = launch_ntt(U, m * 2 * Lp, N, 1, Lp, r->tab, true, st);
         }
         if (e == cudaSuccess)
-            e = launch_ks_moddown(U, ct, n, L, N, c0, m, kid, kper, b_zero, r->tab, r->pinv,
+            e = launch_ks_moddown(U, ct, n, N, c0, m, kid, kper, b_zero, r->tab, r->g, r->pinv,
                                   r->pinv_s, out, n_out, st);
         if (e != cudaSuccess) return MODPP_ERR_CUDA;
     }
@@ -351,7 +365,7 @@ bool ws_ok(const void *ws, size_t have, size_t need) {
 
 // Debug-mode range checks of ring inputs (off unless debug_checks_on()): a
 // batch [2][Lc][n][N] of coefficients below the chain primes, and switching
-// keys [count][L][2][L+1][N] below q_0 .. q_{L-1}, P.  A violation sets
+// keys [count][D][2][L+K][N] below q_0 .. q_{L-1} and the special primes.  A violation sets
 // MODPP_ERR_RANGE in the ring's status word (sticky until read).
 int check_batch(const modpp_ring_s *r, const uint64_t *ct, int64_t n, int Lc, cudaStream_t st) {
     if (!debug_checks_on() || n == 0) return MODPP_OK;
@@ -361,8 +375,8 @@ int check_batch(const modpp_ring_s *r, const uint64_t *ct, int64_t n, int Lc, cu
 }
 int check_keys(const modpp_ring_s *r, const uint64_t *keys, int64_t count, cudaStream_t st) {
     if (!debug_checks_on() || count == 0) return MODPP_OK;
-    return cuda_status(range_planes(keys, count * r->L * 2 * (r->L + 1), 1, r->N, r->N, r->N,
-                                    r->primes.data(), r->L + 1, r->status, st));
+    return cuda_status(range_planes(keys, count * r->Dg * 2 * ks_planes(r), 1, r->N, r->N, r->N,
+                                    r->primes.data(), ks_planes(r), r->status, st));
 }
 
 
@@ -370,17 +384,29 @@ int check_keys(const modpp_ring_s *r, const uint64_t *keys, int64_t count, cudaS
 
 extern "C" {
 
-size_t modpp_ring_bytes(int64_t N, int L) {
-    if (N < 2 || N > kMaxN || log2_exact(N) < 0 || L < 1 || L > kMaxChain) return 0;
-    return ring_layout(N, L).total;
+// Gadget limits: 1 <= D <= L digits of at most two primes (every digit
+// non-empty), one or two special primes.
+bool gadget_args_ok(int L, int K, int D) {
+    if (L < 1 || L > kMaxChain || K < 1 || K > 2 || D < 1 || D > L || D > kMaxGadgetDigits) return false;
+    const int alpha = (L + D - 1) / D;
+    return alpha <= 2 && (D - 1) * alpha < L;
 }
 
-int modpp_ring_create(int64_t N, int L, const uint64_t *primes_host, void *mem, size_t mem_bytes,
-                      void *stream, modpp_ring *ring) {
+size_t modpp_ring_bytes_ks(int64_t N, int L, int K, int dnum) {
+    if (N < 2 || N > kMaxN || log2_exact(N) < 0 || !gadget_args_ok(L, K, dnum)) return 0;
+    return ring_layout(N, L, K).total;
+}
+
+size_t modpp_ring_bytes(int64_t N, int L) { return modpp_ring_bytes_ks(N, L, 1, L); }
+
+int modpp_ring_create_ks(int64_t N, int L, int K, int dnum, const uint64_t *primes_host, void *mem,
+                         size_t mem_bytes, void *stream, modpp_ring *ring) {
     if (ring == nullptr || primes_host == nullptr) return MODPP_ERR_ARG;
     *ring = nullptr;
-    if (N < 2 || N > kMaxN || log2_exact(N) < 0 || L < 1 || L > kMaxChain) return MODPP_ERR_ARG;
-    for (int i = 0; i <= L; ++i) {
+    if (N < 2 || N > kMaxN || log2_exact(N) < 0 || !gadget_args_ok(L, K, dnum))
+        return MODPP_ERR_ARG;
+    const int Lp = L + K;
+    for (int i = 0; i < Lp; ++i) {
         const uint64_t q = primes_host[i];
         if (q < 3 || (q & 1) == 0 || q >= (uint64_t(1) << 62) || (q - 1) % (2 * N) != 0 ||
             !is_prime_u64(q))
@@ -388,18 +414,19 @@ int modpp_ring_create(int64_t N, int L, const uint64_t *primes_host, void *mem, 
         for (int j = 0; j < i; ++j)
             if (primes_host[j] == q) return MODPP_ERR_PRIME;
     }
-    const RingLayout lay = ring_layout(N, L);
+    const RingLayout lay = ring_layout(N, L, K);
     if (!ws_ok(mem, mem_bytes, lay.total)) return MODPP_ERR_WORKSPACE;
     auto *r = new (std::nothrow) modpp_ring_s;
     if (!r) return MODPP_ERR_ARG;
     r->N = N;
     r->L = L;
+    r->K = K;
+    r->Dg = dnum;
     r->logN = log2_exact(N);
-    r->primes.assign(primes_host, primes_host + L + 1);
+    r->primes.assign(primes_host, primes_host + Lp);
     r->mem = static_cast<char *>(mem);
 
     std::vector<char> host(lay.total, 0);
-    const int Lp = L + 1;
     auto *tabs = reinterpret_cast<uint64_t *>(host.data() + lay.tables);
     const uint64_t *dtabs = reinterpret_cast<const uint64_t *>(r->mem + lay.tables);
     auto *tab = reinterpret_cast<NttPlane *>(host.data() + lay.tab);
@@ -449,11 +476,16 @@ int modpp_ring_create(int64_t N, int L, const uint64_t *primes_host, void *mem, 
         t.inv2 = reinterpret_cast<const ulonglong2 *>(dtabs + (static_cast<int64_t>(8 * k) + 6) * N);
     }
     auto *consts = reinterpret_cast<uint64_t *>(host.data() + lay.consts);
-    const uint64_t P = primes_host[L];
     const uint64_t ql = primes_host[L - 1];
+    // P mod q: the product of the special primes
+    auto p_mod = [&](uint64_t q) {
+        uint64_t v = 1 % q;
+        for (int t = 0; t < K; ++t) v = mulmod(v, primes_host[L + t] % q, q);
+        return v;
+    };
     for (int k = 0; k < Lp; ++k) {
         const uint64_t q = primes_host[k];
-        consts[0 * Lp + k] = invmod(P % q, q);
+        consts[0 * Lp + k] = k < L ? invmod(p_mod(q), q) : 0;
         consts[1 * Lp + k] = shoup(consts[0 * Lp + k], q);
         consts[2 * Lp + k] = k < L - 1 ? invmod(ql % q, q) : 0;
         consts[3 * Lp + k] = k < L - 1 ? shoup(consts[2 * Lp + k], q) : 0;
@@ -468,6 +500,48 @@ int modpp_ring_create(int64_t N, int L, const uint64_t *primes_host, void *mem, 
     r->qlinv_s = dconsts + 3 * Lp;
     r->ninv = dconsts + 4 * Lp;
     r->ninv_s = dconsts + 5 * Lp;
+    // The key-switching gadget: digit constants (Garner's lift of two-prime
+    // digits) and ModDown's constants for two special primes.
+    KsGadget &g = r->g;
+    g.L = L;
+    g.K = K;
+    g.D = dnum;
+    g.alpha = (L + dnum - 1) / dnum;
+    g.chain_max = *std::max_element(primes_host, primes_host + L);
+    auto *gad = reinterpret_cast<uint64_t *>(host.data() + lay.gadget);
+    const uint64_t *dgad = reinterpret_cast<const uint64_t *>(r->mem + lay.gadget);
+    uint64_t *cq = gad, *cq_s = gad + kMaxGadgetDigits * Lp, *p0k = gad + 2 * kMaxGadgetDigits * Lp;
+    uint64_t *p0k_s = p0k + L, *Pk = p0k + 2 * L;
+    for (int d = 0; d < dnum; ++d) {
+        const int j0 = d * g.alpha;
+        if (std::min(L, j0 + g.alpha) - j0 < 2) continue;
+        const uint64_t q0 = primes_host[j0], q1 = primes_host[j0 + 1];
+        g.ginv[d] = invmod(q0 % q1, q1);
+        g.ginv_s[d] = shoup(g.ginv[d], q1);
+        for (int k = 0; k < Lp; ++k) {
+            const uint64_t q = primes_host[k];
+            cq[d * Lp + k] = q0 % q;
+            cq_s[d * Lp + k] = shoup(q0 % q, q);
+        }
+    }
+    g.cq = dgad;
+    g.cq_s = dgad + kMaxGadgetDigits * Lp;
+    if (K == 2) {
+        const uint64_t p0 = primes_host[L], p1 = primes_host[L + 1];
+        g.p0inv = invmod(p0 % p1, p1);
+        g.p0inv_s = shoup(g.p0inv, p1);
+        g.m1 = (p1 - 1) / 2;
+        g.h0 = (p0 + 1) / 2;
+        for (int k = 0; k < L; ++k) {
+            const uint64_t q = primes_host[k];
+            p0k[k] = p0 % q;
+            p0k_s[k] = shoup(p0 % q, q);
+            Pk[k] = p_mod(q);
+        }
+    }
+    g.p0k = dgad + 2 * kMaxGadgetDigits * Lp;
+    g.p0k_s = g.p0k + L;
+    g.Pk = g.p0k + 2 * L;
     // Index tables of Alg. 4 (ints, period N).
     auto *ints = reinterpret_cast<int *>(host.data() + lay.ints);
     const int *dints = reinterpret_cast<const int *>(r->mem + lay.ints);
@@ -508,6 +582,11 @@ int modpp_ring_create(int64_t N, int L, const uint64_t *primes_host, void *mem, 
     return MODPP_OK;
 }
 
+int modpp_ring_create(int64_t N, int L, const uint64_t *primes_host, void *mem, size_t mem_bytes,
+                      void *stream, modpp_ring *ring) {
+    return modpp_ring_create_ks(N, L, 1, L, primes_host, mem, mem_bytes, stream, ring);
+}
+
 int modpp_ring_destroy(modpp_ring ring) {
     if (ring == nullptr) return MODPP_ERR_ARG;
     for (auto &ev : ring->ev)
@@ -518,8 +597,8 @@ int modpp_ring_destroy(modpp_ring ring) {
 
 int modpp_ring_prepare_keys(modpp_ring r, uint64_t *keys, int64_t count, void *stream) {
     if (r == nullptr || count < 0 || (count > 0 && !a16(keys))) return MODPP_ERR_ARG;
-    const int Lp = r->L + 1;
-    const int64_t polys = count * r->L * 2 * Lp;
+    const int Lp = ks_planes(r);
+    const int64_t polys = count * r->Dg * 2 * Lp;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     const int rc = check_keys(r, keys, count, st);
     if (rc) return rc;
@@ -720,7 +799,7 @@ int cc_mm(modpp_ring r, const uint64_t *ct1, const uint64_t *ct2, const uint64_t
 // ---------------------------------------------------------------- Alg. 7
 // CP-MM with precomputation on a shared-a encryption, then the key switches
 // back to one secret.  Workspace: the Mod-PP-MM workspace (status word
-// first), the shared digits D of a (L * (L+1) transforms), key-switch
+// first), the shared digits D of a (D * (L+K) transforms), key-switch
 // products for a chunk of output ciphertexts, and, with the Rescale flag,
 // the unrescaled batch.
 struct PrecompLayout {
@@ -729,13 +808,13 @@ struct PrecompLayout {
 };
 PrecompLayout precomp_layout(const modpp_ring_s *r, int64_t d2, int64_t d3, int flags) {
     PrecompLayout p{};
-    const int L = r->L, Lp = L + 1;
+    const int L = r->L, Lp = ks_planes(r);
     const int64_t N = r->N;
     size_t off = 0;
     p.mm = off;
     off = align_up(off + modpp_mm_workspace(d3, d2, N, r->primes.data(), L, MODPP_PATH_F16));
     p.dig = off;
-    off = align_up(off + sizeof(uint64_t) * L * Lp * N);
+    off = align_up(off + sizeof(uint64_t) * r->Dg * Lp * N);
     const int64_t per_ct = 2 * static_cast<int64_t>(Lp) * N;
     p.chunk = std::max<int64_t>(1, std::min<int64_t>(d3, static_cast<int64_t>(ks_chunk_budget() / 8) / per_ct));
     p.u = off;
@@ -765,7 +844,7 @@ int pc_mm_precomp(modpp_ring r, int64_t d2, int64_t d3, const int8_t *Ut, const 
     const PrecompLayout lay = precomp_layout(r, d2, d3, flags);
     if (!ws_ok(ws, ws_bytes, lay.total)) return MODPP_ERR_WORKSPACE;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    const int L = r->L, Lp = L + 1;
+    const int L = r->L, Lp = ks_planes(r);
     const int N = static_cast<int>(r->N);
     char *base = static_cast<char *>(ws);
     int rc = MODPP_OK;
@@ -793,18 +872,19 @@ int pc_mm_precomp(modpp_ring r, int64_t d2, int64_t d3, const int8_t *Ut, const 
     uint64_t *Ubuf = reinterpret_cast<uint64_t *>(base + lay.u);
     cudaError_t e;
     if (ntt_fast_supported(N)) {
-        e = launch_ks_digits_ntt(a, 1, L, N, 0, 1, r->tab, D, st);
+        e = launch_ks_digits_ntt(a, 1, N, 0, 1, r->tab, r->g, D, st);
     } else {
-        e = launch_ks_decompose(a, 1, L, N, 0, 1, r->tab, D, st);
-        if (e == cudaSuccess) e = launch_ntt(D, L * Lp, N, 1, Lp, r->tab, false, st);
+        e = launch_ks_decompose(a, 1, N, 0, 1, r->tab, r->g, D, st);
+        if (e == cudaSuccess) e = launch_ntt(D, r->Dg * Lp, N, 1, Lp, r->tab, false, st);
     }
     if (e != cudaSuccess) return MODPP_ERR_CUDA;
     for (int64_t c0 = 0; c0 < d3; c0 += lay.chunk) {
         const int64_t m = std::min(lay.chunk, d3 - c0);
-        e = launch_ks_multacc(D, keys, nullptr, 1, L, N, c0, m, r->tab, Ubuf, st, /*d_shared=*/1);
+        e = launch_ks_multacc(D, keys, nullptr, 1, r->g, N, c0, m, r->tab, Ubuf, st,
+                              /*d_shared=*/1);
         if (e == cudaSuccess) e = launch_ntt(Ubuf, m * 2 * Lp, N, 1, Lp, r->tab, true, st);
         if (e == cudaSuccess)
-            e = launch_ks_moddown(Ubuf, X, d3, L, N, c0, m, nullptr, 1, 0, r->tab, r->pinv,
+            e = launch_ks_moddown(Ubuf, X, d3, N, c0, m, nullptr, 1, 0, r->tab, r->g, r->pinv,
                                   r->pinv_s, X, d3, st);
         if (e != cudaSuccess) return MODPP_ERR_CUDA;
     }

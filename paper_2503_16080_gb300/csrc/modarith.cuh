@@ -32,6 +32,23 @@ __device__ __forceinline__ uint64_t shoup_mulmod(uint64_t a, uint64_t w, uint64_
     return r;
 }
 
+// a * w mod q up to one multiple of q: the result lies in [0, 2q).
+__device__ __forceinline__ uint64_t shoup_lazy(uint64_t a, uint64_t w, uint64_t ws, uint64_t q) {
+    return a * w - __umul64hi(a, ws) * q;
+}
+
+// a * w mod q up to three multiples of q, [0, 4q), for any 64-bit a: Shoup's
+// quotient from three of the four 32 x 32-bit partial products of a * ws.
+// The low product and the low halves of the two middle ones are each below
+// 2^64 after scaling, so the quotient falls short of floor(a * ws / 2^64) by
+// at most 2, and the remainder of the exact quotient is below 2q.
+__device__ __forceinline__ uint64_t shoup_lazy3(uint64_t a, uint64_t w, uint64_t ws, uint64_t q) {
+    const uint32_t a0 = static_cast<uint32_t>(a), a1 = static_cast<uint32_t>(a >> 32);
+    const uint32_t s0 = static_cast<uint32_t>(ws), s1 = static_cast<uint32_t>(ws >> 32);
+    const uint64_t qh = static_cast<uint64_t>(a1) * s1 + __umulhi(a1, s0) + __umulhi(a0, s1);
+    return a * w - qh * q;
+}
+
 __device__ __forceinline__ uint64_t sub_mod(uint64_t a, uint64_t b, uint64_t q) {
     return a >= b ? a - b : a + q - b;
 }

@@ -19,6 +19,7 @@
 
 #include <cstdlib>
 
+#include "ks_gadget.cuh"
 #include "modarith.cuh"
 #include "ring_internal.h"
 
@@ -29,35 +30,18 @@ namespace {
 // threads then fall into different banks.
 __device__ __forceinline__ int pad_idx(int j) { return j + (j >> 5); }
 
-// a * w mod q up to one multiple of q: the result lies in [0, 2q).
-__device__ __forceinline__ uint64_t shoup_lazy(uint64_t a, uint64_t w, uint64_t ws, uint64_t q) {
-    return a * w - __umul64hi(a, ws) * q;
-}
-
-// a * w mod q up to three multiples of q, [0, 4q), for any 64-bit a: Shoup's
-// quotient from three of the four 32 x 32-bit partial products of a * ws.
-// The low product and the low halves of the two middle ones are each below
-// 2^64 after scaling, so the quotient falls short of floor(a * ws / 2^64) by
-// at most 2, and the remainder of the exact quotient is below 2q.
-__device__ __forceinline__ uint64_t shoup_lazy3(uint64_t a, uint64_t w, uint64_t ws, uint64_t q) {
-    const uint32_t a0 = static_cast<uint32_t>(a), a1 = static_cast<uint32_t>(a >> 32);
-    const uint32_t s0 = static_cast<uint32_t>(ws), s1 = static_cast<uint32_t>(ws >> 32);
-    const uint64_t qh = static_cast<uint64_t>(a1) * s1 + __umulhi(a1, s0) + __umulhi(a0, s1);
-    return a * w - qh * q;
-}
-
 struct NttFastArgs {
     uint64_t *polys;
     int N, logN;
     int64_t inner;
     int nplanes;
     const NttPlane *tab;
-    // Key-switching source (forward only): polynomial p = (c * L + i) * (L + 1) + k
-    // reads the a-part plane i of ciphertext c0 + c of a batch with plane
-    // stride n, reduced modulo prime k.  Null: transform polys in place.
+    // Key-switching source (forward only): polynomial p = (c * D + d) * (L + K) + k
+    // reads digit d of the a-part of ciphertext c0 + c of a batch with plane
+    // stride n, modulo prime k (the gadget g).  Null: transform polys in place.
     const uint64_t *ks_ct;
     int64_t ks_n, ks_c0;
-    int ks_L;
+    KsGadget g;
 };
 
 // Constants of the polynomial's prime, held in registers.
@@ -132,7 +116,8 @@ template <int E, int S, bool FWD, bool MAC = false, bool GROW = false>
 __device__ __forceinline__ void ntt_pass(uint64_t *sa, const uint64_t *gin, uint64_t *gout,
                                          bool reduce_in, int N, int logN, int lu, bool first,
                                          bool last, const PlaneRegs &pr,
-                                         const MacSink *mk = nullptr) {
+                                         const MacSink *mk = nullptr,
+                                         const DigitSrc *ds = nullptr) {
     constexpr int G = E >> S;  // groups of 2^S coefficients per thread
     constexpr int W = 1 << S;
     const int T = N / E;
@@ -146,8 +131,12 @@ __device__ __forceinline__ void ntt_pass(uint64_t *sa, const uint64_t *gin, uint
         for (int k = 0; k < W; ++k) {
             uint64_t x;
             if (first) {
-                x = gin[j0 + (k << lu)];
-                if (reduce_in) x = barrett_u64(x, pr.q, pr.mu);
+                if (ds) {
+                    x = digit_at(*ds, j0 + (k << lu), pr.q, pr.mu, reduce_in);
+                } else {
+                    x = gin[j0 + (k << lu)];
+                    if (reduce_in) x = barrett_u64(x, pr.q, pr.mu);
+                }
             } else {
                 x = sa[p0 + pad_off(k, lu)];
             }
@@ -263,17 +252,17 @@ struct NttShape {
 template <int E, bool FWD, bool MAC, bool GROW, int LOGN, int PI = 0, int DONE = 0>
 __device__ __forceinline__ void ntt_run_c(uint64_t *sa, const uint64_t *gin, uint64_t *gout,
                                           bool reduce_in, const PlaneRegs &pr, bool from_smem,
-                                          const MacSink *mk) {
+                                          const MacSink *mk, const DigitSrc *ds = nullptr) {
     constexpr int SM = NttShape<E>::kLogE;
     constexpr int PASSES = (LOGN + SM - 1) / SM;
     constexpr int S = pass_stages(LOGN, PASSES, PI);
     constexpr bool LAST = DONE + S == LOGN;
     constexpr int LU = FWD ? LOGN - DONE - S : DONE;
     ntt_pass<E, S, FWD, MAC, GROW>(sa, gin, gout, reduce_in, 1 << LOGN, LOGN, LU,
-                                   PI == 0 && !from_smem, LAST, pr, mk);
+                                   PI == 0 && !from_smem, LAST, pr, mk, ds);
     if constexpr (!LAST)
         ntt_run_c<E, FWD, MAC, GROW, LOGN, PI + 1, DONE + S>(sa, gin, gout, reduce_in, pr,
-                                                             from_smem, mk);
+                                                             from_smem, mk, ds);
 }
 
 // LOGN > 0: the degree is 2^LOGN, known at compile time (ntt_run_c); 0: a.N
@@ -286,13 +275,17 @@ __global__ void __launch_bounds__(NttShape<E>::kMaxThreads, 1) ntt_e_kernel(NttF
     const int N = a.N;
     int plane;
     const uint64_t *gin;
-    if (a.ks_ct) {
-        const int Lp = a.ks_L + 1;
+    DigitSrc dsrc{};
+    const DigitSrc *ds = nullptr;
+    if (FWD && a.ks_ct) {
+        const int Lp = a.g.L + a.g.K;
         plane = static_cast<int>(p % Lp);
         const int64_t r = p / Lp;
-        const int i = static_cast<int>(r % a.ks_L);
-        const int64_t c = r / a.ks_L;
-        gin = a.ks_ct + (static_cast<int64_t>(i) * a.ks_n + a.ks_c0 + c) * N;
+        const int d = static_cast<int>(r % a.g.D);
+        const int64_t c = r / a.g.D;
+        gin = a.ks_ct + (static_cast<int64_t>(gadget_lo(a.g, d)) * a.ks_n + a.ks_c0 + c) * N;
+        dsrc = make_digit_src(a.g, a.tab, gin, a.ks_n * N, d, plane);
+        ds = &dsrc;
     } else {
         plane = static_cast<int>((p / a.inner) % a.nplanes);
         gin = a.polys + p * N;
@@ -306,20 +299,17 @@ __global__ void __launch_bounds__(NttShape<E>::kMaxThreads, 1) ntt_e_kernel(NttF
     pr.ninv = tp.ninv;
     pr.ninv_s = tp.ninv_s;
     pr.tw = FWD ? tp.fwd2 : tp.inv2;
-    const bool reduce_in = a.ks_ct != nullptr;
+    const bool reduce_in = FWD && a.ks_ct != nullptr;
     uint64_t *gout = a.polys + p * N;
     if constexpr (LOGN > 0) {
-        // Uniform per CTA (one plane, one modulus).  Key-switch digits are
-        // residues mod the chain primes: unreduced they are below the
-        // largest of them.
-        uint64_t in_max = 0;
-        if (reduce_in)
-            for (int i = 0; i < a.ks_L; ++i) in_max = max(in_max, a.tab[i].q);
+        // Uniform per CTA (one plane, one modulus).  Unreduced key-switch
+        // digits stay below digit_bound.
+        const uint64_t in_max = reduce_in ? digit_bound(a.g, pr.q) : 0;
         const bool grow = FWD ? ntt_grow_ok_fwd(pr.q, in_max, LOGN) : ntt_grow_ok_inv(pr.q, LOGN);
         if (grow)
-            ntt_run_c<E, FWD, false, true, LOGN>(sa, gin, gout, false, pr, false, nullptr);
+            ntt_run_c<E, FWD, false, true, LOGN>(sa, gin, gout, false, pr, false, nullptr, ds);
         else
-            ntt_run_c<E, FWD, false, false, LOGN>(sa, gin, gout, reduce_in, pr, false, nullptr);
+            ntt_run_c<E, FWD, false, false, LOGN>(sa, gin, gout, reduce_in, pr, false, nullptr, ds);
         return;
     }
     const int logN = a.logN;
@@ -332,15 +322,20 @@ __global__ void __launch_bounds__(NttShape<E>::kMaxThreads, 1) ntt_e_kernel(NttF
         // forward: distances fall from N/2; inverse: they rise from 1
         const int lu = FWD ? logN - done - s : done;
         if (s == SM) {
-            ntt_pass<E, SM, FWD>(sa, gin, gout, reduce_in, N, logN, lu, first, last, pr);
+            ntt_pass<E, SM, FWD>(sa, gin, gout, reduce_in, N, logN, lu, first, last, pr, nullptr,
+                                  ds);
         } else if (s == 4) {
-            ntt_pass<E, (SM > 4 ? 4 : 1), FWD>(sa, gin, gout, reduce_in, N, logN, lu, first, last, pr);
+            ntt_pass<E, (SM > 4 ? 4 : 1), FWD>(sa, gin, gout, reduce_in, N, logN, lu, first, last, pr, nullptr,
+                                  ds);
         } else if (s == 3) {
-            ntt_pass<E, (SM > 3 ? 3 : 1), FWD>(sa, gin, gout, reduce_in, N, logN, lu, first, last, pr);
+            ntt_pass<E, (SM > 3 ? 3 : 1), FWD>(sa, gin, gout, reduce_in, N, logN, lu, first, last, pr, nullptr,
+                                  ds);
         } else if (s == 2) {
-            ntt_pass<E, 2, FWD>(sa, gin, gout, reduce_in, N, logN, lu, first, last, pr);
+            ntt_pass<E, 2, FWD>(sa, gin, gout, reduce_in, N, logN, lu, first, last, pr, nullptr,
+                                  ds);
         } else {
-            ntt_pass<E, 1, FWD>(sa, gin, gout, reduce_in, N, logN, lu, first, last, pr);
+            ntt_pass<E, 1, FWD>(sa, gin, gout, reduce_in, N, logN, lu, first, last, pr, nullptr,
+                                  ds);
         }
         done += s;
         first = false;
@@ -352,7 +347,8 @@ __global__ void __launch_bounds__(NttShape<E>::kMaxThreads, 1) ntt_e_kernel(NttF
 template <int E, bool FWD, bool MAC, bool GROW = false>
 __device__ __forceinline__ void ntt_run(uint64_t *sa, const uint64_t *gin, uint64_t *gout,
                                         bool reduce_in, int N, int logN, const PlaneRegs &pr,
-                                        bool from_smem, const MacSink *mk) {
+                                        bool from_smem, const MacSink *mk,
+                                        const DigitSrc *ds = nullptr) {
     constexpr int SM = NttShape<E>::kLogE;
     const int passes = (logN + SM - 1) / SM;
     int done = 0;
@@ -362,17 +358,17 @@ __device__ __forceinline__ void ntt_run(uint64_t *sa, const uint64_t *gin, uint6
         const bool last = done + s == logN;
         const int lu = FWD ? logN - done - s : done;
         if (s == SM) {
-            ntt_pass<E, SM, FWD, MAC, GROW>(sa, gin, gout, reduce_in, N, logN, lu, first, last, pr, mk);
+            ntt_pass<E, SM, FWD, MAC, GROW>(sa, gin, gout, reduce_in, N, logN, lu, first, last, pr, mk, ds);
         } else if (s == 4) {
             ntt_pass<E, (SM > 4 ? 4 : 1), FWD, MAC, GROW>(sa, gin, gout, reduce_in, N, logN, lu, first,
-                                                    last, pr, mk);
+                                                    last, pr, mk, ds);
         } else if (s == 3) {
             ntt_pass<E, (SM > 3 ? 3 : 1), FWD, MAC, GROW>(sa, gin, gout, reduce_in, N, logN, lu, first,
-                                                    last, pr, mk);
+                                                    last, pr, mk, ds);
         } else if (s == 2) {
-            ntt_pass<E, 2, FWD, MAC, GROW>(sa, gin, gout, reduce_in, N, logN, lu, first, last, pr, mk);
+            ntt_pass<E, 2, FWD, MAC, GROW>(sa, gin, gout, reduce_in, N, logN, lu, first, last, pr, mk, ds);
         } else {
-            ntt_pass<E, 1, FWD, MAC, GROW>(sa, gin, gout, reduce_in, N, logN, lu, first, last, pr, mk);
+            ntt_pass<E, 1, FWD, MAC, GROW>(sa, gin, gout, reduce_in, N, logN, lu, first, last, pr, mk, ds);
         }
         done += s;
         first = false;
@@ -382,12 +378,13 @@ __device__ __forceinline__ void ntt_run(uint64_t *sa, const uint64_t *gin, uint6
 struct KsFusedArgs {
     const uint64_t *ct;  // batch [2][L][n][N]; digits come from the a-parts
     int64_t n, c0;
-    int L, N, logN;
+    int N, logN;
     const NttPlane *tab;
-    const uint64_t *keys;  // [count][L][2][L+1][N], prepared
+    KsGadget g;
+    const uint64_t *keys;  // [count][D][2][L+K][N], prepared
     const int *kid;
     int kper;
-    uint64_t *U;  // [nb][2][L+1][N]: sum_i digit_i * key_i[part] mod q_k, coefficients
+    uint64_t *U;  // [nb][2][L+K][N]: sum_d digit_d * key_d[part] mod q_k, coefficients
 };
 
 // Key switching's digits, products and sums for one (ciphertext, target
@@ -401,7 +398,7 @@ __global__ void __launch_bounds__(NttShape<E>::kMaxThreads, 1) ks_fused_kernel(K
     const int N = a.N;
     const int Wd = N + N / 32;
     uint64_t *sa = smem, *acc0 = smem + Wd, *acc1 = smem + 2 * Wd;
-    const int Lp = a.L + 1;
+    const int Lp = a.g.L + a.g.K;
     const int k = static_cast<int>(blockIdx.x % Lp);
     const int64_t c = blockIdx.x / Lp;
     const int kc = a.kid[(a.c0 + c) % a.kper];
@@ -416,23 +413,23 @@ __global__ void __launch_bounds__(NttShape<E>::kMaxThreads, 1) ks_fused_kernel(K
     fw.ninv_s = iv.ninv_s = tp.ninv_s;
     fw.tw = tp.fwd2;
     iv.tw = tp.inv2;
-    const int64_t key_stride = static_cast<int64_t>(a.L) * 2 * Lp * N;
+    const int64_t key_stride = static_cast<int64_t>(a.g.D) * 2 * Lp * N;
     const uint64_t *key = a.keys + kc * key_stride;
-    uint64_t in_max = 0;  // digits are residues mod the chain primes
-    for (int i = 0; i < a.L; ++i) in_max = max(in_max, a.tab[i].q);
-    const bool grow_f = ntt_grow_ok_fwd(tp.q, in_max, a.logN);
-    for (int i = 0; i < a.L; ++i) {
-        const uint64_t *gin = a.ct + (static_cast<int64_t>(i) * a.n + a.c0 + c) * N;
-        MacSink mk{acc0, acc1, key + (static_cast<int64_t>(i * 2 + 0) * Lp + k) * N,
-                   key + (static_cast<int64_t>(i * 2 + 1) * Lp + k) * N, tp.qinv_neg, i == 0};
+    const bool grow_f = ntt_grow_ok_fwd(tp.q, digit_bound(a.g, tp.q), a.logN);
+    for (int d = 0; d < a.g.D; ++d) {
+        const uint64_t *gin =
+            a.ct + (static_cast<int64_t>(gadget_lo(a.g, d)) * a.n + a.c0 + c) * N;
+        const DigitSrc ds = make_digit_src(a.g, a.tab, gin, a.n * N, d, k);
+        MacSink mk{acc0, acc1, key + (static_cast<int64_t>(d * 2 + 0) * Lp + k) * N,
+                   key + (static_cast<int64_t>(d * 2 + 1) * Lp + k) * N, tp.qinv_neg, d == 0};
 
         if constexpr (LOGN > 0) {
             if (grow_f)  // unreduced digits
-                ntt_run_c<E, true, true, true, LOGN>(sa, gin, nullptr, false, fw, false, &mk);
+                ntt_run_c<E, true, true, true, LOGN>(sa, gin, nullptr, false, fw, false, &mk, &ds);
             else
-                ntt_run_c<E, true, true, false, LOGN>(sa, gin, nullptr, true, fw, false, &mk);
+                ntt_run_c<E, true, true, false, LOGN>(sa, gin, nullptr, true, fw, false, &mk, &ds);
         } else {
-            ntt_run<E, true, true>(sa, gin, nullptr, true, N, a.logN, fw, false, &mk);
+            ntt_run<E, true, true>(sa, gin, nullptr, true, N, a.logN, fw, false, &mk, &ds);
         }
         __syncthreads();  // sa is rewritten by the next digit; acc read by the inverse
     }
@@ -508,15 +505,15 @@ constexpr int kKsE = 8;
 
 bool ks_fused_supported(int N) { return N >= 1024 && N <= 8192 && (N & (N - 1)) == 0; }
 
-cudaError_t launch_ks_fused(const uint64_t *ct, int64_t n, int L, int N, int64_t c0, int64_t nb,
-                            const NttPlane *tab, const uint64_t *keys, const int *kid, int kper,
-                            uint64_t *U, cudaStream_t s) {
+cudaError_t launch_ks_fused(const uint64_t *ct, int64_t n, int N, int64_t c0, int64_t nb,
+                            const NttPlane *tab, const KsGadget &g, const uint64_t *keys,
+                            const int *kid, int kper, uint64_t *U, cudaStream_t s) {
     if (nb == 0) return cudaSuccess;
     KsFusedArgs a{};
     a.ct = ct;
     a.n = n;
     a.c0 = c0;
-    a.L = L;
+    a.g = g;
     a.N = N;
     a.logN = 31 - __builtin_clz(N);
     a.tab = tab;
@@ -525,7 +522,7 @@ cudaError_t launch_ks_fused(const uint64_t *ct, int64_t n, int L, int N, int64_t
     a.kper = kper;
     a.U = U;
     const size_t smem = 3 * static_cast<size_t>(N + N / 32) * sizeof(uint64_t);
-    const dim3 grid(static_cast<unsigned>(nb * (L + 1)));
+    const dim3 grid(static_cast<unsigned>(nb * (g.L + g.K)));
     auto go = [&](auto kernel) {
         cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              static_cast<int>(smem));
@@ -558,8 +555,9 @@ cudaError_t launch_ntt_fast(uint64_t *polys, int64_t npolys, int N, int64_t inne
     return inverse ? launch_fast<false>(a, npolys, s) : launch_fast<true>(a, npolys, s);
 }
 
-cudaError_t launch_ks_digits_ntt(const uint64_t *ct, int64_t n, int L, int N, int64_t c0,
-                                 int64_t nb, const NttPlane *tab, uint64_t *D, cudaStream_t s) {
+cudaError_t launch_ks_digits_ntt(const uint64_t *ct, int64_t n, int N, int64_t c0, int64_t nb,
+                                 const NttPlane *tab, const KsGadget &g, uint64_t *D,
+                                 cudaStream_t s) {
     if (nb == 0) return cudaSuccess;
     NttFastArgs a{};
     a.polys = D;
@@ -567,13 +565,13 @@ cudaError_t launch_ks_digits_ntt(const uint64_t *ct, int64_t n, int L, int N, in
     a.logN = 0;
     while ((1 << a.logN) < N) ++a.logN;
     a.inner = 1;
-    a.nplanes = L + 1;
+    a.nplanes = g.L + g.K;
     a.tab = tab;
     a.ks_ct = ct;
     a.ks_n = n;
     a.ks_c0 = c0;
-    a.ks_L = L;
-    return launch_fast<true>(a, nb * L * (L + 1), s);
+    a.g = g;
+    return launch_fast<true>(a, nb * g.D * (g.L + g.K), s);
 }
 
 }  // namespace modpp

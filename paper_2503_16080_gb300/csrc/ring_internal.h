@@ -21,6 +21,31 @@ struct NttPlane {
     const ulonglong2 *inv2;
 };
 
+// Gadget of the ring's key switching (SWKGen with gadget rank D, Sec. 2.2):
+// the L chain primes fall into D digits of at most two consecutive primes
+// (digit d: primes d * alpha .. min(L, (d + 1) * alpha) - 1), and K <= 2
+// special primes, whose product is P, follow the chain (planes L .. L+K-1).
+// Digit d of an a-part is its residue modulo the product Q_d of the digit's
+// primes.  Switching keys: [count][D][2][L+K][N].  Device pointers point into
+// the ring's tables.
+constexpr int kMaxGadgetDigits = 16;
+struct KsGadget {
+    int L, K, D, alpha;
+    uint64_t chain_max;  // largest chain prime: bound of an unreduced one-prime digit
+    // ModUp of a two-prime digit (primes j0 and j1 = j0 + 1): the digit is
+    // the integer v0 + q_j0 * v1 in [0, q_j0 q_j1), v0 = a_j0 and
+    // v1 = (a_j1 - v0) * q_j0^-1 mod q_j1 (Garner's mixed radix).
+    uint64_t ginv[kMaxGadgetDigits], ginv_s[kMaxGadgetDigits];  // q_j0^-1 mod q_j1, Shoup quotient
+    const uint64_t *cq, *cq_s;                      // [D][L+K]: q_j0 mod q_k, Shoup quotient
+    // ModDown with two special primes p0, p1: [u]_P = v0 + p0 * v1 with
+    // v0 = u mod p0, v1 = (u_p1 - v0) * p0^-1 mod p1; the centred value is
+    // [u]_P - P when (v1, v0) >= (m1, h0) lexicographically, i.e. when
+    // [u]_P >= (P + 1) / 2 = h0 + p0 * m1.
+    uint64_t p0inv, p0inv_s, m1, h0;
+    const uint64_t *p0k, *p0k_s;  // [L]: p0 mod q_k, Shoup quotient
+    const uint64_t *Pk;           // [L]: P mod q_k
+};
+
 // Per-ciphertext tables of a gather: every table has period `per` over the
 // batch (ciphertext c reads entry c mod per; source indices are relative to
 // the period block of c, and per is a power of two).  Null tables mean
@@ -42,30 +67,36 @@ bool ntt_fast_supported(int N);
 cudaError_t launch_ntt_fast(uint64_t *polys, int64_t npolys, int N, int64_t inner, int nplanes,
                             const NttPlane *tab, bool inverse, cudaStream_t s);
 // Key switching's digits, NTTs, key products and inverse NTTs in one kernel
-// (1024 <= N <= 8192): U[c][part][k] = sum_i a_i * key_i[part] mod q_k (coefficients).
+// (1024 <= N <= 8192): U[c][part][k] = sum_d digit_d * key_d[part] mod q_k
+// (coefficients), k < L + K.
 bool ks_fused_supported(int N);
-cudaError_t launch_ks_fused(const uint64_t *ct, int64_t n, int L, int N, int64_t c0, int64_t nb,
-                            const NttPlane *tab, const uint64_t *keys, const int *kid, int kper,
-                            uint64_t *U, cudaStream_t s);
+cudaError_t launch_ks_fused(const uint64_t *ct, int64_t n, int N, int64_t c0, int64_t nb,
+                            const NttPlane *tab, const KsGadget &g, const uint64_t *keys,
+                            const int *kid, int kper, uint64_t *U, cudaStream_t s);
 // Digits of key switching fused with their forward NTT (N >= 1024):
-// D[c][i][k] = NTT_k(a_i of ciphertext c0 + c mod q_k), c < nb.
-cudaError_t launch_ks_digits_ntt(const uint64_t *ct, int64_t n, int L, int N, int64_t c0,
-                                 int64_t nb, const NttPlane *tab, uint64_t *D, cudaStream_t s);
+// D[c][d][k] = NTT_k(digit d of the a-part of ciphertext c0 + c, mod q_k), c < nb.
+cudaError_t launch_ks_digits_ntt(const uint64_t *ct, int64_t n, int N, int64_t c0, int64_t nb,
+                                 const NttPlane *tab, const KsGadget &g, uint64_t *D,
+                                 cudaStream_t s);
 cudaError_t launch_to_montgomery(uint64_t *polys, int64_t npolys, int N, int64_t inner,
                                  int nplanes, const NttPlane *tab, cudaStream_t s);
-cudaError_t launch_ks_decompose(const uint64_t *ct, int64_t n, int L, int N, int64_t c0,
-                                int64_t nb, const NttPlane *tab, uint64_t *D, cudaStream_t s);
+// The digits alone (coefficients), D[c][d][k] as above.
+cudaError_t launch_ks_decompose(const uint64_t *ct, int64_t n, int N, int64_t c0, int64_t nb,
+                                const NttPlane *tab, const KsGadget &g, uint64_t *D,
+                                cudaStream_t s);
 // kid null: ciphertext c takes key c.  d_shared: one set of digits D[0] for
 // every ciphertext (a batch sharing one a-part).
 cudaError_t launch_ks_multacc(const uint64_t *D, const uint64_t *keys, const int *kid, int kper,
-                              int L, int N, int64_t c0, int64_t nb, const NttPlane *tab,
-                              uint64_t *U, cudaStream_t s, int d_shared = 0);
+                              const KsGadget &g, int N, int64_t c0, int64_t nb,
+                              const NttPlane *tab, uint64_t *U, cudaStream_t s,
+                              int d_shared = 0);
 // Writes ciphertext c0 + c of the chunk to plane stride n_out of `out`; kid
-// null: no ciphertext is copied unchanged.
-cudaError_t launch_ks_moddown(const uint64_t *U, const uint64_t *ct, int64_t n, int L, int N,
-                              int64_t c0, int64_t nb, const int *kid, int kper, int b_zero,
-                              const NttPlane *tab, const uint64_t *pinv, const uint64_t *pinv_s,
-                              uint64_t *out, int64_t n_out, cudaStream_t s);
+// null: no ciphertext is copied unchanged.  pinv: P^-1 mod q_k (Shoup).
+cudaError_t launch_ks_moddown(const uint64_t *U, const uint64_t *ct, int64_t n, int N, int64_t c0,
+                              int64_t nb, const int *kid, int kper, int b_zero,
+                              const NttPlane *tab, const KsGadget &g, const uint64_t *pinv,
+                              const uint64_t *pinv_s, uint64_t *out, int64_t n_out,
+                              cudaStream_t s);
 // parts = 2: both parts of every ciphertext; 1: the a-parts only.
 cudaError_t launch_ct_gather(const uint64_t *in, uint64_t *out, int64_t n, int L, int N,
                              const GatherTables &t, const NttPlane *tab, cudaStream_t s,

@@ -21,6 +21,7 @@
 #include <algorithm>
 
 #include "modarith.cuh"
+#include "ks_gadget.cuh"
 #include "ring_internal.h"
 
 namespace modpp {
@@ -116,38 +117,39 @@ cudaError_t launch_to_montgomery(uint64_t *polys, int64_t npolys, int N, int64_t
 
 // ------------------------------------------------------------ key switching
 // Digits of the a-parts of ciphertexts [c0, c0 + nb) (planes 0..L-1 of a
-// batch [2][L][n][N]): D[c][i][k] = (a_i of ciphertext c) mod q_k, k <= L.
-__global__ void ks_decompose_kernel(const uint64_t *__restrict__ ct, int64_t n, int L, int N,
-                                    int64_t c0, int64_t nb, const NttPlane *__restrict__ tab,
+// batch [2][L][n][N]): D[c][d][k] = (digit d of the a-part of ciphertext c)
+// mod q_k, k < L + K (ModUp: the digit's exact residue modulo Q_d).
+__global__ void ks_decompose_kernel(const uint64_t *__restrict__ ct, int64_t n, int N, int64_t c0,
+                                    int64_t nb, const NttPlane *__restrict__ tab, KsGadget g,
                                     uint64_t *__restrict__ D) {
-    const int Lp = L + 1;
-    const int64_t total = nb * L * Lp * static_cast<int64_t>(N);
+    const int Lp = g.L + g.K;
+    const int64_t total = nb * g.D * Lp * static_cast<int64_t>(N);
     for (int64_t x = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; x < total;
          x += static_cast<int64_t>(gridDim.x) * blockDim.x) {
         const int m = static_cast<int>(x % N);
         int64_t r = x / N;
         const int k = static_cast<int>(r % Lp);
         r /= Lp;
-        const int i = static_cast<int>(r % L);
-        const int64_t c = r / L;
-        const uint64_t v = ct[(static_cast<int64_t>(i) * n + c0 + c) * N + m];  // part 0, plane i
-        D[x] = barrett_u64(v, tab[k].q, tab[k].mu);
+        const int d = static_cast<int>(r % g.D);
+        const int64_t c = r / g.D;
+        const uint64_t *a0 = ct + (static_cast<int64_t>(gadget_lo(g, d)) * n + c0 + c) * N;
+        const DigitSrc s = make_digit_src(g, tab, a0, n * N, d, k);
+        D[x] = digit_at(s, m, tab[k].q, tab[k].mu, true);
     }
 }
 
-// U[c][part][k] = sum_i D[c][i][k] * key[kid(c)][i][part][k] in the evaluation
-// domain (keys in Montgomery form, digits plain: the product is plain).
-// kid null: ciphertext c0 + c takes key c0 + c.  d_shared: every ciphertext
-// shares the digits D[0] (one a-part for the whole batch).
-// nb * (L+1) < 2^31 and N = 2^logN.
+// U[c][part][k] = sum_d D[c][d][k] * key[kid(c)][d][part][k] in the
+// evaluation domain (keys in Montgomery form, digits plain: the product is
+// plain), k < L + K.  kid null: ciphertext c0 + c takes key c0 + c.
+// d_shared: every ciphertext shares the digits D[0] (one a-part for the
+// whole batch).  nb * (L + K) < 2^31 and N = 2^logN.
 __global__ void ks_multacc_kernel(const uint64_t *__restrict__ D, const uint64_t *__restrict__ keys,
-                                  const int *__restrict__ kid, int kper, int L, int logN,
+                                  const int *__restrict__ kid, int kper, int Dg, int Lp, int logN,
                                   int64_t c0, int64_t nb, const NttPlane *__restrict__ tab,
                                   uint64_t *__restrict__ U, int d_shared) {
     // Two neighbouring coefficients per thread (16-byte accesses).
-    const int Lp = L + 1;
     const int N = 1 << logN;
-    const int64_t key_stride = static_cast<int64_t>(L) * 2 * Lp << logN;
+    const int64_t key_stride = static_cast<int64_t>(Dg) * 2 * Lp << logN;
     const int64_t total = (nb * Lp) << (logN - 1);
     for (int64_t x = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; x < total;
          x += static_cast<int64_t>(gridDim.x) * blockDim.x) {
@@ -160,12 +162,12 @@ __global__ void ks_multacc_kernel(const uint64_t *__restrict__ D, const uint64_t
         const uint64_t q = tab[k].q, qinv = tab[k].qinv_neg;
         const uint64_t *key = keys + kc * key_stride + (static_cast<int64_t>(k) << logN) + m;
         const uint64_t *d =
-            D + ((static_cast<int64_t>(d_shared ? 0 : c) * L * Lp + k) << logN) + m;
-        const int64_t dstep = static_cast<int64_t>(Lp) << logN;     // next digit i
-        const int64_t kstep = static_cast<int64_t>(2 * Lp) << logN; // next key digit i
+            D + ((static_cast<int64_t>(d_shared ? 0 : c) * Dg * Lp + k) << logN) + m;
+        const int64_t dstep = static_cast<int64_t>(Lp) << logN;     // next digit
+        const int64_t kstep = static_cast<int64_t>(2 * Lp) << logN; // next key digit
         const int64_t kpart = static_cast<int64_t>(Lp) << logN;     // part 1 of a key digit
         ulonglong2 u0 = make_ulonglong2(0, 0), u1 = make_ulonglong2(0, 0);
-        for (int i = 0; i < L; ++i) {
+        for (int i = 0; i < Dg; ++i) {
             const ulonglong2 di = *reinterpret_cast<const ulonglong2 *>(d + i * dstep);
             const ulonglong2 k0 = *reinterpret_cast<const ulonglong2 *>(key + i * kstep);
             const ulonglong2 k1 = *reinterpret_cast<const ulonglong2 *>(key + i * kstep + kpart);
@@ -181,31 +183,22 @@ __global__ void ks_multacc_kernel(const uint64_t *__restrict__ D, const uint64_t
 }
 
 // ModDown by P and accumulation: out_a = round(U_a / P), out_b = b + round(U_b / P),
-// with round(x / P) = (x_k - r) * P^-1 mod q_k, r = [x]_P centred.
-// Ciphertexts with kid < 0 are copied unchanged.  With b_zero the input
-// b-part is taken as 0 (Relin(D0, 0) in Alg. 8).  One thread takes two
-// neighbouring coefficients of one (ciphertext, part) for every chain prime,
-// so the special prime's plane is read once.
-__device__ __forceinline__ uint64_t centred_mod(uint64_t up, uint64_t P, uint64_t q, uint64_t mu) {
-    // [up]_P centred (up - P if up > P/2), as a residue mod q
-    if (up > P / 2) {
-        const uint64_t mag = barrett_u64(P - up, q, mu);
-        return mag == 0 ? 0 : q - mag;
-    }
-    return barrett_u64(up, q, mu);
-}
-
+// with round(x / P) = (x_k - r) * P^-1 mod q_k, r = [x]_P centred (the CRT
+// lift of x's special residues, ks_gadget.cuh).  Ciphertexts with kid < 0 are
+// copied unchanged.  With b_zero the input b-part is taken as 0 (Relin(D0, 0)
+// in Alg. 8).  One thread takes two neighbouring coefficients of one
+// (ciphertext, part) for every chain prime, so the special planes are read
+// once.
 __global__ void ks_moddown_kernel(const uint64_t *__restrict__ U, const uint64_t *__restrict__ ct,
-                                  int64_t n, int L, int logN, int64_t c0, int64_t nb,
+                                  int64_t n, int logN, int64_t c0, int64_t nb,
                                   const int *__restrict__ kid, int kper, int b_zero,
-                                  const NttPlane *__restrict__ tab,
+                                  const NttPlane *__restrict__ tab, KsGadget g,
                                   const uint64_t *__restrict__ pinv,
                                   const uint64_t *__restrict__ pinv_s, uint64_t *__restrict__ out,
                                   int64_t n_out) {
-    const int Lp = L + 1;
+    const int L = g.L, Lp = g.L + g.K;
     const int N = 1 << logN;
     const int part = blockIdx.y;
-    const uint64_t P = tab[L].q;
     const int64_t total = nb << (logN - 1);
     for (int64_t x = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; x < total;
          x += static_cast<int64_t>(gridDim.x) * blockDim.x) {
@@ -213,8 +206,17 @@ __global__ void ks_moddown_kernel(const uint64_t *__restrict__ U, const uint64_t
         const int64_t c = x >> (logN - 1);
         const bool copy = kid != nullptr && kid[(c0 + c) % kper] < 0;
         const int64_t ub = ((c * 2 + part) * Lp) << logN;
-        ulonglong2 up = make_ulonglong2(0, 0);
-        if (!copy) up = *reinterpret_cast<const ulonglong2 *>(U + ub + (static_cast<int64_t>(L) << logN) + m);
+        CentredP rx{}, ry{};
+        if (!copy) {
+            const ulonglong2 u0 =
+                *reinterpret_cast<const ulonglong2 *>(U + ub + (static_cast<int64_t>(L) << logN) + m);
+            ulonglong2 u1 = make_ulonglong2(0, 0);
+            if (g.K == 2)
+                u1 = *reinterpret_cast<const ulonglong2 *>(
+                    U + ub + (static_cast<int64_t>(L + 1) << logN) + m);
+            rx = centred_p_digits(g, tab, u0.x, u1.x);
+            ry = centred_p_digits(g, tab, u0.y, u1.y);
+        }
         for (int k = 0; k < L; ++k) {
             const int64_t io = ((static_cast<int64_t>(part) * L + k) * n + c0 + c) * N + m;
             const int64_t oo = ((static_cast<int64_t>(part) * L + k) * n_out + c0 + c) * N + m;
@@ -223,11 +225,11 @@ __global__ void ks_moddown_kernel(const uint64_t *__restrict__ U, const uint64_t
                 v = (part == 1 && b_zero) ? make_ulonglong2(0, 0)
                                           : *reinterpret_cast<const ulonglong2 *>(ct + io);
             } else {
-                const uint64_t q = tab[k].q, mu = tab[k].mu, pv = pinv[k], pvs = pinv_s[k];
+                const uint64_t q = tab[k].q, pv = pinv[k], pvs = pinv_s[k];
                 const ulonglong2 uk =
                     *reinterpret_cast<const ulonglong2 *>(U + ub + (static_cast<int64_t>(k) << logN) + m);
-                v.x = shoup_mulmod(sub_mod(uk.x, centred_mod(up.x, P, q, mu), q), pv, pvs, q);
-                v.y = shoup_mulmod(sub_mod(uk.y, centred_mod(up.y, P, q, mu), q), pv, pvs, q);
+                v.x = shoup_mulmod(sub_mod(uk.x, centred_p_mod(g, tab, rx, k), q), pv, pvs, q);
+                v.y = shoup_mulmod(sub_mod(uk.y, centred_p_mod(g, tab, ry, k), q), pv, pvs, q);
                 if (part == 1 && !b_zero) {
                     const ulonglong2 b = *reinterpret_cast<const ulonglong2 *>(ct + io);
                     v.x = add_mod(b.x, v.x, q);
@@ -239,32 +241,35 @@ __global__ void ks_moddown_kernel(const uint64_t *__restrict__ U, const uint64_t
     }
 }
 
-cudaError_t launch_ks_decompose(const uint64_t *ct, int64_t n, int L, int N, int64_t c0,
-                                int64_t nb, const NttPlane *tab, uint64_t *D, cudaStream_t s) {
+cudaError_t launch_ks_decompose(const uint64_t *ct, int64_t n, int N, int64_t c0, int64_t nb,
+                                const NttPlane *tab, const KsGadget &g, uint64_t *D,
+                                cudaStream_t s) {
     if (nb == 0) return cudaSuccess;
-    ks_decompose_kernel<<<152 * 16, 256, 0, s>>>(ct, n, L, N, c0, nb, tab, D);
+    ks_decompose_kernel<<<152 * 16, 256, 0, s>>>(ct, n, N, c0, nb, tab, g, D);
     return cudaGetLastError();
 }
 cudaError_t launch_ks_multacc(const uint64_t *D, const uint64_t *keys, const int *kid, int kper,
-                              int L, int N, int64_t c0, int64_t nb, const NttPlane *tab,
-                              uint64_t *U, cudaStream_t s, int d_shared) {
+                              const KsGadget &g, int N, int64_t c0, int64_t nb,
+                              const NttPlane *tab, uint64_t *U, cudaStream_t s, int d_shared) {
     if (nb == 0) return cudaSuccess;
     const int logN = 31 - __builtin_clz(N);
-    const int64_t total = nb * (L + 1) * N / 2;
+    const int Lp = g.L + g.K;
+    const int64_t total = nb * Lp * N / 2;
     const int64_t bx = std::min<int64_t>((total + 255) / 256, 152 * 16);
-    ks_multacc_kernel<<<static_cast<unsigned>(bx), 256, 0, s>>>(D, keys, kid, kper, L, logN, c0, nb,
-                                                                tab, U, d_shared);
+    ks_multacc_kernel<<<static_cast<unsigned>(bx), 256, 0, s>>>(D, keys, kid, kper, g.D, Lp, logN,
+                                                                c0, nb, tab, U, d_shared);
     return cudaGetLastError();
 }
-cudaError_t launch_ks_moddown(const uint64_t *U, const uint64_t *ct, int64_t n, int L, int N,
-                              int64_t c0, int64_t nb, const int *kid, int kper, int b_zero,
-                              const NttPlane *tab, const uint64_t *pinv, const uint64_t *pinv_s,
-                              uint64_t *out, int64_t n_out, cudaStream_t s) {
+cudaError_t launch_ks_moddown(const uint64_t *U, const uint64_t *ct, int64_t n, int N, int64_t c0,
+                              int64_t nb, const int *kid, int kper, int b_zero,
+                              const NttPlane *tab, const KsGadget &g, const uint64_t *pinv,
+                              const uint64_t *pinv_s, uint64_t *out, int64_t n_out,
+                              cudaStream_t s) {
     if (nb == 0) return cudaSuccess;
     const int logN = 31 - __builtin_clz(N);
     const int64_t bx = std::min<int64_t>((nb * N / 2 + 255) / 256, 152 * 8);
     ks_moddown_kernel<<<dim3(static_cast<unsigned>(bx), 2), 256, 0, s>>>(
-        U, ct, n, L, logN, c0, nb, kid, kper, b_zero, tab, pinv, pinv_s, out, n_out);
+        U, ct, n, logN, c0, nb, kid, kper, b_zero, tab, g, pinv, pinv_s, out, n_out);
     return cudaGetLastError();
 }
 

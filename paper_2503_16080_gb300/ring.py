@@ -30,7 +30,10 @@ def _register():
     P, I64, I, SZ = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_size_t
     L.modpp_ring_bytes.argtypes = [I64, I]
     L.modpp_ring_bytes.restype = SZ
+    L.modpp_ring_bytes_ks.argtypes = [I64, I, I, I]
+    L.modpp_ring_bytes_ks.restype = SZ
     L.modpp_ring_create.argtypes = [I64, I, P, P, SZ, P, P]
+    L.modpp_ring_create_ks.argtypes = [I64, I, I, I, P, P, SZ, P, P]
     L.modpp_ring_destroy.argtypes = [P]
     L.modpp_ring_prepare_keys.argtypes = [P, P, I64, P]
     L.modpp_keyswitch_workspace.argtypes = [P, I64]
@@ -60,27 +63,36 @@ def _register():
 
 
 class Ring:
-    """R_q = Z_q[X]/(X^N+1) over the chain primes[:L] with the special prime
-    primes[L] for key switching.  Holds the library's ring tables on `device`."""
+    """R_q = Z_q[X]/(X^N+1) over the chain primes[:L] with the K special
+    primes primes[L:] for key switching, whose gadget has dnum digits (default
+    K = 1, dnum = L).  Holds the library's ring tables on `device`."""
 
-    def __init__(self, N: int, primes_with_P: Sequence[int], device="cuda", stream=None):
+    def __init__(self, N: int, primes_with_P: Sequence[int], device="cuda", stream=None,
+                 special: int = 1, dnum: int | None = None):
         L = _register()
         self.N = int(N)
         self.primes = [int(q) for q in primes_with_P]
-        self.L = len(self.primes) - 1
+        self.K = int(special)
+        self.L = len(self.primes) - self.K
+        self.dnum = self.L if dnum is None else int(dnum)
         self.device = torch.device(device)
         if self.device.index is None:
             self.device = torch.device("cuda", torch.cuda.current_device())
-        nbytes = int(L.modpp_ring_bytes(self.N, self.L))
+        nbytes = int(L.modpp_ring_bytes_ks(self.N, self.L, self.K, self.dnum))
         if nbytes == 0:
-            raise ModppError(-1, "modpp_ring_bytes")
+            raise ModppError(-1, "modpp_ring_bytes_ks")
         self._mem = torch.empty(nbytes, dtype=torch.uint8, device=self.device)
         self._pr = np.ascontiguousarray(self.primes, dtype=np.uint64)
         h = ctypes.c_void_p()
-        _check(L.modpp_ring_create(self.N, self.L, self._pr.ctypes.data, self._mem.data_ptr(),
-                                   nbytes, _stream_handle(stream), ctypes.byref(h)),
-               "modpp_ring_create")
+        _check(L.modpp_ring_create_ks(self.N, self.L, self.K, self.dnum, self._pr.ctypes.data,
+                                      self._mem.data_ptr(), nbytes, _stream_handle(stream),
+                                      ctypes.byref(h)),
+               "modpp_ring_create_ks")
         self._h = h
+
+    def key_shape(self) -> tuple:
+        """Shape of one switching key: (dnum, 2, L + K, N)."""
+        return (self.dnum, 2, self.L + self.K, self.N)
 
     def close(self):
         if getattr(self, "_h", None) and self._h.value:
@@ -107,8 +119,8 @@ class Ring:
             raise TypeError(f"{name} must be a contiguous uint64 CUDA tensor")
         if k.dim() == 4:
             k = k.unsqueeze(0)
-        if tuple(k.shape[1:]) != (self.L, 2, self.L + 1, self.N):
-            raise ValueError(f"{name} must have shape (count, {self.L}, 2, {self.L + 1}, {self.N})")
+        if tuple(k.shape[1:]) != self.key_shape():
+            raise ValueError(f"{name} must have shape (count,) + {self.key_shape()}")
         return int(k.shape[0])
 
     # ------------------------------------------------------------ calls

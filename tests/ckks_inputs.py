@@ -99,11 +99,11 @@ def encrypt_shared_a(oracle_mod, M, secrets, delta, seed, primes=PR):
     return cts, m, e
 
 
-def precomp_keys(oracle_mod, secrets, U, s_new, N, seed, primes_with_P=PRP):
+def precomp_keys(oracle_mod, secrets, U, s_new, N, seed, primes_with_P=PRP, L=None, dnum=None):
     """Key k switches s'_k = sum_j U[j, k] s_j (column k of S * U) to s_new."""
     S = np.stack([np.asarray(x, dtype=np.int64) for x in secrets])      # d2 x N
     SU = (U.astype(np.int64).T @ S)                                      # d3 x N: row k = s'_k
-    return [switching_key(oracle_mod, SU[k], s_new, N, seed + k, primes_with_P)
+    return [switching_key(oracle_mod, SU[k], s_new, N, seed + k, primes_with_P, L, dnum)
             for k in range(U.shape[1])], SU
 
 

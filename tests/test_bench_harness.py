@@ -5,6 +5,7 @@ decrypt, and its decryption of the oracle's CC-MM (Alg. 8) and PC-MM outputs
 recovers the FP64 products within 2^-20 of the scale.  A planted wrong secret
 must fail the check."""
 import numpy as np
+import pytest
 import torch
 
 import bench
@@ -12,39 +13,43 @@ import ckks_inputs as C
 from paper_2503_16080_gb300 import synth
 
 
-def _ccmm_setup(n):
+def _ccmm_setup(n, K=1, dnum=None):
     L = 4
     primes = synth.ntt_primes(50, L)
-    prp = primes + synth.ntt_primes(60, 1)
-    inp = bench.ccmm_inputs(n, primes, prp, torch.device("cpu"))
+    prp = primes + synth.ntt_primes(60, K)
+    inp = bench.ccmm_inputs(n, primes, prp, torch.device("cpu"), dnum=dnum)
     return primes, prp, inp
 
 
-def test_ccmm_harness_keys_are_oracle_keys(oracle_mod):
+@pytest.mark.parametrize("K,dnum", [(1, None), (2, 2)])
+def test_ccmm_harness_keys_are_oracle_keys(oracle_mod, K, dnum):
     n = 16
-    primes, prp, inp = _ccmm_setup(n)
+    primes, prp, inp = _ccmm_setup(n, K, dnum)
     s = inp["s"].numpy()
     L = len(primes)
+    D = L if dnum is None else dnum
     for j in (1, 5, n - 1):
         key = inp["keys"][j].numpy()
         a = np.ascontiguousarray(key[:, 0])
-        # errors: b + a*s on the special prime's plane (no gadget term there), centred
+        # errors: b + a*s on a special prime's plane (no gadget term there), centred
         q = prp[L]
-        e = np.zeros((L, n), dtype=np.int64)
-        for i in range(L):
+        e = np.zeros((D, n), dtype=np.int64)
+        for i in range(D):
             v = oracle_mod.rlwe_decrypt_rows(a[i][L][None, None, :], key[i, 1, L][None, None, :],
                                              s, [q])[0, 0].astype(object)
             e[i] = np.where(v > q // 2, v - q, v).astype(np.int64)
         assert np.abs(e).max() <= 19
-        want = oracle_mod.ks_keygen(oracle_mod.aut_key_secret(s, 2 * j + 1), s, prp, a, e)
+        want = oracle_mod.ks_keygen(oracle_mod.aut_key_secret(s, 2 * j + 1), s, prp, a, e,
+                                    L=L, dnum=D)
         assert np.array_equal(key, want)
     rk = inp["rkey"][0].numpy()
-    assert rk.shape == (L, 2, L + 1, n)
+    assert rk.shape == (D, 2, L + K, n)
 
 
-def test_ccmm_harness_decrypts_oracle_product(oracle_mod):
+@pytest.mark.parametrize("K,dnum", [(1, None), (2, 2)])
+def test_ccmm_harness_decrypts_oracle_product(oracle_mod, K, dnum):
     n = 32
-    primes, prp, inp = _ccmm_setup(n)
+    primes, prp, inp = _ccmm_setup(n, K, dnum)
     ct1 = C.from_batch(inp["ct1"].numpy())
     ct2 = C.from_batch(inp["ct2"].numpy())
     keys = [None] + [inp["keys"][j].numpy() for j in range(1, n)]
