@@ -154,10 +154,14 @@ int64_t key_words(const modpp_ring_s *r) {
     return static_cast<int64_t>(r->Dg) * 2 * ks_planes(r) * r->N;
 }
 
+// Garner digits (two-prime gadget digits): one row per digit and ciphertext.
+bool ks_two_prime(const modpp_ring_s *r) { return r->g.alpha == 2; }
+
 // Ciphertexts per key-switching chunk and the chunk's scratch words.
 int64_t ks_chunk(const modpp_ring_s *r, int64_t n) {
     const int64_t Lp = ks_planes(r);
-    const int64_t per_ct = static_cast<int64_t>(r->Dg) * Lp * r->N + 2 * Lp * r->N;
+    const int64_t per_ct = static_cast<int64_t>(r->Dg) * Lp * r->N + 2 * Lp * r->N +
+                           (ks_two_prime(r) ? r->Dg * r->N : 0);
     int64_t nb = static_cast<int64_t>(ks_chunk_budget() / 8) / per_ct;
     nb = std::max<int64_t>(1, std::min(nb, n));
     return nb;
@@ -167,7 +171,8 @@ size_t ks_scratch_bytes(const modpp_ring_s *r, int64_t n) {
     const int64_t nb = ks_chunk(r, n);
     const int64_t Lp = ks_planes(r);
     return align_up(sizeof(uint64_t) * nb * r->Dg * Lp * r->N) +
-           align_up(sizeof(uint64_t) * nb * 2 * Lp * r->N);
+           align_up(sizeof(uint64_t) * nb * 2 * Lp * r->N) +
+           (ks_two_prime(r) ? align_up(sizeof(uint64_t) * nb * r->Dg * r->N) : 0);
 }
 
 // KeySwitch of ciphertexts [0, count) of a batch with plane stride n, written
@@ -183,20 +188,24 @@ int ks_run(const modpp_ring_s *r, const uint64_t *ct, int64_t n, int64_t count, 
     uint64_t *D = reinterpret_cast<uint64_t *>(scratch);
     uint64_t *U = reinterpret_cast<uint64_t *>(
         scratch + align_up(sizeof(uint64_t) * nb * r->Dg * Lp * r->N));
+    uint64_t *V = ks_two_prime(r) ? U + align_up(sizeof(uint64_t) * nb * 2 * Lp * r->N) / 8
+                                  : nullptr;
     for (int64_t c0 = 0; c0 < count; c0 += nb) {
         const int64_t m = std::min(nb, count - c0);
-        cudaError_t e;
+        cudaError_t e = cudaSuccess;
+        if (V) e = launch_ks_garner(ct, n, N, c0, m, r->tab, r->g, V, st);
+        if (e != cudaSuccess) return MODPP_ERR_CUDA;
         // One key for every ciphertext (relinearisation, modpp_keyswitch):
         // the fused kernel, whose key reads then hit L2.  One key per
         // ciphertext (the automorphisms of Alg. 4): the streaming
         // multiply-accumulate kernel reads the keys at full bandwidth.
         if (kper == 1 && ks_fused_supported(N)) {
-            e = launch_ks_fused(ct, n, N, c0, m, r->tab, r->g, keys, kid, kper, U, st);
+            e = launch_ks_fused(ct, n, N, c0, m, r->tab, r->g, V, keys, kid, kper, U, st);
         } else {
             if (ntt_fast_supported(N)) {
-                e = launch_ks_digits_ntt(ct, n, N, c0, m, r->tab, r->g, D, st);
+                e = launch_ks_digits_ntt(ct, n, N, c0, m, r->tab, r->g, V, D, st);
             } else {
-                e = launch_ks_decompose(ct, n, N, c0, m, r->tab, r->g, D, st);
+                e = launch_ks_decompose(ct, n, N, c0, m, r->tab, r->g, V, D, st);
                 if (e == cudaSuccess)
                     e = launch_ntt(D, m * r->Dg * Lp, N, 1, Lp, r->tab, false, st);
             }
@@ -803,7 +812,7 @@ int cc_mm(modpp_ring r, const uint64_t *ct1, const uint64_t *ct2, const uint64_t
 // products for a chunk of output ciphertexts, and, with the Rescale flag,
 // the unrescaled batch.
 struct PrecompLayout {
-    size_t mm = 0, dig = 0, u = 0, x = 0, total = 0;
+    size_t mm = 0, dig = 0, v = 0, u = 0, x = 0, total = 0;
     int64_t chunk = 0;
 };
 PrecompLayout precomp_layout(const modpp_ring_s *r, int64_t d2, int64_t d3, int flags) {
@@ -815,6 +824,8 @@ PrecompLayout precomp_layout(const modpp_ring_s *r, int64_t d2, int64_t d3, int 
     off = align_up(off + modpp_mm_workspace(d3, d2, N, r->primes.data(), L, MODPP_PATH_F16));
     p.dig = off;
     off = align_up(off + sizeof(uint64_t) * r->Dg * Lp * N);
+    p.v = off;  // Garner digits of the shared a-part (two-prime digits)
+    off = align_up(off + sizeof(uint64_t) * r->Dg * N);
     const int64_t per_ct = 2 * static_cast<int64_t>(Lp) * N;
     p.chunk = std::max<int64_t>(1, std::min<int64_t>(d3, static_cast<int64_t>(ks_chunk_budget() / 8) / per_ct));
     p.u = off;
@@ -870,11 +881,14 @@ int pc_mm_precomp(modpp_ring r, int64_t d2, int64_t d3, const int8_t *Ut, const 
     // products, the inverse transforms and ModDown (in place on X).
     uint64_t *D = reinterpret_cast<uint64_t *>(base + lay.dig);
     uint64_t *Ubuf = reinterpret_cast<uint64_t *>(base + lay.u);
-    cudaError_t e;
+    uint64_t *V = ks_two_prime(r) ? reinterpret_cast<uint64_t *>(base + lay.v) : nullptr;
+    cudaError_t e = cudaSuccess;
+    if (V) e = launch_ks_garner(a, 1, N, 0, 1, r->tab, r->g, V, st);
+    if (e != cudaSuccess) return MODPP_ERR_CUDA;
     if (ntt_fast_supported(N)) {
-        e = launch_ks_digits_ntt(a, 1, N, 0, 1, r->tab, r->g, D, st);
+        e = launch_ks_digits_ntt(a, 1, N, 0, 1, r->tab, r->g, V, D, st);
     } else {
-        e = launch_ks_decompose(a, 1, N, 0, 1, r->tab, r->g, D, st);
+        e = launch_ks_decompose(a, 1, N, 0, 1, r->tab, r->g, V, D, st);
         if (e == cudaSuccess) e = launch_ntt(D, r->Dg * Lp, N, 1, Lp, r->tab, false, st);
     }
     if (e != cudaSuccess) return MODPP_ERR_CUDA;

@@ -15,27 +15,30 @@ __host__ __device__ __forceinline__ int gadget_count(const KsGadget &g, int d) {
     return (hi < g.L ? hi : g.L) - d * g.alpha;
 }
 
-// Digit d of one a-part for target plane k: a0 (and a1 for a two-prime
-// digit) point to the a-part's coefficients mod q_j0 (and q_j1).
+// Garner's second mixed-radix digit of a two-prime gadget digit at one
+// coefficient: v1 = (a_j1 - a_j0) * q_j0^-1 mod q_j1, canonical, so that the
+// digit is the integer a_j0 + q_j0 * v1 in [0, q_j0 q_j1).
+__device__ __forceinline__ uint64_t garner_v1(const KsGadget &g, const NttPlane *tab, int d,
+                                              uint64_t a_j0, uint64_t a_j1) {
+    const NttPlane &t1 = tab[gadget_lo(g, d) + 1];
+    return shoup_mulmod(sub_mod(a_j1, barrett_u64(a_j0, t1.q, t1.mu), t1.q), g.ginv[d],
+                        g.ginv_s[d], t1.q);
+}
+
+// Digit d of one a-part for target plane k: a0 points to the a-part's
+// coefficients mod q_j0, v1 (two-prime digits only) to their Garner digits.
 struct DigitSrc {
-    const uint64_t *a0, *a1;  // a1 null: one-prime digit
-    uint64_t q1, mu1, ginv, ginv_s;
+    const uint64_t *a0, *v1;  // v1 null: one-prime digit
     uint64_t c, c_s;          // q_j0 mod q_k, Shoup quotient
 };
 
-__device__ __forceinline__ DigitSrc make_digit_src(const KsGadget &g, const NttPlane *tab,
-                                                   const uint64_t *a_j0, int64_t plane_stride,
-                                                   int d, int k) {
+__device__ __forceinline__ DigitSrc make_digit_src(const KsGadget &g, const uint64_t *a_j0,
+                                                   const uint64_t *v1, int d, int k) {
     DigitSrc s{};
     s.a0 = a_j0;
     if (gadget_count(g, d) == 2) {
-        const int j1 = gadget_lo(g, d) + 1;
-        s.a1 = a_j0 + plane_stride;
-        s.q1 = tab[j1].q;
-        s.mu1 = tab[j1].mu;
-        s.ginv = g.ginv[d];
-        s.ginv_s = g.ginv_s[d];
         const int Lp = g.L + g.K;
+        s.v1 = v1;
         s.c = g.cq[d * Lp + k];
         s.c_s = g.cq_s[d * Lp + k];
     }
@@ -48,11 +51,7 @@ __device__ __forceinline__ DigitSrc make_digit_src(const KsGadget &g, const NttP
 __device__ __forceinline__ uint64_t digit_at(const DigitSrc &s, int64_t j, uint64_t q, uint64_t mu,
                                              bool reduce) {
     uint64_t x = s.a0[j];
-    if (s.a1) {
-        const uint64_t v1 = shoup_mulmod(sub_mod(s.a1[j], barrett_u64(x, s.q1, s.mu1), s.q1),
-                                         s.ginv, s.ginv_s, s.q1);
-        x += shoup_lazy3(v1, s.c, s.c_s, q);
-    }
+    if (s.v1) x += shoup_lazy3(s.v1[j], s.c, s.c_s, q);
     return reduce ? barrett_u64(x, q, mu) : x;
 }
 

@@ -41,6 +41,7 @@ struct NttFastArgs {
     // stride n, modulo prime k (the gadget g).  Null: transform polys in place.
     const uint64_t *ks_ct;
     int64_t ks_n, ks_c0;
+    const uint64_t *ks_v;  // Garner digits of two-prime digits, [nb][D][N]
     KsGadget g;
 };
 
@@ -284,7 +285,8 @@ __global__ void __launch_bounds__(NttShape<E>::kMaxThreads, 1) ntt_e_kernel(NttF
         const int d = static_cast<int>(r % a.g.D);
         const int64_t c = r / a.g.D;
         gin = a.ks_ct + (static_cast<int64_t>(gadget_lo(a.g, d)) * a.ks_n + a.ks_c0 + c) * N;
-        dsrc = make_digit_src(a.g, a.tab, gin, a.ks_n * N, d, plane);
+        dsrc = make_digit_src(a.g, gin, a.ks_v ? a.ks_v + (c * a.g.D + d) * N : nullptr, d,
+                              plane);
         ds = &dsrc;
     } else {
         plane = static_cast<int>((p / a.inner) % a.nplanes);
@@ -381,6 +383,7 @@ struct KsFusedArgs {
     int N, logN;
     const NttPlane *tab;
     KsGadget g;
+    const uint64_t *V;     // Garner digits of two-prime digits, [nb][D][N]
     const uint64_t *keys;  // [count][D][2][L+K][N], prepared
     const int *kid;
     int kper;
@@ -419,7 +422,8 @@ __global__ void __launch_bounds__(NttShape<E>::kMaxThreads, 1) ks_fused_kernel(K
     for (int d = 0; d < a.g.D; ++d) {
         const uint64_t *gin =
             a.ct + (static_cast<int64_t>(gadget_lo(a.g, d)) * a.n + a.c0 + c) * N;
-        const DigitSrc ds = make_digit_src(a.g, a.tab, gin, a.n * N, d, k);
+        const DigitSrc ds =
+            make_digit_src(a.g, gin, a.V ? a.V + (c * a.g.D + d) * N : nullptr, d, k);
         MacSink mk{acc0, acc1, key + (static_cast<int64_t>(d * 2 + 0) * Lp + k) * N,
                    key + (static_cast<int64_t>(d * 2 + 1) * Lp + k) * N, tp.qinv_neg, d == 0};
 
@@ -506,10 +510,12 @@ constexpr int kKsE = 8;
 bool ks_fused_supported(int N) { return N >= 1024 && N <= 8192 && (N & (N - 1)) == 0; }
 
 cudaError_t launch_ks_fused(const uint64_t *ct, int64_t n, int N, int64_t c0, int64_t nb,
-                            const NttPlane *tab, const KsGadget &g, const uint64_t *keys,
-                            const int *kid, int kper, uint64_t *U, cudaStream_t s) {
+                            const NttPlane *tab, const KsGadget &g, const uint64_t *V,
+                            const uint64_t *keys, const int *kid, int kper, uint64_t *U,
+                            cudaStream_t s) {
     if (nb == 0) return cudaSuccess;
     KsFusedArgs a{};
+    a.V = V;
     a.ct = ct;
     a.n = n;
     a.c0 = c0;
@@ -556,8 +562,8 @@ cudaError_t launch_ntt_fast(uint64_t *polys, int64_t npolys, int N, int64_t inne
 }
 
 cudaError_t launch_ks_digits_ntt(const uint64_t *ct, int64_t n, int N, int64_t c0, int64_t nb,
-                                 const NttPlane *tab, const KsGadget &g, uint64_t *D,
-                                 cudaStream_t s) {
+                                 const NttPlane *tab, const KsGadget &g, const uint64_t *V,
+                                 uint64_t *D, cudaStream_t s) {
     if (nb == 0) return cudaSuccess;
     NttFastArgs a{};
     a.polys = D;
@@ -570,6 +576,7 @@ cudaError_t launch_ks_digits_ntt(const uint64_t *ct, int64_t n, int N, int64_t c
     a.ks_ct = ct;
     a.ks_n = n;
     a.ks_c0 = c0;
+    a.ks_v = V;
     a.g = g;
     return launch_fast<true>(a, nb * g.D * (g.L + g.K), s);
 }

@@ -66,24 +66,31 @@ cudaError_t launch_ntt(uint64_t *polys, int64_t npolys, int N, int64_t inner, in
 bool ntt_fast_supported(int N);
 cudaError_t launch_ntt_fast(uint64_t *polys, int64_t npolys, int N, int64_t inner, int nplanes,
                             const NttPlane *tab, bool inverse, cudaStream_t s);
+// Garner digits of the two-prime gadget digits of ciphertexts [c0, c0 + nb):
+// V[c][d][m] = (a_j1 - a_j0) * q_j0^-1 mod q_j1 at coefficient m (rows of
+// one-prime digits are left untouched).  Every digit source below takes V
+// (null when every digit has one prime).
+cudaError_t launch_ks_garner(const uint64_t *ct, int64_t n, int N, int64_t c0, int64_t nb,
+                             const NttPlane *tab, const KsGadget &g, uint64_t *V, cudaStream_t s);
 // Key switching's digits, NTTs, key products and inverse NTTs in one kernel
 // (1024 <= N <= 8192): U[c][part][k] = sum_d digit_d * key_d[part] mod q_k
 // (coefficients), k < L + K.
 bool ks_fused_supported(int N);
 cudaError_t launch_ks_fused(const uint64_t *ct, int64_t n, int N, int64_t c0, int64_t nb,
-                            const NttPlane *tab, const KsGadget &g, const uint64_t *keys,
-                            const int *kid, int kper, uint64_t *U, cudaStream_t s);
+                            const NttPlane *tab, const KsGadget &g, const uint64_t *V,
+                            const uint64_t *keys, const int *kid, int kper, uint64_t *U,
+                            cudaStream_t s);
 // Digits of key switching fused with their forward NTT (N >= 1024):
 // D[c][d][k] = NTT_k(digit d of the a-part of ciphertext c0 + c, mod q_k), c < nb.
 cudaError_t launch_ks_digits_ntt(const uint64_t *ct, int64_t n, int N, int64_t c0, int64_t nb,
-                                 const NttPlane *tab, const KsGadget &g, uint64_t *D,
-                                 cudaStream_t s);
+                                 const NttPlane *tab, const KsGadget &g, const uint64_t *V,
+                                 uint64_t *D, cudaStream_t s);
 cudaError_t launch_to_montgomery(uint64_t *polys, int64_t npolys, int N, int64_t inner,
                                  int nplanes, const NttPlane *tab, cudaStream_t s);
 // The digits alone (coefficients), D[c][d][k] as above.
 cudaError_t launch_ks_decompose(const uint64_t *ct, int64_t n, int N, int64_t c0, int64_t nb,
-                                const NttPlane *tab, const KsGadget &g, uint64_t *D,
-                                cudaStream_t s);
+                                const NttPlane *tab, const KsGadget &g, const uint64_t *V,
+                                uint64_t *D, cudaStream_t s);
 // kid null: ciphertext c takes key c.  d_shared: one set of digits D[0] for
 // every ciphertext (a batch sharing one a-part).
 cudaError_t launch_ks_multacc(const uint64_t *D, const uint64_t *keys, const int *kid, int kper,

@@ -119,9 +119,26 @@ cudaError_t launch_to_montgomery(uint64_t *polys, int64_t npolys, int N, int64_t
 // Digits of the a-parts of ciphertexts [c0, c0 + nb) (planes 0..L-1 of a
 // batch [2][L][n][N]): D[c][d][k] = (digit d of the a-part of ciphertext c)
 // mod q_k, k < L + K (ModUp: the digit's exact residue modulo Q_d).
+__global__ void ks_garner_kernel(const uint64_t *__restrict__ ct, int64_t n, int logN, int64_t c0,
+                                 int64_t nb, const NttPlane *__restrict__ tab, KsGadget g,
+                                 uint64_t *__restrict__ V) {
+    const int N = 1 << logN;
+    const int64_t total = (nb * g.D) << logN;
+    for (int64_t x = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; x < total;
+         x += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        const int m = static_cast<int>(x) & (N - 1);
+        const int64_t r = x >> logN;
+        const int d = static_cast<int>(r % g.D);
+        if (gadget_count(g, d) != 2) continue;
+        const int64_t c = r / g.D;
+        const uint64_t *a0 = ct + (static_cast<int64_t>(gadget_lo(g, d)) * n + c0 + c) * N + m;
+        V[x] = garner_v1(g, tab, d, a0[0], a0[n * N]);
+    }
+}
+
 __global__ void ks_decompose_kernel(const uint64_t *__restrict__ ct, int64_t n, int N, int64_t c0,
                                     int64_t nb, const NttPlane *__restrict__ tab, KsGadget g,
-                                    uint64_t *__restrict__ D) {
+                                    const uint64_t *__restrict__ V, uint64_t *__restrict__ D) {
     const int Lp = g.L + g.K;
     const int64_t total = nb * g.D * Lp * static_cast<int64_t>(N);
     for (int64_t x = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; x < total;
@@ -133,7 +150,7 @@ __global__ void ks_decompose_kernel(const uint64_t *__restrict__ ct, int64_t n, 
         const int d = static_cast<int>(r % g.D);
         const int64_t c = r / g.D;
         const uint64_t *a0 = ct + (static_cast<int64_t>(gadget_lo(g, d)) * n + c0 + c) * N;
-        const DigitSrc s = make_digit_src(g, tab, a0, n * N, d, k);
+        const DigitSrc s = make_digit_src(g, a0, V ? V + (c * g.D + d) * N : nullptr, d, k);
         D[x] = digit_at(s, m, tab[k].q, tab[k].mu, true);
     }
 }
@@ -241,11 +258,19 @@ __global__ void ks_moddown_kernel(const uint64_t *__restrict__ U, const uint64_t
     }
 }
 
-cudaError_t launch_ks_decompose(const uint64_t *ct, int64_t n, int N, int64_t c0, int64_t nb,
-                                const NttPlane *tab, const KsGadget &g, uint64_t *D,
-                                cudaStream_t s) {
+cudaError_t launch_ks_garner(const uint64_t *ct, int64_t n, int N, int64_t c0, int64_t nb,
+                             const NttPlane *tab, const KsGadget &g, uint64_t *V, cudaStream_t s) {
     if (nb == 0) return cudaSuccess;
-    ks_decompose_kernel<<<152 * 16, 256, 0, s>>>(ct, n, N, c0, nb, tab, g, D);
+    const int64_t bx = std::min<int64_t>((nb * g.D * N + 255) / 256, 152 * 16);
+    ks_garner_kernel<<<static_cast<unsigned>(bx), 256, 0, s>>>(ct, n, 31 - __builtin_clz(N), c0,
+                                                               nb, tab, g, V);
+    return cudaGetLastError();
+}
+cudaError_t launch_ks_decompose(const uint64_t *ct, int64_t n, int N, int64_t c0, int64_t nb,
+                                const NttPlane *tab, const KsGadget &g, const uint64_t *V,
+                                uint64_t *D, cudaStream_t s) {
+    if (nb == 0) return cudaSuccess;
+    ks_decompose_kernel<<<152 * 16, 256, 0, s>>>(ct, n, N, c0, nb, tab, g, V, D);
     return cudaGetLastError();
 }
 cudaError_t launch_ks_multacc(const uint64_t *D, const uint64_t *keys, const int *kid, int kper,
