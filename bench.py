@@ -52,8 +52,8 @@ WORKLOAD = ("PC-MM n=4096: U 4096x4096 int8 (N(0,1)*2^5) x row-RLWE ciphertext m
 
 
 # DRAM bytes (read + write) of one gemm_f16_kernel launch of this workload, from
-# one ncu capture of the current kernel: 1273489664 read + 792201472 written.
-GEMM_TRAFFIC_N4096 = 1273489664 + 792201472
+# one ncu capture of the current kernel: 1264641536 read + 791442432 written.
+GEMM_TRAFFIC_N4096 = 1264641536 + 791442432
 
 
 def mod_ops_per_step() -> float:
