@@ -19,6 +19,8 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cstdlib>
+#include <type_traits>
 
 #include "modarith.cuh"
 #include "ks_gadget.cuh"
@@ -585,39 +587,50 @@ cudaError_t launch_tweak_radix4(const uint64_t *in, uint64_t *out, int64_t n, in
 // 22 rotated 16-byte reads (the re-reads of a window hit in L2) and eight
 // writes per thread replace three radix-2 passes' reads and writes of the
 // batch.  All rotations stay even (8h <= N), so coefficient pairs move together.
-template <bool MI, bool MO>
-__global__ void tweak_radix8_kernel(const uint64_t *__restrict__ in, uint64_t *__restrict__ out,
-                                    int64_t n, int L, int logN, int lh,
-                                    const NttPlane *__restrict__ tab, TweakMap mp) {
+// IDX: int when a (part, prime) plane of n * N words has fewer than 2^31 of
+// them (64 registers: four CTAs of 256 threads per SM), else int64_t.
+template <bool MI, bool MO, typename IDX>
+__global__ void __launch_bounds__(256, sizeof(IDX) == 4 ? 4 : 3)
+    tweak_radix8_kernel(const uint64_t *__restrict__ in, uint64_t *__restrict__ out, int64_t n,
+                        int L, int logN, int lh, const NttPlane *__restrict__ tab, TweakMap mp) {
     const int r = blockIdx.y;  // part * L + plane
     const uint64_t q = tab[r % L].q;
     const int N = 1 << logN;
     const uint64_t *inp = in + static_cast<int64_t>(r) * n * N;
     uint64_t *outp = out + static_cast<int64_t>(r) * n * N;
-    const int64_t total = (n >> 3) << (logN - 1);  // groups of eight x coefficient pairs
-    const int64_t h_mask = (int64_t(1) << lh) - 1;
+    const IDX total = static_cast<IDX>((n >> 3) << (logN - 1));  // groups of eight x coefficient pairs
+    const IDX h_mask = (IDX(1) << lh) - 1;
+    const IDX h = IDX(1) << lh;
     const int halfN = N >> 1, quarterN = N >> 2;
-    for (int64_t w = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; w < total;
-         w += static_cast<int64_t>(gridDim.x) * blockDim.x) {
-        const int m = (static_cast<int>(w) << 1) & (N - 1);
-        const int64_t g = w >> (logN - 1);
-        const int64_t jj = g & h_mask;
-        const int64_t i0 = ((g >> lh) << (lh + 3)) + jj;
-        const int64_t h = int64_t(1) << lh;
+    for (IDX w = static_cast<IDX>(blockIdx.x * blockDim.x + threadIdx.x); w < total;
+         w += static_cast<IDX>(gridDim.x * blockDim.x)) {
+        const int m = static_cast<int>(w << 1) & (N - 1);
+        const IDX g = w >> (logN - 1);
+        const IDX jj = g & h_mask;
+        const IDX i0 = ((g >> lh) << (lh + 3)) + jj;
         const int tA = static_cast<int>(jj << (logN - lh));
         const int tB = static_cast<int>(jj << (logN - lh - 1));
         const int tC = static_cast<int>(jj << (logN - lh - 2));
         int rx[8];
-        const uint64_t *x[8];
+        const uint64_t *xs[8];
+        if constexpr (MI) {
 #pragma unroll
-        for (int k = 0; k < 8; ++k) x[k] = tw_src<MI>(inp, i0 + k * h, logN, mp, rx[k]);
+            for (int k = 0; k < 8; ++k) xs[k] = tw_src<MI>(inp, i0 + k * h, logN, mp, rx[k]);
+        } else {
+#pragma unroll
+            for (int k = 0; k < 8; ++k) rx[k] = 0;
+        }
+        auto x = [&](int k) -> const uint64_t * {
+            if constexpr (MI) return xs[k];
+            else return inp + (static_cast<std::make_unsigned_t<IDX>>(i0 + k * h) << logN);
+        };
         // z0..z3: the first two stages on x0..x3
-        const ulonglong2 a = tw_load0<MI>(x[0], m, rx[0], N, q);
-        const ulonglong2 b = tw_load<MI>(x[1], m, tA, rx[1], N, q);
-        const ulonglong2 c0 = tw_load<MI>(x[2], m, tB, rx[2], N, q);
-        const ulonglong2 c1 = tw_load<MI>(x[2], m, tB + halfN, rx[2], N, q);
-        const ulonglong2 d0 = tw_load<MI>(x[3], m, tA + tB, rx[3], N, q);
-        const ulonglong2 d1 = tw_load<MI>(x[3], m, tA + tB + halfN, rx[3], N, q);
+        const ulonglong2 a = tw_load0<MI>(x(0), m, rx[0], N, q);
+        const ulonglong2 b = tw_load<MI>(x(1), m, tA, rx[1], N, q);
+        const ulonglong2 c0 = tw_load<MI>(x(2), m, tB, rx[2], N, q);
+        const ulonglong2 c1 = tw_load<MI>(x(2), m, tB + halfN, rx[2], N, q);
+        const ulonglong2 d0 = tw_load<MI>(x(3), m, tA + tB, rx[3], N, q);
+        const ulonglong2 d1 = tw_load<MI>(x(3), m, tA + tB + halfN, rx[3], N, q);
         ulonglong2 z[4];
         {
             const uint64_t p = add_mod(a.x, b.x, q), mm = sub_mod(a.x, b.x, q);
@@ -639,10 +652,10 @@ __global__ void tweak_radix8_kernel(const uint64_t *__restrict__ in, uint64_t *_
         for (int k = 0; k < 4; ++k) {
             const int c = tC + k * quarterN;
             const int tb = (k & 1) ? tB + halfN : tB;
-            const ulonglong2 e4 = tw_load<MI>(x[4], m, c, rx[4], N, q);
-            const ulonglong2 e5 = tw_load<MI>(x[5], m, c + tA, rx[5], N, q);
-            const ulonglong2 e6 = tw_load<MI>(x[6], m, c + tb, rx[6], N, q);
-            const ulonglong2 e7 = tw_load<MI>(x[7], m, c + tA + tb, rx[7], N, q);
+            const ulonglong2 e4 = tw_load<MI>(x(4), m, c, rx[4], N, q);
+            const ulonglong2 e5 = tw_load<MI>(x(5), m, c + tA, rx[5], N, q);
+            const ulonglong2 e6 = tw_load<MI>(x(6), m, c + tb, rx[6], N, q);
+            const ulonglong2 e7 = tw_load<MI>(x(7), m, c + tA + tb, rx[7], N, q);
             // u = e4 +- e5 +- e6 +- e7 with the signs of row k
             ulonglong2 u;
             {
@@ -666,10 +679,15 @@ __global__ void tweak_radix8_kernel(const uint64_t *__restrict__ in, uint64_t *_
     }
 }
 
+// MODPP_TWEAK_WIDE_INDEX=1 takes the 64-bit-index form at every size (tests).
 template <bool MI, bool MO>
 static void tweak_radix8_go(dim3 g, cudaStream_t s, const uint64_t *in, uint64_t *out, int64_t n,
                             int L, int logN, int lh, const NttPlane *tab, const TweakMap &mp) {
-    tweak_radix8_kernel<MI, MO><<<g, 256, 0, s>>>(in, out, n, L, logN, lh, tab, mp);
+    const char *wide = std::getenv("MODPP_TWEAK_WIDE_INDEX");
+    if ((n << logN) < (int64_t(1) << 31) && !(wide && wide[0] == '1'))
+        tweak_radix8_kernel<MI, MO, int><<<g, 256, 0, s>>>(in, out, n, L, logN, lh, tab, mp);
+    else
+        tweak_radix8_kernel<MI, MO, int64_t><<<g, 256, 0, s>>>(in, out, n, L, logN, lh, tab, mp);
 }
 
 cudaError_t launch_tweak_radix8(const uint64_t *in, uint64_t *out, int64_t n, int L, int N,

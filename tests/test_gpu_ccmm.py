@@ -87,6 +87,18 @@ def test_tweak_bit_exact(oracle_mod, lib_ready, N, n):
     assert np.array_equal(C.from_batch(got), want)
 
 
+@pytest.mark.parametrize("N,n", [(256, 256), (64, 128)])
+def test_tweak_wide_index_form_bit_exact(oracle_mod, lib_ready, monkeypatch, N, n):
+    # The radix-8 passes' 64-bit-index form (planes of 2^31 words or more),
+    # forced at a small size.
+    monkeypatch.setenv("MODPP_TWEAK_WIDE_INDEX", "1")
+    R = lib_ready.Ring(N, C.PRP)
+    cts = C.rand_cts(9 * n + N, n, N, C.PR)
+    want = oracle_mod.tweak_alg(cts, C.PR) if n <= N else oracle_mod.tweak_def(cts, C.PR)
+    got = host(R.tweak(dev(C.to_batch(cts))))
+    assert np.array_equal(C.from_batch(got), want)
+
+
 @pytest.mark.parametrize("N", [16, 64])
 def test_rescale_bit_exact(oracle_mod, lib_ready, N):
     R = lib_ready.Ring(N, C.PRP)
