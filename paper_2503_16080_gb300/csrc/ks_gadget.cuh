@@ -48,10 +48,12 @@ __device__ __forceinline__ DigitSrc make_digit_src(const KsGadget &g, const uint
 // The digit at coefficient j modulo q.  Unreduced (reduce false), a
 // one-prime digit is below the largest chain prime and a two-prime digit
 // below q_j0 + 4q; reduced, the canonical residue.
+// TWO: the digit is known to have two primes (v1 present).
+template <bool TWO = false>
 __device__ __forceinline__ uint64_t digit_at(const DigitSrc &s, int64_t j, uint64_t q, uint64_t mu,
                                              bool reduce) {
     uint64_t x = s.a0[j];
-    if (s.v1) x += shoup_lazy3(s.v1[j], s.c, s.c_s, q);
+    if (TWO || s.v1) x += shoup_lazy3(s.v1[j], s.c, s.c_s, q);
     return reduce ? barrett_u64(x, q, mu) : x;
 }
 

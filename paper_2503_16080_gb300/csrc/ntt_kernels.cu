@@ -113,7 +113,9 @@ __device__ __forceinline__ uint64_t grow_inv_bound(uint64_t q, int m) {
 // index is pad_idx(j0) plus a constant of k and lu.
 __device__ __forceinline__ int pad_off(int k, int lu) { return (k << lu) + ((k << lu) >> 5); }
 
-template <int E, int S, bool FWD, bool MAC = false, bool GROW = false>
+// TWO: the first pass reads a two-prime key-switch digit through ds (its
+// Garner digits present); otherwise ds, when given, is read at run time.
+template <int E, int S, bool FWD, bool MAC = false, bool GROW = false, bool TWO = false>
 __device__ __forceinline__ void ntt_pass(uint64_t *sa, const uint64_t *gin, uint64_t *gout,
                                          bool reduce_in, int N, int logN, int lu, bool first,
                                          bool last, const PlaneRegs &pr,
@@ -132,8 +134,8 @@ __device__ __forceinline__ void ntt_pass(uint64_t *sa, const uint64_t *gin, uint
         for (int k = 0; k < W; ++k) {
             uint64_t x;
             if (first) {
-                if (ds) {
-                    x = digit_at(*ds, j0 + (k << lu), pr.q, pr.mu, reduce_in);
+                if (TWO || ds) {
+                    x = digit_at<TWO>(*ds, j0 + (k << lu), pr.q, pr.mu, reduce_in);
                 } else {
                     x = gin[j0 + (k << lu)];
                     if (reduce_in) x = barrett_u64(x, pr.q, pr.mu);
@@ -250,7 +252,8 @@ struct NttShape {
 // (N = 2^LOGN): each pass's stage count, distance and first/last role are
 // constants, so the index arithmetic of ntt_pass folds away.  Same passes
 // and arithmetic as ntt_run.
-template <int E, bool FWD, bool MAC, bool GROW, int LOGN, int PI = 0, int DONE = 0>
+template <int E, bool FWD, bool MAC, bool GROW, int LOGN, bool TWO = false, int PI = 0,
+          int DONE = 0>
 __device__ __forceinline__ void ntt_run_c(uint64_t *sa, const uint64_t *gin, uint64_t *gout,
                                           bool reduce_in, const PlaneRegs &pr, bool from_smem,
                                           const MacSink *mk, const DigitSrc *ds = nullptr) {
@@ -259,11 +262,11 @@ __device__ __forceinline__ void ntt_run_c(uint64_t *sa, const uint64_t *gin, uin
     constexpr int S = pass_stages(LOGN, PASSES, PI);
     constexpr bool LAST = DONE + S == LOGN;
     constexpr int LU = FWD ? LOGN - DONE - S : DONE;
-    ntt_pass<E, S, FWD, MAC, GROW>(sa, gin, gout, reduce_in, 1 << LOGN, LOGN, LU,
-                                   PI == 0 && !from_smem, LAST, pr, mk, ds);
+    ntt_pass<E, S, FWD, MAC, GROW, TWO && PI == 0>(sa, gin, gout, reduce_in, 1 << LOGN, LOGN, LU,
+                                                   PI == 0 && !from_smem, LAST, pr, mk, ds);
     if constexpr (!LAST)
-        ntt_run_c<E, FWD, MAC, GROW, LOGN, PI + 1, DONE + S>(sa, gin, gout, reduce_in, pr,
-                                                             from_smem, mk, ds);
+        ntt_run_c<E, FWD, MAC, GROW, LOGN, TWO, PI + 1, DONE + S>(sa, gin, gout, reduce_in, pr,
+                                                                  from_smem, mk, ds);
 }
 
 // LOGN > 0: the degree is 2^LOGN, known at compile time (ntt_run_c); 0: a.N
@@ -308,10 +311,21 @@ __global__ void __launch_bounds__(NttShape<E>::kMaxThreads, 1) ntt_e_kernel(NttF
         // digits stay below digit_bound.
         const uint64_t in_max = reduce_in ? digit_bound(a.g, pr.q) : 0;
         const bool grow = FWD ? ntt_grow_ok_fwd(pr.q, in_max, LOGN) : ntt_grow_ok_inv(pr.q, LOGN);
-        if (grow)
-            ntt_run_c<E, FWD, false, true, LOGN>(sa, gin, gout, false, pr, false, nullptr, ds);
-        else
-            ntt_run_c<E, FWD, false, false, LOGN>(sa, gin, gout, reduce_in, pr, false, nullptr, ds);
+        // One-prime digits read gin itself (a0 of the digit source).
+        if (ds && dsrc.v1) {
+            if (grow)
+                ntt_run_c<E, FWD, false, true, LOGN, true>(sa, gin, gout, false, pr, false,
+                                                           nullptr, ds);
+            else
+                ntt_run_c<E, FWD, false, false, LOGN, true>(sa, gin, gout, reduce_in, pr, false,
+                                                            nullptr, ds);
+        } else {
+            if (grow)
+                ntt_run_c<E, FWD, false, true, LOGN>(sa, gin, gout, false, pr, false, nullptr);
+            else
+                ntt_run_c<E, FWD, false, false, LOGN>(sa, gin, gout, reduce_in, pr, false,
+                                                      nullptr);
+        }
         return;
     }
     const int logN = a.logN;
@@ -428,10 +442,19 @@ __global__ void __launch_bounds__(NttShape<E>::kMaxThreads, 1) ks_fused_kernel(K
                    key + (static_cast<int64_t>(d * 2 + 1) * Lp + k) * N, tp.qinv_neg, d == 0};
 
         if constexpr (LOGN > 0) {
-            if (grow_f)  // unreduced digits
-                ntt_run_c<E, true, true, true, LOGN>(sa, gin, nullptr, false, fw, false, &mk, &ds);
-            else
-                ntt_run_c<E, true, true, false, LOGN>(sa, gin, nullptr, true, fw, false, &mk, &ds);
+            if (ds.v1) {  // two-prime digit
+                if (grow_f)  // unreduced digits
+                    ntt_run_c<E, true, true, true, LOGN, true>(sa, gin, nullptr, false, fw, false,
+                                                               &mk, &ds);
+                else
+                    ntt_run_c<E, true, true, false, LOGN, true>(sa, gin, nullptr, true, fw, false,
+                                                                &mk, &ds);
+            } else {
+                if (grow_f)
+                    ntt_run_c<E, true, true, true, LOGN>(sa, gin, nullptr, false, fw, false, &mk);
+                else
+                    ntt_run_c<E, true, true, false, LOGN>(sa, gin, nullptr, true, fw, false, &mk);
+            }
         } else {
             ntt_run<E, true, true>(sa, gin, nullptr, true, N, a.logN, fw, false, &mk, &ds);
         }
