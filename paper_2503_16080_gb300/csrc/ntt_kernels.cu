@@ -7,14 +7,18 @@
 // butterfly stages on them before the coefficients go back to shared memory;
 // the log2(N) stages are spread as evenly as possible over
 // ceil(log2(N) / log2(E)) shared-memory round trips.  The first pass reads
-// global memory and the last writes it.  Butterflies keep values lazily
-// reduced (D. Harvey, "Faster arithmetic for number-theoretic transforms",
-// J. Symb. Comp. 2014): forward values live in [0, 4q), inverse ones in
-// [0, 2q), which needs 4q < 2^64 (q < 2^62).
+// global memory and the last writes it.  For the default shapes the degree
+// is a template parameter, so the pass schedule is fixed at compile time.
+// Butterflies keep values lazily reduced: in Harvey's form (D. Harvey,
+// "Faster arithmetic for number-theoretic transforms", J. Symb. Comp. 2014)
+// forward values live in [0, 4q) and inverse ones in [0, 2q), for q < 2^62;
+// for the primes where 64-bit words have room the bounds grow instead (see
+// ntt_grow_ok_fwd / ntt_grow_ok_inv).
 //
 // The forward transform can also read its input from the a-part of a
-// ciphertext batch and reduce it modulo the target prime on the fly: the
-// digit decomposition of key switching fused into the transform.
+// ciphertext batch: the digit of key switching (ks_gadget.cuh) is formed on
+// the fly in the first pass, so the decomposition is fused into the
+// transform.
 #include <cuda_runtime.h>
 
 #include <cstdlib>
@@ -405,8 +409,8 @@ struct KsFusedArgs {
 };
 
 // Key switching's digits, products and sums for one (ciphertext, target
-// prime k) per CTA, in shared memory: for every digit i the forward
-// transform of (a_i mod q_k), multiplied in its last pass by key i (both
+// prime k) per CTA, in shared memory: for every gadget digit d the forward
+// transform of (digit d mod q_k), multiplied in its last pass by key d (both
 // parts) and summed into two accumulators; then both inverse transforms,
 // written to U.  Shared memory: three padded polynomials (N <= 8192).
 template <int E, int LOGN = 0>
