@@ -4,7 +4,8 @@ Rescale and CC-MM (Alg. 8).
 
 Argument marshalling only.  Ciphertext batches are uint64 CUDA tensors of
 shape (2, L, n, N) -- part (a, b), prime, ciphertext, coefficient -- and
-switching keys are (count, L, 2, L+1, N).  The ring tables and every
+switching keys are (count, dnum, 2, L+K, N) for the ring's gadget of dnum
+digits and K special primes (``Ring.key_shape``).  The ring tables and every
 workspace are PyTorch allocations handed to the library as device pointers.
 """
 from __future__ import annotations
@@ -252,7 +253,7 @@ class Ring:
                       workspace=None) -> torch.Tensor:
         """Alg. 7 on a shared-a encryption, then the key switches back to one
         secret: Ut (d3, d2) int8 = U^T; a (L, N) the shared a-part; B (L, d2, N)
-        the b-parts; keys (d3, L, 2, L+1, N) prepared, key k from column k of
+        the b-parts; keys (d3,) + key_shape() prepared, key k from column k of
         S*U.  Returns the batch (2, L or L-1, d3, N)."""
         if not (Ut.is_cuda and Ut.dtype == torch.int8 and Ut.dim() == 2 and Ut.is_contiguous()):
             raise TypeError("Ut must be a contiguous 2-D int8 CUDA tensor")
