@@ -122,9 +122,31 @@ def _path(path) -> int:
     return int(Path(path))
 
 
-def _primes_arr(primes: Sequence[int]) -> np.ndarray:
-    arr = np.ascontiguousarray([int(q) for q in primes], dtype=np.uint64)
-    return arr
+class _Primes:
+    """A uint64 array of primes and its address, kept alive by the cache below."""
+    __slots__ = ("arr", "data")
+
+    def __init__(self, key: tuple):
+        self.arr = np.ascontiguousarray(key, dtype=np.uint64)
+        self.data = self.arr.ctypes.data
+
+    def __len__(self) -> int:
+        return len(self.arr)
+
+
+# Prime lists seen so far: building the array and reading its address cost
+# microseconds per call, which show in the small, latency-bound products.
+_primes_cache: dict[tuple, _Primes] = {}
+
+
+def _primes_arr(primes: Sequence[int]) -> _Primes:
+    key = tuple(int(q) for q in primes)
+    hit = _primes_cache.get(key)
+    if hit is None:
+        if len(_primes_cache) > 256:
+            _primes_cache.clear()
+        hit = _primes_cache[key] = _Primes(key)
+    return hit
 
 
 def _stream_handle(stream) -> int:
@@ -170,7 +192,7 @@ def workspace_bytes(d: int, k: int, n: int, primes: Sequence[int], path="f16",
                     kind: str = "modpp_mm") -> int:
     pr = _primes_arr(primes)
     fn = lib().modpp_mm_workspace if kind == "modpp_mm" else lib().pc_mm_workspace
-    return int(fn(int(d), int(k), int(n), pr.ctypes.data, len(pr), _path(path)))
+    return int(fn(int(d), int(k), int(n), pr.data, len(pr), _path(path)))
 
 
 def last_status(device: torch.device | int | None = None, stream=None,
@@ -223,7 +245,7 @@ def wide_plan_info(k: int, primes: Sequence[int]) -> int:
     """Small primes of the CRT form for inner dimension k (0: digit form)."""
     pr = _primes_arr(primes)
     out = ctypes.c_int()
-    _check(lib().modpp_wide_plan_info(int(k), pr.ctypes.data, len(pr), ctypes.byref(out)),
+    _check(lib().modpp_wide_plan_info(int(k), pr.data, len(pr), ctypes.byref(out)),
            "modpp_wide_plan_info")
     return out.value
 
@@ -297,7 +319,7 @@ def modpp_mm(U: torch.Tensor, A: torch.Tensor, primes: Sequence[int], *, path="f
         raise ValueError("out must be (P, d, n) with unit stride along n")
     pr = _primes_arr(primes)
     p = _path(path)
-    need = int(lib().modpp_mm_workspace(d, k, n, pr.ctypes.data, P, p))
+    need = int(lib().modpp_mm_workspace(d, k, n, pr.data, P, p))
     if need == 0:
         raise ModppError(-1, "modpp_mm_workspace")
     ws_ptr, ws_len = _workspace(need, A3.device, workspace)
@@ -306,7 +328,7 @@ def modpp_mm(U: torch.Tensor, A: torch.Tensor, primes: Sequence[int], *, path="f
     lda, sa = (A3.stride(1), A3.stride(0)) if A3.numel() else (n, k * n)
     ldc, sc = (out3.stride(1), out3.stride(0)) if out3.numel() else (n, d * n)
     rc = lib().modpp_mm(d, k, n, U.data_ptr(), ukind, ldu, A3.data_ptr(), lda, sa,
-                        out3.data_ptr(), ldc, sc, pr.ctypes.data, P, p, ws_ptr, ws_len,
+                        out3.data_ptr(), ldc, sc, pr.data, P, p, ws_ptr, ws_len,
                         _stream_handle(stream))
     _check(rc, "modpp_mm")
     return out3[0] if squeeze else out3
@@ -328,7 +350,7 @@ def modpp_mm_wide(U: torch.Tensor, A: torch.Tensor, primes: Sequence[int], *,
     if out is None:
         out = torch.empty((P, d, n), dtype=torch.uint64, device=A.device)
     pr = _primes_arr(primes)
-    need = int(lib().modpp_mm_wide_workspace(d, k, n, pr.ctypes.data, P))
+    need = int(lib().modpp_mm_wide_workspace(d, k, n, pr.data, P))
     if need == 0:
         raise ModppError(-1, "modpp_mm_wide_workspace")
     ws_ptr, ws_len = _workspace(need, A.device, workspace)
@@ -336,7 +358,7 @@ def modpp_mm_wide(U: torch.Tensor, A: torch.Tensor, primes: Sequence[int], *,
     la, sa = (A.stride(1), A.stride(0)) if A.numel() else (n, k * n)
     lc, sc = (out.stride(1), out.stride(0)) if out.numel() else (n, d * n)
     _check(lib().modpp_mm_wide(d, k, n, U.data_ptr(), lu, su, A.data_ptr(), la, sa,
-                               out.data_ptr(), lc, sc, pr.ctypes.data, P, ws_ptr, ws_len,
+                               out.data_ptr(), lc, sc, pr.data, P, ws_ptr, ws_len,
                                _stream_handle(stream)), "modpp_mm_wide")
     return out
 
@@ -424,18 +446,18 @@ def _pc(fn_name: str, U, A, B, primes, path, out, stream, workspace):
         raise ValueError("outputs must be contiguous (P, d, N) tensors")
     pr = _primes_arr(primes)
     p = _path(path)
-    need = int(lib().pc_mm_workspace(d, kct, N, pr.ctypes.data, P, p))
+    need = int(lib().pc_mm_workspace(d, kct, N, pr.data, P, p))
     if need == 0:
         raise ModppError(-1, "pc_mm_workspace")
     ws_ptr, ws_len = _workspace(need, A.device, workspace)
     if prepared:
         rc = lib().pc_mm_u16(d, kct, N, U.data_ptr(), A.data_ptr(), B.data_ptr(),
-                             Aout.data_ptr(), Bout.data_ptr(), pr.ctypes.data, P, ws_ptr, ws_len,
+                             Aout.data_ptr(), Bout.data_ptr(), pr.data, P, ws_ptr, ws_len,
                              _stream_handle(stream))
         _check(rc, "pc_mm_u16")
         return Aout, Bout
     rc = getattr(lib(), fn_name)(d, kct, N, U.data_ptr(), A.data_ptr(), B.data_ptr(),
-                                 Aout.data_ptr(), Bout.data_ptr(), pr.ctypes.data, P, p, ws_ptr,
+                                 Aout.data_ptr(), Bout.data_ptr(), pr.data, P, p, ws_ptr,
                                  ws_len, _stream_handle(stream))
     _check(rc, fn_name)
     return Aout, Bout
@@ -506,7 +528,7 @@ class GroupedPlan:
             ldu = U.stride(0) if U.numel() else k
             lda, sa = (A3.stride(1), A3.stride(0)) if A3.numel() else (n, k * n)
             arr[i] = _Problem(d, k, n, U.data_ptr(), ldu, A3.data_ptr(), lda, sa,
-                              C.data_ptr(), C.stride(1), C.stride(0), pr.ctypes.data, P)
+                              C.data_ptr(), C.stride(1), C.stride(0), pr.data, P)
             dev = A3.device
         self._arr = arr
         need = int(lib().modpp_group_workspace(ctypes.byref(arr), len(problems)))

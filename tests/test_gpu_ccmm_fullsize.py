@@ -117,14 +117,16 @@ def test_cc_mm_n1024_decrypts(oracle_mod, pkg):
     ring.close()
 
 
-def test_cc_mm_n8192_real_keys_decrypts(pkg):
+@pytest.mark.parametrize("K,dnum", [(1, None), (2, 2)], ids=["one-prime-digits", "paper-dnum2"])
+def test_cc_mm_n8192_real_keys_decrypts(pkg, K, dnum):
+    # The benchmark's configuration (both key-switching gadgets).
     import bench
     N, L = 8192, 4
     primes = synth.ntt_primes(50, L)
-    prp = primes + synth.ntt_primes(60, 1)
+    prp = primes + synth.ntt_primes(60, K)
     dev = torch.device("cuda")
-    ring = pkg.Ring(N, prp)
-    inp = bench.ccmm_inputs(N, primes, prp, dev, seed=77)
+    ring = pkg.Ring(N, prp, special=K, dnum=dnum)
+    inp = bench.ccmm_inputs(N, primes, prp, dev, seed=77, dnum=dnum)
     keys = ring.prepare_keys(inp.pop("keys"))
     rkey = ring.prepare_keys(inp.pop("rkey"))
     out = ring.cc_mm(inp["ct1"], inp["ct2"], keys, rkey)
