@@ -109,7 +109,10 @@ int modpp_abi_version(void);
  * Residues are split into balanced b-bit digits, b in {8, 9, 10}; the inner
  * dimension is accumulated in exact FP32 chunks of 2^(18-b).  Narrower
  * digits mean more digit products but fewer drains of the accumulators.
- * 0 restores the default.  Returns MODPP_OK or MODPP_ERR_ARG.  Changing it
+ * 0 restores the default: 9-bit digits, and 8-bit digits for products of at
+ * most 32 output columns per plane (such thin products, PC-Mv for one, are
+ * bound by the drains).  modpp_get_digit_bits and modpp_plan_info report the
+ * width of wider products.  Returns MODPP_OK or MODPP_ERR_ARG.  Changing it
  * while calls are in flight on other threads is not supported.
  */
 int modpp_set_digit_bits(int bits);

@@ -55,6 +55,15 @@ int current_digit_bits() {
     const int b = g_digit_bits.load();
     return b == 0 ? kDefaultDigitBits : b;
 }
+// The width a product with n output columns per plane takes.  At the default,
+// thin products (n <= 32, e.g. PC-Mv) are bound by the accumulator drains,
+// not by the tensor pipe: 8-bit digits (exact FP32 chunks of 1024) halve the
+// drains for one more digit product (measured 6% faster on 16384^2 x 32).
+int digit_bits_for(int64_t n) {
+    const int b = g_digit_bits.load();
+    if (b != 0) return b;
+    return n <= 32 ? 8 : kDefaultDigitBits;
+}
 
 bool path_ok(int path) {
     return path == MODPP_PATH_F16 || path == MODPP_PATH_FP64 || path == MODPP_PATH_FP64_TIGHT;
@@ -91,7 +100,7 @@ bool use_pair(int64_t d, int64_t n) { return g_gemm_pair.load() != 0 && d >= 2 *
 F16Layout f16_layout(int64_t d, int64_t k, int64_t n, const uint64_t *qs, int planes,
                      bool pair_ok = false) {
     F16Layout lay;
-    lay.b = current_digit_bits();
+    lay.b = digit_bits_for(n);
     for (int i = 0; i < planes; ++i) {
         const int l = f16_digit_count(qs[i], lay.b);
         if (l > lay.L) lay.L = l;
