@@ -210,6 +210,20 @@ def test_ring_bytes_sizes(api):
         assert L.modpp_ring_bytes(N, Lc) == 0, (N, Lc)
 
 
+def test_ring_bytes_gadgets(api):
+    # Gadgets of dnum digits of at most two chain primes (every digit
+    # non-empty) and one or two special primes; anything else is rejected.
+    L = _ring_lib(api)
+    assert L.modpp_ring_bytes_ks(16, 3, 1, 3) == L.modpp_ring_bytes(16, 3)
+    for Lc, K, dnum in ((4, 2, 2), (3, 2, 2), (4, 2, 4), (2, 2, 1), (4, 1, 2), (16, 2, 8)):
+        assert L.modpp_ring_bytes_ks(8192, Lc, K, dnum) > 0, (Lc, K, dnum)
+    # two special primes need more table space than one
+    assert L.modpp_ring_bytes_ks(8192, 4, 2, 2) > L.modpp_ring_bytes_ks(8192, 4, 1, 2)
+    for Lc, K, dnum in ((4, 3, 2), (4, 0, 2), (4, 2, 0), (4, 2, 5), (5, 2, 2), (6, 2, 2),
+                        (4, 2, 1), (17, 2, 9)):
+        assert L.modpp_ring_bytes_ks(16, Lc, K, dnum) == 0, (Lc, K, dnum)
+
+
 def test_ring_create_validates_before_touching_memory(api):
     import ctypes
     L = _ring_lib(api)
